@@ -1,0 +1,83 @@
+"""Initial states sampled at the solution points of a quad mesh.
+
+The state array layout is ``u[e, pt, v]`` with ``pt = a + (p+1) b`` where
+``a`` indexes the 1D Gauss-Legendre node along xi and ``b`` along eta, and
+``v`` the conserved variable.  Node placement uses numpy's Gauss-Legendre
+rule and the bilinear corner interpolation of the element; this module only
+places input data and does no part of the discretisation.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+
+def sample_points(mesh, p: int) -> np.ndarray:
+    """Physical coordinates (E, (p+1)^2, 2) of the Gauss-Legendre tensor nodes."""
+    xg, _ = np.polynomial.legendre.leggauss(p + 1)
+    n = p + 1
+    xi = np.tile(xg, n)  # a fastest
+    eta = np.repeat(xg, n)
+    N = np.stack(
+        [
+            0.25 * (1 - xi) * (1 - eta),
+            0.25 * (1 + xi) * (1 - eta),
+            0.25 * (1 - xi) * (1 + eta),
+            0.25 * (1 + xi) * (1 + eta),
+        ],
+        axis=1,
+    )  # (Ns, 4)
+    return np.einsum("sk,ekd->esd", N, mesh.verts)
+
+
+def gaussian_scalar(xy: np.ndarray, center=(0.5, 0.5), alpha=50.0) -> np.ndarray:
+    """u = exp(-alpha |x - c|^2), shape (..., 1)."""
+    r2 = (xy[..., 0] - center[0]) ** 2 + (xy[..., 1] - center[1]) ** 2
+    return np.exp(-alpha * r2)[..., None]
+
+
+def isentropic_vortex(
+    xy: np.ndarray,
+    gamma=1.4,
+    mach=0.5,
+    strength=5.0,
+    center=(5.0, 5.0),
+    rho_inf=1.0,
+) -> np.ndarray:
+    """Conserved variables (rho, rho u, rho v, E) of the isentropic vortex.
+
+    Free stream: rho = rho_inf, p = rho_inf / gamma (unit sound speed),
+    velocity (mach, 0).  Tangential velocity perturbation
+    (strength / 2 pi) r exp((1 - r^2)/2) about ``center``; temperature
+    T = p / rho lowered by (gamma - 1) strength^2 / (8 gamma pi^2) exp(1 - r^2);
+    density from isentropy.
+    """
+    dx = xy[..., 0] - center[0]
+    dy = xy[..., 1] - center[1]
+    r2 = dx * dx + dy * dy
+    amp = strength / (2.0 * np.pi) * np.exp(0.5 * (1.0 - r2))
+    u = mach - amp * dy
+    v = amp * dx
+    T_inf = 1.0 / gamma
+    T = T_inf - (gamma - 1.0) * strength**2 / (8.0 * gamma * np.pi**2) * np.exp(1.0 - r2)
+    rho = rho_inf * (T / T_inf) ** (1.0 / (gamma - 1.0))
+    p = rho * T
+    E = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)
+    return np.stack([rho, rho * u, rho * v, E], axis=-1)
+
+
+def freestream(shape, gamma=1.4, mach=0.5, rho_inf=1.0, angle=0.0) -> np.ndarray:
+    """Uniform state of the given leading shape: (..., 4)."""
+    p = rho_inf / gamma
+    u = mach * np.cos(angle)
+    v = mach * np.sin(angle)
+    E = p / (gamma - 1.0) + 0.5 * rho_inf * (u * u + v * v)
+    out = np.empty(tuple(shape) + (4,))
+    out[...] = np.array([rho_inf, rho_inf * u, rho_inf * v, E])
+    return out
+
+
+def uniform_noise(shape, amplitude: float, seed: int) -> np.ndarray:
+    """Seeded U(-amplitude, amplitude) noise (numpy PCG64)."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-amplitude, amplitude, size=shape)
