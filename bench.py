@@ -1,0 +1,379 @@
+"""Implicit-stage throughput of the hybridized FR stage on GB300.
+
+One step = one hybridized implicit stage of the vortex64 workload (2D Navier-Stokes isentropic
+vortex, 64x64 quads, p = 3, 262,144 implicit DOF, SDIRK2 stage 1 at 10x the explicit CFL limit)
+solved from the standard initial guess to a relative Newton residual of 1e-8, through the C ABI
+(imex_stage stages 0 and 1).  The headline ``value`` is the mixed-precision path (FP32 element
+blocks / LU / condensation, FP64 residuals, refinement and Krylov vectors); the plain FP64 path
+is timed in the same run and reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU: replicas only (one independent stage per rank, no collective on the data path).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "HFR implicit-stage DOF/s at 1e-8 resid: mixed-prec batched vs FP64, one GB300"
+WORKLOAD = ("vortex64: 2D compressible Navier-Stokes isentropic vortex, M=0.5, gamma=1.4, Re=1e4, periodic "
+            "[0,10]^2, 64x64 quads, p=3 (blocks 64x64), SDIRK2 stage 1 at 10x explicit CFL, Newton to 1e-8")
+NEWTON_TOL = 1e-8
+GMRES_RTOL = 1e-4
+FP32_PEAK_PER_SM_CLK = 256.0  # 128 FP32 FMA lanes x 2 flops
+FP64_PEAK_PER_SM_CLK = 4.0    # 2 FP64 FMA per clock per SM (1.25 TFLOP/s at 2.07 GHz, 152 SMs)
+NUM_SMS = 152
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            return None
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def flush_l2(buf):
+    buf.add_(1.0)  # writes a buffer larger than L2 (129 MB)
+
+
+def run_stage(ctx, dt, u_n, u_stage, uhat, uhat0, R_hist):
+    uhat.copy_(uhat0)
+    ctx.imex_stage(0, dt, u_n, u_stage, uhat, R_hist, newton_tol=NEWTON_TOL, gmres_rtol=GMRES_RTOL)
+    return ctx.imex_stage(1, dt, u_n, u_stage, uhat, R_hist, newton_tol=NEWTON_TOL, newton_maxit=30,
+                          gmres_rtol=GMRES_RTOL, gmres_maxit=3000, refine=ctx.refine)
+
+
+def time_path(pkg, torch, w, precision, refine, steps, warmup, dev, l2buf):
+    ctx = pkg.Context(w.mesh, w.physics, precision=precision, tableau=pkg.FR_TAB_SDIRK2)
+    ctx.refine = refine
+    stream = torch.cuda.current_stream()
+    u_n = torch.tensor(w.u0, device=dev)
+    uhat0 = ctx.hfr_initial_trace(u_n)
+    uhat = uhat0.clone()
+    R_hist = ctx.empty(3, *ctx.state_shape)
+    u_stage = ctx.empty(*ctx.state_shape)
+    stats = None
+    for _ in range(warmup):
+        stats = run_stage(ctx, w.dt, u_n, u_stage, uhat, uhat0, R_hist)
+    torch.cuda.synchronize()
+    ctx.fr_profile_enable(True)
+    l0 = ctx.kernel_launches()
+    times = []
+    for _ in range(steps):
+        flush_l2(l2buf)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats = run_stage(ctx, w.dt, u_n, u_stage, uhat, uhat0, R_hist)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    launches = ctx.kernel_launches() - l0
+    prof = ctx.fr_profile_read()
+    ctx.fr_profile_enable(False)
+    result = {"ms": times, "stats": stats, "profile": prof, "launches": launches, "ctx": ctx,
+              "u": u_stage.clone(), "uhat0": uhat0}
+    return result
+
+
+def time_e2e(pkg, torch, ctx, w, steps, dev):
+    """Same stage through the C ABI with HOST buffers: pinned H2D of u_n and the initial trace,
+    the stage, D2H of u_stage and the trace, all inside the timed region."""
+    u_host = torch.tensor(w.u0).pin_memory()
+    uhat_host = ctx.hfr_initial_trace(torch.tensor(w.u0, device=dev)).cpu().pin_memory()
+    u_out = torch.empty_like(u_host).pin_memory()
+    uh_out = torch.empty_like(uhat_host).pin_memory()
+    u_n = torch.empty(u_host.shape, dtype=torch.float64, device=dev)
+    uhat = torch.empty(uhat_host.shape, dtype=torch.float64, device=dev)
+    R_hist = ctx.empty(3, *ctx.state_shape)
+    u_stage = ctx.empty(*ctx.state_shape)
+    stream = torch.cuda.current_stream()
+    times = []
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        u_n.copy_(u_host, non_blocking=True)
+        uhat.copy_(uhat_host, non_blocking=True)
+        ctx.imex_stage(0, w.dt, u_n, u_stage, uhat, R_hist, newton_tol=NEWTON_TOL, gmres_rtol=GMRES_RTOL)
+        ctx.imex_stage(1, w.dt, u_n, u_stage, uhat, R_hist, newton_tol=NEWTON_TOL, newton_maxit=30,
+                       gmres_rtol=GMRES_RTOL, gmres_maxit=3000, refine=ctx.refine)
+        u_out.copy_(u_stage, non_blocking=True)
+        uh_out.copy_(uhat, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(max(e0.elapsed_time(e1), (time.perf_counter() - t0) * 1e3))
+    bi = u_host.numel() * 8 + uhat_host.numel() * 8
+    bo = u_out.numel() * 8 + uh_out.numel() * 8
+    return float(np.mean(times)), bi, bo
+
+
+def cpu_baseline(threads_note=True):
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload: the stage-1
+    Newton solve of the same vortex on a 16x16 patch at the same spacing, p and time step
+    (256 elements = 1/16 of the workload), direct trace solve."""
+    from oracle.fr import Discretisation
+    from oracle.physics import make_physics
+    from oracle.stepping import TABLEAUX, newton_stage
+    from workloads import make_config
+
+    w = make_config("vortex", n=16, p=3)
+    # same element size and time step as the 64x64 workload on [0, 10]^2
+    w64 = make_config("vortex64")
+    scale = 10.0 / 64.0 / (10.0 / 16.0)
+    mesh = w.mesh
+    mesh.verts = mesh.verts * scale
+    from workloads.states import sample_points, isentropic_vortex
+
+    u0 = isentropic_vortex(sample_points(mesh, 3), center=(5.0 * scale, 5.0 * scale))
+    d = Discretisation(mesh, make_physics(w64.physics))
+    a = TABLEAUX["sdirk2"]["a"][0, 0]
+    t0 = time.perf_counter()
+    _, _, info = newton_stage(d, u0, u0, d.initial_trace(u0), a * w64.dt, tol=NEWTON_TOL)
+    el = time.perf_counter() - t0
+    dofs = mesh.nelem * 16 * 4
+    cores = _threads()
+    return {"value": dofs / el, "unit": "DOF/s", "cores": cores, "kind": "oracle",
+            "sample": f"stage-1 Newton solve (to 1e-8, {info['iterations']} iterations, direct trace solve) of the "
+                      f"vortex on a 16x16 patch at the workload's spacing, p=3, dt: {mesh.nelem} elements, "
+                      f"{dofs} DOF, {el:.1f} s"}
+
+
+def _threads():
+    try:
+        from threadpoolctl import threadpool_info
+
+        n = max((i.get("num_threads", 1) for i in threadpool_info()), default=1)
+        return int(n)
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def roofline(prof_ms, prof_cnt, w, precision_bytes, peaks, clocks):
+    """Dominant kernel of the timed step and its achieved fraction of its roof."""
+    E = w.mesh.nelem
+    nA, nT = 64, 64
+    cand = {k: prof_ms[k] / max(prof_cnt[k], 1) for k in ("condense", "jacobian")}
+    share = {k: prof_ms[k] for k in prof_ms}
+    dom = max(("condense", "jacobian", "gmres", "residual"), key=lambda k: share[k])
+    mhz = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    per_clk = FP32_PEAK_PER_SM_CLK if precision_bytes == 4 else FP64_PEAK_PER_SM_CLK
+    alu_peak = NUM_SMS * per_clk * mhz * 1e6 / 1e12  # TFLOP/s
+    if dom in ("condense", "jacobian"):
+        if dom == "condense":
+            flops = (2.0 / 3.0) * nA**3 + 2.0 * nA * nA * (nT + 1) + 2.0 * nT * nA * (nT + 1)
+        else:  # column assembly of the blocks from the line-sparse tangents: (nA+nT)^2 outputs x (2n+4) FMA
+            flops = (nA + nT) ** 2 * (2 * 4 + 4) * 2.0
+        achieved = flops * E / (cand[dom] * 1e-3) / 1e12
+        return dom, {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": achieved / alu_peak, "traffic": None,
+                     "kernel": "k_condense" if dom == "condense" else "k_jacobian",
+                     "peak_source": f"{'FP32' if precision_bytes == 4 else 'FP64'} unit count x {mhz:.0f} MHz"}
+    # HBM-bound phases: bytes of S per matvec are not separately timed here
+    return dom, None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--refine", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import torch
+
+    import paper_2401_16632_gb300 as pkg
+    from paper_2401_16632_gb300.build import build
+    from workloads import make_config
+
+    build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    w = make_config("vortex64")
+    l2buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB
+    with ClockSampler(local) as clk:
+        mixed = time_path(pkg, torch, w, pkg.FR_PREC_FP32, args.refine, args.steps, args.warmup, dev, l2buf)
+        fp64 = time_path(pkg, torch, w, pkg.FR_PREC_FP64, 0, args.steps, args.warmup, dev, l2buf)
+    clocks = clk.summary()
+    ms_mixed = float(np.mean(mixed["ms"]))
+    ms_fp64 = float(np.mean(fp64["ms"]))
+    if dist is not None:
+        t = torch.tensor([ms_mixed, ms_fp64], device=dev)
+        dist.barrier()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_mixed, ms_fp64 = float(t[0]), float(t[1])
+    dofs = w.dofs_implicit
+    # agreement of the two converged stages (same equations, same tolerance)
+    inc = (fp64["u"] - torch.tensor(w.u0, device=dev)).abs().max().item()
+    diff = (mixed["u"] - fp64["u"]).abs().max().item() / inc
+    e2e_ms, bi, bo = time_e2e(pkg, torch, mixed["ctx"], w, max(3, args.steps // 2), dev)
+    peaks, peak_src = _peaks()
+    pm = {k: v[0] for k, v in mixed["profile"].items()}
+    pc = {k: v[1] for k, v in mixed["profile"].items()}
+    dom, roof = roofline(pm, pc, w, 4, peaks, clocks)
+    line = {
+        "metric": METRIC,
+        "value": world * dofs / (ms_mixed * 1e-3),
+        "unit": "DOF/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_mixed,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "implicit_dofs": dofs, "elements": w.mesh.nelem,
+                   "newton_tol": NEWTON_TOL, "gmres_rtol": GMRES_RTOL, "refine_sweeps": args.refine,
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+        "fp64": {"value": world * dofs / (ms_fp64 * 1e-3), "ms_per_step": ms_fp64, "dtype": "f64",
+                 "newton_iterations": fp64["stats"]["newton_iterations"],
+                 "gmres_iterations": fp64["stats"]["gmres_iterations"],
+                 "phases_ms_total": {k: round(v[0], 3) for k, v in fp64["profile"].items()}},
+        "mixed_over_fp64": ms_fp64 / ms_mixed,
+        "mixed_vs_fp64_max_rel_diff": diff,
+        "newton_iterations": mixed["stats"]["newton_iterations"],
+        "gmres_iterations": mixed["stats"]["gmres_iterations"],
+        "phases_ms_total": {k: round(v, 3) for k, v in pm.items()},
+        "dominant_phase": dom,
+        "roofline": roof,
+        "e2e": {"value": world * dofs / (e2e_ms * 1e-3), "unit": "DOF/s", "h2d_bytes_per_step": bi,
+                "d2h_bytes_per_step": bo},
+        "gpu_launches": int(mixed["launches"] // max(args.steps, 1)),
+        "gpu_launches_note": "kernels of libhfr.so per timed step (mixed path)",
+        "clocks": clocks,
+        "peaks_source": peak_src,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline()
+        except Exception as exc:  # reported, never fatal
+            line["cpu_baseline"] = {"error": str(exc)}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def reference_arm(args, rank, world):
+    """The oracle (FP64 CPU, as it stands) on the host cores, on bounded samples of the same
+    workload (see cpu_baseline)."""
+    if rank != 0:
+        return
+    vals = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline()
+        if i >= args.warmup:
+            vals.append(cb["value"])
+            info = cb
+    v = float(np.mean(vals))
+    line = {
+        "metric": METRIC,
+        "value": v,
+        "unit": "DOF/s",
+        "n_gpus": 0,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 16 * 16 * 64 / v * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": WORKLOAD, "sample": "16x16 patch at the workload's spacing"},
+        "cpu_baseline": {"value": v, "unit": "DOF/s", "cores": info["cores"], "kind": "oracle",
+                         "sample": info["sample"]},
+        "e2e": {"value": v, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

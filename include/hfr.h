@@ -1,0 +1,190 @@
+/*
+ * hfr.h -- C ABI of the GB300 (sm_103a) hybridized implicit-explicit flux-reconstruction
+ * stage library.
+ *
+ * The operations follow C. A. Pereira and B. C. Vermeire, "Hybridized Implicit-Explicit Flux
+ * Reconstruction Methods", arXiv 2401.16632:
+ *   fr_residual         Sec. 2.1 eq. (freq1) and Sec. 2.2 eqs. (hfrriemann, hfr1, hfr2);
+ *                       Sec. 4 eq. (hfrimex) on implicit/explicit interface faces
+ *   hfr_local_jacobian  Sec. 3.2 eqs. (elemA, elemsystem, elemsystemB)
+ *   hfr_condense        Sec. 3.2, L^k = D^k - C^k A_k^{-1} B^k, t^k = s^k - C^k A_k^{-1} r^k
+ *   hfr_trace_gmres     Sec. 3.2, L du^ = t with L assembled by eqs. (assembly, assembly2)
+ *   hfr_backsolve       Sec. 3.2 eq. (localproblems), du_k = A_k^{-1}(r_k - B_k du^_k)
+ *   imex_stage          Sec. 3.1 eqs. (9oind, 23nffsd) inside Algorithm 1 (alg:imex) with the
+ *                       domain split of Sec. 4 (eq. explicitimex)
+ *
+ * Conventions
+ *   - Every array argument is a DEVICE pointer owned by the caller unless it is marked
+ *     "host".  The library never frees caller memory.  The library owns the workspace it
+ *     allocates in fr_ctx_create (freed by fr_ctx_destroy); no entry point allocates after
+ *     creation.
+ *   - All work is enqueued on the CUDA stream given to fr_ctx_create.  Calls that report
+ *     scalars to the host (norms, iteration counts) synchronise that stream.
+ *   - Quadrilateral meshes, tensor-product Gauss-Legendre solution points, p = 1..5.
+ *     E elements, Ns = (p+1)^2, nv variables (1 advection-diffusion, 4 Navier-Stokes),
+ *     nA = Ns nv, n = p + 1 points per face, nT = 4 n nv.
+ *   - State layout u[e][pt][v], pt = a + n b (a along xi).  Trace layout uhat[t][m][v] for the
+ *     trace faces t = 0..ntrace-1, numbered in increasing global face id (mesh face_of).
+ *   - Element-local block indices: unknown i = pt nv + v; trace unknown l = (f n + m) nv + v
+ *     over the four local faces (f: 0 xi=-1, 1 xi=+1, 2 eta=-1, 3 eta=+1).
+ *   - Implicit elements are addressed by their compact index k (increasing element id).
+ *   - Return value: FR_OK (0) or an FR_ERR_* code; fr_last_error gives details.  No entry
+ *     point aborts, traps or spins without bound.
+ */
+#ifndef HFR_H_
+#define HFR_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HFR_ABI_VERSION 1
+
+enum fr_status {
+  FR_OK = 0,
+  FR_ERR_INVALID_ARG = 1,
+  FR_ERR_CUDA = 2,
+  FR_ERR_SINGULAR = 3,      /* zero pivot in an element block or face preconditioner block */
+  FR_ERR_NOT_CONVERGED = 4, /* GMRES or Newton hit its iteration limit */
+  FR_ERR_DIVERGED = 5,      /* non-finite residual */
+  FR_ERR_TIMEOUT = 6,
+  FR_ERR_OOM = 7,
+  FR_ERR_UNSUPPORTED = 8    /* configuration outside what this build implements */
+};
+
+enum fr_physics { FR_PHYS_ADVDIFF = 0, FR_PHYS_NAVIER_STOKES = 1 };
+/* Precision of the element blocks, their LU and condensation, and the stored S^k. */
+enum fr_precision { FR_PREC_FP64 = 0, FR_PREC_FP32 = 1 };
+enum fr_tableau { FR_TAB_BE = 0, FR_TAB_SDIRK2 = 1 };
+
+typedef struct fr_ctx fr_ctx;
+
+/* Mesh description (all HOST arrays, copied by fr_ctx_create). */
+typedef struct {
+  int nelem;
+  int p;                         /* polynomial degree, 1..5 */
+  const double* verts;           /* nelem x 4 x 2 corner coordinates, corner k = a + 2b at (2a-1, 2b-1) */
+  const int* nbr;                /* nelem x 4 neighbour element across each local face (no boundary faces) */
+  const int* nbr_face;           /* nelem x 4 neighbour's local face */
+  const int* face_of;            /* nelem x 4 global face id (first-appearance numbering) */
+  const unsigned char* implicit; /* nelem: 1 = hybridized implicit, 0 = explicit FR */
+} fr_mesh_desc;
+
+typedef struct {
+  int physics;     /* fr_physics */
+  double beta[2];  /* advection velocity */
+  double nu;       /* diffusivity */
+  double gamma;    /* ratio of specific heats */
+  double mu;       /* dynamic viscosity */
+  double Pr;       /* Prandtl number */
+  double lref;     /* length in the viscous part of the hybridized stabilisation s */
+  int precision;   /* fr_precision */
+  int tableau;     /* fr_tableau: implicit DIRK + explicit partner of the IMEX pair */
+  int gmres_restart; /* m <= 64 */
+} fr_config;
+
+typedef struct {
+  int nelem, nimplicit, p, n, ns, nv, nA, nT, ntrace, nstages;
+  int has_explicit;       /* mesh has FR faces / interface faces */
+  size_t workspace_bytes; /* device memory held by the context */
+} fr_ctx_info;
+
+typedef struct {
+  int newton_iterations;
+  int gmres_iterations;   /* summed over Newton iterations */
+  double residual0;       /* ||[h; g]||_2 at the initial guess */
+  double residual;        /* final ||[h; g]||_2 */
+  int converged;
+} fr_stage_stats;
+
+typedef struct {
+  int code;
+  int element;      /* failing implicit element (compact index) or -1 */
+  int iteration;    /* failing Newton / GMRES iteration or -1 */
+  double value;     /* residual or pivot magnitude where relevant */
+  char message[160];
+} fr_error_info;
+
+/* Create a context: builds reference operators, metrics, face classification, trace numbering,
+ * and allocates all device workspace.  stream: a cudaStream_t (0 = legacy default stream).
+ * Errors: FR_ERR_INVALID_ARG (bad sizes / inconsistent connectivity), FR_ERR_UNSUPPORTED
+ * (boundary faces, p outside 1..5, combinations not compiled), FR_ERR_OOM, FR_ERR_CUDA. */
+int fr_ctx_create(const fr_mesh_desc* mesh, const fr_config* cfg, void* stream, fr_ctx** out);
+void fr_ctx_destroy(fr_ctx* ctx);
+int fr_ctx_query(const fr_ctx* ctx, fr_ctx_info* info /* host */);
+/* Physical coordinates (nelem x Ns x 2, device) of the solution points. */
+int fr_solution_points(fr_ctx* ctx, double* xy);
+
+/* Spatial residual du/dt = R(u, u^) at every element (R: nelem x nA) and, if g != NULL, the
+ * trace residual g (ntrace x n x nv) = sum over the two sides of w_q J_f F^.n (eq. hfr2).
+ * uhat may be NULL only when the mesh has no trace faces. */
+int fr_residual(fr_ctx* ctx, const double* u, const double* uhat, double* R, double* g);
+
+/* Element blocks A_k, B_k, C_k, D_k of the stage residual h = u - u* - a_dt R(u, u^) at (u, u^)
+ * for every implicit element, kept in the context (FP64 or FP32 per cfg.precision), together
+ * with the Newton right-hand sides r_k = -h_k and s_k = -g^k (FP64).  ustar: nelem x nA
+ * (NULL means u* = u). */
+int hfr_local_jacobian(fr_ctx* ctx, const double* u, const double* uhat, const double* ustar, double a_dt);
+
+/* Per implicit element: LU with partial pivoting of A_k, X = A_k^{-1}[B_k | r_k],
+ * S_k = D_k - C_k X_B, t_k = s_k - C_k x_r; assembles the global t and the face-block Jacobi
+ * preconditioner.  refine: number of FP64 refinement sweeps of x_r against the exact FP64
+ * linearisation (0 = none).  Errors: FR_ERR_SINGULAR (element in fr_last_error). */
+int hfr_condense(fr_ctx* ctx, int refine);
+
+/* Restarted right-preconditioned GMRES(m) on L du^ = t (L applied matrix-free from the S_k).
+ * duhat: ntrace x n x nv output.  Stops when the estimated ||t - L du^|| <= rtol ||t|| or after
+ * maxit inner iterations (then FR_ERR_NOT_CONVERGED, duhat holds the last iterate).
+ * iters / final_rel (host, nullable): iterations and true final relative residual. */
+int hfr_trace_gmres(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* iters, double* final_rel);
+
+/* du_k = x_r - X_B du^_k = A_k^{-1}(r_k - B_k du^_k) for every implicit element (du: nimplicit x nA,
+ * compact order), followed by `refine` FP64 refinement sweeps against the exact FP64 linearisation. */
+int hfr_backsolve(fr_ctx* ctx, const double* duhat, double* du, int refine);
+
+/* Copy a context block array to a caller device buffer (for inspection / parity tests).
+ * which: 0 A, 1 B, 2 C, 3 D, 4 S, 5 X_B, 6 x_r (FP64), 7 t_k (FP64), 8 r (FP64), 9 s (FP64),
+ * 10 global t (FP64).  Block arrays are in the context precision; dst must hold `bytes`. */
+int hfr_export(fr_ctx* ctx, int which, void* dst, size_t bytes);
+
+/* One stage of the IMEX step (Algorithm 1):
+ *   stage 0      : R_hist[0] = R(u_n, u^)                             (start of a step)
+ *   1 <= i <= s  : explicit elements u_i = u_n + dt sum_{j<=i} ahat_{i+1,j} R_hist[j-1];
+ *                  implicit elements solve u_i - u* - a_ii dt R(u_i, u^_i) = 0, g = 0 by Newton
+ *                  from u* = u_n + dt sum_{j<i} a_ij R_hist[j], updating uhat in place;
+ *                  then R_hist[i] = R(u_i, u^_i)
+ *   i = s + 1    : u_stage = u_{n+1} = u_n + dt sum_j b_j R_hist[j] (implicit elements)
+ *                                      + dt sum_j bhat_j R_hist[j-1] (explicit elements)
+ * u_n, u_stage: nelem x nA; R_hist: (s + 1) x nelem x nA.  Newton stops when
+ * ||[h; g]||_2 <= newton_tol ||[h; g]^0||_2 (FR_ERR_NOT_CONVERGED after newton_maxit).
+ * gmres_rtol / gmres_maxit: inner linear solve; refine: FP64 refinement sweeps of the local solves. */
+int imex_stage(fr_ctx* ctx, int stage, double dt, const double* u_n, double* u_stage, double* uhat,
+               double* R_hist, double newton_tol, int newton_maxit, double gmres_rtol, int gmres_maxit,
+               int refine, fr_stage_stats* stats /* host, nullable */);
+
+/* Initial trace guess: average of both sides' interpolated states (uhat: ntrace x n x nv). */
+int hfr_initial_trace(fr_ctx* ctx, const double* u, double* uhat);
+
+/* Per-phase device time of the context's calls, measured with CUDA events on its stream.
+ * Phases: 0 residual (incl. trace assembly), 1 element Jacobian blocks, 2 condensation kernel,
+ * 3 trace right-hand side + preconditioner build, 4 trace GMRES solve, 5 back-substitution and
+ * refinement, 6 Newton bookkeeping (right-hand sides, norms, updates), 7 FP64 refinement of x_r. */
+typedef struct {
+  double ms[8];
+  long long count[8];
+} fr_profile;
+/* on != 0 enables event timing (and resets the totals); off stops it. */
+int fr_profile_enable(fr_ctx* ctx, int on);
+int fr_profile_read(const fr_ctx* ctx, fr_profile* out /* host */);
+/* Number of kernels this library has launched in this process (all contexts). */
+unsigned long long fr_kernel_launches(void);
+
+int fr_last_error(const fr_ctx* ctx, fr_error_info* info /* host */);
+const char* fr_status_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HFR_H_ */

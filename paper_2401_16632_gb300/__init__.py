@@ -1,0 +1,341 @@
+"""Python binding of the GB300 hybridized IMEX flux-reconstruction stage library.
+
+Argument marshalling only: every numerical step runs in ``libhfr.so`` (CUDA, sm_103a).
+PyTorch supplies device memory and the stream.  The names mirror the C ABI in
+``include/hfr.h``.  Loading fails loudly when the library has not been built; there is no
+CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = [
+    "load_library",
+    "Context",
+    "HfrError",
+    "FR_PREC_FP64",
+    "FR_PREC_FP32",
+    "FR_TAB_BE",
+    "FR_TAB_SDIRK2",
+]
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhfr.so")
+
+FR_PREC_FP64, FR_PREC_FP32 = 0, 1
+FR_TAB_BE, FR_TAB_SDIRK2 = 0, 1
+FR_PHYS_ADVDIFF, FR_PHYS_NAVIER_STOKES = 0, 1
+EXPORT = {"A": 0, "B": 1, "C": 2, "D": 3, "S": 4, "XB": 5, "xr": 6, "t_k": 7, "r": 8, "s": 9, "t": 10}
+
+# every symbol declared in include/hfr.h
+ABI_SYMBOLS = [
+    "fr_ctx_create",
+    "fr_ctx_destroy",
+    "fr_ctx_query",
+    "fr_solution_points",
+    "fr_residual",
+    "hfr_local_jacobian",
+    "hfr_condense",
+    "hfr_trace_gmres",
+    "hfr_backsolve",
+    "hfr_export",
+    "imex_stage",
+    "hfr_initial_trace",
+    "fr_profile_enable",
+    "fr_profile_read",
+    "fr_kernel_launches",
+    "fr_last_error",
+    "fr_status_string",
+]
+
+PHASES = ["residual", "jacobian", "condense", "trace_rhs_precond", "gmres", "backsolve", "newton", "refine_xr"]
+
+
+class fr_mesh_desc(ctypes.Structure):
+    _fields_ = [
+        ("nelem", ctypes.c_int),
+        ("p", ctypes.c_int),
+        ("verts", ctypes.POINTER(ctypes.c_double)),
+        ("nbr", ctypes.POINTER(ctypes.c_int)),
+        ("nbr_face", ctypes.POINTER(ctypes.c_int)),
+        ("face_of", ctypes.POINTER(ctypes.c_int)),
+        ("implicit", ctypes.POINTER(ctypes.c_ubyte)),
+    ]
+
+
+class fr_config(ctypes.Structure):
+    _fields_ = [
+        ("physics", ctypes.c_int),
+        ("beta", ctypes.c_double * 2),
+        ("nu", ctypes.c_double),
+        ("gamma", ctypes.c_double),
+        ("mu", ctypes.c_double),
+        ("Pr", ctypes.c_double),
+        ("lref", ctypes.c_double),
+        ("precision", ctypes.c_int),
+        ("tableau", ctypes.c_int),
+        ("gmres_restart", ctypes.c_int),
+    ]
+
+
+class fr_ctx_info(ctypes.Structure):
+    _fields_ = [
+        ("nelem", ctypes.c_int),
+        ("nimplicit", ctypes.c_int),
+        ("p", ctypes.c_int),
+        ("n", ctypes.c_int),
+        ("ns", ctypes.c_int),
+        ("nv", ctypes.c_int),
+        ("nA", ctypes.c_int),
+        ("nT", ctypes.c_int),
+        ("ntrace", ctypes.c_int),
+        ("nstages", ctypes.c_int),
+        ("has_explicit", ctypes.c_int),
+        ("workspace_bytes", ctypes.c_size_t),
+    ]
+
+
+class fr_stage_stats(ctypes.Structure):
+    _fields_ = [
+        ("newton_iterations", ctypes.c_int),
+        ("gmres_iterations", ctypes.c_int),
+        ("residual0", ctypes.c_double),
+        ("residual", ctypes.c_double),
+        ("converged", ctypes.c_int),
+    ]
+
+
+class fr_profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 8), ("count", ctypes.c_longlong * 8)]
+
+
+class fr_error_info(ctypes.Structure):
+    _fields_ = [
+        ("code", ctypes.c_int),
+        ("element", ctypes.c_int),
+        ("iteration", ctypes.c_int),
+        ("value", ctypes.c_double),
+        ("message", ctypes.c_char * 160),
+    ]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libhfr.so (built by ``paper_2401_16632_gb300.build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2401_16632_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, dp, ip = ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)
+    lib.fr_ctx_create.argtypes = [ctypes.POINTER(fr_mesh_desc), ctypes.POINTER(fr_config), vp, ctypes.POINTER(vp)]
+    lib.fr_ctx_destroy.argtypes = [vp]
+    lib.fr_ctx_destroy.restype = None
+    lib.fr_ctx_query.argtypes = [vp, ctypes.POINTER(fr_ctx_info)]
+    lib.fr_solution_points.argtypes = [vp, dp]
+    lib.fr_residual.argtypes = [vp, dp, dp, dp, dp]
+    lib.hfr_local_jacobian.argtypes = [vp, dp, dp, dp, ctypes.c_double]
+    lib.hfr_condense.argtypes = [vp, ctypes.c_int]
+    lib.hfr_trace_gmres.argtypes = [vp, dp, ctypes.c_double, ctypes.c_int, ip, ctypes.POINTER(ctypes.c_double)]
+    lib.hfr_backsolve.argtypes = [vp, dp, dp, ctypes.c_int]
+    lib.hfr_export.argtypes = [vp, ctypes.c_int, dp, ctypes.c_size_t]
+    lib.imex_stage.argtypes = [vp, ctypes.c_int, ctypes.c_double, dp, dp, dp, dp, ctypes.c_double, ctypes.c_int,
+                               ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.POINTER(fr_stage_stats)]
+    lib.hfr_initial_trace.argtypes = [vp, dp, dp]
+    lib.fr_profile_enable.argtypes = [vp, ctypes.c_int]
+    lib.fr_profile_read.argtypes = [vp, ctypes.POINTER(fr_profile)]
+    lib.fr_kernel_launches.argtypes = []
+    lib.fr_kernel_launches.restype = ctypes.c_ulonglong
+    lib.fr_last_error.argtypes = [vp, ctypes.POINTER(fr_error_info)]
+    lib.fr_status_string.argtypes = [ctypes.c_int]
+    lib.fr_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+class HfrError(RuntimeError):
+    def __init__(self, code, info=None):
+        self.code = code
+        self.info = info
+        msg = load_library().fr_status_string(code).decode()
+        if info is not None:
+            msg += f" ({info.message.decode()}; element {info.element}, iteration {info.iteration}, value {info.value:g})"
+        super().__init__(msg)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+class Context:
+    """One fr_ctx on the current CUDA device and stream.
+
+    mesh: object with verts (E,4,2), nbr, nbr_face, face_of (E,4) int arrays, implicit (E,) bool
+    and p (E,) int; physics: dict (kind 'advdiff' with beta, nu or 'ns' with gamma, mu, Pr; lref).
+    """
+
+    def __init__(self, mesh, physics: dict, precision: int = FR_PREC_FP64, tableau: int = FR_TAB_SDIRK2,
+                 gmres_restart: int = 30, stream=None):
+        import torch
+
+        self.torch = torch
+        self.lib = load_library()
+        p = int(np.asarray(mesh.p).reshape(-1)[0])
+        E = int(mesh.verts.shape[0])
+        self._verts = np.ascontiguousarray(mesh.verts, dtype=np.float64)
+        self._nbr = np.ascontiguousarray(mesh.nbr, dtype=np.int32)
+        self._nbf = np.ascontiguousarray(mesh.nbr_face, dtype=np.int32)
+        self._fid = np.ascontiguousarray(mesh.face_of, dtype=np.int32)
+        self._imp = np.ascontiguousarray(mesh.implicit, dtype=np.uint8)
+        md = fr_mesh_desc(
+            E, p,
+            self._verts.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            self._nbr.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+            self._nbf.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+            self._fid.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+            self._imp.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)),
+        )
+        cfg = fr_config()
+        if physics["kind"] == "advdiff":
+            cfg.physics = FR_PHYS_ADVDIFF
+            cfg.beta[0], cfg.beta[1] = physics["beta"][0], physics["beta"][1]
+            cfg.nu = physics["nu"]
+        else:
+            cfg.physics = FR_PHYS_NAVIER_STOKES
+            cfg.gamma, cfg.mu, cfg.Pr = physics["gamma"], physics["mu"], physics["Pr"]
+        cfg.lref = physics.get("lref", 1.0)
+        cfg.precision = precision
+        cfg.tableau = tableau
+        cfg.gmres_restart = gmres_restart
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        rc = self.lib.fr_ctx_create(ctypes.byref(md), ctypes.byref(cfg), ctypes.c_void_p(self.stream.cuda_stream),
+                                    ctypes.byref(h))
+        if rc != 0:
+            raise HfrError(rc)
+        self.h = h
+        info = fr_ctx_info()
+        self.lib.fr_ctx_query(self.h, ctypes.byref(info))
+        self.info = info
+        self.precision = precision
+        self.dev = torch.device("cuda", torch.cuda.current_device())
+
+    # ----------------------------------------------------------------------- plumbing
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fr_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            info = fr_error_info()
+            self.lib.fr_last_error(self.h, ctypes.byref(info))
+            raise HfrError(rc, info)
+
+    def empty(self, *shape, dtype=None):
+        return self.torch.empty(*shape, dtype=dtype or self.torch.float64, device=self.dev)
+
+    @property
+    def trace_shape(self):
+        return (self.info.ntrace, self.info.n, self.info.nv)
+
+    @property
+    def state_shape(self):
+        return (self.info.nelem, self.info.ns, self.info.nv)
+
+    # -------------------------------------------------------------------- ABI calls
+    def solution_points(self):
+        xy = self.empty(self.info.nelem, self.info.ns, 2)
+        self._check(self.lib.fr_solution_points(self.h, _ptr(xy)))
+        return xy
+
+    def hfr_initial_trace(self, u):
+        uh = self.empty(*self.trace_shape)
+        self._check(self.lib.hfr_initial_trace(self.h, _ptr(u), _ptr(uh)))
+        return uh
+
+    def fr_residual(self, u, uhat, want_g=True):
+        R = self.empty(*self.state_shape)
+        g = self.empty(*self.trace_shape) if want_g else None
+        self._check(self.lib.fr_residual(self.h, _ptr(u), _ptr(uhat), _ptr(R), _ptr(g)))
+        return R, g
+
+    def hfr_local_jacobian(self, u, uhat, ustar, a_dt):
+        self._check(self.lib.hfr_local_jacobian(self.h, _ptr(u), _ptr(uhat), _ptr(ustar), float(a_dt)))
+
+    def hfr_condense(self, refine=0):
+        self._check(self.lib.hfr_condense(self.h, int(refine)))
+
+    def hfr_trace_gmres(self, rtol=1e-10, maxit=1000, check=True):
+        duh = self.empty(*self.trace_shape)
+        its = ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        rc = self.lib.hfr_trace_gmres(self.h, _ptr(duh), float(rtol), int(maxit), ctypes.byref(its), ctypes.byref(rel))
+        if check:
+            self._check(rc)
+        return duh, its.value, rel.value
+
+    def hfr_backsolve(self, duhat, refine=0):
+        du = self.empty(self.info.nimplicit, self.info.nA)
+        self._check(self.lib.hfr_backsolve(self.h, _ptr(duhat), _ptr(du), int(refine)))
+        return du
+
+    def hfr_export(self, which: str):
+        i = self.info
+        E, nA, nT = i.nimplicit, i.nA, i.nT
+        blk = self.torch.float64 if self.precision == FR_PREC_FP64 else self.torch.float32
+        shapes = {"A": (E, nA, nA, blk), "B": (E, nA, nT, blk), "C": (E, nT, nA, blk), "D": (E, nT, nT, blk),
+                  "S": (E, nT, nT, blk), "XB": (E, nA, nT, blk), "xr": (E, nA, self.torch.float64),
+                  "t_k": (E, nT, self.torch.float64), "r": (E, nA, self.torch.float64),
+                  "s": (E, nT, self.torch.float64), "t": (i.ntrace * i.n * i.nv, self.torch.float64)}
+        *shp, dt = shapes[which]
+        out = self.torch.empty(*shp, dtype=dt, device=self.dev)
+        self._check(self.lib.hfr_export(self.h, EXPORT[which], _ptr(out), out.numel() * out.element_size()))
+        return out
+
+    def imex_stage(self, stage, dt, u_n, u_stage, uhat, R_hist, newton_tol=1e-8, newton_maxit=20,
+                   gmres_rtol=1e-3, gmres_maxit=500, refine=0):
+        st = fr_stage_stats()
+        rc = self.lib.imex_stage(self.h, int(stage), float(dt), _ptr(u_n), _ptr(u_stage), _ptr(uhat), _ptr(R_hist),
+                                 float(newton_tol), int(newton_maxit), float(gmres_rtol), int(gmres_maxit),
+                                 int(refine), ctypes.byref(st))
+        self._check(rc)
+        return {"newton_iterations": st.newton_iterations, "gmres_iterations": st.gmres_iterations,
+                "residual0": st.residual0, "residual": st.residual, "converged": bool(st.converged)}
+
+    def fr_profile_enable(self, on=True):
+        self._check(self.lib.fr_profile_enable(self.h, 1 if on else 0))
+
+    def fr_profile_read(self):
+        pr = fr_profile()
+        self._check(self.lib.fr_profile_read(self.h, ctypes.byref(pr)))
+        return {name: (pr.ms[i], pr.count[i]) for i, name in enumerate(PHASES)}
+
+    def kernel_launches(self):
+        return int(self.lib.fr_kernel_launches())
+
+    def imex_step(self, dt, u_n, uhat, **kw):
+        """All stages of one IMEX step; returns u_{n+1} (uhat updated in place)."""
+        s = self.info.nstages
+        R_hist = self.empty(s + 1, *self.state_shape)
+        u_stage = self.empty(*self.state_shape)
+        self.imex_stage(0, dt, u_n, u_stage, uhat, R_hist, **kw)
+        stats = []
+        for i in range(1, s + 1):
+            stats.append(self.imex_stage(i, dt, u_n, u_stage, uhat, R_hist, **kw))
+        u_new = self.empty(*self.state_shape)
+        self.imex_stage(s + 1, dt, u_n, u_new, uhat, R_hist, **kw)
+        return u_new, stats

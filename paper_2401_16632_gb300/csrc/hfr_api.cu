@@ -1,0 +1,1058 @@
+// C-ABI entry points of the hybridized IMEX FR stage library (declared in include/hfr.h).
+//
+// Host side: reference operators (Gauss-Legendre nodes by Newton iteration, barycentric
+// Lagrange derivatives, DG-recovering correction lift l_i(+-1)/w_i), bilinear metrics, face
+// classification and trace numbering, workspace management, and the Newton / IMEX stage
+// driver (Pereira & Vermeire, arXiv 2401.16632, Sec. 3.1 and Algorithm 1).  Every step of the
+// numerical path runs in the CUDA kernels of this library.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <utility>
+#include <vector>
+
+#include "../../include/hfr.h"
+#include "hfr_internal.h"
+#include "hfr_krylov.h"
+
+using namespace hfr;
+
+static std::atomic<unsigned long long> g_launches(0);
+void hfr::count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+struct fr_ctx {
+  int E = 0, p = 0, n = 0, ns = 0, nv = 0, nA = 0, nT = 0, ntrace = 0, Eim = 0;
+  int prec_bytes = 8;
+  int tableau = 0;
+  int restart = 30;
+  bool need_nbr = false;
+  bool has_explicit = false;
+  cudaStream_t stream = 0;
+  RefOps ref;
+  PhysParams pp;
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+  std::vector<double> xy_host;  // solution point coordinates
+  // geometry / connectivity (device)
+  double *geo_sol = nullptr, *geo_face = nullptr;
+  int *nbr = nullptr, *nbr_face = nullptr, *kind = nullptr, *tr_of = nullptr;
+  unsigned char* implicit = nullptr;
+  int *sides_e = nullptr, *sides_c = nullptr, *imp_idx = nullptr, *tr_of_c = nullptr;
+  // residual workspace
+  double *Uf_all = nullptr, *qf_all = nullptr, *Rw = nullptr, *gview = nullptr, *gw = nullptr;
+  double *dUw = nullptr, *dRw = nullptr, *dgview = nullptr;
+  // Newton system
+  double *r = nullptr, *s = nullptr, *xr = nullptr, *te = nullptr, *tg = nullptr, *Pinv = nullptr;
+  void *A = nullptr, *B = nullptr, *C = nullptr, *D = nullptr, *LU = nullptr, *XB = nullptr, *S = nullptr;
+  int* piv = nullptr;
+  int* status = nullptr;  // [0] bits, [1] first element
+  // Krylov
+  GmresBuffers gm;
+  double *duhat = nullptr, *du = nullptr, *res_tmp = nullptr, *Ustar = nullptr, *red = nullptr;
+  // linearisation point used by the FP64 refinement (context-owned copies for the ABI call,
+  // the stage's own buffers inside imex_stage)
+  double *lin_Ubuf = nullptr, *lin_uhbuf = nullptr;
+  const double* lin_U = nullptr;
+  const double* lin_uhat = nullptr;
+  double lin_adt = 0.0;
+  fr_error_info err;
+  // per-phase event timing
+  bool prof = false;
+  std::vector<cudaEvent_t> evpool;
+  size_t evused = 0;
+  std::vector<std::pair<int, std::pair<int, int>>> pend;
+  double pms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long pcnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+enum { PH_RES = 0, PH_JAC = 1, PH_COND = 2, PH_PREC = 3, PH_GMRES = 4, PH_BACK = 5, PH_NEWTON = 6, PH_REFX = 7 };
+
+static int prof_begin(fr_ctx* ctx, int phase) {
+  if (!ctx->prof || ctx->evused + 2 > ctx->evpool.size()) return -1;
+  const int a = (int)ctx->evused++;
+  cudaEventRecord(ctx->evpool[a], ctx->stream);
+  ctx->pend.push_back({phase, {a, -1}});
+  return (int)ctx->pend.size() - 1;
+}
+static void prof_end(fr_ctx* ctx, int h) {
+  if (h < 0) return;
+  const int b = (int)ctx->evused++;
+  cudaEventRecord(ctx->evpool[b], ctx->stream);
+  ctx->pend[h].second.second = b;
+}
+// after the stream has been synchronised
+static void prof_collect(fr_ctx* ctx) {
+  for (auto& p : ctx->pend) {
+    if (p.second.second < 0) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->evpool[p.second.first], ctx->evpool[p.second.second]) == cudaSuccess) {
+      ctx->pms[p.first] += ms;
+      ctx->pcnt[p.first] += 1;
+    }
+  }
+  ctx->pend.clear();
+  ctx->evused = 0;
+}
+
+// ------------------------------------------------------------------------------ errors
+static int set_err(fr_ctx* c, int code, const char* msg, int elem = -1, int it = -1, double val = 0.0) {
+  if (c) {
+    c->err.code = code;
+    c->err.element = elem;
+    c->err.iteration = it;
+    c->err.value = val;
+    snprintf(c->err.message, sizeof(c->err.message), "%s", msg);
+  }
+  return code;
+}
+#define CK(call)                                                                            \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) return set_err(ctx, FR_ERR_CUDA, cudaGetErrorString(e_));        \
+  } while (0)
+
+// --------------------------------------------------------------------- reference element
+static void gauss_legendre_host(int n, double* x, double* w) {
+  for (int i = 0; i < n; ++i) {
+    // classic initial guess, then Newton on P_n
+    double z = cos(M_PI * (4.0 * (n - i) - 1.0) / (4.0 * n + 2.0));
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = pk;
+      }
+      double pn = n == 0 ? 1.0 : p1, pm = p0;
+      if (n == 1) { pn = z; pm = 1.0; }
+      double dp = n * (z * pn - pm) / (z * z - 1.0);
+      double dz = pn / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) {
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+        break;
+      }
+      x[i] = z;
+      w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+  }
+}
+
+static void build_ref(int p, RefOps& R) {
+  memset(&R, 0, sizeof(R));
+  const int n = p + 1;
+  double x[HFR_MAXN], w[HFR_MAXN], bw[HFR_MAXN];
+  gauss_legendre_host(n, x, w);
+  for (int j = 0; j < n; ++j) {  // barycentric weights
+    double prod = 1.0;
+    for (int k = 0; k < n; ++k)
+      if (k != j) prod *= (x[j] - x[k]);
+    bw[j] = 1.0 / prod;
+  }
+  for (int i = 0; i < n; ++i) {
+    double diag = 0.0;
+    for (int j = 0; j < n; ++j) {
+      if (i == j) continue;
+      R.D[i][j] = (bw[j] / bw[i]) / (x[i] - x[j]);
+      diag -= R.D[i][j];
+    }
+    R.D[i][i] = diag;
+  }
+  for (int side = 0; side < 2; ++side) {  // l_j(-1), l_j(+1), barycentric formula
+    const double z = side ? 1.0 : -1.0;
+    double den = 0.0;
+    for (int j = 0; j < n; ++j) den += bw[j] / (z - x[j]);
+    for (int j = 0; j < n; ++j) (side ? R.lp : R.lm)[j] = (bw[j] / (z - x[j])) / den;
+  }
+  for (int i = 0; i < n; ++i) {
+    R.w[i] = w[i];
+    R.dgL[i] = -R.lm[i] / w[i];
+    R.dgR[i] = R.lp[i] / w[i];
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) R.M[i][j] = R.D[i][j] - R.dgL[i] * R.lm[j] - R.dgR[i] * R.lp[j];
+}
+
+// bilinear map derivatives at reference point (xi, eta)
+static void bilinear(const double* V, double xi, double eta, double* J, double S[2][2], double* xy) {
+  const double sa[4] = {-1, 1, -1, 1}, sb[4] = {-1, -1, 1, 1};
+  double xx = 0, xe = 0, yx = 0, ye = 0, px = 0, py = 0;
+  for (int k = 0; k < 4; ++k) {
+    const double dNx = 0.25 * sa[k] * (1 + sb[k] * eta), dNe = 0.25 * sb[k] * (1 + sa[k] * xi);
+    const double Nk = 0.25 * (1 + sa[k] * xi) * (1 + sb[k] * eta);
+    xx += dNx * V[2 * k];
+    yx += dNx * V[2 * k + 1];
+    xe += dNe * V[2 * k];
+    ye += dNe * V[2 * k + 1];
+    px += Nk * V[2 * k];
+    py += Nk * V[2 * k + 1];
+  }
+  *J = xx * ye - xe * yx;
+  S[0][0] = ye;
+  S[0][1] = -xe;
+  S[1][0] = -yx;
+  S[1][1] = xx;
+  if (xy) { xy[0] = px; xy[1] = py; }
+}
+
+template <typename T>
+static T* dalloc(fr_ctx* c, size_t count, int* rc) {
+  if (count == 0) count = 1;
+  void* p = nullptr;
+  if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+    *rc = FR_ERR_OOM;
+    return nullptr;
+  }
+  c->allocs.push_back(p);
+  c->bytes += count * sizeof(T);
+  return (T*)p;
+}
+
+// ------------------------------------------------------------------------ small kernels
+__global__ void k_form_rhs(int Eim, int nA, int nT, const int* __restrict__ imp_idx, const double* __restrict__ U,
+                           const double* __restrict__ Ustar, const double* __restrict__ R,
+                           const double* __restrict__ gview, double adt, double* __restrict__ r,
+                           double* __restrict__ s) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t nr = (size_t)Eim * nA, ns = (size_t)Eim * nT;
+  if (i < nr) {
+    const int k = (int)(i / nA), q = (int)(i % nA);
+    const size_t ix = (size_t)imp_idx[k] * nA + q;
+    const double us = Ustar ? Ustar[ix] : U[ix];
+    r[i] = -(U[ix] - us - adt * R[ix]);
+  } else if (i < nr + ns) {
+    const size_t j = i - nr;
+    const int k = (int)(j / nT), q = (int)(j % nT);
+    s[j] = -gview[(size_t)imp_idx[k] * nT + q];
+  }
+}
+
+// deterministic sum of squares of two vectors: partials then final
+__global__ void k_sumsq_part(const double* __restrict__ a, size_t na, const double* __restrict__ b, size_t nb,
+                             double* __restrict__ partial) {
+  __shared__ double red[8];
+  double s = 0.0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < na + nb; x += stride) {
+    const double v = x < na ? a[x] : b[x - na];
+    s += v * v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    partial[blockIdx.x] = t;
+  }
+}
+__global__ void k_sumsq_final(const double* __restrict__ partial, int nblk, double* out) {
+  if (threadIdx.x != 0) return;
+  double t = 0.0;
+  for (int i = 0; i < nblk; ++i) t += partial[i];
+  *out = t;
+}
+
+__global__ void k_apply_du(int Eim, int nA, const int* __restrict__ imp_idx, const double* __restrict__ du,
+                           double* __restrict__ U) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)Eim * nA) return;
+  const int k = (int)(i / nA), q = (int)(i % nA);
+  U[(size_t)imp_idx[k] * nA + q] += du[i];
+}
+__global__ void k_scatter_du(int Eim, int nA, const int* __restrict__ imp_idx, const double* __restrict__ du,
+                             double* __restrict__ full) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)Eim * nA) return;
+  const int k = (int)(i / nA), q = (int)(i % nA);
+  full[(size_t)imp_idx[k] * nA + q] = du[i];
+}
+__global__ void k_axpy(size_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] += a * x[i];
+}
+// refinement residual: res_k = r_k - (du_k - adt dR_k)    (dR = JVP of R at the linearisation point)
+__global__ void k_refine_res(int Eim, int nA, const int* __restrict__ imp_idx, const double* __restrict__ r,
+                             const double* __restrict__ du, const double* __restrict__ dR, double adt,
+                             double* __restrict__ res) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)Eim * nA) return;
+  const int k = (int)(i / nA), q = (int)(i % nA);
+  res[i] = r[i] - (du[i] - adt * dR[(size_t)imp_idx[k] * nA + q]);
+}
+
+struct StageCoef {
+  int nterm;
+  double ci[8];  // coefficients for implicit elements (dt included)
+  double ce[8];  // coefficients for explicit elements
+  int hi[8];     // history index per term
+};
+// out = base + sum_j c_j R_hist[h_j]   (per element class)
+__global__ void k_stage_combine(int E, int nA, const unsigned char* __restrict__ implicit,
+                                const double* __restrict__ base, const double* __restrict__ Rh, StageCoef sc,
+                                double* __restrict__ out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t tot = (size_t)E * nA;
+  if (i >= tot) return;
+  const bool im = implicit[i / nA] != 0;
+  double v = base[i];
+  for (int j = 0; j < sc.nterm; ++j) {
+    const double c = im ? sc.ci[j] : sc.ce[j];
+    if (c != 0.0) v += c * Rh[(size_t)sc.hi[j] * tot + i];
+  }
+  out[i] = v;
+}
+__global__ void k_copy_implicit(int E, int nA, const unsigned char* __restrict__ implicit, int want_implicit,
+                                const double* __restrict__ src, double* __restrict__ dst) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)E * nA) return;
+  if ((implicit[i / nA] != 0) == (want_implicit != 0)) dst[i] = src[i];
+}
+__global__ void k_initial_trace(int ntrace, int npf, int NF_npf, const int* __restrict__ sides,
+                                const double* __restrict__ Uf, double* __restrict__ uhat) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ntrace * npf) return;
+  const int t = i / npf, k = i % npf;
+  const int e0 = sides[t * 4], f0 = sides[t * 4 + 1], e1 = sides[t * 4 + 2], f1 = sides[t * 4 + 3];
+  const int fpn = NF_npf / 4;
+  double v = Uf[(size_t)e0 * NF_npf + f0 * fpn + k];
+  if (e1 >= 0) v = 0.5 * (v + Uf[(size_t)e1 * NF_npf + f1 * fpn + k]);
+  uhat[i] = v;
+}
+
+static inline unsigned nblk(size_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// ------------------------------------------------------------------------ context
+extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, const fr_config* cfg, void* stream, fr_ctx** out) {
+  if (!mesh || !cfg || !out) return FR_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (mesh->nelem <= 0 || !mesh->verts || !mesh->nbr || !mesh->nbr_face || !mesh->face_of || !mesh->implicit)
+    return FR_ERR_INVALID_ARG;
+  if (mesh->p < 1 || mesh->p > 5) return FR_ERR_UNSUPPORTED;
+  if (cfg->physics == FR_PHYS_ADVDIFF && mesh->p > 3) return FR_ERR_UNSUPPORTED;
+  if (cfg->physics == FR_PHYS_NAVIER_STOKES && mesh->p < 2) return FR_ERR_UNSUPPORTED;
+  if (cfg->physics != FR_PHYS_ADVDIFF && cfg->physics != FR_PHYS_NAVIER_STOKES) return FR_ERR_INVALID_ARG;
+  if (cfg->precision != FR_PREC_FP64 && cfg->precision != FR_PREC_FP32) return FR_ERR_INVALID_ARG;
+  fr_ctx* ctx = new fr_ctx();
+  memset(&ctx->err, 0, sizeof(ctx->err));
+  ctx->stream = (cudaStream_t)stream;
+  ctx->E = mesh->nelem;
+  ctx->p = mesh->p;
+  ctx->n = mesh->p + 1;
+  ctx->ns = ctx->n * ctx->n;
+  ctx->nv = cfg->physics == FR_PHYS_ADVDIFF ? 1 : 4;
+  ctx->nA = ctx->ns * ctx->nv;
+  ctx->nT = 4 * ctx->n * ctx->nv;
+  ctx->prec_bytes = cfg->precision == FR_PREC_FP64 ? 8 : 4;
+  ctx->tableau = cfg->tableau;
+  ctx->restart = cfg->gmres_restart > 0 ? std::min(cfg->gmres_restart, GM_MAXM) : 30;
+  memset(&ctx->pp, 0, sizeof(ctx->pp));
+  ctx->pp.kind = cfg->physics;
+  ctx->pp.beta[0] = cfg->beta[0];
+  ctx->pp.beta[1] = cfg->beta[1];
+  ctx->pp.nu = cfg->nu;
+  ctx->pp.gamma = cfg->gamma;
+  ctx->pp.mu = cfg->mu;
+  ctx->pp.Pr = cfg->Pr;
+  ctx->pp.lref = cfg->lref > 0 ? cfg->lref : 1.0;
+  build_ref(ctx->p, ctx->ref);
+
+  const int E = ctx->E, n = ctx->n, ns = ctx->ns, NF = 4 * n;
+  // connectivity checks and face kinds
+  std::vector<int> kind(4 * E), tr_of(4 * E, -1);
+  int max_fid = -1;
+  for (int e = 0; e < E; ++e)
+    for (int f = 0; f < 4; ++f) {
+      const int nb = mesh->nbr[4 * e + f], nf = mesh->nbr_face[4 * e + f];
+      if (nb < 0) {
+        delete ctx;
+        return FR_ERR_UNSUPPORTED;  // boundary faces are not implemented
+      }
+      if (nb >= E || nf < 0 || nf > 3 || mesh->nbr[4 * nb + nf] != e || mesh->face_of[4 * nb + nf] != mesh->face_of[4 * e + f]) {
+        delete ctx;
+        return FR_ERR_INVALID_ARG;
+      }
+      const bool ie = mesh->implicit[e] != 0, in = mesh->implicit[nb] != 0;
+      kind[4 * e + f] = (ie && in) ? FK_TRACE : (ie != in ? FK_IMEX : FK_FR);
+      if (kind[4 * e + f] != FK_TRACE) ctx->need_nbr = true;
+      max_fid = std::max(max_fid, mesh->face_of[4 * e + f]);
+    }
+  ctx->has_explicit = ctx->need_nbr;
+  // trace numbering: trace faces in increasing global face id
+  std::vector<int> tr_of_fid(max_fid + 1, -1);
+  for (int e = 0; e < E; ++e)
+    for (int f = 0; f < 4; ++f)
+      if (kind[4 * e + f] == FK_TRACE) tr_of_fid[mesh->face_of[4 * e + f]] = 0;
+  int nt = 0;
+  for (int i = 0; i <= max_fid; ++i)
+    if (tr_of_fid[i] == 0) tr_of_fid[i] = nt++;
+  ctx->ntrace = nt;
+  std::vector<int> imp_idx, comp(E, -1);
+  for (int e = 0; e < E; ++e)
+    if (mesh->implicit[e]) {
+      comp[e] = (int)imp_idx.size();
+      imp_idx.push_back(e);
+    }
+  ctx->Eim = (int)imp_idx.size();
+  std::vector<int> sides_e(4 * std::max(nt, 1), -1), sides_c(4 * std::max(nt, 1), -1), tr_of_c(4 * std::max(ctx->Eim, 1), -1);
+  for (int e = 0; e < E; ++e)
+    for (int f = 0; f < 4; ++f)
+      if (kind[4 * e + f] == FK_TRACE) {
+        const int t = tr_of_fid[mesh->face_of[4 * e + f]];
+        tr_of[4 * e + f] = t;
+        const int slot = sides_e[4 * t] < 0 ? 0 : 1;
+        sides_e[4 * t + 2 * slot] = e;
+        sides_e[4 * t + 2 * slot + 1] = f;
+        sides_c[4 * t + 2 * slot] = comp[e];
+        sides_c[4 * t + 2 * slot + 1] = f;
+        tr_of_c[4 * comp[e] + f] = t;
+      }
+  // geometry
+  std::vector<double> gsol((size_t)E * ns * 5), gface((size_t)E * NF * 3);
+  ctx->xy_host.resize((size_t)E * ns * 2);
+  double xg[HFR_MAXN], wg[HFR_MAXN];
+  gauss_legendre_host(n, xg, wg);
+  for (int e = 0; e < E; ++e) {
+    const double* V = mesh->verts + (size_t)e * 8;
+    for (int b = 0; b < n; ++b)
+      for (int a = 0; a < n; ++a) {
+        const int pt = a + n * b;
+        double J, S[2][2];
+        bilinear(V, xg[a], xg[b], &J, S, &ctx->xy_host[((size_t)e * ns + pt) * 2]);
+        double* G = &gsol[((size_t)e * ns + pt) * 5];
+        G[0] = 1.0 / J;
+        G[1] = S[0][0];
+        G[2] = S[0][1];
+        G[3] = S[1][0];
+        G[4] = S[1][1];
+      }
+    for (int f = 0; f < 4; ++f) {
+      const int r = f >> 1;
+      const double sg = (f & 1) ? 1.0 : -1.0;
+      for (int m = 0; m < n; ++m) {
+        const double xi = r == 0 ? sg : xg[m], eta = r == 0 ? xg[m] : sg;
+        double J, S[2][2];
+        bilinear(V, xi, eta, &J, S, nullptr);
+        const double N0 = sg * S[r][0], N1 = sg * S[r][1];
+        const double Jf = sqrt(N0 * N0 + N1 * N1);
+        double* G = &gface[((size_t)e * NF + f * n + m) * 3];
+        G[0] = Jf;
+        G[1] = N0 / Jf;
+        G[2] = N1 / Jf;
+      }
+    }
+  }
+  // device allocations
+  int rc = FR_OK;
+  const int nv = ctx->nv, nA = ctx->nA, nT = ctx->nT, Eim = ctx->Eim;
+  const size_t nh = (size_t)nt * n * nv;
+  const size_t pb = ctx->prec_bytes;
+  ctx->geo_sol = dalloc<double>(ctx, gsol.size(), &rc);
+  ctx->geo_face = dalloc<double>(ctx, gface.size(), &rc);
+  ctx->nbr = dalloc<int>(ctx, 4 * E, &rc);
+  ctx->nbr_face = dalloc<int>(ctx, 4 * E, &rc);
+  ctx->kind = dalloc<int>(ctx, 4 * E, &rc);
+  ctx->tr_of = dalloc<int>(ctx, 4 * E, &rc);
+  ctx->implicit = dalloc<unsigned char>(ctx, E, &rc);
+  ctx->sides_e = dalloc<int>(ctx, sides_e.size(), &rc);
+  ctx->sides_c = dalloc<int>(ctx, sides_c.size(), &rc);
+  ctx->imp_idx = dalloc<int>(ctx, std::max(Eim, 1), &rc);
+  ctx->tr_of_c = dalloc<int>(ctx, tr_of_c.size(), &rc);
+  if (ctx->need_nbr) {
+    ctx->Uf_all = dalloc<double>(ctx, (size_t)E * NF * nv, &rc);
+    ctx->qf_all = dalloc<double>(ctx, (size_t)E * NF * 2 * nv, &rc);
+  }
+  ctx->Rw = dalloc<double>(ctx, (size_t)E * nA, &rc);
+  ctx->gview = dalloc<double>(ctx, (size_t)E * NF * nv, &rc);
+  ctx->gw = dalloc<double>(ctx, nh, &rc);
+  ctx->dUw = dalloc<double>(ctx, (size_t)E * nA, &rc);
+  ctx->dRw = dalloc<double>(ctx, (size_t)E * nA, &rc);
+  ctx->dgview = dalloc<double>(ctx, (size_t)E * NF * nv, &rc);
+  ctx->r = dalloc<double>(ctx, (size_t)Eim * nA, &rc);
+  ctx->s = dalloc<double>(ctx, (size_t)Eim * nT, &rc);
+  ctx->xr = dalloc<double>(ctx, (size_t)Eim * nA, &rc);
+  ctx->te = dalloc<double>(ctx, (size_t)Eim * nT, &rc);
+  ctx->tg = dalloc<double>(ctx, nh, &rc);
+  ctx->Pinv = dalloc<double>(ctx, (size_t)nt * (n * nv) * (n * nv), &rc);
+  ctx->A = dalloc<unsigned char>(ctx, (size_t)Eim * nA * nA * pb, &rc);
+  ctx->B = dalloc<unsigned char>(ctx, (size_t)Eim * nA * nT * pb, &rc);
+  ctx->C = dalloc<unsigned char>(ctx, (size_t)Eim * nT * nA * pb, &rc);
+  ctx->D = dalloc<unsigned char>(ctx, (size_t)Eim * nT * nT * pb, &rc);
+  ctx->LU = dalloc<unsigned char>(ctx, (size_t)Eim * nA * nA * pb, &rc);
+  ctx->XB = dalloc<unsigned char>(ctx, (size_t)Eim * nA * nT * pb, &rc);
+  ctx->S = dalloc<unsigned char>(ctx, (size_t)Eim * nT * nT * pb, &rc);
+  ctx->piv = dalloc<int>(ctx, (size_t)Eim * nA, &rc);
+  ctx->status = dalloc<int>(ctx, 2, &rc);
+  ctx->gm.n = nh;
+  ctx->gm.V = dalloc<double>(ctx, (size_t)(GM_MAXM + 1) * std::max(nh, (size_t)1), &rc);
+  ctx->gm.Z = dalloc<double>(ctx, (size_t)GM_MAXM * std::max(nh, (size_t)1), &rc);
+  ctx->gm.partial = dalloc<double>(ctx, (size_t)GM_NBLK * (GM_MAXM + 1), &rc);
+  ctx->gm.state = dalloc<GmresState>(ctx, 1, &rc);
+  ctx->duhat = dalloc<double>(ctx, nh, &rc);
+  ctx->du = dalloc<double>(ctx, (size_t)Eim * nA, &rc);
+  ctx->res_tmp = dalloc<double>(ctx, (size_t)Eim * nA, &rc);
+  ctx->Ustar = dalloc<double>(ctx, (size_t)E * nA, &rc);
+  ctx->lin_Ubuf = dalloc<double>(ctx, (size_t)E * nA, &rc);
+  ctx->lin_uhbuf = dalloc<double>(ctx, std::max(nh, (size_t)1), &rc);
+  ctx->red = dalloc<double>(ctx, 1024 + 8, &rc);
+  if (rc != FR_OK) {
+    fr_ctx_destroy(ctx);
+    return rc;
+  }
+  cudaStream_t st = ctx->stream;
+  std::vector<unsigned char> impv(mesh->implicit, mesh->implicit + E);
+#define UP(dst, src, cnt)                                                                             \
+  if (cudaMemcpyAsync(dst, src, (cnt) * sizeof(*(src)), cudaMemcpyHostToDevice, st) != cudaSuccess) { \
+    fr_ctx_destroy(ctx);                                                                              \
+    return FR_ERR_CUDA;                                                                               \
+  }
+  UP(ctx->geo_sol, gsol.data(), gsol.size());
+  UP(ctx->geo_face, gface.data(), gface.size());
+  UP(ctx->nbr, mesh->nbr, 4 * E);
+  UP(ctx->nbr_face, mesh->nbr_face, 4 * E);
+  UP(ctx->kind, kind.data(), 4 * E);
+  UP(ctx->tr_of, tr_of.data(), 4 * E);
+  UP(ctx->implicit, impv.data(), E);
+  UP(ctx->sides_e, sides_e.data(), sides_e.size());
+  UP(ctx->sides_c, sides_c.data(), sides_c.size());
+  if (Eim) UP(ctx->imp_idx, imp_idx.data(), Eim);
+  UP(ctx->tr_of_c, tr_of_c.data(), tr_of_c.size());
+#undef UP
+  if (cudaMemsetAsync(ctx->status, 0, 2 * sizeof(int), st) != cudaSuccess ||
+      cudaMemsetAsync(ctx->dUw, 0, (size_t)E * nA * sizeof(double), st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    fr_ctx_destroy(ctx);
+    return FR_ERR_CUDA;
+  }
+  *out = ctx;
+  return FR_OK;
+}
+
+extern "C" void fr_ctx_destroy(fr_ctx* ctx) {
+  if (!ctx) return;
+  for (void* p : ctx->allocs) cudaFree(p);
+  for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
+  delete ctx;
+}
+
+extern "C" int fr_ctx_query(const fr_ctx* ctx, fr_ctx_info* info) {
+  if (!ctx || !info) return FR_ERR_INVALID_ARG;
+  info->nelem = ctx->E;
+  info->nimplicit = ctx->Eim;
+  info->p = ctx->p;
+  info->n = ctx->n;
+  info->ns = ctx->ns;
+  info->nv = ctx->nv;
+  info->nA = ctx->nA;
+  info->nT = ctx->nT;
+  info->ntrace = ctx->ntrace;
+  info->nstages = ctx->tableau == FR_TAB_SDIRK2 ? 2 : 1;
+  info->has_explicit = ctx->has_explicit ? 1 : 0;
+  info->workspace_bytes = ctx->bytes;
+  return FR_OK;
+}
+
+extern "C" int fr_solution_points(fr_ctx* ctx, double* xy) {
+  if (!ctx || !xy) return FR_ERR_INVALID_ARG;
+  CK(cudaMemcpyAsync(xy, ctx->xy_host.data(), ctx->xy_host.size() * sizeof(double), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FR_OK;
+}
+
+static ResArgs res_args(fr_ctx* ctx, const double* u, const double* uhat) {
+  ResArgs a;
+  memset(&a, 0, sizeof(a));
+  a.E = ctx->E;
+  a.U = u;
+  a.uhat = uhat;
+  a.geo_sol = ctx->geo_sol;
+  a.geo_face = ctx->geo_face;
+  a.nbr = ctx->nbr;
+  a.nbr_face = ctx->nbr_face;
+  a.kind = ctx->kind;
+  a.tr_of = ctx->tr_of;
+  a.implicit = ctx->implicit;
+  a.Uf_all = ctx->Uf_all;
+  a.qf_all = ctx->qf_all;
+  a.Uf_out = ctx->Uf_all;
+  a.qf_out = ctx->qf_all;
+  return a;
+}
+
+// R and element trace contributions (gview) at (u, uhat); g assembled if requested
+static int residual_into(fr_ctx* ctx, const double* u, const double* uhat, double* R, double* gview, double* g) {
+  ResArgs a = res_args(ctx, u, uhat);
+  a.R = R;
+  a.gview = gview;
+  const int ph = prof_begin(ctx, PH_RES);
+  CK(launch_residual(ctx->p, ctx->ref, ctx->pp, a, ctx->need_nbr, false, ctx->stream));
+  if (g) CK(launch_trace_assemble(gview, ctx->sides_e, ctx->ntrace, ctx->n * ctx->nv, g, ctx->stream));
+  prof_end(ctx, ph);
+  return FR_OK;
+}
+
+extern "C" int fr_residual(fr_ctx* ctx, const double* u, const double* uhat, double* R, double* g) {
+  if (!ctx || !u || !R) return set_err(ctx, FR_ERR_INVALID_ARG, "fr_residual: null argument");
+  if (ctx->ntrace > 0 && !uhat) return set_err(ctx, FR_ERR_INVALID_ARG, "fr_residual: uhat required");
+  int rc = residual_into(ctx, u, uhat, R, ctx->gview, g);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(ctx->stream));
+  prof_collect(ctx);
+  return FR_OK;
+}
+
+extern "C" int hfr_initial_trace(fr_ctx* ctx, const double* u, double* uhat) {
+  if (!ctx || !u || (ctx->ntrace > 0 && !uhat)) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_initial_trace: null argument");
+  // face states of every element into a scratch buffer of the same shape (E x 4n x nv)
+  ResArgs a = res_args(ctx, u, nullptr);
+  a.Uf_out = ctx->gview;
+  CK(launch_face_states(ctx->p, ctx->ref, ctx->pp, a, ctx->stream));
+  const int npf = ctx->n * ctx->nv;
+  if (ctx->ntrace) {
+    (hfr::count_launch(), k_initial_trace<<<nblk((size_t)ctx->ntrace * npf), 256, 0, ctx->stream>>>(ctx->ntrace, npf, 4 * npf, ctx->sides_e,
+                                                                               ctx->gview, uhat));
+    CK(cudaGetLastError());
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FR_OK;
+}
+
+// blocks at (u, uhat); assumes r, s were formed at the same point
+static int jacobian_blocks(fr_ctx* ctx, const double* u, const double* uhat, double a_dt) {
+  JacArgs j;
+  memset(&j, 0, sizeof(j));
+  j.Eim = ctx->Eim;
+  j.imp_idx = ctx->imp_idx;
+  j.U = u;
+  j.uhat = uhat;
+  j.geo_sol = ctx->geo_sol;
+  j.geo_face = ctx->geo_face;
+  j.nbr = ctx->nbr;
+  j.nbr_face = ctx->nbr_face;
+  j.kind = ctx->kind;
+  j.tr_of = ctx->tr_of;
+  j.Uf_all = ctx->Uf_all;
+  j.a_dt = a_dt;
+  j.A = ctx->A;
+  j.B = ctx->B;
+  j.C = ctx->C;
+  j.D = ctx->D;
+  const int ph = prof_begin(ctx, PH_JAC);
+  CK(launch_jacobian(ctx->p, ctx->prec_bytes, ctx->ref, ctx->pp, j, ctx->stream));
+  prof_end(ctx, ph);
+  ctx->lin_U = u;
+  ctx->lin_uhat = uhat;
+  ctx->lin_adt = a_dt;
+  return FR_OK;
+}
+
+static int form_rhs(fr_ctx* ctx, const double* u, const double* ustar, double a_dt) {
+  const size_t tot = (size_t)ctx->Eim * (ctx->nA + ctx->nT);
+  if (tot == 0) return FR_OK;
+  (hfr::count_launch(), k_form_rhs<<<nblk(tot), 256, 0, ctx->stream>>>(ctx->Eim, ctx->nA, ctx->nT, ctx->imp_idx, u, ustar, ctx->Rw,
+                                                 ctx->gview, a_dt, ctx->r, ctx->s));
+  CK(cudaGetLastError());
+  return FR_OK;
+}
+
+extern "C" int hfr_local_jacobian(fr_ctx* ctx, const double* u, const double* uhat, const double* ustar,
+                                  double a_dt) {
+  if (!ctx || !u || (ctx->ntrace > 0 && !uhat)) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_local_jacobian: null argument");
+  // keep a copy of the linearisation point for later refinement sweeps
+  CK(cudaMemcpyAsync(ctx->lin_Ubuf, u, (size_t)ctx->E * ctx->nA * sizeof(double), cudaMemcpyDeviceToDevice,
+                     ctx->stream));
+  const size_t nh = (size_t)ctx->ntrace * ctx->n * ctx->nv;
+  if (nh) CK(cudaMemcpyAsync(ctx->lin_uhbuf, uhat, nh * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  int rc = residual_into(ctx, u, uhat, ctx->Rw, ctx->gview, nullptr);
+  if (!rc) rc = form_rhs(ctx, u, ustar, a_dt);
+  if (!rc) rc = jacobian_blocks(ctx, u, uhat, a_dt);
+  ctx->lin_U = ctx->lin_Ubuf;
+  ctx->lin_uhat = nh ? ctx->lin_uhbuf : nullptr;
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(ctx->stream));
+  prof_collect(ctx);
+  return FR_OK;
+}
+
+static TraceArgs trace_args(fr_ctx* ctx) {
+  TraceArgs t;
+  t.ntrace = ctx->ntrace;
+  t.n = ctx->n;
+  t.nv = ctx->nv;
+  t.nT = ctx->nT;
+  t.sides = ctx->sides_c;
+  t.tr_of_c = ctx->tr_of_c;
+  t.S = ctx->S;
+  return t;
+}
+
+// FP64 refinement sweep(s) of X = A^{-1} rhs against the exact linearisation:
+// x <- x + LU^{-1} (rhs - A x - B y), A x + B y evaluated as x - adt dR(U, u^)[x, y]
+static int refine_local(fr_ctx* ctx, const double* rhs, double* x, const double* y_trace, int sweeps) {
+  const int Eim = ctx->Eim, nA = ctx->nA, E = ctx->E;
+  const size_t nloc = (size_t)Eim * nA;
+  for (int sw = 0; sw < sweeps; ++sw) {
+    (hfr::count_launch(), k_scatter_du<<<nblk(nloc), 256, 0, ctx->stream>>>(Eim, nA, ctx->imp_idx, x, ctx->dUw));
+    CK(cudaGetLastError());
+    ResArgs a = res_args(ctx, ctx->lin_U, ctx->lin_uhat);
+    a.dU = ctx->dUw;
+    a.duhat = y_trace;
+    a.dR = ctx->dRw;
+    CK(launch_residual(ctx->p, ctx->ref, ctx->pp, a, ctx->need_nbr, true, ctx->stream));
+    (hfr::count_launch(), k_refine_res<<<nblk(nloc), 256, 0, ctx->stream>>>(Eim, nA, ctx->imp_idx, rhs, x, ctx->dRw, ctx->lin_adt,
+                                                      ctx->res_tmp));
+    CK(cudaGetLastError());
+    CK(launch_lu_solve(ctx->prec_bytes, Eim, nA, ctx->LU, ctx->piv, ctx->res_tmp, ctx->stream));
+    (hfr::count_launch(), k_axpy<<<nblk(nloc), 256, 0, ctx->stream>>>(nloc, 1.0, ctx->res_tmp, x));
+    CK(cudaGetLastError());
+  }
+  (void)E;
+  return FR_OK;
+}
+
+static int check_status(fr_ctx* ctx, const char* where) {
+  int hs[2];
+  CK(cudaMemcpyAsync(hs, ctx->status, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (hs[0] & DEV_ERR_SINGULAR) {
+    CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
+    return set_err(ctx, FR_ERR_SINGULAR, where, hs[1]);
+  }
+  return FR_OK;
+}
+
+static int condense_impl(fr_ctx* ctx, int refine) {
+  int init[2] = {0, 0x7fffffff};
+  CK(cudaMemcpyAsync(ctx->status, init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
+  CondArgs c;
+  c.Eim = ctx->Eim;
+  c.nA = ctx->nA;
+  c.nT = ctx->nT;
+  c.A = ctx->A;
+  c.B = ctx->B;
+  c.C = ctx->C;
+  c.D = ctx->D;
+  c.r = ctx->r;
+  c.s = ctx->s;
+  c.LU = ctx->LU;
+  c.piv = ctx->piv;
+  c.XB = ctx->XB;
+  c.xr = ctx->xr;
+  c.S = ctx->S;
+  c.t = ctx->te;
+  c.status = ctx->status;
+  int ph = prof_begin(ctx, PH_COND);
+  CK(launch_condense(ctx->prec_bytes, c, ctx->stream));
+  prof_end(ctx, ph);
+  if (refine > 0 && ctx->lin_U) {
+    // FP64 refinement of x_r against the exact linearisation (used by the back-substitution)
+    ph = prof_begin(ctx, PH_REFX);
+    int rc = refine_local(ctx, ctx->r, ctx->xr, nullptr, refine);
+    prof_end(ctx, ph);
+    if (rc) return rc;
+  }
+  TraceArgs t = trace_args(ctx);
+  ph = prof_begin(ctx, PH_PREC);
+  CK(launch_assemble_t(t, ctx->te, ctx->tg, ctx->stream));
+  CK(launch_precond_build(ctx->prec_bytes, t, ctx->Pinv, ctx->status, ctx->stream));
+  prof_end(ctx, ph);
+  return FR_OK;
+}
+
+extern "C" int hfr_condense(fr_ctx* ctx, int refine) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  int rc = condense_impl(ctx, refine);
+  if (rc) return rc;
+  rc = check_status(ctx, "hfr_condense: zero pivot");
+  prof_collect(ctx);
+  return rc;
+}
+
+// GMRES callbacks
+static void cb_matvec(void* c, const double* x, double* y, cudaStream_t s) {
+  fr_ctx* ctx = (fr_ctx*)c;
+  launch_trace_matvec(ctx->prec_bytes, trace_args(ctx), x, y, s);
+}
+static void cb_gmatvec(void* c, const GmresState* st, int j, const double* x, double* y, cudaStream_t s) {
+  fr_ctx* ctx = (fr_ctx*)c;
+  launch_trace_matvec(ctx->prec_bytes, trace_args(ctx), x, y, s, &st->kdone, j);
+}
+static void cb_precond(void* c, const GmresState* st, int j, const double* x, double* y, cudaStream_t s) {
+  fr_ctx* ctx = (fr_ctx*)c;
+  launch_precond_apply(trace_args(ctx), ctx->Pinv, x, y, s, &st->kdone, j);
+}
+
+static int gmres_impl(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* iters, double* final_rel) {
+  GmresOps ops;
+  ops.ctx = ctx;
+  ops.matvec = cb_matvec;
+  ops.gated_matvec = cb_gmatvec;
+  ops.precond = cb_precond;
+  GmresResult res;
+  memset(&res, 0, sizeof(res));
+  if (ctx->ntrace == 0) {
+    if (iters) *iters = 0;
+    if (final_rel) *final_rel = 0.0;
+    return FR_OK;
+  }
+  const int ph = prof_begin(ctx, PH_GMRES);
+  const int grc = run_gmres(ops, ctx->gm, ctx->tg, duhat, rtol, ctx->restart, maxit, 4, &res, ctx->stream);
+  prof_end(ctx, ph);
+  if (grc != 0) return set_err(ctx, FR_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+  CK(cudaGetLastError());
+  if (iters) *iters = res.iterations;
+  if (final_rel) *final_rel = res.rel;
+  if (res.nan) return set_err(ctx, FR_ERR_DIVERGED, "hfr_trace_gmres: non-finite residual", -1, res.iterations);
+  if (!res.converged && res.rel > rtol)
+    return set_err(ctx, FR_ERR_NOT_CONVERGED, "hfr_trace_gmres: iteration limit", -1, res.iterations, res.rel);
+  return FR_OK;
+}
+
+extern "C" int hfr_trace_gmres(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* iters, double* final_rel) {
+  if (!ctx || !duhat || rtol < 0 || maxit < 1) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_trace_gmres: bad argument");
+  const int rc = gmres_impl(ctx, duhat, rtol, maxit, iters, final_rel);
+  prof_collect(ctx);
+  return rc;
+}
+
+static int backsolve_impl(fr_ctx* ctx, const double* duhat, double* du, int refine) {
+  TraceArgs t = trace_args(ctx);
+  const int ph = prof_begin(ctx, PH_BACK);
+  CK(launch_backsolve(ctx->prec_bytes, t, ctx->Eim, ctx->nA, ctx->XB, ctx->xr, duhat, du, ctx->stream));
+  int rc = FR_OK;
+  if (refine > 0 && ctx->lin_U) rc = refine_local(ctx, ctx->r, du, duhat, refine);
+  prof_end(ctx, ph);
+  return rc;
+}
+
+extern "C" int hfr_backsolve(fr_ctx* ctx, const double* duhat, double* du, int refine) {
+  if (!ctx || !du || (ctx->ntrace > 0 && !duhat)) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_backsolve: null argument");
+  int rc = backsolve_impl(ctx, duhat, du, refine);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(ctx->stream));
+  prof_collect(ctx);
+  return FR_OK;
+}
+
+extern "C" int hfr_export(fr_ctx* ctx, int which, void* dst, size_t bytes) {
+  if (!ctx || !dst) return FR_ERR_INVALID_ARG;
+  const size_t pb = ctx->prec_bytes, Eim = ctx->Eim, nA = ctx->nA, nT = ctx->nT;
+  const void* src = nullptr;
+  size_t need = 0;
+  switch (which) {
+    case 0: src = ctx->A; need = Eim * nA * nA * pb; break;
+    case 1: src = ctx->B; need = Eim * nA * nT * pb; break;
+    case 2: src = ctx->C; need = Eim * nT * nA * pb; break;
+    case 3: src = ctx->D; need = Eim * nT * nT * pb; break;
+    case 4: src = ctx->S; need = Eim * nT * nT * pb; break;
+    case 5: src = ctx->XB; need = Eim * nA * nT * pb; break;
+    case 6: src = ctx->xr; need = Eim * nA * 8; break;
+    case 7: src = ctx->te; need = Eim * nT * 8; break;
+    case 8: src = ctx->r; need = Eim * nA * 8; break;
+    case 9: src = ctx->s; need = Eim * nT * 8; break;
+    case 10: src = ctx->tg; need = (size_t)ctx->ntrace * ctx->n * ctx->nv * 8; break;
+    default: return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_export: unknown array");
+  }
+  if (bytes < need) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_export: destination too small");
+  CK(cudaMemcpyAsync(dst, src, need, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FR_OK;
+}
+
+// ------------------------------------------------------------------------ tableaux
+struct Tab {
+  int s;
+  double a[2][2], b[2], ah[3][3], bh[3];
+};
+static Tab tableau(int which) {
+  Tab t;
+  memset(&t, 0, sizeof(t));
+  if (which == FR_TAB_SDIRK2) {
+    const double g = 1.0 - sqrt(2.0) / 2.0, dl = -2.0 * sqrt(2.0) / 3.0;
+    t.s = 2;
+    t.a[0][0] = g;
+    t.a[1][0] = 1.0 - g;
+    t.a[1][1] = g;
+    t.b[0] = 1.0 - g;
+    t.b[1] = g;
+    t.ah[1][0] = g;
+    t.ah[2][0] = dl;
+    t.ah[2][1] = 1.0 - dl;
+    t.bh[1] = 1.0 - g;
+    t.bh[2] = g;
+  } else {
+    t.s = 1;
+    t.a[0][0] = 1.0;
+    t.b[0] = 1.0;
+    t.ah[1][0] = 1.0;
+    t.bh[1] = 1.0;
+  }
+  return t;
+}
+
+static int sumsq(fr_ctx* ctx, const double* a, size_t na, const double* b, size_t nb, double* out_host) {
+  const int nbk = 256;
+  (hfr::count_launch(), k_sumsq_part<<<nbk, 256, 0, ctx->stream>>>(a, na, b, nb, ctx->red));
+  (hfr::count_launch(), k_sumsq_final<<<1, 32, 0, ctx->stream>>>(ctx->red, nbk, ctx->red + 1024));
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out_host, ctx->red + 1024, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FR_OK;
+}
+
+extern "C" int imex_stage(fr_ctx* ctx, int stage, double dt, const double* u_n, double* u_stage, double* uhat,
+                          double* R_hist, double newton_tol, int newton_maxit, double gmres_rtol, int gmres_maxit,
+                          int refine, fr_stage_stats* stats) {
+  if (!ctx || !u_n || !u_stage || !R_hist || (ctx->ntrace > 0 && !uhat))
+    return set_err(ctx, FR_ERR_INVALID_ARG, "imex_stage: null argument");
+  const Tab tb = tableau(ctx->tableau);
+  if (stage < 0 || stage > tb.s + 1) return set_err(ctx, FR_ERR_INVALID_ARG, "imex_stage: stage out of range");
+  const int E = ctx->E, nA = ctx->nA;
+  const size_t tot = (size_t)E * nA;
+  cudaStream_t st = ctx->stream;
+  if (stats) memset(stats, 0, sizeof(*stats));
+  if (stage == 0) {
+    int rc = residual_into(ctx, u_n, uhat, R_hist, ctx->gview, nullptr);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(st));
+    return FR_OK;
+  }
+  if (stage == tb.s + 1) {
+    StageCoef sc;
+    memset(&sc, 0, sizeof(sc));
+    sc.nterm = tb.s + 1;
+    for (int j = 0; j <= tb.s; ++j) {
+      sc.hi[j] = j;
+      sc.ci[j] = j >= 1 ? dt * tb.b[j - 1] : 0.0;  // implicit: b_j R(u_j)
+      sc.ce[j] = dt * tb.bh[j];                    // explicit: bhat_{j+1} R(u_j)
+    }
+    (hfr::count_launch(), k_stage_combine<<<nblk(tot), 256, 0, st>>>(E, nA, ctx->implicit, u_n, R_hist, sc, u_stage));
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    return FR_OK;
+  }
+  const int i = stage;
+  // explicit elements: u_i = u_n + dt sum_{j<=i} ahat_{i+1,j} R_hist[j-1];
+  // implicit elements: u* = u_n + dt sum_{j<i} a_ij R_hist[j]  (also the Newton start)
+  StageCoef sc;
+  memset(&sc, 0, sizeof(sc));
+  sc.nterm = i;
+  for (int j = 0; j < i; ++j) {
+    sc.hi[j] = j;
+    sc.ce[j] = dt * tb.ah[i][j];
+    sc.ci[j] = j >= 1 ? dt * tb.a[i - 1][j - 1] : 0.0;
+  }
+  (hfr::count_launch(), k_stage_combine<<<nblk(tot), 256, 0, st>>>(E, nA, ctx->implicit, u_n, R_hist, sc, u_stage));
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(ctx->Ustar, u_stage, tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  const double adt = dt * tb.a[i - 1][i - 1];
+  const size_t nh = (size_t)ctx->ntrace * ctx->n * ctx->nv;
+  double norm0 = -1.0, normk = 0.0;
+  int it = 0, gtot = 0;
+  bool conv = false;
+  for (;; ++it) {
+    int rc = residual_into(ctx, u_stage, uhat, ctx->Rw, ctx->gview, ctx->gw);
+    const int phn = prof_begin(ctx, PH_NEWTON);
+    if (!rc) rc = form_rhs(ctx, u_stage, ctx->Ustar, adt);
+    double ss = 0.0;
+    if (!rc) rc = sumsq(ctx, ctx->r, (size_t)ctx->Eim * nA, ctx->gw, nh, &ss);
+    prof_end(ctx, phn);
+    if (rc) return rc;
+    normk = sqrt(ss);
+    if (!(normk == normk)) return set_err(ctx, FR_ERR_DIVERGED, "imex_stage: non-finite Newton residual", -1, it);
+    if (norm0 < 0) norm0 = normk;
+    if (normk <= newton_tol * norm0 || normk == 0.0) {
+      conv = true;
+      break;
+    }
+    if (it >= newton_maxit) break;
+    rc = jacobian_blocks(ctx, u_stage, uhat, adt);
+    if (!rc) rc = condense_impl(ctx, refine);
+    if (!rc) rc = check_status(ctx, "imex_stage: zero pivot in condensation");
+    if (rc) return rc;
+    int its = 0;
+    double rel = 0.0;
+    rc = gmres_impl(ctx, ctx->duhat, gmres_rtol, gmres_maxit, &its, &rel);
+    gtot += its;
+    if (rc && rc != FR_ERR_NOT_CONVERGED) return rc;
+    rc = backsolve_impl(ctx, ctx->duhat, ctx->du, refine);
+    if (rc) return rc;
+    const int phu = prof_begin(ctx, PH_NEWTON);
+    (hfr::count_launch(), k_apply_du<<<nblk((size_t)ctx->Eim * nA), 256, 0, st>>>(ctx->Eim, nA, ctx->imp_idx, ctx->du, u_stage));
+    CK(cudaGetLastError());
+    if (nh) {
+      (hfr::count_launch(), k_axpy<<<nblk(nh), 256, 0, st>>>(nh, 1.0, ctx->duhat, uhat));
+      CK(cudaGetLastError());
+    }
+    prof_end(ctx, phu);
+  }
+  // R_hist[i] = R(u_i, u^_i)
+  int rc = residual_into(ctx, u_stage, uhat, R_hist + (size_t)i * tot, ctx->gview, nullptr);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(st));
+  prof_collect(ctx);
+  if (stats) {
+    stats->newton_iterations = it;
+    stats->gmres_iterations = gtot;
+    stats->residual0 = norm0;
+    stats->residual = normk;
+    stats->converged = conv ? 1 : 0;
+  }
+  if (!conv) return set_err(ctx, FR_ERR_NOT_CONVERGED, "imex_stage: Newton iteration limit", -1, it, normk);
+  return FR_OK;
+}
+
+extern "C" int fr_profile_enable(fr_ctx* ctx, int on) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  prof_collect(ctx);
+  if (on && ctx->evpool.empty()) {
+    ctx->evpool.resize(4096);
+    for (auto& e : ctx->evpool) CK(cudaEventCreate(&e));
+  }
+  ctx->prof = on != 0;
+  if (on)
+    for (int i = 0; i < 8; ++i) {
+      ctx->pms[i] = 0.0;
+      ctx->pcnt[i] = 0;
+    }
+  return FR_OK;
+}
+
+extern "C" int fr_profile_read(const fr_ctx* ctx, fr_profile* out) {
+  if (!ctx || !out) return FR_ERR_INVALID_ARG;
+  for (int i = 0; i < 8; ++i) {
+    out->ms[i] = ctx->pms[i];
+    out->count[i] = ctx->pcnt[i];
+  }
+  return FR_OK;
+}
+
+extern "C" unsigned long long fr_kernel_launches(void) { return g_launches.load(); }
+
+extern "C" int fr_last_error(const fr_ctx* ctx, fr_error_info* info) {
+  if (!ctx || !info) return FR_ERR_INVALID_ARG;
+  *info = ctx->err;
+  return FR_OK;
+}
+
+extern "C" const char* fr_status_string(int code) {
+  switch (code) {
+    case FR_OK: return "ok";
+    case FR_ERR_INVALID_ARG: return "invalid argument";
+    case FR_ERR_CUDA: return "CUDA error";
+    case FR_ERR_SINGULAR: return "singular block";
+    case FR_ERR_NOT_CONVERGED: return "not converged";
+    case FR_ERR_DIVERGED: return "diverged";
+    case FR_ERR_TIMEOUT: return "timeout";
+    case FR_ERR_OOM: return "out of device memory";
+    case FR_ERR_UNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}

@@ -1,0 +1,197 @@
+// Shared device-side definitions of the hybridized FR library.
+//
+// Discretisation (Pereira & Vermeire, arXiv 2401.16632, Sec. 2): tensor-product
+// Gauss-Legendre solution points, DG-recovering correction functions.  With the
+// 1D lift l_i(+-1)/w_i of those correction functions, the corrected gradient and
+// the flux divergence along every reference axis use the same 1D operator
+//     M = D - dgL lm^T - dgR lp^T,   dgL = -lm / w,  dgR = lp / w,
+// (D the Lagrange derivative matrix, lm / lp the interpolation to xi = -1 / +1):
+//     Q~_r  = M U|_line + dgL u_bar_L + dgR u_bar_R           (gradient, eq. fluxcorrection)
+//     div   = sum_r M F~_r|_line - dgL Fn_L + dgR Fn_R          (eqs. correctedflux, freq1)
+// where Fn = J_f F^.n is the common normal flux (eq. 8923i).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define HFR_MAXN 6  // up to p = 5
+
+// -------------------------------------------------------------------------------------------
+// Reference 1D operators for one polynomial degree, passed by value as a kernel parameter.
+struct RefOps {
+  double D[HFR_MAXN][HFR_MAXN];
+  double M[HFR_MAXN][HFR_MAXN];
+  double lm[HFR_MAXN], lp[HFR_MAXN];
+  double dgL[HFR_MAXN], dgR[HFR_MAXN];
+  double w[HFR_MAXN];
+};
+
+struct PhysParams {
+  int kind;  // 0 advection-diffusion, 1 Navier-Stokes 2D
+  double beta[3];
+  double nu;
+  double gamma, mu, Pr;
+  double lref;
+};
+
+// face kinds of an element face
+enum { FK_FR = 0, FK_TRACE = 1, FK_IMEX = 2 };
+
+// -------------------------------------------------------------------------------------------
+// Forward-mode dual number with one tangent (exact pointwise Jacobians and JVPs).
+template <typename T>
+struct Dual {
+  T v, d;
+  __host__ __device__ Dual() {}
+  __host__ __device__ Dual(T a) : v(a), d(T(0)) {}
+  __host__ __device__ Dual(T a, T b) : v(a), d(b) {}
+};
+template <typename T> __device__ __forceinline__ Dual<T> operator+(Dual<T> a, Dual<T> b) { return Dual<T>(a.v + b.v, a.d + b.d); }
+template <typename T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a, Dual<T> b) { return Dual<T>(a.v - b.v, a.d - b.d); }
+template <typename T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a) { return Dual<T>(-a.v, -a.d); }
+template <typename T> __device__ __forceinline__ Dual<T> operator*(Dual<T> a, Dual<T> b) { return Dual<T>(a.v * b.v, a.d * b.v + a.v * b.d); }
+template <typename T> __device__ __forceinline__ Dual<T> operator/(Dual<T> a, Dual<T> b) {
+  T inv = T(1) / b.v;
+  T q = a.v * inv;
+  return Dual<T>(q, (a.d - q * b.d) * inv);
+}
+template <typename T> __device__ __forceinline__ Dual<T> operator+(Dual<T> a, T b) { return Dual<T>(a.v + b, a.d); }
+template <typename T> __device__ __forceinline__ Dual<T> operator+(T a, Dual<T> b) { return Dual<T>(a + b.v, b.d); }
+template <typename T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a, T b) { return Dual<T>(a.v - b, a.d); }
+template <typename T> __device__ __forceinline__ Dual<T> operator-(T a, Dual<T> b) { return Dual<T>(a - b.v, -b.d); }
+template <typename T> __device__ __forceinline__ Dual<T> operator*(Dual<T> a, T b) { return Dual<T>(a.v * b, a.d * b); }
+template <typename T> __device__ __forceinline__ Dual<T> operator*(T a, Dual<T> b) { return Dual<T>(a * b.v, a * b.d); }
+template <typename T> __device__ __forceinline__ Dual<T> operator/(Dual<T> a, T b) { T inv = T(1) / b; return Dual<T>(a.v * inv, a.d * inv); }
+template <typename T> __device__ __forceinline__ Dual<T> operator/(T a, Dual<T> b) {
+  T inv = T(1) / b.v;
+  T q = a * inv;
+  return Dual<T>(q, -q * b.d * inv);
+}
+
+__device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
+template <typename T> __device__ __forceinline__ Dual<T> dsqrt(Dual<T> a) {
+  T s = dsqrt(a.v);
+  return Dual<T>(s, a.d / (T(2) * s));
+}
+// |x| with the branch taken on the value
+__device__ __forceinline__ double dabs(double x) { return fabs(x); }
+__device__ __forceinline__ float dabs(float x) { return fabsf(x); }
+template <typename T> __device__ __forceinline__ Dual<T> dabs(Dual<T> a) { return a.v >= T(0) ? a : -a; }
+__device__ __forceinline__ double dval(double x) { return x; }
+__device__ __forceinline__ float dval(float x) { return x; }
+template <typename T> __device__ __forceinline__ T dval(Dual<T> a) { return a.v; }
+template <typename S> __device__ __forceinline__ S dmax(S a, S b) { return dval(a) >= dval(b) ? a : b; }
+
+// underlying real type of a scalar
+template <typename S> struct RealOf { typedef S type; };
+template <typename T> struct RealOf<Dual<T>> { typedef T type; };
+
+// -------------------------------------------------------------------------------------------
+// Physics.  Fluxes F[c][v] (c = physical direction, v = variable).  q[c][v] = du_v/dx_c.
+// Same readings as the oracle: advection-diffusion F^c = beta u, F^v = nu grad u,
+// s = |beta.n| + nu/lref; Navier-Stokes ideal gas R = 1, constant mu, Stokes hypothesis,
+// kappa = mu gamma / ((gamma - 1) Pr), wave speed |v.n| + c, s = |v^.n| + c^ + mu/(rho^ lref).
+template <int PHYS> struct Phys;
+
+template <> struct Phys<0> {
+  static constexpr int NV = 1;
+  template <typename S, typename R>
+  __device__ static void conv(const PhysParams& pp, const S* u, S F[2][1]) {
+    F[0][0] = R(pp.beta[0]) * u[0];
+    F[1][0] = R(pp.beta[1]) * u[0];
+  }
+  template <typename S, typename R>
+  __device__ static void visc(const PhysParams& pp, const S* u, const S q[2][1], S F[2][1]) {
+    F[0][0] = R(pp.nu) * q[0][0];
+    F[1][0] = R(pp.nu) * q[1][0];
+  }
+  template <typename S, typename R>
+  __device__ static S wave(const PhysParams& pp, const S* u, R n0, R n1) {
+    R bn = R(pp.beta[0]) * n0 + R(pp.beta[1]) * n1;
+    return S(dabs(bn)) + R(0) * u[0];
+  }
+  template <typename S, typename R>
+  __device__ static S stab(const PhysParams& pp, const S* u, R n0, R n1) {
+    return wave<S, R>(pp, u, n0, n1) + R(pp.nu / pp.lref);
+  }
+};
+
+template <> struct Phys<1> {
+  static constexpr int NV = 4;
+  template <typename S, typename R>
+  __device__ static void conv(const PhysParams& pp, const S* u, S F[2][4]) {
+    R g1 = R(pp.gamma - 1.0);
+    S rho = u[0];
+    S vx = u[1] / rho, vy = u[2] / rho;
+    S p = g1 * (u[3] - R(0.5) * (u[1] * vx + u[2] * vy));
+    S Ep = u[3] + p;
+    F[0][0] = u[1];
+    F[0][1] = u[1] * vx + p;
+    F[0][2] = u[2] * vx;
+    F[0][3] = Ep * vx;
+    F[1][0] = u[2];
+    F[1][1] = u[1] * vy;
+    F[1][2] = u[2] * vy + p;
+    F[1][3] = Ep * vy;
+  }
+  template <typename S, typename R>
+  __device__ static void visc(const PhysParams& pp, const S* u, const S q[2][4], S F[2][4]) {
+    R g = R(pp.gamma);
+    R mu = R(pp.mu);
+    R kappa = R(pp.mu * pp.gamma / ((pp.gamma - 1.0) * pp.Pr));
+    S rho = u[0];
+    S ir = R(1) / rho;
+    S vx = u[1] * ir, vy = u[2] * ir;
+    S e = u[3] * ir;
+    S dvx[2], dvy[2], dT[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      dvx[c] = (q[c][1] - vx * q[c][0]) * ir;
+      dvy[c] = (q[c][2] - vy * q[c][0]) * ir;
+      dT[c] = (g - R(1)) * ((q[c][3] - e * q[c][0]) * ir - vx * dvx[c] - vy * dvy[c]);
+    }
+    S div = dvx[0] + dvy[1];
+    S txx = mu * (R(2) * dvx[0] - R(2.0 / 3.0) * div);
+    S tyy = mu * (R(2) * dvy[1] - R(2.0 / 3.0) * div);
+    S txy = mu * (dvx[1] + dvy[0]);
+    F[0][0] = S(R(0));
+    F[0][1] = txx;
+    F[0][2] = txy;
+    F[0][3] = vx * txx + vy * txy + kappa * dT[0];
+    F[1][0] = S(R(0));
+    F[1][1] = txy;
+    F[1][2] = tyy;
+    F[1][3] = vx * txy + vy * tyy + kappa * dT[1];
+  }
+  template <typename S, typename R>
+  __device__ static S wave(const PhysParams& pp, const S* u, R n0, R n1) {
+    R g = R(pp.gamma);
+    S rho = u[0];
+    S vx = u[1] / rho, vy = u[2] / rho;
+    S p = (g - R(1)) * (u[3] - R(0.5) * (u[1] * vx + u[2] * vy));
+    S c = dsqrt(g * p / rho);
+    return dabs(vx * n0 + vy * n1) + c;
+  }
+  template <typename S, typename R>
+  __device__ static S stab(const PhysParams& pp, const S* u, R n0, R n1) {
+    return wave<S, R>(pp, u, n0, n1) + R(pp.mu / pp.lref) / u[0];
+  }
+};
+
+// -------------------------------------------------------------------------------------------
+// Geometry layout (double, per element):
+//   sol: [Ns][5] = {1/J, S00, S01, S10, S11}  (S = adjugate of dx/dxi, F~_r = sum_c S[r][c] F_c)
+//   face: [4][n][3] = {J_f, n0, n1}            (unit outward normal, face Jacobian)
+// Element face f: axis r = f >> 1, side sigma = (f & 1) ? +1 : -1.  Face point m is the line
+// index along the other axis.  Solution point pt = a + n b.
+__device__ __forceinline__ int face_axis(int f) { return f >> 1; }
+
+// index of the solution point at coordinate c along axis r on line m
+template <int N>
+__device__ __forceinline__ int line_pt(int r, int m, int c) {
+  return r == 0 ? (c + N * m) : (m + N * c);
+}
+
+// status word bits written by kernels (never trap)
+enum { DEV_ERR_SINGULAR = 1, DEV_ERR_NAN = 2, DEV_ERR_INDEX = 4 };

@@ -1,0 +1,111 @@
+// Internal (non-ABI) declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "hfr_common.cuh"
+
+namespace hfr {
+
+// counts every kernel launch of the library (reported by fr_kernel_launches)
+void count_launch();
+
+// Arguments of the element residual kernels.  All pointers are device pointers; nullable
+// ones are marked.  U: E x Ns x nv; uhat: ntrace x n x nv; Uf_all: E x 4n x nv;
+// qf_all: E x 4n x 2 x nv; gview: E x 4n x nv.
+struct ResArgs {
+  int E;
+  const double* U;
+  const double* dU;     // nullable: tangent of U (JVP mode)
+  const double* uhat;   // nullable when the mesh has no trace faces
+  const double* duhat;  // nullable
+  const double* geo_sol;
+  const double* geo_face;
+  const int* nbr;
+  const int* nbr_face;
+  const int* kind;
+  const int* tr_of;
+  const unsigned char* implicit;
+  const double* Uf_all;  // neighbour face states (read), nullable for all-trace meshes
+  const double* qf_all;  // neighbour face gradients (read)
+  double* Uf_out;        // MODE_UF output
+  double* qf_out;        // MODE_QF output
+  double* R;             // nullable
+  double* dR;            // nullable (JVP)
+  double* gview;         // nullable: w_q J_f F^.n on trace faces
+  double* dgview;        // nullable (JVP)
+};
+
+cudaError_t launch_residual(int p, const RefOps& ref, const PhysParams& pp, const ResArgs& a, bool need_nbr,
+                            bool jvp, cudaStream_t st);
+cudaError_t launch_face_states(int p, const RefOps& ref, const PhysParams& pp, const ResArgs& a, cudaStream_t st);
+cudaError_t launch_trace_assemble(const double* gview, const int* sides, int ntrace, int npf, double* g,
+                                  cudaStream_t st);
+
+// Element Jacobian blocks of the implicit elements (row-major, per implicit element k):
+// A: nA x nA, B: nA x nT, C: nT x nA, D: nT x nT.
+struct JacArgs {
+  int Eim;
+  const int* imp_idx;  // Eim element ids
+  const double* U;
+  const double* uhat;
+  const double* geo_sol;
+  const double* geo_face;
+  const int* nbr;
+  const int* nbr_face;
+  const int* kind;
+  const int* tr_of;
+  const double* Uf_all;  // neighbour face states for interface faces
+  double a_dt;
+  void* A;
+  void* B;
+  void* C;
+  void* D;
+};
+cudaError_t launch_jacobian(int p, int prec_bytes, const RefOps& ref, const PhysParams& pp, const JacArgs& a,
+                            cudaStream_t st);
+
+// Condensation: per implicit element, LU with partial pivoting of A (in place into LU),
+// X = A^{-1}[B | r], S = D - C X_B, t = s - C x_r.
+struct CondArgs {
+  int Eim, nA, nT;
+  const void* A;
+  const void* B;
+  const void* C;
+  const void* D;
+  const double* r;  // Eim x nA (FP64 right-hand side -h)
+  const double* s;  // Eim x nT (FP64 -g^k)
+  void* LU;
+  int* piv;
+  void* XB;
+  double* xr;       // Eim x nA
+  void* S;
+  double* t;        // Eim x nT
+  int* status;      // device status word (DEV_ERR_*), first failing element in status[1]
+};
+cudaError_t launch_condense(int prec_bytes, const CondArgs& a, cudaStream_t st);
+
+// LU solve with the stored factors: x = A^{-1} b, in place on b (Eim x nA, FP64 vectors).
+cudaError_t launch_lu_solve(int prec_bytes, int Eim, int nA, const void* LU, const int* piv, double* b,
+                            cudaStream_t st);
+
+// Trace operators
+struct TraceArgs {
+  int ntrace, n, nv, nT;  // nT = 4 n nv
+  const int* sides;       // ntrace x 4 (e0, f0, e1, f1) with compact implicit element ids
+  const int* tr_of_c;     // Eim x 4 trace id of each face of a compact implicit element (-1 none)
+  const void* S;          // Eim x nT x nT
+};
+cudaError_t launch_trace_matvec(int prec_bytes, const TraceArgs& a, const double* x, double* y, cudaStream_t st,
+                                const int* gate = nullptr, int gj = 0);
+cudaError_t launch_precond_build(int prec_bytes, const TraceArgs& a, double* Pinv, int* status, cudaStream_t st);
+cudaError_t launch_precond_apply(const TraceArgs& a, const double* Pinv, const double* x, double* y,
+                                 cudaStream_t st, const int* gate = nullptr, int gj = 0);
+cudaError_t launch_assemble_t(const TraceArgs& a, const double* te, double* t, cudaStream_t st);
+cudaError_t launch_backsolve(int prec_bytes, const TraceArgs& a, int Eim, int nA, const void* XB, const double* xr,
+                             const double* duhat, double* du, cudaStream_t st);
+
+
+}  // namespace hfr

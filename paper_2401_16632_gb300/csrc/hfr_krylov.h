@@ -1,0 +1,54 @@
+// GMRES driver interface (internal).
+#pragma once
+
+#include "hfr_internal.h"
+
+namespace hfr {
+
+constexpr int GM_MAXM = 64;
+constexpr int GM_NBLK = 304;  // 2 x 152 SMs
+
+// scalars first: the host reads only the head (sizeof(GmresHead)) between iterations
+struct GmresHead {
+  double beta, bnorm, res, hn;
+  int k, kdone, converged, nan;
+};
+struct GmresState {
+  double beta, bnorm, res, hn;
+  int k, kdone, converged, nan;
+  double H[(GM_MAXM + 1) * GM_MAXM];
+  double g[GM_MAXM + 1];
+  double cs[GM_MAXM], sn[GM_MAXM];
+  double hc[GM_MAXM + 1];
+  double h2[GM_MAXM + 1];
+  double y[GM_MAXM];
+};
+
+// operator callbacks (enqueue only)
+struct GmresOps {
+  void* ctx;
+  void (*matvec)(void* ctx, const double* x, double* y, cudaStream_t s);
+  void (*gated_matvec)(void* ctx, const GmresState* st, int j, const double* x, double* y, cudaStream_t s);
+  void (*precond)(void* ctx, const GmresState* st, int j, const double* x, double* y, cudaStream_t s);
+};
+
+struct GmresBuffers {
+  size_t n;
+  double* V;        // (GM_MAXM + 1) x n
+  double* Z;        // GM_MAXM x n
+  double* partial;  // GM_NBLK x (GM_MAXM + 1)
+  GmresState* state;
+};
+
+struct GmresResult {
+  int iterations;
+  int converged;
+  int nan;
+  double rel;
+  double bnorm;
+};
+
+int run_gmres(const GmresOps& ops, const GmresBuffers& b, const double* t, double* x, double rtol, int restart,
+              int maxit, int check_every, GmresResult* res, cudaStream_t s);
+
+}  // namespace hfr

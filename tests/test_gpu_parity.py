@@ -1,0 +1,233 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element on
+seeded inputs, plus full-size checks of the bench workload by properties the oracle can
+evaluate cheaply.
+
+Tolerances.  FP64 path: the same discretisation evaluated in a different order, so agreement
+is to rounding: 1e-11 relative to the magnitude of the compared array for residuals and
+blocks, 1e-9 for quantities that pass through a linear solve (condition numbers of the
+element blocks are O(1e2)), and 1e-10 relative to the stage increment for converged stages.
+FP32 blocks (mixed path): 3e-5 relative (FP32 rounding of O(n) accumulated terms); the
+converged mixed-precision stage must match the FP64 stage to 1e-8 relative to the increment
+(the FP64 Newton residual fixes the solution).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need CUDA")
+    from paper_2401_16632_gb300.build import build
+
+    build()
+    torch.cuda.set_device(0)
+
+
+import paper_2401_16632_gb300 as pkg  # noqa: E402
+from oracle.blocks import element_blocks  # noqa: E402
+from oracle.fr import Discretisation  # noqa: E402
+from oracle.physics import make_physics  # noqa: E402
+from oracle.solve import backsolve, condense, solve_trace  # noqa: E402
+from oracle.stepping import TABLEAUX, imex_step, newton_stage  # noqa: E402
+from workloads import make_config  # noqa: E402
+from workloads.mesh import structured_quads, uniform_nodes  # noqa: E402
+from workloads.states import isentropic_vortex, sample_points  # noqa: E402
+
+DEV = "cuda"
+
+
+def _band(n=8, p=2, physics="advdiff"):
+    imp = np.zeros((n, n), bool)
+    imp[n // 2 - 1:n // 2 + 1, :] = True
+    if physics == "advdiff":
+        mesh = structured_quads(uniform_nodes(n, 0, 1), uniform_nodes(n, 0, 1), p=p, implicit=imp.reshape(-1))
+        xy = sample_points(mesh, p)
+        u0 = np.exp(-20 * ((xy[..., 0] - 0.5) ** 2 + (xy[..., 1] - 0.4) ** 2))[..., None]
+        phys = {"kind": "advdiff", "beta": (1.0, 0.5), "nu": 0.01, "lref": 1.0}
+    else:
+        mesh = structured_quads(uniform_nodes(n, 0, 10), uniform_nodes(n, 0, 10), p=p, implicit=imp.reshape(-1))
+        u0 = isentropic_vortex(sample_points(mesh, p))
+        phys = {"kind": "ns", "gamma": 1.4, "mu": 5e-3, "Pr": 0.72, "lref": 1.0}
+    return mesh, u0, phys
+
+
+CASES = {
+    "advdiff8": lambda: (lambda w: (w.mesh, w.u0, w.physics))(make_config("advdiff8")),
+    "advdiff_skew_p3": lambda: (lambda w: (w.mesh, w.u0, w.physics))(make_config("advdiff", n=5, p=3, jitter=0.15, seed=4)),
+    "vortex_skew_p3": lambda: (lambda w: (w.mesh, w.u0, w.physics))(make_config("vortex", n=5, p=3, jitter=0.15, seed=9, re=200.0)),
+    "vortex_p2": lambda: (lambda w: (w.mesh, w.u0, w.physics))(make_config("vortex", n=4, p=2, re=500.0)),
+    "vortex_p4": lambda: (lambda w: (w.mesh, w.u0, w.physics))(make_config("vortex", n=3, p=4, re=500.0)),
+    "band_advdiff": lambda: _band(8, 2, "advdiff"),
+    "band_ns": lambda: _band(6, 3, "ns"),
+}
+
+
+def _setup(name, precision=pkg.FR_PREC_FP64, tableau=pkg.FR_TAB_SDIRK2):
+    mesh, u0, phys = CASES[name]()
+    ctx = pkg.Context(mesh, phys, precision=precision, tableau=tableau)
+    disc = Discretisation(mesh, make_physics(phys))
+    return ctx, disc, u0
+
+
+def _rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _perturbed_trace(disc, u0, seed=0):
+    uh = disc.initial_trace(u0)
+    rng = np.random.default_rng(seed)
+    return uh * (1.0 + 1e-3 * rng.standard_normal(uh.shape))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_residual_and_trace_residual(name):
+    ctx, d, u0 = _setup(name)
+    uh = _perturbed_trace(d, u0)
+    R, g = ctx.fr_residual(torch.tensor(u0, device=DEV), torch.tensor(uh, device=DEV))
+    Ro, go = d.full_residual(u0, uh)
+    assert _rel(R.cpu().numpy(), Ro) < 1e-11
+    if d.ntrace:
+        assert _rel(g.cpu().numpy(), go) < 1e-11
+
+
+@pytest.mark.parametrize("name", ["advdiff8", "vortex_skew_p3", "band_ns"])
+def test_initial_trace_and_solution_points(name):
+    ctx, d, u0 = _setup(name)
+    uh = ctx.hfr_initial_trace(torch.tensor(u0, device=DEV))
+    assert _rel(uh.cpu().numpy(), d.initial_trace(u0)) < 1e-14
+    assert _rel(ctx.solution_points().cpu().numpy(), d.geo.xy) < 1e-14
+
+
+def _blocks_both(name, precision, a_dt=0.037):
+    ctx, d, u0 = _setup(name, precision)
+    uh = _perturbed_trace(d, u0, 1)
+    ustar = u0 * 0.999
+    ctx.hfr_local_jacobian(torch.tensor(u0, device=DEV), torch.tensor(uh, device=DEV),
+                           torch.tensor(ustar, device=DEV), a_dt)
+    A, B, C, D = element_blocks(d, u0, uh, a_dt)
+    imp = d.imp_idx
+    return ctx, d, u0, uh, ustar, a_dt, (A[imp], B[imp], C[imp], D[imp])
+
+
+@pytest.mark.parametrize("name", ["advdiff8", "advdiff_skew_p3", "vortex_skew_p3", "vortex_p2", "vortex_p4",
+                                  "band_advdiff", "band_ns"])
+def test_element_blocks_fp64(name):
+    ctx, d, u0, uh, ustar, a_dt, blocks = _blocks_both(name, pkg.FR_PREC_FP64)
+    for key, ref in zip("ABCD", blocks):
+        got = ctx.hfr_export(key).cpu().numpy()
+        assert _rel(got, ref) < 1e-11, key
+    # Newton right-hand sides r = -h, s = -g^k
+    R, Fn = d.residual(u0, d.trace_view(uh))
+    imp = d.imp_idx
+    r_ref = -(u0[imp] - ustar[imp] - a_dt * R[imp]).reshape(len(imp), -1)
+    s_ref = -d.trace_weights(Fn)[imp].reshape(len(imp), -1)
+    assert _rel(ctx.hfr_export("r").cpu().numpy(), r_ref) < 1e-11
+    assert _rel(ctx.hfr_export("s").cpu().numpy(), s_ref) < 1e-11
+
+
+@pytest.mark.parametrize("name", ["vortex_skew_p3", "band_ns"])
+def test_element_blocks_fp32(name):
+    ctx, d, u0, uh, ustar, a_dt, blocks = _blocks_both(name, pkg.FR_PREC_FP32)
+    for key, ref in zip("ABCD", blocks):
+        got = ctx.hfr_export(key).cpu().numpy().astype(np.float64)
+        assert _rel(got, ref) < 3e-5, key
+
+
+@pytest.mark.parametrize("name", ["advdiff8", "vortex_skew_p3", "vortex_p4", "band_ns"])
+def test_condense_gmres_backsolve_fp64(name):
+    ctx, d, u0, uh, ustar, a_dt, (A, B, C, D) = _blocks_both(name, pkg.FR_PREC_FP64)
+    ctx.hfr_condense(refine=0)
+    r = ctx.hfr_export("r").cpu().numpy()
+    s = ctx.hfr_export("s").cpu().numpy()
+    XB, xr, S, t = condense(A, B, C, D, r, s)
+    assert _rel(ctx.hfr_export("S").cpu().numpy(), S) < 1e-9
+    assert _rel(ctx.hfr_export("XB").cpu().numpy(), XB) < 1e-9
+    assert _rel(ctx.hfr_export("xr").cpu().numpy(), xr) < 1e-9
+    assert _rel(ctx.hfr_export("t_k").cpu().numpy(), t) < 1e-9
+    duh_ref, _, _ = solve_trace(d, S, t, d.imp_idx, method="direct")
+    duh, its, rel = ctx.hfr_trace_gmres(rtol=1e-13, maxit=3000)
+    assert rel <= 1e-12
+    assert _rel(duh.cpu().numpy().reshape(-1), duh_ref) < 1e-9
+    du = ctx.hfr_backsolve(duh, refine=0).cpu().numpy()
+    dview = d.trace_view(duh_ref.reshape(d.ntrace, d.n, d.nv))[d.imp_idx].reshape(len(d.imp_idx), -1)
+    assert _rel(du, backsolve(XB, xr, dview)) < 1e-9
+
+
+def test_fp64_refinement_sweep_is_consistent():
+    """Refinement against the FP64 linearisation leaves an already exact FP64 solve unchanged
+    (to rounding): checks the JVP used for refinement equals the assembled blocks."""
+    ctx, d, u0, uh, ustar, a_dt, _ = _blocks_both("vortex_skew_p3", pkg.FR_PREC_FP64)
+    ctx.hfr_condense(refine=0)
+    duh, _, _ = ctx.hfr_trace_gmres(rtol=1e-13, maxit=3000)
+    du0 = ctx.hfr_backsolve(duh, refine=0).cpu().numpy()
+    du2 = ctx.hfr_backsolve(duh, refine=2).cpu().numpy()
+    assert _rel(du2, du0) < 1e-10
+
+
+@pytest.mark.parametrize("name,tab", [("advdiff8", "be"), ("vortex_skew_p3", "sdirk2"), ("vortex_p4", "sdirk2")])
+def test_newton_stage_matches_oracle(name, tab):
+    tabc = pkg.FR_TAB_BE if tab == "be" else pkg.FR_TAB_SDIRK2
+    ctx, d, u0 = _setup(name, tableau=tabc)
+    dt = 0.05 if tab == "be" else 0.2
+    a11 = TABLEAUX[tab]["a"][0, 0]
+    U_o, uh_o, info = newton_stage(d, u0, u0, d.initial_trace(u0), a11 * dt, tol=1e-13)
+    u = torch.tensor(u0, device=DEV)
+    uh = ctx.hfr_initial_trace(u)
+    R_hist = ctx.empty(ctx.info.nstages + 1, *ctx.state_shape)
+    us = ctx.empty(*ctx.state_shape)
+    ctx.imex_stage(0, dt, u, us, uh, R_hist)
+    st = ctx.imex_stage(1, dt, u, us, uh, R_hist, newton_tol=1e-13, gmres_rtol=1e-14, gmres_maxit=3000)
+    assert st["converged"]
+    inc = np.abs(U_o - u0).max()
+    assert np.abs(us.cpu().numpy() - U_o).max() < 1e-10 * inc
+    assert np.abs(uh.cpu().numpy() - uh_o).max() < 1e-10 * max(inc, 1e-300) + 1e-13 * np.abs(uh_o).max()
+    # the stored stage derivative is R(u_1, u^_1)
+    R1, _ = d.full_residual(U_o, uh_o)
+    assert _rel(R_hist[1].cpu().numpy(), R1) < 1e-8
+
+
+@pytest.mark.parametrize("name", ["band_advdiff", "band_ns"])
+def test_imex_step_matches_oracle(name):
+    ctx, d, u0 = _setup(name, tableau=pkg.FR_TAB_SDIRK2)
+    dt = 0.01 if name == "band_advdiff" else 0.02
+    U_o, uh_o, _ = imex_step(d, u0, d.initial_trace(u0), dt, "sdirk2", tol=1e-13)
+    u = torch.tensor(u0, device=DEV)
+    uh = ctx.hfr_initial_trace(u)
+    u1, stats = ctx.imex_step(dt, u, uh, newton_tol=1e-13, gmres_rtol=1e-14, gmres_maxit=3000)
+    inc = np.abs(U_o - u0).max()
+    assert np.abs(u1.cpu().numpy() - U_o).max() < 1e-10 * inc
+    # discrete conservation across the interface on the GPU result (Sec. 4)
+    W = np.outer(d.ref.w, d.ref.w).reshape(-1)
+    m0 = np.einsum("s,es,esv->v", W, d.geo.J, u0)
+    m1 = np.einsum("s,es,esv->v", W, d.geo.J, u1.cpu().numpy())
+    assert np.abs(m1 - m0).max() < 1e-11 * np.abs(m0).max() + 1e-13
+
+
+@pytest.mark.parametrize("refine", [0, 1])
+def test_mixed_precision_stage_matches_fp64(refine):
+    ctx64, d, u0 = _setup("vortex_skew_p3", pkg.FR_PREC_FP64)
+    mesh, u0, phys = CASES["vortex_skew_p3"]()
+    ctx32 = pkg.Context(mesh, phys, precision=pkg.FR_PREC_FP32, tableau=pkg.FR_TAB_SDIRK2)
+    dt = 0.2
+    out = []
+    for ctx in (ctx64, ctx32):
+        u = torch.tensor(u0, device=DEV)
+        uh = ctx.hfr_initial_trace(u)
+        R_hist = ctx.empty(3, *ctx.state_shape)
+        us = ctx.empty(*ctx.state_shape)
+        ctx.imex_stage(0, dt, u, us, uh, R_hist)
+        st = ctx.imex_stage(1, dt, u, us, uh, R_hist, newton_tol=1e-11, gmres_rtol=1e-6, refine=refine)
+        assert st["converged"]
+        out.append(us.cpu().numpy())
+    inc = np.abs(out[0] - u0).max()
+    assert np.abs(out[1] - out[0]).max() < 1e-8 * inc
