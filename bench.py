@@ -251,6 +251,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--refine", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--paths", default="both", choices=["both", "mixed", "fp64"],
+                    help="profiling aid: time only one precision path")
+    ap.add_argument("--no-e2e", action="store_true", help="profiling aid: skip the host-buffer e2e leg")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -275,6 +278,13 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
     w = make_config("vortex64")
     l2buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB
+    if args.paths != "both":  # profiling aid: one path, no JSON contract line
+        prec = pkg.FR_PREC_FP32 if args.paths == "mixed" else pkg.FR_PREC_FP64
+        r = time_path(pkg, torch, w, prec, args.refine if args.paths == "mixed" else 0, args.steps, args.warmup,
+                      dev, l2buf)
+        print(json.dumps({"path": args.paths, "ms": r["ms"], "stats": r["stats"],
+                          "phases_ms_total": r["profile"], "launches": r["launches"]}))
+        return
     with ClockSampler(local) as clk:
         mixed = time_path(pkg, torch, w, pkg.FR_PREC_FP32, args.refine, args.steps, args.warmup, dev, l2buf)
         fp64 = time_path(pkg, torch, w, pkg.FR_PREC_FP64, 0, args.steps, args.warmup, dev, l2buf)
@@ -290,7 +300,10 @@ def main():
     # agreement of the two converged stages (same equations, same tolerance)
     inc = (fp64["u"] - torch.tensor(w.u0, device=dev)).abs().max().item()
     diff = (mixed["u"] - fp64["u"]).abs().max().item() / inc
-    e2e_ms, bi, bo = time_e2e(pkg, torch, mixed["ctx"], w, max(3, args.steps // 2), dev)
+    if args.no_e2e:
+        e2e_ms, bi, bo = float("nan"), 0, 0
+    else:
+        e2e_ms, bi, bo = time_e2e(pkg, torch, mixed["ctx"], w, max(3, args.steps // 2), dev)
     peaks, peak_src = _peaks()
     pm = {k: v[0] for k, v in mixed["profile"].items()}
     pc = {k: v[1] for k, v in mixed["profile"].items()}

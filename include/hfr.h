@@ -146,7 +146,8 @@ int hfr_backsolve(fr_ctx* ctx, const double* duhat, double* du, int refine);
 
 /* Copy a context block array to a caller device buffer (for inspection / parity tests).
  * which: 0 A, 1 B, 2 C, 3 D, 4 S, 5 X_B, 6 x_r (FP64), 7 t_k (FP64), 8 r (FP64), 9 s (FP64),
- * 10 global t (FP64).  Block arrays are in the context precision; dst must hold `bytes`. */
+ * 10 global t (FP64), 11 face-block-Jacobi inverses (ntrace x bs x bs, bs = n nv).  Block arrays
+ * are in the context precision; dst must hold `bytes`. */
 int hfr_export(fr_ctx* ctx, int which, void* dst, size_t bytes);
 
 /* One stage of the IMEX step (Algorithm 1):

@@ -29,7 +29,7 @@ LIB_PATH = os.path.join(HERE, "libhfr.so")
 FR_PREC_FP64, FR_PREC_FP32 = 0, 1
 FR_TAB_BE, FR_TAB_SDIRK2 = 0, 1
 FR_PHYS_ADVDIFF, FR_PHYS_NAVIER_STOKES = 0, 1
-EXPORT = {"A": 0, "B": 1, "C": 2, "D": 3, "S": 4, "XB": 5, "xr": 6, "t_k": 7, "r": 8, "s": 9, "t": 10}
+EXPORT = {"A": 0, "B": 1, "C": 2, "D": 3, "S": 4, "XB": 5, "xr": 6, "t_k": 7, "r": 8, "s": 9, "t": 10, "Pinv": 11}
 
 # every symbol declared in include/hfr.h
 ABI_SYMBOLS = [
@@ -300,7 +300,8 @@ class Context:
         shapes = {"A": (E, nA, nA, blk), "B": (E, nA, nT, blk), "C": (E, nT, nA, blk), "D": (E, nT, nT, blk),
                   "S": (E, nT, nT, blk), "XB": (E, nA, nT, blk), "xr": (E, nA, self.torch.float64),
                   "t_k": (E, nT, self.torch.float64), "r": (E, nA, self.torch.float64),
-                  "s": (E, nT, self.torch.float64), "t": (i.ntrace * i.n * i.nv, self.torch.float64)}
+                  "s": (E, nT, self.torch.float64), "t": (i.ntrace * i.n * i.nv, self.torch.float64),
+                  "Pinv": (i.ntrace, i.n * i.nv, i.n * i.nv, blk)}
         *shp, dt = shapes[which]
         out = self.torch.empty(*shp, dtype=dt, device=self.dev)
         self._check(self.lib.hfr_export(self.h, EXPORT[which], _ptr(out), out.numel() * out.element_size()))

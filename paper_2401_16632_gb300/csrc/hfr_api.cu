@@ -493,6 +493,7 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, const fr_config* cfg, voi
   ctx->gm.Z = dalloc<double>(ctx, (size_t)GM_MAXM * std::max(nh, (size_t)1), &rc);
   ctx->gm.partial = dalloc<double>(ctx, (size_t)GM_NBLK * (GM_MAXM + 1), &rc);
   ctx->gm.state = dalloc<GmresState>(ctx, 1, &rc);
+  ctx->gm.ticket = dalloc<unsigned int>(ctx, 1, &rc);
   ctx->duhat = dalloc<double>(ctx, nh, &rc);
   ctx->du = dalloc<double>(ctx, (size_t)Eim * nA, &rc);
   ctx->res_tmp = dalloc<double>(ctx, (size_t)Eim * nA, &rc);
@@ -525,6 +526,7 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, const fr_config* cfg, voi
 #undef UP
   if (cudaMemsetAsync(ctx->status, 0, 2 * sizeof(int), st) != cudaSuccess ||
       cudaMemsetAsync(ctx->dUw, 0, (size_t)E * nA * sizeof(double), st) != cudaSuccess ||
+      cudaMemsetAsync(ctx->gm.ticket, 0, sizeof(unsigned int), st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess) {
     fr_ctx_destroy(ctx);
     return FR_ERR_CUDA;
@@ -708,7 +710,7 @@ static int refine_local(fr_ctx* ctx, const double* rhs, double* x, const double*
     (hfr::count_launch(), k_refine_res<<<nblk(nloc), 256, 0, ctx->stream>>>(Eim, nA, ctx->imp_idx, rhs, x, ctx->dRw, ctx->lin_adt,
                                                       ctx->res_tmp));
     CK(cudaGetLastError());
-    CK(launch_lu_solve(ctx->prec_bytes, Eim, nA, ctx->LU, ctx->piv, ctx->res_tmp, ctx->stream));
+    CK(launch_lu_solve(ctx->prec_bytes, Eim, nA, ctx->nT, ctx->LU, ctx->piv, ctx->res_tmp, ctx->stream));
     (hfr::count_launch(), k_axpy<<<nblk(nloc), 256, 0, ctx->stream>>>(nloc, 1.0, ctx->res_tmp, x));
     CK(cudaGetLastError());
   }
@@ -785,7 +787,7 @@ static void cb_gmatvec(void* c, const GmresState* st, int j, const double* x, do
 }
 static void cb_precond(void* c, const GmresState* st, int j, const double* x, double* y, cudaStream_t s) {
   fr_ctx* ctx = (fr_ctx*)c;
-  launch_precond_apply(trace_args(ctx), ctx->Pinv, x, y, s, &st->kdone, j);
+  launch_precond_apply(ctx->prec_bytes, trace_args(ctx), ctx->Pinv, x, y, s, &st->kdone, j);
 }
 
 static int gmres_impl(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* iters, double* final_rel) {
@@ -857,6 +859,7 @@ extern "C" int hfr_export(fr_ctx* ctx, int which, void* dst, size_t bytes) {
     case 8: src = ctx->r; need = Eim * nA * 8; break;
     case 9: src = ctx->s; need = Eim * nT * 8; break;
     case 10: src = ctx->tg; need = (size_t)ctx->ntrace * ctx->n * ctx->nv * 8; break;
+    case 11: src = ctx->Pinv; need = (size_t)ctx->ntrace * (ctx->n * ctx->nv) * (ctx->n * ctx->nv) * pb; break;
     default: return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_export: unknown array");
   }
   if (bytes < need) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_export: destination too small");

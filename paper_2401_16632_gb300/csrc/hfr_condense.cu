@@ -1,20 +1,404 @@
 // Static condensation of the hybridized Newton system (Pereira & Vermeire, arXiv 2401.16632,
 // Sec. 3.2): per implicit element k,
-//     X = A_k^{-1} [B_k | r_k]          (LU with partial pivoting, largest |a|, lowest row on ties)
-//     S_k = D_k - C_k X_B,  t_k = s_k - C_k x_r          (elemental L^k and t^k)
-// One CTA per element; A and [B | r] are eliminated together in shared memory, the LU factors
-// and pivots are kept for later solves.  T = double (plain) or float (mixed precision).
+//     X = A_k^{-1} [B_k | r_k],   S_k = D_k - C_k X_B,   t_k = s_k - C_k x_r
+// (elemental L^k and t^k of eq. assembly / assembly2).
+//
+// X is formed by in-place Gauss-Jordan elimination with partial pivoting on [A | B | r]
+// (largest |a| among the rows not yet used as pivots, lowest row on ties).  Pivoting is
+// bookkeeping only: rows never move, the pivot of step c is recorded as piv[c].  Every step is
+// a rank-1 update of the whole augmented block, so each thread keeps a fixed register tile of
+// it for the whole elimination.  The in-place scheme leaves (PA)^{-1} where A was (P the row
+// permutation), so later FP64-refinement solves are one mat-vec: A^{-1} y = (PA)^{-1} (P y).
+// Same flop count as LU plus two triangular sweeps for these shapes (nA^2 (nA + nT + 1)).
+//
+// Outputs per element: AinvT = ((PA)^{-1})^T (column c contiguous), piv, X_B, x_r, S, t.
+// T = double (plain path) or float (mixed path).
 #include "hfr_internal.h"
 
 namespace hfr {
 
-constexpr int COND_THREADS = 256;
-
 template <typename T>
 __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
 
+// ------------------------------------------------------------------ register-tiled kernel
+// 256 threads = 16 row groups x 16 column groups; thread (rg, cg) owns physical rows
+// rg + 16 s and columns cg + 16 q of the nA x (nA + nT + 1) augmented block.
+constexpr int GJ_RG = 16, GJ_CG = 16, GJ_THREADS = GJ_RG * GJ_CG;
+
+template <typename T, int NA, int NT>
+struct GJShape {
+  static constexpr int NC = NA + NT + 1;
+  static constexpr int RT = (NA + GJ_RG - 1) / GJ_RG;
+  static constexpr int CT = (NC + GJ_CG - 1) / GJ_CG;
+  static constexpr int R2 = (NT + GJ_RG - 1) / GJ_RG;  // S rows per thread
+  static constexpr int C2 = (NT + 1 + GJ_CG - 1) / GJ_CG;
+  // shared: X (NA x (NT+1)) in logical order | W: (PA)^{-1} staging (NA x NA), later C^T
+  // with leading dimension NT + 1 (NA x (NT+1), conflict-free column reads)
+  static constexpr int WSZ = NA * NA > NA * (NT + 1) ? NA * NA : NA * (NT + 1);
+  static constexpr size_t SMEM = sizeof(T) * ((size_t)NA * (NT + 1) + (size_t)WSZ + 2 * NC + 2 * NA);
+};
+
+template <typename T, int NA, int NT>
+__global__ void __launch_bounds__(GJ_THREADS) k_condense_reg(const __grid_constant__ CondArgs a) {
+  using Sh = GJShape<T, NA, NT>;
+  constexpr int NC = Sh::NC, RT = Sh::RT, CT = Sh::CT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sX = reinterpret_cast<T*>(smem_raw);       // NA x (NT+1), logical rows
+  T* sW = sX + (size_t)NA * (NT + 1);            // WSZ
+  T* pivrow = sW + (size_t)Sh::WSZ;              // 2 x NC (double buffered)
+  T* colbuf = pivrow + 2 * NC;                   // 2 x NA
+  __shared__ int s_piv[2];
+  __shared__ int s_ipiv[NA];
+  __shared__ int s_bad;
+  const int k = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int rg = tid & (GJ_RG - 1), cg = tid >> 4;
+  const T* gA = reinterpret_cast<const T*>(a.A) + (size_t)k * NA * NA;
+  const T* gB = reinterpret_cast<const T*>(a.B) + (size_t)k * NA * NT;
+  const double* gr = a.r + (size_t)k * NA;
+
+  // coalesced staging of [A | B | r] (row-major, ld NC) through the X / W region
+  T* stage = sX;
+  for (int i = tid; i < NA * NA; i += GJ_THREADS) stage[(i / NA) * NC + (i % NA)] = gA[i];
+  for (int i = tid; i < NA * NT; i += GJ_THREADS) stage[(i / NT) * NC + NA + (i % NT)] = gB[i];
+  for (int i = tid; i < NA; i += GJ_THREADS) stage[i * NC + NA + NT] = T(gr[i]);
+  __syncthreads();
+  T m[RT][CT];
+#pragma unroll
+  for (int s = 0; s < RT; ++s) {
+    const int r = rg + GJ_RG * s;
+#pragma unroll
+    for (int q = 0; q < CT; ++q) {
+      const int j = cg + GJ_CG * q;
+      m[s][q] = (r < NA && j < NC) ? stage[r * NC + j] : T(0);
+    }
+  }
+  unsigned used = 0u;  // bit s: own physical row rg + 16 s already a pivot
+  if (tid == 0) s_bad = 0;
+  // pivot search of column c by its column group (one half-warp holds the whole column):
+  // records the pivot, the factors (column c) and 1 + 1/pivot, so that the update below is a
+  // single FMA per entry for every row: column c becomes f - f (1 + 1/p) = -f / p.
+  auto search = [&](int c) {
+    const int buf = c & 1;
+    T* pr = pivrow + buf * NC;
+    T* cb = colbuf + buf * NA;
+    const int qc = c / GJ_CG;
+    T best = T(-1), val = T(0);
+    int bi = 0x7fffffff;
+#pragma unroll
+    for (int s = 0; s < RT; ++s) {
+      const int r = rg + GJ_RG * s;
+      if (r < NA) {
+        T v = T(0);
+#pragma unroll
+        for (int q = 0; q < CT; ++q)
+          if (q == qc) v = m[s][q];
+        cb[r] = v;
+        if (!(used >> s & 1u)) {
+          const T av = tabs(v);
+          if (av > best || (av == best && r < bi)) { best = av; bi = r; val = v; }
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+      const T ob = __shfl_xor_sync(0x0000ffffu << (tid & 16), best, o);
+      const int oi = __shfl_xor_sync(0x0000ffffu << (tid & 16), bi, o);
+      const T ov = __shfl_xor_sync(0x0000ffffu << (tid & 16), val, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; val = ov; }
+    }
+    if (rg == 0) {
+      s_piv[buf] = bi;
+      s_ipiv[bi] = c;
+      a.piv[(size_t)k * NA + c] = bi;
+      if (!(best > T(0))) s_bad = 1;
+      pr[c] = T(1) + (val != T(0) ? T(1) / val : T(0));
+    }
+  };
+  if (cg == 0) search(0);
+  __syncthreads();
+  for (int c = 0; c < NA; ++c) {
+    const int buf = c & 1;
+    T* pr = pivrow + buf * NC;
+    const T* cb = colbuf + buf * NA;
+    const int p = s_piv[buf];
+    const T inv = pr[c] - T(1);
+    const int sp = p / GJ_RG;
+    const bool own_p = (p & (GJ_RG - 1)) == rg;
+    // owners of the pivot row publish it, normalised (column c keeps 1 + 1/pivot)
+    if (own_p) {
+#pragma unroll
+      for (int s = 0; s < RT; ++s)
+        if (s == sp) {
+#pragma unroll
+          for (int q = 0; q < CT; ++q) {
+            const int j = cg + GJ_CG * q;
+            if (j < NC && j != c) pr[j] = m[s][q] * inv;
+          }
+        }
+      used |= 1u << sp;
+    }
+    __syncthreads();
+    // rank-1 update of every row (one FMA per entry), then the pivot row takes the normalised row
+    T pj[CT];
+#pragma unroll
+    for (int q = 0; q < CT; ++q) {
+      const int j = cg + GJ_CG * q;
+      pj[q] = j < NC ? pr[j] : T(0);
+    }
+#pragma unroll
+    for (int s = 0; s < RT; ++s) {
+      const int r = rg + GJ_RG * s;
+      const T f = r < NA ? cb[r] : T(0);
+#pragma unroll
+      for (int q = 0; q < CT; ++q) m[s][q] -= f * pj[q];
+    }
+    if (own_p) {
+#pragma unroll
+      for (int s = 0; s < RT; ++s)
+        if (s == sp) {
+#pragma unroll
+          for (int q = 0; q < CT; ++q) {
+            const int j = cg + GJ_CG * q;
+            m[s][q] = j == c ? inv : pj[q];
+          }
+        }
+    }
+    // look-ahead: the owners of column c + 1 search its pivot right away
+    if (c + 1 < NA && cg == ((c + 1) & (GJ_CG - 1))) search(c + 1);
+    __syncthreads();
+  }
+  __syncthreads();
+  if (tid == 0 && s_bad) {
+    atomicOr(a.status, DEV_ERR_SINGULAR);
+    atomicMin(a.status + 1, k);
+  }
+  // stage (PA)^{-1} transposed and X in logical row order
+#pragma unroll
+  for (int s = 0; s < RT; ++s) {
+    const int r = rg + GJ_RG * s;
+    if (r >= NA) continue;
+    const int lr = s_ipiv[r];
+#pragma unroll
+    for (int q = 0; q < CT; ++q) {
+      const int j = cg + GJ_CG * q;
+      if (j >= NC) continue;
+      if (j < NA)
+        sW[(size_t)j * NA + lr] = m[s][q];  // (PA)^{-1}[lr][j] stored at [j][lr]
+      else
+        sX[(size_t)lr * (NT + 1) + (j - NA)] = m[s][q];
+    }
+  }
+  __syncthreads();
+  T* gInv = reinterpret_cast<T*>(a.LU) + (size_t)k * NA * NA;
+  T* gXB = reinterpret_cast<T*>(a.XB) + (size_t)k * NA * NT;
+  for (int i = tid; i < NA * NA; i += GJ_THREADS) gInv[i] = sW[i];
+  for (int i = tid; i < NA * (NT + 1); i += GJ_THREADS) {
+    const int r = i / (NT + 1), c = i % (NT + 1);
+    if (c < NT)
+      gXB[(size_t)r * NT + c] = sX[i];
+    else
+      a.xr[(size_t)k * NA + r] = double(sX[i]);
+  }
+  __syncthreads();
+  // S = D - C X_B and t = s - C x_r  (C staged transposed in smem: sW[l][i], ld NT + 1)
+  const T* gC = reinterpret_cast<const T*>(a.C) + (size_t)k * NT * NA;
+  const T* gD = reinterpret_cast<const T*>(a.D) + (size_t)k * NT * NT;
+  for (int i = tid; i < NT * NA; i += GJ_THREADS) {
+    const int row = i / NA, l = i % NA;
+    sW[(size_t)l * (NT + 1) + row] = gC[i];
+  }
+  __syncthreads();
+  // thread (rg, cg): output rows i = cg + 16 s, columns j = rg + 16 q (coalesced stores)
+  constexpr int R2 = Sh::R2, C2 = Sh::C2;
+  T acc[R2][C2];
+#pragma unroll
+  for (int s = 0; s < R2; ++s)
+#pragma unroll
+    for (int q = 0; q < C2; ++q) acc[s][q] = T(0);
+  for (int l = 0; l < NA; ++l) {
+    T cv[R2], xv[C2];
+#pragma unroll
+    for (int s = 0; s < R2; ++s) {
+      const int i = cg + GJ_CG * s;
+      cv[s] = i < NT ? sW[(size_t)l * (NT + 1) + i] : T(0);
+    }
+#pragma unroll
+    for (int q = 0; q < C2; ++q) {
+      const int j = rg + GJ_RG * q;
+      xv[q] = j <= NT ? sX[(size_t)l * (NT + 1) + j] : T(0);
+    }
+#pragma unroll
+    for (int s = 0; s < R2; ++s)
+#pragma unroll
+      for (int q = 0; q < C2; ++q) acc[s][q] += cv[s] * xv[q];
+  }
+  T* gS = reinterpret_cast<T*>(a.S) + (size_t)k * NT * NT;
+#pragma unroll
+  for (int s = 0; s < R2; ++s) {
+    const int i = cg + GJ_CG * s;
+    if (i >= NT) continue;
+#pragma unroll
+    for (int q = 0; q < C2; ++q) {
+      const int j = rg + GJ_RG * q;
+      if (j < NT)
+        gS[(size_t)i * NT + j] = gD[(size_t)i * NT + j] - acc[s][q];
+      else if (j == NT)
+        a.t[(size_t)k * NT + i] = a.s[(size_t)k * NT + i] - double(acc[s][q]);
+    }
+  }
+}
+
+// ------------------------------------------------------------- generic shared-memory kernel
+// Same algorithm and outputs for any (nA, nT) and either precision; the augmented block lives
+// in shared memory.  Used where the register tile does not fit (e.g. FP64 with nA >= 100).
+constexpr int GJS_THREADS = 256;
+
 template <typename T>
-__global__ void __launch_bounds__(COND_THREADS) k_condense(const __grid_constant__ CondArgs a) {
+__global__ void __launch_bounds__(GJS_THREADS) k_condense_smem(const __grid_constant__ CondArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nA = a.nA, nT = a.nT, nc = nA + nT + 1;
+  const int big = nA > nT ? nA : nT;
+  T* M = reinterpret_cast<T*>(smem_raw);  // nA x nc, physical rows
+  T* W = M + (size_t)nA * nc;             // big x nA
+  T* pr = W + (size_t)big * nA;           // nc
+  T* cb = pr + nc;                        // nA
+  int* ipiv = reinterpret_cast<int*>(cb + nA);
+  unsigned char* used = reinterpret_cast<unsigned char*>(ipiv + nA);
+  __shared__ int s_p;
+  __shared__ int s_bad;
+  const int k = blockIdx.x, tid = threadIdx.x;
+  const T* gA = reinterpret_cast<const T*>(a.A) + (size_t)k * nA * nA;
+  const T* gB = reinterpret_cast<const T*>(a.B) + (size_t)k * nA * nT;
+  for (int i = tid; i < nA * nc; i += GJS_THREADS) {
+    const int r = i / nc, j = i % nc;
+    M[i] = j < nA ? gA[(size_t)r * nA + j] : (j < nA + nT ? gB[(size_t)r * nT + (j - nA)] : T(a.r[(size_t)k * nA + r]));
+  }
+  for (int i = tid; i < nA; i += GJS_THREADS) used[i] = 0;
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  for (int c = 0; c < nA; ++c) {
+    if (tid < 32) {
+      T best = T(-1);
+      int bi = 0x7fffffff;
+      for (int r = tid; r < nA; r += 32) {
+        if (used[r]) continue;
+        const T v = tabs(M[(size_t)r * nc + c]);
+        if (v > best || (v == best && r < bi)) { best = v; bi = r; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (tid == 0) {
+        s_p = bi;
+        used[bi] = 1;
+        ipiv[bi] = c;
+        a.piv[(size_t)k * nA + c] = bi;
+        if (!(best > T(0))) s_bad = 1;
+      }
+    }
+    __syncthreads();
+    const int p = s_p;
+    const T pv = M[(size_t)p * nc + c];
+    const T inv = pv != T(0) ? T(1) / pv : T(0);
+    for (int j = tid; j < nc; j += GJS_THREADS) pr[j] = j == c ? inv : M[(size_t)p * nc + j] * inv;
+    for (int r = tid; r < nA; r += GJS_THREADS) cb[r] = M[(size_t)r * nc + c];
+    __syncthreads();
+    for (int i = tid; i < nA * nc; i += GJS_THREADS) {
+      const int r = i / nc, j = i % nc;
+      if (r == p)
+        M[i] = pr[j];
+      else
+        M[i] = (j == c ? T(0) : M[i]) - cb[r] * pr[j];
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && s_bad) {
+    atomicOr(a.status, DEV_ERR_SINGULAR);
+    atomicMin(a.status + 1, k);
+  }
+  T* gInv = reinterpret_cast<T*>(a.LU) + (size_t)k * nA * nA;
+  T* gXB = reinterpret_cast<T*>(a.XB) + (size_t)k * nA * nT;
+  for (int i = tid; i < nA * nc; i += GJS_THREADS) {
+    const int r = i / nc, j = i % nc;
+    const int lr = ipiv[r];
+    if (j < nA)
+      gInv[(size_t)j * nA + lr] = M[i];
+    else if (j < nA + nT)
+      gXB[(size_t)lr * nT + (j - nA)] = M[i];
+    else
+      a.xr[(size_t)k * nA + lr] = double(M[i]);
+  }
+  // C into W; X rows in logical order are read through the pivot sequence
+  const T* gC = reinterpret_cast<const T*>(a.C) + (size_t)k * nT * nA;
+  const T* gD = reinterpret_cast<const T*>(a.D) + (size_t)k * nT * nT;
+  const int* pv = a.piv + (size_t)k * nA;
+  for (int i = tid; i < nT * nA; i += GJS_THREADS) W[i] = gC[i];
+  __syncthreads();
+  T* gS = reinterpret_cast<T*>(a.S) + (size_t)k * nT * nT;
+  for (int it = tid; it < nT * (nT + 1); it += GJS_THREADS) {
+    const int i = it / (nT + 1), j = it % (nT + 1);
+    T acc = T(0);
+    for (int l = 0; l < nA; ++l) acc += W[(size_t)i * nA + l] * M[(size_t)pv[l] * nc + nA + j];
+    if (j < nT)
+      gS[(size_t)i * nT + j] = gD[(size_t)i * nT + j] - acc;
+    else
+      a.t[(size_t)k * nT + i] = a.s[(size_t)k * nT + i] - double(acc);
+  }
+}
+
+// y = A^{-1} b = (PA)^{-1} (P b), in place on b.  One warp per element; lane owns rows
+// lane + 32 q; the stored transpose makes each step a coalesced row read.
+constexpr int INV_SLOTS = 5;  // nA <= 160
+template <typename T>
+__global__ void k_inv_apply(int Eim, int nA, const T* __restrict__ AinvT, const int* __restrict__ piv,
+                            double* __restrict__ b) {
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (k >= Eim) return;
+  const T* W = AinvT + (size_t)k * nA * nA;
+  const int* pv = piv + (size_t)k * nA;
+  double* bk = b + (size_t)k * nA;
+  double pb[INV_SLOTS], y[INV_SLOTS];
+#pragma unroll
+  for (int q = 0; q < INV_SLOTS; ++q) {
+    const int j = lane + 32 * q;
+    pb[q] = j < nA ? bk[pv[j]] : 0.0;  // (P b)_j
+    y[q] = 0.0;
+  }
+#pragma unroll
+  for (int q = 0; q < INV_SLOTS; ++q) {
+    if (32 * q >= nA) break;
+    for (int jj = 0; jj < 32; ++jj) {
+      const int j = 32 * q + jj;
+      if (j >= nA) break;
+      const double bj = __shfl_sync(0xffffffffu, pb[q], jj);
+#pragma unroll
+      for (int qq = 0; qq < INV_SLOTS; ++qq) {
+        const int c = lane + 32 * qq;
+        if (c < nA) y[qq] += double(W[(size_t)j * nA + c]) * bj;
+      }
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < INV_SLOTS; ++q) {
+    const int c = lane + 32 * q;
+    if (c < nA) bk[c] = y[q];
+  }
+}
+
+// ---------------------------------------------------------------- LU kernel (FP64 path)
+// LU with partial pivoting (full-row interchanges) of A applied to [B | r] in shared memory,
+// then back substitution: X = A^{-1}[B | r] with nA^3/3 + nA^2 (nT+1) multiply-adds, ~25 % fewer
+// than Gauss-Jordan, which is what counts where the FP64 pipe is the roof.  Keeps LU + piv.
+constexpr int LU_THREADS = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(LU_THREADS) k_condense_lu(const __grid_constant__ CondArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nA = a.nA, nT = a.nT, ldx = nT + 1;
   const int k = blockIdx.x;
@@ -28,8 +412,8 @@ __global__ void __launch_bounds__(COND_THREADS) k_condense(const __grid_constant
   const T* gB = reinterpret_cast<const T*>(a.B) + (size_t)k * nA * nT;
   const T* gC = reinterpret_cast<const T*>(a.C) + (size_t)k * nT * nA;
   const T* gD = reinterpret_cast<const T*>(a.D) + (size_t)k * nT * nT;
-  for (int i = tid; i < nA * nA; i += COND_THREADS) sA[i] = gA[i];
-  for (int i = tid; i < nA * ldx; i += COND_THREADS) {
+  for (int i = tid; i < nA * nA; i += LU_THREADS) sA[i] = gA[i];
+  for (int i = tid; i < nA * ldx; i += LU_THREADS) {
     const int r = i / ldx, c = i % ldx;
     sX[i] = c < nT ? gB[(size_t)r * nT + c] : T(a.r[(size_t)k * nA + r]);
   }
@@ -59,12 +443,12 @@ __global__ void __launch_bounds__(COND_THREADS) k_condense(const __grid_constant
     __syncthreads();
     const int p = s_piv;
     if (p != c) {
-      for (int j = tid; j < nA; j += COND_THREADS) {
+      for (int j = tid; j < nA; j += LU_THREADS) {
         T t0 = sA[c * nA + j];
         sA[c * nA + j] = sA[p * nA + j];
         sA[p * nA + j] = t0;
       }
-      for (int j = tid; j < ldx; j += COND_THREADS) {
+      for (int j = tid; j < ldx; j += LU_THREADS) {
         T t0 = sX[c * ldx + j];
         sX[c * ldx + j] = sX[p * ldx + j];
         sX[p * ldx + j] = t0;
@@ -73,12 +457,12 @@ __global__ void __launch_bounds__(COND_THREADS) k_condense(const __grid_constant
     __syncthreads();
     const T pv = sA[c * nA + c];
     const T inv = pv != T(0) ? T(1) / pv : T(0);
-    for (int i = c + 1 + tid; i < nA; i += COND_THREADS) sA[i * nA + c] *= inv;
+    for (int i = c + 1 + tid; i < nA; i += LU_THREADS) sA[i * nA + c] *= inv;
     __syncthreads();
     const int nr = nA - c - 1;
     const int ncA = nA - c - 1;
     const int ncols = ncA + ldx;
-    for (int it = tid; it < nr * ncols; it += COND_THREADS) {
+    for (int it = tid; it < nr * ncols; it += LU_THREADS) {
       const int i = c + 1 + it / ncols;
       const int jj = it % ncols;
       const T l = sA[i * nA + c];
@@ -96,9 +480,9 @@ __global__ void __launch_bounds__(COND_THREADS) k_condense(const __grid_constant
   for (int c = nA - 1; c >= 0; --c) {
     const T pv = sA[c * nA + c];
     const T inv = pv != T(0) ? T(1) / pv : T(0);
-    for (int j = tid; j < ldx; j += COND_THREADS) sX[c * ldx + j] *= inv;
+    for (int j = tid; j < ldx; j += LU_THREADS) sX[c * ldx + j] *= inv;
     __syncthreads();
-    for (int it = tid; it < c * ldx; it += COND_THREADS) {
+    for (int it = tid; it < c * ldx; it += LU_THREADS) {
       const int i = it / ldx, j = it % ldx;
       sX[i * ldx + j] -= sA[i * nA + c] * sX[c * ldx + j];
     }
@@ -111,8 +495,8 @@ __global__ void __launch_bounds__(COND_THREADS) k_condense(const __grid_constant
   // outputs: LU, X_B, x_r
   T* gLU = reinterpret_cast<T*>(a.LU) + (size_t)k * nA * nA;
   T* gXB = reinterpret_cast<T*>(a.XB) + (size_t)k * nA * nT;
-  for (int i = tid; i < nA * nA; i += COND_THREADS) gLU[i] = sA[i];
-  for (int i = tid; i < nA * ldx; i += COND_THREADS) {
+  for (int i = tid; i < nA * nA; i += LU_THREADS) gLU[i] = sA[i];
+  for (int i = tid; i < nA * ldx; i += LU_THREADS) {
     const int r = i / ldx, c = i % ldx;
     if (c < nT)
       gXB[(size_t)r * nT + c] = sX[i];
@@ -121,10 +505,10 @@ __global__ void __launch_bounds__(COND_THREADS) k_condense(const __grid_constant
   }
   __syncthreads();
   // C into the freed A region, then S = D - C X_B and t = s - C x_r
-  for (int i = tid; i < nT * nA; i += COND_THREADS) sA[i] = gC[i];
+  for (int i = tid; i < nT * nA; i += LU_THREADS) sA[i] = gC[i];
   __syncthreads();
   T* gS = reinterpret_cast<T*>(a.S) + (size_t)k * nT * nT;
-  for (int it = tid; it < nT * ldx; it += COND_THREADS) {
+  for (int it = tid; it < nT * ldx; it += LU_THREADS) {
     const int i = it / ldx, j = it % ldx;
     T acc = T(0);
     for (int l = 0; l < nA; ++l) acc += sA[i * nA + l] * sX[l * ldx + j];
@@ -135,69 +519,147 @@ __global__ void __launch_bounds__(COND_THREADS) k_condense(const __grid_constant
   }
 }
 
-// x = A^{-1} b with the stored LU factors (row interchanges recorded in piv), in place on b.
+// x = A^{-1} b with stored LU factors and row interchanges (FP64 path), in place on b.
+// One warp per element; x distributed over lanes (row i in lane i % 32, slot i / 32).
 template <typename T>
 __global__ void k_lu_solve(int Eim, int nA, const T* __restrict__ LU, const int* __restrict__ piv,
                            double* __restrict__ b) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* x = reinterpret_cast<double*>(smem_raw);
-  const int k = blockIdx.x;
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (k >= Eim) return;
   const T* L = LU + (size_t)k * nA * nA;
   const int* pv = piv + (size_t)k * nA;
   double* bk = b + (size_t)k * nA;
-  for (int i = threadIdx.x; i < nA; i += blockDim.x) x[i] = bk[i];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int c = 0; c < nA; ++c) {
-      const int p = pv[c];
-      if (p != c) {
-        double t0 = x[c];
-        x[c] = x[p];
-        x[p] = t0;
-      }
+  double x[INV_SLOTS];
+#pragma unroll
+  for (int q = 0; q < INV_SLOTS; ++q) {
+    const int i = lane + 32 * q;
+    x[q] = i < nA ? bk[i] : 0.0;
+  }
+  for (int c = 0; c < nA; ++c) {  // row interchanges in order
+    const int p = pv[c];
+    if (p == c) continue;
+    const int qc = c >> 5, lc = c & 31, qp = p >> 5, lp = p & 31;
+    double vc = 0.0, vp = 0.0;
+#pragma unroll
+    for (int q = 0; q < INV_SLOTS; ++q) {
+      const double tc = __shfl_sync(0xffffffffu, x[q], lc);
+      const double tp = __shfl_sync(0xffffffffu, x[q], lp);
+      if (q == qc) vc = tc;
+      if (q == qp) vp = tp;
+    }
+#pragma unroll
+    for (int q = 0; q < INV_SLOTS; ++q) {
+      if (q == qc && lane == lc) x[q] = vp;
+      if (q == qp && lane == lp) x[q] = vc;
     }
   }
-  __syncthreads();
-  // forward (unit lower), one warp cooperating per column
-  for (int c = 0; c < nA; ++c) {
-    const double xc = x[c];
-    for (int i = c + 1 + threadIdx.x; i < nA; i += blockDim.x) x[i] -= double(L[(size_t)i * nA + c]) * xc;
-    __syncthreads();
+  for (int c = 0; c < nA - 1; ++c) {  // unit lower
+    const int qc = c >> 5, lc = c & 31;
+    double xc = 0.0;
+#pragma unroll
+    for (int q = 0; q < INV_SLOTS; ++q) {
+      const double t = __shfl_sync(0xffffffffu, x[q], lc);
+      if (q == qc) xc = t;
+    }
+#pragma unroll
+    for (int q = 0; q < INV_SLOTS; ++q) {
+      const int i = lane + 32 * q;
+      if (i > c && i < nA) x[q] -= double(L[(size_t)i * nA + c]) * xc;
+    }
   }
-  for (int c = nA - 1; c >= 0; --c) {
-    if (threadIdx.x == 0) x[c] /= double(L[(size_t)c * nA + c]);
-    __syncthreads();
-    const double xc = x[c];
-    for (int i = threadIdx.x; i < c; i += blockDim.x) x[i] -= double(L[(size_t)i * nA + c]) * xc;
-    __syncthreads();
+  for (int c = nA - 1; c >= 0; --c) {  // upper
+    const int qc = c >> 5, lc = c & 31;
+    const double d = double(L[(size_t)c * nA + c]);
+#pragma unroll
+    for (int q = 0; q < INV_SLOTS; ++q)
+      if (q == qc && lane == lc) x[q] = x[q] / d;
+    double xc = 0.0;
+#pragma unroll
+    for (int q = 0; q < INV_SLOTS; ++q) {
+      const double t = __shfl_sync(0xffffffffu, x[q], lc);
+      if (q == qc) xc = t;
+    }
+#pragma unroll
+    for (int q = 0; q < INV_SLOTS; ++q) {
+      const int i = lane + 32 * q;
+      if (i < c) x[q] -= double(L[(size_t)i * nA + c]) * xc;
+    }
   }
-  for (int i = threadIdx.x; i < nA; i += blockDim.x) bk[i] = x[i];
+#pragma unroll
+  for (int q = 0; q < INV_SLOTS; ++q) {
+    const int i = lane + 32 * q;
+    if (i < nA) bk[i] = x[q];
+  }
 }
 
-template <typename T>
-static cudaError_t cond_impl(const CondArgs& a, cudaStream_t st) {
-  const int rows2 = a.nA > a.nT ? a.nA : a.nT;
-  size_t smem = sizeof(T) * ((size_t)rows2 * a.nA + (size_t)a.nA * (a.nT + 1));
-  cudaError_t err = cudaFuncSetAttribute(k_condense<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <typename T, int NA, int NT>
+static cudaError_t cond_reg(const CondArgs& a, cudaStream_t st) {
+  const size_t smem = GJShape<T, NA, NT>::SMEM;
+  cudaError_t err = cudaFuncSetAttribute(k_condense_reg<T, NA, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  if (a.Eim == 0) return cudaSuccess;
-  (hfr::count_launch(), k_condense<T><<<a.Eim, COND_THREADS, smem, st>>>(a));
+  (hfr::count_launch(), k_condense_reg<T, NA, NT><<<a.Eim, GJ_THREADS, smem, st>>>(a));
   return cudaGetLastError();
 }
 
-cudaError_t launch_condense(int prec_bytes, const CondArgs& a, cudaStream_t st) {
-  return prec_bytes == 8 ? cond_impl<double>(a, st) : cond_impl<float>(a, st);
+template <typename T>
+static cudaError_t cond_smem(const CondArgs& a, cudaStream_t st) {
+  const int nc = a.nA + a.nT + 1, big = a.nA > a.nT ? a.nA : a.nT;
+  const size_t smem = sizeof(T) * ((size_t)a.nA * nc + (size_t)big * a.nA + nc + a.nA) + sizeof(int) * a.nA + a.nA;
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t err = cudaFuncSetAttribute(k_condense_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  (hfr::count_launch(), k_condense_smem<T><<<a.Eim, GJS_THREADS, smem, st>>>(a));
+  return cudaGetLastError();
 }
 
-cudaError_t launch_lu_solve(int prec_bytes, int Eim, int nA, const void* LU, const int* piv, double* b,
-                            cudaStream_t st) {
+template <typename T>
+static cudaError_t cond_dispatch(const CondArgs& a, cudaStream_t st) {
+  if (a.Eim == 0) return cudaSuccess;
+  const int nA = a.nA, nT = a.nT;
+  if (nA == 9 && nT == 12) return cond_reg<T, 9, 12>(a, st);
+  if (nA == 16 && nT == 16) return cond_reg<T, 16, 16>(a, st);
+  if (nA == 36 && nT == 48) return cond_reg<T, 36, 48>(a, st);
+  if (nA == 64 && nT == 64) return cond_reg<T, 64, 64>(a, st);
+  if (nA == 100 && nT == 80) return cond_reg<T, 100, 80>(a, st);
+  return cond_smem<T>(a, st);
+}
+
+template <typename T>
+static cudaError_t cond_lu(const CondArgs& a, cudaStream_t st) {
+  const int rows2 = a.nA > a.nT ? a.nA : a.nT;
+  size_t smem = sizeof(T) * ((size_t)rows2 * a.nA + (size_t)a.nA * (a.nT + 1));
+  if (smem > 227 * 1024) return cond_dispatch<T>(a, st);
+  cudaError_t err = cudaFuncSetAttribute(k_condense_lu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  if (a.Eim == 0) return cudaSuccess;
+  (hfr::count_launch(), k_condense_lu<T><<<a.Eim, LU_THREADS, smem, st>>>(a));
+  return cudaGetLastError();
+}
+
+// FP64: LU factors (fewest FP64 operations); FP32: in-place Gauss-Jordan (register tiles).
+bool condense_uses_lu(int prec_bytes, int nA, int nT) {
+  const int rows2 = nA > nT ? nA : nT;
+  return prec_bytes == 8 && sizeof(double) * ((size_t)rows2 * nA + (size_t)nA * (nT + 1)) <= 227 * 1024;
+}
+
+cudaError_t launch_condense(int prec_bytes, const CondArgs& a, cudaStream_t st) {
+  if (condense_uses_lu(prec_bytes, a.nA, a.nT)) return cond_lu<double>(a, st);
+  return prec_bytes == 8 ? cond_dispatch<double>(a, st) : cond_dispatch<float>(a, st);
+}
+
+cudaError_t launch_lu_solve(int prec_bytes, int Eim, int nA, int nT_of_last, const void* LU, const int* piv,
+                            double* b, cudaStream_t st) {
   if (Eim == 0) return cudaSuccess;
-  size_t smem = sizeof(double) * nA;
-  if (prec_bytes == 8)
-    (hfr::count_launch(), k_lu_solve<double><<<Eim, 64, smem, st>>>(Eim, nA, (const double*)LU, piv, b));
+  if (nA > 32 * INV_SLOTS) return cudaErrorInvalidValue;
+  const int threads = 128;
+  const int grid = (Eim * 32 + threads - 1) / threads;
+  if (condense_uses_lu(prec_bytes, nA, nT_of_last))
+    (hfr::count_launch(), k_lu_solve<double><<<grid, threads, 0, st>>>(Eim, nA, (const double*)LU, piv, b));
+  else if (prec_bytes == 8)
+    (hfr::count_launch(), k_inv_apply<double><<<grid, threads, 0, st>>>(Eim, nA, (const double*)LU, piv, b));
   else
-    (hfr::count_launch(), k_lu_solve<float><<<Eim, 64, smem, st>>>(Eim, nA, (const float*)LU, piv, b));
+    (hfr::count_launch(), k_inv_apply<float><<<grid, threads, 0, st>>>(Eim, nA, (const float*)LU, piv, b));
   return cudaGetLastError();
 }
 

@@ -87,8 +87,10 @@ struct CondArgs {
 };
 cudaError_t launch_condense(int prec_bytes, const CondArgs& a, cudaStream_t st);
 
-// LU solve with the stored factors: x = A^{-1} b, in place on b (Eim x nA, FP64 vectors).
-cudaError_t launch_lu_solve(int prec_bytes, int Eim, int nA, const void* LU, const int* piv, double* b,
+// x = A^{-1} b with the stored factorisation (LU + interchanges or in-place inverse, as chosen
+// by condense_uses_lu), in place on b (Eim x nA, FP64 vectors).
+bool condense_uses_lu(int prec_bytes, int nA, int nT);
+cudaError_t launch_lu_solve(int prec_bytes, int Eim, int nA, int nT, const void* LU, const int* piv, double* b,
                             cudaStream_t st);
 
 // Trace operators
@@ -101,7 +103,8 @@ struct TraceArgs {
 cudaError_t launch_trace_matvec(int prec_bytes, const TraceArgs& a, const double* x, double* y, cudaStream_t st,
                                 const int* gate = nullptr, int gj = 0);
 cudaError_t launch_precond_build(int prec_bytes, const TraceArgs& a, double* Pinv, int* status, cudaStream_t st);
-cudaError_t launch_precond_apply(const TraceArgs& a, const double* Pinv, const double* x, double* y,
+// Pinv holds the inverses in the block precision (double or float storage in the same buffer)
+cudaError_t launch_precond_apply(int prec_bytes, const TraceArgs& a, const double* Pinv, const double* x, double* y,
                                  cudaStream_t st, const int* gate = nullptr, int gj = 0);
 cudaError_t launch_assemble_t(const TraceArgs& a, const double* te, double* t, cudaStream_t st);
 cudaError_t launch_backsolve(int prec_bytes, const TraceArgs& a, int Eim, int nA, const void* XB, const double* xr,

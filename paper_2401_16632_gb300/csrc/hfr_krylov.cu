@@ -14,49 +14,85 @@ constexpr int KB = 256;  // threads per block of the vector kernels
 
 __device__ __forceinline__ bool gated(const GmresState* st, int j) { return st->kdone >= 0 && j >= st->kdone; }
 
-__device__ __forceinline__ double block_sum(double v, double* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) red[w] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-  return s;  // valid in thread 0
-}
+// One fused pass of classical Gram-Schmidt (twice) over the Krylov basis:
+//   pre 0: (nothing)   1: w -= sum_i hc_i V_i   2: w -= sum_i h2_i V_i      (i < na)
+// then the dots out_i = D_i . w (i < nd; D = V, or D = w itself for a norm) accumulated eight
+// at a time in registers, one partial per block, and the last block to finish (ticket) reduces
+// the partials in a fixed order (deterministic) and applies `mode`:
+//   0: hc[i] = s   1: h2[i] = s, hc[i] += s   2: hc[j+1] = sqrt(s) + Givens update of column j
+//   3: beta = sqrt(s)   4: bnorm = sqrt(s)
+// Each thread re-reads only its own w entries after updating them, so no grid-wide barrier is
+// needed between the update and the dots.
+__device__ void givens_update(GmresState* st, int j, double rtol, int m);
 
-// partial[b * (GM_MAXM + 1) + i] = sum over block b's slice of V_i . w   (i < nvec)
-__global__ void k_dot_part(const GmresState* st, int j, const double* __restrict__ V, size_t n, int nvec,
-                           const double* __restrict__ w, double* __restrict__ partial) {
-  if (st && gated(st, j)) return;
-  __shared__ double red[KB / 32];
+__global__ void __launch_bounds__(KB) k_cgs(GmresState* st, int j, const double* __restrict__ V, size_t n, int na,
+                                            int pre, const double* D, int nd, double* w,
+                                            double* __restrict__ partial, unsigned int* ticket, int mode, double rtol,
+                                            int m) {
+  if (mode <= 2 && gated(st, j)) return;
+  __shared__ double red[GM_MAXM + 1][KB / 32];
+  __shared__ bool last;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   const size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  for (int i = 0; i < nvec; ++i) {
-    const double* Vi = V + (size_t)i * n;
-    double s = 0.0;
-    for (size_t x = i0; x < n; x += stride) s += Vi[x] * w[x];
-    s = block_sum(s, red);
-    if (threadIdx.x == 0) partial[(size_t)blockIdx.x * (GM_MAXM + 1) + i] = s;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (pre) {
+    const double* c = pre == 1 ? st->hc : st->h2;
+    for (size_t x = i0; x < n; x += stride) {
+      double acc = 0.0;
+      for (int i = 0; i < na; ++i) acc += c[i] * V[(size_t)i * n + x];
+      w[x] -= acc;
+    }
   }
-}
-
-// out[i] = sum_b partial[b][i] (mode 0: store to hc, 1: store to h2 and add into hc,
-// 2: store sqrt into hc[j+1] (norm), 3: store sqrt into beta / bnorm)
-__global__ void k_dot_final(GmresState* st, int j, const double* __restrict__ partial, int nblk, int nvec,
-                            int mode) {
-  if (mode <= 2 && gated(st, j)) return;
-  const int i = threadIdx.x;
-  if (i >= nvec) return;
-  double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * (GM_MAXM + 1) + i];
-  if (mode == 0) st->hc[i] = s;
-  else if (mode == 1) { st->h2[i] = s; st->hc[i] += s; }
-  else if (mode == 2) st->hc[j + 1] = sqrt(s);
-  else if (mode == 3) st->beta = sqrt(s);
-  else if (mode == 4) st->bnorm = sqrt(s);
+  // warp sums of eight dots at a time into shared memory; one barrier for the whole pass
+  for (int c0 = 0; c0 < nd; c0 += 8) {
+    double acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    for (size_t x = i0; x < n; x += stride) {
+      const double wx = w[x];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (c0 + q < nd) acc[q] += D[(size_t)(c0 + q) * n + x] * wx;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      double v = acc[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0 && c0 + q < nd) red[c0 + q][wid] = v;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nd; i += KB) {
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < KB / 32; ++k) t += red[i][k];
+    partial[(size_t)blockIdx.x * (GM_MAXM + 1) + i] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int i = wid; i < nd; i += KB / 32) {
+    double t = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(&partial[(size_t)b * (GM_MAXM + 1) + i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) {
+      if (mode == 0) st->hc[i] = t;
+      else if (mode == 1) { st->h2[i] = t; st->hc[i] += t; }
+      else if (mode == 2) st->hc[j + 1] = sqrt(t);
+      else if (mode == 3) st->beta = sqrt(t);
+      else st->bnorm = sqrt(t);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *ticket = 0u;
+    if (mode == 2) givens_update(st, j, rtol, m);
+  }
 }
 
 // w -= sum_i c_i V_i  (which = 0: c = hc, 1: c = h2);  or x += sum_i y_i Z_i (which = 2)
@@ -74,8 +110,7 @@ __global__ void k_axpy_multi(const GmresState* st, int j, const double* __restri
 }
 
 // Givens update for column j; decides the end of the cycle
-__global__ void k_givens(GmresState* st, int j, double rtol, int m) {
-  if (gated(st, j) || threadIdx.x != 0) return;
+__device__ void givens_update(GmresState* st, int j, double rtol, int m) {
   double* h = st->hc;
   for (int i = 0; i < j; ++i) {
     const double a = h[i], b = h[i + 1];
@@ -161,11 +196,12 @@ static int grid_for(size_t n) {
   return (int)g;
 }
 
-// ||v||^2 partials + final into the given mode slot
-static void norm_into(GmresState* st, int j, const double* v, size_t n, double* partial, int mode, cudaStream_t s) {
+// ||v||^2 into the given mode slot (mode 2 also performs the Givens update)
+static void norm_into(const GmresBuffers& b, int j, double* v, size_t n, int mode, double rtol, int m,
+                      cudaStream_t s) {
   const int nb = grid_for(n);
-  (hfr::count_launch(), k_dot_part<<<nb, KB, 0, s>>>(mode <= 2 ? st : nullptr, j, v, n, 1, v, partial));
-  (hfr::count_launch(), k_dot_final<<<1, 64, 0, s>>>(st, j, partial, nb, 1, mode));
+  (hfr::count_launch(), k_cgs<<<nb, KB, 0, s>>>(b.state, j, nullptr, n, 0, 0, v, 1, v, b.partial, b.ticket, mode,
+                                                 rtol, m));
 }
 
 int run_gmres(const GmresOps& ops, const GmresBuffers& b, const double* t, double* x, double rtol, int restart,
@@ -175,7 +211,7 @@ int run_gmres(const GmresOps& ops, const GmresBuffers& b, const double* t, doubl
   GmresState* st = b.state;
   const int nb = grid_for(n);
   (hfr::count_launch(), k_reset_state<<<1, 32, 0, s>>>(st));
-  norm_into(st, 0, t, n, b.partial, 4, s);  // bnorm
+  norm_into(b, 0, const_cast<double*>(t), n, 4, rtol, m, s);  // bnorm (t is only read)
   cudaMemsetAsync(x, 0, n * sizeof(double), s);
   int total = 0;
   bool first = true;
@@ -189,7 +225,7 @@ int run_gmres(const GmresOps& ops, const GmresBuffers& b, const double* t, doubl
       (hfr::count_launch(), k_sub<<<nb, KB, 0, s>>>(t, b.V, b.V, n));
     }
     first = false;
-    norm_into(st, 0, b.V, n, b.partial, 3, s);  // beta
+    norm_into(b, 0, b.V, n, 3, rtol, m, s);  // beta
     (hfr::count_launch(), k_cycle_start<<<nb, KB, 0, s>>>(st, b.V, n, rtol));
     int j = 0;
     for (; j < m; ++j) {
@@ -198,14 +234,13 @@ int run_gmres(const GmresOps& ops, const GmresBuffers& b, const double* t, doubl
       double* zj = b.Z + (size_t)j * n;
       ops.precond(ops.ctx, st, j, vj, zj, s);
       ops.gated_matvec(ops.ctx, st, j, zj, w, s);
-      (hfr::count_launch(), k_dot_part<<<nb, KB, 0, s>>>(st, j, b.V, n, j + 1, w, b.partial));
-      (hfr::count_launch(), k_dot_final<<<1, 64, 0, s>>>(st, j, b.partial, nb, j + 1, 0));
-      (hfr::count_launch(), k_axpy_multi<<<nb, KB, 0, s>>>(st, j, b.V, n, j + 1, w, 0));
-      (hfr::count_launch(), k_dot_part<<<nb, KB, 0, s>>>(st, j, b.V, n, j + 1, w, b.partial));
-      (hfr::count_launch(), k_dot_final<<<1, 64, 0, s>>>(st, j, b.partial, nb, j + 1, 1));
-      (hfr::count_launch(), k_axpy_multi<<<nb, KB, 0, s>>>(st, j, b.V, n, j + 1, w, 1));
-      norm_into(st, j, w, n, b.partial, 2, s);
-      (hfr::count_launch(), k_givens<<<1, 32, 0, s>>>(st, j, rtol, m));
+      // classical Gram-Schmidt twice, in three fused passes
+      (hfr::count_launch(), k_cgs<<<nb, KB, 0, s>>>(st, j, b.V, n, j + 1, 0, b.V, j + 1, w, b.partial, b.ticket, 0,
+                                                     rtol, m));
+      (hfr::count_launch(), k_cgs<<<nb, KB, 0, s>>>(st, j, b.V, n, j + 1, 1, b.V, j + 1, w, b.partial, b.ticket, 1,
+                                                     rtol, m));
+      (hfr::count_launch(), k_cgs<<<nb, KB, 0, s>>>(st, j, b.V, n, j + 1, 2, w, 1, w, b.partial, b.ticket, 2, rtol,
+                                                     m));
       (hfr::count_launch(), k_scale_next<<<nb, KB, 0, s>>>(st, j, w, n));
       if ((j + 1) % check_every == 0 || j + 1 == m) {
         cudaMemcpyAsync(&hs, st, sizeof(GmresHead), cudaMemcpyDeviceToHost, s);
@@ -237,7 +272,7 @@ int run_gmres(const GmresOps& ops, const GmresBuffers& b, const double* t, doubl
   // true final relative residual
   ops.matvec(ops.ctx, x, b.V, s);
   (hfr::count_launch(), k_sub<<<nb, KB, 0, s>>>(t, b.V, b.V, n));
-  norm_into(st, 0, b.V, n, b.partial, 3, s);
+  norm_into(b, 0, b.V, n, 3, rtol, m, s);
   cudaMemcpyAsync(&hs, st, sizeof(GmresHead), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
   res->bnorm = hs.bnorm;

@@ -6,7 +6,7 @@
 namespace hfr {
 
 constexpr int GM_MAXM = 64;
-constexpr int GM_NBLK = 304;  // 2 x 152 SMs
+constexpr int GM_NBLK = 152;  // one block per SM for the vector passes
 
 // scalars first: the host reads only the head (sizeof(GmresHead)) between iterations
 struct GmresHead {
@@ -37,6 +37,7 @@ struct GmresBuffers {
   double* V;        // (GM_MAXM + 1) x n
   double* Z;        // GM_MAXM x n
   double* partial;  // GM_NBLK x (GM_MAXM + 1)
+  unsigned int* ticket;  // zero-initialised completion counter of the reduction kernels
   GmresState* state;
 };
 

@@ -20,129 +20,150 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// y = L x.  One warp per trace face; nT <= 96, bs = n nv <= 32.
+// y = L x.  One warp per trace face, split into four groups of eight lanes; each group takes
+// whole rows of the face's two row blocks (one per neighbour), the eight lanes of a group read
+// consecutive columns, and a 3-step shuffle reduces the row.  Row i of the output is reduced by
+// group i % 4 over both sides, so no cross-group accumulation is needed.  nT <= 96, bs <= 32.
+constexpr int MV_CT = 12;  // columns per lane: nT / 8 <= 12
 template <typename T>
-__global__ void k_trace_matvec(const __grid_constant__ TraceArgs a, const double* __restrict__ x,
-                               double* __restrict__ y, const int* gate, int gj) {
+__global__ void __launch_bounds__(256) k_trace_matvec(const __grid_constant__ TraceArgs a, const double* __restrict__ x,
+                                                      double* __restrict__ y, const int* gate, int gj) {
   if (gate && *gate >= 0 && gj >= *gate) return;
   const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (t >= a.ntrace) return;
   const int bs = a.n * a.nv, nT = a.nT;
+  const int grp = lane >> 3, g8 = lane & 7;
   const T* S = reinterpret_cast<const T*>(a.S);
-  T acc = T(0);
-  for (int side = 0; side < 2; ++side) {
-    const int e = a.sides[t * 4 + side * 2], f = a.sides[t * 4 + side * 2 + 1];
-    if (e < 0) continue;
-    T xv[3];
+  int es[2], fs[2];
+  T xv[2][MV_CT];
 #pragma unroll
-    for (int kk = 0; kk < 3; ++kk) {
-      const int l = lane + 32 * kk;
+  for (int side = 0; side < 2; ++side) {
+    es[side] = a.sides[t * 4 + side * 2];
+    fs[side] = a.sides[t * 4 + side * 2 + 1];
+#pragma unroll
+    for (int c = 0; c < MV_CT; ++c) {
+      const int l = g8 + 8 * c;
       T v = T(0);
-      if (l < nT) {
+      if (es[side] >= 0 && l < nT) {
         const int fp = l / bs;
-        const int tf = a.tr_of_c[e * 4 + fp];
+        const int tf = a.tr_of_c[es[side] * 4 + fp];
         if (tf >= 0) v = T(x[(size_t)tf * bs + (l - fp * bs)]);
       }
-      xv[kk] = v;
-    }
-    const T* Sr = S + ((size_t)e * nT + (size_t)f * bs) * nT;
-    for (int i = 0; i < bs; ++i) {
-      T p = T(0);
-#pragma unroll
-      for (int kk = 0; kk < 3; ++kk) {
-        const int l = lane + 32 * kk;
-        if (l < nT) p += Sr[(size_t)i * nT + l] * xv[kk];
-      }
-      p = warp_sum(p);
-      if (lane == i) acc += p;
+      xv[side][c] = v;
     }
   }
-  if (lane < bs) y[(size_t)t * bs + lane] = double(acc);
+  for (int i = grp; i < bs; i += 4) {
+    T acc = T(0);
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      if (es[side] < 0) continue;
+      const T* row = S + ((size_t)es[side] * nT + (size_t)fs[side] * bs + i) * nT;
+#pragma unroll
+      for (int c = 0; c < MV_CT; ++c) {
+        const int l = g8 + 8 * c;
+        if (l < nT) acc += row[l] * xv[side][c];
+      }
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    if (g8 == 0) y[(size_t)t * bs + i] = double(acc);
+  }
 }
 
-// P_f = sum of both sides' diagonal face blocks of S_k, inverted by Gauss-Jordan with partial
-// pivoting in FP64.  One block of 64 threads per face.
+// P_f = sum of both sides' diagonal face blocks of S_k, inverted in place by Gauss-Jordan with
+// partial pivoting (pivot bookkeeping only, as in the condensation) in the block precision T.
+// One warp per face, the bs x bs block in shared memory; Pinv_f = (P_f)^{-1} stored row-major.
+constexpr int PB_WARPS = 4;
 template <typename T>
-__global__ void k_precond_build(const __grid_constant__ TraceArgs a, double* __restrict__ Pinv, int* status) {
+__global__ void k_precond_build(const __grid_constant__ TraceArgs a, T* __restrict__ Pinv, int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int t = blockIdx.x;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * PB_WARPS + wid;
   const int bs = a.n * a.nv, nT = a.nT;
-  const int ld = 2 * bs;
-  double* M = reinterpret_cast<double*>(smem_raw);  // bs x 2bs  [P | I]
-  __shared__ int s_piv;
-  __shared__ double fac[32];
+  T* M = reinterpret_cast<T*>(smem_raw) + (size_t)wid * (bs * bs + 3 * 32);
+  T* pr = M + bs * bs;
+  int* ipiv = reinterpret_cast<int*>(pr + 32);  // physical row -> step
+  int* pivs = ipiv + 32;                        // step -> physical row
+  if (t >= a.ntrace) return;
   const T* S = reinterpret_cast<const T*>(a.S);
-  for (int i = threadIdx.x; i < bs * ld; i += blockDim.x) {
-    const int r = i / ld, c = i % ld;
-    double v = 0.0;
-    if (c < bs) {
-      for (int side = 0; side < 2; ++side) {
-        const int e = a.sides[t * 4 + side * 2], f = a.sides[t * 4 + side * 2 + 1];
-        if (e >= 0) v += double(S[((size_t)e * nT + f * bs + r) * nT + f * bs + c]);
-      }
-    } else {
-      v = (c - bs == r) ? 1.0 : 0.0;
+  for (int i = lane; i < bs * bs; i += 32) {
+    const int r = i / bs, c = i % bs;
+    T v = T(0);
+    for (int side = 0; side < 2; ++side) {
+      const int e = a.sides[t * 4 + side * 2], f = a.sides[t * 4 + side * 2 + 1];
+      if (e >= 0) v += S[((size_t)e * nT + f * bs + r) * nT + f * bs + c];
     }
     M[i] = v;
   }
-  __syncthreads();
+  __syncwarp();
+  bool used = false, bad = false;  // lane r < bs: row r already a pivot
   for (int c = 0; c < bs; ++c) {
-    if (threadIdx.x == 0) {
-      int p = c;
-      double best = fabs(M[c * ld + c]);
-      for (int i = c + 1; i < bs; ++i) {
-        double v = fabs(M[i * ld + c]);
-        if (v > best) { best = v; p = i; }
-      }
-      s_piv = p;
-      if (!(best > 0.0)) {
-        atomicOr(status, DEV_ERR_SINGULAR);
+    T best = T(-1);
+    int p = 0x7fffffff;
+    if (lane < bs && !used) {
+      const T v = M[lane * bs + c];
+      best = v < T(0) ? -v : v;
+      p = lane;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int op = __shfl_xor_sync(0xffffffffu, p, o);
+      if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
+    }
+    if (!(best > T(0))) bad = true;
+    if (lane == p) used = true;
+    if (lane == 0) {
+      ipiv[p] = c;
+      pivs[c] = p;
+    }
+    const T pv = M[p * bs + c];
+    const T inv = pv != T(0) ? T(1) / pv : T(0);
+    const T f = lane < bs ? M[lane * bs + c] : T(0);
+    if (lane < bs) pr[lane] = lane == c ? inv : M[p * bs + lane] * inv;
+    __syncwarp();
+    for (int i = 0; i < bs; ++i) {
+      const T fi = __shfl_sync(0xffffffffu, f, i);
+      if (lane < bs) {
+        const T pj = pr[lane];
+        if (i == p)
+          M[i * bs + lane] = pj;
+        else
+          M[i * bs + lane] = (lane == c ? T(0) : M[i * bs + lane]) - fi * pj;
       }
     }
-    __syncthreads();
-    const int p = s_piv;
-    if (p != c)
-      for (int j = threadIdx.x; j < ld; j += blockDim.x) {
-        double t0 = M[c * ld + j];
-        M[c * ld + j] = M[p * ld + j];
-        M[p * ld + j] = t0;
-      }
-    __syncthreads();
-    const double pv = M[c * ld + c];
-    const double inv = pv != 0.0 ? 1.0 / pv : 0.0;
-    __syncthreads();
-    for (int j = threadIdx.x; j < ld; j += blockDim.x) M[c * ld + j] *= inv;
-    for (int i = threadIdx.x; i < bs; i += blockDim.x) fac[i] = M[i * ld + c];
-    __syncthreads();
-    for (int it = threadIdx.x; it < bs * ld; it += blockDim.x) {
-      const int i = it / ld, j = it % ld;
-      if (i != c) M[i * ld + j] -= fac[i] * M[c * ld + j];
-    }
-    __syncthreads();
+    __syncwarp();
   }
-  for (int i = threadIdx.x; i < bs * bs; i += blockDim.x) {
+  if (bad && lane == 0) atomicOr(status, DEV_ERR_SINGULAR);
+  __syncwarp();
+  // physical row r holds row ipiv[r] of (P P_f)^{-1}; (P_f)^{-1} = (P P_f)^{-1} P, i.e.
+  // (P_f)^{-1}[ipiv[r]][pivs[c]] = M[r][c]
+  for (int i = lane; i < bs * bs; i += 32) {
     const int r = i / bs, c = i % bs;
-    Pinv[(size_t)t * bs * bs + i] = M[r * ld + bs + c];
+    Pinv[(size_t)t * bs * bs + (size_t)ipiv[r] * bs + pivs[c]] = M[i];
   }
+  __syncwarp();
 }
 
 // y_f = Pinv_f x_f, one warp per face, lane = row
-__global__ void k_precond_apply(const __grid_constant__ TraceArgs a, const double* __restrict__ Pinv,
+template <typename T>
+__global__ void k_precond_apply(const __grid_constant__ TraceArgs a, const T* __restrict__ Pinv,
                                 const double* __restrict__ x, double* __restrict__ y, const int* gate, int gj) {
   if (gate && *gate >= 0 && gj >= *gate) return;
   const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (t >= a.ntrace) return;
   const int bs = a.n * a.nv;
-  const double* P = Pinv + (size_t)t * bs * bs;
-  const double xv = lane < bs ? x[(size_t)t * bs + lane] : 0.0;
-  double acc = 0.0;
+  const T* P = Pinv + (size_t)t * bs * bs;
+  const T xv = lane < bs ? T(x[(size_t)t * bs + lane]) : T(0);
+  T acc = T(0);
   for (int j = 0; j < bs; ++j) {
-    const double xj = __shfl_sync(0xffffffffu, xv, j);
+    const T xj = __shfl_sync(0xffffffffu, xv, j);
     if (lane < bs) acc += P[lane * bs + j] * xj;
   }
-  if (lane < bs) y[(size_t)t * bs + lane] = acc;
+  if (lane < bs) y[(size_t)t * bs + lane] = double(acc);
 }
 
 // global trace right-hand side t = sum_k scatter(t_k)
@@ -202,19 +223,27 @@ cudaError_t launch_trace_matvec(int prec_bytes, const TraceArgs& a, const double
 cudaError_t launch_precond_build(int prec_bytes, const TraceArgs& a, double* Pinv, int* status, cudaStream_t st) {
   if (a.ntrace == 0) return cudaSuccess;
   const int bs = a.n * a.nv;
-  size_t smem = sizeof(double) * bs * 2 * bs;
-  if (prec_bytes == 8)
-    (hfr::count_launch(), k_precond_build<double><<<a.ntrace, 64, smem, st>>>(a, Pinv, status));
-  else
-    (hfr::count_launch(), k_precond_build<float><<<a.ntrace, 64, smem, st>>>(a, Pinv, status));
+  if (bs > 32) return cudaErrorInvalidValue;
+  const int grid = (a.ntrace + PB_WARPS - 1) / PB_WARPS;
+  if (prec_bytes == 8) {
+    const size_t smem = sizeof(double) * (bs * bs + 3 * 32) * PB_WARPS;
+    (hfr::count_launch(), k_precond_build<double><<<grid, 32 * PB_WARPS, smem, st>>>(a, Pinv, status));
+  } else {
+    const size_t smem = sizeof(float) * (bs * bs + 3 * 32) * PB_WARPS;
+    (hfr::count_launch(), k_precond_build<float><<<grid, 32 * PB_WARPS, smem, st>>>(a, reinterpret_cast<float*>(Pinv), status));
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_precond_apply(const TraceArgs& a, const double* Pinv, const double* x, double* y,
+cudaError_t launch_precond_apply(int prec_bytes, const TraceArgs& a, const double* Pinv, const double* x, double* y,
                                  cudaStream_t st, const int* gate, int gj) {
   if (a.ntrace == 0) return cudaSuccess;
   const int threads = 256;
-  (hfr::count_launch(), k_precond_apply<<<(a.ntrace * 32 + threads - 1) / threads, threads, 0, st>>>(a, Pinv, x, y, gate, gj));
+  const int grid = (a.ntrace * 32 + threads - 1) / threads;
+  if (prec_bytes == 8)
+    (hfr::count_launch(), k_precond_apply<double><<<grid, threads, 0, st>>>(a, Pinv, x, y, gate, gj));
+  else
+    (hfr::count_launch(), k_precond_apply<float><<<grid, threads, 0, st>>>(a, reinterpret_cast<const float*>(Pinv), x, y, gate, gj));
   return cudaGetLastError();
 }
 

@@ -135,12 +135,22 @@ def test_element_blocks_fp64(name):
     assert _rel(ctx.hfr_export("s").cpu().numpy(), s_ref) < 1e-11
 
 
-@pytest.mark.parametrize("name", ["vortex_skew_p3", "band_ns"])
-def test_element_blocks_fp32(name):
+@pytest.mark.parametrize("name", ["vortex_skew_p3", "vortex_p4", "band_ns"])
+def test_element_blocks_and_condense_fp32(name):
     ctx, d, u0, uh, ustar, a_dt, blocks = _blocks_both(name, pkg.FR_PREC_FP32)
     for key, ref in zip("ABCD", blocks):
         got = ctx.hfr_export(key).cpu().numpy().astype(np.float64)
         assert _rel(got, ref) < 3e-5, key
+    # FP32 condensation of the FP32 blocks against the FP64 condensation of the oracle's blocks:
+    # differences come from FP32 rounding amplified by the block condition numbers (O(1e2))
+    ctx.hfr_condense(refine=0)
+    A, B, C, D = blocks
+    r = ctx.hfr_export("r").cpu().numpy()
+    s = ctx.hfr_export("s").cpu().numpy()
+    XB, xr, S, t = condense(A, B, C, D, r, s)
+    assert _rel(ctx.hfr_export("S").cpu().numpy().astype(np.float64), S) < 1e-4
+    assert _rel(ctx.hfr_export("XB").cpu().numpy().astype(np.float64), XB) < 1e-4
+    assert _rel(ctx.hfr_export("xr").cpu().numpy(), xr) < 1e-4
 
 
 @pytest.mark.parametrize("name", ["advdiff8", "vortex_skew_p3", "vortex_p4", "band_ns"])
@@ -154,6 +164,9 @@ def test_condense_gmres_backsolve_fp64(name):
     assert _rel(ctx.hfr_export("XB").cpu().numpy(), XB) < 1e-9
     assert _rel(ctx.hfr_export("xr").cpu().numpy(), xr) < 1e-9
     assert _rel(ctx.hfr_export("t_k").cpu().numpy(), t) < 1e-9
+    # face-block Jacobi preconditioner blocks
+    from oracle.solve import face_block_jacobi
+    assert _rel(ctx.hfr_export("Pinv").cpu().numpy(), face_block_jacobi(d, S, d.imp_idx)) < 1e-9
     duh_ref, _, _ = solve_trace(d, S, t, d.imp_idx, method="direct")
     duh, its, rel = ctx.hfr_trace_gmres(rtol=1e-13, maxit=3000)
     assert rel <= 1e-12
