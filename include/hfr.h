@@ -171,10 +171,11 @@ int hfr_initial_trace(fr_ctx* ctx, const double* u, double* uhat);
 /* Per-phase device time of the context's calls, measured with CUDA events on its stream.
  * Phases: 0 residual (incl. trace assembly), 1 element Jacobian blocks, 2 condensation kernel,
  * 3 trace right-hand side + preconditioner build, 4 trace GMRES solve, 5 back-substitution and
- * refinement, 6 Newton bookkeeping (right-hand sides, norms, updates), 7 FP64 refinement of x_r. */
+ * refinement, 6 Newton bookkeeping (right-hand sides, norms, updates), 7 FP64 refinement of x_r,
+ * 8 one trace mat-vec kernel (the restart / final-residual products inside GMRES), 9 unused. */
 typedef struct {
-  double ms[8];
-  long long count[8];
+  double ms[10];
+  long long count[10];
 } fr_profile;
 /* on != 0 enables event timing (and resets the totals); off stops it. */
 int fr_profile_enable(fr_ctx* ctx, int on);

@@ -52,7 +52,8 @@ ABI_SYMBOLS = [
     "fr_status_string",
 ]
 
-PHASES = ["residual", "jacobian", "condense", "trace_rhs_precond", "gmres", "backsolve", "newton", "refine_xr"]
+PHASES = ["residual", "jacobian", "condense", "trace_rhs_precond", "gmres", "backsolve", "newton", "refine_xr",
+          "trace_matvec", "unused"]
 
 
 class fr_mesh_desc(ctypes.Structure):
@@ -110,7 +111,7 @@ class fr_stage_stats(ctypes.Structure):
 
 
 class fr_profile(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 8), ("count", ctypes.c_longlong * 8)]
+    _fields_ = [("ms", ctypes.c_double * 10), ("count", ctypes.c_longlong * 10)]
 
 
 class fr_error_info(ctypes.Structure):

@@ -64,11 +64,11 @@ struct fr_ctx {
   std::vector<cudaEvent_t> evpool;
   size_t evused = 0;
   std::vector<std::pair<int, std::pair<int, int>>> pend;
-  double pms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  long long pcnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double pms[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  long long pcnt[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
 };
 
-enum { PH_RES = 0, PH_JAC = 1, PH_COND = 2, PH_PREC = 3, PH_GMRES = 4, PH_BACK = 5, PH_NEWTON = 6, PH_REFX = 7 };
+enum { PH_RES = 0, PH_JAC = 1, PH_COND = 2, PH_PREC = 3, PH_GMRES = 4, PH_BACK = 5, PH_NEWTON = 6, PH_REFX = 7, PH_MATVEC = 8 };
 
 static int prof_begin(fr_ctx* ctx, int phase) {
   if (!ctx->prof || ctx->evused + 2 > ctx->evpool.size()) return -1;
@@ -779,7 +779,9 @@ extern "C" int hfr_condense(fr_ctx* ctx, int refine) {
 // GMRES callbacks
 static void cb_matvec(void* c, const double* x, double* y, cudaStream_t s) {
   fr_ctx* ctx = (fr_ctx*)c;
+  const int ph = prof_begin(ctx, PH_MATVEC);
   launch_trace_matvec(ctx->prec_bytes, trace_args(ctx), x, y, s);
+  prof_end(ctx, ph);
 }
 static void cb_gmatvec(void* c, const GmresState* st, int j, const double* x, double* y, cudaStream_t s) {
   fr_ctx* ctx = (fr_ctx*)c;
@@ -1021,7 +1023,7 @@ extern "C" int fr_profile_enable(fr_ctx* ctx, int on) {
   }
   ctx->prof = on != 0;
   if (on)
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < 10; ++i) {
       ctx->pms[i] = 0.0;
       ctx->pcnt[i] = 0;
     }
@@ -1030,7 +1032,7 @@ extern "C" int fr_profile_enable(fr_ctx* ctx, int on) {
 
 extern "C" int fr_profile_read(const fr_ctx* ctx, fr_profile* out) {
   if (!ctx || !out) return FR_ERR_INVALID_ARG;
-  for (int i = 0; i < 8; ++i) {
+  for (int i = 0; i < 10; ++i) {
     out->ms[i] = ctx->pms[i];
     out->count[i] = ctx->pcnt[i];
   }

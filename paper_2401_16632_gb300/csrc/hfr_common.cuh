@@ -92,39 +92,61 @@ template <typename T> struct RealOf<Dual<T>> { typedef T type; };
 // Same readings as the oracle: advection-diffusion F^c = beta u, F^v = nu grad u,
 // s = |beta.n| + nu/lref; Navier-Stokes ideal gas R = 1, constant mu, Stokes hypothesis,
 // kappa = mu gamma / ((gamma - 1) Pr), wave speed |v.n| + c, s = |v^.n| + c^ + mu/(rho^ lref).
+// Physics constants in the compute precision R, derived once per thread from PhysParams so
+// that no double arithmetic or conversion happens inside the flux evaluations of FP32 kernels.
+template <typename R>
+struct PhysConst {
+  R beta0, beta1, nu, nu_lref;          // advection-diffusion
+  R gamma, gm1, mu, kappa, mu_lref;     // Navier-Stokes
+};
+template <typename R>
+__host__ __device__ inline PhysConst<R> phys_const(const PhysParams& pp) {
+  PhysConst<R> c;
+  c.beta0 = R(pp.beta[0]);
+  c.beta1 = R(pp.beta[1]);
+  c.nu = R(pp.nu);
+  c.nu_lref = R(pp.nu / pp.lref);
+  c.gamma = R(pp.gamma);
+  c.gm1 = R(pp.gamma - 1.0);
+  c.mu = R(pp.mu);
+  c.kappa = pp.kind == 1 ? R(pp.mu * pp.gamma / ((pp.gamma - 1.0) * pp.Pr)) : R(0);
+  c.mu_lref = R(pp.mu / pp.lref);
+  return c;
+}
+
 template <int PHYS> struct Phys;
 
 template <> struct Phys<0> {
   static constexpr int NV = 1;
   template <typename S, typename R>
-  __device__ static void conv(const PhysParams& pp, const S* u, S F[2][1]) {
-    F[0][0] = R(pp.beta[0]) * u[0];
-    F[1][0] = R(pp.beta[1]) * u[0];
+  __device__ static void conv(const PhysConst<R>& pc, const S* u, S F[2][1]) {
+    F[0][0] = pc.beta0 * u[0];
+    F[1][0] = pc.beta1 * u[0];
   }
   template <typename S, typename R>
-  __device__ static void visc(const PhysParams& pp, const S* u, const S q[2][1], S F[2][1]) {
-    F[0][0] = R(pp.nu) * q[0][0];
-    F[1][0] = R(pp.nu) * q[1][0];
+  __device__ static void visc(const PhysConst<R>& pc, const S* u, const S q[2][1], S F[2][1]) {
+    F[0][0] = pc.nu * q[0][0];
+    F[1][0] = pc.nu * q[1][0];
   }
   template <typename S, typename R>
-  __device__ static S wave(const PhysParams& pp, const S* u, R n0, R n1) {
-    R bn = R(pp.beta[0]) * n0 + R(pp.beta[1]) * n1;
+  __device__ static S wave(const PhysConst<R>& pc, const S* u, R n0, R n1) {
+    R bn = pc.beta0 * n0 + pc.beta1 * n1;
     return S(dabs(bn)) + R(0) * u[0];
   }
   template <typename S, typename R>
-  __device__ static S stab(const PhysParams& pp, const S* u, R n0, R n1) {
-    return wave<S, R>(pp, u, n0, n1) + R(pp.nu / pp.lref);
+  __device__ static S stab(const PhysConst<R>& pc, const S* u, R n0, R n1) {
+    return wave<S, R>(pc, u, n0, n1) + pc.nu_lref;
   }
 };
 
 template <> struct Phys<1> {
   static constexpr int NV = 4;
   template <typename S, typename R>
-  __device__ static void conv(const PhysParams& pp, const S* u, S F[2][4]) {
-    R g1 = R(pp.gamma - 1.0);
+  __device__ static void conv(const PhysConst<R>& pc, const S* u, S F[2][4]) {
     S rho = u[0];
-    S vx = u[1] / rho, vy = u[2] / rho;
-    S p = g1 * (u[3] - R(0.5) * (u[1] * vx + u[2] * vy));
+    S ir = R(1) / rho;
+    S vx = u[1] * ir, vy = u[2] * ir;
+    S p = pc.gm1 * (u[3] - R(0.5) * (u[1] * vx + u[2] * vy));
     S Ep = u[3] + p;
     F[0][0] = u[1];
     F[0][1] = u[1] * vx + p;
@@ -136,10 +158,8 @@ template <> struct Phys<1> {
     F[1][3] = Ep * vy;
   }
   template <typename S, typename R>
-  __device__ static void visc(const PhysParams& pp, const S* u, const S q[2][4], S F[2][4]) {
-    R g = R(pp.gamma);
-    R mu = R(pp.mu);
-    R kappa = R(pp.mu * pp.gamma / ((pp.gamma - 1.0) * pp.Pr));
+  __device__ static void visc(const PhysConst<R>& pc, const S* u, const S q[2][4], S F[2][4]) {
+    const R mu = pc.mu;
     S rho = u[0];
     S ir = R(1) / rho;
     S vx = u[1] * ir, vy = u[2] * ir;
@@ -149,7 +169,7 @@ template <> struct Phys<1> {
     for (int c = 0; c < 2; ++c) {
       dvx[c] = (q[c][1] - vx * q[c][0]) * ir;
       dvy[c] = (q[c][2] - vy * q[c][0]) * ir;
-      dT[c] = (g - R(1)) * ((q[c][3] - e * q[c][0]) * ir - vx * dvx[c] - vy * dvy[c]);
+      dT[c] = pc.gm1 * ((q[c][3] - e * q[c][0]) * ir - vx * dvx[c] - vy * dvy[c]);
     }
     S div = dvx[0] + dvy[1];
     S txx = mu * (R(2) * dvx[0] - R(2.0 / 3.0) * div);
@@ -158,24 +178,24 @@ template <> struct Phys<1> {
     F[0][0] = S(R(0));
     F[0][1] = txx;
     F[0][2] = txy;
-    F[0][3] = vx * txx + vy * txy + kappa * dT[0];
+    F[0][3] = vx * txx + vy * txy + pc.kappa * dT[0];
     F[1][0] = S(R(0));
     F[1][1] = txy;
     F[1][2] = tyy;
-    F[1][3] = vx * txy + vy * tyy + kappa * dT[1];
+    F[1][3] = vx * txy + vy * tyy + pc.kappa * dT[1];
   }
   template <typename S, typename R>
-  __device__ static S wave(const PhysParams& pp, const S* u, R n0, R n1) {
-    R g = R(pp.gamma);
+  __device__ static S wave(const PhysConst<R>& pc, const S* u, R n0, R n1) {
     S rho = u[0];
-    S vx = u[1] / rho, vy = u[2] / rho;
-    S p = (g - R(1)) * (u[3] - R(0.5) * (u[1] * vx + u[2] * vy));
-    S c = dsqrt(g * p / rho);
+    S ir = R(1) / rho;
+    S vx = u[1] * ir, vy = u[2] * ir;
+    S p = pc.gm1 * (u[3] - R(0.5) * (u[1] * vx + u[2] * vy));
+    S c = dsqrt(pc.gamma * p * ir);
     return dabs(vx * n0 + vy * n1) + c;
   }
   template <typename S, typename R>
-  __device__ static S stab(const PhysParams& pp, const S* u, R n0, R n1) {
-    return wave<S, R>(pp, u, n0, n1) + R(pp.mu / pp.lref) / u[0];
+  __device__ static S stab(const PhysConst<R>& pc, const S* u, R n0, R n1) {
+    return wave<S, R>(pc, u, n0, n1) + pc.mu_lref / u[0];
   }
 };
 

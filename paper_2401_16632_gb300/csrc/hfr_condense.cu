@@ -356,18 +356,19 @@ constexpr int INV_SLOTS = 5;  // nA <= 160
 template <typename T>
 __global__ void k_inv_apply(int Eim, int nA, const T* __restrict__ AinvT, const int* __restrict__ piv,
                             double* __restrict__ b) {
+  // arithmetic in the block precision T: the result is a correction, T-accurate is enough
   const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (k >= Eim) return;
   const T* W = AinvT + (size_t)k * nA * nA;
   const int* pv = piv + (size_t)k * nA;
   double* bk = b + (size_t)k * nA;
-  double pb[INV_SLOTS], y[INV_SLOTS];
+  T pb[INV_SLOTS], y[INV_SLOTS];
 #pragma unroll
   for (int q = 0; q < INV_SLOTS; ++q) {
     const int j = lane + 32 * q;
-    pb[q] = j < nA ? bk[pv[j]] : 0.0;  // (P b)_j
-    y[q] = 0.0;
+    pb[q] = j < nA ? T(bk[pv[j]]) : T(0);  // (P b)_j
+    y[q] = T(0);
   }
 #pragma unroll
   for (int q = 0; q < INV_SLOTS; ++q) {
@@ -375,11 +376,11 @@ __global__ void k_inv_apply(int Eim, int nA, const T* __restrict__ AinvT, const 
     for (int jj = 0; jj < 32; ++jj) {
       const int j = 32 * q + jj;
       if (j >= nA) break;
-      const double bj = __shfl_sync(0xffffffffu, pb[q], jj);
+      const T bj = __shfl_sync(0xffffffffu, pb[q], jj);
 #pragma unroll
       for (int qq = 0; qq < INV_SLOTS; ++qq) {
         const int c = lane + 32 * qq;
-        if (c < nA) y[qq] += double(W[(size_t)j * nA + c]) * bj;
+        if (c < nA) y[qq] += W[(size_t)j * nA + c] * bj;
       }
     }
   }
@@ -387,7 +388,7 @@ __global__ void k_inv_apply(int Eim, int nA, const T* __restrict__ AinvT, const 
 #pragma unroll
   for (int q = 0; q < INV_SLOTS; ++q) {
     const int c = lane + 32 * q;
-    if (c < nA) bk[c] = y[q];
+    if (c < nA) bk[c] = double(y[q]);
   }
 }
 

@@ -41,12 +41,13 @@ struct JacWork {
   T dFt[NS][2][NV][JAC_SB];
   T dq[NS][2][JAC_SB];
   T dFn[NF][NV][JAC_SB];
+  T rM[N][N], rdgL[N], rdgR[N], rlm[N], rlp[N], rw[N];  // reference operators in T
   int kf[4];
 };
 
 // total flux F = F^c - F^v at a solution point
 template <int PHYS, typename S, typename R, int NV>
-__device__ __forceinline__ void vol_flux(const PhysParams& pp, bool visc, const S* u, const S q[2][NV], S F[2][NV]) {
+__device__ __forceinline__ void vol_flux(const PhysConst<R>& pp, bool visc, const S* u, const S q[2][NV], S F[2][NV]) {
   Phys<PHYS>::template conv<S, R>(pp, u, F);
   if (visc) {
     S Fv[2][NV];
@@ -60,7 +61,7 @@ __device__ __forceinline__ void vol_flux(const PhysParams& pp, bool visc, const 
 
 // common normal flux J_f F^.n of an implicit element's face (trace or IMEX-interface face)
 template <int PHYS, typename S, typename R, int NV>
-__device__ __forceinline__ void imp_face_flux(const PhysParams& pp, bool visc, int kf, const S* Uf, const S* ub,
+__device__ __forceinline__ void imp_face_flux(const PhysConst<R>& pp, bool visc, int kf, const S* Uf, const S* ub,
                                               const S qf[2][NV], const S* un, R Jf, R n0, R n1, S* Fn) {
   S F[2][NV];
   if (kf == FK_TRACE) {
@@ -106,6 +107,7 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobian(const __grid_constant_
   const int e = a.imp_idx[k];
   const int tid = threadIdx.x;
   const bool visc = pp.kind == 0 ? (pp.nu != 0.0) : (pp.mu != 0.0);
+  const PhysConst<T> pc = phys_const<T>(pp);
   const double* gs = a.geo_sol + (size_t)e * NS * 5;
   const double* gf = a.geo_face + (size_t)e * NF * 3;
 
@@ -124,16 +126,24 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobian(const __grid_constant_
     w.fn[j][1] = T(gf[j * 3 + 2]);
   }
   if (tid < 4) w.kf[tid] = a.kind[e * 4 + tid];
+  for (int i = tid; i < N * N; i += JAC_THREADS) w.rM[i / N][i % N] = T(ref.M[i / N][i % N]);
+  if (tid < N) {
+    w.rdgL[tid] = T(ref.dgL[tid]);
+    w.rdgR[tid] = T(ref.dgR[tid]);
+    w.rlm[tid] = T(ref.lm[tid]);
+    w.rlp[tid] = T(ref.lp[tid]);
+    w.rw[tid] = T(ref.w[tid]);
+  }
   __syncthreads();
   for (int j = tid; j < NF; j += JAC_THREADS) {
     const int f = j / N, m = j % N, r = f >> 1;
-    const double* l = (f & 1) ? ref.lp : ref.lm;
+    const T* l = (f & 1) ? w.rlp : w.rlm;
     const int kf = w.kf[f];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       T s = T(0);
 #pragma unroll
-      for (int c = 0; c < N; ++c) s += T(l[c]) * w.U[line_pt<N>(r, m, c)][v];
+      for (int c = 0; c < N; ++c) s += l[c] * w.U[line_pt<N>(r, m, c)][v];
       w.Uf[j][v] = s;
     }
     if (kf == FK_TRACE) {
@@ -159,12 +169,12 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobian(const __grid_constant_
       const int ai = i % N, bi = i / N;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        T q0 = T(ref.dgL[ai]) * w.ub[bi][v] + T(ref.dgR[ai]) * w.ub[N + bi][v];
-        T q1 = T(ref.dgL[bi]) * w.ub[2 * N + ai][v] + T(ref.dgR[bi]) * w.ub[3 * N + ai][v];
+        T q0 = w.rdgL[ai] * w.ub[bi][v] + w.rdgR[ai] * w.ub[N + bi][v];
+        T q1 = w.rdgL[bi] * w.ub[2 * N + ai][v] + w.rdgR[bi] * w.ub[3 * N + ai][v];
 #pragma unroll
         for (int c = 0; c < N; ++c) {
-          q0 += T(ref.M[ai][c]) * w.U[c + N * bi][v];
-          q1 += T(ref.M[bi][c]) * w.U[ai + N * c][v];
+          q0 += w.rM[ai][c] * w.U[c + N * bi][v];
+          q1 += w.rM[bi][c] * w.U[ai + N * c][v];
         }
         w.q[i][0][v] = w.iJ[i] * (w.Sm[i][0][0] * q0 + w.Sm[i][1][0] * q1);
         w.q[i][1][v] = w.iJ[i] * (w.Sm[i][0][1] * q0 + w.Sm[i][1][1] * q1);
@@ -173,14 +183,14 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobian(const __grid_constant_
     __syncthreads();
     for (int j = tid; j < NF; j += JAC_THREADS) {
       const int f = j / N, m = j % N, r = f >> 1;
-      const double* l = (f & 1) ? ref.lp : ref.lm;
+      const T* l = (f & 1) ? w.rlp : w.rlm;
 #pragma unroll
       for (int c2 = 0; c2 < 2; ++c2)
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           T s = T(0);
 #pragma unroll
-          for (int c = 0; c < N; ++c) s += T(l[c]) * w.q[line_pt<N>(r, m, c)][c2][v];
+          for (int c = 0; c < N; ++c) s += l[c] * w.q[line_pt<N>(r, m, c)][c2][v];
           w.qf[j][c2][v] = s;
         }
     }
@@ -202,7 +212,7 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobian(const __grid_constant_
       qd[1][v] = DT(w.q[i][1][v]);
     }
     if (!isq) {
-      vol_flux<PHYS, DT, T, NV>(pp, visc, u, qd, F);
+      vol_flux<PHYS, DT, T, NV>(pc, visc, u, qd, F);
 #pragma unroll
       for (int r = 0; r < 2; ++r)
 #pragma unroll
@@ -219,7 +229,7 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobian(const __grid_constant_
 #pragma unroll
         for (int c2 = 0; c2 < 2; ++c2) {
           qd[c2][vp].d = T(1);
-          vol_flux<PHYS, DT, T, NV>(pp, visc, u, qd, F);
+          vol_flux<PHYS, DT, T, NV>(pc, visc, u, qd, F);
           qd[c2][vp].d = T(0);
 #pragma unroll
           for (int r = 0; r < 2; ++r)
@@ -254,7 +264,7 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobian(const __grid_constant_
       qf[1][v] = DT(w.qf[j][1][v], (grp == 3 && v == vp) ? T(1) : T(0));
     }
     bool zero = (grp >= 2 && !visc) || (grp == 1 && kf != FK_TRACE);
-    if (!zero) imp_face_flux<PHYS, DT, T, NV>(pp, visc, kf, Uf, ub, qf, un, w.fJ[j], w.fn[j][0], w.fn[j][1], Fn);
+    if (!zero) imp_face_flux<PHYS, DT, T, NV>(pc, visc, kf, Uf, ub, qf, un, w.fJ[j], w.fn[j][0], w.fn[j][1], Fn);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       T d = zero ? T(0) : Fn[v].d;
@@ -285,19 +295,19 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobian(const __grid_constant_
         const int P0 = sd / NV;
         v0 = sd % NV;
         const int a0 = P0 % N, b0 = P0 / N;
-        if (bi == b0) dQ0 = T(ref.M[ai][a0]);
-        if (ai == a0) dQ1 = T(ref.M[bi][b0]);
+        if (bi == b0) dQ0 = w.rM[ai][a0];
+        if (ai == a0) dQ1 = w.rM[bi][b0];
         self = (i == P0);
       } else if (sd < NSEED) {
         const int l = sd - nA;
         const int f0 = l / (N * NV), m0 = (l / NV) % N;
         v0 = l % NV;
         if (w.kf[f0] == FK_TRACE) {
-          const double* dg = (f0 & 1) ? ref.dgR : ref.dgL;
+          const T* dg = (f0 & 1) ? w.rdgR : w.rdgL;
           if ((f0 >> 1) == 0) {
-            if (bi == m0) dQ0 = T(dg[ai]);
+            if (bi == m0) dQ0 = dg[ai];
           } else {
-            if (ai == m0) dQ1 = T(dg[bi]);
+            if (ai == m0) dQ1 = dg[bi];
           }
         }
       }
@@ -318,7 +328,7 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobian(const __grid_constant_
       const int s = it % JAC_SB, j = it / JAC_SB;
       const int sd = s0 + s;
       const int f = j / N, m = j % N, r = f >> 1;
-      const double* l = (f & 1) ? ref.lp : ref.lm;
+      const T* l = (f & 1) ? w.rlp : w.rlm;
       T dUf = T(0);
       int v0 = 0;
       bool selft = false;
@@ -327,7 +337,7 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobian(const __grid_constant_
         v0 = sd % NV;
         const int a0 = P0 % N, b0 = P0 / N;
         const int along = r == 0 ? a0 : b0, line = r == 0 ? b0 : a0;
-        if (m == line) dUf = T(l[along]);
+        if (m == line) dUf = l[along];
       } else if (sd < NSEED) {
         const int lt = sd - nA;
         v0 = lt % NV;
@@ -337,8 +347,8 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobian(const __grid_constant_
 #pragma unroll
       for (int c = 0; c < N; ++c) {
         const int pt = line_pt<N>(r, m, c);
-        dqf0 += T(l[c]) * w.dq[pt][0][s];
-        dqf1 += T(l[c]) * w.dq[pt][1][s];
+        dqf0 += l[c] * w.dq[pt][0][s];
+        dqf1 += l[c] * w.dq[pt][1][s];
       }
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -357,11 +367,11 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobian(const __grid_constant_
           T val;
           if (i < nA) {
             const int pt = i / NV, v = i % NV, ai = pt % N, bi = pt / N;
-            T d = -T(ref.dgL[ai]) * w.dFn[bi][v][s] + T(ref.dgR[ai]) * w.dFn[N + bi][v][s] -
-                  T(ref.dgL[bi]) * w.dFn[2 * N + ai][v][s] + T(ref.dgR[bi]) * w.dFn[3 * N + ai][v][s];
+            T d = -w.rdgL[ai] * w.dFn[bi][v][s] + w.rdgR[ai] * w.dFn[N + bi][v][s] -
+                  w.rdgL[bi] * w.dFn[2 * N + ai][v][s] + w.rdgR[bi] * w.dFn[3 * N + ai][v][s];
 #pragma unroll
             for (int c = 0; c < N; ++c)
-              d += T(ref.M[ai][c]) * w.dFt[c + N * bi][0][v][s] + T(ref.M[bi][c]) * w.dFt[ai + N * c][1][v][s];
+              d += w.rM[ai][c] * w.dFt[c + N * bi][0][v][s] + w.rM[bi][c] * w.dFt[ai + N * c][1][v][s];
             const T dR = -w.iJ[pt] * d;
             if (sd < nA) {
               val = (i == sd ? T(1) : T(0)) - adt * dR;
@@ -372,7 +382,7 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobian(const __grid_constant_
           } else {
             const int lr = i - nA;
             const int f = lr / (N * NV), m = (lr / NV) % N, v = lr % NV;
-            val = w.kf[f] == FK_TRACE ? T(ref.w[m]) * w.dFn[f * N + m][v][s] : T(0);
+            val = w.kf[f] == FK_TRACE ? w.rw[m] * w.dFn[f * N + m][v][s] : T(0);
             if (sd < nA)
               C[(size_t)lr * nA + sd] = val;
             else

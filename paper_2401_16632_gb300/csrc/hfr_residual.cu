@@ -45,6 +45,7 @@ __global__ void __launch_bounds__(TPE* EPB) k_element(const __grid_constant__ Re
   const bool live = e < a.E;
   W& w = works[g];
   const bool viscous = pp.kind == 0 ? (pp.nu != 0.0) : (pp.mu != 0.0);
+  const PhysConst<double> pc = phys_const<double>(pp);
   const bool is_imp = live ? (a.implicit[e] != 0) : false;
   const double* gs = a.geo_sol + (size_t)e * NS * 5;
   const double* gf = a.geo_face + (size_t)e * NF * 3;
@@ -125,10 +126,10 @@ __global__ void __launch_bounds__(TPE* EPB) k_element(const __grid_constant__ Re
       for (int i = lt; i < NS; i += TPE) {
         const double* G = gs + i * 5;
         S F[2][NV];
-        Phys<PHYS>::template conv<S, double>(pp, w.U[i], F);
+        Phys<PHYS>::template conv<S, double>(pc, w.U[i], F);
         if (viscous) {
           S Fv[2][NV];
-          Phys<PHYS>::template visc<S, double>(pp, w.U[i], w.q[i], Fv);
+          Phys<PHYS>::template visc<S, double>(pc, w.U[i], w.q[i], Fv);
 #pragma unroll
           for (int c = 0; c < 2; ++c)
 #pragma unroll
@@ -177,13 +178,13 @@ __global__ void __launch_bounds__(TPE* EPB) k_element(const __grid_constant__ Re
       S Fh[NV];
       if (kf == FK_TRACE) {
         S Fc[2][NV];
-        Phys<PHYS>::template conv<S, double>(pp, w.ub[j], Fc);
-        S s = Phys<PHYS>::template stab<S, double>(pp, w.ub[j], n0, n1);
+        Phys<PHYS>::template conv<S, double>(pc, w.ub[j], Fc);
+        S s = Phys<PHYS>::template stab<S, double>(pc, w.ub[j], n0, n1);
 #pragma unroll
         for (int v = 0; v < NV; ++v) Fh[v] = n0 * Fc[0][v] + n1 * Fc[1][v] + s * (w.Uf[j][v] - w.ub[j][v]);
         if (viscous) {
           S Fv[2][NV];
-          Phys<PHYS>::template visc<S, double>(pp, w.ub[j], w.qf[j], Fv);
+          Phys<PHYS>::template visc<S, double>(pc, w.ub[j], w.qf[j], Fv);
 #pragma unroll
           for (int v = 0; v < NV; ++v) Fh[v] = Fh[v] - (n0 * Fv[0][v] + n1 * Fv[1][v]);
         }
@@ -194,10 +195,10 @@ __global__ void __launch_bounds__(TPE* EPB) k_element(const __grid_constant__ Re
 #pragma unroll
         for (int v = 0; v < NV; ++v) un[v] = S(a.Uf_all[nix * NV + v]);
         S Fa[2][NV], Fb[2][NV];
-        Phys<PHYS>::template conv<S, double>(pp, w.Uf[j], Fa);
-        Phys<PHYS>::template conv<S, double>(pp, un, Fb);
-        S lam = dmax(Phys<PHYS>::template wave<S, double>(pp, w.Uf[j], n0, n1),
-                     Phys<PHYS>::template wave<S, double>(pp, un, n0, n1));
+        Phys<PHYS>::template conv<S, double>(pc, w.Uf[j], Fa);
+        Phys<PHYS>::template conv<S, double>(pc, un, Fb);
+        S lam = dmax(Phys<PHYS>::template wave<S, double>(pc, w.Uf[j], n0, n1),
+                     Phys<PHYS>::template wave<S, double>(pc, un, n0, n1));
 #pragma unroll
         for (int v = 0; v < NV; ++v)
           Fh[v] = 0.5 * (n0 * (Fa[0][v] + Fb[0][v]) + n1 * (Fa[1][v] + Fb[1][v])) + 0.5 * lam * (w.Uf[j][v] - un[v]);
@@ -210,16 +211,16 @@ __global__ void __launch_bounds__(TPE* EPB) k_element(const __grid_constant__ Re
           S Fv[2][NV];
           if (kf == FK_FR) {
             S Fw[2][NV];
-            Phys<PHYS>::template visc<S, double>(pp, w.Uf[j], w.qf[j], Fv);
-            Phys<PHYS>::template visc<S, double>(pp, un, qn, Fw);
+            Phys<PHYS>::template visc<S, double>(pc, w.Uf[j], w.qf[j], Fv);
+            Phys<PHYS>::template visc<S, double>(pc, un, qn, Fw);
 #pragma unroll
             for (int v = 0; v < NV; ++v)
               Fh[v] = Fh[v] - 0.5 * (n0 * (Fv[0][v] + Fw[0][v]) + n1 * (Fv[1][v] + Fw[1][v]));
           } else {
             if (is_imp)
-              Phys<PHYS>::template visc<S, double>(pp, w.Uf[j], w.qf[j], Fv);
+              Phys<PHYS>::template visc<S, double>(pc, w.Uf[j], w.qf[j], Fv);
             else
-              Phys<PHYS>::template visc<S, double>(pp, un, qn, Fv);
+              Phys<PHYS>::template visc<S, double>(pc, un, qn, Fv);
 #pragma unroll
             for (int v = 0; v < NV; ++v) Fh[v] = Fh[v] - (n0 * Fv[0][v] + n1 * Fv[1][v]);
           }
