@@ -183,6 +183,24 @@ int fr_profile_read(const fr_ctx* ctx, fr_profile* out /* host */);
 /* Number of kernels this library has launched in this process (all contexts). */
 unsigned long long fr_kernel_launches(void);
 
+/* Allocation-free condensation, for callers that cannot let a library allocate device memory
+ * (a host code with its own pooled device-memory budget, a plugin handed pre-allocated buffers).
+ * The paper has no counterpart; the operation is that of hfr_condense on caller-provided blocks:
+ * X = A^{-1}[B | r], S = D - C X_B, t = s - C x_r for nimplicit elements, blocks row-major in the
+ * given precision (A: nA x nA, B: nA x nT, C: nT x nA, D, S: nT x nT, XB: nA x nT; r, xr: nA and
+ * s, t: nT per element in FP64).  All pointers are device pointers; stream is a cudaStream_t.
+ * The factors and pivots are kept in one file-scope device array of HFR_NOALLOC_SCRATCH_BYTES
+ * (held by every GPU that loads the library until the process exits).  Limit:
+ *   256 + round_up_256(nimplicit nA 4) + nimplicit nA^2 (8 for FP64, 4 for FP32) <= 16 MiB,
+ * larger requests return FR_ERR_INVALID_ARG (nA <= 160).  The first call on a device looks up the
+ * array's device address; make that first call before any stream capture.  Every call uses the
+ * same array, so calls that overlap on the GPU (other streams, other threads) race.  No
+ * cudaMalloc / cudaFree is made.  Synchronises the stream; FR_ERR_SINGULAR on a zero pivot. */
+#define HFR_NOALLOC_SCRATCH_BYTES (16u << 20)
+int hfr_condense_noalloc(int nimplicit, int nA, int nT, int precision, const void* A, const void* B, const void* C,
+                         const void* D, const double* r, const double* s, void* XB, double* xr, void* S, double* t,
+                         void* stream);
+
 int fr_last_error(const fr_ctx* ctx, fr_error_info* info /* host */);
 const char* fr_status_string(int code);
 

@@ -48,6 +48,7 @@ ABI_SYMBOLS = [
     "fr_profile_enable",
     "fr_profile_read",
     "fr_kernel_launches",
+    "hfr_condense_noalloc",
     "fr_last_error",
     "fr_status_string",
 ]
@@ -154,6 +155,8 @@ def load_library(path: str = LIB_PATH):
     lib.fr_profile_read.argtypes = [vp, ctypes.POINTER(fr_profile)]
     lib.fr_kernel_launches.argtypes = []
     lib.fr_kernel_launches.restype = ctypes.c_ulonglong
+    lib.hfr_condense_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp,
+                                         dp, dp, dp, dp, dp, vp]
     lib.fr_last_error.argtypes = [vp, ctypes.POINTER(fr_error_info)]
     lib.fr_status_string.argtypes = [ctypes.c_int]
     lib.fr_status_string.restype = ctypes.c_char_p
@@ -173,6 +176,19 @@ class HfrError(RuntimeError):
 
 def _ptr(t):
     return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def hfr_condense_noalloc(A, B, C, D, r, s, XB, xr, S, t, precision=FR_PREC_FP64, stream=None):
+    """Allocation-free condensation on caller-provided device tensors (see include/hfr.h):
+    shapes (E, nA, nA), (E, nA, nT), (E, nT, nA), (E, nT, nT), (E, nA), (E, nT) in, XB, xr, S, t out.
+    Returns the status code (0 = ok)."""
+    import torch
+
+    lib = load_library()
+    E, nA, nT = int(A.shape[0]), int(A.shape[1]), int(B.shape[2])
+    st = stream if stream is not None else torch.cuda.current_stream()
+    return lib.hfr_condense_noalloc(E, nA, nT, int(precision), _ptr(A), _ptr(B), _ptr(C), _ptr(D), _ptr(r), _ptr(s),
+                                    _ptr(XB), _ptr(xr), _ptr(S), _ptr(t), ctypes.c_void_p(st.cuda_stream))
 
 
 class Context:
