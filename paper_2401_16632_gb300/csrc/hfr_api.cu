@@ -494,6 +494,7 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, const fr_config* cfg, voi
   ctx->gm.partial = dalloc<double>(ctx, (size_t)GM_NBLK * (GM_MAXM + 1), &rc);
   ctx->gm.state = dalloc<GmresState>(ctx, 1, &rc);
   ctx->gm.ticket = dalloc<unsigned int>(ctx, 1, &rc);
+  ctx->gm.z32 = ctx->prec_bytes == 4 ? dalloc<float>(ctx, std::max(nh, (size_t)1), &rc) : nullptr;
   ctx->duhat = dalloc<double>(ctx, nh, &rc);
   ctx->du = dalloc<double>(ctx, (size_t)Eim * nA, &rc);
   ctx->res_tmp = dalloc<double>(ctx, (size_t)Eim * nA, &rc);
@@ -783,13 +784,15 @@ static void cb_matvec(void* c, const double* x, double* y, cudaStream_t s) {
   launch_trace_matvec(ctx->prec_bytes, trace_args(ctx), x, y, s);
   prof_end(ctx, ph);
 }
-static void cb_gmatvec(void* c, const GmresState* st, int j, const double* x, double* y, cudaStream_t s) {
+static void cb_gmatvec(void* c, const GmresState* st, int j, const double* x, const float* x32, double* y,
+                       cudaStream_t s) {
   fr_ctx* ctx = (fr_ctx*)c;
-  launch_trace_matvec(ctx->prec_bytes, trace_args(ctx), x, y, s, &st->kdone, j);
+  launch_trace_matvec(ctx->prec_bytes, trace_args(ctx), x, y, s, &st->kdone, j, x32);
 }
-static void cb_precond(void* c, const GmresState* st, int j, const double* x, double* y, cudaStream_t s) {
+static void cb_precond(void* c, const GmresState* st, int j, double* x, double* y, float* y32, cudaStream_t s) {
   fr_ctx* ctx = (fr_ctx*)c;
-  launch_precond_apply(ctx->prec_bytes, trace_args(ctx), ctx->Pinv, x, y, s, &st->kdone, j);
+  launch_precond_apply(ctx->prec_bytes, trace_args(ctx), ctx->Pinv, x, y, s, &st->kdone, j,
+                       j > 0 ? &st->inv_hn : nullptr, y32);
 }
 
 static int gmres_impl(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* iters, double* final_rel) {
@@ -978,7 +981,9 @@ extern "C" int imex_stage(fr_ctx* ctx, int stage, double dt, const double* u_n, 
     }
     if (it >= newton_maxit) break;
     rc = jacobian_blocks(ctx, u_stage, uhat, adt);
-    if (!rc) rc = condense_impl(ctx, refine);
+    // the local solves are refined once, at the back-substitution (du = A^{-1}(r - B du^)); refining
+    // x_r as well would not change the converged step
+    if (!rc) rc = condense_impl(ctx, 0);
     if (!rc) rc = check_status(ctx, "imex_stage: zero pivot in condensation");
     if (rc) return rc;
     int its = 0;

@@ -100,12 +100,15 @@ struct TraceArgs {
   const int* tr_of_c;     // Eim x 4 trace id of each face of a compact implicit element (-1 none)
   const void* S;          // Eim x nT x nT
 };
+// x32 (nullable): FP32 copy of x read instead of x by the FP32 fixed-shape kernels
 cudaError_t launch_trace_matvec(int prec_bytes, const TraceArgs& a, const double* x, double* y, cudaStream_t st,
-                                const int* gate = nullptr, int gj = 0);
+                                const int* gate = nullptr, int gj = 0, const float* x32 = nullptr);
 cudaError_t launch_precond_build(int prec_bytes, const TraceArgs& a, double* Pinv, int* status, cudaStream_t st);
 // Pinv holds the inverses in the block precision (double or float storage in the same buffer)
-cudaError_t launch_precond_apply(int prec_bytes, const TraceArgs& a, const double* Pinv, const double* x, double* y,
-                                 cudaStream_t st, const int* gate = nullptr, int gj = 0);
+// inv_h (nullable): x is first scaled in place by *inv_h; y32 (nullable): FP32 copy of y
+cudaError_t launch_precond_apply(int prec_bytes, const TraceArgs& a, const double* Pinv, double* x, double* y,
+                                 cudaStream_t st, const int* gate = nullptr, int gj = 0, const double* inv_h = nullptr,
+                                 float* y32 = nullptr);
 cudaError_t launch_assemble_t(const TraceArgs& a, const double* te, double* t, cudaStream_t st);
 cudaError_t launch_backsolve(int prec_bytes, const TraceArgs& a, int Eim, int nA, const void* XB, const double* xr,
                              const double* duhat, double* du, cudaStream_t st);

@@ -28,8 +28,9 @@ __device__ void givens_update(GmresState* st, int j, double rtol, int m);
 __global__ void __launch_bounds__(KB) k_cgs(GmresState* st, int j, const double* __restrict__ V, size_t n, int na,
                                             int pre, const double* D, int nd, double* w,
                                             double* __restrict__ partial, unsigned int* ticket, int mode, double rtol,
-                                            int m) {
-  if (mode <= 2 && gated(st, j)) return;
+                                            int m, int only_if_reorth) {
+  if ((mode <= 2 || mode >= 5) && gated(st, j)) return;
+  if (only_if_reorth && !st->reorth) return;
   __shared__ double red[GM_MAXM + 1][KB / 32];
   __shared__ bool last;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -38,9 +39,14 @@ __global__ void __launch_bounds__(KB) k_cgs(GmresState* st, int j, const double*
   if (pre) {
     const double* c = pre == 1 ? st->hc : st->h2;
     for (size_t x = i0; x < n; x += stride) {
-      double acc = 0.0;
-      for (int i = 0; i < na; ++i) acc += c[i] * V[(size_t)i * n + x];
-      w[x] -= acc;
+      double a0 = 0.0, a1 = 0.0;
+      int i = 0;
+      for (; i + 1 < na; i += 2) {
+        a0 += c[i] * V[(size_t)i * n + x];
+        a1 += c[i + 1] * V[(size_t)(i + 1) * n + x];
+      }
+      if (i < na) a0 += c[i] * V[(size_t)i * n + x];
+      w[x] -= a0 + a1;
     }
   }
   // warp sums of eight dots at a time into shared memory; one barrier for the whole pass
@@ -83,15 +89,23 @@ __global__ void __launch_bounds__(KB) k_cgs(GmresState* st, int j, const double*
     if (lane == 0) {
       if (mode == 0) st->hc[i] = t;
       else if (mode == 1) { st->h2[i] = t; st->hc[i] += t; }
-      else if (mode == 2) st->hc[j + 1] = sqrt(t);
+      else if (mode == 2 || mode == 6) st->hc[j + 1] = sqrt(t);
       else if (mode == 3) st->beta = sqrt(t);
-      else st->bnorm = sqrt(t);
+      else if (mode == 4) st->bnorm = sqrt(t);
+      else if (mode == 5) { if (i < nd - 1) st->hc[i] = t; else st->wnorm_old = sqrt(t); }
     }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     *ticket = 0u;
-    if (mode == 2) givens_update(st, j, rtol, m);
+    if (mode == 2) {
+      st->reorth = 0;
+      givens_update(st, j, rtol, m);
+    } else if (mode == 6) {
+      // DGKS: a second Gram-Schmidt pass only when the projection removed most of w
+      if (st->hc[j + 1] < 0.70710678118654752 * st->wnorm_old) st->reorth = 1;
+      else givens_update(st, j, rtol, m);
+    }
   }
 }
 
@@ -119,6 +133,7 @@ __device__ void givens_update(GmresState* st, int j, double rtol, int m) {
   }
   const double a = h[j], b = h[j + 1];
   st->hn = b;
+  st->inv_hn = b != 0.0 ? 1.0 / b : 0.0;
   const double r = sqrt(a * a + b * b);
   double c = 1.0, s = 0.0;
   if (r > 0.0) { c = a / r; s = b / r; }
@@ -186,6 +201,8 @@ __global__ void k_reset_state(GmresState* st) {
     st->nan = 0;
     st->kdone = -1;
     st->k = 0;
+    st->reorth = 0;
+    st->inv_hn = 0.0;
   }
 }
 
@@ -201,7 +218,7 @@ static void norm_into(const GmresBuffers& b, int j, double* v, size_t n, int mod
                       cudaStream_t s) {
   const int nb = grid_for(n);
   (hfr::count_launch(), k_cgs<<<nb, KB, 0, s>>>(b.state, j, nullptr, n, 0, 0, v, 1, v, b.partial, b.ticket, mode,
-                                                 rtol, m));
+                                                 rtol, m, 0));
 }
 
 int run_gmres(const GmresOps& ops, const GmresBuffers& b, const double* t, double* x, double rtol, int restart,
@@ -211,6 +228,7 @@ int run_gmres(const GmresOps& ops, const GmresBuffers& b, const double* t, doubl
   GmresState* st = b.state;
   const int nb = grid_for(n);
   (hfr::count_launch(), k_reset_state<<<1, 32, 0, s>>>(st));
+  // (reorth flag and inv_hn are reset by k_reset_state)
   norm_into(b, 0, const_cast<double*>(t), n, 4, rtol, m, s);  // bnorm (t is only read)
   cudaMemsetAsync(x, 0, n * sizeof(double), s);
   int total = 0;
@@ -232,16 +250,19 @@ int run_gmres(const GmresOps& ops, const GmresBuffers& b, const double* t, doubl
       double* vj = b.V + (size_t)j * n;
       double* w = b.V + (size_t)(j + 1) * n;
       double* zj = b.Z + (size_t)j * n;
-      ops.precond(ops.ctx, st, j, vj, zj, s);
-      ops.gated_matvec(ops.ctx, st, j, zj, w, s);
-      // classical Gram-Schmidt twice, in three fused passes
-      (hfr::count_launch(), k_cgs<<<nb, KB, 0, s>>>(st, j, b.V, n, j + 1, 0, b.V, j + 1, w, b.partial, b.ticket, 0,
-                                                     rtol, m));
-      (hfr::count_launch(), k_cgs<<<nb, KB, 0, s>>>(st, j, b.V, n, j + 1, 1, b.V, j + 1, w, b.partial, b.ticket, 1,
-                                                     rtol, m));
+      // v_j = w_j / h_{j,j-1} is normalised in place by the preconditioner kernel (j > 0)
+      ops.precond(ops.ctx, st, j, vj, zj, b.z32, s);
+      ops.gated_matvec(ops.ctx, st, j, zj, b.z32, w, s);
+      // classical Gram-Schmidt with a conditional second pass (DGKS): pass 1 also yields ||w||,
+      // since w = V_{j+1} follows V_j in memory
+      (hfr::count_launch(), k_cgs<<<nb, KB, 0, s>>>(st, j, b.V, n, j + 1, 0, b.V, j + 2, w, b.partial, b.ticket, 5,
+                                                     rtol, m, 0));
+      (hfr::count_launch(), k_cgs<<<nb, KB, 0, s>>>(st, j, b.V, n, j + 1, 1, w, 1, w, b.partial, b.ticket, 6, rtol,
+                                                     m, 0));
+      (hfr::count_launch(), k_cgs<<<nb, KB, 0, s>>>(st, j, b.V, n, j + 1, 0, b.V, j + 1, w, b.partial, b.ticket, 1,
+                                                     rtol, m, 1));
       (hfr::count_launch(), k_cgs<<<nb, KB, 0, s>>>(st, j, b.V, n, j + 1, 2, w, 1, w, b.partial, b.ticket, 2, rtol,
-                                                     m));
-      (hfr::count_launch(), k_scale_next<<<nb, KB, 0, s>>>(st, j, w, n));
+                                                     m, 1));
       if ((j + 1) % check_every == 0 || j + 1 == m) {
         cudaMemcpyAsync(&hs, st, sizeof(GmresHead), cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return -1;

@@ -16,6 +16,9 @@ struct GmresHead {
 struct GmresState {
   double beta, bnorm, res, hn;
   int k, kdone, converged, nan;
+  double inv_hn;     // 1 / hn, used to normalise the next Krylov vector
+  double wnorm_old;  // ||w|| before orthogonalisation (re-orthogonalisation test)
+  int reorth;        // 1 when the current column needs a second Gram-Schmidt pass
   double H[(GM_MAXM + 1) * GM_MAXM];
   double g[GM_MAXM + 1];
   double cs[GM_MAXM], sn[GM_MAXM];
@@ -28,14 +31,18 @@ struct GmresState {
 struct GmresOps {
   void* ctx;
   void (*matvec)(void* ctx, const double* x, double* y, cudaStream_t s);
-  void (*gated_matvec)(void* ctx, const GmresState* st, int j, const double* x, double* y, cudaStream_t s);
-  void (*precond)(void* ctx, const GmresState* st, int j, const double* x, double* y, cudaStream_t s);
+  void (*gated_matvec)(void* ctx, const GmresState* st, int j, const double* x, const float* x32, double* y,
+                       cudaStream_t s);
+  // z = P^{-1} v_j (and its FP32 copy when z32 != null); for j > 0 it first normalises v_j in
+  // place by st->inv_hn = 1 / h_{j,j-1}
+  void (*precond)(void* ctx, const GmresState* st, int j, double* v, double* z, float* z32, cudaStream_t s);
 };
 
 struct GmresBuffers {
   size_t n;
   double* V;        // (GM_MAXM + 1) x n
   double* Z;        // GM_MAXM x n
+  float* z32;       // n: FP32 copy of the current preconditioned vector (FP32 mat-vec), or null
   double* partial;  // GM_NBLK x (GM_MAXM + 1)
   unsigned int* ticket;  // zero-initialised completion counter of the reduction kernels
   GmresState* state;

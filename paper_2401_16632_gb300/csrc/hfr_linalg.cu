@@ -72,6 +72,72 @@ __global__ void __launch_bounds__(256) k_trace_matvec(const __grid_constant__ Tr
   }
 }
 
+// Same product with the shape fixed at compile time: every row of both row blocks is loaded up
+// front (rows i = grp + 4u), so the loads of a face are all in flight before the reductions.
+template <typename T, int NT, int BS>
+__global__ void __launch_bounds__(256) k_trace_matvec_fixed(const __grid_constant__ TraceArgs a,
+                                                            const double* __restrict__ x,
+                                                            const float* __restrict__ x32, double* __restrict__ y,
+                                                            const int* gate, int gj) {
+  constexpr int CT = (NT + 7) / 8, RU = (BS + 3) / 4;
+  if (gate && *gate >= 0 && gj >= *gate) return;
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= a.ntrace) return;
+  const int grp = lane >> 3, g8 = lane & 7;
+  const T* S = reinterpret_cast<const T*>(a.S);
+  int es[2], fs[2];
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    es[side] = a.sides[t * 4 + side * 2];
+    fs[side] = a.sides[t * 4 + side * 2 + 1];
+  }
+  T sv[2][RU][CT];
+#pragma unroll
+  for (int side = 0; side < 2; ++side)
+#pragma unroll
+    for (int u = 0; u < RU; ++u) {
+      const int i = grp + 4 * u;
+      const bool ok = es[side] >= 0 && i < BS;
+      const T* row = S + ((size_t)(ok ? es[side] : 0) * NT + (size_t)(ok ? fs[side] : 0) * BS + (ok ? i : 0)) * NT;
+#pragma unroll
+      for (int c = 0; c < CT; ++c) {
+        const int l = g8 + 8 * c;
+        sv[side][u][c] = (ok && l < NT) ? row[l] : T(0);
+      }
+    }
+  T xv[2][CT];
+#pragma unroll
+  for (int side = 0; side < 2; ++side)
+#pragma unroll
+    for (int c = 0; c < CT; ++c) {
+      const int l = g8 + 8 * c;
+      T v = T(0);
+      if (es[side] >= 0 && l < NT) {
+        const int fp = l / BS;
+        const int tf = a.tr_of_c[es[side] * 4 + fp];
+        if (tf >= 0) {
+          const size_t ix = (size_t)tf * BS + (l - fp * BS);
+          v = x32 ? T(x32[ix]) : T(x[ix]);
+        }
+      }
+      xv[side][c] = v;
+    }
+#pragma unroll
+  for (int u = 0; u < RU; ++u) {
+    const int i = grp + 4 * u;
+    T acc = T(0);
+#pragma unroll
+    for (int side = 0; side < 2; ++side)
+#pragma unroll
+      for (int c = 0; c < CT; ++c) acc += sv[side][u][c] * xv[side][c];
+    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    if (g8 == 0 && i < BS) y[(size_t)t * BS + i] = double(acc);
+  }
+}
+
 // P_f = sum of both sides' diagonal face blocks of S_k, inverted in place by Gauss-Jordan with
 // partial pivoting (pivot bookkeeping only, as in the condensation) in the block precision T.
 // One warp per face, the bs x bs block in shared memory; Pinv_f = (P_f)^{-1} stored row-major.
@@ -147,23 +213,33 @@ __global__ void k_precond_build(const __grid_constant__ TraceArgs a, T* __restri
   __syncwarp();
 }
 
-// y_f = Pinv_f x_f, one warp per face, lane = row
+// y_f = Pinv_f x_f, one warp per face, lane = row.  With `hn` (GMRES), x is first normalised in
+// place, x <- x / *hn (the new Krylov vector), before it is preconditioned.
 template <typename T>
 __global__ void k_precond_apply(const __grid_constant__ TraceArgs a, const T* __restrict__ Pinv,
-                                const double* __restrict__ x, double* __restrict__ y, const int* gate, int gj) {
+                                double* __restrict__ x, double* __restrict__ y, const int* gate, int gj,
+                                const double* inv_h, float* __restrict__ y32) {
   if (gate && *gate >= 0 && gj >= *gate) return;
   const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (t >= a.ntrace) return;
   const int bs = a.n * a.nv;
   const T* P = Pinv + (size_t)t * bs * bs;
-  const T xv = lane < bs ? T(x[(size_t)t * bs + lane]) : T(0);
+  double xd = lane < bs ? x[(size_t)t * bs + lane] : 0.0;
+  if (inv_h) {
+    xd *= *inv_h;
+    if (lane < bs) x[(size_t)t * bs + lane] = xd;
+  }
+  const T xv = T(xd);
   T acc = T(0);
   for (int j = 0; j < bs; ++j) {
     const T xj = __shfl_sync(0xffffffffu, xv, j);
     if (lane < bs) acc += P[lane * bs + j] * xj;
   }
-  if (lane < bs) y[(size_t)t * bs + lane] = double(acc);
+  if (lane < bs) {
+    y[(size_t)t * bs + lane] = double(acc);
+    if (y32) y32[(size_t)t * bs + lane] = float(acc);
+  }
 }
 
 // global trace right-hand side t = sum_k scatter(t_k)
@@ -209,10 +285,26 @@ __global__ void k_backsolve(const __grid_constant__ TraceArgs a, int Eim, int nA
 }
 
 cudaError_t launch_trace_matvec(int prec_bytes, const TraceArgs& a, const double* x, double* y, cudaStream_t st,
-                                const int* gate, int gj) {
+                                const int* gate, int gj, const float* x32) {
   if (a.ntrace == 0) return cudaSuccess;
   const int threads = 256;
   const int grid = (a.ntrace * 32 + threads - 1) / threads;
+  const int bs = a.n * a.nv;
+#define HFR_MV_FIXED(T_, NT_, BS_)                                                                       \
+  if (a.nT == NT_ && bs == BS_) {                                                                        \
+    (hfr::count_launch(), k_trace_matvec_fixed<T_, NT_, BS_><<<grid, threads, 0, st>>>(a, x, x32, y, gate, gj)); \
+    return cudaGetLastError();                                                                           \
+  }
+  if (prec_bytes == 4) {
+    HFR_MV_FIXED(float, 64, 16)
+    HFR_MV_FIXED(float, 80, 20)
+    HFR_MV_FIXED(float, 48, 12)
+  } else {
+    HFR_MV_FIXED(double, 64, 16)
+    HFR_MV_FIXED(double, 80, 20)
+    HFR_MV_FIXED(double, 48, 12)
+  }
+#undef HFR_MV_FIXED
   if (prec_bytes == 8)
     (hfr::count_launch(), k_trace_matvec<double><<<grid, threads, 0, st>>>(a, x, y, gate, gj));
   else
@@ -235,15 +327,15 @@ cudaError_t launch_precond_build(int prec_bytes, const TraceArgs& a, double* Pin
   return cudaGetLastError();
 }
 
-cudaError_t launch_precond_apply(int prec_bytes, const TraceArgs& a, const double* Pinv, const double* x, double* y,
-                                 cudaStream_t st, const int* gate, int gj) {
+cudaError_t launch_precond_apply(int prec_bytes, const TraceArgs& a, const double* Pinv, double* x, double* y,
+                                 cudaStream_t st, const int* gate, int gj, const double* inv_h, float* y32) {
   if (a.ntrace == 0) return cudaSuccess;
   const int threads = 256;
   const int grid = (a.ntrace * 32 + threads - 1) / threads;
   if (prec_bytes == 8)
-    (hfr::count_launch(), k_precond_apply<double><<<grid, threads, 0, st>>>(a, Pinv, x, y, gate, gj));
+    (hfr::count_launch(), k_precond_apply<double><<<grid, threads, 0, st>>>(a, Pinv, x, y, gate, gj, inv_h, y32));
   else
-    (hfr::count_launch(), k_precond_apply<float><<<grid, threads, 0, st>>>(a, reinterpret_cast<const float*>(Pinv), x, y, gate, gj));
+    (hfr::count_launch(), k_precond_apply<float><<<grid, threads, 0, st>>>(a, reinterpret_cast<const float*>(Pinv), x, y, gate, gj, inv_h, y32));
   return cudaGetLastError();
 }
 
