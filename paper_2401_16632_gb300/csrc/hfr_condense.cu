@@ -249,6 +249,172 @@ __global__ void __launch_bounds__(GJ_THREADS) k_condense_reg(const __grid_consta
   }
 }
 
+// ----------------------------------------------------- row-per-thread kernel (FP32, nA % 32 == 0)
+// One element per CTA of nA threads: thread r owns physical row r of [A | B | r] in registers and
+// the nA pivot steps are unrolled, so every column index is a compile-time constant.  Per step:
+// warp argmax of |column c| over the rows not yet used, a two-candidate combine, the pivot thread
+// publishes its row as it stands (column c replaced by pivot + 1), and every thread performs
+// m_j -= (m_c / pivot) * row_j  (one FMA per entry; the pivot thread uses factor 0 and sets
+// m_c = 1).  A row that has served as pivot is therefore kept multiplied by its own pivot; one
+// division per row at the end restores (PA)^{-1} | X.  S = D - C X uses X transposed in shared
+// memory, read as broadcast float4.
+template <int NA, int NT>
+__device__ __forceinline__ void condense_rows_one(const CondArgs& a, const int k) {
+  constexpr int NC = NA + NT + 1;
+  constexpr int NQ = (NC + 3) / 4;
+  constexpr int NW = NA / 32;
+  constexpr int LX = NA + 4;  // row length of the transposed X in shared memory
+  static_assert(NA % 32 == 0 && NA % 4 == 0 && NT % 4 == 0, "shape");
+  __shared__ __align__(16) float pr[NQ * 4];
+  __shared__ float cval[NW];
+  __shared__ int cidx[NW];
+  __shared__ float s_inv;
+  __shared__ int s_bad;
+  __shared__ __align__(16) float sXt[(NT + 1) * LX];
+  const int r = threadIdx.x, lane = r & 31, wid = r >> 5;
+  const float* gA = reinterpret_cast<const float*>(a.A) + (size_t)k * NA * NA;
+  const float* gB = reinterpret_cast<const float*>(a.B) + (size_t)k * NA * NT;
+  float m[NQ * 4];
+#pragma unroll
+  for (int q = 0; q < NA / 4; ++q) {
+    const float4 v = reinterpret_cast<const float4*>(gA + (size_t)r * NA)[q];
+    m[4 * q] = v.x;
+    m[4 * q + 1] = v.y;
+    m[4 * q + 2] = v.z;
+    m[4 * q + 3] = v.w;
+  }
+#pragma unroll
+  for (int q = 0; q < NT / 4; ++q) {
+    const float4 v = reinterpret_cast<const float4*>(gB + (size_t)r * NT)[q];
+    m[NA + 4 * q] = v.x;
+    m[NA + 4 * q + 1] = v.y;
+    m[NA + 4 * q + 2] = v.z;
+    m[NA + 4 * q + 3] = v.w;
+  }
+  m[NA + NT] = float(a.r[(size_t)k * NA + r]);
+#pragma unroll
+  for (int j = NC; j < NQ * 4; ++j) m[j] = 0.f;
+  if (r == 0) s_bad = 0;
+  bool used = false;
+  float mypiv = 1.f;
+  int mystep = 0;
+#pragma unroll
+  for (int c = 0; c < NA; ++c) {
+    float best = used ? -1.f : fabsf(m[c]);
+    int bi = r;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) {
+      cval[wid] = best;
+      cidx[wid] = bi;
+    }
+    __syncthreads();
+    float b = cval[0];
+    int p = cidx[0];
+#pragma unroll
+    for (int w2 = 1; w2 < NW; ++w2) {
+      const float ob = cval[w2];
+      const int oi = cidx[w2];
+      if (ob > b || (ob == b && oi < p)) { b = ob; p = oi; }
+    }
+    if (r == p) {
+      const float pv = m[c];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q)
+        reinterpret_cast<float4*>(pr)[q] = make_float4(m[4 * q], m[4 * q + 1], m[4 * q + 2], m[4 * q + 3]);
+      pr[c] = pv + 1.f;
+      s_inv = pv != 0.f ? 1.f / pv : 0.f;
+      if (!(b > 0.f)) s_bad = 1;
+      a.piv[(size_t)k * NA + c] = r;
+      used = true;
+      mypiv = pv;
+      mystep = c;
+    }
+    __syncthreads();
+    const float f = (r == p) ? 0.f : m[c] * s_inv;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const float4 pq = reinterpret_cast<const float4*>(pr)[q];
+      m[4 * q] -= f * pq.x;
+      m[4 * q + 1] -= f * pq.y;
+      m[4 * q + 2] -= f * pq.z;
+      m[4 * q + 3] -= f * pq.w;
+    }
+    if (r == p) m[c] = 1.f;
+  }
+  // undo the per-row pivot scaling: physical row r is logical row mystep
+  const float sc = mypiv != 0.f ? 1.f / mypiv : 0.f;
+#pragma unroll
+  for (int j = 0; j < NC; ++j) m[j] *= sc;
+  float* gInv = reinterpret_cast<float*>(a.LU) + (size_t)k * NA * NA;
+  float* gXB = reinterpret_cast<float*>(a.XB) + (size_t)k * NA * NT;
+#pragma unroll
+  for (int j = 0; j < NA; ++j) gInv[(size_t)j * NA + mystep] = m[j];  // ((PA)^{-1})^T
+#pragma unroll
+  for (int q = 0; q < NT / 4; ++q)
+    reinterpret_cast<float4*>(gXB + (size_t)mystep * NT)[q] =
+        make_float4(m[NA + 4 * q], m[NA + 4 * q + 1], m[NA + 4 * q + 2], m[NA + 4 * q + 3]);
+  a.xr[(size_t)k * NA + mystep] = double(m[NA + NT]);
+#pragma unroll
+  for (int j = 0; j <= NT; ++j) sXt[j * LX + mystep] = m[NA + j];
+  __syncthreads();
+  if (r == 0 && s_bad) {
+    atomicOr(a.status, DEV_ERR_SINGULAR);
+    atomicMin(a.status + 1, k);
+  }
+  // S = D - C X_B, t = s - C x_r: thread i < NT computes row i, C row i in registers
+  if (r < NT) {
+    const int i = r;
+    const float* gC = reinterpret_cast<const float*>(a.C) + (size_t)k * NT * NA + (size_t)i * NA;
+    const float* gD = reinterpret_cast<const float*>(a.D) + (size_t)k * NT * NT + (size_t)i * NT;
+    float* gS = reinterpret_cast<float*>(a.S) + (size_t)k * NT * NT + (size_t)i * NT;
+#pragma unroll
+    for (int q = 0; q < NA / 4; ++q) {
+      const float4 v = reinterpret_cast<const float4*>(gC)[q];
+      m[4 * q] = v.x;
+      m[4 * q + 1] = v.y;
+      m[4 * q + 2] = v.z;
+      m[4 * q + 3] = v.w;
+    }
+#pragma unroll 1
+    for (int j0 = 0; j0 < NT; j0 += 4) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int q = 0; q < NA / 4; ++q) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float4 x4 = reinterpret_cast<const float4*>(sXt + (j0 + u) * LX)[q];
+          acc[u] += m[4 * q] * x4.x + m[4 * q + 1] * x4.y + m[4 * q + 2] * x4.z + m[4 * q + 3] * x4.w;
+        }
+      }
+      const float4 d4 = reinterpret_cast<const float4*>(gD)[j0 / 4];
+      reinterpret_cast<float4*>(gS)[j0 / 4] = make_float4(d4.x - acc[0], d4.y - acc[1], d4.z - acc[2], d4.w - acc[3]);
+    }
+    float acc = 0.f;
+#pragma unroll
+    for (int q = 0; q < NA / 4; ++q) {
+      const float4 x4 = reinterpret_cast<const float4*>(sXt + NT * LX)[q];
+      acc += m[4 * q] * x4.x + m[4 * q + 1] * x4.y + m[4 * q + 2] * x4.z + m[4 * q + 3] * x4.w;
+    }
+    a.t[(size_t)k * NT + i] = a.s[(size_t)k * NT + i] - double(acc);
+  }
+}
+
+template <int NA, int NT>
+__global__ void __launch_bounds__(NA) k_condense_rows(const __grid_constant__ CondArgs a) {
+  // persistent: a fixed number of CTAs per SM loop over the elements, so the CTAs resident on an
+  // SM start together and execute the same (data-independent) instruction stream in step, which
+  // keeps the long unrolled body resident in the instruction caches
+  for (int k = blockIdx.x; k < a.Eim; k += gridDim.x) {
+    condense_rows_one<NA, NT>(a, k);
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------- generic shared-memory kernel
 // Same algorithm and outputs for any (nA, nT) and either precision; the augmented block lives
 // in shared memory.  Used where the register tile does not fit (e.g. FP64 with nA >= 100).
@@ -618,6 +784,14 @@ template <typename T>
 static cudaError_t cond_dispatch(const CondArgs& a, cudaStream_t st) {
   if (a.Eim == 0) return cudaSuccess;
   const int nA = a.nA, nT = a.nT;
+  if (sizeof(T) == 4 && nA == 64 && nT == 64) {
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = a.Eim < 4 * nsm ? a.Eim : 4 * nsm;
+    (hfr::count_launch(), k_condense_rows<64, 64><<<grid, 64, 0, st>>>(a));
+    return cudaGetLastError();
+  }
   if (nA == 9 && nT == 12) return cond_reg<T, 9, 12>(a, st);
   if (nA == 16 && nT == 16) return cond_reg<T, 16, 16>(a, st);
   if (nA == 36 && nT == 48) return cond_reg<T, 36, 48>(a, st);

@@ -39,34 +39,61 @@ __global__ void __launch_bounds__(KB) k_cgs(GmresState* st, int j, const double*
   if (pre) {
     const double* c = pre == 1 ? st->hc : st->h2;
     for (size_t x = i0; x < n; x += stride) {
-      double a0 = 0.0, a1 = 0.0;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
       int i = 0;
-      for (; i + 1 < na; i += 2) {
+      for (; i + 3 < na; i += 4) {
         a0 += c[i] * V[(size_t)i * n + x];
         a1 += c[i + 1] * V[(size_t)(i + 1) * n + x];
+        a2 += c[i + 2] * V[(size_t)(i + 2) * n + x];
+        a3 += c[i + 3] * V[(size_t)(i + 3) * n + x];
       }
-      if (i < na) a0 += c[i] * V[(size_t)i * n + x];
-      w[x] -= a0 + a1;
+      for (; i < na; ++i) a0 += c[i] * V[(size_t)i * n + x];
+      w[x] -= (a0 + a1) + (a2 + a3);
     }
   }
-  // warp sums of eight dots at a time into shared memory; one barrier for the whole pass
-  for (int c0 = 0; c0 < nd; c0 += 8) {
-    double acc[8];
+  // sixteen dots at a time: per-thread partial sums, then a warp reduce-scatter (each butterfly
+  // level halves the values a lane carries: 16 shuffles for 16 sums instead of 80), so lane l
+  // ends with the warp sum of value l >> 1
+  for (int c0 = 0; c0 < nd; c0 += 16) {
+    double acc[16];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
     for (size_t x = i0; x < n; x += stride) {
       const double wx = w[x];
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
+      for (int q = 0; q < 16; ++q)
         if (c0 + q < nd) acc[q] += D[(size_t)(c0 + q) * n + x] * wx;
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      double v = acc[q];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0 && c0 + q < nd) red[c0 + q][wid] = v;
+      const bool up = lane & 16;
+      const double send = up ? acc[q] : acc[q + 8];
+      const double keep = up ? acc[q + 8] : acc[q];
+      acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
     }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const bool up = lane & 8;
+      const double send = up ? acc[q] : acc[q + 4];
+      const double keep = up ? acc[q + 4] : acc[q];
+      acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const bool up = lane & 4;
+      const double send = up ? acc[q] : acc[q + 2];
+      const double keep = up ? acc[q + 2] : acc[q];
+      acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    {
+      const bool up = lane & 2;
+      const double send = up ? acc[0] : acc[1];
+      const double keep = up ? acc[1] : acc[0];
+      acc[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
+    const int vi = c0 + (lane >> 1);
+    if ((lane & 1) == 0 && vi < nd) red[vi][wid] = acc[0];
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nd; i += KB) {
