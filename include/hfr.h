@@ -140,6 +140,20 @@ int hfr_condense(fr_ctx* ctx, int refine);
  * iters / final_rel (host, nullable): iterations and true final relative residual. */
 int hfr_trace_gmres(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* iters, double* final_rel);
 
+/* How hfr_trace_gmres (and imex_stage) run a restart cycle.  FR_GMRES_FUSED (the default where
+ * available): the whole cycle -- preconditioner, mat-vecs, Gram-Schmidt, Givens rotations and the
+ * solution update -- is one cooperative launch with one CTA per SM that meets at grid barriers;
+ * available for trace blocks (nT, n nv) = (64,16), (80,20), (48,12) on devices with cooperative
+ * launch.  Each barrier wait is bounded (about 2 s); a wait that runs out ends the launch and
+ * hfr_trace_gmres returns FR_ERR_TIMEOUT.  FR_GMRES_MULTI: one short kernel per step with the
+ * Krylov state on the device (any shape).  Both compute the same iteration (classical
+ * Gram-Schmidt with a conditional second pass); their results agree to rounding.
+ * set: FR_ERR_UNSUPPORTED if FR_GMRES_FUSED is not available for the context.
+ * get: the mode in effect, -1 for a null context.  This switch has no counterpart in the paper. */
+enum fr_gmres_mode { FR_GMRES_MULTI = 0, FR_GMRES_FUSED = 1 };
+int hfr_gmres_set_mode(fr_ctx* ctx, int mode);
+int hfr_gmres_get_mode(const fr_ctx* ctx);
+
 /* du_k = x_r - X_B du^_k = A_k^{-1}(r_k - B_k du^_k) for every implicit element (du: nimplicit x nA,
  * compact order), followed by `refine` FP64 refinement sweeps against the exact FP64 linearisation. */
 int hfr_backsolve(fr_ctx* ctx, const double* duhat, double* du, int refine);

@@ -29,6 +29,7 @@ LIB_PATH = os.path.join(HERE, "libhfr.so")
 FR_PREC_FP64, FR_PREC_FP32 = 0, 1
 FR_TAB_BE, FR_TAB_SDIRK2 = 0, 1
 FR_PHYS_ADVDIFF, FR_PHYS_NAVIER_STOKES = 0, 1
+FR_GMRES_MULTI, FR_GMRES_FUSED = 0, 1
 EXPORT = {"A": 0, "B": 1, "C": 2, "D": 3, "S": 4, "XB": 5, "xr": 6, "t_k": 7, "r": 8, "s": 9, "t": 10, "Pinv": 11}
 
 # every symbol declared in include/hfr.h
@@ -41,6 +42,8 @@ ABI_SYMBOLS = [
     "hfr_local_jacobian",
     "hfr_condense",
     "hfr_trace_gmres",
+    "hfr_gmres_set_mode",
+    "hfr_gmres_get_mode",
     "hfr_backsolve",
     "hfr_export",
     "imex_stage",
@@ -146,6 +149,8 @@ def load_library(path: str = LIB_PATH):
     lib.hfr_local_jacobian.argtypes = [vp, dp, dp, dp, ctypes.c_double]
     lib.hfr_condense.argtypes = [vp, ctypes.c_int]
     lib.hfr_trace_gmres.argtypes = [vp, dp, ctypes.c_double, ctypes.c_int, ip, ctypes.POINTER(ctypes.c_double)]
+    lib.hfr_gmres_set_mode.argtypes = [vp, ctypes.c_int]
+    lib.hfr_gmres_get_mode.argtypes = [vp]
     lib.hfr_backsolve.argtypes = [vp, dp, dp, ctypes.c_int]
     lib.hfr_export.argtypes = [vp, ctypes.c_int, dp, ctypes.c_size_t]
     lib.imex_stage.argtypes = [vp, ctypes.c_int, ctypes.c_double, dp, dp, dp, dp, ctypes.c_double, ctypes.c_int,
@@ -304,6 +309,12 @@ class Context:
         if check:
             self._check(rc)
         return duh, its.value, rel.value
+
+    def hfr_gmres_set_mode(self, mode: int):
+        self._check(self.lib.hfr_gmres_set_mode(self.h, int(mode)))
+
+    def hfr_gmres_get_mode(self) -> int:
+        return int(self.lib.hfr_gmres_get_mode(self.h))
 
     def hfr_backsolve(self, duhat, refine=0):
         du = self.empty(self.info.nimplicit, self.info.nA)

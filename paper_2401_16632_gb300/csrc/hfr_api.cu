@@ -51,6 +51,9 @@ struct fr_ctx {
   int* status = nullptr;  // [0] bits, [1] first element
   // Krylov
   GmresBuffers gm;
+  int gm_mode = 0;          // 0: multi-kernel cycle, 1: one cooperative launch per cycle
+  int gm_fused_grid = 0;    // CTAs of the cooperative launch (0: not available)
+  unsigned* gm_bar = nullptr;
   double *duhat = nullptr, *du = nullptr, *res_tmp = nullptr, *Ustar = nullptr, *red = nullptr;
   // linearisation point used by the FP64 refinement (context-owned copies for the ABI call,
   // the stage's own buffers inside imex_stage)
@@ -491,7 +494,16 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, const fr_config* cfg, voi
   ctx->gm.n = nh;
   ctx->gm.V = dalloc<double>(ctx, (size_t)(GM_MAXM + 1) * std::max(nh, (size_t)1), &rc);
   ctx->gm.Z = dalloc<double>(ctx, (size_t)GM_MAXM * std::max(nh, (size_t)1), &rc);
-  ctx->gm.partial = dalloc<double>(ctx, (size_t)GM_NBLK * (GM_MAXM + 1), &rc);
+  {
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    ctx->gm_fused_grid = fused_gmres_grid(ctx->prec_bytes, nT, n * nv);
+    ctx->gm_mode = ctx->gm_fused_grid > 0 ? 1 : 0;
+    const size_t np = std::max((size_t)GM_NBLK * (GM_MAXM + 1), fused_partial_doubles(std::max(nsm, 1)));
+    ctx->gm.partial = dalloc<double>(ctx, np, &rc);
+    ctx->gm_bar = dalloc<unsigned>(ctx, 64, &rc);
+  }
   ctx->gm.state = dalloc<GmresState>(ctx, 1, &rc);
   ctx->gm.ticket = dalloc<unsigned int>(ctx, 1, &rc);
   ctx->gm.z32 = ctx->prec_bytes == 4 ? dalloc<float>(ctx, std::max(nh, (size_t)1), &rc) : nullptr;
@@ -809,9 +821,34 @@ static int gmres_impl(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* i
     return FR_OK;
   }
   const int ph = prof_begin(ctx, PH_GMRES);
-  const int grc = run_gmres(ops, ctx->gm, ctx->tg, duhat, rtol, ctx->restart, maxit, 4, &res, ctx->stream);
+  int grc = 0, timed_out = 0;
+  if (ctx->gm_mode == 1) {
+    FusedArgs fa;
+    fa.ntrace = ctx->ntrace;
+    fa.nT = ctx->nT;
+    fa.sides = ctx->sides_c;
+    fa.tr_of_c = ctx->tr_of_c;
+    fa.S = ctx->S;
+    fa.Pinv = ctx->Pinv;
+    fa.t = ctx->tg;
+    fa.x = duhat;
+    fa.V = ctx->gm.V;
+    fa.z = ctx->prec_bytes == 4 ? (void*)ctx->gm.z32 : (void*)ctx->gm.Z;
+    fa.partial = ctx->gm.partial;
+    fa.bar = ctx->gm_bar;
+    fa.st = ctx->gm.state;
+    fa.n = ctx->gm.n;
+    fa.m = ctx->restart;
+    fa.rtol = rtol;
+    fa.x_zero = 1;
+    grc = run_gmres_fused(fa, ctx->prec_bytes, ctx->gm_fused_grid, rtol, ctx->restart, maxit, &res, &timed_out,
+                          ctx->stream);
+  } else {
+    grc = run_gmres(ops, ctx->gm, ctx->tg, duhat, rtol, ctx->restart, maxit, 4, &res, ctx->stream);
+  }
   prof_end(ctx, ph);
   if (grc != 0) return set_err(ctx, FR_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+  if (timed_out) return set_err(ctx, FR_ERR_TIMEOUT, "hfr_trace_gmres: grid barrier wait timed out", -1, res.iterations);
   CK(cudaGetLastError());
   if (iters) *iters = res.iterations;
   if (final_rel) *final_rel = res.rel;
@@ -820,6 +857,17 @@ static int gmres_impl(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* i
     return set_err(ctx, FR_ERR_NOT_CONVERGED, "hfr_trace_gmres: iteration limit", -1, res.iterations, res.rel);
   return FR_OK;
 }
+
+extern "C" int hfr_gmres_set_mode(fr_ctx* ctx, int mode) {
+  if (!ctx || (mode != FR_GMRES_MULTI && mode != FR_GMRES_FUSED))
+    return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_gmres_set_mode: bad argument");
+  if (mode == FR_GMRES_FUSED && ctx->gm_fused_grid <= 0)
+    return set_err(ctx, FR_ERR_UNSUPPORTED, "hfr_gmres_set_mode: no single-launch cycle for this shape or device");
+  ctx->gm_mode = mode;
+  return FR_OK;
+}
+
+extern "C" int hfr_gmres_get_mode(const fr_ctx* ctx) { return ctx ? ctx->gm_mode : -1; }
 
 extern "C" int hfr_trace_gmres(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* iters, double* final_rel) {
   if (!ctx || !duhat || rtol < 0 || maxit < 1) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_trace_gmres: bad argument");

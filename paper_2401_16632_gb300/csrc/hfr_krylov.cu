@@ -270,10 +270,12 @@ int run_gmres(const GmresOps& ops, const GmresBuffers& b, const double* t, doubl
       (hfr::count_launch(), k_sub<<<nb, KB, 0, s>>>(t, b.V, b.V, n));
     }
     first = false;
-    norm_into(b, 0, b.V, n, 3, rtol, m, s);  // beta
+    // this cycle's length: the restart length, capped by the iterations left
+    const int mc = m < maxit - total ? m : maxit - total;
+    norm_into(b, 0, b.V, n, 3, rtol, mc, s);  // beta
     (hfr::count_launch(), k_cycle_start<<<nb, KB, 0, s>>>(st, b.V, n, rtol));
     int j = 0;
-    for (; j < m; ++j) {
+    for (; j < mc; ++j) {
       double* vj = b.V + (size_t)j * n;
       double* w = b.V + (size_t)(j + 1) * n;
       double* zj = b.Z + (size_t)j * n;
@@ -283,14 +285,14 @@ int run_gmres(const GmresOps& ops, const GmresBuffers& b, const double* t, doubl
       // classical Gram-Schmidt with a conditional second pass (DGKS): pass 1 also yields ||w||,
       // since w = V_{j+1} follows V_j in memory
       (hfr::count_launch(), k_cgs<<<nb, KB, 0, s>>>(st, j, b.V, n, j + 1, 0, b.V, j + 2, w, b.partial, b.ticket, 5,
-                                                     rtol, m, 0));
+                                                     rtol, mc, 0));
       (hfr::count_launch(), k_cgs<<<nb, KB, 0, s>>>(st, j, b.V, n, j + 1, 1, w, 1, w, b.partial, b.ticket, 6, rtol,
-                                                     m, 0));
+                                                     mc, 0));
       (hfr::count_launch(), k_cgs<<<nb, KB, 0, s>>>(st, j, b.V, n, j + 1, 0, b.V, j + 1, w, b.partial, b.ticket, 1,
-                                                     rtol, m, 1));
+                                                     rtol, mc, 1));
       (hfr::count_launch(), k_cgs<<<nb, KB, 0, s>>>(st, j, b.V, n, j + 1, 2, w, 1, w, b.partial, b.ticket, 2, rtol,
-                                                     m, 1));
-      if ((j + 1) % check_every == 0 || j + 1 == m) {
+                                                     mc, 1));
+      if ((j + 1) % check_every == 0 || j + 1 == mc) {
         cudaMemcpyAsync(&hs, st, sizeof(GmresHead), cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
         if (hs.kdone >= 0) break;

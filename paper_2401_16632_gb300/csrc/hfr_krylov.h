@@ -56,6 +56,33 @@ struct GmresResult {
   double bnorm;
 };
 
+// One restart cycle per cooperative launch (hfr_gmres_fused.cu): fixed shapes (nT, bs) in
+// {(64,16), (80,20), (48,12)} of either block precision.
+struct FusedArgs {
+  int ntrace, nT;
+  const int* sides;    // ntrace x 4 (e0, f0, e1, f1), compact implicit element ids
+  const int* tr_of_c;  // Eim x 4 trace face of each element face
+  const void* S;       // Eim x nT x nT, block precision
+  const void* Pinv;    // ntrace x bs x bs face-block inverses, block precision
+  const double* t;     // right-hand side
+  double* x;           // solution (zeroed by run_gmres_fused)
+  double* V;           // (GM_MAXM + 1) x n Krylov basis
+  void* z;             // n values of the block precision: the current preconditioned vector
+  double* partial;     // fused_partial_doubles(grid)
+  unsigned* bar;       // 2 words: barrier arrivals, abort flag
+  GmresState* st;
+  size_t n;
+  int m;
+  double rtol;
+  int x_zero;
+};
+size_t fused_partial_doubles(int max_blocks);
+// CTAs of the cooperative launch (one per SM), 0 when the shape or the device does not allow it
+int fused_gmres_grid(int prec_bytes, int nT, int bs);
+// returns 0 (result in res; *timed_out = 1 if a grid barrier wait ran out) or -1 on a CUDA error
+int run_gmres_fused(const FusedArgs& a, int prec_bytes, int grid, double rtol, int restart, int maxit,
+                    GmresResult* res, int* timed_out, cudaStream_t s);
+
 int run_gmres(const GmresOps& ops, const GmresBuffers& b, const double* t, double* x, double rtol, int restart,
               int maxit, int check_every, GmresResult* res, cudaStream_t s);
 

@@ -244,3 +244,53 @@ def test_mixed_precision_stage_matches_fp64(refine):
         out.append(us.cpu().numpy())
     inc = np.abs(out[0] - u0).max()
     assert np.abs(out[1] - out[0]).max() < 1e-8 * inc
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", ["vortex_p2", "vortex_skew_p3", "vortex_p4", "band_ns"])
+def test_gmres_single_launch_and_multi_kernel_cycles_agree(name, precision):
+    """The cooperative single-launch cycle and the multi-kernel cycle run the same iteration:
+    both reach the requested residual on the condensed system and agree with its direct
+    solution (FP64: to the solve's rounding; FP32 S: to what FP32 mat-vecs allow)."""
+    prec = pkg.FR_PREC_FP64 if precision == "fp64" else pkg.FR_PREC_FP32
+    ctx, d, *_ = _blocks_both(name, prec)
+    ctx.hfr_condense(refine=0)
+    assert ctx.hfr_gmres_get_mode() == pkg.FR_GMRES_FUSED
+    S = ctx.hfr_export("S").cpu().numpy().astype(np.float64)
+    t = ctx.hfr_export("t_k").cpu().numpy()
+    duh_ref, _, _ = solve_trace(d, S, t, d.imp_idx, method="direct")
+    rtol, tol = (1e-12, 1e-9) if precision == "fp64" else (1e-5, 2e-3)
+    out, its = {}, {}
+    for mode in (pkg.FR_GMRES_FUSED, pkg.FR_GMRES_MULTI):
+        ctx.hfr_gmres_set_mode(mode)
+        duh, it, rel = ctx.hfr_trace_gmres(rtol=rtol, maxit=3000)
+        assert rel <= 10 * rtol, (mode, rel)
+        out[mode] = duh.cpu().numpy().reshape(-1)
+        its[mode] = it
+        assert _rel(out[mode], duh_ref) < tol, mode
+    assert abs(its[pkg.FR_GMRES_FUSED] - its[pkg.FR_GMRES_MULTI]) <= 1 + its[pkg.FR_GMRES_MULTI] // 10
+    assert _rel(out[pkg.FR_GMRES_FUSED], out[pkg.FR_GMRES_MULTI]) < tol
+
+
+def test_gmres_single_launch_restarts_and_iteration_limit():
+    mesh, u0, phys = CASES["vortex_skew_p3"]()
+    ctx = pkg.Context(mesh, phys, precision=pkg.FR_PREC_FP64, gmres_restart=5)
+    d = Discretisation(mesh, make_physics(phys))
+    uh = _perturbed_trace(d, u0, 1)
+    ctx.hfr_local_jacobian(torch.tensor(u0, device=DEV), torch.tensor(uh, device=DEV),
+                           torch.tensor(u0 * 0.999, device=DEV), 0.037)
+    ctx.hfr_condense(refine=0)
+    S = ctx.hfr_export("S").cpu().numpy()
+    t = ctx.hfr_export("t_k").cpu().numpy()
+    duh_ref, _, _ = solve_trace(d, S, t, d.imp_idx, method="direct")
+    for mode in (pkg.FR_GMRES_FUSED, pkg.FR_GMRES_MULTI):
+        ctx.hfr_gmres_set_mode(mode)
+        duh, its, rel = ctx.hfr_trace_gmres(rtol=1e-12, maxit=5000)
+        assert its > 5 and rel <= 1e-11
+        assert _rel(duh.cpu().numpy().reshape(-1), duh_ref) < 1e-9
+        with pytest.raises(pkg.HfrError) as ei:
+            ctx.hfr_trace_gmres(rtol=1e-12, maxit=7)
+        assert ei.value.code == 4 and ei.value.info.iteration == 7
+    with pytest.raises(pkg.HfrError) as ei:
+        ctx.hfr_gmres_set_mode(7)
+    assert ei.value.code == 1
