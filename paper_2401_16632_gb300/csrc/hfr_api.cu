@@ -807,7 +807,10 @@ static void cb_precond(void* c, const GmresState* st, int j, double* x, double* 
                        j > 0 ? &st->inv_hn : nullptr, y32);
 }
 
-static int gmres_impl(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* iters, double* final_rel) {
+// true_res: report the true final residual ||t - L du^|| / ||t|| (else the GMRES estimate, which
+// the Newton iteration does not need)
+static int gmres_impl(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* iters, double* final_rel,
+                      bool true_res = true) {
   GmresOps ops;
   ops.ctx = ctx;
   ops.matvec = cb_matvec;
@@ -829,6 +832,7 @@ static int gmres_impl(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* i
     fa.sides = ctx->sides_c;
     fa.tr_of_c = ctx->tr_of_c;
     fa.S = ctx->S;
+    fa.S_bytes = (size_t)ctx->Eim * ctx->nT * ctx->nT * ctx->prec_bytes;
     fa.Pinv = ctx->Pinv;
     fa.t = ctx->tg;
     fa.x = duhat;
@@ -841,6 +845,7 @@ static int gmres_impl(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* i
     fa.m = ctx->restart;
     fa.rtol = rtol;
     fa.x_zero = 1;
+    fa.true_res = true_res ? 1 : 0;
     grc = run_gmres_fused(fa, ctx->prec_bytes, ctx->gm_fused_grid, rtol, ctx->restart, maxit, &res, &timed_out,
                           ctx->stream);
   } else {
@@ -1036,7 +1041,7 @@ extern "C" int imex_stage(fr_ctx* ctx, int stage, double dt, const double* u_n, 
     if (rc) return rc;
     int its = 0;
     double rel = 0.0;
-    rc = gmres_impl(ctx, ctx->duhat, gmres_rtol, gmres_maxit, &its, &rel);
+    rc = gmres_impl(ctx, ctx->duhat, gmres_rtol, gmres_maxit, &its, &rel, false);
     gtot += its;
     if (rc && rc != FR_ERR_NOT_CONVERGED) return rc;
     rc = backsolve_impl(ctx, ctx->duhat, ctx->du, refine);

@@ -7,13 +7,29 @@
 // trace faces (and so of every Krylov vector), and the CTAs meet at a grid barrier only where an
 // iteration needs data from other faces or a global sum:
 //   (A) after z = P^{-1} v_j        (the mat-vec gathers z on neighbouring faces)
-//   (B) after w = L z and its dots  (classical Gram-Schmidt coefficients and ||w||)
-//   (C) after w -= V h and its dots (second-pass coefficients and ||w||, for the DGKS test)
-//   (D) only when the second pass runs: after it, for the new norm
+//   (B) after w = L z and its dots  (classical Gram-Schmidt coefficients h = V^T w)
+//   (C) after w' = w - V h and its dots (second-pass coefficients d = V^T w' and ||w'||)
+// Classical Gram-Schmidt is applied twice (CGS2).  The second pass w'' = w' - V d is not a pass
+// of its own: its norm follows from ||w''||^2 = ||w'||^2 - ||d||^2 (V orthonormal), and the
+// subtraction is folded into the pass that normalises v_{j+1} = w'' / ||w''|| before the next
+// preconditioner application.  Only when the second pass removes more than a quarter of
+// ||w'||^2 (severe cancellation) is w'' formed and its norm summed explicitly, at one more
+// barrier.
 // Every CTA reduces the per-CTA partial sums in the same fixed order, so all CTAs hold bitwise
 // identical Hessenberg columns, rotations and convergence decisions and take the same path.
 // The barrier waits are bounded: a wait that outlasts PG_TIMEOUT_NS raises an abort flag that the
 // host reads, and every CTA leaves at its next barrier.
+//
+// Precision: the Krylov basis, its dots and updates use the block precision T (FP32 in the mixed
+// path, where FP64 lanes are 1/64 of the FP32 lanes on this GPU and the GMRES tolerance is loose;
+// FP64 in the FP64 path).  The Hessenberg matrix, the Givens rotations, y, the solution du^ and
+// the right-hand side stay FP64.  The Givens update of column j-1 (one thread per CTA) runs while
+// the other warps finish and precondition v_j, which needs only ||w_j||.
+//
+// Each CTA reads and writes only its own range of the Krylov vectors, so those accesses go
+// through L1; values other CTAs read (z, du^, partial sums) use L2-only loads.  The S blocks,
+// re-read by every mat-vec of a cycle, are loaded with an L2 evict-last policy and returned to
+// the normal policy when the cycle ends.
 #include "hfr_krylov.h"
 
 namespace hfr {
@@ -26,15 +42,20 @@ constexpr int PG_ND = GM_MAXM + 2;  // dots per reduction: j + 2 <= m + 1
 constexpr unsigned long long PG_TIMEOUT_NS = 2000000000ull;
 constexpr unsigned PG_MAX_SPINS = 1u << 26;
 
+template <typename T>
 struct PGShared {
-  double red[PG_ND][PG_WARPS];
+  T red[PG_ND][PG_WARPS];
+  T cf[PG_ND];   // Gram-Schmidt coefficients in the vector precision
+  T yT[GM_MAXM];
+  T invT;        // 1 / ||w_j||: normalises v_j
   double dot[PG_ND];
   double H[(GM_MAXM + 1) * GM_MAXM];
   double hc[GM_MAXM + 2];
   double g[GM_MAXM + 1];
   double cs[GM_MAXM], sn[GM_MAXM], y[GM_MAXM];
-  double beta, bnorm, inv, res, hn, ww;
-  int done, k, conv, nan, ok;
+  double rdi[GM_MAXM];  // 1 / H[j][j]
+  double beta, bnorm, res, hn;
+  int done, k, conv, nan, ok, corr;
 };
 
 __device__ __forceinline__ unsigned long long pg_clock() {
@@ -51,28 +72,30 @@ __device__ __forceinline__ unsigned pg_load_acquire(const unsigned* p) {
 
 // Grid barrier of a cooperative launch (all CTAs resident).  bar[0] counts arrivals over the
 // whole launch (zeroed before it), bar[1] is the abort flag.  Returns false on abort.
-__device__ bool pg_sync(PGShared& sh, unsigned* bar, unsigned& epoch) {
+template <typename T>
+__device__ bool pg_sync(PGShared<T>& sh, unsigned* bar, unsigned& epoch) {
   __syncthreads();
   ++epoch;
   if (threadIdx.x == 0) {
     int ok = 1;
     const unsigned target = epoch * gridDim.x;
-    __threadfence();
-    atomicAdd(bar, 1u);
+    // release: the CTA's writes (ordered before by the CTA barrier) are visible before the arrival
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
     const unsigned long long t0 = pg_clock();
     for (unsigned it = 0; pg_load_acquire(bar) < target; ++it) {
-      if (pg_load_acquire(bar + 1) != 0u) {
-        ok = 0;
-        break;
+      if ((it & 63u) == 63u) {
+        if (pg_load_acquire(bar + 1) != 0u) {
+          ok = 0;
+          break;
+        }
+        if (it >= PG_MAX_SPINS || pg_clock() - t0 > PG_TIMEOUT_NS) {
+          atomicExch(bar + 1, 1u);
+          ok = 0;
+          break;
+        }
       }
-      if (it >= PG_MAX_SPINS || ((it & 63u) == 63u && pg_clock() - t0 > PG_TIMEOUT_NS)) {
-        atomicExch(bar + 1, 1u);
-        ok = 0;
-        break;
-      }
-      __nanosleep(32);
+      __nanosleep(20);
     }
-    __threadfence();
     sh.ok = ok;
   }
   __syncthreads();
@@ -80,75 +103,78 @@ __device__ bool pg_sync(PGShared& sh, unsigned* bar, unsigned& epoch) {
 }
 
 // Warp reduce-scatter of 16 per-lane values: afterwards lane l holds the warp sum of value l >> 1.
-__device__ __forceinline__ double pg_scatter16(double (&acc)[16], int lane) {
+template <typename T>
+__device__ __forceinline__ T pg_scatter16(T (&acc)[16], int lane) {
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const bool up = lane & 16;
-    const double send = up ? acc[q] : acc[q + 8];
-    const double keep = up ? acc[q + 8] : acc[q];
+    const T send = up ? acc[q] : acc[q + 8];
+    const T keep = up ? acc[q + 8] : acc[q];
     acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const bool up = lane & 8;
-    const double send = up ? acc[q] : acc[q + 4];
-    const double keep = up ? acc[q + 4] : acc[q];
+    const T send = up ? acc[q] : acc[q + 4];
+    const T keep = up ? acc[q + 4] : acc[q];
     acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
   }
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     const bool up = lane & 4;
-    const double send = up ? acc[q] : acc[q + 2];
-    const double keep = up ? acc[q + 2] : acc[q];
+    const T send = up ? acc[q] : acc[q + 2];
+    const T keep = up ? acc[q + 2] : acc[q];
     acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
   }
   {
     const bool up = lane & 2;
-    const double send = up ? acc[0] : acc[1];
-    const double keep = up ? acc[1] : acc[0];
+    const T send = up ? acc[0] : acc[1];
+    const T keep = up ? acc[1] : acc[0];
     acc[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
   }
   return acc[0] + __shfl_xor_sync(0xffffffffu, acc[0], 1);
 }
 
-// CTA partial of D_i . w over this CTA's entries [x0, x1), i < nd, D_i = V + i n, written to
+// CTA partial of V_i . w over this CTA's entries [x0, x1), i < nd, written to
 // partial[i * gridDim.x + blockIdx.x].  Each thread visits the entries x0 + tid + PG_THREADS u,
 // the same ones the vector updates of this file give it, so it only re-reads its own writes.
-__device__ void pg_block_dots(PGShared& sh, const double* V, size_t n, int nd, const double* w, size_t x0,
-                              size_t x1, double* partial) {
+template <typename T>
+__device__ void pg_block_dots(PGShared<T>& sh, const T* V, size_t n, int nd, const T* w, size_t x0, size_t x1,
+                              T* partial) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int c0 = 0; c0 < nd; c0 += 16) {
-    double acc[16];
+    T acc[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int q = 0; q < 16; ++q) acc[q] = T(0);
     for (size_t x = x0 + threadIdx.x; x < x1; x += PG_THREADS) {
-      const double wx = __ldcg(w + x);
+      const T wx = w[x];
 #pragma unroll
       for (int q = 0; q < 16; ++q)
-        if (c0 + q < nd) acc[q] += __ldcg(V + (size_t)(c0 + q) * n + x) * wx;
+        if (c0 + q < nd) acc[q] += V[(size_t)(c0 + q) * n + x] * wx;
     }
-    const double s = pg_scatter16(acc, lane);
+    const T s = pg_scatter16(acc, lane);
     const int vi = c0 + (lane >> 1);
     if ((lane & 1) == 0 && vi < nd) sh.red[vi][wid] = s;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nd; i += PG_THREADS) {
-    double t = 0.0;
+    T t = T(0);
 #pragma unroll
     for (int k = 0; k < PG_WARPS; ++k) t += sh.red[i][k];
     partial[(size_t)i * gridDim.x + blockIdx.x] = t;
   }
 }
 
-// CTA partials of ||u||^2 (slot 0) and, if v, ||v||^2 (slot 1)
-__device__ void pg_block_sq(PGShared& sh, const double* u, const double* v, size_t x0, size_t x1, double* partial) {
+// CTA partials of ||u||^2 (slot 0) and, if v, ||v||^2 (slot 1), in the vector precision
+template <typename T, typename U2>
+__device__ void pg_block_sq(PGShared<T>& sh, const T* u, const U2* v, size_t x0, size_t x1, T* partial) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  double su = 0.0, sv = 0.0;
+  T su = T(0), sv = T(0);
   for (size_t x = x0 + threadIdx.x; x < x1; x += PG_THREADS) {
-    const double a = __ldcg(u + x);
+    const T a = u[x];
     su += a * a;
     if (v) {
-      const double b = __ldcg(v + x);
+      const T b = T(__ldcg(v + x));
       sv += b * b;
     }
   }
@@ -163,7 +189,7 @@ __device__ void pg_block_sq(PGShared& sh, const double* u, const double* v, size
   }
   __syncthreads();
   if (threadIdx.x < 2) {
-    double t = 0.0;
+    T t = T(0);
 #pragma unroll
     for (int k = 0; k < PG_WARPS; ++k) t += sh.red[threadIdx.x][k];
     partial[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = t;
@@ -171,26 +197,108 @@ __device__ void pg_block_sq(PGShared& sh, const double* u, const double* v, size
 }
 
 // After the barrier: sh.dot[i] = sum over CTAs of partial slot i, in the same order everywhere.
-__device__ void pg_reduce(PGShared& sh, int nd, const double* partial) {
+template <typename T>
+__device__ void pg_reduce(PGShared<T>& sh, int nd, const T* partial) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nb = (int)gridDim.x;
   for (int i = wid; i < nd; i += PG_WARPS) {
-    double t = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(partial + (size_t)i * gridDim.x + b);
+    const T* pi = partial + (size_t)i * nb;
+    T t = T(0);
+    for (int b0 = 0; b0 < nb; b0 += 32 * 8) {
+      T v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int b = b0 + lane + 32 * q;
+        v[q] = b < nb ? __ldcg(pi + b) : T(0);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) t += v[q];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) sh.dot[i] = t;
+    if (lane == 0) sh.dot[i] = double(t);
   }
   __syncthreads();
 }
 
+// Vector loads of VW consecutive values.  The S blocks are read with an L2 evict-last policy so
+// that they stay resident in L2 across the iterations of a cycle (they are the largest operand and
+// are re-read by every mat-vec); everything else uses the default policy.
+template <typename T, int VW>
+struct PGVec {
+  T v[VW];
+};
+
+__device__ __forceinline__ unsigned long long pg_policy_keep() {
+  unsigned long long p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+template <typename T, int VW>
+__device__ __forceinline__ PGVec<T, VW> pg_ld_keep(const T* ptr, unsigned long long pol) {
+  PGVec<T, VW> r;
+  if constexpr (sizeof(T) == 4 && VW == 4) {
+    asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3])
+        : "l"(ptr), "l"(pol));
+  } else if constexpr (sizeof(T) == 4 && VW == 2) {
+    asm("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(r.v[0]), "=f"(r.v[1]) : "l"(ptr), "l"(pol));
+  } else if constexpr (sizeof(T) == 8 && VW == 2) {
+    asm("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(r.v[0]), "=d"(r.v[1]) : "l"(ptr), "l"(pol));
+  } else {
+#pragma unroll
+    for (int q = 0; q < VW; ++q) r.v[q] = __ldg(ptr + q);
+  }
+  return r;
+}
+
+template <typename T, int VW>
+__device__ __forceinline__ PGVec<T, VW> pg_ld_cg(const T* ptr) {
+  PGVec<T, VW> r;
+  if constexpr (sizeof(T) == 4 && VW == 4) {
+    const float4 q = __ldcg(reinterpret_cast<const float4*>(ptr));
+    r.v[0] = q.x;
+    r.v[1] = q.y;
+    r.v[2] = q.z;
+    r.v[3] = q.w;
+  } else if constexpr (sizeof(T) == 4 && VW == 2) {
+    const float2 q = __ldcg(reinterpret_cast<const float2*>(ptr));
+    r.v[0] = q.x;
+    r.v[1] = q.y;
+  } else if constexpr (sizeof(T) == 8 && VW == 2) {
+    const double2 q = __ldcg(reinterpret_cast<const double2*>(ptr));
+    r.v[0] = q.x;
+    r.v[1] = q.y;
+  } else {
+#pragma unroll
+    for (int q = 0; q < VW; ++q) r.v[q] = __ldcg(ptr + q);
+  }
+  return r;
+}
+
+// widest vector (16 bytes at most) that divides both the per-lane column count and the face block
+template <typename T, int NT, int BS>
+struct PGShape {
+  static constexpr int CT = NT / 8;  // columns per lane
+  static constexpr int VMAX = 16 / (int)sizeof(T);
+  static constexpr int VW = (CT % 4 == 0 && BS % 4 == 0 && VMAX >= 4) ? 4 : ((CT % 2 == 0 && BS % 2 == 0) ? 2 : 1);
+  static constexpr int CV = CT / VW;  // vectors per lane and row
+  static constexpr int RU = (BS + 3) / 4;
+  static_assert(NT % 8 == 0, "nT must be a multiple of 8");
+};
+
 // Rows grp + 4u of (L s)_f for trace face f, in every lane of 8-lane group grp: both neighbours'
 // row blocks of S_k against the neighbours' gathered trace values (src in the block precision T,
-// or FP64 when SRC_D).  Lanes of a group read consecutive columns of a row.
+// or FP64 when SRC_D).  Lane g8 of a group holds the columns VW (g8 + 8 c) + q of each row, so
+// every load is a VW-wide vector and no vector crosses a face block.
 template <typename T, int NT, int BS, bool SRC_D>
-__device__ __forceinline__ void pg_face_rows(const FusedArgs& a, int f, const void* src, T (&acc)[(BS + 3) / 4]) {
-  constexpr int CT = (NT + 7) / 8, RU = (BS + 3) / 4;
+__device__ __forceinline__ void pg_face_rows(const FusedArgs& a, int f, const void* src, unsigned long long pol,
+                                             T (&acc)[(BS + 3) / 4]) {
+  using Sh = PGShape<T, NT, BS>;
+  constexpr int VW = Sh::VW, CV = Sh::CV, RU = Sh::RU;
   // both sides' rows in flight at once when they fit in registers
-  constexpr bool BOTH = 2 * RU * CT * (int)sizeof(T) <= 256;
+  constexpr bool BOTH = 2 * RU * CV * VW * (int)sizeof(T) <= 256;
   const int lane = threadIdx.x & 31;
   const int grp = lane >> 3, g8 = lane & 7;
   const T* S = reinterpret_cast<const T*>(a.S);
@@ -201,38 +309,43 @@ __device__ __forceinline__ void pg_face_rows(const FusedArgs& a, int f, const vo
     const int e = __ldg(a.sides + f * 4 + side * 2);
     if (e < 0) continue;
     const int fs = __ldg(a.sides + f * 4 + side * 2 + 1);
-    T sv[RU][CT];
+    PGVec<T, VW> sv[RU][CV];
 #pragma unroll
     for (int u = 0; u < RU; ++u) {
       const int i = grp + 4 * u;
-      const bool ok = i < BS;
-      const T* row = S + ((size_t)e * NT + (size_t)fs * BS + (ok ? i : 0)) * NT;
+      const int ii = i < BS ? i : 0;
+      const T* row = S + ((size_t)e * NT + (size_t)fs * BS + ii) * NT;
 #pragma unroll
-      for (int c = 0; c < CT; ++c) {
-        const int l = g8 + 8 * c;
-        sv[u][c] = (ok && l < NT) ? __ldg(row + l) : T(0);
-      }
+      for (int c = 0; c < CV; ++c) sv[u][c] = pg_ld_keep<T, VW>(row + VW * (g8 + 8 * c), pol);
     }
-    T xv[CT];
+    PGVec<T, VW> xv[CV];
 #pragma unroll
-    for (int c = 0; c < CT; ++c) {
-      const int l = g8 + 8 * c;
-      T v = T(0);
-      if (l < NT) {
-        const int fp = l / BS;
-        const int tf = __ldg(a.tr_of_c + e * 4 + fp);
-        if (tf >= 0) {
-          const size_t ix = (size_t)tf * BS + (l - fp * BS);
-          v = SRC_D ? T(__ldcg(reinterpret_cast<const double*>(src) + ix))
-                    : __ldcg(reinterpret_cast<const T*>(src) + ix);
+    for (int c = 0; c < CV; ++c) {
+      const int l = VW * (g8 + 8 * c);
+      const int fp = l / BS;
+      const int tf = __ldg(a.tr_of_c + e * 4 + fp);
+      const size_t ix = (size_t)(tf >= 0 ? tf : 0) * BS + (l - fp * BS);
+      if (SRC_D) {
+        const PGVec<double, VW> d = pg_ld_cg<double, VW>(reinterpret_cast<const double*>(src) + ix);
+#pragma unroll
+        for (int q = 0; q < VW; ++q) xv[c].v[q] = tf >= 0 ? T(d.v[q]) : T(0);
+      } else {
+        xv[c] = pg_ld_cg<T, VW>(reinterpret_cast<const T*>(src) + ix);
+        if (tf < 0) {
+#pragma unroll
+          for (int q = 0; q < VW; ++q) xv[c].v[q] = T(0);
         }
       }
-      xv[c] = v;
     }
 #pragma unroll
-    for (int u = 0; u < RU; ++u)
+    for (int u = 0; u < RU; ++u) {
+      if (grp + 4 * u < BS) {
 #pragma unroll
-      for (int c = 0; c < CT; ++c) acc[u] += sv[u][c] * xv[c];
+        for (int c = 0; c < CV; ++c)
+#pragma unroll
+          for (int q = 0; q < VW; ++q) acc[u] += sv[u][c].v[q] * xv[c].v[q];
+      }
+    }
   }
 #pragma unroll
   for (int u = 0; u < RU; ++u) {
@@ -242,29 +355,31 @@ __device__ __forceinline__ void pg_face_rows(const FusedArgs& a, int f, const vo
   }
 }
 
-// out_f = t_f - (L src)_f when RES, else (L src)_f, for this CTA's faces (one warp per face)
+// out_f = t_f - (L src)_f when RES, else (L src)_f, for this CTA's faces (one warp per face),
+// stored in the vector precision T
 template <typename T, int NT, int BS, bool SRC_D, bool RES>
-__device__ void pg_matvec(const FusedArgs& a, const void* src, double* out, int fb0, int fb1) {
+__device__ void pg_matvec(const FusedArgs& a, const void* src, T* out, int fb0, int fb1) {
   constexpr int RU = (BS + 3) / 4;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int grp = lane >> 3, g8 = lane & 7;
+  const unsigned long long pol = pg_policy_keep();
   for (int f = fb0 + wid; f < fb1; f += PG_WARPS) {
     T acc[RU];
-    pg_face_rows<T, NT, BS, SRC_D>(a, f, src, acc);
+    pg_face_rows<T, NT, BS, SRC_D>(a, f, src, pol, acc);
     if (g8 == 0) {
 #pragma unroll
       for (int u = 0; u < RU; ++u) {
         const int i = grp + 4 * u;
         if (i < BS) {
           const size_t ix = (size_t)f * BS + i;
-          out[ix] = RES ? __ldcg(a.t + ix) - double(acc[u]) : double(acc[u]);
+          out[ix] = RES ? T(__ldcg(a.t + ix) - double(acc[u])) : acc[u];
         }
       }
     }
   }
 }
 
-// Row r of the face block P_f^{-1} (block precision) into registers, lanes r < BS
+// Row r of the face block P_f^{-1} (block precision) into registers
 template <typename T, int BS>
 __device__ __forceinline__ void pg_prow(const T* P, int f, int r, T (&row)[BS]) {
   const T* src = P + ((size_t)f * BS + r) * BS;
@@ -283,61 +398,95 @@ __device__ __forceinline__ void pg_prow(const T* P, int f, int r, T (&row)[BS]) 
   }
 }
 
-// v_j <- v_j * inv (in place, when scale) and z = P^{-1} v_j in the block precision, one warp per
-// face of this CTA, lane r < BS owns row r
+// z = P^{-1} v_j, one warp per face of this CTA, lane r < BS owns row r.  Warp 0 takes no face:
+// its lane 0 updates the Givens rotations meanwhile.
 template <typename T, int BS>
-__device__ void pg_precond(const FusedArgs& a, double* vj, double inv, bool scale, int fb0, int fb1) {
+__device__ void pg_precond(const FusedArgs& a, const T* vj, int fb0, int fb1) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (wid == 0) return;
   const T* P = reinterpret_cast<const T*>(a.Pinv);
   T* z = reinterpret_cast<T*>(a.z);
   const int r = lane < BS ? lane : 0;
-  for (int f = fb0 + wid; f < fb1; f += PG_WARPS) {
+  for (int f = fb0 + wid - 1; f < fb1; f += PG_WARPS - 1) {
     const size_t ix = (size_t)f * BS + r;
-    double v = 0.0;
-    if (lane < BS) {
-      v = __ldcg(vj + ix);
-      if (scale) {
-        v *= inv;
-        vj[ix] = v;
-      }
-    }
+    const T v = lane < BS ? vj[ix] : T(0);
     T row[BS];
     pg_prow<T, BS>(P, f, r, row);
-    const T vt = T(v);
     T acc = T(0);
 #pragma unroll
-    for (int c = 0; c < BS; ++c) acc += row[c] * __shfl_sync(0xffffffffu, vt, c);
+    for (int c = 0; c < BS; ++c) acc += row[c] * __shfl_sync(0xffffffffu, v, c);
     if (lane < BS) z[ix] = acc;
   }
 }
 
-// x_f += P_f^{-1} (sum_{i<k} y_i V_i)_f in FP64 arithmetic, one warp per face
+// v_j <- (v_j - sum_{i<jc} c_i V_i) * inv over this CTA's entries, by warps 1.. only (jc = 0: scale)
+template <typename T>
+__device__ void pg_finish(const T* V, size_t n, const T* c, int jc, T inv, T* vj, size_t x0, size_t x1) {
+  if (threadIdx.x < 32) return;
+  for (size_t x = x0 + threadIdx.x - 32; x < x1; x += PG_THREADS - 32) {
+    T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+    int i = 0;
+    for (; i + 4 <= jc; i += 4) {
+      s0 += c[i] * V[(size_t)i * n + x];
+      s1 += c[i + 1] * V[(size_t)(i + 1) * n + x];
+      s2 += c[i + 2] * V[(size_t)(i + 2) * n + x];
+      s3 += c[i + 3] * V[(size_t)(i + 3) * n + x];
+    }
+    for (; i < jc; ++i) s0 += c[i] * V[(size_t)i * n + x];
+    vj[x] = (vj[x] - ((s0 + s1) + (s2 + s3))) * inv;
+  }
+}
+
+// named barrier of warps 1 .. PG_WARPS-1 (warp 0 is busy with the Givens update)
+__device__ __forceinline__ void pg_sync_workers() {
+  asm volatile("bar.sync 1, %0;" ::"n"(PG_THREADS - 32) : "memory");
+}
+
+// x_f += P_f^{-1} (sum_{i<k} y_i V_i)_f, one warp per face (vector precision, added to FP64 x)
 template <typename T, int BS>
-__device__ void pg_update_x(const FusedArgs& a, const PGShared& sh, int k, int fb0, int fb1) {
+__device__ void pg_update_x(const FusedArgs& a, const PGShared<T>& sh, const T* V, int k, int fb0, int fb1) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const T* P = reinterpret_cast<const T*>(a.Pinv);
   const int r = lane < BS ? lane : 0;
   for (int f = fb0 + wid; f < fb1; f += PG_WARPS) {
     const size_t ix = (size_t)f * BS + r;
-    double u0 = 0.0, u1 = 0.0;
+    T u0 = T(0), u1 = T(0);
     int i = 0;
     for (; i + 1 < k; i += 2) {
-      u0 += sh.y[i] * __ldcg(a.V + (size_t)i * a.n + ix);
-      u1 += sh.y[i + 1] * __ldcg(a.V + (size_t)(i + 1) * a.n + ix);
+      u0 += sh.yT[i] * V[(size_t)i * a.n + ix];
+      u1 += sh.yT[i + 1] * V[(size_t)(i + 1) * a.n + ix];
     }
-    if (i < k) u0 += sh.y[i] * __ldcg(a.V + (size_t)i * a.n + ix);
-    const double u = lane < BS ? u0 + u1 : 0.0;
+    if (i < k) u0 += sh.yT[i] * V[(size_t)i * a.n + ix];
+    const T u = lane < BS ? u0 + u1 : T(0);
     T row[BS];
     pg_prow<T, BS>(P, f, r, row);
-    double acc = 0.0;
+    T acc = T(0);
 #pragma unroll
-    for (int c = 0; c < BS; ++c) acc += double(row[c]) * __shfl_sync(0xffffffffu, u, c);
-    if (lane < BS) a.x[ix] += acc;
+    for (int c = 0; c < BS; ++c) acc += row[c] * __shfl_sync(0xffffffffu, u, c);
+    if (lane < BS) a.x[ix] += double(acc);
   }
 }
 
-// Givens update of Hessenberg column j (sh.hc[0..j+1]); decides the end of the cycle
-__device__ void pg_givens(PGShared& sh, int j, double rtol, int m) {
+// w -= sum_{i<=j} c_i V_i over this thread's entries (c in the vector precision)
+template <typename T>
+__device__ __forceinline__ void pg_subtract(const T* V, size_t n, const T* c, int j, T* w, size_t x0, size_t x1) {
+  for (size_t x = x0 + threadIdx.x; x < x1; x += PG_THREADS) {
+    T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+    int i = 0;
+    for (; i + 3 <= j; i += 4) {
+      s0 += c[i] * V[(size_t)i * n + x];
+      s1 += c[i + 1] * V[(size_t)(i + 1) * n + x];
+      s2 += c[i + 2] * V[(size_t)(i + 2) * n + x];
+      s3 += c[i + 3] * V[(size_t)(i + 3) * n + x];
+    }
+    for (; i <= j; ++i) s0 += c[i] * V[(size_t)i * n + x];
+    w[x] = w[x] - ((s0 + s1) + (s2 + s3));
+  }
+}
+
+// Givens update of Hessenberg column j (sh.hc[0..j+1]), FP64; decides the end of the cycle
+template <typename T>
+__device__ void pg_givens(PGShared<T>& sh, int j, double rtol, int m) {
   double* h = sh.hc;
   for (int i = 0; i < j; ++i) {
     const double a = h[i], b = h[i + 1];
@@ -346,15 +495,16 @@ __device__ void pg_givens(PGShared& sh, int j, double rtol, int m) {
   }
   const double a = h[j], b = h[j + 1];
   sh.hn = b;
-  sh.inv = b != 0.0 ? 1.0 / b : 0.0;
   const double r = sqrt(a * a + b * b);
+  const double ri = r > 0.0 ? 1.0 / r : 0.0;
   double c = 1.0, s = 0.0;
   if (r > 0.0) {
-    c = a / r;
-    s = b / r;
+    c = a * ri;
+    s = b * ri;
   }
   sh.cs[j] = c;
   sh.sn[j] = s;
+  sh.rdi[j] = ri;
   h[j] = r;
   for (int i = 0; i <= j; ++i) sh.H[i * GM_MAXM + j] = h[i];
   sh.g[j + 1] = -s * sh.g[j];
@@ -375,7 +525,7 @@ __device__ void pg_givens(PGShared& sh, int j, double rtol, int m) {
 template <typename T, int NT, int BS>
 __global__ void __launch_bounds__(PG_THREADS, 1) k_gmres_cycle(const __grid_constant__ FusedArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  PGShared& sh = *reinterpret_cast<PGShared*>(smem_raw);
+  PGShared<T>& sh = *reinterpret_cast<PGShared<T>*>(smem_raw);
   const int F = a.ntrace;
   const int fb0 = (int)((long long)blockIdx.x * F / gridDim.x);
   const int fb1 = (int)((long long)(blockIdx.x + 1) * F / gridDim.x);
@@ -384,18 +534,19 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_gmres_cycle(const __grid_cons
   unsigned epoch = 0;
   int par = 0;
   const size_t pstride = (size_t)PG_ND * gridDim.x;
-  double* V = a.V;
+  T* V = reinterpret_cast<T*>(a.V);
+  T* const partial = reinterpret_cast<T*>(a.partial);
 
   // r0 = t - L x into V_0 (x = 0: r0 = t); beta = ||r0||, bnorm = ||t||
   if (a.x_zero) {
-    for (size_t x = x0 + tid; x < x1; x += PG_THREADS) V[x] = __ldcg(a.t + x);
+    for (size_t x = x0 + tid; x < x1; x += PG_THREADS) V[x] = T(__ldcg(a.t + x));
   } else {
     pg_matvec<T, NT, BS, true, true>(a, a.x, V, fb0, fb1);
   }
   __syncthreads();
-  pg_block_sq(sh, V, a.t, x0, x1, a.partial + par * pstride);
+  pg_block_sq(sh, V, a.t, x0, x1, partial + par * pstride);
   if (!pg_sync(sh, a.bar, epoch)) return;
-  pg_reduce(sh, 2, a.partial + par * pstride);
+  pg_reduce(sh, 2, partial + par * pstride);
   par ^= 1;
   if (tid == 0) {
     const double beta = sqrt(sh.dot[0]);
@@ -403,11 +554,13 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_gmres_cycle(const __grid_cons
     sh.bnorm = sqrt(sh.dot[1]);
     sh.g[0] = beta;
     sh.res = beta;
+    sh.hn = beta;
     sh.k = 0;
     sh.conv = 0;
     sh.nan = 0;
     sh.done = 0;
-    sh.inv = beta > 0.0 ? 1.0 / beta : 0.0;
+    sh.corr = 0;
+    sh.invT = T(beta > 0.0 ? 1.0 / beta : 0.0);
     if (!(beta == beta)) {
       sh.nan = 1;
       sh.done = 1;
@@ -418,73 +571,71 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_gmres_cycle(const __grid_cons
   }
   __syncthreads();
 
-  for (int j = 0; j < a.m && !sh.done; ++j) {
-    double* vj = V + (size_t)j * n;
-    double* w = V + (size_t)(j + 1) * n;
-    // (A) v_j = w_j / h_{j,j-1} (in place), z = P^{-1} v_j
-    pg_precond<T, BS>(a, vj, sh.inv, true, fb0, fb1);
-    if (!pg_sync(sh, a.bar, epoch)) return;
-    // (B) w = L z and its dots with V_0 .. V_j and itself
-    pg_matvec<T, NT, BS, false, false>(a, a.z, w, fb0, fb1);
-    __syncthreads();
-    double* part = a.partial + par * pstride;
-    pg_block_dots(sh, V, n, j + 2, w, x0, x1, part);
-    if (!pg_sync(sh, a.bar, epoch)) return;
-    pg_reduce(sh, j + 2, part);
-    par ^= 1;
-    for (int i = tid; i <= j + 1; i += PG_THREADS) {
-      if (i <= j)
-        sh.hc[i] = sh.dot[i];
-      else
-        sh.ww = sh.dot[i];
-    }
-    __syncthreads();
-    // (C) first Gram-Schmidt pass, then the dots of its result (second-pass coefficients, norm)
-    for (size_t x = x0 + tid; x < x1; x += PG_THREADS) {
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      int i = 0;
-      for (; i + 3 <= j; i += 4) {
-        s0 += sh.hc[i] * __ldcg(V + (size_t)i * n + x);
-        s1 += sh.hc[i + 1] * __ldcg(V + (size_t)(i + 1) * n + x);
-        s2 += sh.hc[i + 2] * __ldcg(V + (size_t)(i + 2) * n + x);
-        s3 += sh.hc[i + 3] * __ldcg(V + (size_t)(i + 3) * n + x);
+  if (!sh.done) {
+    for (int j = 0;; ++j) {
+      T* vj = V + (size_t)j * n;
+      T* w = V + (size_t)(j + 1) * n;
+      // (A) lane 0 of warp 0: Givens rotation of column j-1.  Warps 1..: finish v_j (deferred
+      // second Gram-Schmidt pass, normalisation) and form z = P^{-1} v_j.
+      if (j > 0 && tid == 0) pg_givens(sh, j - 1, a.rtol, a.m);
+      if (tid >= 32) {
+        pg_finish(V, n, sh.cf, sh.corr ? j : 0, sh.invT, vj, x0, x1);
+        pg_sync_workers();
+        pg_precond<T, BS>(a, vj, fb0, fb1);
       }
-      for (; i <= j; ++i) s0 += sh.hc[i] * __ldcg(V + (size_t)i * n + x);
-      w[x] = __ldcg(w + x) - ((s0 + s1) + (s2 + s3));
-    }
-    part = a.partial + par * pstride;
-    pg_block_dots(sh, V, n, j + 2, w, x0, x1, part);
-    if (!pg_sync(sh, a.bar, epoch)) return;
-    pg_reduce(sh, j + 2, part);
-    par ^= 1;
-    // DGKS: a second pass only when the first removed most of w (same decision in every CTA)
-    if (sh.dot[j + 1] < 0.5 * sh.ww) {
-      // (D) w -= V d, h += d, new norm
-      for (size_t x = x0 + tid; x < x1; x += PG_THREADS) {
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        int i = 0;
-        for (; i + 3 <= j; i += 4) {
-          s0 += sh.dot[i] * __ldcg(V + (size_t)i * n + x);
-          s1 += sh.dot[i + 1] * __ldcg(V + (size_t)(i + 1) * n + x);
-          s2 += sh.dot[i + 2] * __ldcg(V + (size_t)(i + 2) * n + x);
-          s3 += sh.dot[i + 3] * __ldcg(V + (size_t)(i + 3) * n + x);
-        }
-        for (; i <= j; ++i) s0 += sh.dot[i] * __ldcg(V + (size_t)i * n + x);
-        w[x] = __ldcg(w + x) - ((s0 + s1) + (s2 + s3));
-      }
-      for (int i = tid; i <= j; i += PG_THREADS) sh.hc[i] += sh.dot[i];
-      part = a.partial + par * pstride;
-      pg_block_sq(sh, w, nullptr, x0, x1, part);
       if (!pg_sync(sh, a.bar, epoch)) return;
-      pg_reduce(sh, 1, part);
+      if (sh.done) break;
+      // (B) w = L z and h = V^T w
+      pg_matvec<T, NT, BS, false, false>(a, a.z, w, fb0, fb1);
+      __syncthreads();
+      T* part = partial + par * pstride;
+      pg_block_dots(sh, V, n, j + 1, w, x0, x1, part);
+      if (!pg_sync(sh, a.bar, epoch)) return;
+      pg_reduce(sh, j + 1, part);
       par ^= 1;
-      if (tid == 0) sh.hc[j + 1] = sqrt(sh.dot[0]);
-    } else if (tid == 0) {
-      sh.hc[j + 1] = sqrt(sh.dot[j + 1]);
+      for (int i = tid; i <= j; i += PG_THREADS) {
+        sh.hc[i] = sh.dot[i];
+        sh.cf[i] = T(sh.dot[i]);
+      }
+      __syncthreads();
+      // (C) w' = w - V h, then d = V^T w' and ||w'||^2 (dot j+1: V_{j+1} is w' itself)
+      pg_subtract(V, n, sh.cf, j, w, x0, x1);
+      part = partial + par * pstride;
+      pg_block_dots(sh, V, n, j + 2, w, x0, x1, part);
+      if (!pg_sync(sh, a.bar, epoch)) return;
+      pg_reduce(sh, j + 2, part);
+      par ^= 1;
+      if (tid < 32) {
+        // ||d||^2 (fixed order), h += d, coefficients of the deferred pass
+        double dd = 0.0;
+        for (int i = tid; i <= j; i += 32) {
+          const double d = sh.dot[i];
+          dd += d * d;
+          sh.hc[i] += d;
+          sh.cf[i] = T(d);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dd += __shfl_xor_sync(0xffffffffu, dd, o);
+        if (tid == 0) {
+          const double n1 = sh.dot[j + 1];
+          sh.corr = dd <= 0.25 * n1 ? 1 : 0;
+          if (sh.corr) sh.hc[j + 1] = sqrt(n1 - dd);
+        }
+      }
+      __syncthreads();
+      if (!sh.corr) {
+        // severe cancellation: form w'' = w' - V d now and sum its norm
+        pg_subtract(V, n, sh.cf, j, w, x0, x1);
+        part = partial + par * pstride;
+        pg_block_sq(sh, w, (const T*)nullptr, x0, x1, part);
+        if (!pg_sync(sh, a.bar, epoch)) return;
+        pg_reduce(sh, 1, part);
+        par ^= 1;
+        if (tid == 0) sh.hc[j + 1] = sqrt(sh.dot[0]);
+      }
+      if (tid == 0) sh.invT = T(sh.hc[j + 1] != 0.0 ? 1.0 / sh.hc[j + 1] : 0.0);
+      __syncthreads();
     }
-    __syncthreads();
-    if (tid == 0) pg_givens(sh, j, a.rtol, a.m);
-    __syncthreads();
   }
 
   // y = H^{-1} g, x += P^{-1} V y
@@ -493,22 +644,29 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_gmres_cycle(const __grid_cons
     for (int i = k - 1; i >= 0; --i) {
       double s = sh.g[i];
       for (int c = i + 1; c < k; ++c) s -= sh.H[i * GM_MAXM + c] * sh.y[c];
-      const double d = sh.H[i * GM_MAXM + i];
-      sh.y[i] = d != 0.0 ? s / d : 0.0;
+      sh.y[i] = s * sh.rdi[i];
+      sh.yT[i] = T(sh.y[i]);
     }
   }
   __syncthreads();
-  if (k > 0) pg_update_x<T, BS>(a, sh, k, fb0, fb1);
-  if (!pg_sync(sh, a.bar, epoch)) return;
-  // true residual ||t - L x|| (V_0 as scratch)
-  pg_matvec<T, NT, BS, true, true>(a, a.x, V, fb0, fb1);
-  __syncthreads();
-  pg_block_sq(sh, V, nullptr, x0, x1, a.partial + par * pstride);
-  if (!pg_sync(sh, a.bar, epoch)) return;
-  pg_reduce(sh, 1, a.partial + par * pstride);
+  if (k > 0) pg_update_x<T, BS>(a, sh, V, k, fb0, fb1);
+  if (a.true_res) {
+    // true residual ||t - L x|| (V_0 as scratch)
+    if (!pg_sync(sh, a.bar, epoch)) return;
+    pg_matvec<T, NT, BS, true, true>(a, a.x, V, fb0, fb1);
+    __syncthreads();
+    pg_block_sq(sh, V, (const T*)nullptr, x0, x1, partial + par * pstride);
+    if (!pg_sync(sh, a.bar, epoch)) return;
+    pg_reduce(sh, 1, partial + par * pstride);
+  }
+  // the S blocks go back to the normal L2 eviction policy (the next condensation rewrites them)
+  for (size_t off = ((size_t)blockIdx.x * PG_THREADS + tid) * 128; off < a.S_bytes;
+       off += (size_t)gridDim.x * PG_THREADS * 128)
+    asm volatile("applypriority.global.L2::evict_normal [%0], 128;" ::"l"(reinterpret_cast<const char*>(a.S) + off)
+                 : "memory");
   if (blockIdx.x == 0 && tid == 0) {
     GmresState* st = a.st;
-    st->beta = sqrt(sh.dot[0]);
+    st->beta = a.true_res ? sqrt(sh.dot[0]) : sh.res;
     st->bnorm = sh.bnorm;
     st->res = sh.res;
     st->hn = sh.hn;
@@ -521,7 +679,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_gmres_cycle(const __grid_cons
 
 template <typename T, int NT, int BS>
 cudaError_t launch_cycle(const FusedArgs& a, int grid, cudaStream_t s) {
-  const size_t smem = sizeof(PGShared);
+  const size_t smem = sizeof(PGShared<T>);
   cudaError_t e = cudaFuncSetAttribute(k_gmres_cycle<T, NT, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   void* args[] = {const_cast<FusedArgs*>(&a)};
@@ -533,7 +691,7 @@ cudaError_t launch_cycle(const FusedArgs& a, int grid, cudaStream_t s) {
 template <typename T, int NT, int BS>
 int occupancy_of() {
   int nb = 0;
-  const size_t smem = sizeof(PGShared);
+  const size_t smem = sizeof(PGShared<T>);
   if (cudaFuncSetAttribute(k_gmres_cycle<T, NT, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 0;
@@ -566,7 +724,7 @@ CycleFn pick(int prec_bytes, int nT, int bs, int* occ) {
 
 }  // namespace
 
-size_t fused_partial_doubles(int max_blocks) { return (size_t)2 * PG_ND * (size_t)max_blocks; }
+size_t fused_partial_doubles(int max_blocks) { return (size_t)2 * PG_ND * (size_t)max_blocks; }  // >= T slots
 
 int fused_gmres_grid(int prec_bytes, int nT, int bs) {
   int dev = 0, coop = 0, nsm = 0, occ = 0;

@@ -63,6 +63,7 @@ struct FusedArgs {
   const int* sides;    // ntrace x 4 (e0, f0, e1, f1), compact implicit element ids
   const int* tr_of_c;  // Eim x 4 trace face of each element face
   const void* S;       // Eim x nT x nT, block precision
+  size_t S_bytes;      // size of S
   const void* Pinv;    // ntrace x bs x bs face-block inverses, block precision
   const double* t;     // right-hand side
   double* x;           // solution (zeroed by run_gmres_fused)
@@ -75,6 +76,7 @@ struct FusedArgs {
   int m;
   double rtol;
   int x_zero;
+  int true_res;  // 1: compute ||t - L x|| after the cycle (else the estimate is reported)
 };
 size_t fused_partial_doubles(int max_blocks);
 // CTAs of the cooperative launch (one per SM), 0 when the shape or the device does not allow it
