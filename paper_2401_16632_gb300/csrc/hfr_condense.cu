@@ -837,6 +837,144 @@ __global__ void __launch_bounds__(InvShape<NA>::THREADS, NA <= 64 ? 8 : 3) k_inv
   }
 }
 
+// One warp per element: lane quad q (q < 8) holds rows RPT q .. RPT q + RPT-1, lane h of the quad
+// columns QW h .. QW h + QW-1 of the cycled row.  The argmax, the pivot broadcast and the shift
+// stay inside the warp (no CTA barrier); each pivot-row value read from shared memory feeds RPT
+// FMAs.  WPB elements (warps) per CTA share nothing but the CTA.
+template <int NA>
+struct InvWShape {
+  static constexpr int RPT = (NA + 7) / 8;  // rows per lane
+  static constexpr int QW = (NA + 3) / 4;   // columns per lane
+  static constexpr int NCP = 4 * QW;
+  static constexpr int WPB = 4;             // elements per CTA
+};
+
+template <int NA>
+__global__ void __launch_bounds__(32 * InvWShape<NA>::WPB) k_inverse_warp(const __grid_constant__ CondArgs a) {
+  using Sh = InvWShape<NA>;
+  constexpr int RPT = Sh::RPT, QW = Sh::QW, NCP = Sh::NCP, WPB = Sh::WPB;
+  __shared__ __align__(16) float s_pr[WPB][NCP + 4];
+  __shared__ float s_pinv[WPB];
+  __shared__ int s_step[WPB][NA];
+  __shared__ float s_piv[WPB][NA];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int k = blockIdx.x * WPB + w;
+  if (k >= a.Eim) return;  // whole warps leave; no CTA barrier follows
+  const int q = lane >> 2, h = lane & 3;
+  float* pr = s_pr[w];
+  const float* gA = reinterpret_cast<const float*>(a.A) + (size_t)k * NA * NA;
+  float m[RPT][QW];
+#pragma unroll
+  for (int s = 0; s < RPT; ++s) {
+    const int r = RPT * q + s;
+#pragma unroll
+    for (int j = 0; j < QW; ++j) {
+      const int J = QW * h + j;
+      m[s][j] = (r < NA && J < NA) ? __ldg(gA + (size_t)r * NA + J) : 0.f;
+    }
+  }
+  if (lane < 4) pr[NCP + lane] = 0.f;
+  unsigned used = 0u;  // lane h == 0: bit s once row RPT q + s has been a pivot (or is padding)
+#pragma unroll
+  for (int s = 0; s < RPT; ++s)
+    if (RPT * q + s >= NA) used |= 1u << s;
+  bool bad = false;
+  __syncwarp();
+#pragma unroll 1
+  for (int c = 0; c < NA; ++c) {
+    float best = -1.f;
+    int bi = 0x7fffffff;
+    if (h == 0) {
+#pragma unroll
+      for (int s = 0; s < RPT; ++s) {
+        const float v = fabsf(m[s][0]);
+        if (!(used >> s & 1u) && v > best) {
+          best = v;
+          bi = RPT * q + s;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o >= 4; o >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
+    }
+    // lanes h != 0 carried -1 and join the quad-0 result of their quad through the butterfly above
+    // only across quads; fetch the winner from lane 0
+    best = __shfl_sync(0xffffffffu, best, 0);
+    const int p = __shfl_sync(0xffffffffu, bi, 0);
+    const int gp = p / RPT, sp = p - RPT * gp;
+    float nxt[RPT];
+#pragma unroll
+    for (int s = 0; s < RPT; ++s) nxt[s] = __shfl_down_sync(0xffffffffu, m[s][0], 1);
+    if (q == gp) {
+#pragma unroll
+      for (int s = 0; s < RPT; ++s) {
+        if (s == sp) {
+#pragma unroll
+          for (int j = 0; j < QW; ++j) pr[QW * h + j] = m[s][j];
+          if (h == 0) {
+            const float pv = m[s][0];
+            s_pinv[w] = pv != 0.f ? 1.f / pv : 0.f;
+            s_piv[w][p] = pv;
+            s_step[w][p] = c;
+            used |= 1u << s;
+          }
+        }
+      }
+    }
+    if (lane == 0) {
+      a.piv[(size_t)k * NA + c] = p;
+      if (!(best > 0.f)) bad = true;
+    }
+    __syncwarp();
+    const float pinv = s_pinv[w];
+    float f[RPT];
+#pragma unroll
+    for (int s = 0; s < RPT; ++s) {
+      const float fs = (h == 0 && RPT * q + s != p) ? m[s][0] * pinv : 0.f;
+      f[s] = __shfl_sync(0xffffffffu, fs, lane & ~3);
+    }
+#pragma unroll
+    for (int j = 0; j < QW; ++j) {
+      const float pj = pr[QW * h + j + 1];
+#pragma unroll
+      for (int s = 0; s < RPT; ++s) {
+        const float old = j < QW - 1 ? m[s][j + 1] : (h < 3 ? nxt[s] : 0.f);
+        m[s][j] = old - f[s] * pj;
+      }
+    }
+    if (h == (NA - 1) / QW) {
+#pragma unroll
+      for (int s = 0; s < RPT; ++s) m[s][(NA - 1) % QW] = (RPT * q + s == p ? 1.f : 0.f) - f[s];
+    }
+    __syncwarp();
+  }
+  if (lane == 0 && bad) {
+    atomicOr(a.status, DEV_ERR_SINGULAR);
+    atomicMin(a.status + 1, k);
+  }
+  float* gInv = reinterpret_cast<float*>(a.LU) + (size_t)k * NA * NA;
+#pragma unroll
+  for (int s = 0; s < RPT; ++s) {
+    const int r = RPT * q + s;
+    if (r < NA) {
+      const int lr = s_step[w][r];
+      const float pv = s_piv[w][r];
+      const float sc = pv != 0.f ? 1.f / pv : 0.f;
+#pragma unroll
+      for (int j = 0; j < QW; ++j) {
+        const int J = QW * h + j;
+        if (J < NA) gInv[(size_t)J * NA + lr] = m[s][j] * sc;  // ((PA)^{-1})^T
+      }
+    }
+  }
+}
+
 template <int NA, int NT>
 struct ProdShape {
   static constexpr int TI = (NA + 7) / 8;  // row tiles of X
@@ -862,20 +1000,47 @@ __global__ void __launch_bounds__(ProdShape<NA, NT>::THREADS) k_condense_product
   const float* gWt = reinterpret_cast<const float*>(a.LU) + (size_t)k * NA * NA;
   const float* gB = reinterpret_cast<const float*>(a.B) + (size_t)k * NA * NT;
   const int* piv = a.piv + (size_t)k * NA;
-  // W[c][i] = (PA)^{-1}[i][c] (stored transposed), Bs[c][:] = [B | r][piv[c]][:]
-  for (int e = t; e < NA * NA; e += THREADS) {
-    const int c = e / NA, i = e % NA;
-    W[c * LDW + i] = __ldg(gWt + e);
+  // W[c][i] = (PA)^{-1}[i][c] (stored transposed), Bs[c][:] = [B | r][piv[c]][:]; the pivots
+  // first (the B rows they select are the only dependent loads), every copy float4-wide and
+  // unrolled so that all of a thread's loads are in flight together
+  __shared__ int s_pv[NA];
+  for (int c = t; c < NA; c += THREADS) s_pv[c] = __ldg(piv + c);
+  static_assert(NA % 4 == 0 || NA * NA % 4 == 0, "W copy");
+  constexpr int W4 = NA * NA / 4;  // float4 of ((PA)^{-1})^T
+  constexpr int B4 = NA * NT / 4;
+  constexpr int C4 = NT * NA / 4;
+#pragma unroll
+  for (int u = 0; u < (W4 + THREADS - 1) / THREADS; ++u) {
+    const int e4 = t + THREADS * u;
+    if (e4 < W4) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(gWt) + e4);
+      const int e = 4 * e4;
+      const int c = e / NA, i = e % NA;  // NA % 4 == 0: the four values share a row
+      *reinterpret_cast<float4*>(W + c * LDW + i) = v;
+    }
   }
   for (int e = t; e < NA * (LDW - NA); e += THREADS) {
     const int c = e / (LDW - NA), i = NA + e % (LDW - NA);
     W[c * LDW + i] = 0.f;
   }
-  for (int e = t; e < NA * NT; e += THREADS) {
-    const int c = e / NT, j = e % NT;
-    Bs[c * LDB + j] = __ldg(gB + (size_t)__ldg(piv + c) * NT + j);
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < (B4 + THREADS - 1) / THREADS; ++u) {
+    const int e4 = t + THREADS * u;
+    if (e4 < B4) {
+      const int c = (4 * e4) / NT, j = (4 * e4) % NT;
+      const float4 v = __ldg(reinterpret_cast<const float4*>(gB + (size_t)s_pv[c] * NT + j));
+      *reinterpret_cast<float4*>(Bs + c * LDB + j) = v;
+    }
   }
-  for (int c = t; c < NA; c += THREADS) Bs[c * LDB + NT] = float(a.r[(size_t)k * NA + __ldg(piv + c)]);
+  for (int c = t; c < NA; c += THREADS) Bs[c * LDB + NT] = float(a.r[(size_t)k * NA + s_pv[c]]);
+  // C and D are pulled into L2 while the first product runs
+  const float* gC = reinterpret_cast<const float*>(a.C) + (size_t)k * NT * NA;
+  const float* gD = reinterpret_cast<const float*>(a.D) + (size_t)k * NT * NT;
+  for (int off = 32 * t; off < NT * NA; off += 32 * THREADS)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(gC + off));
+  for (int off = 32 * t; off < NT * NT; off += 32 * THREADS)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(gD + off));
   __syncthreads();
   // X = W^T Bs: thread tile rows 8 ti .. 8 ti + 7, columns 8 tj .. 8 tj + 7 of X_B
   float acc[8][8];
@@ -927,10 +1092,17 @@ __global__ void __launch_bounds__(ProdShape<NA, NT>::THREADS) k_condense_product
     a.xr[(size_t)k * NA + t] = double(xrv);
     Bs[t * LDB + NT] = xrv;
   }
-  const float* gC = reinterpret_cast<const float*>(a.C) + (size_t)k * NT * NA;
-  for (int e = t; e < NT * NA; e += THREADS) {
-    const int i = e / NA, l = e % NA;
-    W[l * LDW + i] = __ldg(gC + e);
+#pragma unroll
+  for (int u = 0; u < (C4 + THREADS - 1) / THREADS; ++u) {
+    const int e4 = t + THREADS * u;
+    if (e4 < C4) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(gC) + e4);
+      const int i = (4 * e4) / NA, l = (4 * e4) % NA;  // C row i, columns l .. l+3
+      W[l * LDW + i] = v.x;
+      W[(l + 1) * LDW + i] = v.y;
+      W[(l + 2) * LDW + i] = v.z;
+      W[(l + 3) * LDW + i] = v.w;
+    }
   }
   __syncthreads();
   // S = D - C X_B (tiles over nT x nT), t = s - C x_r
@@ -953,7 +1125,6 @@ __global__ void __launch_bounds__(ProdShape<NA, NT>::THREADS) k_condense_product
 #pragma unroll
         for (int v = 0; v < 8; ++v) acc[u][v] += cv[u] * xv[v];
     }
-    const float* gD = reinterpret_cast<const float*>(a.D) + (size_t)k * NT * NT;
     float* gS = reinterpret_cast<float*>(a.S) + (size_t)k * NT * NT;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
@@ -980,7 +1151,12 @@ static cudaError_t cond_two_kernel(const CondArgs& a, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k_condense_products<NA, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)P::SMEM);
   if (e != cudaSuccess) return e;
-  (hfr::count_launch(), k_inverse_q4<NA><<<a.Eim, InvShape<NA>::THREADS, 0, st>>>(a));
+  if constexpr (NA <= 64) {
+    constexpr int WPB = InvWShape<NA>::WPB;
+    (hfr::count_launch(), k_inverse_warp<NA><<<(a.Eim + WPB - 1) / WPB, 32 * WPB, 0, st>>>(a));
+  } else {
+    (hfr::count_launch(), k_inverse_q4<NA><<<a.Eim, InvShape<NA>::THREADS, 0, st>>>(a));
+  }
   (hfr::count_launch(), k_condense_products<NA, NT><<<a.Eim, P::THREADS, P::SMEM, st>>>(a));
   return cudaGetLastError();
 }
