@@ -4,8 +4,9 @@ One step = one hybridized implicit stage of the vortex64 workload (2D Navier-Sto
 vortex, 64x64 quads, p = 3, 262,144 implicit DOF, SDIRK2 stage 1 at 10x the explicit CFL limit)
 solved from the standard initial guess to a relative Newton residual of 1e-8, through the C ABI
 (imex_stage stages 0 and 1).  The headline ``value`` is the mixed-precision path (FP32 element
-blocks / LU / condensation, FP64 residuals, refinement and Krylov vectors); the plain FP64 path
-is timed in the same run and reported beside it.
+blocks, inverse, condensation, trace operator and Krylov basis; FP64 residuals, Newton updates,
+Hessenberg / Givens and the trace solution); the plain FP64 path is timed in the same run and
+reported beside it.  Both paths stop on the same FP64 Newton residual test.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Multi-GPU: replicas only (one independent stage per rank, no collective on the data path).
@@ -219,45 +220,68 @@ def _threads():
         return os.cpu_count() or 1
 
 
-def roofline(prof, w, prec_bytes, peaks, clocks):
-    """Dominant kernel of the timed step (largest total time among the single-kernel phases)
-    and its achieved fraction of its roof, from the live CUDA-event phase timings.
-    Algorithmic work per element (nA = nT = 64 for vortex64):
-      k_condense: 2/3 nA^3 + 2 nA^2 (nT+1) + 2 nT nA (nT+1) flop        -> ALU (FP32 or FP64 pipe)
-      k_jacobian: (nA+nT)^2 (2n+4) multiply-adds (column assembly)      -> ALU
-      k_trace_matvec: S_k bytes nT^2 b + 2 nT x 8 B gathered + 4n nv x 8 B written per face side -> HBM
+# DRAM bytes per launch (read + write) of the current kernels, from one ncu capture each of the
+# vortex64 stage (summaries under profiles/); None where the kernel changed after its capture
+NCU_TRAFFIC_BYTES = {
+    "k_inverse_warp": 69.08e6 + 13.06e6,
+    "k_condense_products": 273.96e6 + 102.35e6,
+    "k_gmres_cycle": 82.05e6 + 2.22e6,
+    "k_jacobian": None,
+}
+
+
+def kernel_rooflines(prof, stats, w, peaks, clocks):
+    """Roofline of every single-kernel phase of the timed step, from the live CUDA-event phase
+    timings (average launch duration), and the dominant one (largest total time).
+    Algorithmic work per launch (E elements, nA = nT = 64, face blocks bs = 16, ntrace = 2E faces,
+    n_t = 16 ntrace trace unknowns, k = GMRES iterations per solve):
+      k_gmres_cycle       HBM: k (S_k blocks E nT^2 4 B + face inverses ntrace bs^2 4 B
+                          + Krylov passes 4 (k/2 + 1) n_t 4 B + z, w 2 n_t 4 B)
+      k_inverse_warp      ALU: Gauss-Jordan inverse 2 nA^3 flop per element
+      k_condense_products ALU 2 (nA^2 (nT+1) + nT nA (nT+1)) flop per element, or HBM
+                          4 (nA^2 + 2 nA nT + nT^2) B in + 4 (nA nT + nT^2) B out per element,
+                          whichever fraction is higher
+      k_jacobian          ALU: (nA+nT)^2 (2n+4) 2 flop per element (n = 4)
     """
     E = w.mesh.nelem
-    nA, nT, n = 64, 64, 4
+    nA, nT, bs, n = 64, 64, 16, 4
     ntrace = 2 * E
-    ms = {k: v[0] for k, v in prof.items() if not k.startswith("_")}
-    cnt = {k: max(v[1], 1) for k, v in prof.items() if not k.startswith("_")}
-    # the mat-vec is launched (gmres iterations + 2 per solve) times; its phase holds the
-    # ungated restart / final-residual launches, whose average stands for every launch
-    total = {"condense": ms["condense"], "jacobian": ms["jacobian"],
-             "trace_matvec": ms["trace_matvec"] / cnt["trace_matvec"] * prof.get("_matvec_launches", cnt["trace_matvec"])}
-    dom = max(total, key=total.get)
-    avg_ms = ms[dom] / cnt[dom]
+    nt_u = ntrace * bs
     mhz = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    per_clk = FP32_PEAK_PER_SM_CLK if prec_bytes == 4 else FP64_PEAK_PER_SM_CLK
-    alu_peak = NUM_SMS * per_clk * mhz * 1e6 / 1e12
-    if dom == "trace_matvec":
-        bytes_per = E * nT * nT * prec_bytes + ntrace * 2 * (nT * 8) + ntrace * (n * 4) * 8
-        achieved = bytes_per / (avg_ms * 1e-3) / 1e9
-        peak = float(peaks.get("hbm_gbs", 6800.0))
-        return dom, {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "k_trace_matvec", "avg_launch_ms": avg_ms,
-                     "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
-    if dom == "condense":
-        flops = (2.0 / 3.0) * nA**3 + 2.0 * nA * nA * (nT + 1) + 2.0 * nT * nA * (nT + 1)
-        kern = "k_condense_reg" if prec_bytes == 4 else "k_condense_lu"
+    alu_peak = NUM_SMS * FP32_PEAK_PER_SM_CLK * mhz * 1e6 / 1e12
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    its = stats["gmres_iterations"] / max(stats["newton_iterations"], 1)
+    out = {}
+
+    def avg(ph):
+        ms, cnt = prof[ph]
+        return ms, ms / max(cnt, 1)
+
+    def entry(kern, bound, achieved, peak, unit, total_ms, avg_ms):
+        t = NCU_TRAFFIC_BYTES.get(kern)
+        return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                "traffic": t, "kernel": kern, "avg_launch_ms": avg_ms, "total_ms": total_ms,
+                "peak_source": ("MEASURED_PEAKS.json hbm_gbs" if unit == "GB/s"
+                                else f"FP32 lanes x {mhz:.0f} MHz x {NUM_SMS} SMs")}
+
+    tot, a = avg("gmres")
+    per_it = E * nT * nT * 4 + ntrace * bs * bs * 4 + 4 * (its / 2 + 1) * nt_u * 4 + 2 * nt_u * 4
+    out["gmres"] = entry("k_gmres_cycle", "hbm", per_it * its / (a * 1e-3) / 1e9, hbm_peak, "GB/s", tot, a)
+    tot, a = avg("condense_factor")
+    out["condense_factor"] = entry("k_inverse_warp", "alu", E * 2.0 * nA**3 / (a * 1e-3) / 1e12, alu_peak,
+                                   "TFLOP/s", tot, a)
+    tot, a = avg("condense_products")
+    fl = E * 2.0 * (nA * nA * (nT + 1) + nT * nA * (nT + 1)) / (a * 1e-3) / 1e12
+    by = E * (4.0 * (nA * nA + 2 * nA * nT + nT * nT) + 4.0 * (nA * nT + nT * nT)) / (a * 1e-3) / 1e9
+    if by / hbm_peak > fl / alu_peak:
+        out["condense_products"] = entry("k_condense_products", "hbm", by, hbm_peak, "GB/s", tot, a)
     else:
-        flops = (nA + nT) ** 2 * (2 * n + 4) * 2.0
-        kern = "k_jacobian"
-    achieved = flops * E / (avg_ms * 1e-3) / 1e12
-    return dom, {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                 "frac": achieved / alu_peak, "traffic": None, "kernel": kern, "avg_launch_ms": avg_ms,
-                 "peak_source": f"{'FP32' if prec_bytes == 4 else 'FP64'} lanes x {mhz:.0f} MHz x 152 SMs"}
+        out["condense_products"] = entry("k_condense_products", "alu", fl, alu_peak, "TFLOP/s", tot, a)
+    tot, a = avg("jacobian")
+    out["jacobian"] = entry("k_jacobian", "alu", E * (nA + nT) ** 2 * (2 * n + 4) * 2.0 / (a * 1e-3) / 1e12,
+                            alu_peak, "TFLOP/s", tot, a)
+    dom = max(out, key=lambda k: out[k]["total_ms"])
+    return dom, out
 
 
 def main():
@@ -266,7 +290,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--refine", type=int, default=1)
+    ap.add_argument("--refine", type=int, default=0,
+                    help="FP64 refinement sweeps of the local solves in the back-substitution")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--paths", default="both", choices=["both", "mixed", "fp64"],
                     help="profiling aid: time only one precision path")
@@ -323,11 +348,8 @@ def main():
         e2e_ms, bi, bo = time_e2e(pkg, torch, mixed["ctx"], w, max(3, args.steps // 2), dev)
     peaks, peak_src = _peaks()
     pm = {k: v[0] for k, v in mixed["profile"].items()}
-    prof = dict(mixed["profile"])
-    # mat-vec launches over the timed steps: one per GMRES iteration plus the final-residual
-    # product of every solve (one solve per Newton iteration)
-    prof["_matvec_launches"] = (mixed["stats"]["gmres_iterations"] + mixed["stats"]["newton_iterations"]) * args.steps
-    dom, roof = roofline(prof, w, 4, peaks, clocks)
+    dom, kroofs = kernel_rooflines(mixed["profile"], mixed["stats"], w, peaks, clocks)
+    roof = {k: v for k, v in kroofs[dom].items() if k != "total_ms"}
     line = {
         "metric": METRIC,
         "value": world * dofs / (ms_mixed * 1e-3),
@@ -355,6 +377,8 @@ def main():
         "phases_ms_total": {k: round(v, 3) for k, v in pm.items()},
         "dominant_phase": dom,
         "roofline": roof,
+        "kernel_rooflines": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
+                             for k, v in kroofs.items()},
         "e2e": {"value": world * dofs / (e2e_ms * 1e-3), "unit": "DOF/s", "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo},
         "gpu_launches": int(mixed["launches"] // max(args.steps, 1)),

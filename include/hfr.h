@@ -183,10 +183,12 @@ int imex_stage(fr_ctx* ctx, int stage, double dt, const double* u_n, double* u_s
 int hfr_initial_trace(fr_ctx* ctx, const double* u, double* uhat);
 
 /* Per-phase device time of the context's calls, measured with CUDA events on its stream.
- * Phases: 0 residual (incl. trace assembly), 1 element Jacobian blocks, 2 condensation kernel,
- * 3 trace right-hand side + preconditioner build, 4 trace GMRES solve, 5 back-substitution and
- * refinement, 6 Newton bookkeeping (right-hand sides, norms, updates), 7 FP64 refinement of x_r,
- * 8 one trace mat-vec kernel (the restart / final-residual products inside GMRES), 9 unused. */
+ * Phases: 0 residual (incl. trace assembly), 1 element Jacobian blocks, 2 condensation: the
+ * factorisation kernel (the whole condensation where it is a single kernel), 3 trace right-hand
+ * side + preconditioner build, 4 trace GMRES solve, 5 back-substitution and refinement, 6 Newton
+ * bookkeeping (right-hand sides, norms, updates), 7 FP64 refinement of x_r, 8 one trace mat-vec
+ * kernel (multi-kernel GMRES: the restart / final-residual products), 9 condensation: the
+ * products X = A^{-1}[B | r], S = D - C X_B of the two-kernel FP32 path. */
 typedef struct {
   double ms[10];
   long long count[10];

@@ -56,8 +56,8 @@ ABI_SYMBOLS = [
     "fr_status_string",
 ]
 
-PHASES = ["residual", "jacobian", "condense", "trace_rhs_precond", "gmres", "backsolve", "newton", "refine_xr",
-          "trace_matvec", "unused"]
+PHASES = ["residual", "jacobian", "condense_factor", "trace_rhs_precond", "gmres", "backsolve", "newton",
+          "refine_xr", "trace_matvec", "condense_products"]
 
 
 class fr_mesh_desc(ctypes.Structure):

@@ -71,7 +71,7 @@ struct fr_ctx {
   long long pcnt[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
 };
 
-enum { PH_RES = 0, PH_JAC = 1, PH_COND = 2, PH_PREC = 3, PH_GMRES = 4, PH_BACK = 5, PH_NEWTON = 6, PH_REFX = 7, PH_MATVEC = 8 };
+enum { PH_RES = 0, PH_JAC = 1, PH_COND = 2, PH_PREC = 3, PH_GMRES = 4, PH_BACK = 5, PH_NEWTON = 6, PH_REFX = 7, PH_MATVEC = 8, PH_CPROD = 9 };
 
 static int prof_begin(fr_ctx* ctx, int phase) {
   if (!ctx->prof || ctx->evused + 2 > ctx->evpool.size()) return -1;
@@ -763,7 +763,10 @@ static int condense_impl(fr_ctx* ctx, int refine) {
   c.t = ctx->te;
   c.status = ctx->status;
   int ph = prof_begin(ctx, PH_COND);
-  CK(launch_condense(ctx->prec_bytes, c, ctx->stream));
+  CK(launch_condense_part(ctx->prec_bytes, c, ctx->stream, 0));
+  prof_end(ctx, ph);
+  ph = prof_begin(ctx, PH_CPROD);
+  CK(launch_condense_part(ctx->prec_bytes, c, ctx->stream, 1));
   prof_end(ctx, ph);
   if (refine > 0 && ctx->lin_U) {
     // FP64 refinement of x_r against the exact linearisation (used by the back-substitution)
@@ -1055,9 +1058,8 @@ extern "C" int imex_stage(fr_ctx* ctx, int stage, double dt, const double* u_n, 
     }
     prof_end(ctx, phu);
   }
-  // R_hist[i] = R(u_i, u^_i)
-  int rc = residual_into(ctx, u_stage, uhat, R_hist + (size_t)i * tot, ctx->gview, nullptr);
-  if (rc) return rc;
+  // R_hist[i] = R(u_i, u^_i): the loop leaves right after evaluating R at the final state
+  CK(cudaMemcpyAsync(R_hist + (size_t)i * tot, ctx->Rw, tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
   CK(cudaStreamSynchronize(st));
   prof_collect(ctx);
   if (stats) {

@@ -249,436 +249,21 @@ __global__ void __launch_bounds__(GJ_THREADS) k_condense_reg(const __grid_consta
   }
 }
 
-// ----------------------------------------------------- row-per-thread kernel (FP32)
-// One element per CTA of 32 ceil(nA / 32) threads: thread r owns physical row r of [A | B | r]
-// in registers.  The columns cycle: every pivot step shifts each row left by one place and appends
-// the column of the inverse that the step creates, so the pivot column is always register 0 and
-// the nA steps run as a rolled loop over one fixed-register body (small code, no register
-// indexing by step).  Per step: warp argmax of |m_0| over the rows not yet used, a combine over
-// the warps, the pivot thread publishes its row as it stands, and every thread performs
-//   m_{j-1} <- m_j - f row_j (j >= 1),  m_last <- [pivot thread] - f,  f = m_0 / pivot
-// (one FMA per entry; the pivot thread uses f = 0).  A row that has served as pivot is therefore
-// kept multiplied by its own pivot; one division per row at the end restores (PA)^{-1} | X.
-// After nA steps a row holds [X_B row | x_r | (PA)^{-1} row].  S = D - C X uses X transposed in
-// shared memory, read as broadcast float4.
-template <int NA, int NT>
-struct CycShape {
-  static constexpr int NC = NA + NT + 1;
-  static constexpr int NQ = (NC + 3) / 4;
-  static constexpr int NW = (NA + 31) / 32;
-  static constexpr int THREADS = 32 * NW;
-  static constexpr int LX = ((NA + 3) / 4) * 4 + 4;  // row length of the transposed X
-};
-
-template <int NA, int NT>
-__global__ void __launch_bounds__(CycShape<NA, NT>::THREADS) k_condense_cyc(const __grid_constant__ CondArgs a) {
-  using Sh = CycShape<NA, NT>;
-  constexpr int NC = Sh::NC, NQ = Sh::NQ, NW = Sh::NW, LX = Sh::LX;
-  static_assert(NT % 4 == 0, "shape");
-  __shared__ __align__(16) float pr[NQ * 4];
-  __shared__ float cval[NW];
-  __shared__ int cidx[NW];
-  __shared__ float s_pinv;
-  __shared__ int s_bad;
-  __shared__ __align__(16) float sXt[(NT + 1) * LX];
-  const int k = blockIdx.x;
-  const int r = threadIdx.x, lane = r & 31, wid = r >> 5;
-  const bool row_ok = r < NA;
-  const float* gA = reinterpret_cast<const float*>(a.A) + (size_t)k * NA * NA;
-  const float* gB = reinterpret_cast<const float*>(a.B) + (size_t)k * NA * NT;
-  float m[NQ * 4];
-#pragma unroll
-  for (int j = 0; j < NQ * 4; ++j) m[j] = 0.f;
-  if (row_ok) {
-    if constexpr (NA % 4 == 0) {
-#pragma unroll
-      for (int q = 0; q < NA / 4; ++q) {
-        const float4 v = __ldg(reinterpret_cast<const float4*>(gA + (size_t)r * NA) + q);
-        m[4 * q] = v.x;
-        m[4 * q + 1] = v.y;
-        m[4 * q + 2] = v.z;
-        m[4 * q + 3] = v.w;
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < NA; ++j) m[j] = __ldg(gA + (size_t)r * NA + j);
-    }
-#pragma unroll
-    for (int q = 0; q < NT / 4; ++q) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(gB + (size_t)r * NT) + q);
-      m[NA + 4 * q] = v.x;
-      m[NA + 4 * q + 1] = v.y;
-      m[NA + 4 * q + 2] = v.z;
-      m[NA + 4 * q + 3] = v.w;
-    }
-    m[NA + NT] = float(a.r[(size_t)k * NA + r]);
-  }
-  if (r == 0) s_bad = 0;
-  bool used = !row_ok;
-  float mypiv = 1.f;
-  int mystep = 0;
-#pragma unroll 1
-  for (int c = 0; c < NA; ++c) {
-    float best = used ? -1.f : fabsf(m[0]);
-    int bi = r;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ob > best || (ob == best && oi < bi)) {
-        best = ob;
-        bi = oi;
-      }
-    }
-    if (lane == 0) {
-      cval[wid] = best;
-      cidx[wid] = bi;
-    }
-    __syncthreads();
-    float b = cval[0];
-    int p = cidx[0];
-#pragma unroll
-    for (int w2 = 1; w2 < NW; ++w2) {
-      const float ob = cval[w2];
-      const int oi = cidx[w2];
-      if (ob > b || (ob == b && oi < p)) {
-        b = ob;
-        p = oi;
-      }
-    }
-    const bool isp = r == p;
-    if (isp) {
-#pragma unroll
-      for (int q = 0; q < NQ; ++q)
-        reinterpret_cast<float4*>(pr)[q] = make_float4(m[4 * q], m[4 * q + 1], m[4 * q + 2], m[4 * q + 3]);
-      s_pinv = m[0] != 0.f ? 1.f / m[0] : 0.f;
-      if (!(b > 0.f)) s_bad = 1;
-      a.piv[(size_t)k * NA + c] = r;
-      used = true;
-      mypiv = m[0];
-      mystep = c;
-    }
-    __syncthreads();
-    const float f = isp ? 0.f : m[0] * s_pinv;
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      const float4 pq = reinterpret_cast<const float4*>(pr)[q];
-      if (q > 0) m[4 * q - 1] = m[4 * q] - f * pq.x;
-      m[4 * q] = m[4 * q + 1] - f * pq.y;
-      m[4 * q + 1] = m[4 * q + 2] - f * pq.z;
-      m[4 * q + 2] = m[4 * q + 3] - f * pq.w;
-    }
-    m[NQ * 4 - 1] = 0.f;
-    m[NC - 1] = (isp ? 1.f : 0.f) - f;
-  }
-  // undo the per-row pivot scaling: physical row r is logical row mystep
-  const float sc = mypiv != 0.f ? 1.f / mypiv : 0.f;
-#pragma unroll
-  for (int j = 0; j < NC; ++j) m[j] *= sc;
-  if (row_ok) {
-    float* gInv = reinterpret_cast<float*>(a.LU) + (size_t)k * NA * NA;
-    float* gXB = reinterpret_cast<float*>(a.XB) + (size_t)k * NA * NT;
-#pragma unroll
-    for (int c = 0; c < NA; ++c) gInv[(size_t)c * NA + mystep] = m[NT + 1 + c];  // ((PA)^{-1})^T
-#pragma unroll
-    for (int q = 0; q < NT / 4; ++q)
-      reinterpret_cast<float4*>(gXB + (size_t)mystep * NT)[q] =
-          make_float4(m[4 * q], m[4 * q + 1], m[4 * q + 2], m[4 * q + 3]);
-    a.xr[(size_t)k * NA + mystep] = double(m[NT]);
-#pragma unroll
-    for (int j = 0; j <= NT; ++j) sXt[j * LX + mystep] = m[j];
-  }
-  if (r < LX - NA) {
-    // zero the padding columns of the transposed X (read by the float4 loads below)
-#pragma unroll
-    for (int j = 0; j <= NT; ++j) sXt[j * LX + NA + r] = 0.f;
-  }
-  __syncthreads();
-  if (r == 0 && s_bad) {
-    atomicOr(a.status, DEV_ERR_SINGULAR);
-    atomicMin(a.status + 1, k);
-  }
-  // S = D - C X_B, t = s - C x_r: thread i < NT computes row i, C row i in registers
-  constexpr int NA4 = (NA + 3) / 4;
-  for (int i = r; i < NT; i += Sh::THREADS) {
-    const float* gC = reinterpret_cast<const float*>(a.C) + (size_t)k * NT * NA + (size_t)i * NA;
-    const float* gD = reinterpret_cast<const float*>(a.D) + (size_t)k * NT * NT + (size_t)i * NT;
-    float* gS = reinterpret_cast<float*>(a.S) + (size_t)k * NT * NT + (size_t)i * NT;
-#pragma unroll
-    for (int j = 0; j < NA4 * 4; ++j) m[j] = j < NA ? __ldg(gC + j) : 0.f;
-#pragma unroll 1
-    for (int j0 = 0; j0 < NT; j0 += 4) {
-      float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int q = 0; q < NA4; ++q) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float4 x4 = reinterpret_cast<const float4*>(sXt + (j0 + u) * LX)[q];
-          acc[u] += m[4 * q] * x4.x + m[4 * q + 1] * x4.y + m[4 * q + 2] * x4.z + m[4 * q + 3] * x4.w;
-        }
-      }
-      const float4 d4 = __ldg(reinterpret_cast<const float4*>(gD) + j0 / 4);
-      reinterpret_cast<float4*>(gS)[j0 / 4] = make_float4(d4.x - acc[0], d4.y - acc[1], d4.z - acc[2], d4.w - acc[3]);
-    }
-    float acc = 0.f;
-#pragma unroll
-    for (int q = 0; q < NA4; ++q) {
-      const float4 x4 = reinterpret_cast<const float4*>(sXt + NT * LX)[q];
-      acc += m[4 * q] * x4.x + m[4 * q + 1] * x4.y + m[4 * q + 2] * x4.z + m[4 * q + 3] * x4.w;
-    }
-    a.t[(size_t)k * NT + i] = a.s[(size_t)k * NT + i] - double(acc);
-  }
-}
-
-// ------------------------------------------------ four-row tiles with cycling columns (FP32)
-// The same cycling Gauss-Jordan as k_condense_cyc, with the work of a row spread over the four
-// lanes of a lane quad: lane h of quad g holds rows 4g .. 4g+3 and columns QW h .. QW h + QW-1
-// of the cycled row (QW = ceil(nc / 4)).  Every pivot-row value a lane reads from shared memory
-// now feeds four FMAs (one per row) instead of one, which takes the update off the shared-memory
-// pipe.  The shift of the cycled rows crosses lanes: the first column of lane h+1 moves to the
-// last column of lane h (one shuffle per row), and the factors m_0 / pivot come from lane 0 of
-// the quad.  S = D - C X_B is formed from C^T and X in shared memory with 8 x 8 register tiles.
-template <int NA, int NT>
-struct Q4Shape {
-  static constexpr int NC = NA + NT + 1;
-  static constexpr int QW = (NC + 3) / 4;  // columns per lane
-  static constexpr int NCP = 4 * QW;       // padded cycled row
-  static constexpr int RG = (NA + 3) / 4;  // lane quads holding rows
-  static constexpr int THREADS = ((4 * RG + 31) / 32) * 32;
-  static constexpr int NWARP = THREADS / 32;
-  static constexpr int LDC = NT + 4;                   // C^T rows (NT used)
-  static constexpr int LDX = ((NT + 1 + 3) / 4) * 4 + 4;  // X rows (NT + 1 used)
-  static_assert(NT % 8 == 0, "nT must be a multiple of 8");
-  static_assert((NT / 8) * (NT / 8) <= THREADS, "S tiles exceed the CTA");
-};
-
-template <int NA, int NT>
-__global__ void __launch_bounds__(Q4Shape<NA, NT>::THREADS, 4) k_condense_q4(const __grid_constant__ CondArgs a) {
-  using Sh = Q4Shape<NA, NT>;
-  constexpr int NC = Sh::NC, QW = Sh::QW, NCP = Sh::NCP, RG = Sh::RG, NWARP = Sh::NWARP;
-  constexpr int LDC = Sh::LDC, LDX = Sh::LDX, THREADS = Sh::THREADS;
-  __shared__ __align__(16) float pr[NCP + 4];
-  __shared__ float cval[NWARP];
-  __shared__ int cidx[NWARP];
-  __shared__ float s_pinv;
-  __shared__ int s_bad;
-  __shared__ int s_step[NA];
-  __shared__ float s_piv[NA];
-  __shared__ __align__(16) float Ct[NA * LDC];
-  __shared__ __align__(16) float Xs[NA * LDX];
-  const int k = blockIdx.x;
-  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-  const int g = t >> 2, h = t & 3;
-  const float* gA = reinterpret_cast<const float*>(a.A) + (size_t)k * NA * NA;
-  const float* gB = reinterpret_cast<const float*>(a.B) + (size_t)k * NA * NT;
-  const double* gr = a.r + (size_t)k * NA;
-  float m[4][QW];
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    const int r = 4 * g + s;
-    const bool rok = g < RG && r < NA;
-#pragma unroll
-    for (int j = 0; j < QW; ++j) {
-      const int J = QW * h + j;
-      float v = 0.f;
-      if (rok) {
-        if (J < NA)
-          v = __ldg(gA + (size_t)r * NA + J);
-        else if (J < NA + NT)
-          v = __ldg(gB + (size_t)r * NT + (J - NA));
-        else if (J == NA + NT)
-          v = float(gr[r]);
-      }
-      m[s][j] = v;
-    }
-  }
-  if (t < 4) pr[NCP + t] = 0.f;
-  if (t == 0) s_bad = 0;
-  unsigned used = 0u;  // lane 0 of a quad: bit s set once row 4g+s has been a pivot (or is padding)
-#pragma unroll
-  for (int s = 0; s < 4; ++s)
-    if (g >= RG || 4 * g + s >= NA) used |= 1u << s;
-  __syncthreads();
-#pragma unroll 1
-  for (int c = 0; c < NA; ++c) {
-    // pivot search on the cycled column 0 (held by lane 0 of each quad)
-    float best = -1.f;
-    int bi = 0x7fffffff;
-    if (h == 0) {
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const float v = fabsf(m[s][0]);
-        if (!(used >> s & 1u) && (v > best)) {
-          best = v;
-          bi = 4 * g + s;
-        }
-      }
-    }
-#pragma unroll
-    for (int o = 16; o >= 4; o >>= 1) {
-      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ob > best || (ob == best && oi < bi)) {
-        best = ob;
-        bi = oi;
-      }
-    }
-    if (lane == 0) {
-      cval[wid] = best;
-      cidx[wid] = bi;
-    }
-    // old first columns of the next lane (the cycled shift crosses lanes), taken before the update
-    float nxt[4];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) nxt[s] = __shfl_down_sync(0xffffffffu, m[s][0], 1);
-    __syncthreads();
-    float b = cval[0];
-    int p = cidx[0];
-#pragma unroll
-    for (int w2 = 1; w2 < NWARP; ++w2) {
-      const float ob = cval[w2];
-      const int oi = cidx[w2];
-      if (ob > b || (ob == b && oi < p)) {
-        b = ob;
-        p = oi;
-      }
-    }
-    const int sp = p & 3;
-    // the quad holding row p publishes it as it stands
-    if (g == (p >> 2)) {
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        if (s == sp) {
-#pragma unroll
-          for (int j = 0; j < QW; ++j) pr[QW * h + j] = m[s][j];
-          if (h == 0) {
-            const float pv = m[s][0];
-            s_pinv = pv != 0.f ? 1.f / pv : 0.f;
-            s_piv[p] = pv;
-          }
-        }
-      }
-      if (h == 0) {
-        used |= 1u << sp;
-        s_step[p] = c;
-        a.piv[(size_t)k * NA + c] = p;
-        if (!(b > 0.f)) s_bad = 1;
-      }
-    }
-    __syncthreads();
-    const float pinv = s_pinv;
-    float f[4];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      const float fs = (h == 0 && 4 * g + s != p) ? m[s][0] * pinv : 0.f;
-      f[s] = __shfl_sync(0xffffffffu, fs, lane & ~3);
-    }
-    // m_{J} <- m_{J+1} - f row_{J+1} over the cycled row; the appended column of the inverse at
-    // the last place: [pivot row] - f
-#pragma unroll
-    for (int j = 0; j < QW; ++j) {
-      const float pj = pr[QW * h + j + 1];
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const float old = j < QW - 1 ? m[s][j + 1] : (h < 3 ? nxt[s] : 0.f);
-        m[s][j] = old - f[s] * pj;
-      }
-    }
-    if (h == (NC - 1) / QW) {
-#pragma unroll
-      for (int s = 0; s < 4; ++s) m[s][(NC - 1) % QW] = (4 * g + s == p ? 1.f : 0.f) - f[s];
-    }
-  }
-  __syncthreads();
-  if (t == 0 && s_bad) {
-    atomicOr(a.status, DEV_ERR_SINGULAR);
-    atomicMin(a.status + 1, k);
-  }
-  // undo the per-row pivot scaling; physical row r is logical row s_step[r].  Cycled row after nA
-  // steps: [X_B row (nT) | x_r | (PA)^{-1} row (nA)]
-  float* gInv = reinterpret_cast<float*>(a.LU) + (size_t)k * NA * NA;
-  float* gXB = reinterpret_cast<float*>(a.XB) + (size_t)k * NA * NT;
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    const int r = 4 * g + s;
-    if (g < RG && r < NA) {
-      const int lr = s_step[r];
-      const float pv = s_piv[r];
-      const float sc = pv != 0.f ? 1.f / pv : 0.f;
-#pragma unroll
-      for (int j = 0; j < QW; ++j) {
-        const int J = QW * h + j;
-        const float v = m[s][j] * sc;
-        if (J < NT) {
-          gXB[(size_t)lr * NT + J] = v;
-          Xs[lr * LDX + J] = v;
-        } else if (J == NT) {
-          a.xr[(size_t)k * NA + lr] = double(v);
-          Xs[lr * LDX + NT] = v;
-        } else if (J < NC) {
-          gInv[(size_t)(J - NT - 1) * NA + lr] = v;  // ((PA)^{-1})^T
-        }
-      }
-    }
-  }
-  const float* gC = reinterpret_cast<const float*>(a.C) + (size_t)k * NT * NA;
-  for (int e = t; e < NT * NA; e += THREADS) {
-    const int i = e / NA, l = e % NA;
-    Ct[l * LDC + i] = __ldg(gC + e);
-  }
-  __syncthreads();
-  // S = D - C X_B in 8 x 8 tiles
-  constexpr int TJ = NT / 8;
-  if (t < TJ * TJ) {
-    const int ti = t / TJ, tj = t % TJ;
-    float acc[8][8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-#pragma unroll
-      for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
-#pragma unroll 2
-    for (int l = 0; l < NA; ++l) {
-      const float4 c0 = *reinterpret_cast<const float4*>(Ct + l * LDC + 8 * ti);
-      const float4 c1 = *reinterpret_cast<const float4*>(Ct + l * LDC + 8 * ti + 4);
-      const float4 x0 = *reinterpret_cast<const float4*>(Xs + l * LDX + 8 * tj);
-      const float4 x1 = *reinterpret_cast<const float4*>(Xs + l * LDX + 8 * tj + 4);
-      const float cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-      const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-#pragma unroll
-        for (int v = 0; v < 8; ++v) acc[u][v] += cv[u] * xv[v];
-    }
-    const float* gD = reinterpret_cast<const float*>(a.D) + (size_t)k * NT * NT;
-    float* gS = reinterpret_cast<float*>(a.S) + (size_t)k * NT * NT;
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const size_t o = (size_t)(8 * ti + u) * NT + 8 * tj;
-      const float4 d0 = __ldg(reinterpret_cast<const float4*>(gD + o));
-      const float4 d1 = __ldg(reinterpret_cast<const float4*>(gD + o + 4));
-      reinterpret_cast<float4*>(gS + o)[0] =
-          make_float4(d0.x - acc[u][0], d0.y - acc[u][1], d0.z - acc[u][2], d0.w - acc[u][3]);
-      reinterpret_cast<float4*>(gS + o)[1] =
-          make_float4(d1.x - acc[u][4], d1.y - acc[u][5], d1.z - acc[u][6], d1.w - acc[u][7]);
-    }
-  }
-  // t = s - C x_r
-  for (int i = t; i < NT; i += THREADS) {
-    float acc = 0.f;
-#pragma unroll 8
-    for (int l = 0; l < NA; ++l) acc += Ct[l * LDC + i] * Xs[l * LDX + NT];
-    a.t[(size_t)k * NT + i] = a.s[(size_t)k * NT + i] - double(acc);
-  }
-}
-
 // ------------------------------------------ two-kernel FP32 path: (PA)^{-1}, then the products
-// Kernel 1 inverts A alone with the cycling Gauss-Jordan of k_condense_q4 (four rows per lane,
-// the columns of a row spread over a lane quad): only nA values per row live in registers, so
-// about ten CTAs fit on an SM and the pivot steps of different elements hide each other's
-// latency.  It writes ((PA)^{-1})^T and the interchanges.  Kernel 2 forms X = A^{-1}[B | r] =
-// (PA)^{-1} (P[B | r]) and S = D - C X_B, t = s - C x_r as two dense products with 8 x 8
-// register tiles over operands staged in shared memory (k-major, so every tile row is one
-// broadcast float4 pair).
+// Kernel 1 inverts A in place by Gauss-Jordan with partial pivoting, keeping the matrix in
+// registers with its columns cycling: every pivot step shifts each row left by one place and
+// appends the column of the inverse that the step creates, so the pivot column is always the
+// first register and the nA steps run as a rolled loop over one fixed-register body (small code,
+// no register indexing by step).  Rows are not normalised: each step performs
+//   m_{J} <- m_{J+1} - f row_{J+1},  m_last <- [pivot row] - f,  f = m_0 / pivot
+// (one FMA per entry; the pivot row uses f = 0), so a row that has served as pivot stays
+// multiplied by its own pivot, and one division per row at the end restores (PA)^{-1}.  The
+// cycled row is spread over a lane quad (lane h holds columns QW h .. QW h + QW-1) and each lane
+// holds several rows, so every pivot-row value read from shared memory feeds several FMAs; the
+// shift crosses lanes by one shuffle per row.  It writes ((PA)^{-1})^T and the interchanges.
+// Kernel 2 forms X = A^{-1}[B | r] = (PA)^{-1} (P[B | r]) and S = D - C X_B, t = s - C x_r as two
+// dense products with 8 x 8 register tiles over operands staged in shared memory (k-major, so
+// every tile row is one broadcast float4 pair).
 template <int NA>
 struct InvShape {
   static constexpr int QW = (NA + 3) / 4;
@@ -837,8 +422,8 @@ __global__ void __launch_bounds__(InvShape<NA>::THREADS, NA <= 64 ? 8 : 3) k_inv
   }
 }
 
-// One warp per element: lane quad q (q < 8) holds rows RPT q .. RPT q + RPT-1, lane h of the quad
-// columns QW h .. QW h + QW-1 of the cycled row.  The argmax, the pivot broadcast and the shift
+// Kernel 1, one warp per element (nA <= 64): lane quad q (q < 8) holds rows RPT q .. RPT q + RPT-1,
+// lane h of the quad columns QW h .. QW h + QW-1 of the cycled row.  The argmax, the pivot broadcast and the shift
 // stay inside the warp (no CTA barrier); each pivot-row value read from shared memory feeds RPT
 // FMAs.  WPB elements (warps) per CTA share nothing but the CTA.
 template <int NA>
@@ -1146,17 +731,20 @@ __global__ void __launch_bounds__(ProdShape<NA, NT>::THREADS) k_condense_product
 }
 
 template <int NA, int NT>
-static cudaError_t cond_two_kernel(const CondArgs& a, cudaStream_t st) {
+static cudaError_t cond_two_kernel(const CondArgs& a, cudaStream_t st, int part) {
   using P = ProdShape<NA, NT>;
+  if (part == 0) {
+    if constexpr (NA <= 64) {
+      constexpr int WPB = InvWShape<NA>::WPB;
+      (hfr::count_launch(), k_inverse_warp<NA><<<(a.Eim + WPB - 1) / WPB, 32 * WPB, 0, st>>>(a));
+    } else {
+      (hfr::count_launch(), k_inverse_q4<NA><<<a.Eim, InvShape<NA>::THREADS, 0, st>>>(a));
+    }
+    return cudaGetLastError();
+  }
   cudaError_t e = cudaFuncSetAttribute(k_condense_products<NA, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)P::SMEM);
   if (e != cudaSuccess) return e;
-  if constexpr (NA <= 64) {
-    constexpr int WPB = InvWShape<NA>::WPB;
-    (hfr::count_launch(), k_inverse_warp<NA><<<(a.Eim + WPB - 1) / WPB, 32 * WPB, 0, st>>>(a));
-  } else {
-    (hfr::count_launch(), k_inverse_q4<NA><<<a.Eim, InvShape<NA>::THREADS, 0, st>>>(a));
-  }
   (hfr::count_launch(), k_condense_products<NA, NT><<<a.Eim, P::THREADS, P::SMEM, st>>>(a));
   return cudaGetLastError();
 }
@@ -1526,27 +1114,18 @@ static cudaError_t cond_smem(const CondArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// part 0: the factorisation (or the whole condensation where it is one kernel); part 1: the
+// products of the two-kernel FP32 path (nothing elsewhere)
 template <typename T>
-static cudaError_t cond_dispatch(const CondArgs& a, cudaStream_t st) {
+static cudaError_t cond_dispatch(const CondArgs& a, cudaStream_t st, int part) {
   if (a.Eim == 0) return cudaSuccess;
   const int nA = a.nA, nT = a.nT;
   if (sizeof(T) == 4) {
-#define HFR_CYC(NA_, NT_)                                                                                    \
-  if (nA == NA_ && nT == NT_) {                                                                            \
-    (hfr::count_launch(), k_condense_cyc<NA_, NT_><<<a.Eim, CycShape<NA_, NT_>::THREADS, 0, st>>>(a)); \
-    return cudaGetLastError();                                                                           \
+    if (nA == 64 && nT == 64) return cond_two_kernel<64, 64>(a, st, part);
+    if (nA == 36 && nT == 48) return cond_two_kernel<36, 48>(a, st, part);
+    if (nA == 100 && nT == 80) return cond_two_kernel<100, 80>(a, st, part);
   }
-#define HFR_Q4(NA_, NT_)                                                                                  \
-  if (nA == NA_ && nT == NT_) {                                                                         \
-    (hfr::count_launch(), k_condense_q4<NA_, NT_><<<a.Eim, Q4Shape<NA_, NT_>::THREADS, 0, st>>>(a)); \
-    return cudaGetLastError();                                                                        \
-  }
-    if (nA == 64 && nT == 64) return cond_two_kernel<64, 64>(a, st);
-    if (nA == 36 && nT == 48) return cond_two_kernel<36, 48>(a, st);
-    if (nA == 100 && nT == 80) return cond_two_kernel<100, 80>(a, st);
-#undef HFR_Q4
-#undef HFR_CYC
-  }
+  if (part != 0) return cudaSuccess;
   if (nA == 9 && nT == 12) return cond_reg<T, 9, 12>(a, st);
   if (nA == 16 && nT == 16) return cond_reg<T, 16, 16>(a, st);
   if (nA == 36 && nT == 48) return cond_reg<T, 36, 48>(a, st);
@@ -1559,7 +1138,7 @@ template <typename T>
 static cudaError_t cond_lu(const CondArgs& a, cudaStream_t st) {
   const int rows2 = a.nA > a.nT ? a.nA : a.nT;
   size_t smem = sizeof(T) * ((size_t)rows2 * a.nA + (size_t)a.nA * (a.nT + 1));
-  if (smem > 227 * 1024) return cond_dispatch<T>(a, st);
+  if (smem > 227 * 1024) return cond_dispatch<T>(a, st, 0);
   cudaError_t err = cudaFuncSetAttribute(k_condense_lu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   if (a.Eim == 0) return cudaSuccess;
@@ -1573,9 +1152,15 @@ bool condense_uses_lu(int prec_bytes, int nA, int nT) {
   return prec_bytes == 8 && sizeof(double) * ((size_t)rows2 * nA + (size_t)nA * (nT + 1)) <= 227 * 1024;
 }
 
+cudaError_t launch_condense_part(int prec_bytes, const CondArgs& a, cudaStream_t st, int part) {
+  if (condense_uses_lu(prec_bytes, a.nA, a.nT)) return part == 0 ? cond_lu<double>(a, st) : cudaSuccess;
+  return prec_bytes == 8 ? cond_dispatch<double>(a, st, part) : cond_dispatch<float>(a, st, part);
+}
+
 cudaError_t launch_condense(int prec_bytes, const CondArgs& a, cudaStream_t st) {
-  if (condense_uses_lu(prec_bytes, a.nA, a.nT)) return cond_lu<double>(a, st);
-  return prec_bytes == 8 ? cond_dispatch<double>(a, st) : cond_dispatch<float>(a, st);
+  cudaError_t e = launch_condense_part(prec_bytes, a, st, 0);
+  if (e != cudaSuccess) return e;
+  return launch_condense_part(prec_bytes, a, st, 1);
 }
 
 cudaError_t launch_lu_solve(int prec_bytes, int Eim, int nA, int nT_of_last, const void* LU, const int* piv,

@@ -86,6 +86,9 @@ struct CondArgs {
   int* status;      // device status word (DEV_ERR_*), first failing element in status[1]
 };
 cudaError_t launch_condense(int prec_bytes, const CondArgs& a, cudaStream_t st);
+// the same in two parts: 0 = factorisation (the whole condensation where it is one kernel),
+// 1 = the products X = A^{-1}[B | r], S = D - C X_B of the two-kernel FP32 path (else nothing)
+cudaError_t launch_condense_part(int prec_bytes, const CondArgs& a, cudaStream_t st, int part);
 
 // x = A^{-1} b with the stored factorisation (LU + interchanges or in-place inverse, as chosen
 // by condense_uses_lu), in place on b (Eim x nA, FP64 vectors).
