@@ -742,9 +742,15 @@ static int check_status(fr_ctx* ctx, const char* where) {
   return FR_OK;
 }
 
+__global__ void k_status_reset(int* status) {
+  status[0] = 0;
+  status[1] = 0x7fffffff;
+}
+
 static int condense_impl(fr_ctx* ctx, int refine) {
-  int init[2] = {0, 0x7fffffff};
-  CK(cudaMemcpyAsync(ctx->status, init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
+  // (a kernel, not a copy from host memory: a pageable host-to-device copy would wait for the stream)
+  (hfr::count_launch(), k_status_reset<<<1, 1, 0, ctx->stream>>>(ctx->status));
+  CK(cudaGetLastError());
   CondArgs c;
   c.Eim = ctx->Eim;
   c.nA = ctx->nA;
@@ -812,8 +818,10 @@ static void cb_precond(void* c, const GmresState* st, int j, double* x, double* 
 
 // true_res: report the true final residual ||t - L du^|| / ||t|| (else the GMRES estimate, which
 // the Newton iteration does not need)
+// cond_status (host, nullable): receives the condensation status words, read back with the
+// GMRES result instead of at a synchronisation of their own
 static int gmres_impl(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* iters, double* final_rel,
-                      bool true_res = true) {
+                      bool true_res = true, int* cond_status = nullptr) {
   GmresOps ops;
   ops.ctx = ctx;
   ops.matvec = cb_matvec;
@@ -824,6 +832,10 @@ static int gmres_impl(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* i
   if (ctx->ntrace == 0) {
     if (iters) *iters = 0;
     if (final_rel) *final_rel = 0.0;
+    if (cond_status) {
+      CK(cudaMemcpyAsync(cond_status, ctx->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+    }
     return FR_OK;
   }
   const int ph = prof_begin(ctx, PH_GMRES);
@@ -850,9 +862,13 @@ static int gmres_impl(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* i
     fa.x_zero = 1;
     fa.true_res = true_res ? 1 : 0;
     grc = run_gmres_fused(fa, ctx->prec_bytes, ctx->gm_fused_grid, rtol, ctx->restart, maxit, &res, &timed_out,
-                          ctx->stream);
+                          ctx->stream, cond_status ? ctx->status : nullptr, cond_status);
   } else {
     grc = run_gmres(ops, ctx->gm, ctx->tg, duhat, rtol, ctx->restart, maxit, 4, &res, ctx->stream);
+    if (grc == 0 && cond_status) {
+      CK(cudaMemcpyAsync(cond_status, ctx->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+    }
   }
   prof_end(ctx, ph);
   if (grc != 0) return set_err(ctx, FR_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
@@ -1040,11 +1056,15 @@ extern "C" int imex_stage(fr_ctx* ctx, int stage, double dt, const double* u_n, 
     // the local solves are refined once, at the back-substitution (du = A^{-1}(r - B du^)); refining
     // x_r as well would not change the converged step
     if (!rc) rc = condense_impl(ctx, 0);
-    if (!rc) rc = check_status(ctx, "imex_stage: zero pivot in condensation");
     if (rc) return rc;
     int its = 0;
     double rel = 0.0;
-    rc = gmres_impl(ctx, ctx->duhat, gmres_rtol, gmres_maxit, &its, &rel, false);
+    int cst[2] = {0, 0};
+    rc = gmres_impl(ctx, ctx->duhat, gmres_rtol, gmres_maxit, &its, &rel, false, cst);
+    if (cst[0] & DEV_ERR_SINGULAR) {
+      CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), st));
+      return set_err(ctx, FR_ERR_SINGULAR, "imex_stage: zero pivot in condensation", cst[1]);
+    }
     gtot += its;
     if (rc && rc != FR_ERR_NOT_CONVERGED) return rc;
     rc = backsolve_impl(ctx, ctx->duhat, ctx->du, refine);

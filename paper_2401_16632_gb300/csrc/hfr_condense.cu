@@ -434,10 +434,18 @@ struct InvWShape {
   static constexpr int WPB = 4;             // elements per CTA
 };
 
+// Pivot key of a candidate: |value| with the low six mantissa bits replaced by 63 - row, so the
+// unsigned maximum over the warp (one redux.sync) picks the largest magnitude, ties (within 2^-17
+// relative, where the choice does not affect stability) going to the lowest row.  0 = no candidate.
+__device__ __forceinline__ unsigned inv_key(float v, int row, bool ok) {
+  return ok ? ((__float_as_uint(fabsf(v)) & ~63u) | (unsigned)(63 - row)) : 0u;
+}
+
 template <int NA>
 __global__ void __launch_bounds__(32 * InvWShape<NA>::WPB) k_inverse_warp(const __grid_constant__ CondArgs a) {
   using Sh = InvWShape<NA>;
   constexpr int RPT = Sh::RPT, QW = Sh::QW, NCP = Sh::NCP, WPB = Sh::WPB;
+  static_assert(NA <= 64 && QW >= 2, "one warp per element needs nA <= 64");
   __shared__ __align__(16) float s_pr[WPB][NCP + 4];
   __shared__ float s_pinv[WPB];
   __shared__ int s_step[WPB][NA];
@@ -459,39 +467,23 @@ __global__ void __launch_bounds__(32 * InvWShape<NA>::WPB) k_inverse_warp(const 
     }
   }
   if (lane < 4) pr[NCP + lane] = 0.f;
-  unsigned used = 0u;  // lane h == 0: bit s once row RPT q + s has been a pivot (or is padding)
+  unsigned used = 0u;  // bit s once row RPT q + s has been a pivot (or is padding)
 #pragma unroll
   for (int s = 0; s < RPT; ++s)
     if (RPT * q + s >= NA) used |= 1u << s;
   bool bad = false;
+  // search of the first pivot (column 0 is held by lane 0 of each quad)
+  auto search = [&]() {
+    unsigned key = 0u;
+#pragma unroll
+    for (int s = 0; s < RPT; ++s) key = max(key, inv_key(m[s][0], RPT * q + s, h == 0 && !(used >> s & 1u)));
+    return __reduce_max_sync(0xffffffffu, key);
+  };
+  unsigned kp = search();
   __syncwarp();
 #pragma unroll 1
   for (int c = 0; c < NA; ++c) {
-    float best = -1.f;
-    int bi = 0x7fffffff;
-    if (h == 0) {
-#pragma unroll
-      for (int s = 0; s < RPT; ++s) {
-        const float v = fabsf(m[s][0]);
-        if (!(used >> s & 1u) && v > best) {
-          best = v;
-          bi = RPT * q + s;
-        }
-      }
-    }
-#pragma unroll
-    for (int o = 16; o >= 4; o >>= 1) {
-      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ob > best || (ob == best && oi < bi)) {
-        best = ob;
-        bi = oi;
-      }
-    }
-    // lanes h != 0 carried -1 and join the quad-0 result of their quad through the butterfly above
-    // only across quads; fetch the winner from lane 0
-    best = __shfl_sync(0xffffffffu, best, 0);
-    const int p = __shfl_sync(0xffffffffu, bi, 0);
+    const int p = 63 - (int)(kp & 63u);
     const int gp = p / RPT, sp = p - RPT * gp;
     float nxt[RPT];
 #pragma unroll
@@ -507,14 +499,14 @@ __global__ void __launch_bounds__(32 * InvWShape<NA>::WPB) k_inverse_warp(const 
             s_pinv[w] = pv != 0.f ? 1.f / pv : 0.f;
             s_piv[w][p] = pv;
             s_step[w][p] = c;
-            used |= 1u << s;
           }
         }
       }
+      used |= 1u << sp;  // (read by lane 0 of the quad only)
     }
     if (lane == 0) {
       a.piv[(size_t)k * NA + c] = p;
-      if (!(best > 0.f)) bad = true;
+      if ((kp & ~63u) == 0u) bad = true;  // zero pivot
     }
     __syncwarp();
     const float pinv = s_pinv[w];
@@ -524,8 +516,15 @@ __global__ void __launch_bounds__(32 * InvWShape<NA>::WPB) k_inverse_warp(const 
       const float fs = (h == 0 && RPT * q + s != p) ? m[s][0] * pinv : 0.f;
       f[s] = __shfl_sync(0xffffffffu, fs, lane & ~3);
     }
+    // the next pivot column first, so that the next search overlaps the rest of the update
+    {
+      const float pj = pr[QW * h + 1];
 #pragma unroll
-    for (int j = 0; j < QW; ++j) {
+      for (int s = 0; s < RPT; ++s) m[s][0] = m[s][1] - f[s] * pj;
+    }
+    const unsigned kn = search();
+#pragma unroll
+    for (int j = 1; j < QW; ++j) {
       const float pj = pr[QW * h + j + 1];
 #pragma unroll
       for (int s = 0; s < RPT; ++s) {
@@ -537,6 +536,7 @@ __global__ void __launch_bounds__(32 * InvWShape<NA>::WPB) k_inverse_warp(const 
 #pragma unroll
       for (int s = 0; s < RPT; ++s) m[s][(NA - 1) % QW] = (RPT * q + s == p ? 1.f : 0.f) - f[s];
     }
+    kp = kn;
     __syncwarp();
   }
   if (lane == 0 && bad) {

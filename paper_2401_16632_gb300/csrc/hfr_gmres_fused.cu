@@ -736,7 +736,7 @@ int fused_gmres_grid(int prec_bytes, int nT, int bs) {
 }
 
 int run_gmres_fused(const FusedArgs& base, int prec_bytes, int grid, double rtol, int restart, int maxit,
-                    GmresResult* res, int* timed_out, cudaStream_t s) {
+                    GmresResult* res, int* timed_out, cudaStream_t s, const int* dev_status, int* host_status) {
   int occ = 0;
   const int bs = (int)(base.n / (size_t)base.ntrace);
   CycleFn fn = pick(prec_bytes, base.nT, bs, &occ);
@@ -747,7 +747,7 @@ int run_gmres_fused(const FusedArgs& base, int prec_bytes, int grid, double rtol
   a.rtol = rtol;
   if (cudaMemsetAsync(a.x, 0, a.n * sizeof(double), s) != cudaSuccess) return -1;
   int total = 0;
-  bool first = true;
+  bool first = true, first_cycle = true;
   for (;;) {
     a.m = m < maxit - total ? m : maxit - total;
     a.x_zero = first ? 1 : 0;
@@ -758,6 +758,10 @@ int run_gmres_fused(const FusedArgs& base, int prec_bytes, int grid, double rtol
     unsigned flags[2] = {0u, 0u};
     if (cudaMemcpyAsync(&hs, a.st, sizeof(GmresHead), cudaMemcpyDeviceToHost, s) != cudaSuccess) return -1;
     if (cudaMemcpyAsync(flags, a.bar, sizeof(flags), cudaMemcpyDeviceToHost, s) != cudaSuccess) return -1;
+    if (dev_status && first_cycle &&
+        cudaMemcpyAsync(host_status, dev_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return -1;
+    first_cycle = false;
     if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
     if (flags[1] != 0u) {
       *timed_out = 1;

@@ -81,9 +81,11 @@ struct FusedArgs {
 size_t fused_partial_doubles(int max_blocks);
 // CTAs of the cooperative launch (one per SM), 0 when the shape or the device does not allow it
 int fused_gmres_grid(int prec_bytes, int nT, int bs);
-// returns 0 (result in res; *timed_out = 1 if a grid barrier wait ran out) or -1 on a CUDA error
+// returns 0 (result in res; *timed_out = 1 if a grid barrier wait ran out) or -1 on a CUDA error.
+// dev_status (nullable): two device status words copied to host_status with the first cycle's result
 int run_gmres_fused(const FusedArgs& a, int prec_bytes, int grid, double rtol, int restart, int maxit,
-                    GmresResult* res, int* timed_out, cudaStream_t s);
+                    GmresResult* res, int* timed_out, cudaStream_t s, const int* dev_status = nullptr,
+                    int* host_status = nullptr);
 
 int run_gmres(const GmresOps& ops, const GmresBuffers& b, const double* t, double* x, double rtol, int restart,
               int maxit, int check_every, GmresResult* res, cudaStream_t s);
