@@ -111,9 +111,13 @@ def run_stage(ctx, dt, u_n, u_stage, uhat, uhat0, R_hist):
                           gmres_rtol=GMRES_RTOL, gmres_maxit=3000, refine=ctx.refine)
 
 
-def time_path(pkg, torch, w, precision, refine, steps, warmup, dev, l2buf):
+JAC_POLICY = {"every": 0, "once": 1}
+
+
+def time_path(pkg, torch, w, precision, refine, steps, warmup, dev, l2buf, jac="every"):
     ctx = pkg.Context(w.mesh, w.physics, precision=precision, tableau=pkg.FR_TAB_SDIRK2)
     ctx.refine = refine
+    ctx.imex_set_jacobian_policy(JAC_POLICY[jac])
     stream = torch.cuda.current_stream()
     u_n = torch.tensor(w.u0, device=dev)
     uhat0 = ctx.hfr_initial_trace(u_n)
@@ -292,6 +296,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--refine", type=int, default=0,
                     help="FP64 refinement sweeps of the local solves in the back-substitution")
+    ap.add_argument("--jacobian", default="every", choices=["every", "once"],
+                    help="re-linearise at every Newton iterate, or once per stage (chord iterations)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--paths", default="both", choices=["both", "mixed", "fp64"],
                     help="profiling aid: time only one precision path")
@@ -323,13 +329,14 @@ def main():
     if args.paths != "both":  # profiling aid: one path, no JSON contract line
         prec = pkg.FR_PREC_FP32 if args.paths == "mixed" else pkg.FR_PREC_FP64
         r = time_path(pkg, torch, w, prec, args.refine if args.paths == "mixed" else 0, args.steps, args.warmup,
-                      dev, l2buf)
+                      dev, l2buf, args.jacobian)
         print(json.dumps({"path": args.paths, "ms": r["ms"], "stats": r["stats"],
                           "phases_ms_total": r["profile"], "launches": r["launches"]}))
         return
     with ClockSampler(local) as clk:
-        mixed = time_path(pkg, torch, w, pkg.FR_PREC_FP32, args.refine, args.steps, args.warmup, dev, l2buf)
-        fp64 = time_path(pkg, torch, w, pkg.FR_PREC_FP64, 0, args.steps, args.warmup, dev, l2buf)
+        mixed = time_path(pkg, torch, w, pkg.FR_PREC_FP32, args.refine, args.steps, args.warmup, dev, l2buf,
+                          args.jacobian)
+        fp64 = time_path(pkg, torch, w, pkg.FR_PREC_FP64, 0, args.steps, args.warmup, dev, l2buf, args.jacobian)
     clocks = clk.summary()
     ms_mixed = float(np.mean(mixed["ms"]))
     ms_fp64 = float(np.mean(fp64["ms"]))
@@ -365,6 +372,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "implicit_dofs": dofs, "elements": w.mesh.nelem,
                    "newton_tol": NEWTON_TOL, "gmres_rtol": GMRES_RTOL, "refine_sweeps": args.refine,
+                   "jacobian": args.jacobian,
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "fp64": {"value": world * dofs / (ms_fp64 * 1e-3), "ms_per_step": ms_fp64, "dtype": "f64",
                  "newton_iterations": fp64["stats"]["newton_iterations"],

@@ -140,7 +140,16 @@ int hfr_condense(fr_ctx* ctx, int refine);
  * iters / final_rel (host, nullable): iterations and true final relative residual. */
 int hfr_trace_gmres(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* iters, double* final_rel);
 
-/* How hfr_trace_gmres (and imex_stage) run a restart cycle.  FR_GMRES_FUSED (the default where
+/* When imex_stage re-linearises.  FR_JAC_EVERY_NEWTON (default): element blocks, condensation and
+ * preconditioner at every Newton iterate (exact Newton on the blocks).  FR_JAC_ONCE_PER_STAGE:
+ * at the stage's first iterate only; later iterations are chord iterations that reuse the blocks,
+ * their factorisation, S_k, X_B and the preconditioner, and recompute only x_r = A^{-1} r,
+ * t_k = s - C x_r and t (the paper keeps its Jacobian for many steps; Sec. 5).  Both stop on the
+ * same FP64 Newton residual test.  FR_ERR_INVALID_ARG for another value. */
+enum fr_jacobian_policy { FR_JAC_EVERY_NEWTON = 0, FR_JAC_ONCE_PER_STAGE = 1 };
+int imex_set_jacobian_policy(fr_ctx* ctx, int policy);
+
+/* How hfr_trace_gmres (and imex_stage) run a restart cycle./* How hfr_trace_gmres (and imex_stage) run a restart cycle.  FR_GMRES_FUSED (the default where
  * available): the whole cycle -- preconditioner, mat-vecs, Gram-Schmidt, Givens rotations and the
  * solution update -- is one cooperative launch with one CTA per SM that meets at grid barriers;
  * available for trace blocks (nT, n nv) = (64,16), (80,20), (48,12) on devices with cooperative

@@ -30,6 +30,7 @@ FR_PREC_FP64, FR_PREC_FP32 = 0, 1
 FR_TAB_BE, FR_TAB_SDIRK2 = 0, 1
 FR_PHYS_ADVDIFF, FR_PHYS_NAVIER_STOKES = 0, 1
 FR_GMRES_MULTI, FR_GMRES_FUSED = 0, 1
+FR_JAC_EVERY_NEWTON, FR_JAC_ONCE_PER_STAGE = 0, 1
 EXPORT = {"A": 0, "B": 1, "C": 2, "D": 3, "S": 4, "XB": 5, "xr": 6, "t_k": 7, "r": 8, "s": 9, "t": 10, "Pinv": 11}
 
 # every symbol declared in include/hfr.h
@@ -42,6 +43,7 @@ ABI_SYMBOLS = [
     "hfr_local_jacobian",
     "hfr_condense",
     "hfr_trace_gmres",
+    "imex_set_jacobian_policy",
     "hfr_gmres_set_mode",
     "hfr_gmres_get_mode",
     "hfr_backsolve",
@@ -149,6 +151,7 @@ def load_library(path: str = LIB_PATH):
     lib.hfr_local_jacobian.argtypes = [vp, dp, dp, dp, ctypes.c_double]
     lib.hfr_condense.argtypes = [vp, ctypes.c_int]
     lib.hfr_trace_gmres.argtypes = [vp, dp, ctypes.c_double, ctypes.c_int, ip, ctypes.POINTER(ctypes.c_double)]
+    lib.imex_set_jacobian_policy.argtypes = [vp, ctypes.c_int]
     lib.hfr_gmres_set_mode.argtypes = [vp, ctypes.c_int]
     lib.hfr_gmres_get_mode.argtypes = [vp]
     lib.hfr_backsolve.argtypes = [vp, dp, dp, ctypes.c_int]
@@ -309,6 +312,9 @@ class Context:
         if check:
             self._check(rc)
         return duh, its.value, rel.value
+
+    def imex_set_jacobian_policy(self, policy: int):
+        self._check(self.lib.imex_set_jacobian_policy(self.h, int(policy)))
 
     def hfr_gmres_set_mode(self, mode: int):
         self._check(self.lib.hfr_gmres_set_mode(self.h, int(mode)))

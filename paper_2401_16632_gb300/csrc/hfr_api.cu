@@ -52,6 +52,7 @@ struct fr_ctx {
   // Krylov
   GmresBuffers gm;
   int gm_mode = 0;          // 0: multi-kernel cycle, 1: one cooperative launch per cycle
+  int jac_policy = 0;       // FR_JAC_EVERY_NEWTON or FR_JAC_ONCE_PER_STAGE
   int gm_fused_grid = 0;    // CTAs of the cooperative launch (0: not available)
   unsigned* gm_bar = nullptr;
   double *duhat = nullptr, *du = nullptr, *res_tmp = nullptr, *Ustar = nullptr, *red = nullptr;
@@ -789,6 +790,22 @@ static int condense_impl(fr_ctx* ctx, int refine) {
   return FR_OK;
 }
 
+// New right-hand sides with the blocks of an earlier condensation (chord Newton iterations):
+// x_r = A^{-1} r with the stored factorisation, t_k = s - C x_r, t = sum scatter(t_k).  S_k, X_B and
+// the face preconditioner are kept.
+static int condense_rhs_impl(fr_ctx* ctx) {
+  const size_t nrA = (size_t)ctx->Eim * ctx->nA;
+  int ph = prof_begin(ctx, PH_COND);
+  CK(cudaMemcpyAsync(ctx->xr, ctx->r, nrA * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(launch_lu_solve(ctx->prec_bytes, ctx->Eim, ctx->nA, ctx->nT, ctx->LU, ctx->piv, ctx->xr, ctx->stream));
+  CK(launch_rhs_condense(ctx->prec_bytes, ctx->Eim, ctx->nA, ctx->nT, ctx->C, ctx->xr, ctx->s, ctx->te, ctx->stream));
+  prof_end(ctx, ph);
+  ph = prof_begin(ctx, PH_PREC);
+  CK(launch_assemble_t(trace_args(ctx), ctx->te, ctx->tg, ctx->stream));
+  prof_end(ctx, ph);
+  return FR_OK;
+}
+
 extern "C" int hfr_condense(fr_ctx* ctx, int refine) {
   if (!ctx) return FR_ERR_INVALID_ARG;
   int rc = condense_impl(ctx, refine);
@@ -879,6 +896,13 @@ static int gmres_impl(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* i
   if (res.nan) return set_err(ctx, FR_ERR_DIVERGED, "hfr_trace_gmres: non-finite residual", -1, res.iterations);
   if (!res.converged && res.rel > rtol)
     return set_err(ctx, FR_ERR_NOT_CONVERGED, "hfr_trace_gmres: iteration limit", -1, res.iterations, res.rel);
+  return FR_OK;
+}
+
+extern "C" int imex_set_jacobian_policy(fr_ctx* ctx, int policy) {
+  if (!ctx || (policy != FR_JAC_EVERY_NEWTON && policy != FR_JAC_ONCE_PER_STAGE))
+    return set_err(ctx, FR_ERR_INVALID_ARG, "imex_set_jacobian_policy: bad argument");
+  ctx->jac_policy = policy;
   return FR_OK;
 }
 
@@ -1052,10 +1076,15 @@ extern "C" int imex_stage(fr_ctx* ctx, int stage, double dt, const double* u_n, 
       break;
     }
     if (it >= newton_maxit) break;
-    rc = jacobian_blocks(ctx, u_stage, uhat, adt);
-    // the local solves are refined once, at the back-substitution (du = A^{-1}(r - B du^)); refining
-    // x_r as well would not change the converged step
-    if (!rc) rc = condense_impl(ctx, 0);
+    if (it == 0 || ctx->jac_policy == FR_JAC_EVERY_NEWTON) {
+      rc = jacobian_blocks(ctx, u_stage, uhat, adt);
+      // the local solves are refined once, at the back-substitution (du = A^{-1}(r - B du^));
+      // refining x_r as well would not change the converged step
+      if (!rc) rc = condense_impl(ctx, 0);
+    } else {
+      // chord iteration: blocks, factors, S_k and preconditioner of the stage's first iterate
+      rc = condense_rhs_impl(ctx);
+    }
     if (rc) return rc;
     int its = 0;
     double rel = 0.0;

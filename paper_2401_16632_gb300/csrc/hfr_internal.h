@@ -113,6 +113,9 @@ cudaError_t launch_precond_apply(int prec_bytes, const TraceArgs& a, const doubl
                                  cudaStream_t st, const int* gate = nullptr, int gj = 0, const double* inv_h = nullptr,
                                  float* y32 = nullptr);
 cudaError_t launch_assemble_t(const TraceArgs& a, const double* te, double* t, cudaStream_t st);
+// t_k = s_k - C_k x_r for every implicit element (C in the block precision)
+cudaError_t launch_rhs_condense(int prec_bytes, int Eim, int nA, int nT, const void* C, const double* xr,
+                                const double* s, double* t, cudaStream_t st);
 cudaError_t launch_backsolve(int prec_bytes, const TraceArgs& a, int Eim, int nA, const void* XB, const double* xr,
                              const double* duhat, double* du, cudaStream_t st);
 

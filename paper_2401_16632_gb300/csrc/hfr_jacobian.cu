@@ -93,7 +93,7 @@ __device__ __forceinline__ void imp_face_flux(const PhysConst<R>& pp, bool visc,
 }
 
 template <int P, int PHYS, typename T>
-__global__ void __launch_bounds__(JAC_THREADS) k_jacobian(const __grid_constant__ RefOps ref,
+__global__ void __launch_bounds__(JAC_THREADS, sizeof(T) == 4 ? 4 : 1) k_jacobian(const __grid_constant__ RefOps ref,
                                                           const __grid_constant__ PhysParams pp,
                                                           const __grid_constant__ JacArgs a) {
   using W = JacWork<P, PHYS, T>;
@@ -358,31 +358,75 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobian(const __grid_constant_
       }
     }
     __syncthreads();
-    // 3. output columns: rows of dR (A or B) and of dg^k (C or D)
+    // 3. output columns.  Thread (s, v, part): seed s of the batch, variable v, and the grid rows
+    // bi = part (mod NPART) and faces f = part (mod NPART) of the element.  The 1D operators sit
+    // in registers; each flux tangent loaded from shared memory feeds several outputs:
+    //   dR(ai, bi) = -iJ [ sum_c M[ai][c] dF~x(c, bi) + M[bi][c] dF~y(ai, c)
+    //                      - dgL[ai] dFn(xi-, bi) + dgR[ai] dFn(xi+, bi)
+    //                      - dgL[bi] dFn(eta-, ai) + dgR[bi] dFn(eta+, ai) ]
+    //   dg^k(f, m) = w_m dFn(f, m)   (trace faces)
+    constexpr int NPART = JAC_THREADS / (JAC_SB * NV);
+    static_assert(NPART * JAC_SB * NV == JAC_THREADS, "phase 3 thread map");
     {
       const int s = tid % JAC_SB;
+      const int v = (tid / JAC_SB) % NV;
+      const int part = tid / (JAC_SB * NV);
       const int sd = s0 + s;
       if (sd < NSEED) {
-        for (int i = tid / JAC_SB; i < nA + nT; i += JAC_THREADS / JAC_SB) {
-          T val;
-          if (i < nA) {
-            const int pt = i / NV, v = i % NV, ai = pt % N, bi = pt / N;
-            T d = -w.rdgL[ai] * w.dFn[bi][v][s] + w.rdgR[ai] * w.dFn[N + bi][v][s] -
-                  w.rdgL[bi] * w.dFn[2 * N + ai][v][s] + w.rdgR[bi] * w.dFn[3 * N + ai][v][s];
+        T rM[N][N], dgl[N], dgr[N];
 #pragma unroll
-            for (int c = 0; c < N; ++c)
-              d += w.rM[ai][c] * w.dFt[c + N * bi][0][v][s] + w.rM[bi][c] * w.dFt[ai + N * c][1][v][s];
-            const T dR = -w.iJ[pt] * d;
-            if (sd < nA) {
-              val = (i == sd ? T(1) : T(0)) - adt * dR;
-              A[(size_t)i * nA + sd] = val;
-            } else {
-              B[(size_t)i * nT + (sd - nA)] = -adt * dR;
+        for (int x = 0; x < N; ++x) {
+          dgl[x] = w.rdgL[x];
+          dgr[x] = w.rdgR[x];
+#pragma unroll
+          for (int c = 0; c < N; ++c) rM[x][c] = w.rM[x][c];
+        }
+        T dyt[N][N];  // dF~y(ai, c) for all ai, c
+#pragma unroll
+        for (int ai = 0; ai < N; ++ai)
+#pragma unroll
+          for (int c = 0; c < N; ++c) dyt[ai][c] = w.dFt[ai + N * c][1][v][s];
+        T fym[N], fyp[N];  // eta-, eta+ face tangents at every ai
+#pragma unroll
+        for (int ai = 0; ai < N; ++ai) {
+          fym[ai] = w.dFn[2 * N + ai][v][s];
+          fyp[ai] = w.dFn[3 * N + ai][v][s];
+        }
+        constexpr int RPP = (N + NPART - 1) / NPART;  // rows per part
+        for (int rb = 0; rb < RPP; ++rb) {
+          const int bi = part + NPART * rb;
+          if (bi < N) {
+            T dxt[N], rMb[N];
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+              dxt[c] = w.dFt[c + N * bi][0][v][s];
+              rMb[c] = w.rM[bi][c];
             }
-          } else {
-            const int lr = i - nA;
-            const int f = lr / (N * NV), m = (lr / NV) % N, v = lr % NV;
-            val = w.kf[f] == FK_TRACE ? w.rw[m] * w.dFn[f * N + m][v][s] : T(0);
+            const T fxm = w.dFn[bi][v][s], fxp = w.dFn[N + bi][v][s];
+            const T dglb = w.rdgL[bi], dgrb = w.rdgR[bi];
+#pragma unroll
+            for (int ai = 0; ai < N; ++ai) {
+              T d = -dgl[ai] * fxm + dgr[ai] * fxp - dglb * fym[ai] + dgrb * fyp[ai];
+#pragma unroll
+              for (int c = 0; c < N; ++c) d += rM[ai][c] * dxt[c] + rMb[c] * dyt[ai][c];
+              const int pt = ai + N * bi;
+              const int i = pt * NV + v;
+              const T dR = -w.iJ[pt] * d;
+              if (sd < nA)
+                A[(size_t)i * nA + sd] = (i == sd ? T(1) : T(0)) - adt * dR;
+              else
+                B[(size_t)i * nT + (sd - nA)] = -adt * dR;
+            }
+          }
+        }
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          if (f % NPART != part) continue;
+          const bool tr = w.kf[f] == FK_TRACE;
+#pragma unroll
+          for (int m = 0; m < N; ++m) {
+            const int lr = (f * N + m) * NV + v;
+            const T val = tr ? w.rw[m] * w.dFn[f * N + m][v][s] : T(0);
             if (sd < nA)
               C[(size_t)lr * nA + sd] = val;
             else
@@ -400,6 +444,9 @@ static cudaError_t jac_impl(const RefOps& ref, const PhysParams& pp, const JacAr
   size_t smem = sizeof(JacWork<P, PHYS, T>);
   auto kern = k_jacobian<P, PHYS, T>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  // several CTAs per SM: ask for the largest shared-memory carveout
+  err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (err != cudaSuccess) return err;
   if (a.Eim == 0) return cudaSuccess;
   (hfr::count_launch(), kern<<<a.Eim, JAC_THREADS, smem, st>>>(ref, pp, a));

@@ -284,6 +284,38 @@ __global__ void k_backsolve(const __grid_constant__ TraceArgs a, int Eim, int nA
   }
 }
 
+// t_k = s_k - C_k x_r per element (the right-hand side of the condensed system for a new r with
+// unchanged blocks): one CTA per element, x_r staged in shared memory, one warp per row of C_k
+// with the lanes on consecutive columns.
+template <typename T>
+__global__ void k_rhs_condense(int Eim, int nA, int nT, const T* __restrict__ C, const double* __restrict__ xr,
+                               const double* __restrict__ s, double* __restrict__ t) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* xv = reinterpret_cast<T*>(smem_raw);
+  const int k = blockIdx.x;
+  if (k >= Eim) return;
+  for (int i = threadIdx.x; i < nA; i += blockDim.x) xv[i] = T(xr[(size_t)k * nA + i]);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const T* Ck = C + (size_t)k * nT * nA;
+  for (int j = warp; j < nT; j += nw) {
+    T p = T(0);
+    for (int i = lane; i < nA; i += 32) p += Ck[(size_t)j * nA + i] * xv[i];
+    p = warp_sum(p);
+    if (lane == 0) t[(size_t)k * nT + j] = s[(size_t)k * nT + j] - double(p);
+  }
+}
+
+cudaError_t launch_rhs_condense(int prec_bytes, int Eim, int nA, int nT, const void* C, const double* xr,
+                                const double* s, double* t, cudaStream_t st) {
+  if (Eim == 0) return cudaSuccess;
+  if (prec_bytes == 8)
+    (hfr::count_launch(), k_rhs_condense<double><<<Eim, 128, sizeof(double) * nA, st>>>(Eim, nA, nT, (const double*)C, xr, s, t));
+  else
+    (hfr::count_launch(), k_rhs_condense<float><<<Eim, 128, sizeof(float) * nA, st>>>(Eim, nA, nT, (const float*)C, xr, s, t));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_trace_matvec(int prec_bytes, const TraceArgs& a, const double* x, double* y, cudaStream_t st,
                                 const int* gate, int gj, const float* x32) {
   if (a.ntrace == 0) return cudaSuccess;

@@ -294,3 +294,29 @@ def test_gmres_single_launch_restarts_and_iteration_limit():
     with pytest.raises(pkg.HfrError) as ei:
         ctx.hfr_gmres_set_mode(7)
     assert ei.value.code == 1
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_chord_newton_stage_reaches_the_same_solution(precision):
+    """Jacobian once per stage (chord iterations reuse blocks, factors and S_k): linear instead of
+    quadratic Newton convergence, same FP64 residual test, same converged stage as the oracle's
+    exact Newton solve."""
+    prec = pkg.FR_PREC_FP64 if precision == "fp64" else pkg.FR_PREC_FP32
+    ctx, d, u0 = _setup("vortex_skew_p3", prec)
+    dt = 0.2
+    a11 = TABLEAUX["sdirk2"]["a"][0, 0]
+    U_o, uh_o, _ = newton_stage(d, u0, u0, d.initial_trace(u0), a11 * dt, tol=1e-13)
+    ctx.imex_set_jacobian_policy(pkg.FR_JAC_ONCE_PER_STAGE)
+    u = torch.tensor(u0, device=DEV)
+    uh = ctx.hfr_initial_trace(u)
+    R_hist = ctx.empty(3, *ctx.state_shape)
+    us = ctx.empty(*ctx.state_shape)
+    ctx.imex_stage(0, dt, u, us, uh, R_hist)
+    st = ctx.imex_stage(1, dt, u, us, uh, R_hist, newton_tol=1e-11, newton_maxit=60, gmres_rtol=1e-9,
+                        gmres_maxit=3000)
+    assert st["converged"] and st["newton_iterations"] >= 2
+    inc = np.abs(U_o - u0).max()
+    assert np.abs(us.cpu().numpy() - U_o).max() < 1e-8 * inc
+    with pytest.raises(pkg.HfrError) as ei:
+        ctx.imex_set_jacobian_policy(5)
+    assert ei.value.code == 1
