@@ -255,11 +255,15 @@ __global__ void k_sumsq_part(const double* __restrict__ a, size_t na, const doub
     partial[blockIdx.x] = t;
   }
 }
+// one warp: lane l sums partials l, l + 32, ... in order, then a fixed butterfly (deterministic)
 __global__ void k_sumsq_final(const double* __restrict__ partial, int nblk, double* out) {
-  if (threadIdx.x != 0) return;
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x >= 32) return;
   double t = 0.0;
-  for (int i = 0; i < nblk; ++i) t += partial[i];
-  *out = t;
+  for (int i = lane; i < nblk; i += 32) t += partial[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0) *out = t;
 }
 
 __global__ void k_apply_du(int Eim, int nA, const int* __restrict__ imp_idx, const double* __restrict__ du,

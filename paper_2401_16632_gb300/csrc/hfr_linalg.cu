@@ -257,31 +257,52 @@ __global__ void k_assemble_t(const __grid_constant__ TraceArgs a, const double* 
   tg[i] = s;
 }
 
-// du_k = x_r - X_B du^_k ; one warp per row, 4 warps per element
-template <typename T>
+// du_k = x_r - X_B du^_k: BE_EPB elements per CTA, one thread per row of X_B (the row read as
+// VW-wide vectors, all of a thread's loads in flight together), du^_k gathered into shared
+// memory once per element.
+constexpr int BE_EPB = 4;
+template <typename T, int VW>
 __global__ void k_backsolve(const __grid_constant__ TraceArgs a, int Eim, int nA, const T* __restrict__ XB,
                             const double* __restrict__ xr, const double* __restrict__ duhat,
                             double* __restrict__ du) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* xv = reinterpret_cast<T*>(smem_raw);
-  const int k = blockIdx.x;
-  if (k >= Eim) return;
   const int bs = a.n * a.nv, nT = a.nT;
-  for (int l = threadIdx.x; l < nT; l += blockDim.x) {
-    const int fp = l / bs;
-    const int tf = a.tr_of_c[k * 4 + fp];
-    xv[l] = tf >= 0 ? T(duhat[(size_t)tf * bs + (l - fp * bs)]) : T(0);
+  const int ld = (nT + 3) & ~3;
+  T* xv_all = reinterpret_cast<T*>(smem_raw);
+  const int per = blockDim.x / BE_EPB;  // threads per element (>= nA)
+  const int g = threadIdx.x / per, i = threadIdx.x % per;
+  const int k = blockIdx.x * BE_EPB + g;
+  T* xv = xv_all + (size_t)g * ld;
+  if (k < Eim) {
+    for (int l = i; l < nT; l += per) {
+      const int fp = l / bs;
+      const int tf = a.tr_of_c[k * 4 + fp];
+      xv[l] = tf >= 0 ? T(duhat[(size_t)tf * bs + (l - fp * bs)]) : T(0);
+    }
   }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nw = blockDim.x >> 5;
-  const T* X = XB + (size_t)k * nA * nT;
-  for (int i = warp; i < nA; i += nw) {
-    T p = T(0);
-    for (int l = lane; l < nT; l += 32) p += X[(size_t)i * nT + l] * xv[l];
-    p = warp_sum(p);
-    if (lane == 0) du[(size_t)k * nA + i] = xr[(size_t)k * nA + i] - double(p);
+  if (k >= Eim || i >= nA) return;
+  const T* X = XB + ((size_t)k * nA + i) * nT;
+  T p0 = T(0), p1 = T(0);
+  if constexpr (VW == 4) {
+#pragma unroll 8
+    for (int l = 0; l < nT; l += 8) {
+      const float4 x0 = __ldg(reinterpret_cast<const float4*>(X + l));
+      const float4 v0 = *reinterpret_cast<const float4*>(xv + l);
+      p0 += x0.x * v0.x + x0.y * v0.y + x0.z * v0.z + x0.w * v0.w;
+      if (l + 4 < nT) {
+        const float4 x1 = __ldg(reinterpret_cast<const float4*>(X + l + 4));
+        const float4 v1 = *reinterpret_cast<const float4*>(xv + l + 4);
+        p1 += x1.x * v1.x + x1.y * v1.y + x1.z * v1.z + x1.w * v1.w;
+      }
+    }
+  } else {
+    for (int l = 0; l < nT; l += 2) {
+      p0 += X[l] * xv[l];
+      if (l + 1 < nT) p1 += X[l + 1] * xv[l + 1];
+    }
   }
+  du[(size_t)k * nA + i] = xr[(size_t)k * nA + i] - double(p0 + p1);
 }
 
 // t_k = s_k - C_k x_r per element (the right-hand side of the condensed system for a new r with
@@ -381,10 +402,17 @@ cudaError_t launch_assemble_t(const TraceArgs& a, const double* te, double* t, c
 cudaError_t launch_backsolve(int prec_bytes, const TraceArgs& a, int Eim, int nA, const void* XB, const double* xr,
                              const double* duhat, double* du, cudaStream_t st) {
   if (Eim == 0) return cudaSuccess;
+  const int per = (nA + 31) & ~31;
+  const int threads = per * BE_EPB;
+  if (threads > 1024) return cudaErrorInvalidValue;
+  const int grid = (Eim + BE_EPB - 1) / BE_EPB;
+  const int ld = (a.nT + 3) & ~3;
   if (prec_bytes == 8)
-    (hfr::count_launch(), k_backsolve<double><<<Eim, 128, sizeof(double) * a.nT, st>>>(a, Eim, nA, (const double*)XB, xr, duhat, du));
+    (hfr::count_launch(), k_backsolve<double, 1><<<grid, threads, sizeof(double) * ld * BE_EPB, st>>>(a, Eim, nA, (const double*)XB, xr, duhat, du));
+  else if (a.nT % 8 == 0)
+    (hfr::count_launch(), k_backsolve<float, 4><<<grid, threads, sizeof(float) * ld * BE_EPB, st>>>(a, Eim, nA, (const float*)XB, xr, duhat, du));
   else
-    (hfr::count_launch(), k_backsolve<float><<<Eim, 128, sizeof(float) * a.nT, st>>>(a, Eim, nA, (const float*)XB, xr, duhat, du));
+    (hfr::count_launch(), k_backsolve<float, 1><<<grid, threads, sizeof(float) * ld * BE_EPB, st>>>(a, Eim, nA, (const float*)XB, xr, duhat, du));
   return cudaGetLastError();
 }
 
