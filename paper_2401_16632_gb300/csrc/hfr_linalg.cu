@@ -213,6 +213,83 @@ __global__ void k_precond_build(const __grid_constant__ TraceArgs a, T* __restri
   __syncwarp();
 }
 
+// The same inverse with the block in registers: one row per lane, W = 16 (bs <= 16, two faces per
+// warp) or 32 lanes per face, cycling columns (every step shifts the rows left by one and appends
+// the new column of the inverse, so the pivot column is always the first register and the bs
+// steps unroll into one straight-line body), rows kept unnormalised (one division per row at the
+// end).  Pivot: largest |a| among rows not yet used (ties: lowest row), by a butterfly over the
+// lanes of the face; the pivot row reaches every lane by shuffles.
+template <typename T, int BS>
+__global__ void __launch_bounds__(128) k_precond_build_reg(const __grid_constant__ TraceArgs a, T* __restrict__ Pinv,
+                                                           int* status) {
+  constexpr int W = BS <= 16 ? 16 : 32;
+  constexpr int FPW = 32 / W;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / W, r = lane % W;
+  const int t = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * FPW + sub;
+  const bool live = t < a.ntrace;
+  const bool row_ok = live && r < BS;
+  const int nT = a.nT;
+  const T* S = reinterpret_cast<const T*>(a.S);
+  T m[BS];
+#pragma unroll
+  for (int c = 0; c < BS; ++c) m[c] = T(0);
+  if (row_ok) {
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int e = a.sides[t * 4 + side * 2], f = a.sides[t * 4 + side * 2 + 1];
+      if (e >= 0) {
+        const T* row = S + ((size_t)e * nT + (size_t)f * BS + r) * nT + (size_t)f * BS;
+#pragma unroll
+        for (int c = 0; c < BS; ++c) m[c] += __ldg(row + c);
+      }
+    }
+  }
+  bool used = !row_ok;
+  int step = 0, pivs[BS];
+  T dpiv = T(1);
+  bool bad = false;
+#pragma unroll
+  for (int c = 0; c < BS; ++c) {
+    // argmax of |m_0| over the unused rows of this face (largest magnitude, lowest row on ties)
+    T best = used ? T(-1) : (m[0] < T(0) ? -m[0] : m[0]);
+    int bi = used ? 0x7fffffff : r;
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) {
+      const T ob = __shfl_xor_sync(0xffffffffu, best, o, W);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o, W);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
+    }
+    const int p = bi < BS ? bi : 0;
+    pivs[c] = p;
+    if (!(best > T(0))) bad = true;
+    T prow[BS];
+#pragma unroll
+    for (int j = 0; j < BS; ++j) prow[j] = __shfl_sync(0xffffffffu, m[j], p, W);
+    const bool isp = r == p;
+    const T pinv = prow[0] != T(0) ? T(1) / prow[0] : T(0);
+    const T fct = isp ? T(0) : m[0] * pinv;
+    if (isp) {
+      used = true;
+      step = c;
+      dpiv = m[0];
+    }
+#pragma unroll
+    for (int j = 1; j < BS; ++j) m[j - 1] = m[j] - fct * prow[j];
+    m[BS - 1] = (isp ? T(1) : T(0)) - fct;
+  }
+  if (bad && row_ok && r == 0) atomicOr(status, DEV_ERR_SINGULAR);
+  if (!row_ok) return;
+  // physical row r is row step of (P P_f)^{-1}; (P_f)^{-1}[step][pivs[c]] = m_c / pivot
+  const T sc = dpiv != T(0) ? T(1) / dpiv : T(0);
+  T* out = Pinv + (size_t)t * BS * BS + (size_t)step * BS;
+#pragma unroll
+  for (int c = 0; c < BS; ++c) out[pivs[c]] = m[c] * sc;
+}
+
 // y_f = Pinv_f x_f, one warp per face, lane = row.  With `hn` (GMRES), x is first normalised in
 // place, x <- x / *hn (the new Krylov vector), before it is preconditioned.
 template <typename T>
@@ -369,6 +446,20 @@ cudaError_t launch_precond_build(int prec_bytes, const TraceArgs& a, double* Pin
   if (a.ntrace == 0) return cudaSuccess;
   const int bs = a.n * a.nv;
   if (bs > 32) return cudaErrorInvalidValue;
+#define HFR_PB(BS_)                                                                                         \
+  if (bs == BS_) {                                                                                          \
+    constexpr int FPW = BS_ <= 16 ? 2 : 1;                                                                  \
+    const int grid = (a.ntrace + 4 * FPW - 1) / (4 * FPW);                                                  \
+    if (prec_bytes == 8)                                                                                    \
+      (hfr::count_launch(), k_precond_build_reg<double, BS_><<<grid, 128, 0, st>>>(a, Pinv, status));     \
+    else                                                                                                    \
+      (hfr::count_launch(), k_precond_build_reg<float, BS_><<<grid, 128, 0, st>>>(a, reinterpret_cast<float*>(Pinv), status)); \
+    return cudaGetLastError();                                                                              \
+  }
+  HFR_PB(16)
+  HFR_PB(12)
+  HFR_PB(20)
+#undef HFR_PB
   const int grid = (a.ntrace + PB_WARPS - 1) / PB_WARPS;
   if (prec_bytes == 8) {
     const size_t smem = sizeof(double) * (bs * bs + 3 * 32) * PB_WARPS;
