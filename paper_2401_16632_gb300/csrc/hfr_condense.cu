@@ -431,7 +431,7 @@ struct InvWShape {
   static constexpr int RPT = (NA + 7) / 8;  // rows per lane
   static constexpr int QW = (NA + 3) / 4;   // columns per lane
   static constexpr int NCP = 4 * QW;
-  static constexpr int WPB = 4;             // elements per CTA
+  static constexpr int WPB = 2;             // elements per CTA
 };
 
 // Pivot key of a candidate: |value| with the low six mantissa bits replaced by 63 - row, so the
@@ -442,7 +442,7 @@ __device__ __forceinline__ unsigned inv_key(float v, int row, bool ok) {
 }
 
 template <int NA>
-__global__ void __launch_bounds__(32 * InvWShape<NA>::WPB) k_inverse_warp(const __grid_constant__ CondArgs a) {
+__global__ void __launch_bounds__(32 * InvWShape<NA>::WPB, 5) k_inverse_warp(const __grid_constant__ CondArgs a) {
   using Sh = InvWShape<NA>;
   constexpr int RPT = Sh::RPT, QW = Sh::QW, NCP = Sh::NCP, WPB = Sh::WPB;
   static_assert(NA <= 64 && QW >= 2, "one warp per element needs nA <= 64");
