@@ -1,9 +1,10 @@
 """Implicit-stage throughput of the hybridized FR stage on GB300.
 
-One step = one hybridized implicit stage of the vortex64 workload (2D Navier-Stokes isentropic
-vortex, 64x64 quads, p = 3, 262,144 implicit DOF, SDIRK2 stage 1 at 10x the explicit CFL limit)
-solved from the standard initial guess to a relative Newton residual of 1e-8, through the C ABI
-(imex_stage stages 0 and 1).  The headline ``value`` is the mixed-precision path (FP32 element
+One step = one hybridized implicit stage of the workload (default vortex256: 2D Navier-Stokes
+isentropic vortex with 1e-3 seeded noise, 256x256 quads, p = 4, 6,553,600 implicit DOF, blocks
+100x100 / 80x80; or vortex64: 64x64 quads, p = 3, 262,144 DOF), SDIRK2 stage 1 at 10x the
+explicit CFL limit, solved from the standard initial guess to a relative Newton residual of 1e-8,
+through the C ABI (imex_stage stages 0 and 1).  The headline ``value`` is the mixed-precision path (FP32 element
 blocks, inverse, condensation, trace operator and Krylov basis; FP64 residuals, Newton updates,
 Hessenberg / Givens and the trace solution); the plain FP64 path is timed in the same run and
 reported beside it.  Both paths stop on the same FP64 Newton residual test.
@@ -28,8 +29,14 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "HFR implicit-stage DOF/s at 1e-8 resid: mixed-prec batched vs FP64, one GB300"
-WORKLOAD = ("vortex64: 2D compressible Navier-Stokes isentropic vortex, M=0.5, gamma=1.4, Re=1e4, periodic "
-            "[0,10]^2, 64x64 quads, p=3 (blocks 64x64), SDIRK2 stage 1 at 10x explicit CFL, Newton to 1e-8")
+WORKLOADS = {
+    "vortex256": ("vortex256: 2D compressible Navier-Stokes isentropic vortex, M=0.5, gamma=1.4, Re=1e4, periodic "
+                  "[0,10]^2, 256x256 quads, p=4 (blocks A 100x100, S 80x80), + U(-1e-3,1e-3) noise (seed 1234), "
+                  "SDIRK2 stage 1 at 10x explicit CFL, Newton to 1e-8"),
+    "vortex64": ("vortex64: 2D compressible Navier-Stokes isentropic vortex, M=0.5, gamma=1.4, Re=1e4, periodic "
+                 "[0,10]^2, 64x64 quads, p=3 (blocks 64x64), SDIRK2 stage 1 at 10x explicit CFL, Newton to 1e-8"),
+}
+PATCH = {"vortex256": 10, "vortex64": 16}  # oracle sample: PATCH x PATCH elements at the workload's spacing
 NEWTON_TOL = 1e-8
 GMRES_RTOL = 1e-4
 FP32_PEAK_PER_SM_CLK = 256.0  # 128 FP32 FMA lanes x 2 flops
@@ -183,35 +190,35 @@ def time_e2e(pkg, torch, ctx, w, steps, dev):
     return float(np.mean(times)), bi, bo
 
 
-def cpu_baseline(threads_note=True):
+def cpu_baseline(workload="vortex256"):
     """The FP64 oracle, as it stands, on a bounded sample of the same workload: the stage-1
-    Newton solve of the same vortex on a 16x16 patch at the same spacing, p and time step
-    (256 elements = 1/16 of the workload), direct trace solve."""
+    Newton solve of the same vortex on a PATCH x PATCH periodic patch at the workload's element
+    size, p and time step, direct trace solve."""
     from oracle.fr import Discretisation
     from oracle.physics import make_physics
     from oracle.stepping import TABLEAUX, newton_stage
     from workloads import make_config
+    from workloads.states import isentropic_vortex, sample_points
 
-    w = make_config("vortex", n=16, p=3)
-    # same element size and time step as the 64x64 workload on [0, 10]^2
-    w64 = make_config("vortex64")
-    scale = 10.0 / 64.0 / (10.0 / 16.0)
+    full = make_config(workload)
+    npatch = PATCH[workload]
+    nfull = int(round(np.sqrt(full.mesh.nelem)))
+    w = make_config("vortex", n=npatch, p=full.p)
+    scale = (10.0 / nfull) / (10.0 / npatch)
     mesh = w.mesh
     mesh.verts = mesh.verts * scale
-    from workloads.states import sample_points, isentropic_vortex
-
-    u0 = isentropic_vortex(sample_points(mesh, 3), center=(5.0 * scale, 5.0 * scale))
-    d = Discretisation(mesh, make_physics(w64.physics))
+    u0 = isentropic_vortex(sample_points(mesh, full.p), center=(5.0 * scale, 5.0 * scale))
+    d = Discretisation(mesh, make_physics(full.physics))
     a = TABLEAUX["sdirk2"]["a"][0, 0]
     t0 = time.perf_counter()
-    _, _, info = newton_stage(d, u0, u0, d.initial_trace(u0), a * w64.dt, tol=NEWTON_TOL)
+    _, _, info = newton_stage(d, u0, u0, d.initial_trace(u0), a * full.dt, tol=NEWTON_TOL)
     el = time.perf_counter() - t0
-    dofs = mesh.nelem * 16 * 4
+    dofs = mesh.nelem * (full.p + 1) ** 2 * 4
     cores = _threads()
-    return {"value": dofs / el, "unit": "DOF/s", "cores": cores, "kind": "oracle",
+    return {"value": dofs / el, "unit": "DOF/s", "cores": cores, "kind": "oracle", "dofs": dofs,
             "sample": f"stage-1 Newton solve (to 1e-8, {info['iterations']} iterations, direct trace solve) of the "
-                      f"vortex on a 16x16 patch at the workload's spacing, p=3, dt: {mesh.nelem} elements, "
-                      f"{dofs} DOF, {el:.1f} s"}
+                      f"vortex on a {npatch}x{npatch} periodic patch at the {workload} spacing, p={full.p}, same dt: "
+                      f"{mesh.nelem} elements, {dofs} DOF, {el:.1f} s"}
 
 
 def _threads():
@@ -224,20 +231,20 @@ def _threads():
         return os.cpu_count() or 1
 
 
-# DRAM bytes per launch (read + write) of the current kernels, from one ncu capture each of the
-# vortex64 stage (summaries under profiles/); None where the kernel changed after its capture
-NCU_TRAFFIC_BYTES = {
+# DRAM bytes per launch (read + write) of the current kernels, from one ncu capture each
+# (summaries under profiles/), per workload; None where not captured or the kernel changed since
+NCU_TRAFFIC_BYTES = {"vortex256": {}, "vortex64": {
     "k_inverse_warp": 69.08e6 + 13.06e6,
     "k_condense_products": 273.96e6 + 102.35e6,
     "k_gmres_cycle": 82.05e6 + 2.22e6,
     "k_jacobian": None,
-}
+}}
 
 
-def kernel_rooflines(prof, stats, w, peaks, clocks):
+def kernel_rooflines(prof, stats, w, peaks, clocks, workload):
     """Roofline of every single-kernel phase of the timed step, from the live CUDA-event phase
     timings (average launch duration), and the dominant one (largest total time).
-    Algorithmic work per launch (E elements, nA = nT = 64, face blocks bs = 16, ntrace = 2E faces,
+    Algorithmic work per launch (E elements, nA = 4 n^2, nT = 16 n, face blocks bs = 4 n, ntrace = 2E faces,
     n_t = 16 ntrace trace unknowns, k = GMRES iterations per solve):
       k_gmres_cycle       HBM: k (S_k blocks E nT^2 4 B + face inverses ntrace bs^2 4 B
                           + Krylov passes 4 (k/2 + 1) n_t 4 B + z, w 2 n_t 4 B)
@@ -245,10 +252,11 @@ def kernel_rooflines(prof, stats, w, peaks, clocks):
       k_condense_products ALU 2 (nA^2 (nT+1) + nT nA (nT+1)) flop per element, or HBM
                           4 (nA^2 + 2 nA nT + nT^2) B in + 4 (nA nT + nT^2) B out per element,
                           whichever fraction is higher
-      k_jacobian          ALU: (nA+nT)^2 (2n+4) 2 flop per element (n = 4)
+      k_jacobian          ALU: (nA+nT)^2 (2n+4) 2 flop per element (n = p + 1)
     """
     E = w.mesh.nelem
-    nA, nT, bs, n = 64, 64, 16, 4
+    n = w.p + 1
+    nA, nT, bs = 4 * n * n, 16 * n, 4 * n
     ntrace = 2 * E
     nt_u = ntrace * bs
     mhz = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
@@ -262,7 +270,7 @@ def kernel_rooflines(prof, stats, w, peaks, clocks):
         return ms, ms / max(cnt, 1)
 
     def entry(kern, bound, achieved, peak, unit, total_ms, avg_ms):
-        t = NCU_TRAFFIC_BYTES.get(kern)
+        t = NCU_TRAFFIC_BYTES.get(workload, {}).get(kern)
         return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
                 "traffic": t, "kernel": kern, "avg_launch_ms": avg_ms, "total_ms": total_ms,
                 "peak_source": ("MEASURED_PEAKS.json hbm_gbs" if unit == "GB/s"
@@ -272,7 +280,7 @@ def kernel_rooflines(prof, stats, w, peaks, clocks):
     per_it = E * nT * nT * 4 + ntrace * bs * bs * 4 + 4 * (its / 2 + 1) * nt_u * 4 + 2 * nt_u * 4
     out["gmres"] = entry("k_gmres_cycle", "hbm", per_it * its / (a * 1e-3) / 1e9, hbm_peak, "GB/s", tot, a)
     tot, a = avg("condense_factor")
-    out["condense_factor"] = entry("k_inverse_warp", "alu", E * 2.0 * nA**3 / (a * 1e-3) / 1e12, alu_peak,
+    out["condense_factor"] = entry("k_inverse_warp" if nA <= 64 else "k_inverse_q4", "alu", E * 2.0 * nA**3 / (a * 1e-3) / 1e12, alu_peak,
                                    "TFLOP/s", tot, a)
     tot, a = avg("condense_products")
     fl = E * 2.0 * (nA * nA * (nT + 1) + nT * nA * (nT + 1)) / (a * 1e-3) / 1e12
@@ -296,6 +304,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--refine", type=int, default=0,
                     help="FP64 refinement sweeps of the local solves in the back-substitution")
+    ap.add_argument("--workload", default="vortex256", choices=list(WORKLOADS))
     ap.add_argument("--jacobian", default="every", choices=["every", "once"],
                     help="re-linearise at every Newton iterate, or once per stage (chord iterations)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -324,7 +333,7 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=dev)
-    w = make_config("vortex64")
+    w = make_config(args.workload)
     l2buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB
     if args.paths != "both":  # profiling aid: one path, no JSON contract line
         prec = pkg.FR_PREC_FP32 if args.paths == "mixed" else pkg.FR_PREC_FP64
@@ -355,7 +364,7 @@ def main():
         e2e_ms, bi, bo = time_e2e(pkg, torch, mixed["ctx"], w, max(3, args.steps // 2), dev)
     peaks, peak_src = _peaks()
     pm = {k: v[0] for k, v in mixed["profile"].items()}
-    dom, kroofs = kernel_rooflines(mixed["profile"], mixed["stats"], w, peaks, clocks)
+    dom, kroofs = kernel_rooflines(mixed["profile"], mixed["stats"], w, peaks, clocks, args.workload)
     roof = {k: v for k, v in kroofs[dom].items() if k != "total_ms"}
     line = {
         "metric": METRIC,
@@ -370,7 +379,7 @@ def main():
         "vs_baseline": None,
         "dtype": "f32+f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "implicit_dofs": dofs, "elements": w.mesh.nelem,
+        "config": {"workload": WORKLOADS[args.workload], "implicit_dofs": dofs, "elements": w.mesh.nelem,
                    "newton_tol": NEWTON_TOL, "gmres_rtol": GMRES_RTOL, "refine_sweeps": args.refine,
                    "jacobian": args.jacobian,
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
@@ -396,7 +405,7 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            line["cpu_baseline"] = cpu_baseline()
+            line["cpu_baseline"] = cpu_baseline(args.workload)
         except Exception as exc:  # reported, never fatal
             line["cpu_baseline"] = {"error": str(exc)}
     if rank == 0:
@@ -413,7 +422,7 @@ def reference_arm(args, rank, world):
     vals = []
     info = None
     for i in range(args.warmup + args.steps):
-        cb = cpu_baseline()
+        cb = cpu_baseline(args.workload)
         if i >= args.warmup:
             vals.append(cb["value"])
             info = cb
@@ -425,14 +434,14 @@ def reference_arm(args, rank, world):
         "n_gpus": 0,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": 16 * 16 * 64 / v * 1e3,
+        "ms_per_step": info["dofs"] / v * 1e3,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
         "impl": "reference",
-        "config": {"workload": WORKLOAD, "sample": "16x16 patch at the workload's spacing"},
+        "config": {"workload": WORKLOADS[args.workload], "sample": info["sample"]},
         "cpu_baseline": {"value": v, "unit": "DOF/s", "cores": info["cores"], "kind": "oracle",
                          "sample": info["sample"]},
         "e2e": {"value": v, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
