@@ -560,6 +560,156 @@ __global__ void __launch_bounds__(32 * InvWShape<NA>::WPB, 5) k_inverse_warp(con
   }
 }
 
+// Kernel 1 for larger blocks (nA > 64): the same register-tiled cycling Gauss-Jordan over a few
+// warps, RPT rows per lane.  Each warp reduces its candidates' pivot keys with one redux.sync and
+// the warps combine them through shared memory; the next step's keys are formed as soon as the
+// next pivot column is updated, so two CTA barriers per step suffice (pivot row published; keys
+// of the next step published).
+template <int BITS>
+__device__ __forceinline__ unsigned inv_keyb(float v, int row, bool ok) {
+  constexpr unsigned MASK = (1u << BITS) - 1u;
+  return ok ? ((__float_as_uint(fabsf(v)) & ~MASK) | (MASK - (unsigned)row)) : 0u;
+}
+
+constexpr int INV_RPT_LARGE = 8;  // rows per lane of the multi-warp inverse
+
+template <int NA, int RPT>
+struct InvRShape {
+  static constexpr int QW = (NA + 3) / 4;
+  static constexpr int NCP = 4 * QW;
+  static constexpr int RG = (NA + RPT - 1) / RPT;
+  static constexpr int THREADS = ((4 * RG + 31) / 32) * 32;
+  static constexpr int NWARP = THREADS / 32;
+  static constexpr int BITS = NA <= 64 ? 6 : (NA <= 128 ? 7 : 8);
+};
+
+template <int NA, int RPT>
+__global__ void __launch_bounds__(InvRShape<NA, RPT>::THREADS) k_inverse_rq(const __grid_constant__ CondArgs a) {
+  using Sh = InvRShape<NA, RPT>;
+  constexpr int QW = Sh::QW, NCP = Sh::NCP, NWARP = Sh::NWARP, BITS = Sh::BITS;
+  constexpr unsigned MASK = (1u << BITS) - 1u;
+  static_assert(NA <= 256 && QW >= 2, "shape");
+  __shared__ __align__(16) float pr[2][NCP + 4];
+  __shared__ float s_pinv[2];
+  __shared__ unsigned s_key[2][NWARP];
+  __shared__ int s_step[NA];
+  __shared__ float s_piv[NA];
+  const int k = blockIdx.x;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int q = t >> 2, h = t & 3;
+  const float* gA = reinterpret_cast<const float*>(a.A) + (size_t)k * NA * NA;
+  float m[RPT][QW];
+#pragma unroll
+  for (int s = 0; s < RPT; ++s) {
+    const int r = RPT * q + s;
+#pragma unroll
+    for (int j = 0; j < QW; ++j) {
+      const int J = QW * h + j;
+      m[s][j] = (r < NA && J < NA) ? __ldg(gA + (size_t)r * NA + J) : 0.f;
+    }
+  }
+  if (t < 8) pr[t >> 2][NCP + (t & 3)] = 0.f;
+  unsigned used = 0u;
+#pragma unroll
+  for (int s = 0; s < RPT; ++s)
+    if (RPT * q + s >= NA) used |= 1u << s;
+  bool bad = false;
+  auto warp_key = [&]() {
+    unsigned key = 0u;
+#pragma unroll
+    for (int s = 0; s < RPT; ++s)
+      key = max(key, inv_keyb<BITS>(m[s][0], RPT * q + s, h == 0 && !(used >> s & 1u)));
+    return __reduce_max_sync(0xffffffffu, key);
+  };
+  {
+    const unsigned wk = warp_key();
+    if (lane == 0) s_key[0][wid] = wk;
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int c = 0; c < NA; ++c) {
+    const int buf = c & 1;
+    unsigned kp = s_key[buf][0];
+#pragma unroll
+    for (int w2 = 1; w2 < NWARP; ++w2) kp = max(kp, s_key[buf][w2]);
+    const int p = (int)(MASK - (kp & MASK));
+    const int gp = p / RPT, sp = p - RPT * gp;
+    float nxt[RPT];
+#pragma unroll
+    for (int s = 0; s < RPT; ++s) nxt[s] = __shfl_down_sync(0xffffffffu, m[s][0], 1);
+    if (q == gp) {
+#pragma unroll
+      for (int s = 0; s < RPT; ++s) {
+        if (s == sp) {
+#pragma unroll
+          for (int j = 0; j < QW; ++j) pr[buf][QW * h + j] = m[s][j];
+          if (h == 0) {
+            const float pv = m[s][0];
+            s_pinv[buf] = pv != 0.f ? 1.f / pv : 0.f;
+            s_piv[p] = pv;
+            s_step[p] = c;
+          }
+        }
+      }
+      used |= 1u << sp;
+    }
+    if (t == 0) {
+      a.piv[(size_t)k * NA + c] = p;
+      if ((kp & ~MASK) == 0u) bad = true;  // zero pivot
+    }
+    __syncthreads();
+    const float pinv = s_pinv[buf];
+    float f[RPT];
+#pragma unroll
+    for (int s = 0; s < RPT; ++s) {
+      const float fs = (h == 0 && RPT * q + s != p) ? m[s][0] * pinv : 0.f;
+      f[s] = __shfl_sync(0xffffffffu, fs, lane & ~3);
+    }
+    {
+      const float pj = pr[buf][QW * h + 1];
+#pragma unroll
+      for (int s = 0; s < RPT; ++s) m[s][0] = m[s][1] - f[s] * pj;
+    }
+    {
+      const unsigned wk = warp_key();
+      if (lane == 0) s_key[buf ^ 1][wid] = wk;
+    }
+#pragma unroll
+    for (int j = 1; j < QW; ++j) {
+      const float pj = pr[buf][QW * h + j + 1];
+#pragma unroll
+      for (int s = 0; s < RPT; ++s) {
+        const float old = j < QW - 1 ? m[s][j + 1] : (h < 3 ? nxt[s] : 0.f);
+        m[s][j] = old - f[s] * pj;
+      }
+    }
+    if (h == (NA - 1) / QW) {
+#pragma unroll
+      for (int s = 0; s < RPT; ++s) m[s][(NA - 1) % QW] = (RPT * q + s == p ? 1.f : 0.f) - f[s];
+    }
+    __syncthreads();
+  }
+  if (t == 0 && bad) {
+    atomicOr(a.status, DEV_ERR_SINGULAR);
+    atomicMin(a.status + 1, k);
+  }
+  float* gInv = reinterpret_cast<float*>(a.LU) + (size_t)k * NA * NA;
+#pragma unroll
+  for (int s = 0; s < RPT; ++s) {
+    const int r = RPT * q + s;
+    if (r < NA) {
+      const int lr = s_step[r];
+      const float pv = s_piv[r];
+      const float sc = pv != 0.f ? 1.f / pv : 0.f;
+#pragma unroll
+      for (int j = 0; j < QW; ++j) {
+        const int J = QW * h + j;
+        if (J < NA) gInv[(size_t)J * NA + lr] = m[s][j] * sc;  // ((PA)^{-1})^T
+      }
+    }
+  }
+}
+
 template <int NA, int NT>
 struct ProdShape {
   static constexpr int TI = (NA + 7) / 8;  // row tiles of X
@@ -738,7 +888,8 @@ static cudaError_t cond_two_kernel(const CondArgs& a, cudaStream_t st, int part)
       constexpr int WPB = InvWShape<NA>::WPB;
       (hfr::count_launch(), k_inverse_warp<NA><<<(a.Eim + WPB - 1) / WPB, 32 * WPB, 0, st>>>(a));
     } else {
-      (hfr::count_launch(), k_inverse_q4<NA><<<a.Eim, InvShape<NA>::THREADS, 0, st>>>(a));
+      constexpr int RPT = INV_RPT_LARGE;
+      (hfr::count_launch(), k_inverse_rq<NA, RPT><<<a.Eim, InvRShape<NA, RPT>::THREADS, 0, st>>>(a));
     }
     return cudaGetLastError();
   }

@@ -146,11 +146,20 @@ __device__ void pg_block_dots(PGShared<T>& sh, const T* V, size_t n, int nd, con
     T acc[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) acc[q] = T(0);
-    for (size_t x = x0 + threadIdx.x; x < x1; x += PG_THREADS) {
-      const T wx = w[x];
+    // two entries per iteration: 34 independent loads in flight per thread
+    for (size_t xa = x0 + threadIdx.x; xa < x1; xa += 2 * PG_THREADS) {
+      const size_t xb = xa + PG_THREADS;
+      const bool okb = xb < x1;
+      const T wa = w[xa];
+      const T wb = okb ? w[xb] : T(0);
+      const size_t xbs = okb ? xb : xa;
 #pragma unroll
       for (int q = 0; q < 16; ++q)
-        if (c0 + q < nd) acc[q] += V[(size_t)(c0 + q) * n + x] * wx;
+        if (c0 + q < nd) {
+          const T va = V[(size_t)(c0 + q) * n + xa];
+          const T vb = V[(size_t)(c0 + q) * n + xbs];
+          acc[q] += va * wa + vb * wb;
+        }
     }
     const T s = pg_scatter16(acc, lane);
     const int vi = c0 + (lane >> 1);
@@ -419,22 +428,49 @@ __device__ void pg_precond(const FusedArgs& a, const T* vj, int fb0, int fb1) {
   }
 }
 
+// dst[x] = (dst[x] - sum_{i<cnt} c_i V_i[x]) * scale over the entries x0 + tid0 + m nthreads of this
+// thread; four entries per iteration and two basis vectors per inner step keep eight independent
+// loads in flight per thread (the basis of a large system streams from HBM)
+template <typename T>
+__device__ __forceinline__ void pg_axpy_multi(const T* V, size_t n, const T* c, int cnt, T* dst, T scale,
+                                              size_t x0, size_t x1, int tid0, int nthreads) {
+  const size_t st = (size_t)nthreads;
+  for (size_t xb = x0 + tid0; xb < x1; xb += 4 * st) {
+    size_t xs[4];
+    bool ok[4];
+    T sacc[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      xs[u] = xb + u * st;
+      ok[u] = xs[u] < x1;
+      if (!ok[u]) xs[u] = xb;
+      sacc[u] = T(0);
+    }
+    int i = 0;
+    for (; i + 2 <= cnt; i += 2) {
+      const T ca = c[i], cb = c[i + 1];
+      const T* Va = V + (size_t)i * n;
+      const T* Vb = Va + n;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) sacc[u] += ca * Va[xs[u]] + cb * Vb[xs[u]];
+    }
+    if (i < cnt) {
+      const T ca = c[i];
+      const T* Va = V + (size_t)i * n;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) sacc[u] += ca * Va[xs[u]];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (ok[u]) dst[xs[u]] = (dst[xs[u]] - sacc[u]) * scale;
+  }
+}
+
 // v_j <- (v_j - sum_{i<jc} c_i V_i) * inv over this CTA's entries, by warps 1.. only (jc = 0: scale)
 template <typename T>
 __device__ void pg_finish(const T* V, size_t n, const T* c, int jc, T inv, T* vj, size_t x0, size_t x1) {
   if (threadIdx.x < 32) return;
-  for (size_t x = x0 + threadIdx.x - 32; x < x1; x += PG_THREADS - 32) {
-    T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-    int i = 0;
-    for (; i + 4 <= jc; i += 4) {
-      s0 += c[i] * V[(size_t)i * n + x];
-      s1 += c[i + 1] * V[(size_t)(i + 1) * n + x];
-      s2 += c[i + 2] * V[(size_t)(i + 2) * n + x];
-      s3 += c[i + 3] * V[(size_t)(i + 3) * n + x];
-    }
-    for (; i < jc; ++i) s0 += c[i] * V[(size_t)i * n + x];
-    vj[x] = (vj[x] - ((s0 + s1) + (s2 + s3))) * inv;
-  }
+  pg_axpy_multi(V, n, c, jc, vj, inv, x0, x1, (int)threadIdx.x - 32, PG_THREADS - 32);
 }
 
 // named barrier of warps 1 .. PG_WARPS-1 (warp 0 is busy with the Givens update)
@@ -442,46 +478,35 @@ __device__ __forceinline__ void pg_sync_workers() {
   asm volatile("bar.sync 1, %0;" ::"n"(PG_THREADS - 32) : "memory");
 }
 
-// x_f += P_f^{-1} (sum_{i<k} y_i V_i)_f, one warp per face (vector precision, added to FP64 x)
+// x_f += P_f^{-1} (sum_{i<k} y_i V_i)_f: first u = V y over this CTA's entries into the z buffer
+// (free at the end of the cycle; a streaming pass with many loads in flight), then P_f^{-1} u_f in
+// the vector precision added to the FP64 solution, one warp per face
 template <typename T, int BS>
 __device__ void pg_update_x(const FusedArgs& a, const PGShared<T>& sh, const T* V, int k, int fb0, int fb1) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const T* P = reinterpret_cast<const T*>(a.Pinv);
+  T* u = reinterpret_cast<T*>(a.z);
+  const size_t x0 = (size_t)fb0 * BS, x1 = (size_t)fb1 * BS;
+  for (size_t x = x0 + threadIdx.x; x < x1; x += PG_THREADS) u[x] = T(0);
+  __syncthreads();
+  pg_axpy_multi(V, a.n, sh.yT, k, u, T(-1), x0, x1, (int)threadIdx.x, PG_THREADS);
+  __syncthreads();
   const int r = lane < BS ? lane : 0;
   for (int f = fb0 + wid; f < fb1; f += PG_WARPS) {
     const size_t ix = (size_t)f * BS + r;
-    T u0 = T(0), u1 = T(0);
-    int i = 0;
-    for (; i + 1 < k; i += 2) {
-      u0 += sh.yT[i] * V[(size_t)i * a.n + ix];
-      u1 += sh.yT[i + 1] * V[(size_t)(i + 1) * a.n + ix];
-    }
-    if (i < k) u0 += sh.yT[i] * V[(size_t)i * a.n + ix];
-    const T u = lane < BS ? u0 + u1 : T(0);
+    const T uv = lane < BS ? u[ix] : T(0);
     T row[BS];
     pg_prow<T, BS>(P, f, r, row);
     T acc = T(0);
 #pragma unroll
-    for (int c = 0; c < BS; ++c) acc += row[c] * __shfl_sync(0xffffffffu, u, c);
+    for (int c = 0; c < BS; ++c) acc += row[c] * __shfl_sync(0xffffffffu, uv, c);
     if (lane < BS) a.x[ix] += double(acc);
   }
 }
 
-// w -= sum_{i<=j} c_i V_i over this thread's entries (c in the vector precision)
 template <typename T>
 __device__ __forceinline__ void pg_subtract(const T* V, size_t n, const T* c, int j, T* w, size_t x0, size_t x1) {
-  for (size_t x = x0 + threadIdx.x; x < x1; x += PG_THREADS) {
-    T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-    int i = 0;
-    for (; i + 3 <= j; i += 4) {
-      s0 += c[i] * V[(size_t)i * n + x];
-      s1 += c[i + 1] * V[(size_t)(i + 1) * n + x];
-      s2 += c[i + 2] * V[(size_t)(i + 2) * n + x];
-      s3 += c[i + 3] * V[(size_t)(i + 3) * n + x];
-    }
-    for (; i <= j; ++i) s0 += c[i] * V[(size_t)i * n + x];
-    w[x] = w[x] - ((s0 + s1) + (s2 + s3));
-  }
+  pg_axpy_multi(V, n, c, j + 1, w, T(1), x0, x1, (int)threadIdx.x, PG_THREADS);
 }
 
 // Givens update of Hessenberg column j (sh.hc[0..j+1]), FP64; decides the end of the cycle
