@@ -445,7 +445,7 @@ template <int NA>
 __global__ void __launch_bounds__(32 * InvWShape<NA>::WPB, 5) k_inverse_warp(const __grid_constant__ CondArgs a) {
   using Sh = InvWShape<NA>;
   constexpr int RPT = Sh::RPT, QW = Sh::QW, NCP = Sh::NCP, WPB = Sh::WPB;
-  static_assert(NA <= 64 && QW >= 2, "one warp per element needs nA <= 64");
+  static_assert(NA <= 64 && QW >= 2 && NA == 4 * QW, "one warp per element needs nA <= 64, nA % 4 == 0");
   __shared__ __align__(16) float s_pr[WPB][NCP + 4];
   __shared__ float s_pinv[WPB];
   __shared__ int s_step[WPB][NA];
@@ -466,7 +466,8 @@ __global__ void __launch_bounds__(32 * InvWShape<NA>::WPB, 5) k_inverse_warp(con
       m[s][j] = (r < NA && J < NA) ? __ldg(gA + (size_t)r * NA + J) : 0.f;
     }
   }
-  if (lane < 4) pr[NCP + lane] = 0.f;
+  // pr[NCP] = 1: lane 3's last column slot receives the new column of the inverse in the shift
+  if (lane < 4) pr[NCP + lane] = lane == 0 ? 1.f : 0.f;
   unsigned used = 0u;  // bit s once row RPT q + s has been a pivot (or is padding)
 #pragma unroll
   for (int s = 0; s < RPT; ++s)
@@ -528,13 +529,9 @@ __global__ void __launch_bounds__(32 * InvWShape<NA>::WPB, 5) k_inverse_warp(con
       const float pj = pr[QW * h + j + 1];
 #pragma unroll
       for (int s = 0; s < RPT; ++s) {
-        const float old = j < QW - 1 ? m[s][j + 1] : (h < 3 ? nxt[s] : 0.f);
+        const float old = j < QW - 1 ? m[s][j + 1] : (h < 3 ? nxt[s] : (RPT * q + s == p ? 1.f : 0.f));
         m[s][j] = old - f[s] * pj;
       }
-    }
-    if (h == (NA - 1) / QW) {
-#pragma unroll
-      for (int s = 0; s < RPT; ++s) m[s][(NA - 1) % QW] = (RPT * q + s == p ? 1.f : 0.f) - f[s];
     }
     kp = kn;
     __syncwarp();
@@ -588,7 +585,7 @@ __global__ void __launch_bounds__(InvRShape<NA, RPT>::THREADS) k_inverse_rq(cons
   using Sh = InvRShape<NA, RPT>;
   constexpr int QW = Sh::QW, NCP = Sh::NCP, NWARP = Sh::NWARP, BITS = Sh::BITS;
   constexpr unsigned MASK = (1u << BITS) - 1u;
-  static_assert(NA <= 256 && QW >= 2, "shape");
+  static_assert(NA <= 256 && QW >= 2 && NA == 4 * QW, "shape");
   __shared__ __align__(16) float pr[2][NCP + 4];
   __shared__ float s_pinv[2];
   __shared__ unsigned s_key[2][NWARP];
@@ -608,7 +605,9 @@ __global__ void __launch_bounds__(InvRShape<NA, RPT>::THREADS) k_inverse_rq(cons
       m[s][j] = (r < NA && J < NA) ? __ldg(gA + (size_t)r * NA + J) : 0.f;
     }
   }
-  if (t < 8) pr[t >> 2][NCP + (t & 3)] = 0.f;
+  // pr[NCP] = 1: the last column slot of lane 3 then receives [pivot row] - f, the new column of
+  // the inverse (nA = 4 QW), inside the shift itself
+  if (t < 8) pr[t >> 2][NCP + (t & 3)] = (t & 3) == 0 ? 1.f : 0.f;
   unsigned used = 0u;
 #pragma unroll
   for (int s = 0; s < RPT; ++s)
@@ -679,13 +678,9 @@ __global__ void __launch_bounds__(InvRShape<NA, RPT>::THREADS) k_inverse_rq(cons
       const float pj = pr[buf][QW * h + j + 1];
 #pragma unroll
       for (int s = 0; s < RPT; ++s) {
-        const float old = j < QW - 1 ? m[s][j + 1] : (h < 3 ? nxt[s] : 0.f);
+        const float old = j < QW - 1 ? m[s][j + 1] : (h < 3 ? nxt[s] : (RPT * q + s == p ? 1.f : 0.f));
         m[s][j] = old - f[s] * pj;
       }
-    }
-    if (h == (NA - 1) / QW) {
-#pragma unroll
-      for (int s = 0; s < RPT; ++s) m[s][(NA - 1) % QW] = (RPT * q + s == p ? 1.f : 0.f) - f[s];
     }
     __syncthreads();
   }
