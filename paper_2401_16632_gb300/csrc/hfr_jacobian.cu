@@ -93,7 +93,7 @@ __device__ __forceinline__ void imp_face_flux(const PhysConst<R>& pp, bool visc,
 }
 
 template <int P, int PHYS, typename T>
-__global__ void __launch_bounds__(JAC_THREADS, sizeof(T) == 4 ? 4 : 1) k_jacobian(const __grid_constant__ RefOps ref,
+__global__ void __launch_bounds__(JAC_THREADS, sizeof(T) == 4 ? (P <= 3 ? 4 : (P == 4 ? 3 : 2)) : 1) k_jacobian(const __grid_constant__ RefOps ref,
                                                           const __grid_constant__ PhysParams pp,
                                                           const __grid_constant__ JacArgs a) {
   using W = JacWork<P, PHYS, T>;
@@ -359,8 +359,9 @@ __global__ void __launch_bounds__(JAC_THREADS, sizeof(T) == 4 ? 4 : 1) k_jacobia
     }
     __syncthreads();
     // 3. output columns.  Thread (s, v, part): seed s of the batch, variable v, and the grid rows
-    // bi = part (mod NPART) and faces f = part (mod NPART) of the element.  The 1D operators sit
-    // in registers; each flux tangent loaded from shared memory feeds several outputs:
+    // bi = part (mod NPART) and faces f = part (mod NPART) of the element.  The y-direction flux
+    // tangents of the element sit in registers; each tangent loaded from shared memory feeds
+    // several outputs (the 1D operators are shared-memory broadcasts):
     //   dR(ai, bi) = -iJ [ sum_c M[ai][c] dF~x(c, bi) + M[bi][c] dF~y(ai, c)
     //                      - dgL[ai] dFn(xi-, bi) + dgR[ai] dFn(xi+, bi)
     //                      - dgL[bi] dFn(eta-, ai) + dgR[bi] dFn(eta+, ai) ]
@@ -373,13 +374,11 @@ __global__ void __launch_bounds__(JAC_THREADS, sizeof(T) == 4 ? 4 : 1) k_jacobia
       const int part = tid / (JAC_SB * NV);
       const int sd = s0 + s;
       if (sd < NSEED) {
-        T rM[N][N], dgl[N], dgr[N];
+        T dgl[N], dgr[N];
 #pragma unroll
         for (int x = 0; x < N; ++x) {
           dgl[x] = w.rdgL[x];
           dgr[x] = w.rdgR[x];
-#pragma unroll
-          for (int c = 0; c < N; ++c) rM[x][c] = w.rM[x][c];
         }
         T dyt[N][N];  // dF~y(ai, c) for all ai, c
 #pragma unroll
@@ -408,7 +407,7 @@ __global__ void __launch_bounds__(JAC_THREADS, sizeof(T) == 4 ? 4 : 1) k_jacobia
             for (int ai = 0; ai < N; ++ai) {
               T d = -dgl[ai] * fxm + dgr[ai] * fxp - dglb * fym[ai] + dgrb * fyp[ai];
 #pragma unroll
-              for (int c = 0; c < N; ++c) d += rM[ai][c] * dxt[c] + rMb[c] * dyt[ai][c];
+              for (int c = 0; c < N; ++c) d += w.rM[ai][c] * dxt[c] + rMb[c] * dyt[ai][c];
               const int pt = ai + N * bi;
               const int i = pt * NV + v;
               const T dR = -w.iJ[pt] * d;
