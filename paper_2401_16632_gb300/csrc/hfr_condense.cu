@@ -785,8 +785,8 @@ __global__ void __launch_bounds__(ProdShape<NA, NT>::THREADS) k_condense_product
     for (int c = 0; c < NA; ++c) {
       const float4 w0 = *reinterpret_cast<const float4*>(W + c * LDW + 8 * ti);
       const float4 w1 = *reinterpret_cast<const float4*>(W + c * LDW + 8 * ti + 4);
-      const float4 b0 = *reinterpret_cast<const float4*>(Bs + c * LDB + 8 * tj);
-      const float4 b1 = *reinterpret_cast<const float4*>(Bs + c * LDB + 8 * tj + 4);
+      const float4 b0 = *reinterpret_cast<const float4*>(Bs + c * LDB + 4 * tj);
+      const float4 b1 = *reinterpret_cast<const float4*>(Bs + c * LDB + NT / 2 + 4 * tj);
       const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
       const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -811,10 +811,10 @@ __global__ void __launch_bounds__(ProdShape<NA, NT>::THREADS) k_condense_product
       if (i < NA) {
         const float4 x0 = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
         const float4 x1 = make_float4(acc[u][4], acc[u][5], acc[u][6], acc[u][7]);
-        reinterpret_cast<float4*>(gXB + (size_t)i * NT + 8 * tj)[0] = x0;
-        reinterpret_cast<float4*>(gXB + (size_t)i * NT + 8 * tj)[1] = x1;
-        *reinterpret_cast<float4*>(Bs + i * LDB + 8 * tj) = x0;
-        *reinterpret_cast<float4*>(Bs + i * LDB + 8 * tj + 4) = x1;
+        *reinterpret_cast<float4*>(gXB + (size_t)i * NT + 4 * tj) = x0;
+        *reinterpret_cast<float4*>(gXB + (size_t)i * NT + NT / 2 + 4 * tj) = x1;
+        *reinterpret_cast<float4*>(Bs + i * LDB + 4 * tj) = x0;
+        *reinterpret_cast<float4*>(Bs + i * LDB + NT / 2 + 4 * tj) = x1;
       }
     }
   }
@@ -846,8 +846,8 @@ __global__ void __launch_bounds__(ProdShape<NA, NT>::THREADS) k_condense_product
     for (int l = 0; l < NA; ++l) {
       const float4 c0 = *reinterpret_cast<const float4*>(W + l * LDW + 8 * si);
       const float4 c1 = *reinterpret_cast<const float4*>(W + l * LDW + 8 * si + 4);
-      const float4 x0 = *reinterpret_cast<const float4*>(Bs + l * LDB + 8 * sj);
-      const float4 x1 = *reinterpret_cast<const float4*>(Bs + l * LDB + 8 * sj + 4);
+      const float4 x0 = *reinterpret_cast<const float4*>(Bs + l * LDB + 4 * sj);
+      const float4 x1 = *reinterpret_cast<const float4*>(Bs + l * LDB + NT / 2 + 4 * sj);
       const float cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
       const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
 #pragma unroll
@@ -858,12 +858,12 @@ __global__ void __launch_bounds__(ProdShape<NA, NT>::THREADS) k_condense_product
     float* gS = reinterpret_cast<float*>(a.S) + (size_t)k * NT * NT;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const size_t o = (size_t)(8 * si + u) * NT + 8 * sj;
-      const float4 d0 = __ldg(reinterpret_cast<const float4*>(gD + o));
-      const float4 d1 = __ldg(reinterpret_cast<const float4*>(gD + o + 4));
-      reinterpret_cast<float4*>(gS + o)[0] =
+      const size_t o0 = (size_t)(8 * si + u) * NT + 4 * sj, o1 = o0 + NT / 2;
+      const float4 d0 = __ldg(reinterpret_cast<const float4*>(gD + o0));
+      const float4 d1 = __ldg(reinterpret_cast<const float4*>(gD + o1));
+      *reinterpret_cast<float4*>(gS + o0) =
           make_float4(d0.x - acc[u][0], d0.y - acc[u][1], d0.z - acc[u][2], d0.w - acc[u][3]);
-      reinterpret_cast<float4*>(gS + o)[1] =
+      *reinterpret_cast<float4*>(gS + o1) =
           make_float4(d1.x - acc[u][4], d1.y - acc[u][5], d1.z - acc[u][6], d1.w - acc[u][7]);
     }
   }
@@ -872,6 +872,210 @@ __global__ void __launch_bounds__(ProdShape<NA, NT>::THREADS) k_condense_product
 #pragma unroll 8
     for (int l = 0; l < NA; ++l) v += W[l * LDW + i] * Bs[l * LDB + NT];
     a.t[(size_t)k * NT + i] = a.s[(size_t)k * NT + i] - double(v);
+  }
+}
+
+// ---------------------------------------- products in two streaming kernels (larger blocks)
+// For nA > 64 the single products kernel needs both whole operands in shared memory (two CTAs per
+// SM).  Here each product streams its k dimension through shared memory in chunks of KC rows
+// with cp.async double buffering, so a CTA holds two small chunks and the next chunk's copy
+// overlaps the current chunk's FMAs:
+//   k_products_x:  X_B = (PA)^{-1} P B and x_r = (PA)^{-1} P r (4 x 8 register tiles, the tiles
+//                  of column block 0 also carry x_r), written to global memory;
+//   k_products_s:  S = D - C X_B and t = s - C x_r, C staged row-major with an odd row stride
+//                  (4-byte copies, conflict-free column reads), X_B rows with 16-byte copies.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int NA, int NT>
+struct StreamShape {
+  static constexpr int KC = NA % 20 == 0 ? 20 : (NA % 16 == 0 ? 16 : (NA % 12 == 0 ? 12 : 4));
+  static constexpr int NCH = NA / KC;
+  static constexpr int TIX = NA / 4, TJ = NT / 8;  // X_B tiles
+  static constexpr int TIS = NT / 4;               // S tiles
+  static constexpr int TX = ((TIX * TJ + 31) / 32) * 32;
+  static constexpr int TSS = ((TIS * TJ + 31) / 32) * 32;
+  static constexpr int LDW = NA + 4, LDB = NT + 4;  // k-major chunk rows (16-byte aligned)
+  static constexpr int LDC = KC + 1;               // C chunk rows (odd: conflict-free columns)
+  static_assert(NA % 4 == 0 && NT % 8 == 0 && NA % KC == 0, "shape");
+  // a thread's eight columns are 4 tj .. 4 tj + 3 and nT/2 + 4 tj .. nT/2 + 4 tj + 3: the eight
+  // lanes of a float4 phase then read 128 contiguous bytes (no bank conflict)
+};
+
+template <int NA, int NT>
+__global__ void __launch_bounds__(StreamShape<NA, NT>::TX) k_products_x(const __grid_constant__ CondArgs a) {
+  using Sh = StreamShape<NA, NT>;
+  constexpr int KC = Sh::KC, NCH = Sh::NCH, TJ = Sh::TJ, LDW = Sh::LDW, LDB = Sh::LDB, TH = Sh::TX;
+  __shared__ __align__(16) float Wc[2][KC * LDW];
+  __shared__ __align__(16) float Bc[2][KC * LDB];
+  __shared__ float rc[2][KC];
+  __shared__ int s_pv[NA];
+  const int k = blockIdx.x, t = threadIdx.x;
+  const float* gWt = reinterpret_cast<const float*>(a.LU) + (size_t)k * NA * NA;
+  const float* gB = reinterpret_cast<const float*>(a.B) + (size_t)k * NA * NT;
+  const double* gr = a.r + (size_t)k * NA;
+  for (int c = t; c < NA; c += TH) s_pv[c] = a.piv[(size_t)k * NA + c];
+  __syncthreads();
+  auto stage = [&](int ch, int buf) {
+    const int c0 = ch * KC;
+    for (int e = t; e < KC * (NA / 4); e += TH) {
+      const int rr = e / (NA / 4), q4 = e % (NA / 4);
+      cp_async16(&Wc[buf][rr * LDW + 4 * q4], gWt + (size_t)(c0 + rr) * NA + 4 * q4);
+    }
+    for (int e = t; e < KC * (NT / 4); e += TH) {
+      const int rr = e / (NT / 4), q4 = e % (NT / 4);
+      cp_async16(&Bc[buf][rr * LDB + 4 * q4], gB + (size_t)s_pv[c0 + rr] * NT + 4 * q4);
+    }
+    cp_async_commit();
+    for (int rr = t; rr < KC; rr += TH) rc[buf][rr] = float(gr[s_pv[c0 + rr]]);
+  };
+  const bool act = t < Sh::TIX * TJ;
+  const int ti = act ? t / TJ : 0, tj = act ? t % TJ : 0;
+  float acc[4][8], accr[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    accr[u] = 0.f;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
+  }
+  stage(0, 0);
+  for (int ch = 0; ch < NCH; ++ch) {
+    const int buf = ch & 1;
+    if (ch + 1 < NCH) {
+      stage(ch + 1, buf ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    if (act) {
+      const float* W = Wc[buf];
+      const float* Bm = Bc[buf];
+#pragma unroll 4
+      for (int c = 0; c < KC; ++c) {
+        const float4 w0 = *reinterpret_cast<const float4*>(W + c * LDW + 4 * ti);
+        const float4 b0 = *reinterpret_cast<const float4*>(Bm + c * LDB + 4 * tj);
+        const float4 b1 = *reinterpret_cast<const float4*>(Bm + c * LDB + NT / 2 + 4 * tj);
+        const float wv[4] = {w0.x, w0.y, w0.z, w0.w};
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 8; ++v) acc[u][v] += wv[u] * bv[v];
+        if (tj == 0) {
+          const float rv = rc[buf][c];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) accr[u] += wv[u] * rv;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (!act) return;
+  float* gXB = reinterpret_cast<float*>(a.XB) + (size_t)k * NA * NT;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = 4 * ti + u;
+    *reinterpret_cast<float4*>(gXB + (size_t)i * NT + 4 * tj) = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+    *reinterpret_cast<float4*>(gXB + (size_t)i * NT + NT / 2 + 4 * tj) =
+        make_float4(acc[u][4], acc[u][5], acc[u][6], acc[u][7]);
+    if (tj == 0) a.xr[(size_t)k * NA + i] = double(accr[u]);
+  }
+}
+
+template <int NA, int NT>
+__global__ void __launch_bounds__(StreamShape<NA, NT>::TSS) k_products_s(const __grid_constant__ CondArgs a) {
+  using Sh = StreamShape<NA, NT>;
+  constexpr int KC = Sh::KC, NCH = Sh::NCH, TJ = Sh::TJ, LDB = Sh::LDB, LDC = Sh::LDC, TH = Sh::TSS;
+  __shared__ __align__(16) float Cc[2][NT * LDC];
+  __shared__ __align__(16) float Xc[2][KC * LDB];
+  __shared__ float xc[2][KC];
+  const int k = blockIdx.x, t = threadIdx.x;
+  const float* gC = reinterpret_cast<const float*>(a.C) + (size_t)k * NT * NA;
+  const float* gX = reinterpret_cast<const float*>(a.XB) + (size_t)k * NA * NT;
+  const double* gxr = a.xr + (size_t)k * NA;
+  const float* gD = reinterpret_cast<const float*>(a.D) + (size_t)k * NT * NT;
+  for (int off = 32 * t; off < NT * NT; off += 32 * TH) asm volatile("prefetch.global.L2 [%0];" ::"l"(gD + off));
+  auto stage = [&](int ch, int buf) {
+    const int l0 = ch * KC;
+    for (int e = t; e < NT * KC; e += TH) {
+      const int i = e / KC, l = e % KC;
+      cp_async4(&Cc[buf][i * LDC + l], gC + (size_t)i * NA + l0 + l);
+    }
+    for (int e = t; e < KC * (NT / 4); e += TH) {
+      const int rr = e / (NT / 4), q4 = e % (NT / 4);
+      cp_async16(&Xc[buf][rr * LDB + 4 * q4], gX + (size_t)(l0 + rr) * NT + 4 * q4);
+    }
+    cp_async_commit();
+    for (int rr = t; rr < KC; rr += TH) xc[buf][rr] = float(gxr[l0 + rr]);
+  };
+  const bool act = t < Sh::TIS * TJ;
+  const int si = act ? t / TJ : 0, sj = act ? t % TJ : 0;
+  float acc[4][8], acct[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    acct[u] = 0.f;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
+  }
+  stage(0, 0);
+  for (int ch = 0; ch < NCH; ++ch) {
+    const int buf = ch & 1;
+    if (ch + 1 < NCH) {
+      stage(ch + 1, buf ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    if (act) {
+      const float* Cm = Cc[buf];
+      const float* Xm = Xc[buf];
+#pragma unroll 4
+      for (int l = 0; l < KC; ++l) {
+        float cv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cv[u] = Cm[(4 * si + u) * LDC + l];
+        const float4 x0 = *reinterpret_cast<const float4*>(Xm + l * LDB + 4 * sj);
+        const float4 x1 = *reinterpret_cast<const float4*>(Xm + l * LDB + NT / 2 + 4 * sj);
+        const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 8; ++v) acc[u][v] += cv[u] * xv[v];
+        if (sj == 0) {
+          const float xrv = xc[buf][l];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acct[u] += cv[u] * xrv;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (!act) return;
+  float* gS = reinterpret_cast<float*>(a.S) + (size_t)k * NT * NT;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = 4 * si + u;
+    const size_t o0 = (size_t)i * NT + 4 * sj, o1 = o0 + NT / 2;
+    const float4 d0 = __ldg(reinterpret_cast<const float4*>(gD + o0));
+    const float4 d1 = __ldg(reinterpret_cast<const float4*>(gD + o1));
+    *reinterpret_cast<float4*>(gS + o0) =
+        make_float4(d0.x - acc[u][0], d0.y - acc[u][1], d0.z - acc[u][2], d0.w - acc[u][3]);
+    *reinterpret_cast<float4*>(gS + o1) =
+        make_float4(d1.x - acc[u][4], d1.y - acc[u][5], d1.z - acc[u][6], d1.w - acc[u][7]);
+    if (sj == 0) a.t[(size_t)k * NT + i] = a.s[(size_t)k * NT + i] - double(acct[u]);
   }
 }
 
@@ -888,11 +1092,18 @@ static cudaError_t cond_two_kernel(const CondArgs& a, cudaStream_t st, int part)
     }
     return cudaGetLastError();
   }
-  cudaError_t e = cudaFuncSetAttribute(k_condense_products<NA, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)P::SMEM);
-  if (e != cudaSuccess) return e;
-  (hfr::count_launch(), k_condense_products<NA, NT><<<a.Eim, P::THREADS, P::SMEM, st>>>(a));
-  return cudaGetLastError();
+  if constexpr (NA > 64) {
+    using SS = StreamShape<NA, NT>;
+    (hfr::count_launch(), k_products_x<NA, NT><<<a.Eim, SS::TX, 0, st>>>(a));
+    (hfr::count_launch(), k_products_s<NA, NT><<<a.Eim, SS::TSS, 0, st>>>(a));
+    return cudaGetLastError();
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(k_condense_products<NA, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)P::SMEM);
+    if (e != cudaSuccess) return e;
+    (hfr::count_launch(), k_condense_products<NA, NT><<<a.Eim, P::THREADS, P::SMEM, st>>>(a));
+    return cudaGetLastError();
+  }
 }
 
 // ------------------------------------------------------------- generic shared-memory kernel
