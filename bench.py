@@ -109,6 +109,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def replica_max(values, dist=None, device="cpu"):
+    """Max over ranks of per-rank timings (replicas: each rank runs the whole workload)."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.barrier()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_value(world, units_per_rank, ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def flush_l2(buf):
     buf.add_(1.0)  # writes a buffer larger than L2 (129 MB)
 
@@ -123,7 +140,7 @@ def run_stage(ctx, dt, u_n, u_stage, uhat, uhat0, R_hist):
 JAC_POLICY = {"every": 0, "once": 1}
 
 
-def time_path(pkg, torch, w, precision, refine, steps, warmup, dev, l2buf, jac="every"):
+def time_path(pkg, torch, w, precision, refine, steps, warmup, dev, l2buf, jac="every", barrier=None):
     ctx = pkg.Context(w.mesh, w.physics, precision=precision, tableau=pkg.FR_TAB_SDIRK2)
     ctx.refine = refine
     ctx.imex_set_jacobian_policy(JAC_POLICY[jac])
@@ -137,6 +154,8 @@ def time_path(pkg, torch, w, precision, refine, steps, warmup, dev, l2buf, jac="
     for _ in range(warmup):
         stats = run_stage(ctx, w.dt, u_n, u_stage, uhat, uhat0, R_hist)
     torch.cuda.synchronize()
+    if barrier is not None:
+        barrier()
     ctx.fr_profile_enable(True)
     l0 = ctx.kernel_launches()
     times = []
@@ -150,6 +169,9 @@ def time_path(pkg, torch, w, precision, refine, steps, warmup, dev, l2buf, jac="
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if barrier is not None:
+        barrier()
     launches = ctx.kernel_launches() - l0
     prof = ctx.fr_profile_read()
     ctx.fr_profile_enable(False)
@@ -353,18 +375,14 @@ def main():
         print(json.dumps({"path": args.paths, "ms": r["ms"], "stats": r["stats"],
                           "phases_ms_total": r["profile"], "launches": r["launches"]}))
         return
+    barrier = dist.barrier if dist is not None else None
     with ClockSampler(local) as clk:
         mixed = time_path(pkg, torch, w, pkg.FR_PREC_FP32, args.refine, args.steps, args.warmup, dev, l2buf,
-                          args.jacobian)
-        fp64 = time_path(pkg, torch, w, pkg.FR_PREC_FP64, 0, args.steps, args.warmup, dev, l2buf, args.jacobian)
+                          args.jacobian, barrier)
+        fp64 = time_path(pkg, torch, w, pkg.FR_PREC_FP64, 0, args.steps, args.warmup, dev, l2buf, args.jacobian,
+                         barrier)
     clocks = clk.summary()
-    ms_mixed = float(np.mean(mixed["ms"]))
-    ms_fp64 = float(np.mean(fp64["ms"]))
-    if dist is not None:
-        t = torch.tensor([ms_mixed, ms_fp64], device=dev)
-        dist.barrier()
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_mixed, ms_fp64 = float(t[0]), float(t[1])
+    ms_mixed, ms_fp64 = replica_max([np.mean(mixed["ms"]), np.mean(fp64["ms"])], dist, dev)
     dofs = w.dofs_implicit
     # agreement of the two converged stages (same equations, same tolerance)
     inc = (fp64["u"] - torch.tensor(w.u0, device=dev)).abs().max().item()
@@ -373,13 +391,14 @@ def main():
         e2e_ms, bi, bo = float("nan"), 0, 0
     else:
         e2e_ms, bi, bo = time_e2e(pkg, torch, mixed["ctx"], w, max(3, args.steps // 2), dev)
+        e2e_ms = replica_max([e2e_ms], dist, dev)[0]
     peaks, peak_src = _peaks()
     pm = {k: v[0] for k, v in mixed["profile"].items()}
     dom, kroofs = kernel_rooflines(mixed["profile"], mixed["stats"], w, peaks, clocks, args.workload)
     roof = {k: v for k, v in kroofs[dom].items() if k != "total_ms"}
     line = {
         "metric": METRIC,
-        "value": world * dofs / (ms_mixed * 1e-3),
+        "value": job_value(world, dofs, ms_mixed),
         "unit": "DOF/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -394,7 +413,7 @@ def main():
                    "newton_tol": NEWTON_TOL, "gmres_rtol": GMRES_RTOL, "refine_sweeps": args.refine,
                    "jacobian": args.jacobian,
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
-        "fp64": {"value": world * dofs / (ms_fp64 * 1e-3), "ms_per_step": ms_fp64, "dtype": "f64",
+        "fp64": {"value": job_value(world, dofs, ms_fp64), "ms_per_step": ms_fp64, "dtype": "f64",
                  "newton_iterations": fp64["stats"]["newton_iterations"],
                  "gmres_iterations": fp64["stats"]["gmres_iterations"],
                  "phases_ms_total": {k: round(v[0], 3) for k, v in fp64["profile"].items()}},
@@ -407,7 +426,7 @@ def main():
         "roofline": roof,
         "kernel_rooflines": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
                              for k, v in kroofs.items()},
-        "e2e": {"value": world * dofs / (e2e_ms * 1e-3), "unit": "DOF/s", "h2d_bytes_per_step": bi,
+        "e2e": {"value": job_value(world, dofs, e2e_ms), "unit": "DOF/s", "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo},
         "gpu_launches": int(mixed["launches"] // max(args.steps, 1)),
         "gpu_launches_note": "kernels of libhfr.so per timed step (mixed path)",

@@ -149,7 +149,7 @@ int hfr_trace_gmres(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* ite
 enum fr_jacobian_policy { FR_JAC_EVERY_NEWTON = 0, FR_JAC_ONCE_PER_STAGE = 1 };
 int imex_set_jacobian_policy(fr_ctx* ctx, int policy);
 
-/* How hfr_trace_gmres (and imex_stage) run a restart cycle./* How hfr_trace_gmres (and imex_stage) run a restart cycle.  FR_GMRES_FUSED (the default where
+/* How hfr_trace_gmres (and imex_stage) run a restart cycle.  FR_GMRES_FUSED (the default where
  * available): the whole cycle -- preconditioner, mat-vecs, Gram-Schmidt, Givens rotations and the
  * solution update -- is one cooperative launch with one CTA per SM that meets at grid barriers;
  * available for trace blocks (nT, n nv) = (64,16), (80,20), (48,12) on devices with cooperative
@@ -162,6 +162,17 @@ int imex_set_jacobian_policy(fr_ctx* ctx, int policy);
 enum fr_gmres_mode { FR_GMRES_MULTI = 0, FR_GMRES_FUSED = 1 };
 int hfr_gmres_set_mode(fr_ctx* ctx, int mode);
 int hfr_gmres_get_mode(const fr_ctx* ctx);
+
+/* Self-test of the bounded grid barrier that the single-launch GMRES cycle meets at (no
+ * counterpart in the paper; failure detection of that cycle).  One cooperative launch of nblocks
+ * CTAs on `stream` passes `rounds` grid barriers; if 0 <= absent_block < nblocks that CTA leaves
+ * without arriving, so the others' wait runs out after timeout_s seconds (0 < timeout_s <= 10),
+ * they raise the abort flag and return.  *barriers_passed (host) = the barriers passed, summed
+ * over CTAs.  Returns FR_OK (no wait ran out), FR_ERR_TIMEOUT (the abort flag was raised; the
+ * CUDA context stays usable), FR_ERR_INVALID_ARG (arguments, or more CTAs than can be resident
+ * at once) or FR_ERR_CUDA. */
+int fr_barrier_selftest(int nblocks, int absent_block, int rounds, double timeout_s, int* barriers_passed,
+                        void* stream);
 
 /* du_k = x_r - X_B du^_k = A_k^{-1}(r_k - B_k du^_k) for every implicit element (du: nimplicit x nA,
  * compact order), followed by `refine` FP64 refinement sweeps against the exact FP64 linearisation. */

@@ -29,14 +29,18 @@ import numpy as np
 EPS = 1.0e-30
 
 
-def element_blocks(disc, U, uhat, a_dt: float):
+def element_blocks(disc, U, uhat, a_dt: float, view=None):
     """A, B, C, D for every element, shapes (E, nA, nA), (E, nA, nT),
-    (E, nT, nA), (E, nT, nT).  Only implicit elements' blocks are meaningful."""
+    (E, nT, nA), (E, nT, nT).  Only implicit elements' blocks are meaningful.
+    view (optional): per element-face trace values (E, 4, n, nv) used instead of
+    disc.trace_view(uhat) (the blocks of a hybridized element depend only on its
+    own state and its own faces' traces)."""
     E = disc.mesh.nelem
     nv, ns, n = disc.nv, disc.ns, disc.n
     nA = ns * nv
     nT = 4 * n * nv
-    view = disc.trace_view(uhat)
+    if view is None:
+        view = disc.trace_view(uhat)
     Uc = U.astype(np.complex128)
     Vc = view.astype(np.complex128)
     imp = disc.imp

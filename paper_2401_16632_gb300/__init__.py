@@ -31,6 +31,8 @@ FR_TAB_BE, FR_TAB_SDIRK2 = 0, 1
 FR_PHYS_ADVDIFF, FR_PHYS_NAVIER_STOKES = 0, 1
 FR_GMRES_MULTI, FR_GMRES_FUSED = 0, 1
 FR_JAC_EVERY_NEWTON, FR_JAC_ONCE_PER_STAGE = 0, 1
+(FR_OK, FR_ERR_INVALID_ARG, FR_ERR_CUDA, FR_ERR_SINGULAR, FR_ERR_NOT_CONVERGED, FR_ERR_DIVERGED, FR_ERR_TIMEOUT,
+ FR_ERR_OOM, FR_ERR_UNSUPPORTED) = range(9)
 EXPORT = {"A": 0, "B": 1, "C": 2, "D": 3, "S": 4, "XB": 5, "xr": 6, "t_k": 7, "r": 8, "s": 9, "t": 10, "Pinv": 11}
 
 # every symbol declared in include/hfr.h
@@ -46,6 +48,7 @@ ABI_SYMBOLS = [
     "imex_set_jacobian_policy",
     "hfr_gmres_set_mode",
     "hfr_gmres_get_mode",
+    "fr_barrier_selftest",
     "hfr_backsolve",
     "hfr_export",
     "imex_stage",
@@ -154,6 +157,7 @@ def load_library(path: str = LIB_PATH):
     lib.imex_set_jacobian_policy.argtypes = [vp, ctypes.c_int]
     lib.hfr_gmres_set_mode.argtypes = [vp, ctypes.c_int]
     lib.hfr_gmres_get_mode.argtypes = [vp]
+    lib.fr_barrier_selftest.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ip, vp]
     lib.hfr_backsolve.argtypes = [vp, dp, dp, ctypes.c_int]
     lib.hfr_export.argtypes = [vp, ctypes.c_int, dp, ctypes.c_size_t]
     lib.imex_stage.argtypes = [vp, ctypes.c_int, ctypes.c_double, dp, dp, dp, dp, ctypes.c_double, ctypes.c_int,
@@ -197,6 +201,18 @@ def hfr_condense_noalloc(A, B, C, D, r, s, XB, xr, S, t, precision=FR_PREC_FP64,
     st = stream if stream is not None else torch.cuda.current_stream()
     return lib.hfr_condense_noalloc(E, nA, nT, int(precision), _ptr(A), _ptr(B), _ptr(C), _ptr(D), _ptr(r), _ptr(s),
                                     _ptr(XB), _ptr(xr), _ptr(S), _ptr(t), ctypes.c_void_p(st.cuda_stream))
+
+
+def fr_barrier_selftest(nblocks, absent_block=-1, rounds=4, timeout_s=0.05, stream=None):
+    """Bounded grid-barrier self-test (see include/hfr.h).  Returns (status, barriers passed)."""
+    import torch
+
+    lib = load_library()
+    passed = ctypes.c_int(0)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib.fr_barrier_selftest(int(nblocks), int(absent_block), int(rounds), float(timeout_s),
+                                 ctypes.byref(passed), ctypes.c_void_p(st.cuda_stream))
+    return rc, passed.value
 
 
 class Context:

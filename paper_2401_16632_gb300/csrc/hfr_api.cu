@@ -663,9 +663,11 @@ static int jacobian_blocks(fr_ctx* ctx, const double* u, const double* uhat, dou
   j.B = ctx->B;
   j.C = ctx->C;
   j.D = ctx->D;
-  const int ph = prof_begin(ctx, PH_JAC);
-  CK(launch_jacobian(ctx->p, ctx->prec_bytes, ctx->ref, ctx->pp, j, ctx->stream));
-  prof_end(ctx, ph);
+  if (ctx->Eim > 0) {  // no implicit element: nothing to linearise
+    const int ph = prof_begin(ctx, PH_JAC);
+    CK(launch_jacobian(ctx->p, ctx->prec_bytes, ctx->ref, ctx->pp, j, ctx->stream));
+    prof_end(ctx, ph);
+  }
   ctx->lin_U = u;
   ctx->lin_uhat = uhat;
   ctx->lin_adt = a_dt;
@@ -756,6 +758,7 @@ static int condense_impl(fr_ctx* ctx, int refine) {
   // (a kernel, not a copy from host memory: a pageable host-to-device copy would wait for the stream)
   (hfr::count_launch(), k_status_reset<<<1, 1, 0, ctx->stream>>>(ctx->status));
   CK(cudaGetLastError());
+  if (ctx->Eim == 0) return FR_OK;  // no implicit element (and so no trace)
   CondArgs c;
   c.Eim = ctx->Eim;
   c.nA = ctx->nA;
@@ -798,6 +801,7 @@ static int condense_impl(fr_ctx* ctx, int refine) {
 // x_r = A^{-1} r with the stored factorisation, t_k = s - C x_r, t = sum scatter(t_k).  S_k, X_B and
 // the face preconditioner are kept.
 static int condense_rhs_impl(fr_ctx* ctx) {
+  if (ctx->Eim == 0) return FR_OK;
   const size_t nrA = (size_t)ctx->Eim * ctx->nA;
   int ph = prof_begin(ctx, PH_COND);
   CK(cudaMemcpyAsync(ctx->xr, ctx->r, nrA * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
@@ -921,6 +925,17 @@ extern "C" int hfr_gmres_set_mode(fr_ctx* ctx, int mode) {
 
 extern "C" int hfr_gmres_get_mode(const fr_ctx* ctx) { return ctx ? ctx->gm_mode : -1; }
 
+extern "C" int fr_barrier_selftest(int nblocks, int absent_block, int rounds, double timeout_s,
+                                   int* barriers_passed, void* stream) {
+  if (!barriers_passed || !(timeout_s > 0.0) || timeout_s > 10.0) return FR_ERR_INVALID_ARG;
+  int timed_out = 0;
+  const int rc = hfr::barrier_selftest(nblocks, absent_block, rounds, timeout_s, barriers_passed, &timed_out,
+                                       (cudaStream_t)stream);
+  if (rc == -2) return FR_ERR_INVALID_ARG;
+  if (rc != 0) return FR_ERR_CUDA;
+  return timed_out ? FR_ERR_TIMEOUT : FR_OK;
+}
+
 extern "C" int hfr_trace_gmres(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* iters, double* final_rel) {
   if (!ctx || !duhat || rtol < 0 || maxit < 1) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_trace_gmres: bad argument");
   const int rc = gmres_impl(ctx, duhat, rtol, maxit, iters, final_rel);
@@ -929,6 +944,7 @@ extern "C" int hfr_trace_gmres(fr_ctx* ctx, double* duhat, double rtol, int maxi
 }
 
 static int backsolve_impl(fr_ctx* ctx, const double* duhat, double* du, int refine) {
+  if (ctx->Eim == 0) return FR_OK;
   TraceArgs t = trace_args(ctx);
   const int ph = prof_begin(ctx, PH_BACK);
   CK(launch_backsolve(ctx->prec_bytes, t, ctx->Eim, ctx->nA, ctx->XB, ctx->xr, duhat, du, ctx->stream));

@@ -71,9 +71,10 @@ __device__ __forceinline__ unsigned pg_load_acquire(const unsigned* p) {
 }
 
 // Grid barrier of a cooperative launch (all CTAs resident).  bar[0] counts arrivals over the
-// whole launch (zeroed before it), bar[1] is the abort flag.  Returns false on abort.
-template <typename T>
-__device__ bool pg_sync(PGShared<T>& sh, unsigned* bar, unsigned& epoch) {
+// whole launch (zeroed before it), bar[1] is the abort flag.  A wait longer than timeout_ns (or
+// PG_MAX_SPINS polls) raises the abort flag; a CTA that sees the flag leaves.  Returns false on
+// abort.  ok: a shared-memory word of the CTA.
+__device__ bool pg_grid_sync(int& ok_shared, unsigned* bar, unsigned& epoch, unsigned long long timeout_ns) {
   __syncthreads();
   ++epoch;
   if (threadIdx.x == 0) {
@@ -88,7 +89,7 @@ __device__ bool pg_sync(PGShared<T>& sh, unsigned* bar, unsigned& epoch) {
           ok = 0;
           break;
         }
-        if (it >= PG_MAX_SPINS || pg_clock() - t0 > PG_TIMEOUT_NS) {
+        if (it >= PG_MAX_SPINS || pg_clock() - t0 > timeout_ns) {
           atomicExch(bar + 1, 1u);
           ok = 0;
           break;
@@ -96,10 +97,27 @@ __device__ bool pg_sync(PGShared<T>& sh, unsigned* bar, unsigned& epoch) {
       }
       __nanosleep(20);
     }
-    sh.ok = ok;
+    ok_shared = ok;
   }
   __syncthreads();
-  return sh.ok != 0;
+  return ok_shared != 0;
+}
+
+template <typename T>
+__device__ __forceinline__ bool pg_sync(PGShared<T>& sh, unsigned* bar, unsigned& epoch) {
+  return pg_grid_sync(sh.ok, bar, epoch, PG_TIMEOUT_NS);
+}
+
+// Self-test of the barrier: `rounds` grid barriers; CTA `absent` (if in range) leaves at once and
+// never arrives, so the others' first wait runs out.  passed[0] += barriers each CTA got through.
+__global__ void __launch_bounds__(128) k_barrier_probe(unsigned* bar, int absent, int rounds,
+                                                       unsigned long long timeout_ns, int* passed) {
+  __shared__ int ok;
+  if ((int)blockIdx.x == absent) return;
+  unsigned epoch = 0;
+  int r = 0;
+  while (r < rounds && pg_grid_sync(ok, bar, epoch, timeout_ns)) ++r;
+  if (threadIdx.x == 0) atomicAdd(passed, r);
 }
 
 // Warp reduce-scatter of 16 per-lane values: afterwards lane l holds the warp sum of value l >> 1.
@@ -803,6 +821,37 @@ int run_gmres_fused(const FusedArgs& base, int prec_bytes, int grid, double rtol
     res->converged = hs.converged;
     if (hs.nan || hs.converged || total >= maxit || hs.k == 0) return 0;
   }
+}
+
+// Host side of the barrier self-test (declared in hfr_krylov.h).
+int barrier_selftest(int nblocks, int absent, int rounds, double timeout_s, int* passed, int* timed_out,
+                     cudaStream_t s) {
+  *passed = 0;
+  *timed_out = 0;
+  int dev = 0, nsm = 0, per_sm = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess) return -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_barrier_probe, 128, 0) != cudaSuccess) return -1;
+  if (!coop || nblocks < 1 || nblocks > nsm * per_sm || rounds < 0) return -2;
+  unsigned* bar = nullptr;
+  int* dpass = nullptr;
+  if (cudaMalloc((void**)&bar, 2 * sizeof(unsigned) + sizeof(int)) != cudaSuccess) return -1;
+  dpass = reinterpret_cast<int*>(bar + 2);
+  int rc = 0;
+  unsigned flags[2] = {0u, 0u};
+  unsigned long long tns = (unsigned long long)(timeout_s * 1e9);
+  void* args[] = {&bar, &absent, &rounds, &tns, &dpass};
+  if (cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned) + sizeof(int), s) != cudaSuccess ||
+      cudaLaunchCooperativeKernel((const void*)k_barrier_probe, dim3(nblocks), dim3(128), args, 0, s) != cudaSuccess ||
+      cudaMemcpyAsync(flags, bar, sizeof(flags), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(passed, dpass, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    rc = -1;
+  cudaStreamSynchronize(s);
+  cudaFree(bar);
+  *timed_out = flags[1] != 0u;
+  return rc;
 }
 
 }  // namespace hfr

@@ -86,6 +86,12 @@ int fused_gmres_grid(int prec_bytes, int nT, int bs);
 int run_gmres_fused(const FusedArgs& a, int prec_bytes, int grid, double rtol, int restart, int maxit,
                     GmresResult* res, int* timed_out, cudaStream_t s, const int* dev_status = nullptr,
                     int* host_status = nullptr);
+// Self-test of the bounded grid barrier used by the single-launch cycle (cooperative launch of
+// nblocks CTAs, `rounds` barriers; CTA `absent` never arrives when 0 <= absent < nblocks).
+// Returns 0 (timed_out set when the abort flag was raised), -1 on a CUDA error, -2 on arguments
+// the device cannot run as one cooperative launch.
+int barrier_selftest(int nblocks, int absent, int rounds, double timeout_s, int* passed, int* timed_out,
+                     cudaStream_t s);
 
 int run_gmres(const GmresOps& ops, const GmresBuffers& b, const double* t, double* x, double rtol, int restart,
               int maxit, int check_every, GmresResult* res, cudaStream_t s);

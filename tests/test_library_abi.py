@@ -59,3 +59,14 @@ def test_binding_fails_loudly_without_library(tmp_path):
             pkg.load_library(str(tmp_path / "nope.so"))
     finally:
         pkg._lib = saved
+
+
+def test_binding_constants_match_the_header():
+    import paper_2401_16632_gb300 as pkg
+
+    src = open(os.path.join(ROOT, "include", "hfr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    consts = dict((k, int(v)) for k, v in re.findall(r"\b(FR_[A-Z0-9_]+)\s*=\s*(\d+)", src))
+    assert "FR_ERR_TIMEOUT" in consts and "FR_GMRES_FUSED" in consts
+    for k, v in consts.items():
+        assert getattr(pkg, k) == v, k
