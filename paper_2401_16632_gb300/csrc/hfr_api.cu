@@ -53,6 +53,7 @@ struct fr_ctx {
   GmresBuffers gm;
   int gm_mode = 0;          // 0: multi-kernel cycle, 1: one cooperative launch per cycle
   int jac_policy = 0;       // FR_JAC_EVERY_NEWTON or FR_JAC_ONCE_PER_STAGE
+  int products_tc = 0;      // FR_PRODUCTS_TENSOR: FP32 condensation products on the tensor cores
   int gm_fused_grid = 0;    // CTAs of the cooperative launch (0: not available)
   unsigned* gm_bar = nullptr;
   double *duhat = nullptr, *du = nullptr, *res_tmp = nullptr, *Ustar = nullptr, *red = nullptr;
@@ -505,6 +506,7 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, const fr_config* cfg, voi
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     ctx->gm_fused_grid = fused_gmres_grid(ctx->prec_bytes, nT, n * nv);
     ctx->gm_mode = ctx->gm_fused_grid > 0 ? 1 : 0;
+    ctx->products_tc = condense_tc_available(ctx->prec_bytes, nA, nT) ? 1 : 0;
     const size_t np = std::max((size_t)GM_NBLK * (GM_MAXM + 1), fused_partial_doubles(std::max(nsm, 1)));
     ctx->gm.partial = dalloc<double>(ctx, np, &rc);
     ctx->gm_bar = dalloc<unsigned>(ctx, 64, &rc);
@@ -746,6 +748,10 @@ static int check_status(fr_ctx* ctx, const char* where) {
     CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
     return set_err(ctx, FR_ERR_SINGULAR, where, hs[1]);
   }
+  if (hs[0] & DEV_ERR_TIMEOUT) {
+    CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), ctx->stream));
+    return set_err(ctx, FR_ERR_TIMEOUT, "hfr_condense: tensor-core completion wait timed out");
+  }
   return FR_OK;
 }
 
@@ -776,6 +782,7 @@ static int condense_impl(fr_ctx* ctx, int refine) {
   c.S = ctx->S;
   c.t = ctx->te;
   c.status = ctx->status;
+  c.products_tc = ctx->products_tc;
   int ph = prof_begin(ctx, PH_COND);
   CK(launch_condense_part(ctx->prec_bytes, c, ctx->stream, 0));
   prof_end(ctx, ph);
@@ -924,6 +931,17 @@ extern "C" int hfr_gmres_set_mode(fr_ctx* ctx, int mode) {
 }
 
 extern "C" int hfr_gmres_get_mode(const fr_ctx* ctx) { return ctx ? ctx->gm_mode : -1; }
+
+extern "C" int hfr_condense_set_products(fr_ctx* ctx, int mode) {
+  if (!ctx || (mode != FR_PRODUCTS_FMA && mode != FR_PRODUCTS_TENSOR))
+    return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_condense_set_products: bad argument");
+  if (mode == FR_PRODUCTS_TENSOR && !condense_tc_available(ctx->prec_bytes, ctx->nA, ctx->nT))
+    return set_err(ctx, FR_ERR_UNSUPPORTED, "hfr_condense_set_products: no tensor-core products for this precision or shape");
+  ctx->products_tc = mode;
+  return FR_OK;
+}
+
+extern "C" int hfr_condense_get_products(const fr_ctx* ctx) { return ctx ? ctx->products_tc : -1; }
 
 extern "C" int fr_barrier_selftest(int nblocks, int absent_block, int rounds, double timeout_s,
                                    int* barriers_passed, void* stream) {
@@ -1113,6 +1131,10 @@ extern "C" int imex_stage(fr_ctx* ctx, int stage, double dt, const double* u_n, 
     if (cst[0] & DEV_ERR_SINGULAR) {
       CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), st));
       return set_err(ctx, FR_ERR_SINGULAR, "imex_stage: zero pivot in condensation", cst[1]);
+    }
+    if (cst[0] & DEV_ERR_TIMEOUT) {
+      CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), st));
+      return set_err(ctx, FR_ERR_TIMEOUT, "imex_stage: tensor-core completion wait timed out");
     }
     gtot += its;
     if (rc && rc != FR_ERR_NOT_CONVERGED) return rc;

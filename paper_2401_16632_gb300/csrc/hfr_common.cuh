@@ -214,4 +214,4 @@ __device__ __forceinline__ int line_pt(int r, int m, int c) {
 }
 
 // status word bits written by kernels (never trap)
-enum { DEV_ERR_SINGULAR = 1, DEV_ERR_NAN = 2, DEV_ERR_INDEX = 4 };
+enum { DEV_ERR_SINGULAR = 1, DEV_ERR_NAN = 2, DEV_ERR_INDEX = 4, DEV_ERR_TIMEOUT = 8 };

@@ -14,6 +14,7 @@
 // Outputs per element: AinvT = ((PA)^{-1})^T (column c contiguous), piv, X_B, x_r, S, t.
 // T = double (plain path) or float (mixed path).
 #include "hfr_internal.h"
+#include "hfr_tc.cuh"
 
 namespace hfr {
 
@@ -1079,6 +1080,369 @@ __global__ void __launch_bounds__(StreamShape<NA, NT>::TSS) k_products_s(const _
   }
 }
 
+// ------------------------------------------------ products on the tensor cores (tcgen05)
+// Both products of the condensation as two transposed GEMMs per element on the fifth-generation
+// tensor cores, in 3xTF32 (each FP32 operand split into a TF32 high part and the TF32 remainder;
+// hi*hi + hi*lo + lo*hi accumulated in FP32 in tensor memory, about 2^-21 relative per product):
+//   GEMM 1:  [X_B | x_r]^T (M = nT + 1 rows, padded to 128)  =  [P B | P r]^T  *  ((PA)^{-1})^T
+//   GEMM 2:  [C X_B | C x_r]^T                               =  [X_B | x_r]^T  *  C^T
+// then S = D - C X_B and t = s - C x_r.  Transposing puts the trace index j on the tensor-memory
+// lanes, so that each thread of the epilogues owns one j: X_B[i][j], S[i][j] and D[i][j] are
+// read and written with the 32 lanes of a warp on 32 consecutive j (coalesced), and the thread's
+// run of consecutive i is one 16-byte chunk of GEMM 2's K-major A operand (conflict-free).
+// Operands are staged K-major without swizzle (see hfr_tc.cuh); the staging maps the 32 lanes of
+// a warp to 8 rows x 4 k, which the layout spreads over all 32 banks.  One CTA of 256 threads per
+// element in a persistent loop; thread 0 issues the MMAs; the next element's blocks are prefetched
+// into L2 while the current one is processed.
+template <int NA, int NT>
+struct TcShape {
+  static constexpr int K1 = (NA + 7) / 8 * 8;     // GEMM K (both GEMMs), padded with zeros
+  static constexpr int N1 = (NA + 15) / 16 * 16;  // GEMM 1 N (the i index of X_B)
+  static constexpr int N2 = (NT + 15) / 16 * 16;  // GEMM 2 N (the i index of S)
+  static constexpr int M = 128;
+  static constexpr int NB = N1 > N2 ? N1 : N2;
+  static constexpr int KG = K1 / 4;               // 4-element k chunks
+  static constexpr uint32_t SBO = (uint32_t)KG * 128u;
+  static constexpr uint32_t A_BYTES = (uint32_t)M * K1 * 4u;   // one of hi / lo
+  static constexpr uint32_t B_BYTES = (uint32_t)NB * K1 * 4u;
+  static constexpr uint32_t SMEM = 2u * A_BYTES + 2u * B_BYTES + 16u + 128u + 2u * NA * 4u + 1024u;
+  // 8 warps: warps 0-6 stage operands, warp 7 (lanes 96-127 of tensor memory, rows the epilogues
+  // do not need while nT < 96) allocates tensor memory and issues the MMAs
+  static constexpr int THREADS = 256, WARPS = 7, ISSUER = 7;
+  // GEMM 1 staging: warp task = 8 rows x 4 k (one value per lane)
+  static constexpr int A_TASKS = (NT / 8) * KG, A_PER = (A_TASKS + WARPS - 1) / WARPS;
+  static constexpr int B_TASKS = ((NA + 7) / 8) * KG, B_PER = (B_TASKS + WARPS - 1) / WARPS;
+  static constexpr int R_PER = (K1 + THREADS - 1) / THREADS;
+  // C staging: warp task = 8 rows x 4 chunks of 4 k (one float4 per lane)
+  static constexpr int CG = (KG + 3) / 4;
+  static constexpr int C_TASKS = (NT / 8) * CG, C_PER = (C_TASKS + WARPS - 1) / WARPS;
+  static constexpr int NCH1 = N1 / 16, H1 = (NCH1 + 1) / 2;  // epilogue column chunks, split in halves
+  static constexpr int NCH2 = N2 / 16, H2 = (NCH2 + 1) / 2;
+  static constexpr uint32_t TMEM_COLS = 256, D2_COL = 128;
+  static_assert(NT < 96 && N1 <= 128 && N2 <= 128, "trace block too large for one 128-row tile");
+  static_assert(NA % 4 == 0 && NT % 8 == 0, "shape");
+  static_assert(SMEM <= 232448, "shared memory");
+};
+
+constexpr unsigned long long TC_TIMEOUT_NS = 2000000000ull;
+
+// GEMM 1 operands of one element held in registers between their load and their store
+template <int NA, int NT>
+struct TcStage {
+  float av[TcShape<NA, NT>::A_PER];
+  float bv[TcShape<NA, NT>::B_PER];
+  float rv[TcShape<NA, NT>::R_PER];
+};
+
+// all loads first (one memory latency per element), pivots from shared memory
+template <int NA, int NT>
+__device__ __forceinline__ void tc_load_stage(TcStage<NA, NT>& g, const CondArgs& a, int k, const int* pv, int t) {
+  using Sh = TcShape<NA, NT>;
+  const int lane = t & 31, w = t >> 5, r8 = lane >> 2, c4 = lane & 3;
+  const float* gWt = reinterpret_cast<const float*>(a.LU) + (size_t)k * NA * NA;
+  const float* gB = reinterpret_cast<const float*>(a.B) + (size_t)k * NA * NT;
+  const double* gr = a.r + (size_t)k * NA;
+#pragma unroll
+  for (int u = 0; u < Sh::A_PER; ++u) {
+    const int task = w + Sh::WARPS * u;
+    const int jj = 8 * (task / Sh::KG) + r8, c = 4 * (task % Sh::KG) + c4;
+    g.av[u] = (task < Sh::A_TASKS && c < NA) ? __ldg(gB + (size_t)pv[c] * NT + jj) : 0.f;
+  }
+#pragma unroll
+  for (int u = 0; u < Sh::B_PER; ++u) {
+    const int task = w + Sh::WARPS * u;
+    const int i = 8 * (task / Sh::KG) + r8, c = 4 * (task % Sh::KG) + c4;
+    g.bv[u] = (task < Sh::B_TASKS && i < NA && c < NA) ? __ldg(gWt + (size_t)c * NA + i) : 0.f;
+  }
+#pragma unroll
+  for (int u = 0; u < Sh::R_PER; ++u) {
+    const int c = t + Sh::THREADS * u;
+    g.rv[u] = c < NA ? float(gr[pv[c]]) : 0.f;
+  }
+}
+
+// A: row jj < NT is column jj of P B, row NT is P r; B: row i is row i of (PA)^{-1} (column i of
+// Wt); K padding zero.  Lanes cover 8 rows x 4 k: conflict-free 4-byte stores.
+template <int NA, int NT>
+__device__ __forceinline__ void tc_store_stage(const TcStage<NA, NT>& g, unsigned char* Ahi, unsigned char* Alo,
+                                               unsigned char* Bhi, unsigned char* Blo, int t) {
+  using Sh = TcShape<NA, NT>;
+  using namespace tc;
+  const int lane = t & 31, w = t >> 5, r8 = lane >> 2, c4 = lane & 3;
+#pragma unroll
+  for (int u = 0; u < Sh::A_PER; ++u) {
+    const int task = w + Sh::WARPS * u;
+    if (task < Sh::A_TASKS) {
+      const int jj = 8 * (task / Sh::KG) + r8, c = 4 * (task % Sh::KG) + c4;
+      float h, l;
+      split_tf32(g.av[u], h, l);
+      *reinterpret_cast<float*>(Ahi + kmajor_offset(jj, c, Sh::SBO)) = h;
+      *reinterpret_cast<float*>(Alo + kmajor_offset(jj, c, Sh::SBO)) = l;
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < Sh::B_PER; ++u) {
+    const int task = w + Sh::WARPS * u;
+    const int i = 8 * (task / Sh::KG) + r8, c = 4 * (task % Sh::KG) + c4;
+    if (task < Sh::B_TASKS && i < NA) {
+      float h, l;
+      split_tf32(g.bv[u], h, l);
+      *reinterpret_cast<float*>(Bhi + kmajor_offset(i, c, Sh::SBO)) = h;
+      *reinterpret_cast<float*>(Blo + kmajor_offset(i, c, Sh::SBO)) = l;
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < Sh::R_PER; ++u) {
+    const int c = t + Sh::THREADS * u;
+    if (c < Sh::K1) {
+      float h, l;
+      split_tf32(g.rv[u], h, l);
+      *reinterpret_cast<float*>(Ahi + kmajor_offset(NT, c, Sh::SBO)) = h;
+      *reinterpret_cast<float*>(Alo + kmajor_offset(NT, c, Sh::SBO)) = l;
+    }
+  }
+}
+
+template <int NA, int NT>
+__device__ __forceinline__ void tc_issue(uint32_t td, unsigned char* Ahi, unsigned char* Alo, unsigned char* Bhi,
+                                         unsigned char* Blo, uint32_t idesc, uint32_t mbar) {
+  using Sh = TcShape<NA, NT>;
+  using namespace tc;
+  fence_after_sync();
+  const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
+#pragma unroll 1
+  for (int kk = 0; kk < Sh::K1 / 8; ++kk) {
+    const uint32_t off = (uint32_t)kk * 256u;  // two core matrices along k per instruction
+    mma_tf32(td, desc_noswizzle(ah + off, 128, Sh::SBO), desc_noswizzle(bh + off, 128, Sh::SBO), idesc, kk > 0);
+    mma_tf32(td, desc_noswizzle(ah + off, 128, Sh::SBO), desc_noswizzle(bl + off, 128, Sh::SBO), idesc, 1);
+    mma_tf32(td, desc_noswizzle(al + off, 128, Sh::SBO), desc_noswizzle(bh + off, 128, Sh::SBO), idesc, 1);
+  }
+  mma_commit(mbar);
+}
+
+template <int NA, int NT>
+__global__ void __launch_bounds__(256, 1) k_products_tc(const __grid_constant__ CondArgs a) {
+  using Sh = TcShape<NA, NT>;
+  using namespace tc;
+  constexpr int K1 = Sh::K1, NA4 = NA / 4;
+  constexpr uint32_t SBO = Sh::SBO;
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  unsigned char* Ahi = tc_smem;
+  unsigned char* Alo = Ahi + Sh::A_BYTES;
+  unsigned char* Bhi = Alo + Sh::A_BYTES;
+  unsigned char* Blo = Bhi + Sh::B_BYTES;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Blo + Sh::B_BYTES);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  float* s_row = reinterpret_cast<float*>(mbar + 2);  // row NT (x_r / C x_r): 2 halves x 16
+  int* s_pv = reinterpret_cast<int*>(s_row + 32);     // two buffers of NA pivots
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const bool issuer = w == Sh::ISSUER;
+  const int q = w & 3, hh = w >> 2;  // tensor-memory lane quarter, column half
+  const int j = 32 * q + lane;       // this thread's row of both accumulators (trace index)
+  const bool epi = q < 3;            // warps whose lanes hold rows j <= NT
+  const bool rowNT = q == NT / 32;   // warps whose lane NT % 32 holds row NT
+  if (t == 0) mbar_init(smem_u32(mbar), 1);
+  if (issuer) tmem_alloc(smem_u32(tslot), Sh::TMEM_COLS);
+  const int G = gridDim.x;
+  int k = blockIdx.x;
+  if (k < a.Eim)
+    for (int c = t; c < NA; c += blockDim.x) s_pv[c] = a.piv[(size_t)k * NA + c];
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *tslot;
+  const uint32_t tlane = (uint32_t)(32 * q) << 16;
+  bool ok = true;
+  uint32_t pend = 0;  // parity of the phase being waited for
+  TcStage<NA, NT> g;
+  if (k < a.Eim && !issuer) tc_load_stage<NA, NT>(g, a, k, s_pv, t);
+  for (int it = 0; k < a.Eim; k += G, ++it) {
+    const int buf = it & 1;
+    const int kn = k + G;
+    if (!issuer) tc_store_stage<NA, NT>(g, Ahi, Alo, Bhi, Blo, t);
+    fence_proxy_async();
+    fence_before_sync();
+    __syncthreads();
+    if (issuer && lane == 0) {
+      tc_issue<NA, NT>(tmem, Ahi, Alo, Bhi, Blo, idesc_tf32(128, Sh::N1), smem_u32(mbar));
+      if (kn < a.Eim) {
+        const size_t o = (size_t)kn;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<const float*>(a.LU) + o * NA * NA),
+                     "r"((unsigned)(NA * NA * 4)) : "memory");
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<const float*>(a.B) + o * NA * NT),
+                     "r"((unsigned)(NA * NT * 4)) : "memory");
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<const float*>(a.C) + o * NT * NA),
+                     "r"((unsigned)(NT * NA * 4)) : "memory");
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<const float*>(a.D) + o * NT * NT),
+                     "r"((unsigned)(NT * NT * 4)) : "memory");
+      }
+    }
+    // the next element's pivots (the other buffer is free: its readers passed the barrier above)
+    if (kn < a.Eim)
+      for (int c = t; c < NA; c += blockDim.x) s_pv[(buf ^ 1) * NA + c] = a.piv[(size_t)kn * NA + c];
+    // C for GEMM 2, read while GEMM 1 runs
+    const float* gC = reinterpret_cast<const float*>(a.C) + (size_t)k * NT * NA;
+    float4 creg[Sh::C_PER];
+#pragma unroll
+    for (int u = 0; u < Sh::C_PER; ++u) {
+      const int task = w + Sh::WARPS * u;
+      const int i = 8 * (task / Sh::CG) + (lane & 7), ch = 4 * (task % Sh::CG) + (lane >> 3);
+      creg[u] = (w < Sh::WARPS && task < Sh::C_TASKS && ch < NA4)
+                    ? __ldg(reinterpret_cast<const float4*>(gC + (size_t)i * NA) + ch)
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    pend = 0;
+    ok = mbar_wait(smem_u32(mbar), 0, TC_TIMEOUT_NS);
+    if (__syncthreads_or(!ok)) {
+      ok = false;
+      break;
+    }
+    fence_after_sync();
+    // ---- epilogue 1: X_B, x_r out; [X_B | x_r]^T as GEMM 2's A operand; C as its B operand
+    if (epi) {
+      float* gXB = reinterpret_cast<float*>(a.XB) + (size_t)k * NA * NT;
+      double* gxr = a.xr + (size_t)k * NA;
+      const int cb = hh == 0 ? 0 : Sh::H1, ce = hh == 0 ? Sh::H1 : Sh::NCH1;
+      for (int cc = cb; cc < ce; ++cc) {
+        float v[16];
+        tmem_ld16(tmem + tlane + (uint32_t)(16 * cc), v);
+        if (rowNT) {  // row NT is x_r: its lane hands the 16 values over through shared memory
+          if (lane == (NT & 31))
+#pragma unroll
+            for (int u = 0; u < 16; u += 4)
+              *reinterpret_cast<float4*>(s_row + 16 * hh + u) = make_float4(v[u], v[u + 1], v[u + 2], v[u + 3]);
+          __syncwarp();
+          if (lane < 16 && 16 * cc + lane < NA) gxr[16 * cc + lane] = double(s_row[16 * hh + lane]);
+          __syncwarp();
+        }
+        if (j <= NT) {
+          if (j < NT) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+              const int i = 16 * cc + u;
+              if (i < NA) gXB[(size_t)i * NT + j] = v[u];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 16; u += 4) {
+            const int i = 16 * cc + u;
+            if (i < K1) {
+              float hs[4], ls[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) split_tf32(i + e < NA ? v[u + e] : 0.f, hs[e], ls[e]);
+              *reinterpret_cast<float4*>(Ahi + kmajor_offset(j, i, SBO)) = make_float4(hs[0], hs[1], hs[2], hs[3]);
+              *reinterpret_cast<float4*>(Alo + kmajor_offset(j, i, SBO)) = make_float4(ls[0], ls[1], ls[2], ls[3]);
+            }
+          }
+        }
+      }
+    }
+    if (w < Sh::WARPS) {
+#pragma unroll
+      for (int u = 0; u < Sh::C_PER; ++u) {
+        const int task = w + Sh::WARPS * u;
+        const int i = 8 * (task / Sh::CG) + (lane & 7), ch = 4 * (task % Sh::CG) + (lane >> 3);
+        if (task < Sh::C_TASKS && ch < Sh::KG) {
+          float hs[4], ls[4];
+          split_tf32(creg[u].x, hs[0], ls[0]);
+          split_tf32(creg[u].y, hs[1], ls[1]);
+          split_tf32(creg[u].z, hs[2], ls[2]);
+          split_tf32(creg[u].w, hs[3], ls[3]);
+          *reinterpret_cast<float4*>(Bhi + kmajor_offset(i, 4 * ch, SBO)) = make_float4(hs[0], hs[1], hs[2], hs[3]);
+          *reinterpret_cast<float4*>(Blo + kmajor_offset(i, 4 * ch, SBO)) = make_float4(ls[0], ls[1], ls[2], ls[3]);
+        }
+      }
+    }
+    fence_proxy_async();
+    fence_before_sync();
+    __syncthreads();
+    if (issuer && lane == 0)
+      tc_issue<NA, NT>(tmem + Sh::D2_COL, Ahi, Alo, Bhi, Blo, idesc_tf32(128, Sh::N2), smem_u32(mbar));
+    // while GEMM 2 runs: the next element's GEMM 1 operands and this element's D and s
+    if (kn < a.Eim && !issuer) tc_load_stage<NA, NT>(g, a, kn, s_pv + (buf ^ 1) * NA, t);
+    const int cb2 = hh == 0 ? 0 : Sh::H2, ce2 = hh == 0 ? Sh::H2 : Sh::NCH2;
+    const float* gD = reinterpret_cast<const float*>(a.D) + (size_t)k * NT * NT;
+    float dreg[16 * Sh::H2];
+#pragma unroll
+    for (int u = 0; u < 16 * Sh::H2; ++u) {
+      const int i = 16 * cb2 + u;
+      dreg[u] = (epi && j < NT && i < 16 * ce2 && i < NT) ? __ldg(gD + (size_t)i * NT + j) : 0.f;
+    }
+    double sreg[Sh::H2];  // lane u of a row-NT warp stores t[16 cc + u]
+#pragma unroll
+    for (int u = 0; u < Sh::H2; ++u) {
+      const int i = 16 * (cb2 + u) + lane;
+      sreg[u] = (rowNT && lane < 16 && cb2 + u < ce2 && i < NT) ? __ldg(a.s + (size_t)k * NT + i) : 0.0;
+    }
+    pend = 1;
+    ok = mbar_wait(smem_u32(mbar), 1, TC_TIMEOUT_NS);
+    if (__syncthreads_or(!ok)) {
+      ok = false;
+      break;
+    }
+    fence_after_sync();
+    // ---- epilogue 2: S = D - C X_B, t = s - C x_r
+    if (epi) {
+      float* gS = reinterpret_cast<float*>(a.S) + (size_t)k * NT * NT;
+      for (int cc = cb2; cc < ce2; ++cc) {
+        float v[16];
+        tmem_ld16(tmem + tlane + Sh::D2_COL + (uint32_t)(16 * cc), v);
+        if (j < NT) {
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const int i = 16 * cc + u;
+            if (i < NT) gS[(size_t)i * NT + j] = dreg[16 * (cc - cb2) + u] - v[u];
+          }
+        }
+        if (rowNT) {
+          if (lane == (NT & 31))
+#pragma unroll
+            for (int u = 0; u < 16; u += 4)
+              *reinterpret_cast<float4*>(s_row + 16 * hh + u) = make_float4(v[u], v[u + 1], v[u + 2], v[u + 3]);
+          __syncwarp();
+          double sv = 0.0;
+#pragma unroll
+          for (int u = 0; u < Sh::H2; ++u)
+            if (cc - cb2 == u) sv = sreg[u];
+          if (lane < 16 && 16 * cc + lane < NT) a.t[(size_t)k * NT + 16 * cc + lane] = sv - double(s_row[16 * hh + lane]);
+          __syncwarp();
+        }
+      }
+    }
+    fence_before_sync();
+  }
+  if (!ok) {
+    if (t == 0) atomicOr(a.status, DEV_ERR_TIMEOUT);
+    mbar_wait(smem_u32(mbar), pend, TC_TIMEOUT_NS);  // let MMAs in flight finish before freeing
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  if (issuer) tmem_dealloc(tmem, Sh::TMEM_COLS);
+}
+
+template <int NA, int NT>
+static cudaError_t launch_products_tc(const CondArgs& a, cudaStream_t st) {
+  using Sh = TcShape<NA, NT>;
+  static int grid = 0;
+  if (grid == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k_products_tc<NA, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Sh::SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0, occ = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_products_tc<NA, NT>, Sh::THREADS, Sh::SMEM)) !=
+        cudaSuccess)
+      return e;
+    // at most two resident CTAs per SM: each holds 256 of the SM's 512 tensor-memory columns
+    grid = nsm * (occ < 1 ? 1 : (occ > 2 ? 2 : occ));
+  }
+  const int g = a.Eim < grid ? a.Eim : grid;
+  (hfr::count_launch(), k_products_tc<NA, NT><<<g, Sh::THREADS, Sh::SMEM, st>>>(a));
+  return cudaGetLastError();
+}
+
 template <int NA, int NT>
 static cudaError_t cond_two_kernel(const CondArgs& a, cudaStream_t st, int part) {
   using P = ProdShape<NA, NT>;
@@ -1092,6 +1456,7 @@ static cudaError_t cond_two_kernel(const CondArgs& a, cudaStream_t st, int part)
     }
     return cudaGetLastError();
   }
+  if (a.products_tc) return launch_products_tc<NA, NT>(a, st);
   if constexpr (NA > 64) {
     using SS = StreamShape<NA, NT>;
     (hfr::count_launch(), k_products_x<NA, NT><<<a.Eim, SS::TX, 0, st>>>(a));
@@ -1504,6 +1869,10 @@ static cudaError_t cond_lu(const CondArgs& a, cudaStream_t st) {
 }
 
 // FP64: LU factors (fewest FP64 operations); FP32: in-place Gauss-Jordan (register tiles).
+bool condense_tc_available(int prec_bytes, int nA, int nT) {
+  return prec_bytes == 4 && ((nA == 100 && nT == 80) || (nA == 64 && nT == 64) || (nA == 36 && nT == 48));
+}
+
 bool condense_uses_lu(int prec_bytes, int nA, int nT) {
   const int rows2 = nA > nT ? nA : nT;
   return prec_bytes == 8 && sizeof(double) * ((size_t)rows2 * nA + (size_t)nA * (nT + 1)) <= 227 * 1024;
