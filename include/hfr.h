@@ -163,16 +163,18 @@ enum fr_gmres_mode { FR_GMRES_MULTI = 0, FR_GMRES_FUSED = 1 };
 int hfr_gmres_set_mode(fr_ctx* ctx, int mode);
 int hfr_gmres_get_mode(const fr_ctx* ctx);
 
-/* Where the FP32 condensation products X = (PA)^{-1}[P B | P r], S = D - C X_B, t = s - C x_r
- * run (Sec. 3.2; this switch has no counterpart in the paper).  FR_PRODUCTS_TENSOR (the default
- * where available: FP32 blocks of shape (nA, nT) = (100, 80), (64, 64), (36, 48)): both products
- * as GEMMs on the tensor cores (tcgen05, TF32 operands split into high and low parts, three
- * products accumulated in FP32: about 2^-21 relative per product term).  FR_PRODUCTS_FMA: the same
- * products on the FP32 FMA pipes.  set: FR_ERR_UNSUPPORTED where the tensor-core form does not
- * exist; get: the mode in effect, -1 for a null context. */
-enum fr_products_mode { FR_PRODUCTS_FMA = 0, FR_PRODUCTS_TENSOR = 1 };
-int hfr_condense_set_products(fr_ctx* ctx, int mode);
-int hfr_condense_get_products(const fr_ctx* ctx);
+/* Which pipes run the FP32 condensation (Sec. 3.2; this switch has no counterpart in the paper).
+ * FR_CONDENSE_TENSOR (the default where available: FP32 blocks of shape (nA, nT) = (100, 80),
+ * (64, 64), (36, 48)): the Gauss-Jordan factorisation as 16-column panels whose trailing updates
+ * are rank-16 products, and the products X = (PA)^{-1}[P B | P r], S = D - C X_B, t = s - C x_r,
+ * all on the tensor cores (tcgen05; TF32 operands split into high and low parts, three products
+ * accumulated in FP32: about 2^-21 relative per product term).  FR_CONDENSE_TENSOR_PRODUCTS: the
+ * products on the tensor cores, the factorisation on the FP32 FMA pipes.  FR_CONDENSE_FMA: both
+ * on the FP32 FMA pipes.  set: FR_ERR_UNSUPPORTED where the requested form does not exist for the
+ * context; get: the mode in effect, -1 for a null context. */
+enum fr_condense_mode { FR_CONDENSE_FMA = 0, FR_CONDENSE_TENSOR_PRODUCTS = 1, FR_CONDENSE_TENSOR = 2 };
+int hfr_condense_set_mode(fr_ctx* ctx, int mode);
+int hfr_condense_get_mode(const fr_ctx* ctx);
 
 /* Self-test of the bounded grid barrier that the single-launch GMRES cycle meets at (no
  * counterpart in the paper; failure detection of that cycle).  One cooperative launch of nblocks

@@ -31,7 +31,7 @@ FR_TAB_BE, FR_TAB_SDIRK2 = 0, 1
 FR_PHYS_ADVDIFF, FR_PHYS_NAVIER_STOKES = 0, 1
 FR_GMRES_MULTI, FR_GMRES_FUSED = 0, 1
 FR_JAC_EVERY_NEWTON, FR_JAC_ONCE_PER_STAGE = 0, 1
-FR_PRODUCTS_FMA, FR_PRODUCTS_TENSOR = 0, 1
+FR_CONDENSE_FMA, FR_CONDENSE_TENSOR_PRODUCTS, FR_CONDENSE_TENSOR = 0, 1, 2
 (FR_OK, FR_ERR_INVALID_ARG, FR_ERR_CUDA, FR_ERR_SINGULAR, FR_ERR_NOT_CONVERGED, FR_ERR_DIVERGED, FR_ERR_TIMEOUT,
  FR_ERR_OOM, FR_ERR_UNSUPPORTED) = range(9)
 EXPORT = {"A": 0, "B": 1, "C": 2, "D": 3, "S": 4, "XB": 5, "xr": 6, "t_k": 7, "r": 8, "s": 9, "t": 10, "Pinv": 11}
@@ -49,8 +49,8 @@ ABI_SYMBOLS = [
     "imex_set_jacobian_policy",
     "hfr_gmres_set_mode",
     "hfr_gmres_get_mode",
-    "hfr_condense_set_products",
-    "hfr_condense_get_products",
+    "hfr_condense_set_mode",
+    "hfr_condense_get_mode",
     "fr_barrier_selftest",
     "hfr_backsolve",
     "hfr_export",
@@ -160,8 +160,8 @@ def load_library(path: str = LIB_PATH):
     lib.imex_set_jacobian_policy.argtypes = [vp, ctypes.c_int]
     lib.hfr_gmres_set_mode.argtypes = [vp, ctypes.c_int]
     lib.hfr_gmres_get_mode.argtypes = [vp]
-    lib.hfr_condense_set_products.argtypes = [vp, ctypes.c_int]
-    lib.hfr_condense_get_products.argtypes = [vp]
+    lib.hfr_condense_set_mode.argtypes = [vp, ctypes.c_int]
+    lib.hfr_condense_get_mode.argtypes = [vp]
     lib.fr_barrier_selftest.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ip, vp]
     lib.hfr_backsolve.argtypes = [vp, dp, dp, ctypes.c_int]
     lib.hfr_export.argtypes = [vp, ctypes.c_int, dp, ctypes.c_size_t]
@@ -343,11 +343,11 @@ class Context:
     def hfr_gmres_get_mode(self) -> int:
         return int(self.lib.hfr_gmres_get_mode(self.h))
 
-    def hfr_condense_set_products(self, mode: int):
-        self._check(self.lib.hfr_condense_set_products(self.h, int(mode)))
+    def hfr_condense_set_mode(self, mode: int):
+        self._check(self.lib.hfr_condense_set_mode(self.h, int(mode)))
 
-    def hfr_condense_get_products(self) -> int:
-        return int(self.lib.hfr_condense_get_products(self.h))
+    def hfr_condense_get_mode(self) -> int:
+        return int(self.lib.hfr_condense_get_mode(self.h))
 
     def hfr_backsolve(self, duhat, refine=0):
         du = self.empty(self.info.nimplicit, self.info.nA)

@@ -53,7 +53,7 @@ struct fr_ctx {
   GmresBuffers gm;
   int gm_mode = 0;          // 0: multi-kernel cycle, 1: one cooperative launch per cycle
   int jac_policy = 0;       // FR_JAC_EVERY_NEWTON or FR_JAC_ONCE_PER_STAGE
-  int products_tc = 0;      // FR_PRODUCTS_TENSOR: FP32 condensation products on the tensor cores
+  int cond_mode = 0;        // fr_condense_mode of the FP32 condensation
   int gm_fused_grid = 0;    // CTAs of the cooperative launch (0: not available)
   unsigned* gm_bar = nullptr;
   double *duhat = nullptr, *du = nullptr, *res_tmp = nullptr, *Ustar = nullptr, *red = nullptr;
@@ -506,7 +506,7 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, const fr_config* cfg, voi
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     ctx->gm_fused_grid = fused_gmres_grid(ctx->prec_bytes, nT, n * nv);
     ctx->gm_mode = ctx->gm_fused_grid > 0 ? 1 : 0;
-    ctx->products_tc = condense_tc_available(ctx->prec_bytes, nA, nT) ? 1 : 0;
+    ctx->cond_mode = condense_tc_available(ctx->prec_bytes, nA, nT);
     const size_t np = std::max((size_t)GM_NBLK * (GM_MAXM + 1), fused_partial_doubles(std::max(nsm, 1)));
     ctx->gm.partial = dalloc<double>(ctx, np, &rc);
     ctx->gm_bar = dalloc<unsigned>(ctx, 64, &rc);
@@ -782,7 +782,7 @@ static int condense_impl(fr_ctx* ctx, int refine) {
   c.S = ctx->S;
   c.t = ctx->te;
   c.status = ctx->status;
-  c.products_tc = ctx->products_tc;
+  c.tc_mode = ctx->cond_mode;
   int ph = prof_begin(ctx, PH_COND);
   CK(launch_condense_part(ctx->prec_bytes, c, ctx->stream, 0));
   prof_end(ctx, ph);
@@ -932,16 +932,16 @@ extern "C" int hfr_gmres_set_mode(fr_ctx* ctx, int mode) {
 
 extern "C" int hfr_gmres_get_mode(const fr_ctx* ctx) { return ctx ? ctx->gm_mode : -1; }
 
-extern "C" int hfr_condense_set_products(fr_ctx* ctx, int mode) {
-  if (!ctx || (mode != FR_PRODUCTS_FMA && mode != FR_PRODUCTS_TENSOR))
-    return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_condense_set_products: bad argument");
-  if (mode == FR_PRODUCTS_TENSOR && !condense_tc_available(ctx->prec_bytes, ctx->nA, ctx->nT))
-    return set_err(ctx, FR_ERR_UNSUPPORTED, "hfr_condense_set_products: no tensor-core products for this precision or shape");
-  ctx->products_tc = mode;
+extern "C" int hfr_condense_set_mode(fr_ctx* ctx, int mode) {
+  if (!ctx || mode < FR_CONDENSE_FMA || mode > FR_CONDENSE_TENSOR)
+    return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_condense_set_mode: bad argument");
+  if (mode > condense_tc_available(ctx->prec_bytes, ctx->nA, ctx->nT))
+    return set_err(ctx, FR_ERR_UNSUPPORTED, "hfr_condense_set_mode: no tensor-core form for this precision or shape");
+  ctx->cond_mode = mode;
   return FR_OK;
 }
 
-extern "C" int hfr_condense_get_products(const fr_ctx* ctx) { return ctx ? ctx->products_tc : -1; }
+extern "C" int hfr_condense_get_mode(const fr_ctx* ctx) { return ctx ? ctx->cond_mode : -1; }
 
 extern "C" int fr_barrier_selftest(int nblocks, int absent_block, int rounds, double timeout_s,
                                    int* barriers_passed, void* stream) {

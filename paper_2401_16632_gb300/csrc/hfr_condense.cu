@@ -706,6 +706,292 @@ __global__ void __launch_bounds__(InvRShape<NA, RPT>::THREADS) k_inverse_rq(cons
   }
 }
 
+// ------------------------------------------- block inverse on the tensor cores (tcgen05)
+// Gauss-Jordan inversion with partial pivoting, in place and without row exchanges, blocked by
+// panels of 16 columns.  The matrix lives in tensor memory (lane = row, one FP32 column per
+// matrix column).  For a panel J the 16 elimination steps run on the panel columns only, in the
+// registers of the row owners (one CTA barrier per step: each warp publishes its best pivot
+// candidate and that row's panel values); the rest of the matrix then receives the panel's
+// combined transformation E A = A + W P as one rank-16 MMA on the tensor cores, with
+// W = E - I on the pivot rows' columns (the panel's in-place result minus the unit entries) and
+// P the pivot rows' values before the panel (zero on the panel columns, which the panel itself
+// produced).  3xTF32 operands, FP32 accumulation in tensor memory.  Output as the register
+// inverse: piv[c] = pivot row of step c and Wt = ((PA)^{-1})^T, Wt[c][c'] = M[piv[c']][c] for the
+// in-place result M.
+template <int NA>
+struct InvTcShape {
+  static constexpr int NC = (NA + 15) / 16 * 16;  // tensor-memory columns / MMA N
+  static constexpr int NP = (NA + 15) / 16;       // panels
+  static constexpr int THREADS = 128;
+  static constexpr int RB = NC + 8;               // row buffer stride (conflict-free transposition)
+  static constexpr uint32_t SBO = 4u * 128u;      // K = 16: four 4-element chunks per 8-row group
+  static constexpr uint32_t W_BYTES = 128u * 16u * 4u, P_BYTES = (uint32_t)NC * 16u * 4u;
+  static constexpr uint32_t OFF_WLO = W_BYTES, OFF_PHI = 2 * W_BYTES, OFF_PLO = 2 * W_BYTES + P_BYTES;
+  static constexpr uint32_t OFF_RB = 2 * W_BYTES + 2 * P_BYTES;
+  static constexpr int NQ = (NC + 31) / 32;     // 32-column groups (tensor-memory loads, output)
+  static constexpr uint32_t OFF_CAND = OFF_RB + 32u * RB * 4u;
+  static constexpr uint32_t OFF_KEY = OFF_CAND + 2u * 4u * 16u * 4u;
+  static constexpr uint32_t OFF_MBAR = OFF_KEY + 2u * 4u * 4u;
+  static constexpr uint32_t NEED = OFF_MBAR + 16u;
+  // requested so that at most four CTAs share an SM: each holds 128 of its 512 tensor-memory columns
+  static constexpr uint32_t SMEM = NEED > 51200u ? NEED : 51200u;
+  static_assert(NA <= 112 && NA % 4 == 0 && 16 * RB >= 16 * NA, "shape");
+};
+
+template <int NA>
+__global__ void __launch_bounds__(128, 4) k_inverse_tc(const __grid_constant__ CondArgs a) {
+  using Sh = InvTcShape<NA>;
+  using namespace tc;
+  constexpr int NC = Sh::NC, NP = Sh::NP, RB = Sh::RB;
+  constexpr unsigned MASK = 127u;
+  extern __shared__ __align__(1024) unsigned char iv_smem[];
+  unsigned char* Whi = iv_smem;
+  unsigned char* Wlo = iv_smem + Sh::OFF_WLO;
+  unsigned char* Phi = iv_smem + Sh::OFF_PHI;
+  unsigned char* Plo = iv_smem + Sh::OFF_PLO;
+  float* rowbuf = reinterpret_cast<float*>(iv_smem + Sh::OFF_RB);
+  float* cand = reinterpret_cast<float*>(iv_smem + Sh::OFF_CAND);  // [2][4][16]
+  unsigned* s_key = reinterpret_cast<unsigned*>(iv_smem + Sh::OFF_KEY);  // [2][4]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(iv_smem + Sh::OFF_MBAR);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int row = t;  // tensor-memory lane of this thread
+  if (t == 0) mbar_init(smem_u32(mbar), 1);
+  if (w == 0) tmem_alloc(smem_u32(tslot), 128);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *tslot;
+  const uint32_t tl = tmem + ((uint32_t)(32 * w) << 16);
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int k = blockIdx.x; k < a.Eim && ok; k += gridDim.x) {
+    // ---- the block into tensor memory (row = lane; columns >= NA zero)
+    const float* gA = reinterpret_cast<const float*>(a.A) + (size_t)k * NA * NA;
+    if (t == 0 && k + (int)gridDim.x < a.Eim)
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(gA + (size_t)gridDim.x * NA * NA),
+                   "r"((unsigned)(NA * NA * 4)) : "memory");
+    // two 16-column chunks per round: eight 16-byte loads of the row in flight
+#pragma unroll 1
+    for (int cc = 0; cc < NP; cc += 2) {
+      float v[2][16];
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int u = 0; u < 16; u += 4) {
+          const int c = 16 * (cc + h) + u;
+          float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (row < NA && c < NA) x = __ldg(reinterpret_cast<const float4*>(gA + (size_t)row * NA + c));
+          v[h][u] = x.x; v[h][u + 1] = x.y; v[h][u + 2] = x.z; v[h][u + 3] = x.w;
+        }
+      tmem_st16(tl + (uint32_t)(16 * cc), v[0]);
+      if (cc + 1 < NP) tmem_st16(tl + (uint32_t)(16 * (cc + 1)), v[1]);
+    }
+    tmem_st_wait();
+    bool used = row >= NA;
+    int mystep = -1;
+    bool bad = false;
+#pragma unroll 1
+    for (int p = 0; p < NP; ++p) {
+      const int ns = NA - 16 * p < 16 ? NA - 16 * p : 16;
+      float v[16];
+      fence_before_sync();
+      __syncthreads();
+      fence_after_sync();
+      tmem_ld16(tl + (uint32_t)(16 * p), v);
+      // pivot candidates of column 0 of the panel
+      {
+        const unsigned key = used ? 0u : ((__float_as_uint(fabsf(v[0])) & ~MASK) | (MASK - (unsigned)row));
+        const unsigned wk = __reduce_max_sync(0xffffffffu, key);
+        if (key == wk && wk != 0u) {
+#pragma unroll
+          for (int u = 0; u < 16; u += 4)
+            *reinterpret_cast<float4*>(cand + (0 * 4 + w) * 16 + u) = make_float4(v[u], v[u + 1], v[u + 2], v[u + 3]);
+        }
+        if (lane == 0) s_key[0 * 4 + w] = wk;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int s = 0; s < 16; ++s) {
+        if (s < ns) {
+          const int b = s & 1;
+          unsigned km = s_key[b * 4 + 0];
+          int wb = 0;
+#pragma unroll
+          for (int w2 = 1; w2 < 4; ++w2) {
+            const unsigned kw = s_key[b * 4 + w2];
+            if (kw > km) {
+              km = kw;
+              wb = w2;
+            }
+          }
+          const int r = (int)(MASK - (km & MASK));
+          if ((km & ~MASK) == 0u) bad = true;
+          float prow[16];
+#pragma unroll
+          for (int u = 0; u < 16; u += 4) {
+            const float4 x = *reinterpret_cast<const float4*>(cand + (b * 4 + wb) * 16 + u);
+            prow[u] = x.x; prow[u + 1] = x.y; prow[u + 2] = x.z; prow[u + 3] = x.w;
+          }
+          const float pv = prow[s];
+          const float pinv = pv != 0.f ? 1.f / pv : 0.f;
+          if (row == r) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) v[u] = prow[u] * pinv;
+            v[s] = pinv;
+            used = true;
+            mystep = 16 * p + s;
+          } else {
+            const float g = v[s] * pinv;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) v[u] -= g * prow[u];
+            v[s] = -g;
+          }
+          if (t == 0) a.piv[(size_t)k * NA + 16 * p + s] = r;
+          if (s + 1 < ns) {
+            const unsigned key = used ? 0u : ((__float_as_uint(fabsf(v[s + 1])) & ~MASK) | (MASK - (unsigned)row));
+            const unsigned wk = __reduce_max_sync(0xffffffffu, key);
+            if (key == wk && wk != 0u) {
+#pragma unroll
+              for (int u = 0; u < 16; u += 4)
+                *reinterpret_cast<float4*>(cand + ((b ^ 1) * 4 + w) * 16 + u) =
+                    make_float4(v[u], v[u + 1], v[u + 2], v[u + 3]);
+            }
+            if (lane == 0) s_key[(b ^ 1) * 4 + w] = wk;
+            __syncthreads();
+          }
+        }
+      }
+      // ---- W = E - I on the pivot columns (rows: all), 3xTF32 split, K-major 16-byte chunks
+#pragma unroll
+      for (int sc = 0; sc < 4; ++sc) {
+        float hs[4], ls[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int s = 4 * sc + e;
+          const float x = s < ns ? v[s] - (mystep == 16 * p + s ? 1.f : 0.f) : 0.f;
+          split_tf32(x, hs[e], ls[e]);
+        }
+        *reinterpret_cast<float4*>(Whi + kmajor_offset(row, 4 * sc, Sh::SBO)) = make_float4(hs[0], hs[1], hs[2], hs[3]);
+        *reinterpret_cast<float4*>(Wlo + kmajor_offset(row, 4 * sc, Sh::SBO)) = make_float4(ls[0], ls[1], ls[2], ls[3]);
+      }
+      // ---- P: the pivot rows before the panel (panel columns zero) into the row buffer; only
+      // warps that hold one of the panel's pivot rows read tensor memory
+      const bool prow_here = used && mystep >= 16 * p && mystep < 16 * p + ns;
+      if (__any_sync(0xffffffffu, prow_here)) {
+        for (int cq = 0; cq < Sh::NQ; ++cq) {
+          float x[32];
+          tmem_ld32(tl + (uint32_t)(32 * cq), x);
+          if (prow_here) {
+            float* dst = rowbuf + (mystep - 16 * p) * RB + 32 * cq;
+#pragma unroll
+            for (int u = 0; u < 32; u += 4) {
+              const int c = 32 * cq + u;
+              if (c < NC)
+                *reinterpret_cast<float4*>(dst + u) = (c >= 16 * p && c < 16 * p + 16)
+                                                          ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                                          : make_float4(x[u], x[u + 1], x[u + 2], x[u + 3]);
+            }
+          }
+        }
+      }
+      if (ns < 16)
+        for (int e = t; e < (16 - ns) * NC; e += Sh::THREADS) rowbuf[(ns + e / NC) * RB + e % NC] = 0.f;
+      // the panel's in-place result replaces its columns (the MMA adds zero there)
+      tmem_st16(tl + (uint32_t)(16 * p), v);
+      tmem_st_wait();
+      __syncthreads();
+      // ---- row buffer -> P operand (rows = matrix columns j, K = pivot index), 3xTF32 split
+      for (int e = t; e < NC * 16; e += Sh::THREADS) {
+        const int sl = e & 3, jl = (e >> 2) & 7, rest = e >> 5;
+        const int sidx = 4 * (rest & 3) + sl, j = 8 * (rest >> 2) + jl;
+        float h, l;
+        split_tf32(rowbuf[sidx * RB + j], h, l);
+        *reinterpret_cast<float*>(Phi + kmajor_offset(j, sidx, Sh::SBO)) = h;
+        *reinterpret_cast<float*>(Plo + kmajor_offset(j, sidx, Sh::SBO)) = l;
+      }
+      fence_proxy_async();
+      fence_before_sync();
+      __syncthreads();
+      if (t == 0) {
+        fence_after_sync();
+        constexpr uint32_t idesc = idesc_tf32(128, NC);
+        const uint32_t wh = smem_u32(Whi), wl = smem_u32(Wlo), ph = smem_u32(Phi), pl = smem_u32(Plo);
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+          const uint32_t off = (uint32_t)kk * 256u;
+          mma_tf32(tmem, desc_noswizzle(wh + off, 128, Sh::SBO), desc_noswizzle(ph + off, 128, Sh::SBO), idesc, 1);
+          mma_tf32(tmem, desc_noswizzle(wh + off, 128, Sh::SBO), desc_noswizzle(pl + off, 128, Sh::SBO), idesc, 1);
+          mma_tf32(tmem, desc_noswizzle(wl + off, 128, Sh::SBO), desc_noswizzle(ph + off, 128, Sh::SBO), idesc, 1);
+        }
+        mma_commit(smem_u32(mbar));
+      }
+      ok = mbar_wait(smem_u32(mbar), phase, tc::TIMEOUT_NS);
+      phase ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        ok = false;
+        break;
+      }
+      fence_after_sync();
+    }
+    if (!ok) break;
+    if (__syncthreads_or(bad) && t == 0) {
+      atomicOr(a.status, DEV_ERR_SINGULAR);
+      atomicMin(a.status + 1, k);
+    }
+    // ---- output: Wt[c][c'] = M[piv[c']][c], through the row buffer 32 columns at a time
+    float* gWt = reinterpret_cast<float*>(a.LU) + (size_t)k * NA * NA;
+#pragma unroll 1
+    for (int cq = 0; cq < Sh::NQ; ++cq) {
+      float x[32];
+      tmem_ld32(tl + (uint32_t)(32 * cq), x);
+      if (row < NA && mystep >= 0)
+#pragma unroll
+        for (int u = 0; u < 32; ++u)
+          if (32 * cq + u < NA) rowbuf[u * RB + mystep] = x[u];
+      __syncthreads();
+      const int nrow = NA - 32 * cq < 32 ? NA - 32 * cq : 32;
+      for (int e = t; e < nrow * (NA / 4); e += Sh::THREADS) {
+        const int u = e / (NA / 4), i4 = e % (NA / 4);
+        *reinterpret_cast<float4*>(gWt + (size_t)(32 * cq + u) * NA + 4 * i4) =
+            *reinterpret_cast<const float4*>(rowbuf + u * RB + 4 * i4);
+      }
+      __syncthreads();
+    }
+  }
+  if (!ok) {
+    if (t == 0) atomicOr(a.status, DEV_ERR_TIMEOUT);
+    mbar_wait(smem_u32(mbar), phase ^ 1u, tc::TIMEOUT_NS);
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  if (w == 0) tmem_dealloc(tmem, 128);
+}
+
+template <int NA>
+static cudaError_t launch_inverse_tc(const CondArgs& a, cudaStream_t st) {
+  using Sh = InvTcShape<NA>;
+  static int grid = 0;
+  if (grid == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k_inverse_tc<NA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_inverse_tc<NA>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    // resident CTAs per SM from the shared-memory arithmetic (at most four: tensor memory)
+    int dev = 0, nsm = 0, smem_sm = 0, resv = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess) return e;
+    int fit = smem_sm / (int)(Sh::SMEM + (uint32_t)resv);
+    grid = nsm * (fit < 1 ? 1 : (fit > 4 ? 4 : fit));
+  }
+  const int g = a.Eim < grid ? a.Eim : grid;
+  (hfr::count_launch(), k_inverse_tc<NA><<<g, Sh::THREADS, Sh::SMEM, st>>>(a));
+  return cudaGetLastError();
+}
+
 template <int NA, int NT>
 struct ProdShape {
   static constexpr int TI = (NA + 7) / 8;  // row tiles of X
@@ -1124,8 +1410,6 @@ struct TcShape {
   static_assert(SMEM <= 232448, "shared memory");
 };
 
-constexpr unsigned long long TC_TIMEOUT_NS = 2000000000ull;
-
 // GEMM 1 operands of one element held in registers between their load and their store
 template <int NA, int NT>
 struct TcStage {
@@ -1292,7 +1576,7 @@ __global__ void __launch_bounds__(256, 1) k_products_tc(const __grid_constant__ 
                     : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     pend = 0;
-    ok = mbar_wait(smem_u32(mbar), 0, TC_TIMEOUT_NS);
+    ok = mbar_wait(smem_u32(mbar), 0, tc::TIMEOUT_NS);
     if (__syncthreads_or(!ok)) {
       ok = false;
       break;
@@ -1375,7 +1659,7 @@ __global__ void __launch_bounds__(256, 1) k_products_tc(const __grid_constant__ 
       sreg[u] = (rowNT && lane < 16 && cb2 + u < ce2 && i < NT) ? __ldg(a.s + (size_t)k * NT + i) : 0.0;
     }
     pend = 1;
-    ok = mbar_wait(smem_u32(mbar), 1, TC_TIMEOUT_NS);
+    ok = mbar_wait(smem_u32(mbar), 1, tc::TIMEOUT_NS);
     if (__syncthreads_or(!ok)) {
       ok = false;
       break;
@@ -1413,7 +1697,7 @@ __global__ void __launch_bounds__(256, 1) k_products_tc(const __grid_constant__ 
   }
   if (!ok) {
     if (t == 0) atomicOr(a.status, DEV_ERR_TIMEOUT);
-    mbar_wait(smem_u32(mbar), pend, TC_TIMEOUT_NS);  // let MMAs in flight finish before freeing
+    mbar_wait(smem_u32(mbar), pend, tc::TIMEOUT_NS);  // let MMAs in flight finish before freeing
   }
   fence_before_sync();
   __syncthreads();
@@ -1428,6 +1712,8 @@ static cudaError_t launch_products_tc(const CondArgs& a, cudaStream_t st) {
   if (grid == 0) {
     cudaError_t e = cudaFuncSetAttribute(k_products_tc<NA, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Sh::SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_products_tc<NA, NT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0, occ = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -1447,6 +1733,7 @@ template <int NA, int NT>
 static cudaError_t cond_two_kernel(const CondArgs& a, cudaStream_t st, int part) {
   using P = ProdShape<NA, NT>;
   if (part == 0) {
+    if (a.tc_mode == 2) return launch_inverse_tc<NA>(a, st);
     if constexpr (NA <= 64) {
       constexpr int WPB = InvWShape<NA>::WPB;
       (hfr::count_launch(), k_inverse_warp<NA><<<(a.Eim + WPB - 1) / WPB, 32 * WPB, 0, st>>>(a));
@@ -1456,7 +1743,7 @@ static cudaError_t cond_two_kernel(const CondArgs& a, cudaStream_t st, int part)
     }
     return cudaGetLastError();
   }
-  if (a.products_tc) return launch_products_tc<NA, NT>(a, st);
+  if (a.tc_mode >= 1) return launch_products_tc<NA, NT>(a, st);
   if constexpr (NA > 64) {
     using SS = StreamShape<NA, NT>;
     (hfr::count_launch(), k_products_x<NA, NT><<<a.Eim, SS::TX, 0, st>>>(a));
@@ -1869,8 +2156,8 @@ static cudaError_t cond_lu(const CondArgs& a, cudaStream_t st) {
 }
 
 // FP64: LU factors (fewest FP64 operations); FP32: in-place Gauss-Jordan (register tiles).
-bool condense_tc_available(int prec_bytes, int nA, int nT) {
-  return prec_bytes == 4 && ((nA == 100 && nT == 80) || (nA == 64 && nT == 64) || (nA == 36 && nT == 48));
+int condense_tc_available(int prec_bytes, int nA, int nT) {
+  return prec_bytes == 4 && ((nA == 100 && nT == 80) || (nA == 64 && nT == 64) || (nA == 36 && nT == 48)) ? 2 : 0;
 }
 
 bool condense_uses_lu(int prec_bytes, int nA, int nT) {

@@ -84,7 +84,9 @@ struct CondArgs {
   void* S;
   double* t;        // Eim x nT
   int* status;      // device status word (DEV_ERR_*), first failing element in status[1]
-  int products_tc = 0;  // FP32 blocks: products on the tensor cores (3xTF32) instead of FP32 FMA
+  // FP32 blocks: 0 = factorisation and products on the FP32 FMA pipes, 1 = products on the tensor
+  // cores (3xTF32), 2 = factorisation and products on the tensor cores
+  int tc_mode = 0;
 };
 cudaError_t launch_condense(int prec_bytes, const CondArgs& a, cudaStream_t st);
 // the same in two parts: 0 = factorisation (the whole condensation where it is one kernel),
@@ -94,8 +96,8 @@ cudaError_t launch_condense_part(int prec_bytes, const CondArgs& a, cudaStream_t
 // x = A^{-1} b with the stored factorisation (LU + interchanges or in-place inverse, as chosen
 // by condense_uses_lu), in place on b (Eim x nA, FP64 vectors).
 bool condense_uses_lu(int prec_bytes, int nA, int nT);
-// the tensor-core products (CondArgs::products_tc) exist for this precision and block shape
-bool condense_tc_available(int prec_bytes, int nA, int nT);
+// highest CondArgs::tc_mode available for this precision and block shape (0: none)
+int condense_tc_available(int prec_bytes, int nA, int nT);
 cudaError_t launch_lu_solve(int prec_bytes, int Eim, int nA, int nT, const void* LU, const int* piv, double* b,
                             cudaStream_t st);
 

@@ -42,7 +42,7 @@ def test_noalloc_condense_matches_context_condense(precision):
     w = make_config("vortex", n=5, p=3, jitter=0.15, seed=9, re=200.0)
     ctx = pkg.Context(w.mesh, w.physics, precision=prec)
     if prec == pkg.FR_PREC_FP32:  # the allocation-free entry runs the FP32-FMA products
-        ctx.hfr_condense_set_products(pkg.FR_PRODUCTS_FMA)
+        ctx.hfr_condense_set_mode(pkg.FR_CONDENSE_FMA)
     u = torch.tensor(w.u0, device="cuda")
     uh = ctx.hfr_initial_trace(u)
     ctx.hfr_local_jacobian(u, uh, u * 0.999, 0.037)
