@@ -43,6 +43,7 @@ NEWTON_TOL = 1e-8
 GMRES_RTOL = 1e-4
 FP32_PEAK_PER_SM_CLK = 256.0  # 128 FP32 FMA lanes x 2 flops
 FP64_PEAK_PER_SM_CLK = 4.0    # 2 FP64 FMA per clock per SM (1.25 TFLOP/s at 2.07 GHz, 152 SMs)
+TF32_PER_BF16 = 0.5           # dense TF32 tensor rate / dense BF16 rate
 NUM_SMS = 152
 
 
@@ -259,10 +260,12 @@ def _threads():
 # (summaries under profiles/), per workload; None where not captured or the kernel changed since
 # vortex256: captured on the same kernels over 64x64 elements (p = 4) and scaled by the element
 # count (x16) where the traffic is per element (factorisation, products, Jacobian)
-NCU_TRAFFIC_BYTES = {"vortex256": {"k_inverse_rq": 16 * (169.68e6 + 109.01e6),
+NCU_TRAFFIC_BYTES = {"vortex256": {"k_inverse_tc": 16 * (165.59e6 + 109.09e6),
+                                   "k_products_tc": 16 * (539.30e6 + 211.38e6),
+                                   "k_inverse_rq": 16 * (169.68e6 + 109.01e6),
                                    "k_products_x": 16 * (299.90e6 + 101.01e6),
                                    "k_products_s": 16 * (372.94e6 + 85.81e6),
-                                   "k_jacobian": 16 * (20.99e6 + 476.61e6)},
+                                   "k_jacobian": 16 * (21.17e6 + 476.68e6)},
                      "vortex64": {
     "k_inverse_warp": 69.08e6 + 13.06e6,
     "k_condense_products": 273.96e6 + 102.35e6,
@@ -271,16 +274,18 @@ NCU_TRAFFIC_BYTES = {"vortex256": {"k_inverse_rq": 16 * (169.68e6 + 109.01e6),
 }}
 
 
-def kernel_rooflines(prof, stats, w, peaks, clocks, workload):
+def kernel_rooflines(prof, stats, w, peaks, clocks, workload, cond_mode=2):
     """Roofline of every single-kernel phase of the timed step, from the live CUDA-event phase
     timings (average launch duration), and the dominant one (largest total time).
     Algorithmic work per launch (E elements, nA = 4 n^2, nT = 16 n, face blocks bs = 4 n, ntrace = 2E faces,
     n_t = 16 ntrace trace unknowns, k = GMRES iterations per solve):
       k_gmres_cycle       HBM: k (S_k blocks E nT^2 4 B + face inverses ntrace bs^2 4 B
                           + Krylov passes 4 (k/2 + 1) n_t 4 B + z, w 2 n_t 4 B)
-      k_inverse_warp      ALU: Gauss-Jordan inverse 2 nA^3 flop per element
-      k_condense_products ALU 2 (nA^2 (nT+1) + nT nA (nT+1)) flop per element, or HBM
-                          4 (nA^2 + 2 nA nT + nT^2) B in + 4 (nA nT + nT^2) B out per element,
+      k_inverse_tc        Gauss-Jordan inverse 2 nA^3 flop per element, against the FP32 FMA roof (the
+                          panel eliminations on the FP32 pipes set its time; the rank-16 trailing
+                          updates run on the tensor cores)
+      k_products_tc       HBM 4 (nA^2 + 2 nA nT + nT^2) B in + 4 (nA nT + nT^2) B out per element, or the
+                          TF32 tensor roof for 2 (nA^2 (nT+1) + nT nA (nT+1)) flop per element,
                           whichever fraction is higher
       k_jacobian          ALU: (nA+nT)^2 (2n+4) 2 flop per element (n = p + 1)
     """
@@ -292,6 +297,7 @@ def kernel_rooflines(prof, stats, w, peaks, clocks, workload):
     mhz = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
     alu_peak = NUM_SMS * FP32_PEAK_PER_SM_CLK * mhz * 1e6 / 1e12
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    tf32_peak = float(peaks.get("bf16_tflops", 1900.0)) * TF32_PER_BF16
     its = stats["gmres_iterations"] / max(stats["newton_iterations"], 1)
     out = {}
 
@@ -302,25 +308,30 @@ def kernel_rooflines(prof, stats, w, peaks, clocks, workload):
     def entry(kern, bound, achieved, peak, unit, total_ms, avg_ms):
         tw = NCU_TRAFFIC_BYTES.get(workload, {})
         t = sum(tw[kk] for kk in kern.split("+")) if all(tw.get(kk) for kk in kern.split("+")) else None
-        return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-                "traffic": t, "kernel": kern, "avg_launch_ms": avg_ms, "total_ms": total_ms,
-                "peak_source": ("MEASURED_PEAKS.json hbm_gbs" if unit == "GB/s"
-                                else f"FP32 lanes x {mhz:.0f} MHz x {NUM_SMS} SMs")}
+        src = {"GB/s": "MEASURED_PEAKS.json hbm_gbs",
+               "TFLOP/s": f"FP32 lanes x {mhz:.0f} MHz x {NUM_SMS} SMs",
+               "TF32 TFLOP/s": f"MEASURED_PEAKS.json bf16_tflops x {TF32_PER_BF16} (nominal TF32 / BF16 ratio)"}[unit]
+        return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit.replace("TF32 ", ""),
+                "frac": achieved / peak, "traffic": t, "kernel": kern, "avg_launch_ms": avg_ms, "total_ms": total_ms,
+                "peak_source": src}
 
     tot, a = avg("gmres")
     per_it = E * nT * nT * 4 + ntrace * bs * bs * 4 + 4 * (its / 2 + 1) * nt_u * 4 + 2 * nt_u * 4
     out["gmres"] = entry("k_gmres_cycle", "hbm", per_it * its / (a * 1e-3) / 1e9, hbm_peak, "GB/s", tot, a)
     tot, a = avg("condense_factor")
-    out["condense_factor"] = entry("k_inverse_warp" if nA <= 64 else "k_inverse_rq", "alu", E * 2.0 * nA**3 / (a * 1e-3) / 1e12, alu_peak,
-                                   "TFLOP/s", tot, a)
+    inv = "k_inverse_tc" if cond_mode == 2 else ("k_inverse_warp" if nA <= 64 else "k_inverse_rq")
+    out["condense_factor"] = entry(inv, "alu", E * 2.0 * nA**3 / (a * 1e-3) / 1e12, alu_peak, "TFLOP/s", tot, a)
     tot, a = avg("condense_products")
     fl = E * 2.0 * (nA * nA * (nT + 1) + nT * nA * (nT + 1)) / (a * 1e-3) / 1e12
     by = E * (4.0 * (nA * nA + 2 * nA * nT + nT * nT) + 4.0 * (nA * nT + nT * nT)) / (a * 1e-3) / 1e9
-    pk = "k_condense_products" if nA <= 64 else "k_products_x+k_products_s"
-    if by / hbm_peak > fl / alu_peak:
+    if cond_mode >= 1:
+        pk, fpk, funit = "k_products_tc", tf32_peak, "TF32 TFLOP/s"
+    else:
+        pk, fpk, funit = ("k_condense_products" if nA <= 64 else "k_products_x+k_products_s"), alu_peak, "TFLOP/s"
+    if by / hbm_peak > fl / fpk:
         out["condense_products"] = entry(pk, "hbm", by, hbm_peak, "GB/s", tot, a)
     else:
-        out["condense_products"] = entry(pk, "alu", fl, alu_peak, "TFLOP/s", tot, a)
+        out["condense_products"] = entry(pk, "tensor" if cond_mode >= 1 else "alu", fl, fpk, funit, tot, a)
     tot, a = avg("jacobian")
     out["jacobian"] = entry("k_jacobian", "alu", E * (nA + nT) ** 2 * (2 * n + 4) * 2.0 / (a * 1e-3) / 1e12,
                             alu_peak, "TFLOP/s", tot, a)
@@ -394,7 +405,8 @@ def main():
         e2e_ms = replica_max([e2e_ms], dist, dev)[0]
     peaks, peak_src = _peaks()
     pm = {k: v[0] for k, v in mixed["profile"].items()}
-    dom, kroofs = kernel_rooflines(mixed["profile"], mixed["stats"], w, peaks, clocks, args.workload)
+    dom, kroofs = kernel_rooflines(mixed["profile"], mixed["stats"], w, peaks, clocks, args.workload,
+                                   mixed["ctx"].hfr_condense_get_mode())
     roof = {k: v for k, v in kroofs[dom].items() if k != "total_ms"}
     line = {
         "metric": METRIC,
