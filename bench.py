@@ -266,12 +266,7 @@ NCU_TRAFFIC_BYTES = {"vortex256": {"k_inverse_tc": 16 * (165.59e6 + 109.09e6),
                                    "k_products_x": 16 * (299.90e6 + 101.01e6),
                                    "k_products_s": 16 * (372.94e6 + 85.81e6),
                                    "k_jacobian": 16 * (21.17e6 + 476.68e6)},
-                     "vortex64": {
-    "k_inverse_warp": 69.08e6 + 13.06e6,
-    "k_condense_products": 273.96e6 + 102.35e6,
-    "k_gmres_cycle": 82.05e6 + 2.22e6,
-    "k_jacobian": None,
-}}
+                     "vortex64": {}}
 
 
 def kernel_rooflines(prof, stats, w, peaks, clocks, workload, cond_mode=2):
