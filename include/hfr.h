@@ -212,6 +212,19 @@ int imex_stage(fr_ctx* ctx, int stage, double dt, const double* u_n, double* u_s
                double* R_hist, double newton_tol, int newton_maxit, double gmres_rtol, int gmres_maxit,
                int refine, fr_stage_stats* stats /* host, nullable */);
 
+/* Run each implicit stage of imex_stage as one CUDA graph (on = 1; no counterpart in the paper).
+ * The graph holds the whole stage: the Newton loop as a conditional WHILE node, its linear solve
+ * (blocks, condensation, GMRES restart cycles as a nested WHILE node, back-substitution, update)
+ * as a conditional IF node, with the convergence tests of Algorithm 1 and of GMRES taken by small
+ * device kernels, so that the host launches the stage once and reads its counters once.  The
+ * first call with a given (stage, dt, buffers, tolerances, limits, refine) captures and
+ * instantiates the graph; later calls with the same arguments replay it.  Results equal the
+ * stream path's.  Requires implicit elements, FR_JAC_EVERY_NEWTON and (with a trace)
+ * FR_GMRES_FUSED: FR_ERR_UNSUPPORTED otherwise.  Per-phase profiling (fr_profile_*) sees no
+ * phases of a graph stage. */
+int imex_stage_set_graph(fr_ctx* ctx, int on);
+int imex_stage_get_graph(const fr_ctx* ctx);
+
 /* Initial trace guess: average of both sides' interpolated states (uhat: ntrace x n x nv). */
 int hfr_initial_trace(fr_ctx* ctx, const double* u, double* uhat);
 

@@ -51,6 +51,8 @@ ABI_SYMBOLS = [
     "hfr_gmres_get_mode",
     "hfr_condense_set_mode",
     "hfr_condense_get_mode",
+    "imex_stage_set_graph",
+    "imex_stage_get_graph",
     "fr_barrier_selftest",
     "hfr_backsolve",
     "hfr_export",
@@ -162,6 +164,8 @@ def load_library(path: str = LIB_PATH):
     lib.hfr_gmres_get_mode.argtypes = [vp]
     lib.hfr_condense_set_mode.argtypes = [vp, ctypes.c_int]
     lib.hfr_condense_get_mode.argtypes = [vp]
+    lib.imex_stage_set_graph.argtypes = [vp, ctypes.c_int]
+    lib.imex_stage_get_graph.argtypes = [vp]
     lib.fr_barrier_selftest.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ip, vp]
     lib.hfr_backsolve.argtypes = [vp, dp, dp, ctypes.c_int]
     lib.hfr_export.argtypes = [vp, ctypes.c_int, dp, ctypes.c_size_t]
@@ -342,6 +346,12 @@ class Context:
 
     def hfr_gmres_get_mode(self) -> int:
         return int(self.lib.hfr_gmres_get_mode(self.h))
+
+    def imex_stage_set_graph(self, on: bool = True):
+        self._check(self.lib.imex_stage_set_graph(self.h, 1 if on else 0))
+
+    def imex_stage_get_graph(self) -> int:
+        return int(self.lib.imex_stage_get_graph(self.h))
 
     def hfr_condense_set_mode(self, mode: int):
         self._check(self.lib.hfr_condense_set_mode(self.h, int(mode)))

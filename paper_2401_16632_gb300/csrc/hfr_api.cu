@@ -23,6 +23,26 @@ using namespace hfr;
 static std::atomic<unsigned long long> g_launches(0);
 void hfr::count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+// Device-side state of a stage run as one CUDA graph (imex_stage_set_graph): Newton norms and
+// counters, and the arguments of the next GMRES restart cycle.
+struct StageDev {
+  double norm0, norm;
+  int it, gtot, conv, err;  // err bits: 1 non-finite residual, 2 non-finite GMRES, 4 barrier timeout
+  int gm_total, cycles;
+  int dyn[2];  // x_zero, m of the next restart cycle
+};
+
+struct StageGraphKey {
+  int stage, nmax, gmax, refine;
+  double dt, ntol, grtol;
+  const double *u_n, *u_stage, *uhat, *R_hist;
+  bool operator==(const StageGraphKey& o) const {
+    return stage == o.stage && nmax == o.nmax && gmax == o.gmax && refine == o.refine && dt == o.dt &&
+           ntol == o.ntol && grtol == o.grtol && u_n == o.u_n && u_stage == o.u_stage && uhat == o.uhat &&
+           R_hist == o.R_hist;
+  }
+};
+
 struct fr_ctx {
   int E = 0, p = 0, n = 0, ns = 0, nv = 0, nA = 0, nT = 0, ntrace = 0, Eim = 0;
   int prec_bytes = 8;
@@ -54,6 +74,16 @@ struct fr_ctx {
   int gm_mode = 0;          // 0: multi-kernel cycle, 1: one cooperative launch per cycle
   int jac_policy = 0;       // FR_JAC_EVERY_NEWTON or FR_JAC_ONCE_PER_STAGE
   int cond_mode = 0;        // fr_condense_mode of the FP32 condensation
+  // whole-stage CUDA graph
+  int use_graph = 0;
+  StageDev* sdev = nullptr;
+  cudaStream_t cap[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool gvalid = false;
+  StageGraphKey gkey{};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int gl_top = 0, gl_newton = 0, gl_solve = 0, gl_cycle = 0;  // kernel launches per part of the graph
+  unsigned long long gl_replayed = 0;                            // kernel executions in graph replays
   int gm_fused_grid = 0;    // CTAs of the cooperative launch (0: not available)
   unsigned* gm_bar = nullptr;
   double *duhat = nullptr, *du = nullptr, *res_tmp = nullptr, *Ustar = nullptr, *red = nullptr;
@@ -512,6 +542,7 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, const fr_config* cfg, voi
     ctx->gm_bar = dalloc<unsigned>(ctx, 64, &rc);
   }
   ctx->gm.state = dalloc<GmresState>(ctx, 1, &rc);
+  ctx->sdev = dalloc<StageDev>(ctx, 1, &rc);
   ctx->gm.ticket = dalloc<unsigned int>(ctx, 1, &rc);
   ctx->gm.z32 = ctx->prec_bytes == 4 ? dalloc<float>(ctx, std::max(nh, (size_t)1), &rc) : nullptr;
   ctx->duhat = dalloc<double>(ctx, nh, &rc);
@@ -557,6 +588,10 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, const fr_config* cfg, voi
 
 extern "C" void fr_ctx_destroy(fr_ctx* ctx) {
   if (!ctx) return;
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  for (cudaStream_t c : ctx->cap)
+    if (c) cudaStreamDestroy(c);
   for (void* p : ctx->allocs) cudaFree(p);
   for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
   delete ctx;
@@ -1048,6 +1083,317 @@ static int sumsq(fr_ctx* ctx, const double* a, size_t na, const double* b, size_
   return FR_OK;
 }
 
+// ------------------------------------------------------------------ whole-stage CUDA graph
+// The implicit stage as one executable graph: the Newton loop is a WHILE node, its linear solve
+// an IF node (skipped on the iteration that finds the residual converged) and the GMRES restart
+// cycles a nested WHILE node.  Small kernels decide on the device what the host decides in the
+// stream path (same tests, same order), so one graph launch runs the whole stage and the host
+// reads the counters once at the end.
+__global__ void k_stage_init(StageDev* sd) {
+  sd->norm0 = -1.0;
+  sd->norm = 0.0;
+  sd->it = 0;
+  sd->gtot = 0;
+  sd->conv = 0;
+  sd->err = 0;
+  sd->gm_total = 0;
+  sd->cycles = 0;
+}
+
+__global__ void k_newton_check(StageDev* sd, const double* ss, double tol, int maxit, cudaGraphConditionalHandle hn,
+                               cudaGraphConditionalHandle hs) {
+  const double nrm = sqrt(*ss);
+  if (sd->norm0 < 0.0) sd->norm0 = nrm;
+  sd->norm = nrm;
+  if (!(nrm == nrm)) sd->err |= 1;
+  const int conv = (nrm <= tol * sd->norm0 || nrm == 0.0) ? 1 : 0;
+  sd->conv = conv;
+  const int cont = (!conv && sd->err == 0 && sd->it < maxit) ? 1 : 0;
+  if (cont) sd->it += 1;
+  cudaGraphSetConditional(hn, (unsigned)cont);
+  cudaGraphSetConditional(hs, (unsigned)cont);
+}
+
+__global__ void k_gmres_begin(StageDev* sd, int m, int maxit, cudaGraphConditionalHandle hg) {
+  sd->gm_total = 0;
+  sd->dyn[0] = 1;
+  sd->dyn[1] = m < maxit ? m : maxit;
+  cudaGraphSetConditional(hg, 1u);
+}
+
+__global__ void k_gmres_after(StageDev* sd, const GmresState* st, const unsigned* bar, int m, int maxit,
+                              cudaGraphConditionalHandle hg) {
+  int cont = 0;
+  if (bar[1] != 0u) {
+    sd->err |= 4;
+  } else {
+    sd->gm_total += st->k;
+    sd->cycles += 1;
+    if (st->nan) sd->err |= 2;
+    cont = (st->nan || st->converged || sd->gm_total >= maxit || st->k == 0) ? 0 : 1;
+    const int rem = maxit - sd->gm_total;
+    sd->dyn[0] = 0;
+    sd->dyn[1] = m < rem ? m : rem;
+  }
+  cudaGraphSetConditional(hg, (unsigned)cont);
+}
+
+__global__ void k_gmres_end(StageDev* sd) { sd->gtot += sd->gm_total; }
+
+// a conditional node after the work captured so far on s; returns its body graph
+static cudaError_t add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                                   cudaGraph_t* body) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  // zeroed storage (the struct's union has no default constructor)
+  alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+  memset(raw, 0, sizeof(raw));
+  cudaGraphNodeParams& p = *reinterpret_cast<cudaGraphNodeParams*>(raw);
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = type;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  if ((e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &p)) != cudaSuccess) return e;
+  *body = p.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+static int stage_graph_capture(fr_ctx* ctx, const StageGraphKey& key) {
+  const Tab tb = tableau(ctx->tableau);
+  const int i = key.stage, E = ctx->E, nA = ctx->nA;
+  const size_t tot = (size_t)E * nA;
+  const size_t nh = (size_t)ctx->ntrace * ctx->n * ctx->nv;
+  for (auto& c : ctx->cap)
+    if (!c) CK(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
+  cudaStream_t user = ctx->stream;
+  const bool prof = ctx->prof;
+  ctx->prof = false;
+  cudaGraph_t g = nullptr, bn = nullptr, bs = nullptr, bg = nullptr;
+  int depth = 0;  // capture streams currently capturing
+  int rc = FR_OK;
+  unsigned long long l0 = 0, l1 = 0, l2 = 0, l3 = 0, l4 = 0, l5 = 0, l6 = 0;
+  auto fail = [&](int code) {
+    for (int d = depth - 1; d >= 0; --d) {
+      cudaGraph_t tmp = nullptr;
+      cudaStreamEndCapture(ctx->cap[d], &tmp);
+    }
+    ctx->stream = user;
+    ctx->prof = prof;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return code ? code : FR_ERR_CUDA;
+  };
+#define GK(x)                                                         \
+  do {                                                                \
+    cudaError_t e_ = (x);                                             \
+    if (e_ != cudaSuccess) {                                          \
+      set_err(ctx, FR_ERR_CUDA, cudaGetErrorString(e_));              \
+      return fail(FR_ERR_CUDA);                                       \
+    }                                                                 \
+  } while (0)
+#define GR(x)                     \
+  do {                            \
+    const int r_ = (x);           \
+    if (r_ != FR_OK) return fail(r_); \
+  } while (0)
+  GK(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle hn;
+  GK(cudaGraphConditionalHandleCreate(&hn, g, 1u, cudaGraphCondAssignDefault));
+  // ---- top level: stage combination, u*, counters
+  GK(cudaStreamBeginCaptureToGraph(ctx->cap[0], g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  depth = 1;
+  ctx->stream = ctx->cap[0];
+  l0 = fr_kernel_launches();
+  {
+    StageCoef sc;
+    memset(&sc, 0, sizeof(sc));
+    sc.nterm = i;
+    for (int j = 0; j < i; ++j) {
+      sc.hi[j] = j;
+      sc.ce[j] = key.dt * tb.ah[i][j];
+      sc.ci[j] = j >= 1 ? key.dt * tb.a[i - 1][j - 1] : 0.0;
+    }
+    (hfr::count_launch(), k_stage_combine<<<nblk(tot), 256, 0, ctx->stream>>>(E, nA, ctx->implicit, key.u_n, key.R_hist,
+                                                                                sc, const_cast<double*>(key.u_stage)));
+    GK(cudaGetLastError());
+  }
+  GK(cudaMemcpyAsync(ctx->Ustar, key.u_stage, tot * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  (hfr::count_launch(), k_stage_init<<<1, 1, 0, ctx->stream>>>(ctx->sdev));
+  GK(cudaGetLastError());
+  const double adt = key.dt * tb.a[i - 1][i - 1];
+  double* u_stage = const_cast<double*>(key.u_stage);
+  double* uhat = const_cast<double*>(key.uhat);
+  GK(add_conditional(ctx->cap[0], hn, cudaGraphCondTypeWhile, &bn));
+  l1 = fr_kernel_launches();
+  // ---- Newton body: residual, right-hand sides, norm test
+  cudaGraphConditionalHandle hs;
+  GK(cudaGraphConditionalHandleCreate(&hs, bn, 0u, 0u));
+  GK(cudaStreamBeginCaptureToGraph(ctx->cap[1], bn, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  depth = 2;
+  ctx->stream = ctx->cap[1];
+  GR(residual_into(ctx, u_stage, uhat, ctx->Rw, ctx->gview, ctx->gw));
+  GR(form_rhs(ctx, u_stage, ctx->Ustar, adt));
+  {
+    const int nbk = 256;
+    (hfr::count_launch(), k_sumsq_part<<<nbk, 256, 0, ctx->stream>>>(ctx->r, (size_t)ctx->Eim * nA, ctx->gw, nh, ctx->red));
+    (hfr::count_launch(), k_sumsq_final<<<1, 32, 0, ctx->stream>>>(ctx->red, nbk, ctx->red + 1024));
+    (hfr::count_launch(), k_newton_check<<<1, 1, 0, ctx->stream>>>(ctx->sdev, ctx->red + 1024, key.ntol, key.nmax, hn, hs));
+    GK(cudaGetLastError());
+  }
+  GK(add_conditional(ctx->cap[1], hs, cudaGraphCondTypeIf, &bs));
+  l2 = fr_kernel_launches();
+  // ---- solve body: blocks, condensation, GMRES cycles, back-substitution, update
+  GK(cudaStreamBeginCaptureToGraph(ctx->cap[2], bs, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  depth = 3;
+  ctx->stream = ctx->cap[2];
+  GR(jacobian_blocks(ctx, u_stage, uhat, adt));
+  GR(condense_impl(ctx, 0));
+  if (ctx->ntrace > 0) {
+    FusedArgs fa;
+    fa.ntrace = ctx->ntrace;
+    fa.nT = ctx->nT;
+    fa.sides = ctx->sides_c;
+    fa.tr_of_c = ctx->tr_of_c;
+    fa.S = ctx->S;
+    fa.S_bytes = (size_t)ctx->Eim * ctx->nT * ctx->nT * ctx->prec_bytes;
+    fa.Pinv = ctx->Pinv;
+    fa.t = ctx->tg;
+    fa.x = ctx->duhat;
+    fa.V = ctx->gm.V;
+    fa.z = ctx->prec_bytes == 4 ? (void*)ctx->gm.z32 : (void*)ctx->gm.Z;
+    fa.partial = ctx->gm.partial;
+    fa.bar = ctx->gm_bar;
+    fa.st = ctx->gm.state;
+    fa.n = ctx->gm.n;
+    fa.m = ctx->restart > GM_MAXM ? GM_MAXM : ctx->restart;
+    fa.rtol = key.grtol;
+    fa.x_zero = 1;
+    fa.true_res = 0;
+    fa.dyn = ctx->sdev->dyn;
+    cudaGraphConditionalHandle hg;
+    GK(cudaGraphConditionalHandleCreate(&hg, bs, 0u, 0u));
+    GK(cudaMemsetAsync(ctx->duhat, 0, nh * sizeof(double), ctx->stream));
+    (hfr::count_launch(), k_gmres_begin<<<1, 1, 0, ctx->stream>>>(ctx->sdev, fa.m, key.gmax, hg));
+    GK(cudaGetLastError());
+    GK(add_conditional(ctx->cap[2], hg, cudaGraphCondTypeWhile, &bg));
+    l3 = fr_kernel_launches();
+    // ---- GMRES body: one restart cycle and the device-side restart decision
+    GK(cudaStreamBeginCaptureToGraph(ctx->cap[3], bg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    depth = 4;
+    ctx->stream = ctx->cap[3];
+    GK(cudaMemsetAsync(ctx->gm_bar, 0, 2 * sizeof(unsigned), ctx->stream));
+    GK(launch_gmres_cycle(fa, ctx->prec_bytes, ctx->gm_fused_grid, ctx->stream));
+    (hfr::count_launch(), k_gmres_after<<<1, 1, 0, ctx->stream>>>(ctx->sdev, ctx->gm.state, ctx->gm_bar, fa.m, key.gmax, hg));
+    GK(cudaGetLastError());
+    GK(cudaStreamEndCapture(ctx->cap[3], &bg));
+    depth = 3;
+    l4 = fr_kernel_launches();
+    ctx->stream = ctx->cap[2];
+    (hfr::count_launch(), k_gmres_end<<<1, 1, 0, ctx->stream>>>(ctx->sdev));
+    GK(cudaGetLastError());
+  } else {
+    l3 = l4 = fr_kernel_launches();
+  }
+  GR(backsolve_impl(ctx, ctx->duhat, ctx->du, key.refine));
+  (hfr::count_launch(), k_apply_du<<<nblk((size_t)ctx->Eim * nA), 256, 0, ctx->stream>>>(ctx->Eim, nA, ctx->imp_idx, ctx->du, u_stage));
+  GK(cudaGetLastError());
+  if (nh) {
+    (hfr::count_launch(), k_axpy<<<nblk(nh), 256, 0, ctx->stream>>>(nh, 1.0, ctx->duhat, uhat));
+    GK(cudaGetLastError());
+  }
+  GK(cudaStreamEndCapture(ctx->cap[2], &bs));
+  depth = 2;
+  l5 = fr_kernel_launches();
+  GK(cudaStreamEndCapture(ctx->cap[1], &bn));
+  depth = 1;
+  // ---- after the loop: R_hist[i] = R(u_i, u^_i), the last residual the loop evaluated
+  ctx->stream = ctx->cap[0];
+  GK(cudaMemcpyAsync(const_cast<double*>(key.R_hist) + (size_t)i * tot, ctx->Rw, tot * sizeof(double),
+                     cudaMemcpyDeviceToDevice, ctx->stream));
+  GK(cudaStreamEndCapture(ctx->cap[0], &g));
+  depth = 0;
+  l6 = fr_kernel_launches();
+  ctx->stream = user;
+  ctx->prof = prof;
+  cudaGraphExec_t ex = nullptr;
+  {
+    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      cudaGetLastError();
+      return set_err(ctx, FR_ERR_CUDA, cudaGetErrorString(e));
+    }
+  }
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  ctx->graph = g;
+  ctx->gexec = ex;
+  ctx->gkey = key;
+  ctx->gvalid = true;
+  // capture counted each kernel once: the launches of one replay follow from the iteration counts
+  g_launches.fetch_sub(l6 - l0, std::memory_order_relaxed);
+  ctx->gl_top = (int)((l1 - l0) + (l6 - l5));
+  ctx->gl_newton = (int)(l2 - l1);
+  ctx->gl_cycle = (int)(l4 - l3);
+  ctx->gl_solve = (int)((l5 - l2) - (l4 - l3));
+#undef GK
+#undef GR
+  return rc;
+}
+
+static int imex_stage_graph(fr_ctx* ctx, const StageGraphKey& key, fr_stage_stats* stats) {
+  if (!ctx->gvalid || !(ctx->gkey == key)) {
+    const int rc = stage_graph_capture(ctx, key);
+    if (rc) return rc;
+  }
+  cudaStream_t st = ctx->stream;
+  CK(cudaGraphLaunch(ctx->gexec, st));
+  StageDev h;
+  int hs[2] = {0, 0};
+  CK(cudaMemcpyAsync(&h, ctx->sdev, sizeof(h), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hs, ctx->status, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const unsigned long long n = (unsigned long long)ctx->gl_top + (unsigned long long)(h.it + 1) * ctx->gl_newton +
+                               (unsigned long long)h.it * ctx->gl_solve + (unsigned long long)h.cycles * ctx->gl_cycle;
+  g_launches.fetch_add(n, std::memory_order_relaxed);
+  if (stats) {
+    stats->newton_iterations = h.it;
+    stats->gmres_iterations = h.gtot;
+    stats->residual0 = h.norm0;
+    stats->residual = h.norm;
+    stats->converged = h.conv;
+  }
+  if (hs[0] & DEV_ERR_SINGULAR) {
+    CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), st));
+    return set_err(ctx, FR_ERR_SINGULAR, "imex_stage: zero pivot in condensation", hs[1]);
+  }
+  if ((hs[0] & DEV_ERR_TIMEOUT) || (h.err & 4)) {
+    CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), st));
+    return set_err(ctx, FR_ERR_TIMEOUT, "imex_stage: a bounded device wait timed out", -1, h.it);
+  }
+  if (h.err & 1) return set_err(ctx, FR_ERR_DIVERGED, "imex_stage: non-finite Newton residual", -1, h.it);
+  if (h.err & 2) return set_err(ctx, FR_ERR_DIVERGED, "imex_stage: non-finite GMRES residual", -1, h.it);
+  if (!h.conv) return set_err(ctx, FR_ERR_NOT_CONVERGED, "imex_stage: Newton iteration limit", -1, h.it, h.norm);
+  return FR_OK;
+}
+
+extern "C" int imex_stage_set_graph(fr_ctx* ctx, int on) {
+  if (!ctx || (on != 0 && on != 1)) return set_err(ctx, FR_ERR_INVALID_ARG, "imex_stage_set_graph: bad argument");
+  if (on && (ctx->Eim == 0 || (ctx->ntrace > 0 && ctx->gm_mode != 1)))
+    return set_err(ctx, FR_ERR_UNSUPPORTED, "imex_stage_set_graph: needs implicit elements and the single-launch GMRES cycle");
+  ctx->use_graph = on;
+  ctx->gvalid = false;
+  return FR_OK;
+}
+
+extern "C" int imex_stage_get_graph(const fr_ctx* ctx) { return ctx ? ctx->use_graph : -1; }
+
 extern "C" int imex_stage(fr_ctx* ctx, int stage, double dt, const double* u_n, double* u_stage, double* uhat,
                           double* R_hist, double newton_tol, int newton_maxit, double gmres_rtol, int gmres_maxit,
                           int refine, fr_stage_stats* stats) {
@@ -1078,6 +1424,12 @@ extern "C" int imex_stage(fr_ctx* ctx, int stage, double dt, const double* u_n, 
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
     return FR_OK;
+  }
+  if (ctx->use_graph) {
+    if (ctx->jac_policy != FR_JAC_EVERY_NEWTON || (ctx->ntrace > 0 && ctx->gm_mode != 1))
+      return set_err(ctx, FR_ERR_UNSUPPORTED, "imex_stage: the graph runs the exact-Newton, single-launch GMRES stage");
+    StageGraphKey key{stage, newton_maxit, gmres_maxit, refine, dt, newton_tol, gmres_rtol, u_n, u_stage, uhat, R_hist};
+    return imex_stage_graph(ctx, key, stats);
   }
   const int i = stage;
   // explicit elements: u_i = u_n + dt sum_{j<=i} ahat_{i+1,j} R_hist[j-1];

@@ -580,8 +580,10 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_gmres_cycle(const __grid_cons
   T* V = reinterpret_cast<T*>(a.V);
   T* const partial = reinterpret_cast<T*>(a.partial);
 
+  const int xz = a.dyn ? a.dyn[0] : a.x_zero;
+  const int mm = a.dyn ? a.dyn[1] : a.m;
   // r0 = t - L x into V_0 (x = 0: r0 = t); beta = ||r0||, bnorm = ||t||
-  if (a.x_zero) {
+  if (xz) {
     for (size_t x = x0 + tid; x < x1; x += PG_THREADS) V[x] = T(__ldcg(a.t + x));
   } else {
     pg_matvec<T, NT, BS, true, true>(a, a.x, V, fb0, fb1);
@@ -620,7 +622,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_gmres_cycle(const __grid_cons
       T* w = V + (size_t)(j + 1) * n;
       // (A) lane 0 of warp 0: Givens rotation of column j-1.  Warps 1..: finish v_j (deferred
       // second Gram-Schmidt pass, normalisation) and form z = P^{-1} v_j.
-      if (j > 0 && tid == 0) pg_givens(sh, j - 1, a.rtol, a.m);
+      if (j > 0 && tid == 0) pg_givens(sh, j - 1, a.rtol, mm);
       if (tid >= 32) {
         pg_finish(V, n, sh.cf, sh.corr ? j : 0, sh.invT, vj, x0, x1);
         pg_sync_workers();
@@ -821,6 +823,14 @@ int run_gmres_fused(const FusedArgs& base, int prec_bytes, int grid, double rtol
     res->converged = hs.converged;
     if (hs.nan || hs.converged || total >= maxit || hs.k == 0) return 0;
   }
+}
+
+cudaError_t launch_gmres_cycle(const FusedArgs& a, int prec_bytes, int grid, cudaStream_t s) {
+  int occ = 0;
+  const int bs = (int)(a.n / (size_t)(a.ntrace > 0 ? a.ntrace : 1));
+  CycleFn fn = pick(prec_bytes, a.nT, bs, &occ);
+  if (!fn || grid < 1) return cudaErrorInvalidValue;
+  return fn(a, grid, s);
 }
 
 // Host side of the barrier self-test (declared in hfr_krylov.h).

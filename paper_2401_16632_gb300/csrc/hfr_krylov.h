@@ -77,6 +77,9 @@ struct FusedArgs {
   double rtol;
   int x_zero;
   int true_res;  // 1: compute ||t - L x|| after the cycle (else the estimate is reported)
+  // nullable: device words {x_zero, m} read by the cycle instead of the two fields above (a cycle
+  // captured once in a graph whose restarts a device kernel decides)
+  const int* dyn = nullptr;
 };
 size_t fused_partial_doubles(int max_blocks);
 // CTAs of the cooperative launch (one per SM), 0 when the shape or the device does not allow it
@@ -86,6 +89,9 @@ int fused_gmres_grid(int prec_bytes, int nT, int bs);
 int run_gmres_fused(const FusedArgs& a, int prec_bytes, int grid, double rtol, int restart, int maxit,
                     GmresResult* res, int* timed_out, cudaStream_t s, const int* dev_status = nullptr,
                     int* host_status = nullptr);
+// one restart cycle (enqueue only; a.bar must be zeroed before it): cudaErrorInvalidValue when
+// the shape has no single-launch cycle
+cudaError_t launch_gmres_cycle(const FusedArgs& a, int prec_bytes, int grid, cudaStream_t s);
 // Self-test of the bounded grid barrier used by the single-launch cycle (cooperative launch of
 // nblocks CTAs, `rounds` barriers; CTA `absent` never arrives when 0 <= absent < nblocks).
 // Returns 0 (timed_out set when the abort flag was raised), -1 on a CUDA error, -2 on arguments

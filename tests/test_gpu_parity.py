@@ -347,3 +347,45 @@ def test_tensor_core_and_fma_condensation_agree(name):
         assert _rel(out[pkg.FR_CONDENSE_TENSOR][key], fma[key]) < 5e-5, key
         for mode in modes:
             assert _rel(out[mode][key], ref) < 1e-4, (mode, key)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", ["vortex_skew_p3", "vortex_p4", "band_ns"])
+def test_graph_stage_equals_stream_stage(name, precision):
+    """The stage as one CUDA graph (conditional WHILE / IF nodes, device-side tests) runs the same
+    kernels in the same order as the stream path: same solution, same iteration counts; a
+    replay of the cached graph (same buffers) gives the same result again."""
+    prec = pkg.FR_PREC_FP64 if precision == "fp64" else pkg.FR_PREC_FP32
+    mesh, u0, phys = CASES[name]()
+    dt = 0.2 if name != "band_ns" else 0.02
+
+    def run(ctx, bufs):
+        u, us, uh, uh0, R_hist = bufs
+        uh.copy_(uh0)
+        ctx.imex_stage(0, dt, u, us, uh, R_hist)
+        l0 = ctx.kernel_launches()
+        st = ctx.imex_stage(1, dt, u, us, uh, R_hist, newton_tol=1e-10, gmres_rtol=1e-6, gmres_maxit=3000)
+        assert st["converged"]
+        return (us.cpu().numpy(), uh.cpu().numpy(), R_hist[1].cpu().numpy(), st["newton_iterations"],
+                st["gmres_iterations"], ctx.kernel_launches() - l0)
+
+    def buffers(ctx):
+        u = torch.tensor(u0, device=DEV)
+        uh0 = ctx.hfr_initial_trace(u)
+        return u, ctx.empty(*ctx.state_shape), uh0.clone(), uh0, ctx.empty(3, *ctx.state_shape)
+
+    ctx_s = pkg.Context(mesh, phys, precision=prec, tableau=pkg.FR_TAB_SDIRK2)
+    ref = run(ctx_s, buffers(ctx_s))
+    ctx_g = pkg.Context(mesh, phys, precision=prec, tableau=pkg.FR_TAB_SDIRK2)
+    ctx_g.imex_stage_set_graph(True)
+    assert ctx_g.imex_stage_get_graph() == 1
+    bufs = buffers(ctx_g)
+    inc = np.abs(ref[0] - u0).max()
+    for _ in range(2):  # capture, then replay
+        got = run(ctx_g, bufs)
+        assert np.abs(got[0] - ref[0]).max() <= 1e-12 * inc
+        assert _rel(got[1], ref[1]) < 1e-12
+        assert _rel(got[2], ref[2]) < 1e-12
+        assert got[3] == ref[3] and got[4] == ref[4]
+        # kernel executions of a graph stage: the stream path's plus the device-side decisions
+        assert got[5] > ref[5]
