@@ -151,6 +151,9 @@ def time_path(pkg, torch, w, precision, refine, steps, warmup, dev, l2buf, jac="
     u_n = torch.tensor(w.u0, device=dev)
     uhat0 = ctx.hfr_initial_trace(u_n)
     uhat = uhat0.clone()
+    tune = None
+    if precision == pkg.FR_PREC_FP32:  # pick the condensation form and GMRES cycle on this workload
+        tune = ctx.hfr_autotune(u_n, uhat0, u_n, w.dt * (1.0 - 0.5 ** 0.5))
     R_hist = ctx.empty(3, *ctx.state_shape)
     u_stage = ctx.empty(*ctx.state_shape)
     stats = None
@@ -179,7 +182,7 @@ def time_path(pkg, torch, w, precision, refine, steps, warmup, dev, l2buf, jac="
     prof = ctx.fr_profile_read()
     ctx.fr_profile_enable(False)
     result = {"ms": times, "stats": stats, "profile": prof, "launches": launches, "ctx": ctx,
-              "u": u_stage.clone(), "uhat0": uhat0}
+              "u": u_stage.clone(), "uhat0": uhat0, "tune": tune}
     return result
 
 
@@ -437,6 +440,7 @@ def main():
                    "newton_tol": NEWTON_TOL, "gmres_rtol": GMRES_RTOL, "refine_sweeps": args.refine,
                    "jacobian": args.jacobian,
                    "stage_execution": "one CUDA graph per stage" if graph else "stream, kernel by kernel",
+                   "autotune": ({k: v for k, v in mixed["tune"].items()} if mixed.get("tune") else None),
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "fp64": {"value": job_value(world, dofs, ms_fp64), "ms_per_step": ms_fp64, "dtype": "f64",
                  "newton_iterations": fp64["stats"]["newton_iterations"],

@@ -212,6 +212,24 @@ int imex_stage(fr_ctx* ctx, int stage, double dt, const double* u_n, double* u_s
                double* R_hist, double newton_tol, int newton_maxit, double gmres_rtol, int gmres_maxit,
                int refine, fr_stage_stats* stats /* host, nullable */);
 
+/* Autotuner (no counterpart in the paper): forms the element blocks at (u, uhat, ustar, a_dt) as
+ * hfr_local_jacobian does, then times on them, with CUDA events on the context stream (best of
+ * two after a warm-up), every condensation form available for the context's precision and block
+ * shape -- FMA, tensor-core products, tensor-core factorisation and products with 1 to 4 resident
+ * CTAs per SM for the factorisation -- and both GMRES cycle forms on the condensed system
+ * (rtol 1e-4, at most 500 iterations), and keeps the fastest of each in the context.  out (host,
+ * nullable): the times (ms, -1 where not available) and the choices. */
+typedef struct {
+  int condense_mode;        /* fr_condense_mode chosen */
+  int inverse_ctas_per_sm;  /* 0 = default residency */
+  int gmres_mode;           /* fr_gmres_mode chosen */
+  double condense_ms[3];    /* per fr_condense_mode (best residency for the tensor-core form) */
+  double inverse_ms[4];     /* tensor-core form, 1..4 CTAs per SM */
+  double gmres_ms[2];       /* per fr_gmres_mode */
+} fr_tune_report;
+int hfr_autotune(fr_ctx* ctx, const double* u, const double* uhat, const double* ustar, double a_dt,
+                 fr_tune_report* out);
+
 /* Run each implicit stage of imex_stage as one CUDA graph (on = 1; no counterpart in the paper).
  * The graph holds the whole stage: the Newton loop as a conditional WHILE node, its linear solve
  * (blocks, condensation, GMRES restart cycles as a nested WHILE node, back-substitution, update)

@@ -51,6 +51,7 @@ ABI_SYMBOLS = [
     "hfr_gmres_get_mode",
     "hfr_condense_set_mode",
     "hfr_condense_get_mode",
+    "hfr_autotune",
     "imex_stage_set_graph",
     "imex_stage_get_graph",
     "fr_barrier_selftest",
@@ -128,6 +129,17 @@ class fr_profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 10), ("count", ctypes.c_longlong * 10)]
 
 
+class fr_tune_report(ctypes.Structure):
+    _fields_ = [
+        ("condense_mode", ctypes.c_int),
+        ("inverse_ctas_per_sm", ctypes.c_int),
+        ("gmres_mode", ctypes.c_int),
+        ("condense_ms", ctypes.c_double * 3),
+        ("inverse_ms", ctypes.c_double * 4),
+        ("gmres_ms", ctypes.c_double * 2),
+    ]
+
+
 class fr_error_info(ctypes.Structure):
     _fields_ = [
         ("code", ctypes.c_int),
@@ -164,6 +176,7 @@ def load_library(path: str = LIB_PATH):
     lib.hfr_gmres_get_mode.argtypes = [vp]
     lib.hfr_condense_set_mode.argtypes = [vp, ctypes.c_int]
     lib.hfr_condense_get_mode.argtypes = [vp]
+    lib.hfr_autotune.argtypes = [vp, dp, dp, dp, ctypes.c_double, ctypes.POINTER(fr_tune_report)]
     lib.imex_stage_set_graph.argtypes = [vp, ctypes.c_int]
     lib.imex_stage_get_graph.argtypes = [vp]
     lib.fr_barrier_selftest.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ip, vp]
@@ -346,6 +359,13 @@ class Context:
 
     def hfr_gmres_get_mode(self) -> int:
         return int(self.lib.hfr_gmres_get_mode(self.h))
+
+    def hfr_autotune(self, u, uhat, ustar, a_dt):
+        rep = fr_tune_report()
+        self._check(self.lib.hfr_autotune(self.h, _ptr(u), _ptr(uhat), _ptr(ustar), float(a_dt), ctypes.byref(rep)))
+        return {"condense_mode": rep.condense_mode, "inverse_ctas_per_sm": rep.inverse_ctas_per_sm,
+                "gmres_mode": rep.gmres_mode, "condense_ms": list(rep.condense_ms),
+                "inverse_ms": list(rep.inverse_ms), "gmres_ms": list(rep.gmres_ms)}
 
     def imex_stage_set_graph(self, on: bool = True):
         self._check(self.lib.imex_stage_set_graph(self.h, 1 if on else 0))

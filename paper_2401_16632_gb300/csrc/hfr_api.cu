@@ -74,6 +74,7 @@ struct fr_ctx {
   int gm_mode = 0;          // 0: multi-kernel cycle, 1: one cooperative launch per cycle
   int jac_policy = 0;       // FR_JAC_EVERY_NEWTON or FR_JAC_ONCE_PER_STAGE
   int cond_mode = 0;        // fr_condense_mode of the FP32 condensation
+  int inv_ctas = 0;         // CTAs per SM of the tensor-core inverse (0: default)
   // whole-stage CUDA graph
   int use_graph = 0;
   StageDev* sdev = nullptr;
@@ -818,6 +819,7 @@ static int condense_impl(fr_ctx* ctx, int refine) {
   c.t = ctx->te;
   c.status = ctx->status;
   c.tc_mode = ctx->cond_mode;
+  c.inv_ctas = ctx->inv_ctas;
   int ph = prof_begin(ctx, PH_COND);
   CK(launch_condense_part(ctx->prec_bytes, c, ctx->stream, 0));
   prof_end(ctx, ph);
@@ -977,6 +979,107 @@ extern "C" int hfr_condense_set_mode(fr_ctx* ctx, int mode) {
 }
 
 extern "C" int hfr_condense_get_mode(const fr_ctx* ctx) { return ctx ? ctx->cond_mode : -1; }
+
+// Autotuner: time the compiled alternatives on the context's own blocks and keep the fastest.
+extern "C" int hfr_autotune(fr_ctx* ctx, const double* u, const double* uhat, const double* ustar, double a_dt,
+                            fr_tune_report* out) {
+  if (!ctx || !u || (ctx->ntrace > 0 && !uhat) || !ustar) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_autotune: null argument");
+  fr_tune_report rep;
+  memset(&rep, 0, sizeof(rep));
+  for (int i = 0; i < 3; ++i) rep.condense_ms[i] = -1.0;
+  for (int i = 0; i < 4; ++i) rep.inverse_ms[i] = -1.0;
+  for (int i = 0; i < 2; ++i) rep.gmres_ms[i] = -1.0;
+  if (ctx->Eim == 0) {
+    if (out) *out = rep;
+    return FR_OK;
+  }
+  int rc = hfr_local_jacobian(ctx, u, uhat, ustar, a_dt);
+  if (rc) return rc;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const bool prof = ctx->prof;
+  ctx->prof = false;
+  auto time_it = [&](auto&& fn, double* ms_out) -> int {
+    int r = fn();  // warm-up (first-use attributes, caches)
+    if (r) return r;
+    float best = 1e30f;
+    for (int rep_i = 0; rep_i < 2; ++rep_i) {
+      CK(cudaEventRecord(e0, ctx->stream));
+      r = fn();
+      if (r) return r;
+      CK(cudaEventRecord(e1, ctx->stream));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      best = ms < best ? ms : best;
+    }
+    *ms_out = best;
+    return FR_OK;
+  };
+  auto condense = [&]() -> int {
+    const int r = condense_impl(ctx, 0);
+    if (r) return r;
+    return check_status(ctx, "hfr_autotune: zero pivot");
+  };
+  // condensation: every available mode; for the tensor-core inverse every residency 1..4 CTAs per SM
+  const int avail = condense_tc_available(ctx->prec_bytes, ctx->nA, ctx->nT);
+  int best_mode = ctx->cond_mode, best_ctas = ctx->inv_ctas;
+  double best_ms = 1e30;
+  for (int mode = 0; mode <= avail && !rc; ++mode) {
+    ctx->cond_mode = mode;
+    const int nv = mode == 2 ? 4 : 1;
+    for (int v = 0; v < nv && !rc; ++v) {
+      ctx->inv_ctas = mode == 2 ? v + 1 : 0;
+      double ms = 0.0;
+      rc = time_it(condense, &ms);
+      if (rc) break;
+      if (mode == 2) rep.inverse_ms[v] = ms;
+      if (rep.condense_ms[mode] < 0.0 || ms < rep.condense_ms[mode]) rep.condense_ms[mode] = ms;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_mode = mode;
+        best_ctas = ctx->inv_ctas;
+      }
+    }
+  }
+  ctx->cond_mode = best_mode;
+  ctx->inv_ctas = best_ctas;
+  // GMRES cycle form (same iteration either way): on the condensed system of the chosen mode
+  int best_gm = ctx->gm_mode;
+  if (!rc && ctx->ntrace > 0) rc = condense();
+  if (!rc && ctx->ntrace > 0) {
+    double bg = 1e30;
+    for (int mode = 1; mode >= 0 && !rc; --mode) {
+      if (mode == 1 && ctx->gm_fused_grid <= 0) continue;
+      ctx->gm_mode = mode;
+      double ms = 0.0;
+      rc = time_it([&]() -> int {
+        int its = 0;
+        double rel = 0.0;
+        const int r = gmres_impl(ctx, ctx->duhat, 1e-4, 500, &its, &rel, false, nullptr);
+        return r == FR_ERR_NOT_CONVERGED ? FR_OK : r;
+      }, &ms);
+      if (rc) break;
+      rep.gmres_ms[mode] = ms;
+      if (ms < bg) {
+        bg = ms;
+        best_gm = mode;
+      }
+    }
+  }
+  ctx->gm_mode = best_gm;
+  ctx->gvalid = false;
+  ctx->prof = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  rep.condense_mode = ctx->cond_mode;
+  rep.inverse_ctas_per_sm = ctx->inv_ctas;
+  rep.gmres_mode = ctx->gm_mode;
+  if (out) *out = rep;
+  return FR_OK;
+}
 
 extern "C" int fr_barrier_selftest(int nblocks, int absent_block, int rounds, double timeout_s,
                                    int* barriers_passed, void* stream) {

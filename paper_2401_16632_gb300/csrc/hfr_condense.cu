@@ -972,14 +972,14 @@ __global__ void __launch_bounds__(128, 4) k_inverse_tc(const __grid_constant__ C
 template <int NA>
 static cudaError_t launch_inverse_tc(const CondArgs& a, cudaStream_t st) {
   using Sh = InvTcShape<NA>;
-  static int grid = 0;
+  static int grid = 0, nsm = 0;
   if (grid == 0) {
     cudaError_t e = cudaFuncSetAttribute(k_inverse_tc<NA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_inverse_tc<NA>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     // resident CTAs per SM from the shared-memory arithmetic (at most four: tensor memory)
-    int dev = 0, nsm = 0, smem_sm = 0, resv = 0;
+    int dev = 0, smem_sm = 0, resv = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess) return e;
@@ -987,7 +987,9 @@ static cudaError_t launch_inverse_tc(const CondArgs& a, cudaStream_t st) {
     int fit = smem_sm / (int)(Sh::SMEM + (uint32_t)resv);
     grid = nsm * (fit < 1 ? 1 : (fit > 4 ? 4 : fit));
   }
-  const int g = a.Eim < grid ? a.Eim : grid;
+  int gr = grid;
+  if (a.inv_ctas > 0 && a.inv_ctas * nsm < grid) gr = a.inv_ctas * nsm;
+  const int g = a.Eim < gr ? a.Eim : gr;
   (hfr::count_launch(), k_inverse_tc<NA><<<g, Sh::THREADS, Sh::SMEM, st>>>(a));
   return cudaGetLastError();
 }

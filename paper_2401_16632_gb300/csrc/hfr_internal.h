@@ -87,6 +87,7 @@ struct CondArgs {
   // FP32 blocks: 0 = factorisation and products on the FP32 FMA pipes, 1 = products on the tensor
   // cores (3xTF32), 2 = factorisation and products on the tensor cores
   int tc_mode = 0;
+  int inv_ctas = 0;  // resident CTAs per SM of the tensor-core inverse (0: as many as fit, at most 4)
 };
 cudaError_t launch_condense(int prec_bytes, const CondArgs& a, cudaStream_t st);
 // the same in two parts: 0 = factorisation (the whole condensation where it is one kernel),

@@ -389,3 +389,25 @@ def test_graph_stage_equals_stream_stage(name, precision):
         assert got[3] == ref[3] and got[4] == ref[4]
         # kernel executions of a graph stage: the stream path's plus the device-side decisions
         assert got[5] > ref[5]
+
+
+@pytest.mark.parametrize("name", ["vortex_p4", "band_ns"])
+def test_autotune_picks_a_valid_configuration(name):
+    """hfr_autotune times the condensation forms (and the tensor-core inverse's residency) and
+    both GMRES cycle forms, keeps the fastest, and the tuned context still solves the stage."""
+    mesh, u0, phys = CASES[name]()
+    ctx = pkg.Context(mesh, phys, precision=pkg.FR_PREC_FP32, tableau=pkg.FR_TAB_SDIRK2)
+    u = torch.tensor(u0, device=DEV)
+    uh = ctx.hfr_initial_trace(u)
+    rep = ctx.hfr_autotune(u, uh, u * 0.999, 0.05)
+    assert rep["condense_mode"] == ctx.hfr_condense_get_mode()
+    assert rep["gmres_mode"] == ctx.hfr_gmres_get_mode()
+    assert all(rep["condense_ms"][m] > 0 for m in range(3))
+    assert all(t > 0 for t in rep["inverse_ms"])
+    assert rep["condense_ms"][rep["condense_mode"]] == min(rep["condense_ms"])
+    assert 1 <= rep["inverse_ctas_per_sm"] or rep["condense_mode"] != pkg.FR_CONDENSE_TENSOR
+    d = Discretisation(mesh, make_physics(phys))
+    dt = 0.2 if name != "band_ns" else 0.02
+    U_o, uh_o, _ = imex_step(d, u0, d.initial_trace(u0), dt, "sdirk2", tol=1e-12)
+    u1, _ = ctx.imex_step(dt, u, ctx.hfr_initial_trace(u), newton_tol=1e-12, gmres_rtol=1e-8, gmres_maxit=3000)
+    assert np.abs(u1.cpu().numpy() - U_o).max() < 1e-8 * np.abs(U_o - u0).max()
