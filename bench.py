@@ -141,7 +141,8 @@ def run_stage(ctx, dt, u_n, u_stage, uhat, uhat0, R_hist):
 JAC_POLICY = {"every": 0, "once": 1}
 
 
-def time_path(pkg, torch, w, precision, refine, steps, warmup, dev, l2buf, jac="every", barrier=None, graph=False):
+def time_path(pkg, torch, w, precision, refine, steps, warmup, dev, l2buf, jac="every", barrier=None, graph=False,
+              autotune=True):
     ctx = pkg.Context(w.mesh, w.physics, precision=precision, tableau=pkg.FR_TAB_SDIRK2)
     ctx.refine = refine
     ctx.imex_set_jacobian_policy(JAC_POLICY[jac])
@@ -152,7 +153,7 @@ def time_path(pkg, torch, w, precision, refine, steps, warmup, dev, l2buf, jac="
     uhat0 = ctx.hfr_initial_trace(u_n)
     uhat = uhat0.clone()
     tune = None
-    if precision == pkg.FR_PREC_FP32:  # pick the condensation form and GMRES cycle on this workload
+    if autotune and precision == pkg.FR_PREC_FP32:  # pick the condensation form and GMRES cycle on this workload
         tune = ctx.hfr_autotune(u_n, uhat0, u_n, w.dt * (1.0 - 0.5 ** 0.5))
     R_hist = ctx.empty(3, *ctx.state_shape)
     u_stage = ctx.empty(*ctx.state_shape)
@@ -360,6 +361,8 @@ def main():
     ap.add_argument("--paths", default="both", choices=["both", "mixed", "fp64"],
                     help="profiling aid: time only one precision path")
     ap.add_argument("--no-e2e", action="store_true", help="profiling aid: skip the host-buffer e2e leg")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="profiling aid: keep the default kernel forms (timings under a profiler would mislead the tuner)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -388,21 +391,21 @@ def main():
     if args.paths != "both":  # profiling aid: one path, no JSON contract line
         prec = pkg.FR_PREC_FP32 if args.paths == "mixed" else pkg.FR_PREC_FP64
         r = time_path(pkg, torch, w, prec, args.refine if args.paths == "mixed" else 0, args.steps, args.warmup,
-                      dev, l2buf, args.jacobian)
+                      dev, l2buf, args.jacobian, autotune=not args.no_autotune)
         print(json.dumps({"path": args.paths, "ms": r["ms"], "stats": r["stats"],
                           "phases_ms_total": r["profile"], "launches": r["launches"]}))
         return
     barrier = dist.barrier if dist is not None else None
     with ClockSampler(local) as clk:
         mixed = time_path(pkg, torch, w, pkg.FR_PREC_FP32, args.refine, args.steps, args.warmup, dev, l2buf,
-                          args.jacobian, barrier)
+                          args.jacobian, barrier, autotune=not args.no_autotune)
         fp64 = time_path(pkg, torch, w, pkg.FR_PREC_FP64, 0, args.steps, args.warmup, dev, l2buf, args.jacobian,
                          barrier)
         # the same mixed stage as one CUDA graph (no per-kernel phases: timed as a whole)
         graph = None
         if args.jacobian == "every":
             graph = time_path(pkg, torch, w, pkg.FR_PREC_FP32, args.refine, args.steps, args.warmup, dev, l2buf,
-                              args.jacobian, barrier, graph=True)
+                              args.jacobian, barrier, graph=True, autotune=not args.no_autotune)
     clocks = clk.summary()
     ms_mixed, ms_fp64 = replica_max([np.mean(mixed["ms"]), np.mean(fp64["ms"])], dist, dev)
     ms_graph = replica_max([np.mean(graph["ms"])], dist, dev)[0] if graph else None

@@ -815,16 +815,12 @@ __global__ void __launch_bounds__(128, 4) k_inverse_tc(const __grid_constant__ C
       for (int s = 0; s < 16; ++s) {
         if (s < ns) {
           const int b = s & 1;
-          unsigned km = s_key[b * 4 + 0];
+          const uint4 kq = *reinterpret_cast<const uint4*>(s_key + b * 4);
+          unsigned km = kq.x;
           int wb = 0;
-#pragma unroll
-          for (int w2 = 1; w2 < 4; ++w2) {
-            const unsigned kw = s_key[b * 4 + w2];
-            if (kw > km) {
-              km = kw;
-              wb = w2;
-            }
-          }
+          if (kq.y > km) { km = kq.y; wb = 1; }
+          if (kq.z > km) { km = kq.z; wb = 2; }
+          if (kq.w > km) { km = kq.w; wb = 3; }
           const int r = (int)(MASK - (km & MASK));
           if ((km & ~MASK) == 0u) bad = true;
           float prow[16];
@@ -834,7 +830,7 @@ __global__ void __launch_bounds__(128, 4) k_inverse_tc(const __grid_constant__ C
             prow[u] = x.x; prow[u + 1] = x.y; prow[u + 2] = x.z; prow[u + 3] = x.w;
           }
           const float pv = prow[s];
-          const float pinv = pv != 0.f ? 1.f / pv : 0.f;
+          const float pinv = pv != 0.f ? __frcp_rn(pv) : 0.f;
           if (row == r) {
 #pragma unroll
             for (int u = 0; u < 16; ++u) v[u] = prow[u] * pinv;
@@ -1390,16 +1386,21 @@ struct TcShape {
   static constexpr int M = 128;
   static constexpr int NB = N1 > N2 ? N1 : N2;
   static constexpr int KG = K1 / 4;               // 4-element k chunks
-  static constexpr uint32_t SBO = (uint32_t)KG * 128u;
-  static constexpr uint32_t A_BYTES = (uint32_t)M * K1 * 4u;   // one of hi / lo
-  static constexpr uint32_t B_BYTES = (uint32_t)NB * K1 * 4u;
+  // 8-row groups padded by 16 bytes: with SBO = 16 (mod 128) the 4-byte stores of a float4 read
+  // along the rows (lanes = 4 k x 8 row quads) fall in 32 distinct banks
+  static constexpr uint32_t SBO = (uint32_t)KG * 128u + 16u;
+  static constexpr uint32_t A_BYTES = (uint32_t)(M / 8) * SBO;   // one of hi / lo
+  static constexpr uint32_t B_BYTES = (uint32_t)(NB / 8) * SBO;
   static constexpr uint32_t SMEM = 2u * A_BYTES + 2u * B_BYTES + 16u + 128u + 2u * NA * 4u + 1024u;
   // 8 warps: warps 0-6 stage operands, warp 7 (lanes 96-127 of tensor memory, rows the epilogues
   // do not need while nT < 96) allocates tensor memory and issues the MMAs
   static constexpr int THREADS = 256, WARPS = 7, ISSUER = 7;
-  // GEMM 1 staging: warp task = 8 rows x 4 k (one value per lane)
-  static constexpr int A_TASKS = (NT / 8) * KG, A_PER = (A_TASKS + WARPS - 1) / WARPS;
-  static constexpr int B_TASKS = ((NA + 7) / 8) * KG, B_PER = (B_TASKS + WARPS - 1) / WARPS;
+  // GEMM 1 staging: slots of one float4 (four consecutive rows of one k), enumerated k mod 4
+  // fastest, then the row quad, then k / 4
+  static constexpr int AQ = NT / 4, BQ = NA / 4;  // row quads of the A and B operands
+  static constexpr int A_SLOTS = AQ * K1, B_SLOTS = BQ * K1;
+  static constexpr int A_PER = (A_SLOTS + WARPS * 32 - 1) / (WARPS * 32);
+  static constexpr int B_PER = (B_SLOTS + WARPS * 32 - 1) / (WARPS * 32);
   static constexpr int R_PER = (K1 + THREADS - 1) / THREADS;
   // C staging: warp task = 8 rows x 4 chunks of 4 k (one float4 per lane)
   static constexpr int CG = (KG + 3) / 4;
@@ -1412,33 +1413,44 @@ struct TcShape {
   static_assert(SMEM <= 232448, "shared memory");
 };
 
+// slot -> (k, first row) of the float4 staging of a GEMM 1 operand with NQ row quads
+template <int NQ>
+__device__ __forceinline__ void tc_slot(int slot, int& c, int& r0) {
+  const int c_lo = slot & 3, rest = slot >> 2;
+  r0 = 4 * (rest % NQ);
+  c = 4 * (rest / NQ) + c_lo;
+}
+
 // GEMM 1 operands of one element held in registers between their load and their store
 template <int NA, int NT>
 struct TcStage {
-  float av[TcShape<NA, NT>::A_PER];
-  float bv[TcShape<NA, NT>::B_PER];
+  float4 av[TcShape<NA, NT>::A_PER];
+  float4 bv[TcShape<NA, NT>::B_PER];
   float rv[TcShape<NA, NT>::R_PER];
 };
 
-// all loads first (one memory latency per element), pivots from shared memory
+// all loads first (one memory latency per element), 16 bytes per lane along the contiguous
+// dimension, pivots from shared memory
 template <int NA, int NT>
 __device__ __forceinline__ void tc_load_stage(TcStage<NA, NT>& g, const CondArgs& a, int k, const int* pv, int t) {
   using Sh = TcShape<NA, NT>;
-  const int lane = t & 31, w = t >> 5, r8 = lane >> 2, c4 = lane & 3;
   const float* gWt = reinterpret_cast<const float*>(a.LU) + (size_t)k * NA * NA;
   const float* gB = reinterpret_cast<const float*>(a.B) + (size_t)k * NA * NT;
   const double* gr = a.r + (size_t)k * NA;
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
   for (int u = 0; u < Sh::A_PER; ++u) {
-    const int task = w + Sh::WARPS * u;
-    const int jj = 8 * (task / Sh::KG) + r8, c = 4 * (task % Sh::KG) + c4;
-    g.av[u] = (task < Sh::A_TASKS && c < NA) ? __ldg(gB + (size_t)pv[c] * NT + jj) : 0.f;
+    const int slot = t + Sh::WARPS * 32 * u;
+    int c, j0;
+    tc_slot<Sh::AQ>(slot, c, j0);
+    g.av[u] = (slot < Sh::A_SLOTS && c < NA) ? __ldg(reinterpret_cast<const float4*>(gB + (size_t)pv[c] * NT + j0)) : z;
   }
 #pragma unroll
   for (int u = 0; u < Sh::B_PER; ++u) {
-    const int task = w + Sh::WARPS * u;
-    const int i = 8 * (task / Sh::KG) + r8, c = 4 * (task % Sh::KG) + c4;
-    g.bv[u] = (task < Sh::B_TASKS && i < NA && c < NA) ? __ldg(gWt + (size_t)c * NA + i) : 0.f;
+    const int slot = t + Sh::WARPS * 32 * u;
+    int c, i0;
+    tc_slot<Sh::BQ>(slot, c, i0);
+    g.bv[u] = (slot < Sh::B_SLOTS && c < NA) ? __ldg(reinterpret_cast<const float4*>(gWt + (size_t)c * NA + i0)) : z;
   }
 #pragma unroll
   for (int u = 0; u < Sh::R_PER; ++u) {
@@ -1448,33 +1460,42 @@ __device__ __forceinline__ void tc_load_stage(TcStage<NA, NT>& g, const CondArgs
 }
 
 // A: row jj < NT is column jj of P B, row NT is P r; B: row i is row i of (PA)^{-1} (column i of
-// Wt); K padding zero.  Lanes cover 8 rows x 4 k: conflict-free 4-byte stores.
+// Wt); K padding zero.  Four 4-byte stores per float4, conflict-free with the padded row groups.
 template <int NA, int NT>
 __device__ __forceinline__ void tc_store_stage(const TcStage<NA, NT>& g, unsigned char* Ahi, unsigned char* Alo,
                                                unsigned char* Bhi, unsigned char* Blo, int t) {
   using Sh = TcShape<NA, NT>;
   using namespace tc;
-  const int lane = t & 31, w = t >> 5, r8 = lane >> 2, c4 = lane & 3;
 #pragma unroll
   for (int u = 0; u < Sh::A_PER; ++u) {
-    const int task = w + Sh::WARPS * u;
-    if (task < Sh::A_TASKS) {
-      const int jj = 8 * (task / Sh::KG) + r8, c = 4 * (task % Sh::KG) + c4;
-      float h, l;
-      split_tf32(g.av[u], h, l);
-      *reinterpret_cast<float*>(Ahi + kmajor_offset(jj, c, Sh::SBO)) = h;
-      *reinterpret_cast<float*>(Alo + kmajor_offset(jj, c, Sh::SBO)) = l;
+    const int slot = t + Sh::WARPS * 32 * u;
+    if (slot < Sh::A_SLOTS) {
+      int c, j0;
+      tc_slot<Sh::AQ>(slot, c, j0);
+      const float x[4] = {g.av[u].x, g.av[u].y, g.av[u].z, g.av[u].w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        float h, l;
+        split_tf32(x[e], h, l);
+        *reinterpret_cast<float*>(Ahi + kmajor_offset(j0 + e, c, Sh::SBO)) = h;
+        *reinterpret_cast<float*>(Alo + kmajor_offset(j0 + e, c, Sh::SBO)) = l;
+      }
     }
   }
 #pragma unroll
   for (int u = 0; u < Sh::B_PER; ++u) {
-    const int task = w + Sh::WARPS * u;
-    const int i = 8 * (task / Sh::KG) + r8, c = 4 * (task % Sh::KG) + c4;
-    if (task < Sh::B_TASKS && i < NA) {
-      float h, l;
-      split_tf32(g.bv[u], h, l);
-      *reinterpret_cast<float*>(Bhi + kmajor_offset(i, c, Sh::SBO)) = h;
-      *reinterpret_cast<float*>(Blo + kmajor_offset(i, c, Sh::SBO)) = l;
+    const int slot = t + Sh::WARPS * 32 * u;
+    if (slot < Sh::B_SLOTS) {
+      int c, i0;
+      tc_slot<Sh::BQ>(slot, c, i0);
+      const float x[4] = {g.bv[u].x, g.bv[u].y, g.bv[u].z, g.bv[u].w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        float h, l;
+        split_tf32(x[e], h, l);
+        *reinterpret_cast<float*>(Bhi + kmajor_offset(i0 + e, c, Sh::SBO)) = h;
+        *reinterpret_cast<float*>(Blo + kmajor_offset(i0 + e, c, Sh::SBO)) = l;
+      }
     }
   }
 #pragma unroll
@@ -1542,17 +1563,34 @@ __global__ void __launch_bounds__(256, 1) k_products_tc(const __grid_constant__ 
   uint32_t pend = 0;  // parity of the phase being waited for
   TcStage<NA, NT> g;
   if (k < a.Eim && !issuer) tc_load_stage<NA, NT>(g, a, k, s_pv, t);
+  static_assert(NA <= Sh::THREADS, "one pivot per thread");
+  if (issuer && lane == 0 && k + G < a.Eim) {  // the first iteration loads element k + G
+    const size_t o = (size_t)k + G;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<const float*>(a.LU) + o * NA * NA),
+                 "r"((unsigned)(NA * NA * 4)) : "memory");
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<const float*>(a.B) + o * NA * NT),
+                 "r"((unsigned)(NA * NT * 4)) : "memory");
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<const float*>(a.C) + o * NT * NA),
+                 "r"((unsigned)(NT * NA * 4)) : "memory");
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<const float*>(a.D) + o * NT * NT),
+                 "r"((unsigned)(NT * NT * 4)) : "memory");
+  }
+  int pv_next = (k + G < a.Eim && t < NA) ? __ldg(a.piv + (size_t)(k + G) * NA + t) : 0;
   for (int it = 0; k < a.Eim; k += G, ++it) {
     const int buf = it & 1;
     const int kn = k + G;
     if (!issuer) tc_store_stage<NA, NT>(g, Ahi, Alo, Bhi, Blo, t);
+    // the next element's pivots, read one iteration ahead (this buffer's last reader was two
+    // iterations ago)
+    if (kn < a.Eim && t < NA) s_pv[(buf ^ 1) * NA + t] = pv_next;
     fence_proxy_async();
     fence_before_sync();
     __syncthreads();
     if (issuer && lane == 0) {
       tc_issue<NA, NT>(tmem, Ahi, Alo, Bhi, Blo, idesc_tf32(128, Sh::N1), smem_u32(mbar));
-      if (kn < a.Eim) {
-        const size_t o = (size_t)kn;
+      // L2 prefetch two elements ahead: the next element's operands are loaded in this iteration
+      if (kn + G < a.Eim) {
+        const size_t o = (size_t)kn + G;
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<const float*>(a.LU) + o * NA * NA),
                      "r"((unsigned)(NA * NA * 4)) : "memory");
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<const float*>(a.B) + o * NA * NT),
@@ -1563,9 +1601,6 @@ __global__ void __launch_bounds__(256, 1) k_products_tc(const __grid_constant__ 
                      "r"((unsigned)(NT * NT * 4)) : "memory");
       }
     }
-    // the next element's pivots (the other buffer is free: its readers passed the barrier above)
-    if (kn < a.Eim)
-      for (int c = t; c < NA; c += blockDim.x) s_pv[(buf ^ 1) * NA + c] = a.piv[(size_t)kn * NA + c];
     // C for GEMM 2, read while GEMM 1 runs
     const float* gC = reinterpret_cast<const float*>(a.C) + (size_t)k * NT * NA;
     float4 creg[Sh::C_PER];
@@ -1577,6 +1612,8 @@ __global__ void __launch_bounds__(256, 1) k_products_tc(const __grid_constant__ 
                     ? __ldg(reinterpret_cast<const float4*>(gC + (size_t)i * NA) + ch)
                     : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    // the next element's GEMM 1 operands, in flight during GEMM 1, epilogue 1 and GEMM 2
+    if (kn < a.Eim && !issuer) tc_load_stage<NA, NT>(g, a, kn, s_pv + (buf ^ 1) * NA, t);
     pend = 0;
     ok = mbar_wait(smem_u32(mbar), 0, tc::TIMEOUT_NS);
     if (__syncthreads_or(!ok)) {
@@ -1644,8 +1681,8 @@ __global__ void __launch_bounds__(256, 1) k_products_tc(const __grid_constant__ 
     __syncthreads();
     if (issuer && lane == 0)
       tc_issue<NA, NT>(tmem + Sh::D2_COL, Ahi, Alo, Bhi, Blo, idesc_tf32(128, Sh::N2), smem_u32(mbar));
-    // while GEMM 2 runs: the next element's GEMM 1 operands and this element's D and s
-    if (kn < a.Eim && !issuer) tc_load_stage<NA, NT>(g, a, kn, s_pv + (buf ^ 1) * NA, t);
+    if (kn + G < a.Eim && t < NA) pv_next = __ldg(a.piv + (size_t)(kn + G) * NA + t);
+    // while GEMM 2 runs: this element's D and s
     const int cb2 = hh == 0 ? 0 : Sh::H2, ce2 = hh == 0 ? Sh::H2 : Sh::NCH2;
     const float* gD = reinterpret_cast<const float*>(a.D) + (size_t)k * NT * NT;
     float dreg[16 * Sh::H2];
