@@ -126,10 +126,54 @@ class NavierStokes2D:
         return self.wave_speed(uh, n) + self.mu / (uh[..., 0] * self.lref)
 
 
+class EDAC2D:
+    """Entropically damped artificial compressibility (Appendix A): u = (P, v_x, v_y),
+    F^c_i = (v_i (P + Theta), v_i v_x + P delta_ix, v_i v_y + P delta_iy), F^v_i = nu du/dx_i,
+    Theta = 1 / M^2 (artificial Mach number), nu = 1 / Re.
+
+    * Standard-FR Rusanov speed: the largest eigenvalue magnitude of the normal flux Jacobian,
+      3/2 |v.n| + sqrt((v.n)^2 / 4 + P + Theta) (the eigenvalues are v.n and
+      3/2 v.n +- sqrt((v.n)^2/4 + P + Theta)).
+    * HFR stabilisation (Sec. 5.4): s = 3/2 |v^| + d^, d^2 = |v^|^2 / 4 + P^ + Theta, isotropic, at
+      the trace state; plus nu / lref for the viscous terms (as for the other two laws).
+      |v^| has no derivative at v^ = 0: states with a nonzero velocity everywhere are assumed.
+    """
+
+    nv = 3
+
+    def __init__(self, theta=100.0, nu=1e-3, lref=1.0):
+        self.theta = float(theta)
+        self.nu = float(nu)
+        self.lref = float(lref)
+        self.viscous = self.nu != 0.0
+
+    def conv(self, u):
+        P, vx, vy = u[..., 0], u[..., 1], u[..., 2]
+        Pt = P + self.theta
+        Fx = np.stack([vx * Pt, vx * vx + P, vx * vy], axis=-1)
+        Fy = np.stack([vy * Pt, vy * vx, vy * vy + P], axis=-1)
+        return np.stack([Fx, Fy], axis=-2)
+
+    def visc(self, u, q):
+        return self.nu * q
+
+    def wave_speed(self, u, n):
+        P, vx, vy = u[..., 0], u[..., 1], u[..., 2]
+        vn = vx * n[..., 0] + vy * n[..., 1]
+        return 1.5 * cabs(vn) + np.sqrt(0.25 * vn * vn + P + self.theta)
+
+    def stab(self, uh, n):
+        P, vx, vy = uh[..., 0], uh[..., 1], uh[..., 2]
+        v2 = vx * vx + vy * vy
+        return 1.5 * np.sqrt(v2) + np.sqrt(0.25 * v2 + P + self.theta) + self.nu / self.lref
+
+
 def make_physics(spec: dict):
     kind = spec["kind"]
     if kind == "advdiff":
         return AdvectionDiffusion(spec["beta"], spec["nu"], spec.get("lref", 1.0))
     if kind == "ns":
         return NavierStokes2D(spec["gamma"], spec["mu"], spec["Pr"], spec.get("lref", 1.0))
+    if kind == "edac":
+        return EDAC2D(spec["theta"], spec["nu"], spec.get("lref", 1.0))
     raise KeyError(kind)

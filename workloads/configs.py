@@ -12,7 +12,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from .mesh import structured_quads, uniform_nodes
-from .states import sample_points, gaussian_scalar, isentropic_vortex, uniform_noise
+from .states import edac_vortex, sample_points, gaussian_scalar, isentropic_vortex, uniform_noise
 
 
 @dataclass
@@ -64,6 +64,19 @@ def _vortex(n=64, p=3, noise=0.0, seed=1234, cfl_mult=10.0, jitter=0.0, implicit
     return mesh, u0, phys, cfl_mult * dt_ex
 
 
+def _edac(n=16, p=3, theta=100.0, re=1.0e3, cfl_mult=10.0, jitter=0.0, seed=0, implicit=None, noise=0.0):
+    L = 10.0
+    mesh = structured_quads(uniform_nodes(n, 0.0, L), uniform_nodes(n, 0.0, L),
+                            periodic=(True, True), jitter=jitter, seed=seed, p=p, implicit=implicit)
+    u0 = edac_vortex(sample_points(mesh, p), strength=1.0, speed=1.0, center=(5.0, 5.0))
+    if noise > 0.0:
+        u0 = u0 + uniform_noise(u0.shape, noise, seed)
+    phys = {"kind": "edac", "theta": theta, "nu": 1.0 / re, "lref": 1.0}
+    lam = 1.5 + np.sqrt(0.25 + theta)  # largest wave speed of the uniform stream
+    dt_ex = (L / n) / (lam * (2 * p + 1))
+    return mesh, u0, phys, cfl_mult * dt_ex
+
+
 def make_config(name: str, **kw) -> Workload:
     if name == "advdiff8":  # 8x8 p=2 advection-diffusion, one backward-Euler step
         mesh, u0, phys, dt = _advdiff(**kw)
@@ -80,6 +93,9 @@ def make_config(name: str, **kw) -> Workload:
         return Workload(name, mesh, int(mesh.p[0]), phys, u0, dt, "sdirk2")
     if name == "vortex":  # generic vortex of any size for tests
         mesh, u0, phys, dt = _vortex(**kw)
+        return Workload(name, mesh, int(mesh.p[0]), phys, u0, dt, "sdirk2")
+    if name == "edac":  # EDAC vortex in a uniform stream (Theta = 100), one SDIRK2 step at 10x CFL
+        mesh, u0, phys, dt = _edac(**kw)
         return Workload(name, mesh, int(mesh.p[0]), phys, u0, dt, "sdirk2")
     if name == "advdiff":
         mesh, u0, phys, dt = _advdiff(**kw)

@@ -81,3 +81,18 @@ def uniform_noise(shape, amplitude: float, seed: int) -> np.ndarray:
     """Seeded U(-amplitude, amplitude) noise (numpy PCG64)."""
     rng = np.random.default_rng(seed)
     return rng.uniform(-amplitude, amplitude, size=shape)
+
+
+def edac_vortex(xy: np.ndarray, strength=1.0, speed=1.0, center=(5.0, 5.0)) -> np.ndarray:
+    """(P, v_x, v_y) of an incompressible vortex carried by a uniform stream (speed, 0): the
+    velocity perturbation (strength / 2 pi) r exp((1 - r^2)/2) about ``center`` and the pressure
+    -strength^2 / (8 pi^2) exp(1 - r^2) that balances it.  With strength < 2 pi speed / 1.2 the
+    velocity never vanishes."""
+    dx = xy[..., 0] - center[0]
+    dy = xy[..., 1] - center[1]
+    r2 = dx * dx + dy * dy
+    amp = strength / (2.0 * np.pi) * np.exp(0.5 * (1.0 - r2))
+    vx = speed - amp * dy
+    vy = amp * dx
+    P = -strength**2 / (8.0 * np.pi**2) * np.exp(1.0 - r2)
+    return np.stack([P, vx, vy], axis=-1)
