@@ -54,7 +54,10 @@ enum fr_status {
   FR_ERR_UNSUPPORTED = 8    /* configuration outside what this build implements */
 };
 
-enum fr_physics { FR_PHYS_ADVDIFF = 0, FR_PHYS_NAVIER_STOKES = 1 };
+/* FR_PHYS_EDAC: entropically damped artificial compressibility (Appendix A), u = (P, v_x, v_y),
+ * parameters theta = 1 / M^2 and nu = 1 / Re; p = 2..4; the velocity must not vanish at a trace
+ * point (the hybridized stabilisation of Sec. 5.4 contains |v^|). */
+enum fr_physics { FR_PHYS_ADVDIFF = 0, FR_PHYS_NAVIER_STOKES = 1, FR_PHYS_EDAC = 2 };
 /* Precision of the element blocks, their LU and condensation, and the stored S^k. */
 enum fr_precision { FR_PREC_FP64 = 0, FR_PREC_FP32 = 1 };
 enum fr_tableau { FR_TAB_BE = 0, FR_TAB_SDIRK2 = 1 };
@@ -75,7 +78,7 @@ typedef struct {
 typedef struct {
   int physics;     /* fr_physics */
   double beta[2];  /* advection velocity */
-  double nu;       /* diffusivity */
+  double nu;       /* diffusivity (advection-diffusion), 1 / Re (EDAC) */
   double gamma;    /* ratio of specific heats */
   double mu;       /* dynamic viscosity */
   double Pr;       /* Prandtl number */
@@ -83,6 +86,7 @@ typedef struct {
   int precision;   /* fr_precision */
   int tableau;     /* fr_tableau: implicit DIRK + explicit partner of the IMEX pair */
   int gmres_restart; /* m <= 64 */
+  double theta;    /* EDAC: 1 / M^2 of the artificial Mach number */
 } fr_config;
 
 typedef struct {

@@ -28,7 +28,7 @@ LIB_PATH = os.path.join(HERE, "libhfr.so")
 
 FR_PREC_FP64, FR_PREC_FP32 = 0, 1
 FR_TAB_BE, FR_TAB_SDIRK2 = 0, 1
-FR_PHYS_ADVDIFF, FR_PHYS_NAVIER_STOKES = 0, 1
+FR_PHYS_ADVDIFF, FR_PHYS_NAVIER_STOKES, FR_PHYS_EDAC = 0, 1, 2
 FR_GMRES_MULTI, FR_GMRES_FUSED = 0, 1
 FR_JAC_EVERY_NEWTON, FR_JAC_ONCE_PER_STAGE = 0, 1
 FR_CONDENSE_FMA, FR_CONDENSE_TENSOR_PRODUCTS, FR_CONDENSE_TENSOR = 0, 1, 2
@@ -95,6 +95,7 @@ class fr_config(ctypes.Structure):
         ("precision", ctypes.c_int),
         ("tableau", ctypes.c_int),
         ("gmres_restart", ctypes.c_int),
+        ("theta", ctypes.c_double),
     ]
 
 
@@ -270,6 +271,9 @@ class Context:
             cfg.physics = FR_PHYS_ADVDIFF
             cfg.beta[0], cfg.beta[1] = physics["beta"][0], physics["beta"][1]
             cfg.nu = physics["nu"]
+        elif physics["kind"] == "edac":
+            cfg.physics = FR_PHYS_EDAC
+            cfg.theta, cfg.nu = physics["theta"], physics["nu"]
         else:
             cfg.physics = FR_PHYS_NAVIER_STOKES
             cfg.gamma, cfg.mu, cfg.Pr = physics["gamma"], physics["mu"], physics["Pr"]

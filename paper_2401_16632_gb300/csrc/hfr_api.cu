@@ -374,9 +374,11 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, const fr_config* cfg, voi
   if (mesh->nelem <= 0 || !mesh->verts || !mesh->nbr || !mesh->nbr_face || !mesh->face_of || !mesh->implicit)
     return FR_ERR_INVALID_ARG;
   if (mesh->p < 1 || mesh->p > 5) return FR_ERR_UNSUPPORTED;
+  if (cfg->physics != FR_PHYS_ADVDIFF && cfg->physics != FR_PHYS_NAVIER_STOKES && cfg->physics != FR_PHYS_EDAC)
+    return FR_ERR_INVALID_ARG;
   if (cfg->physics == FR_PHYS_ADVDIFF && mesh->p > 3) return FR_ERR_UNSUPPORTED;
   if (cfg->physics == FR_PHYS_NAVIER_STOKES && mesh->p < 2) return FR_ERR_UNSUPPORTED;
-  if (cfg->physics != FR_PHYS_ADVDIFF && cfg->physics != FR_PHYS_NAVIER_STOKES) return FR_ERR_INVALID_ARG;
+  if (cfg->physics == FR_PHYS_EDAC && (mesh->p < 2 || mesh->p > 4 || !(cfg->theta > 0.0))) return FR_ERR_UNSUPPORTED;
   if (cfg->precision != FR_PREC_FP64 && cfg->precision != FR_PREC_FP32) return FR_ERR_INVALID_ARG;
   fr_ctx* ctx = new fr_ctx();
   memset(&ctx->err, 0, sizeof(ctx->err));
@@ -385,7 +387,7 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, const fr_config* cfg, voi
   ctx->p = mesh->p;
   ctx->n = mesh->p + 1;
   ctx->ns = ctx->n * ctx->n;
-  ctx->nv = cfg->physics == FR_PHYS_ADVDIFF ? 1 : 4;
+  ctx->nv = cfg->physics == FR_PHYS_ADVDIFF ? 1 : (cfg->physics == FR_PHYS_EDAC ? 3 : 4);
   ctx->nA = ctx->ns * ctx->nv;
   ctx->nT = 4 * ctx->n * ctx->nv;
   ctx->prec_bytes = cfg->precision == FR_PREC_FP64 ? 8 : 4;
@@ -400,6 +402,7 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, const fr_config* cfg, voi
   ctx->pp.mu = cfg->mu;
   ctx->pp.Pr = cfg->Pr;
   ctx->pp.lref = cfg->lref > 0 ? cfg->lref : 1.0;
+  ctx->pp.theta = cfg->physics == FR_PHYS_EDAC ? cfg->theta : 0.0;
   build_ref(ctx->p, ctx->ref);
 
   const int E = ctx->E, n = ctx->n, ns = ctx->ns, NF = 4 * n;

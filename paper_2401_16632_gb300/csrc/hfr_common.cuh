@@ -27,12 +27,15 @@ struct RefOps {
 };
 
 struct PhysParams {
-  int kind;  // 0 advection-diffusion, 1 Navier-Stokes 2D
+  int kind;  // 0 advection-diffusion, 1 Navier-Stokes 2D, 2 EDAC 2D
   double beta[3];
   double nu;
   double gamma, mu, Pr;
   double lref;
+  double theta;  // EDAC: 1 / M^2 of the artificial Mach number
 };
+// viscous terms present (advection-diffusion and EDAC: nu; Navier-Stokes: mu)
+__host__ __device__ inline bool phys_viscous(const PhysParams& pp) { return pp.kind == 1 ? pp.mu != 0.0 : pp.nu != 0.0; }
 
 // face kinds of an element face
 enum { FK_FR = 0, FK_TRACE = 1, FK_IMEX = 2 };
@@ -98,6 +101,7 @@ template <typename R>
 struct PhysConst {
   R beta0, beta1, nu, nu_lref;          // advection-diffusion
   R gamma, gm1, mu, kappa, mu_lref;     // Navier-Stokes
+  R theta;                              // EDAC
 };
 template <typename R>
 __host__ __device__ inline PhysConst<R> phys_const(const PhysParams& pp) {
@@ -111,6 +115,7 @@ __host__ __device__ inline PhysConst<R> phys_const(const PhysParams& pp) {
   c.mu = R(pp.mu);
   c.kappa = pp.kind == 1 ? R(pp.mu * pp.gamma / ((pp.gamma - 1.0) * pp.Pr)) : R(0);
   c.mu_lref = R(pp.mu / pp.lref);
+  c.theta = R(pp.theta);
   return c;
 }
 
@@ -196,6 +201,41 @@ template <> struct Phys<1> {
   template <typename S, typename R>
   __device__ static S stab(const PhysConst<R>& pc, const S* u, R n0, R n1) {
     return wave<S, R>(pc, u, n0, n1) + pc.mu_lref / u[0];
+  }
+};
+
+// EDAC (Appendix A): u = (P, v_x, v_y), F^c_i = (v_i (P + Theta), v_i v_x + P delta_ix,
+// v_i v_y + P delta_iy), F^v_i = nu du/dx_i.  Rusanov speed: the largest eigenvalue magnitude of
+// the normal flux Jacobian, 3/2 |v.n| + sqrt((v.n)^2/4 + P + Theta); hybridized stabilisation
+// (Sec. 5.4): 3/2 |v| + sqrt(|v|^2/4 + P + Theta), isotropic, plus nu / lref.
+template <> struct Phys<2> {
+  static constexpr int NV = 3;
+  template <typename S, typename R>
+  __device__ static void conv(const PhysConst<R>& pc, const S* u, S F[2][3]) {
+    const S Pt = u[0] + pc.theta;
+    F[0][0] = u[1] * Pt;
+    F[0][1] = u[1] * u[1] + u[0];
+    F[0][2] = u[1] * u[2];
+    F[1][0] = u[2] * Pt;
+    F[1][1] = u[2] * u[1];
+    F[1][2] = u[2] * u[2] + u[0];
+  }
+  template <typename S, typename R>
+  __device__ static void visc(const PhysConst<R>& pc, const S* u, const S q[2][3], S F[2][3]) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int v = 0; v < 3; ++v) F[c][v] = pc.nu * q[c][v];
+  }
+  template <typename S, typename R>
+  __device__ static S wave(const PhysConst<R>& pc, const S* u, R n0, R n1) {
+    const S vn = u[1] * n0 + u[2] * n1;
+    return R(1.5) * dabs(vn) + dsqrt(R(0.25) * vn * vn + u[0] + pc.theta);
+  }
+  template <typename S, typename R>
+  __device__ static S stab(const PhysConst<R>& pc, const S* u, R n0, R n1) {
+    const S v2 = u[1] * u[1] + u[2] * u[2];
+    return R(1.5) * dsqrt(v2) + dsqrt(R(0.25) * v2 + u[0] + pc.theta) + pc.nu_lref;
   }
 };
 

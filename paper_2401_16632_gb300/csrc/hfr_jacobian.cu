@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(JAC_THREADS, sizeof(T) == 4 ? (P <= 3 ? 4 : (P
   if (k >= a.Eim) return;
   const int e = a.imp_idx[k];
   const int tid = threadIdx.x;
-  const bool visc = pp.kind == 0 ? (pp.nu != 0.0) : (pp.mu != 0.0);
+  const bool visc = phys_viscous(pp);
   const PhysConst<T> pc = phys_const<T>(pp);
   const double* gs = a.geo_sol + (size_t)e * NS * 5;
   const double* gf = a.geo_face + (size_t)e * NF * 3;
@@ -366,14 +366,14 @@ __global__ void __launch_bounds__(JAC_THREADS, sizeof(T) == 4 ? (P <= 3 ? 4 : (P
     //                      - dgL[ai] dFn(xi-, bi) + dgR[ai] dFn(xi+, bi)
     //                      - dgL[bi] dFn(eta-, ai) + dgR[bi] dFn(eta+, ai) ]
     //   dg^k(f, m) = w_m dFn(f, m)   (trace faces)
-    constexpr int NPART = JAC_THREADS / (JAC_SB * NV);
-    static_assert(NPART * JAC_SB * NV == JAC_THREADS, "phase 3 thread map");
+    constexpr int NPART = JAC_THREADS / (JAC_SB * NV);  // threads beyond NPART JAC_SB NV idle here
+    static_assert(NPART >= 1, "phase 3 thread map");
     {
       const int s = tid % JAC_SB;
       const int v = (tid / JAC_SB) % NV;
       const int part = tid / (JAC_SB * NV);
       const int sd = s0 + s;
-      if (sd < NSEED) {
+      if (sd < NSEED && part < NPART) {
         T dgl[N], dgr[N];
 #pragma unroll
         for (int x = 0; x < N; ++x) {
@@ -459,6 +459,12 @@ static cudaError_t jac_dispatch(int p, const RefOps& ref, const PhysParams& pp, 
       case 1: return jac_impl<1, 0, T>(ref, pp, a, st);
       case 2: return jac_impl<2, 0, T>(ref, pp, a, st);
       case 3: return jac_impl<3, 0, T>(ref, pp, a, st);
+    }
+  } else if (pp.kind == 2) {
+    switch (p) {
+      case 2: return jac_impl<2, 2, T>(ref, pp, a, st);
+      case 3: return jac_impl<3, 2, T>(ref, pp, a, st);
+      case 4: return jac_impl<4, 2, T>(ref, pp, a, st);
     }
   } else {
     switch (p) {

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(TPE* EPB) k_element(const __grid_constant__ Re
   const int e = blockIdx.x * EPB + g;
   const bool live = e < a.E;
   W& w = works[g];
-  const bool viscous = pp.kind == 0 ? (pp.nu != 0.0) : (pp.mu != 0.0);
+  const bool viscous = phys_viscous(pp);
   const PhysConst<double> pc = phys_const<double>(pp);
   const bool is_imp = live ? (a.implicit[e] != 0) : false;
   const double* gs = a.geo_sol + (size_t)e * NS * 5;
@@ -314,6 +314,12 @@ cudaError_t launch_residual(int p, const RefOps& ref, const PhysParams& pp, cons
       case 2: return residual_impl<2, 0>(ref, pp, a, need_nbr, jvp, st);
       case 3: return residual_impl<3, 0>(ref, pp, a, need_nbr, jvp, st);
     }
+  } else if (pp.kind == 2) {
+    switch (p) {
+      case 2: return residual_impl<2, 2>(ref, pp, a, need_nbr, jvp, st);
+      case 3: return residual_impl<3, 2>(ref, pp, a, need_nbr, jvp, st);
+      case 4: return residual_impl<4, 2>(ref, pp, a, need_nbr, jvp, st);
+    }
   } else {
     switch (p) {
       case 2: return residual_impl<2, 1>(ref, pp, a, need_nbr, jvp, st);
@@ -331,6 +337,12 @@ cudaError_t launch_face_states(int p, const RefOps& ref, const PhysParams& pp, c
       case 1: return launch_elem<1, 0, double, MODE_UF>(ref, pp, a, st);
       case 2: return launch_elem<2, 0, double, MODE_UF>(ref, pp, a, st);
       case 3: return launch_elem<3, 0, double, MODE_UF>(ref, pp, a, st);
+    }
+  } else if (pp.kind == 2) {
+    switch (p) {
+      case 2: return launch_elem<2, 2, double, MODE_UF>(ref, pp, a, st);
+      case 3: return launch_elem<3, 2, double, MODE_UF>(ref, pp, a, st);
+      case 4: return launch_elem<4, 2, double, MODE_UF>(ref, pp, a, st);
     }
   } else {
     switch (p) {
