@@ -216,6 +216,15 @@ int imex_stage(fr_ctx* ctx, int stage, double dt, const double* u_n, double* u_s
                double* R_hist, double newton_tol, int newton_maxit, double gmres_rtol, int gmres_maxit,
                int refine, fr_stage_stats* stats /* host, nullable */);
 
+/* Modal filter of Appendix B, in place on u (device, nelem x ns x nv): on every element of the
+ * selection (which: 0 all, 1 implicit, 2 explicit) and every variable, u <- F u with
+ * F = V Lambda* V^{-1}, V the tensor-product orthonormal Legendre basis at the solution points,
+ * Lambda = diag(sigma(i + j)) for the mode of degrees (i, j): sigma = 1 below eta_c,
+ * exp(-alpha ((eta - eta_c) / (2p - eta_c))^s) from eta_c to 2p.  Lambda* = Lambda^dt_ratio with
+ * dt_ratio = dt / dt_ref (a reading of the paper's time-step normalisation; 1 for Lambda* = Lambda).
+ * Keeps each element's mean.  FR_ERR_INVALID_ARG for alpha < 0, s <= 0, eta_c < 0, dt_ratio <= 0. */
+int fr_modal_filter(fr_ctx* ctx, double* u, double alpha, double s, int eta_c, double dt_ratio, int which);
+
 /* Autotuner (no counterpart in the paper): forms the element blocks at (u, uhat, ustar, a_dt) as
  * hfr_local_jacobian does, then times on them, with CUDA events on the context stream (best of
  * two after a warm-up), every condensation form available for the context's precision and block

@@ -51,6 +51,7 @@ ABI_SYMBOLS = [
     "hfr_gmres_get_mode",
     "hfr_condense_set_mode",
     "hfr_condense_get_mode",
+    "fr_modal_filter",
     "hfr_autotune",
     "imex_stage_set_graph",
     "imex_stage_get_graph",
@@ -177,6 +178,7 @@ def load_library(path: str = LIB_PATH):
     lib.hfr_gmres_get_mode.argtypes = [vp]
     lib.hfr_condense_set_mode.argtypes = [vp, ctypes.c_int]
     lib.hfr_condense_get_mode.argtypes = [vp]
+    lib.fr_modal_filter.argtypes = [vp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int]
     lib.hfr_autotune.argtypes = [vp, dp, dp, dp, ctypes.c_double, ctypes.POINTER(fr_tune_report)]
     lib.imex_stage_set_graph.argtypes = [vp, ctypes.c_int]
     lib.imex_stage_get_graph.argtypes = [vp]
@@ -363,6 +365,12 @@ class Context:
 
     def hfr_gmres_get_mode(self) -> int:
         return int(self.lib.hfr_gmres_get_mode(self.h))
+
+    def fr_modal_filter(self, u, alpha, s, eta_c, dt_ratio=1.0, which=0):
+        """In place on u (device tensor): the modal filter of Appendix B (see include/hfr.h)."""
+        self._check(self.lib.fr_modal_filter(self.h, _ptr(u), float(alpha), float(s), int(eta_c), float(dt_ratio),
+                                             int(which)))
+        return u
 
     def hfr_autotune(self, u, uhat, ustar, a_dt):
         rep = fr_tune_report()

@@ -75,6 +75,7 @@ struct fr_ctx {
   int jac_policy = 0;       // FR_JAC_EVERY_NEWTON or FR_JAC_ONCE_PER_STAGE
   int cond_mode = 0;        // fr_condense_mode of the FP32 condensation
   int inv_ctas = 0;         // CTAs per SM of the tensor-core inverse (0: default)
+  double* filt = nullptr;   // ns x ns modal filter operator (fr_modal_filter)
   // whole-stage CUDA graph
   int use_graph = 0;
   StageDev* sdev = nullptr;
@@ -556,6 +557,7 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, const fr_config* cfg, voi
   ctx->lin_Ubuf = dalloc<double>(ctx, (size_t)E * nA, &rc);
   ctx->lin_uhbuf = dalloc<double>(ctx, std::max(nh, (size_t)1), &rc);
   ctx->red = dalloc<double>(ctx, 1024 + 8, &rc);
+  ctx->filt = dalloc<double>(ctx, (size_t)ctx->ns * ctx->ns, &rc);
   if (rc != FR_OK) {
     fr_ctx_destroy(ctx);
     return rc;
@@ -1081,6 +1083,96 @@ extern "C" int hfr_autotune(fr_ctx* ctx, const double* u, const double* uhat, co
   rep.inverse_ctas_per_sm = ctx->inv_ctas;
   rep.gmres_mode = ctx->gm_mode;
   if (out) *out = rep;
+  return FR_OK;
+}
+
+// ------------------------------------------------------------------ modal filter (Appendix B)
+// u[e][i][v] <- sum_k F[i][k] u[e][k][v] on the selected elements, F = V Lambda* V^{-1}; one thread
+// per (element, variable) holds its column, so the update is in place.
+template <int NS>
+__global__ void k_modal_filter(int E, int nv, const double* __restrict__ F, const unsigned char* __restrict__ implicit,
+                               int which, double* __restrict__ U) {
+  __shared__ double sF[NS * NS];
+  for (int i = threadIdx.x; i < NS * NS; i += blockDim.x) sF[i] = F[i];
+  __syncthreads();
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)E * nv) return;
+  const int e = (int)(t / nv), v = (int)(t % nv);
+  if (which == 1 && !implicit[e]) return;
+  if (which == 2 && implicit[e]) return;
+  double* u = U + (size_t)e * NS * nv + v;
+  double x[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) x[k] = u[(size_t)k * nv];
+#pragma unroll 4
+  for (int i = 0; i < NS; ++i) {
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) acc += sF[i * NS + k] * x[k];
+    u[(size_t)i * nv] = acc;
+  }
+}
+
+// F = V Lambda* V^{-1} with V^{-1} = V^T W (the orthonormal basis is orthonormal under the tensor
+// Gauss rule), V the tensor products of psi_k = sqrt((2k+1)/2) P_k at the Gauss points, Lambda* =
+// sigma(i + j)^dt_ratio
+static void modal_filter_operator(int p, double alpha, double s, int eta_c, double dt_ratio, double* F) {
+  const int n = p + 1, ns = n * n, eta_max = 2 * p;
+  double x[HFR_MAXN], w[HFR_MAXN], psi[HFR_MAXN][HFR_MAXN];  // psi[a][k] = psi_k(x_a)
+  gauss_legendre_host(n, x, w);
+  for (int a = 0; a < n; ++a) {
+    double pm = 1.0, pk = x[a];
+    for (int k = 0; k < n; ++k) {
+      double P;
+      if (k == 0) P = 1.0;
+      else if (k == 1) P = x[a];
+      else {
+        const double pn = ((2.0 * k - 1.0) * x[a] * pk - (k - 1.0) * pm) / k;
+        pm = pk;
+        pk = pn;
+        P = pn;
+      }
+      psi[a][k] = sqrt((2.0 * k + 1.0) / 2.0) * P;
+    }
+  }
+  double lam[2 * HFR_MAXN];
+  for (int eta = 0; eta <= eta_max; ++eta) {
+    double sg = 1.0;
+    if (eta >= eta_c) sg = eta_max > eta_c ? exp(-alpha * pow((double)(eta - eta_c) / (eta_max - eta_c), s)) : exp(-alpha);
+    lam[eta] = pow(sg, dt_ratio);
+  }
+  for (int i = 0; i < ns; ++i) {
+    const int a = i % n, b = i / n;
+    for (int k = 0; k < ns; ++k) {
+      const int ak = k % n, bk = k / n;
+      double acc = 0.0;
+      for (int jj = 0; jj < n; ++jj)
+        for (int ii = 0; ii < n; ++ii) acc += psi[a][ii] * psi[b][jj] * lam[ii + jj] * psi[ak][ii] * psi[bk][jj];
+      F[i * ns + k] = acc * w[ak] * w[bk];
+    }
+  }
+}
+
+extern "C" int fr_modal_filter(fr_ctx* ctx, double* u, double alpha, double s, int eta_c, double dt_ratio, int which) {
+  if (!ctx || !u || !(alpha >= 0.0) || !(s > 0.0) || eta_c < 0 || !(dt_ratio > 0.0) || which < 0 || which > 2)
+    return set_err(ctx, FR_ERR_INVALID_ARG, "fr_modal_filter: bad argument");
+  const int ns = ctx->ns;
+  std::vector<double> F((size_t)ns * ns);
+  modal_filter_operator(ctx->p, alpha, s, eta_c, dt_ratio, F.data());
+  CK(cudaMemcpyAsync(ctx->filt, F.data(), F.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  const size_t nt = (size_t)ctx->E * ctx->nv;
+  if (nt == 0) return FR_OK;
+  const unsigned grid = nblk(nt, 128);
+  switch (ns) {
+    case 4: (hfr::count_launch(), k_modal_filter<4><<<grid, 128, 0, ctx->stream>>>(ctx->E, ctx->nv, ctx->filt, ctx->implicit, which, u)); break;
+    case 9: (hfr::count_launch(), k_modal_filter<9><<<grid, 128, 0, ctx->stream>>>(ctx->E, ctx->nv, ctx->filt, ctx->implicit, which, u)); break;
+    case 16: (hfr::count_launch(), k_modal_filter<16><<<grid, 128, 0, ctx->stream>>>(ctx->E, ctx->nv, ctx->filt, ctx->implicit, which, u)); break;
+    case 25: (hfr::count_launch(), k_modal_filter<25><<<grid, 128, 0, ctx->stream>>>(ctx->E, ctx->nv, ctx->filt, ctx->implicit, which, u)); break;
+    case 36: (hfr::count_launch(), k_modal_filter<36><<<grid, 128, 0, ctx->stream>>>(ctx->E, ctx->nv, ctx->filt, ctx->implicit, which, u)); break;
+    default: return set_err(ctx, FR_ERR_UNSUPPORTED, "fr_modal_filter: degree");
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->stream));  // the host operator buffer is released on return
   return FR_OK;
 }
 

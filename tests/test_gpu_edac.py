@@ -126,3 +126,22 @@ def test_edac_imex_step_matches_oracle(name, precision, graph):
                               gmres_rtol=1e-13 if precision == "fp64" else 1e-8, gmres_maxit=3000)
     inc = np.abs(U_o - w.u0).max()
     assert np.abs(u1.cpu().numpy() - U_o).max() < (1e-9 if precision == "fp64" else 1e-8) * inc
+
+
+@pytest.mark.parametrize("which", [0, 1, 2])
+@pytest.mark.parametrize("name", ["edac_p2", "edac_band_p3", "edac_p4"])
+def test_modal_filter_matches_oracle(name, which):
+    """Appendix B's modal filter on the GPU (operator built through orthonormality, V^{-1} =
+    V^T W) against the oracle's (explicit Vandermonde inverse), on all, implicit or explicit
+    elements."""
+    from oracle.filter import apply_filter
+
+    w, ctx, d = _setup(name)
+    u = torch.tensor(w.u0, device=DEV)
+    for alpha, s, ec, ratio in ((100.0, 1.0, 3, 1.0), (10.0, 2.0, 1, 0.25)):
+        got = ctx.fr_modal_filter(u.clone(), alpha, s, ec, ratio, which).cpu().numpy()
+        sel = {0: None, 1: d.imp_idx, 2: d.ex_idx}[which]
+        ref = apply_filter(w.u0, w.p, alpha, s, ec, ratio, elements=sel)
+        assert _rel(got, ref) < 1e-13
+    with pytest.raises(pkg.HfrError):
+        ctx.fr_modal_filter(u, -1.0, 1.0, 3)
