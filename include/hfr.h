@@ -51,7 +51,7 @@ enum fr_status {
   FR_ERR_DIVERGED = 5,      /* non-finite residual */
   FR_ERR_TIMEOUT = 6,
   FR_ERR_OOM = 7,
-  FR_ERR_UNSUPPORTED = 8    /* configuration outside what this build implements */
+  FR_ERR_UNSUPPORTED = 8    /* configuration outside what the library implements */
 };
 
 /* FR_PHYS_EDAC: entropically damped artificial compressibility (Appendix A), u = (P, v_x, v_y),
