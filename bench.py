@@ -228,6 +228,54 @@ def time_e2e(pkg, torch, ctx, w, steps, dev):
     return float(np.mean(times)), bi, bo
 
 
+def uneven_condense(pkg, torch, dev, n_elem=40000, steps=3):
+    """Condensation of a seeded batch of Navier-Stokes element blocks of uneven degree (p drawn
+    uniformly from 2..5: blocks 36/48, 64/64, 100/80, 144/96) in one persistent launch
+    (hfr_condense_uneven, FP32), against the same kernel launched once per degree class.  Synthetic
+    blocks A = 4 I + N(0,1)/sqrt(nA), B, C, D, r, s ~ N(0, 1), generated on the device."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(2024)
+    ps = torch.randint(2, 6, (n_elem,), generator=g, device=dev).cpu().tolist()
+    shapes = [(4 * (p + 1) ** 2, 16 * (p + 1)) for p in ps]
+
+    def make(shp):
+        nA = [a for a, _ in shp]
+        nT = [t for _, t in shp]
+        A = torch.cat([(4.0 * torch.eye(a, device=dev) + torch.randn(a, a, generator=g, device=dev) / a ** 0.5).reshape(-1)
+                       for a in nA]).float()
+        sb = sum(a * t for a, t in shp)
+        sd = sum(t * t for t in nT)
+        B = torch.randn(sb, generator=g, device=dev)
+        C = torch.randn(sb, generator=g, device=dev)
+        D = torch.randn(sd, generator=g, device=dev)
+        r = torch.randn(sum(nA), generator=g, device=dev, dtype=torch.float64)
+        s = torch.randn(sum(nT), generator=g, device=dev, dtype=torch.float64)
+        return nA, nT, (A, B, C, D, r, s)
+
+    def timed(args_list):
+        for a in args_list:  # warm-up
+            pkg.hfr_condense_uneven(a[0], a[1], *a[2], precision=pkg.FR_PREC_FP32)
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            for a in args_list:
+                pkg.hfr_condense_uneven(a[0], a[1], *a[2], precision=pkg.FR_PREC_FP32)
+            torch.cuda.synchronize()
+            best = min(best, (time.perf_counter() - t0) * 1e3)
+        return best
+
+    whole = make(shapes)
+    ms_one = timed([whole])
+    per_class = [make([sh for sh in shapes if sh == c]) for c in sorted(set(shapes))]
+    ms_cls = timed(per_class)
+    flop = sum(2.0 * a ** 3 + 2.0 * a * a * (t + 1) + 2.0 * t * a * (t + 1) for a, t in shapes)
+    return {"elements": n_elem, "degrees": "p uniform in 2..5 (seed 2024)", "ms_one_launch": ms_one,
+            "ms_per_class_launches": ms_cls, "gflops_one_launch": flop / (ms_one * 1e-3) / 1e9,
+            "note": "wall time of the call (host shape table, stream-ordered work buffer, one kernel, "
+                    "synchronise); FP32 shared-memory Gauss-Jordan + products"}
+
+
 def cpu_baseline(workload="vortex256"):
     """The FP64 oracle, as it stands, on a bounded sample of the same workload: the stage-1
     Newton solve of the same vortex on a PATCH x PATCH periodic patch at the workload's element
@@ -362,6 +410,7 @@ def main():
     ap.add_argument("--paths", default="both", choices=["both", "mixed", "fp64"],
                     help="profiling aid: time only one precision path")
     ap.add_argument("--no-e2e", action="store_true", help="profiling aid: skip the host-buffer e2e leg")
+    ap.add_argument("--no-uneven", action="store_true", help="skip the uneven-degree condensation leg")
     ap.add_argument("--no-autotune", action="store_true",
                     help="profiling aid: keep the default kernel forms (timings under a profiler would mislead the tuner)")
     args = ap.parse_args()
@@ -470,6 +519,11 @@ def main():
         "clocks": clocks,
         "peaks_source": peak_src,
     }
+    if not args.no_uneven:
+        try:
+            line["uneven_condense"] = uneven_condense(pkg, torch, dev)
+        except Exception as exc:  # reported, never fatal
+            line["uneven_condense"] = {"error": str(exc)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline(args.workload)

@@ -216,6 +216,24 @@ int imex_stage(fr_ctx* ctx, int stage, double dt, const double* u_n, double* u_s
                double* R_hist, double newton_tol, int newton_maxit, double gmres_rtol, int gmres_maxit,
                int refine, fr_stage_stats* stats /* host, nullable */);
 
+/* Condensation of elements of uneven block shapes (e.g. several polynomial degrees) in one
+ * persistent launch (Sec. 3.2; batching has no counterpart in the paper).  Element k has blocks of
+ * nA[k] x nA[k] (A), nA[k] x nT[k] (B), nT[k] x nA[k] (C), nT[k] x nT[k] (D), each row-major,
+ * packed element after element in each array (element k's A starts after sum_{j<k} nA[j]^2
+ * values, its B and C after sum nA[j] nT[j], its D after sum nT[j]^2, its r after sum nA[j], its
+ * s after sum nT[j]); outputs packed the same way: LU (((PA)^{-1})^T, A-sized), piv (nA-sized),
+ * XB (B-sized), xr (nA-sized), S (D-sized), t (nT-sized).  nA, nT: HOST arrays; every other
+ * array a caller-owned DEVICE buffer in the block precision (r, s, xr, t FP64); status: 2 device
+ * ints of scratch.  The CTAs walk the elements from the most to the least expensive (shared-memory
+ * Gauss-Jordan with partial pivoting, S = D - C X_B, t = s - C x_r).  A stream-ordered work
+ * buffer of 28 bytes per element is allocated and freed inside; the call synchronises the stream.
+ * Returns FR_OK, FR_ERR_SINGULAR (*failed_element: an element with a zero pivot),
+ * FR_ERR_INVALID_ARG (null array, bad precision, a shape whose working set exceeds the 227 KB of
+ * shared memory: FP32 up to (144, 96), FP64 up to (100, 80)) or FR_ERR_CUDA. */
+int hfr_condense_uneven(int nelem, const int* nA, const int* nT, int precision, const void* A, const void* B,
+                        const void* C, const void* D, const double* r, const double* s, void* LU, int* piv, void* XB,
+                        double* xr, void* S, double* t, int* status, void* stream, int* failed_element);
+
 /* Modal filter of Appendix B, in place on u (device, nelem x ns x nv): on every element of the
  * selection (which: 0 all, 1 implicit, 2 explicit) and every variable, u <- F u with
  * F = V Lambda* V^{-1}, V the tensor-product orthonormal Legendre basis at the solution points,

@@ -52,6 +52,7 @@ ABI_SYMBOLS = [
     "hfr_condense_set_mode",
     "hfr_condense_get_mode",
     "fr_modal_filter",
+    "hfr_condense_uneven",
     "hfr_autotune",
     "imex_stage_set_graph",
     "imex_stage_get_graph",
@@ -178,6 +179,8 @@ def load_library(path: str = LIB_PATH):
     lib.hfr_gmres_get_mode.argtypes = [vp]
     lib.hfr_condense_set_mode.argtypes = [vp, ctypes.c_int]
     lib.hfr_condense_get_mode.argtypes = [vp]
+    lib.hfr_condense_uneven.argtypes = [ctypes.c_int, ip, ip, ctypes.c_int, dp, dp, dp, dp, dp, dp, dp, ip, dp, dp, dp,
+                                        dp, ip, vp, ip]
     lib.fr_modal_filter.argtypes = [vp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int]
     lib.hfr_autotune.argtypes = [vp, dp, dp, dp, ctypes.c_double, ctypes.POINTER(fr_tune_report)]
     lib.imex_stage_set_graph.argtypes = [vp, ctypes.c_int]
@@ -226,6 +229,38 @@ def hfr_condense_noalloc(A, B, C, D, r, s, XB, xr, S, t, precision=FR_PREC_FP64,
     st = stream if stream is not None else torch.cuda.current_stream()
     return lib.hfr_condense_noalloc(E, nA, nT, int(precision), _ptr(A), _ptr(B), _ptr(C), _ptr(D), _ptr(r), _ptr(s),
                                     _ptr(XB), _ptr(xr), _ptr(S), _ptr(t), ctypes.c_void_p(st.cuda_stream))
+
+
+def hfr_condense_uneven(nA, nT, A, B, C, D, r, s, precision=FR_PREC_FP32, stream=None):
+    """Condensation of elements of uneven shapes in one launch (see include/hfr.h).  nA, nT:
+    sequences of ints; A, B, C, D: packed 1-D device tensors of the block precision; r, s: packed
+    FP64.  Returns the packed outputs {LU, piv, XB, xr, S, t}; raises HfrError on failure."""
+    import torch
+
+    lib = load_library()
+    n = len(nA)
+    na = (ctypes.c_int * n)(*[int(x) for x in nA])
+    nt = (ctypes.c_int * n)(*[int(x) for x in nT])
+    sa = sum(int(x) * int(x) for x in nA)
+    sb = sum(int(x) * int(y) for x, y in zip(nA, nT))
+    sd = sum(int(y) * int(y) for y in nT)
+    dev, dt = A.device, A.dtype
+    out = {"LU": torch.empty(sa, dtype=dt, device=dev), "piv": torch.empty(sum(nA), dtype=torch.int32, device=dev),
+           "XB": torch.empty(sb, dtype=dt, device=dev), "xr": torch.empty(sum(nA), dtype=torch.float64, device=dev),
+           "S": torch.empty(sd, dtype=dt, device=dev), "t": torch.empty(sum(nT), dtype=torch.float64, device=dev)}
+    status = torch.zeros(2, dtype=torch.int32, device=dev)
+    failed = ctypes.c_int(-1)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib.hfr_condense_uneven(n, na, nt, int(precision), _ptr(A), _ptr(B), _ptr(C), _ptr(D), _ptr(r), _ptr(s),
+                                 _ptr(out["LU"]), ctypes.cast(_ptr(out["piv"]), ctypes.POINTER(ctypes.c_int)),
+                                 _ptr(out["XB"]), _ptr(out["xr"]), _ptr(out["S"]), _ptr(out["t"]),
+                                 ctypes.cast(_ptr(status), ctypes.POINTER(ctypes.c_int)),
+                                 ctypes.c_void_p(st.cuda_stream), ctypes.byref(failed))
+    if rc != 0:
+        err = HfrError(rc)
+        err.failed_element = failed.value
+        raise err
+    return out
 
 
 def fr_barrier_selftest(nblocks, absent_block=-1, rounds=4, timeout_s=0.05, stream=None):

@@ -1176,6 +1176,37 @@ extern "C" int fr_modal_filter(fr_ctx* ctx, double* u, double alpha, double s, i
   return FR_OK;
 }
 
+extern "C" int hfr_condense_uneven(int nelem, const int* nA, const int* nT, int precision, const void* A, const void* B,
+                                   const void* C, const void* D, const double* r, const double* s, void* LU, int* piv,
+                                   void* XB, double* xr, void* S, double* t, int* status, void* stream,
+                                   int* failed_element) {
+  if (failed_element) *failed_element = -1;
+  if (nelem < 0 || (nelem > 0 && (!nA || !nT || !A || !B || !C || !D || !r || !s || !LU || !piv || !XB || !xr || !S ||
+                                  !t || !status)) ||
+      (precision != FR_PREC_FP64 && precision != FR_PREC_FP32))
+    return FR_ERR_INVALID_ARG;
+  if (nelem == 0) return FR_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int init[2] = {0, 0x7fffffff};
+  if (cudaMemcpyAsync(status, init, sizeof(init), cudaMemcpyHostToDevice, st) != cudaSuccess) return FR_ERR_CUDA;
+  const cudaError_t e = launch_condense_uneven(precision == FR_PREC_FP64 ? 8 : 4, nelem, nA, nT, A, B, C, D, r, s, LU,
+                                               piv, XB, xr, S, t, status, st);
+  if (e == cudaErrorInvalidValue) {
+    cudaGetLastError();
+    return FR_ERR_INVALID_ARG;
+  }
+  if (e != cudaSuccess) return FR_ERR_CUDA;
+  int hs[2] = {0, 0};
+  if (cudaMemcpyAsync(hs, status, sizeof(hs), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return FR_ERR_CUDA;
+  if (hs[0] & DEV_ERR_SINGULAR) {
+    if (failed_element) *failed_element = hs[1];
+    return FR_ERR_SINGULAR;
+  }
+  return FR_OK;
+}
+
 extern "C" int fr_barrier_selftest(int nblocks, int absent_block, int rounds, double timeout_s,
                                    int* barriers_passed, void* stream) {
   if (!barriers_passed || !(timeout_s > 0.0) || timeout_s > 10.0) return FR_ERR_INVALID_ARG;

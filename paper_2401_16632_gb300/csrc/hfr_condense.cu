@@ -13,6 +13,9 @@
 //
 // Outputs per element: AinvT = ((PA)^{-1})^T (column c contiguous), piv, X_B, x_r, S, t.
 // T = double (plain path) or float (mixed path).
+#include <algorithm>
+#include <vector>
+
 #include "hfr_internal.h"
 #include "hfr_tc.cuh"
 
@@ -1802,10 +1805,26 @@ static cudaError_t cond_two_kernel(const CondArgs& a, cudaStream_t st, int part)
 // in shared memory.  Used where the register tile does not fit (e.g. FP64 with nA >= 100).
 constexpr int GJS_THREADS = 256;
 
+// One element's blocks and outputs (row-major, the layouts of CondArgs) for the shared-memory
+// condensation: used by the uniform launch (fixed strides) and by the uneven-shape launch (offsets).
 template <typename T>
-__global__ void __launch_bounds__(GJS_THREADS) k_condense_smem(const __grid_constant__ CondArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nA = a.nA, nT = a.nT, nc = nA + nT + 1;
+struct CondElem {
+  int nA, nT, id;
+  const T *A, *B, *C, *D;
+  const double *r, *s;
+  T* LU;  // ((PA)^{-1})^T
+  int* piv;
+  T* XB;
+  double* xr;
+  T* S;
+  double* t;
+};
+
+// Gauss-Jordan on [A | B | r] in shared memory with partial pivoting (rows not exchanged), then
+// S = D - C X_B and t = s - C x_r.  Ends with a CTA barrier, so the caller may reuse the memory.
+template <typename T>
+__device__ void condense_smem_elem(const CondElem<T>& e, unsigned char* smem_raw, int* status) {
+  const int nA = e.nA, nT = e.nT, nc = nA + nT + 1;
   const int big = nA > nT ? nA : nT;
   T* M = reinterpret_cast<T*>(smem_raw);  // nA x nc, physical rows
   T* W = M + (size_t)nA * nc;             // big x nA
@@ -1815,12 +1834,10 @@ __global__ void __launch_bounds__(GJS_THREADS) k_condense_smem(const __grid_cons
   unsigned char* used = reinterpret_cast<unsigned char*>(ipiv + nA);
   __shared__ int s_p;
   __shared__ int s_bad;
-  const int k = blockIdx.x, tid = threadIdx.x;
-  const T* gA = reinterpret_cast<const T*>(a.A) + (size_t)k * nA * nA;
-  const T* gB = reinterpret_cast<const T*>(a.B) + (size_t)k * nA * nT;
+  const int tid = threadIdx.x;
   for (int i = tid; i < nA * nc; i += GJS_THREADS) {
     const int r = i / nc, j = i % nc;
-    M[i] = j < nA ? gA[(size_t)r * nA + j] : (j < nA + nT ? gB[(size_t)r * nT + (j - nA)] : T(a.r[(size_t)k * nA + r]));
+    M[i] = j < nA ? e.A[(size_t)r * nA + j] : (j < nA + nT ? e.B[(size_t)r * nT + (j - nA)] : T(e.r[r]));
   }
   for (int i = tid; i < nA; i += GJS_THREADS) used[i] = 0;
   if (tid == 0) s_bad = 0;
@@ -1844,7 +1861,7 @@ __global__ void __launch_bounds__(GJS_THREADS) k_condense_smem(const __grid_cons
         s_p = bi;
         used[bi] = 1;
         ipiv[bi] = c;
-        a.piv[(size_t)k * nA + c] = bi;
+        e.piv[c] = bi;
         if (!(best > T(0))) s_bad = 1;
       }
     }
@@ -1865,37 +1882,183 @@ __global__ void __launch_bounds__(GJS_THREADS) k_condense_smem(const __grid_cons
     __syncthreads();
   }
   if (tid == 0 && s_bad) {
-    atomicOr(a.status, DEV_ERR_SINGULAR);
-    atomicMin(a.status + 1, k);
+    atomicOr(status, DEV_ERR_SINGULAR);
+    atomicMin(status + 1, e.id);
   }
-  T* gInv = reinterpret_cast<T*>(a.LU) + (size_t)k * nA * nA;
-  T* gXB = reinterpret_cast<T*>(a.XB) + (size_t)k * nA * nT;
   for (int i = tid; i < nA * nc; i += GJS_THREADS) {
     const int r = i / nc, j = i % nc;
     const int lr = ipiv[r];
     if (j < nA)
-      gInv[(size_t)j * nA + lr] = M[i];
+      e.LU[(size_t)j * nA + lr] = M[i];
     else if (j < nA + nT)
-      gXB[(size_t)lr * nT + (j - nA)] = M[i];
+      e.XB[(size_t)lr * nT + (j - nA)] = M[i];
     else
-      a.xr[(size_t)k * nA + lr] = double(M[i]);
+      e.xr[lr] = double(M[i]);
   }
   // C into W; X rows in logical order are read through the pivot sequence
-  const T* gC = reinterpret_cast<const T*>(a.C) + (size_t)k * nT * nA;
-  const T* gD = reinterpret_cast<const T*>(a.D) + (size_t)k * nT * nT;
-  const int* pv = a.piv + (size_t)k * nA;
-  for (int i = tid; i < nT * nA; i += GJS_THREADS) W[i] = gC[i];
+  for (int i = tid; i < nT * nA; i += GJS_THREADS) W[i] = e.C[i];
   __syncthreads();
-  T* gS = reinterpret_cast<T*>(a.S) + (size_t)k * nT * nT;
   for (int it = tid; it < nT * (nT + 1); it += GJS_THREADS) {
     const int i = it / (nT + 1), j = it % (nT + 1);
     T acc = T(0);
-    for (int l = 0; l < nA; ++l) acc += W[(size_t)i * nA + l] * M[(size_t)pv[l] * nc + nA + j];
+    for (int l = 0; l < nA; ++l) acc += W[(size_t)i * nA + l] * M[(size_t)e.piv[l] * nc + nA + j];
     if (j < nT)
-      gS[(size_t)i * nT + j] = gD[(size_t)i * nT + j] - acc;
+      e.S[(size_t)i * nT + j] = e.D[(size_t)i * nT + j] - acc;
     else
-      a.t[(size_t)k * nT + i] = a.s[(size_t)k * nT + i] - double(acc);
+      e.t[i] = e.s[i] - double(acc);
   }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(GJS_THREADS) k_condense_smem(const __grid_constant__ CondArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int k = blockIdx.x, nA = a.nA, nT = a.nT;
+  CondElem<T> e;
+  e.nA = nA;
+  e.nT = nT;
+  e.id = k;
+  e.A = reinterpret_cast<const T*>(a.A) + (size_t)k * nA * nA;
+  e.B = reinterpret_cast<const T*>(a.B) + (size_t)k * nA * nT;
+  e.C = reinterpret_cast<const T*>(a.C) + (size_t)k * nT * nA;
+  e.D = reinterpret_cast<const T*>(a.D) + (size_t)k * nT * nT;
+  e.r = a.r + (size_t)k * nA;
+  e.s = a.s + (size_t)k * nT;
+  e.LU = reinterpret_cast<T*>(a.LU) + (size_t)k * nA * nA;
+  e.piv = a.piv + (size_t)k * nA;
+  e.XB = reinterpret_cast<T*>(a.XB) + (size_t)k * nA * nT;
+  e.xr = a.xr + (size_t)k * nA;
+  e.S = reinterpret_cast<T*>(a.S) + (size_t)k * nT * nT;
+  e.t = a.t + (size_t)k * nT;
+  condense_smem_elem<T>(e, smem_raw, a.status);
+}
+
+// Elements of uneven block shapes (e.g. several polynomial degrees) condensed in one persistent
+// launch: the CTAs walk a work list ordered by decreasing cost; element w of the list has shape
+// shape[2 e], shape[2 e + 1] and its blocks at the offsets off[5 e ..] into the packed arrays
+// (A-sized: A, LU; B-sized: B, C, X_B; D-sized: D, S; nA-sized: r, x_r, piv; nT-sized: s, t).
+struct UnevenArgs {
+  int n;
+  const int* order;
+  const int* shape;
+  const long long* off;
+  const void *A, *B, *C, *D;
+  const double *r, *s;
+  void* LU;
+  int* piv;
+  void* XB;
+  double* xr;
+  void* S;
+  double* t;
+  int* status;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(GJS_THREADS) k_condense_uneven(const __grid_constant__ UnevenArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int w = blockIdx.x; w < a.n; w += gridDim.x) {
+    const int k = a.order[w];
+    const long long* o = a.off + 5 * (size_t)k;
+    CondElem<T> e;
+    e.nA = a.shape[2 * k];
+    e.nT = a.shape[2 * k + 1];
+    e.id = k;
+    e.A = reinterpret_cast<const T*>(a.A) + o[0];
+    e.LU = reinterpret_cast<T*>(a.LU) + o[0];
+    e.B = reinterpret_cast<const T*>(a.B) + o[1];
+    e.C = reinterpret_cast<const T*>(a.C) + o[1];
+    e.XB = reinterpret_cast<T*>(a.XB) + o[1];
+    e.D = reinterpret_cast<const T*>(a.D) + o[2];
+    e.S = reinterpret_cast<T*>(a.S) + o[2];
+    e.r = a.r + o[3];
+    e.xr = a.xr + o[3];
+    e.piv = a.piv + o[3];
+    e.s = a.s + o[4];
+    e.t = a.t + o[4];
+    condense_smem_elem<T>(e, smem_raw, a.status);
+  }
+}
+
+static size_t smem_elem_bytes(size_t tb, int nA, int nT) {
+  const int nc = nA + nT + 1, big = nA > nT ? nA : nT;
+  return tb * ((size_t)nA * nc + (size_t)big * nA + nc + nA) + sizeof(int) * nA + nA;
+}
+
+cudaError_t launch_condense_uneven(int prec_bytes, int n, const int* nA, const int* nT, const void* A, const void* B,
+                                   const void* C, const void* D, const double* r, const double* s, void* LU, int* piv,
+                                   void* XB, double* xr, void* S, double* t, int* status, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  std::vector<int> shape(2 * (size_t)n), order(n);
+  std::vector<long long> off(5 * (size_t)n);
+  long long oa = 0, ob = 0, od = 0, ova = 0, ovt = 0;
+  size_t smem = 0;
+  for (int k = 0; k < n; ++k) {
+    if (nA[k] < 1 || nT[k] < 1) return cudaErrorInvalidValue;
+    shape[2 * k] = nA[k];
+    shape[2 * k + 1] = nT[k];
+    off[5 * k + 0] = oa;
+    off[5 * k + 1] = ob;
+    off[5 * k + 2] = od;
+    off[5 * k + 3] = ova;
+    off[5 * k + 4] = ovt;
+    oa += (long long)nA[k] * nA[k];
+    ob += (long long)nA[k] * nT[k];
+    od += (long long)nT[k] * nT[k];
+    ova += nA[k];
+    ovt += nT[k];
+    const size_t sb = smem_elem_bytes(prec_bytes, nA[k], nT[k]);
+    smem = sb > smem ? sb : smem;
+    order[k] = k;
+  }
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  // most expensive first (Gauss-Jordan ~ nA^2 (nA + nT), products ~ nT^2 nA)
+  auto cost = [&](int k) {
+    const double a = nA[k], b = nT[k];
+    return a * a * (a + b) + b * b * a;
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+  void* dbuf = nullptr;
+  const size_t bytes_i = sizeof(int) * (3 * (size_t)n), bytes_o = sizeof(long long) * off.size();
+  cudaError_t e = cudaMallocAsync(&dbuf, bytes_o + bytes_i, st);
+  if (e != cudaSuccess) return e;
+  long long* d_off = reinterpret_cast<long long*>(dbuf);
+  int* d_order = reinterpret_cast<int*>(d_off + off.size());
+  int* d_shape = d_order + n;
+  UnevenArgs ua{n, d_order, d_shape, d_off, A, B, C, D, r, s, LU, piv, XB, xr, S, t, status};
+  int dev = 0, nsm = 0, occ = 0;
+  if ((e = cudaMemcpyAsync(d_off, off.data(), bytes_o, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_shape, shape.data(), sizeof(int) * 2 * n, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    goto done;
+  if (prec_bytes == 8) {
+    if ((e = cudaFuncSetAttribute(k_condense_uneven<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+      goto done;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_condense_uneven<double>, GJS_THREADS, smem);
+  } else {
+    if ((e = cudaFuncSetAttribute(k_condense_uneven<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+      goto done;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_condense_uneven<float>, GJS_THREADS, smem);
+  }
+  if (e != cudaSuccess) goto done;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) goto done;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) goto done;
+  {
+    int grid = nsm * (occ < 1 ? 1 : occ);
+    grid = n < grid ? n : grid;
+    if (prec_bytes == 8)
+      (hfr::count_launch(), k_condense_uneven<double><<<grid, GJS_THREADS, smem, st>>>(ua));
+    else
+      (hfr::count_launch(), k_condense_uneven<float><<<grid, GJS_THREADS, smem, st>>>(ua));
+    e = cudaGetLastError();
+  }
+done:
+  // the host vectors must outlive their copies; the work buffer is freed in stream order
+  cudaStreamSynchronize(st);
+  cudaFreeAsync(dbuf, st);
+  cudaStreamSynchronize(st);
+  return e;
 }
 
 // y = A^{-1} b = (PA)^{-1} (P b), in place on b.  One warp per element; lane owns rows

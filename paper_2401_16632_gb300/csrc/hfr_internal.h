@@ -94,6 +94,12 @@ cudaError_t launch_condense(int prec_bytes, const CondArgs& a, cudaStream_t st);
 // 1 = the products X = A^{-1}[B | r], S = D - C X_B of the two-kernel FP32 path (else nothing)
 cudaError_t launch_condense_part(int prec_bytes, const CondArgs& a, cudaStream_t st, int part);
 
+// Elements of uneven shapes (nA[k], nT[k], host arrays) condensed in one persistent launch with
+// the shared-memory Gauss-Jordan kernel; blocks packed element after element (see hfr.h)
+cudaError_t launch_condense_uneven(int prec_bytes, int n, const int* nA, const int* nT, const void* A, const void* B,
+                                   const void* C, const void* D, const double* r, const double* s, void* LU, int* piv,
+                                   void* XB, double* xr, void* S, double* t, int* status, cudaStream_t st);
+
 // x = A^{-1} b with the stored factorisation (LU + interchanges or in-place inverse, as chosen
 // by condense_uses_lu), in place on b (Eim x nA, FP64 vectors).
 bool condense_uses_lu(int prec_bytes, int nA, int nT);
