@@ -819,13 +819,10 @@ __global__ void __launch_bounds__(128, 4) k_inverse_tc(const __grid_constant__ C
         if (s < ns) {
           const int b = s & 1;
           const uint4 kq = *reinterpret_cast<const uint4*>(s_key + b * 4);
-          unsigned km = kq.x;
-          int wb = 0;
-          if (kq.y > km) { km = kq.y; wb = 1; }
-          if (kq.z > km) { km = kq.z; wb = 2; }
-          if (kq.w > km) { km = kq.w; wb = 3; }
+          const unsigned km = max(max(kq.x, kq.y), max(kq.z, kq.w));
           const int r = (int)(MASK - (km & MASK));
-          if ((km & ~MASK) == 0u) bad = true;
+          const int wb = r >> 5;                      // the warp that holds row r
+          if ((km & 0x7F800000u) == 0u) bad = true;  // |pivot| below FLT_MIN (or no pivot left)
           float prow[16];
 #pragma unroll
           for (int u = 0; u < 16; u += 4) {
@@ -833,7 +830,7 @@ __global__ void __launch_bounds__(128, 4) k_inverse_tc(const __grid_constant__ C
             prow[u] = x.x; prow[u + 1] = x.y; prow[u + 2] = x.z; prow[u + 3] = x.w;
           }
           const float pv = prow[s];
-          const float pinv = pv != 0.f ? __frcp_rn(pv) : 0.f;
+          const float pinv = pv != 0.f ? rcp_approx(pv) : 0.f;  // 1-ulp hardware reciprocal
           if (row == r) {
 #pragma unroll
             for (int u = 0; u < 16; ++u) v[u] = prow[u] * pinv;
@@ -846,7 +843,6 @@ __global__ void __launch_bounds__(128, 4) k_inverse_tc(const __grid_constant__ C
             for (int u = 0; u < 16; ++u) v[u] -= g * prow[u];
             v[s] = -g;
           }
-          if (t == 0) a.piv[(size_t)k * NA + 16 * p + s] = r;
           if (s + 1 < ns) {
             const unsigned key = used ? 0u : ((__float_as_uint(fabsf(v[s + 1])) & ~MASK) | (MASK - (unsigned)row));
             const unsigned wk = __reduce_max_sync(0xffffffffu, key);
@@ -901,13 +897,13 @@ __global__ void __launch_bounds__(128, 4) k_inverse_tc(const __grid_constant__ C
       tmem_st_wait();
       __syncthreads();
       // ---- row buffer -> P operand (rows = matrix columns j, K = pivot index), 3xTF32 split
-      for (int e = t; e < NC * 16; e += Sh::THREADS) {
-        const int sl = e & 3, jl = (e >> 2) & 7, rest = e >> 5;
-        const int sidx = 4 * (rest & 3) + sl, j = 8 * (rest >> 2) + jl;
-        float h, l;
-        split_tf32(rowbuf[sidx * RB + j], h, l);
-        *reinterpret_cast<float*>(Phi + kmajor_offset(j, sidx, Sh::SBO)) = h;
-        *reinterpret_cast<float*>(Plo + kmajor_offset(j, sidx, Sh::SBO)) = l;
+      for (int e = t; e < NC * 4; e += Sh::THREADS) {
+        const int j = e % NC, sc = e / NC;  // lanes along j: conflict-free reads, 16-byte stores
+        float hs[4], ls[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) split_tf32(rowbuf[(4 * sc + q) * RB + j], hs[q], ls[q]);
+        *reinterpret_cast<float4*>(Phi + kmajor_offset(j, 4 * sc, Sh::SBO)) = make_float4(hs[0], hs[1], hs[2], hs[3]);
+        *reinterpret_cast<float4*>(Plo + kmajor_offset(j, 4 * sc, Sh::SBO)) = make_float4(ls[0], ls[1], ls[2], ls[3]);
       }
       fence_proxy_async();
       fence_before_sync();
@@ -938,6 +934,8 @@ __global__ void __launch_bounds__(128, 4) k_inverse_tc(const __grid_constant__ C
       atomicOr(a.status, DEV_ERR_SINGULAR);
       atomicMin(a.status + 1, k);
     }
+    // pivot row of each step, written once by its owner
+    if (row < NA && mystep >= 0) a.piv[(size_t)k * NA + mystep] = row;
     // ---- output: Wt[c][c'] = M[piv[c']][c], through the row buffer 32 columns at a time
     float* gWt = reinterpret_cast<float*>(a.LU) + (size_t)k * NA * NA;
 #pragma unroll 1

@@ -148,5 +148,14 @@ __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
   lo = x - hi;
 }
 
+// reciprocal by the hardware approximation (rcp.approx.ftz.f32: within 1 ulp, subnormal inputs
+// flushed to zero): one instruction on the Gauss-Jordan pivot chain instead of the correctly
+// rounded sequence; callers treat pivots below FLT_MIN as singular
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 }  // namespace tc
 }  // namespace hfr
