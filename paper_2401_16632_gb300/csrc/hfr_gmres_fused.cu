@@ -153,13 +153,120 @@ __device__ __forceinline__ T pg_scatter16(T (&acc)[16], int lane) {
   return acc[0] + __shfl_xor_sync(0xffffffffu, acc[0], 1);
 }
 
+// Warp reduce-scatter of 8 per-lane values: afterwards lane l holds the warp sum of value l >> 2.
+template <typename T>
+__device__ __forceinline__ T pg_scatter8(T (&acc)[8], int lane) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const bool up = lane & 16;
+    const T send = up ? acc[q] : acc[q + 4];
+    const T keep = up ? acc[q + 4] : acc[q];
+    acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const bool up = lane & 8;
+    const T send = up ? acc[q] : acc[q + 2];
+    const T keep = up ? acc[q + 2] : acc[q];
+    acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  {
+    const bool up = lane & 4;
+    const T send = up ? acc[0] : acc[1];
+    const T keep = up ? acc[1] : acc[0];
+    acc[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 2);
+  return acc[0] + __shfl_xor_sync(0xffffffffu, acc[0], 1);
+}
+
+// 16-byte vector of W values of the basis (W = 16 / sizeof(T)), default (L1-allocating) loads
+template <typename T, int W>
+struct PGV {
+  T v[W];
+};
+template <typename T, int W>
+__device__ __forceinline__ PGV<T, W> pg_ldv(const T* p) {
+  PGV<T, W> r;
+  if constexpr (sizeof(T) == 4 && W == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    r.v[0] = q.x;
+    r.v[1] = q.y;
+    r.v[2] = q.z;
+    r.v[3] = q.w;
+  } else if constexpr (sizeof(T) == 8 && W == 2) {
+    const double2 q = *reinterpret_cast<const double2*>(p);
+    r.v[0] = q.x;
+    r.v[1] = q.y;
+  } else {
+#pragma unroll
+    for (int e = 0; e < W; ++e) r.v[e] = p[e];
+  }
+  return r;
+}
+// basis vectors per step of the vector dot pass (two W-vectors of each in flight per thread)
+constexpr int PG_VC = 4;
+// vector width of the dot pass: 16 bytes when face blocks (hence every CTA's range and the vector
+// length) are whole vectors, else scalar
+template <typename T, int BS>
+__host__ __device__ constexpr int pg_basis_width() {
+  return BS % (16 / (int)sizeof(T)) == 0 ? 16 / (int)sizeof(T) : 1;
+}
+
 // CTA partial of V_i . w over this CTA's entries [x0, x1), i < nd, written to
 // partial[i * gridDim.x + blockIdx.x].  Each thread visits the entries x0 + tid + PG_THREADS u,
 // the same ones the vector updates of this file give it, so it only re-reads its own writes.
-template <typename T>
+// With W > 1 the thread visits the W-vectors x0 / W + tid + PG_THREADS u instead (two W-vectors of
+// w and of PG_VC basis vectors per step, 2 PG_VC + 2 loads of 16 bytes in flight); w's entries are
+// then not the thread's own writes, so the caller puts a block barrier between the update of w and
+// this pass.
+template <typename T, int W = 1>
 __device__ void pg_block_dots(PGShared<T>& sh, const T* V, size_t n, int nd, const T* w, size_t x0, size_t x1,
                               T* partial) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if constexpr (W > 1) {
+    const size_t g0 = x0 / W, g1 = x1 / W, nW = n / W;
+    for (int c0 = 0; c0 < nd; c0 += PG_VC) {
+      T acc[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] = T(0);
+      for (size_t ga = g0 + threadIdx.x; ga < g1; ga += 2 * PG_THREADS) {
+        const size_t gb = ga + PG_THREADS;
+        const bool okb = gb < g1;
+        const size_t gbs = okb ? gb : ga;
+        const PGV<T, W> wa = pg_ldv<T, W>(w + ga * W);
+        PGV<T, W> wb = pg_ldv<T, W>(w + gbs * W);
+        if (!okb) {
+#pragma unroll
+          for (int e = 0; e < W; ++e) wb.v[e] = T(0);
+        }
+        PGV<T, W> va[PG_VC], vb[PG_VC];
+#pragma unroll
+        for (int q = 0; q < PG_VC; ++q)
+          if (c0 + q < nd) {
+            va[q] = pg_ldv<T, W>(V + ((size_t)(c0 + q) * nW + ga) * W);
+            vb[q] = pg_ldv<T, W>(V + ((size_t)(c0 + q) * nW + gbs) * W);
+          }
+#pragma unroll
+        for (int q = 0; q < PG_VC; ++q)
+          if (c0 + q < nd) {
+#pragma unroll
+            for (int e = 0; e < W; ++e) acc[q] += va[q].v[e] * wa.v[e] + vb[q].v[e] * wb.v[e];
+          }
+      }
+      const T s = pg_scatter8(acc, lane);
+      const int vi = c0 + (lane >> 2);
+      if ((lane & 3) == 0 && vi < nd) sh.red[vi][wid] = s;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nd; i += PG_THREADS) {
+      T t = T(0);
+#pragma unroll
+      for (int k = 0; k < PG_WARPS; ++k) t += sh.red[i][k];
+      partial[(size_t)i * gridDim.x + blockIdx.x] = t;
+    }
+    return;
+  }
   for (int c0 = 0; c0 < nd; c0 += 16) {
     T acc[16];
 #pragma unroll
@@ -425,8 +532,8 @@ __device__ __forceinline__ void pg_prow(const T* P, int f, int r, T (&row)[BS]) 
   }
 }
 
-// z = P^{-1} v_j, one warp per face of this CTA, lane r < BS owns row r.  Warp 0 takes no face:
-// its lane 0 updates the Givens rotations meanwhile.
+// z = P^{-1} v_j, one warp per face of this CTA (two faces per step), lane r < BS owns row r.
+// Warp 0 takes no face: its lane 0 updates the Givens rotations meanwhile.
 template <typename T, int BS>
 __device__ void pg_precond(const FusedArgs& a, const T* vj, int fb0, int fb1) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -434,15 +541,27 @@ __device__ void pg_precond(const FusedArgs& a, const T* vj, int fb0, int fb1) {
   const T* P = reinterpret_cast<const T*>(a.Pinv);
   T* z = reinterpret_cast<T*>(a.z);
   const int r = lane < BS ? lane : 0;
-  for (int f = fb0 + wid - 1; f < fb1; f += PG_WARPS - 1) {
-    const size_t ix = (size_t)f * BS + r;
+  constexpr int NW = PG_WARPS - 1;
+  for (int f = fb0 + wid - 1; f < fb1; f += 2 * NW) {
+    // two faces per step: both blocks' loads in flight together
+    const int f2 = f + NW;
+    const bool two = f2 < fb1;
+    const size_t ix = (size_t)f * BS + r, ix2 = (size_t)(two ? f2 : f) * BS + r;
     const T v = lane < BS ? vj[ix] : T(0);
-    T row[BS];
+    const T v2 = lane < BS ? vj[ix2] : T(0);
+    T row[BS], row2[BS];
     pg_prow<T, BS>(P, f, r, row);
-    T acc = T(0);
+    pg_prow<T, BS>(P, two ? f2 : f, r, row2);
+    T acc = T(0), acc2 = T(0);
 #pragma unroll
-    for (int c = 0; c < BS; ++c) acc += row[c] * __shfl_sync(0xffffffffu, v, c);
-    if (lane < BS) z[ix] = acc;
+    for (int c = 0; c < BS; ++c) {
+      acc += row[c] * __shfl_sync(0xffffffffu, v, c);
+      acc2 += row2[c] * __shfl_sync(0xffffffffu, v2, c);
+    }
+    if (lane < BS) {
+      z[ix] = acc;
+      if (two) z[ix2] = acc2;
+    }
   }
 }
 
@@ -573,6 +692,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_gmres_cycle(const __grid_cons
   const int fb0 = (int)((long long)blockIdx.x * F / gridDim.x);
   const int fb1 = (int)((long long)(blockIdx.x + 1) * F / gridDim.x);
   const size_t n = a.n, x0 = (size_t)fb0 * BS, x1 = (size_t)fb1 * BS;
+  constexpr int VWB = pg_basis_width<T, BS>();
   const int tid = threadIdx.x;
   unsigned epoch = 0;
   int par = 0;
@@ -634,7 +754,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_gmres_cycle(const __grid_cons
       pg_matvec<T, NT, BS, false, false>(a, a.z, w, fb0, fb1);
       __syncthreads();
       T* part = partial + par * pstride;
-      pg_block_dots(sh, V, n, j + 1, w, x0, x1, part);
+      pg_block_dots<T, VWB>(sh, V, n, j + 1, w, x0, x1, part);
       if (!pg_sync(sh, a.bar, epoch)) return;
       pg_reduce(sh, j + 1, part);
       par ^= 1;
@@ -645,8 +765,9 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_gmres_cycle(const __grid_cons
       __syncthreads();
       // (C) w' = w - V h, then d = V^T w' and ||w'||^2 (dot j+1: V_{j+1} is w' itself)
       pg_subtract(V, n, sh.cf, j, w, x0, x1);
+      if (VWB > 1) __syncthreads();  // the dot pass visits w in its own (vector) order
       part = partial + par * pstride;
-      pg_block_dots(sh, V, n, j + 2, w, x0, x1, part);
+      pg_block_dots<T, VWB>(sh, V, n, j + 2, w, x0, x1, part);
       if (!pg_sync(sh, a.bar, epoch)) return;
       pg_reduce(sh, j + 2, part);
       par ^= 1;
