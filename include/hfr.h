@@ -148,10 +148,16 @@ int hfr_trace_gmres(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* ite
  * preconditioner at every Newton iterate (exact Newton on the blocks).  FR_JAC_ONCE_PER_STAGE:
  * at the stage's first iterate only; later iterations are chord iterations that reuse the blocks,
  * their factorisation, S_k, X_B and the preconditioner, and recompute only x_r = A^{-1} r,
- * t_k = s - C x_r and t (the paper keeps its Jacobian for many steps; Sec. 5).  Both stop on the
+ * t_k = s - C x_r and t.  FR_JAC_KEEP: the condensation is held across stages and steps (the
+ * paper keeps its Jacobian for 100 steps; Sec. 5, turbulent cylinder) and every Newton iteration
+ * is a chord iteration, except that the first iterate of a stage re-linearises when no
+ * condensation is held, when a_ii dt differs from the held one, or after imex_refresh_jacobian;
+ * hfr_local_jacobian, hfr_condense and hfr_autotune drop the held one.  All policies stop on the
  * same FP64 Newton residual test.  FR_ERR_INVALID_ARG for another value. */
-enum fr_jacobian_policy { FR_JAC_EVERY_NEWTON = 0, FR_JAC_ONCE_PER_STAGE = 1 };
+enum fr_jacobian_policy { FR_JAC_EVERY_NEWTON = 0, FR_JAC_ONCE_PER_STAGE = 1, FR_JAC_KEEP = 2 };
 int imex_set_jacobian_policy(fr_ctx* ctx, int policy);
+/* FR_JAC_KEEP: re-linearise at the next stage's first Newton iterate.  FR_OK. */
+int imex_refresh_jacobian(fr_ctx* ctx);
 
 /* How hfr_trace_gmres (and imex_stage) run a restart cycle.  FR_GMRES_FUSED (the default where
  * available): the whole cycle -- preconditioner, mat-vecs, Gram-Schmidt, Givens rotations and the
@@ -215,6 +221,27 @@ int hfr_export(fr_ctx* ctx, int which, void* dst, size_t bytes);
 int imex_stage(fr_ctx* ctx, int stage, double dt, const double* u_n, double* u_stage, double* uhat,
                double* R_hist, double newton_tol, int newton_maxit, double gmres_rtol, int gmres_maxit,
                int refine, fr_stage_stats* stats /* host, nullable */);
+
+/* Totals of imex_steps. */
+typedef struct fr_steps_stats {
+  int steps;               /* steps completed */
+  int newton_iterations;   /* over all implicit stages */
+  int gmres_iterations;
+  int jacobian_refreshes;  /* linearisations (element blocks + condensation) made */
+  double max_rel_residual; /* largest final ||[h; g]|| / ||[h; g]^0|| of the implicit stages */
+  int converged;           /* 1 when every stage met newton_tol */
+} fr_steps_stats;
+
+/* nsteps whole IMEX steps of size dt (Algorithm 1, all stages and the final combination), in
+ * place: u (nelem x nA) holds u_n on entry and u_{n+nsteps} on return, uhat the traces.  R_hist
+ * ((s + 1) x nelem x nA) and u_stage (nelem x nA) are caller-owned device scratch.  With
+ * FR_JAC_KEEP the held condensation is refreshed at steps 0, refresh_every, 2 refresh_every, ...
+ * (refresh_every <= 0: only when needed, see imex_set_jacobian_policy); other policies ignore it.
+ * Stops at the first failing stage with its status (stats then count the completed steps).
+ * Newton and GMRES arguments as for imex_stage.  Synchronises the stream. */
+int imex_steps(fr_ctx* ctx, int nsteps, double dt, double* u, double* uhat, double* R_hist, double* u_stage,
+               int refresh_every, double newton_tol, int newton_maxit, double gmres_rtol, int gmres_maxit,
+               int refine, fr_steps_stats* stats /* host, nullable */);
 
 /* Condensation of elements of uneven block shapes (e.g. several polynomial degrees) in one
  * persistent launch (Sec. 3.2; batching has no counterpart in the paper).  Element k has blocks of

@@ -30,7 +30,7 @@ FR_PREC_FP64, FR_PREC_FP32 = 0, 1
 FR_TAB_BE, FR_TAB_SDIRK2 = 0, 1
 FR_PHYS_ADVDIFF, FR_PHYS_NAVIER_STOKES, FR_PHYS_EDAC = 0, 1, 2
 FR_GMRES_MULTI, FR_GMRES_FUSED = 0, 1
-FR_JAC_EVERY_NEWTON, FR_JAC_ONCE_PER_STAGE = 0, 1
+FR_JAC_EVERY_NEWTON, FR_JAC_ONCE_PER_STAGE, FR_JAC_KEEP = 0, 1, 2
 FR_CONDENSE_FMA, FR_CONDENSE_TENSOR_PRODUCTS, FR_CONDENSE_TENSOR = 0, 1, 2
 (FR_OK, FR_ERR_INVALID_ARG, FR_ERR_CUDA, FR_ERR_SINGULAR, FR_ERR_NOT_CONVERGED, FR_ERR_DIVERGED, FR_ERR_TIMEOUT,
  FR_ERR_OOM, FR_ERR_UNSUPPORTED) = range(9)
@@ -47,6 +47,7 @@ ABI_SYMBOLS = [
     "hfr_condense",
     "hfr_trace_gmres",
     "imex_set_jacobian_policy",
+    "imex_refresh_jacobian",
     "hfr_gmres_set_mode",
     "hfr_gmres_get_mode",
     "hfr_condense_set_mode",
@@ -60,6 +61,7 @@ ABI_SYMBOLS = [
     "hfr_backsolve",
     "hfr_export",
     "imex_stage",
+    "imex_steps",
     "hfr_initial_trace",
     "fr_profile_enable",
     "fr_profile_read",
@@ -128,6 +130,17 @@ class fr_stage_stats(ctypes.Structure):
     ]
 
 
+class fr_steps_stats(ctypes.Structure):
+    _fields_ = [
+        ("steps", ctypes.c_int),
+        ("newton_iterations", ctypes.c_int),
+        ("gmres_iterations", ctypes.c_int),
+        ("jacobian_refreshes", ctypes.c_int),
+        ("max_rel_residual", ctypes.c_double),
+        ("converged", ctypes.c_int),
+    ]
+
+
 class fr_profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 10), ("count", ctypes.c_longlong * 10)]
 
@@ -175,6 +188,9 @@ def load_library(path: str = LIB_PATH):
     lib.hfr_condense.argtypes = [vp, ctypes.c_int]
     lib.hfr_trace_gmres.argtypes = [vp, dp, ctypes.c_double, ctypes.c_int, ip, ctypes.POINTER(ctypes.c_double)]
     lib.imex_set_jacobian_policy.argtypes = [vp, ctypes.c_int]
+    lib.imex_refresh_jacobian.argtypes = [vp]
+    lib.imex_steps.argtypes = [vp, ctypes.c_int, ctypes.c_double, dp, dp, dp, dp, ctypes.c_int, ctypes.c_double,
+                               ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.POINTER(fr_steps_stats)]
     lib.hfr_gmres_set_mode.argtypes = [vp, ctypes.c_int]
     lib.hfr_gmres_get_mode.argtypes = [vp]
     lib.hfr_condense_set_mode.argtypes = [vp, ctypes.c_int]
@@ -395,6 +411,9 @@ class Context:
     def imex_set_jacobian_policy(self, policy: int):
         self._check(self.lib.imex_set_jacobian_policy(self.h, int(policy)))
 
+    def imex_refresh_jacobian(self):
+        self._check(self.lib.imex_refresh_jacobian(self.h))
+
     def hfr_gmres_set_mode(self, mode: int):
         self._check(self.lib.hfr_gmres_set_mode(self.h, int(mode)))
 
@@ -454,6 +473,20 @@ class Context:
         self._check(rc)
         return {"newton_iterations": st.newton_iterations, "gmres_iterations": st.gmres_iterations,
                 "residual0": st.residual0, "residual": st.residual, "converged": bool(st.converged)}
+
+    def imex_steps(self, nsteps, dt, u, uhat, refresh_every=0, newton_tol=1e-8, newton_maxit=20, gmres_rtol=1e-3,
+                   gmres_maxit=500, refine=0):
+        """nsteps whole IMEX steps in place on u and uhat (C entry imex_steps); returns the totals."""
+        R_hist = self.empty(self.info.nstages + 1, *self.state_shape)
+        u_stage = self.empty(*self.state_shape)
+        st = fr_steps_stats()
+        rc = self.lib.imex_steps(self.h, int(nsteps), float(dt), _ptr(u), _ptr(uhat), _ptr(R_hist), _ptr(u_stage),
+                                 int(refresh_every), float(newton_tol), int(newton_maxit), float(gmres_rtol),
+                                 int(gmres_maxit), int(refine), ctypes.byref(st))
+        self._check(rc)
+        return {"steps": st.steps, "newton_iterations": st.newton_iterations, "gmres_iterations": st.gmres_iterations,
+                "jacobian_refreshes": st.jacobian_refreshes, "max_rel_residual": st.max_rel_residual,
+                "converged": bool(st.converged)}
 
     def fr_profile_enable(self, on=True):
         self._check(self.lib.fr_profile_enable(self.h, 1 if on else 0))

@@ -72,7 +72,12 @@ struct fr_ctx {
   // Krylov
   GmresBuffers gm;
   int gm_mode = 0;          // 0: multi-kernel cycle, 1: one cooperative launch per cycle
-  int jac_policy = 0;       // FR_JAC_EVERY_NEWTON or FR_JAC_ONCE_PER_STAGE
+  int jac_policy = 0;       // fr_jacobian_policy
+  // condensation held for FR_JAC_KEEP: valid, for which a_ii dt, refresh asked by the caller
+  int keep_valid = 0;
+  double keep_adt = 0.0;
+  int keep_refresh = 0;
+  long long jac_refreshes = 0;  // element-block linearisations made by imex_stage
   int cond_mode = 0;        // fr_condense_mode of the FP32 condensation
   int inv_ctas = 0;         // CTAs per SM of the tensor-core inverse (0: default)
   double* filt = nullptr;   // ns x ns modal filter operator (fr_modal_filter)
@@ -729,6 +734,7 @@ static int form_rhs(fr_ctx* ctx, const double* u, const double* ustar, double a_
 extern "C" int hfr_local_jacobian(fr_ctx* ctx, const double* u, const double* uhat, const double* ustar,
                                   double a_dt) {
   if (!ctx || !u || (ctx->ntrace > 0 && !uhat)) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_local_jacobian: null argument");
+  ctx->keep_valid = 0;  // the blocks no longer belong to an imex_stage linearisation
   // keep a copy of the linearisation point for later refinement sweeps
   CK(cudaMemcpyAsync(ctx->lin_Ubuf, u, (size_t)ctx->E * ctx->nA * sizeof(double), cudaMemcpyDeviceToDevice,
                      ctx->stream));
@@ -865,6 +871,7 @@ static int condense_rhs_impl(fr_ctx* ctx) {
 
 extern "C" int hfr_condense(fr_ctx* ctx, int refine) {
   if (!ctx) return FR_ERR_INVALID_ARG;
+  ctx->keep_valid = 0;
   int rc = condense_impl(ctx, refine);
   if (rc) return rc;
   rc = check_status(ctx, "hfr_condense: zero pivot");
@@ -957,9 +964,15 @@ static int gmres_impl(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* i
 }
 
 extern "C" int imex_set_jacobian_policy(fr_ctx* ctx, int policy) {
-  if (!ctx || (policy != FR_JAC_EVERY_NEWTON && policy != FR_JAC_ONCE_PER_STAGE))
+  if (!ctx || (policy != FR_JAC_EVERY_NEWTON && policy != FR_JAC_ONCE_PER_STAGE && policy != FR_JAC_KEEP))
     return set_err(ctx, FR_ERR_INVALID_ARG, "imex_set_jacobian_policy: bad argument");
   ctx->jac_policy = policy;
+  return FR_OK;
+}
+
+extern "C" int imex_refresh_jacobian(fr_ctx* ctx) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  ctx->keep_refresh = 1;
   return FR_OK;
 }
 
@@ -1695,13 +1708,21 @@ extern "C" int imex_stage(fr_ctx* ctx, int stage, double dt, const double* u_n, 
       break;
     }
     if (it >= newton_maxit) break;
-    if (it == 0 || ctx->jac_policy == FR_JAC_EVERY_NEWTON) {
+    bool fresh;
+    if (ctx->jac_policy == FR_JAC_KEEP)
+      fresh = it == 0 && (!ctx->keep_valid || ctx->keep_adt != adt || ctx->keep_refresh);
+    else
+      fresh = it == 0 || ctx->jac_policy == FR_JAC_EVERY_NEWTON;
+    if (fresh) {
+      ctx->keep_valid = 0;
       rc = jacobian_blocks(ctx, u_stage, uhat, adt);
       // the local solves are refined once, at the back-substitution (du = A^{-1}(r - B du^));
       // refining x_r as well would not change the converged step
       if (!rc) rc = condense_impl(ctx, 0);
+      ++ctx->jac_refreshes;
     } else {
-      // chord iteration: blocks, factors, S_k and preconditioner of the stage's first iterate
+      // chord iteration: blocks, factors, S_k and preconditioner of an earlier iterate (this
+      // stage's first, or with FR_JAC_KEEP an earlier stage's or step's)
       rc = condense_rhs_impl(ctx);
     }
     if (rc) return rc;
@@ -1716,6 +1737,11 @@ extern "C" int imex_stage(fr_ctx* ctx, int stage, double dt, const double* u_n, 
     if (cst[0] & DEV_ERR_TIMEOUT) {
       CK(cudaMemsetAsync(ctx->status, 0, sizeof(int), st));
       return set_err(ctx, FR_ERR_TIMEOUT, "imex_stage: tensor-core completion wait timed out");
+    }
+    if (fresh) {  // a factorisation without a zero pivot: held for later chord iterations
+      ctx->keep_valid = 1;
+      ctx->keep_adt = adt;
+      ctx->keep_refresh = 0;
     }
     gtot += its;
     if (rc && rc != FR_ERR_NOT_CONVERGED) return rc;
@@ -1743,6 +1769,52 @@ extern "C" int imex_stage(fr_ctx* ctx, int stage, double dt, const double* u_n, 
   }
   if (!conv) return set_err(ctx, FR_ERR_NOT_CONVERGED, "imex_stage: Newton iteration limit", -1, it, normk);
   return FR_OK;
+}
+
+// nsteps IMEX steps in place: per step, stage 0 (R at u_n), the implicit stages 1..s and the
+// final combination into u_stage, copied back to u.  With FR_JAC_KEEP the held condensation is
+// refreshed at every refresh_every-th step (and whenever a_ii dt changes or none is held).
+extern "C" int imex_steps(fr_ctx* ctx, int nsteps, double dt, double* u, double* uhat, double* R_hist,
+                          double* u_stage, int refresh_every, double newton_tol, int newton_maxit,
+                          double gmres_rtol, int gmres_maxit, int refine, fr_steps_stats* stats) {
+  if (!ctx || !u || !R_hist || !u_stage || (ctx->ntrace > 0 && !uhat) || nsteps < 0 || !(dt > 0.0))
+    return set_err(ctx, FR_ERR_INVALID_ARG, "imex_steps: bad argument");
+  const Tab tb = tableau(ctx->tableau);
+  fr_steps_stats acc;
+  memset(&acc, 0, sizeof(acc));
+  acc.converged = 1;
+  const long long r0 = ctx->jac_refreshes;
+  int rc = FR_OK;
+  for (int k = 0; k < nsteps && rc == FR_OK; ++k) {
+    if (ctx->jac_policy == FR_JAC_KEEP && refresh_every > 0 && k % refresh_every == 0) ctx->keep_refresh = 1;
+    rc = imex_stage(ctx, 0, dt, u, u_stage, uhat, R_hist, newton_tol, newton_maxit, gmres_rtol, gmres_maxit,
+                    refine, nullptr);
+    for (int i = 1; i <= tb.s && rc == FR_OK; ++i) {
+      fr_stage_stats ss;
+      rc = imex_stage(ctx, i, dt, u, u_stage, uhat, R_hist, newton_tol, newton_maxit, gmres_rtol, gmres_maxit,
+                      refine, &ss);
+      acc.newton_iterations += ss.newton_iterations;
+      acc.gmres_iterations += ss.gmres_iterations;
+      const double rel = ss.residual0 > 0.0 ? ss.residual / ss.residual0 : 0.0;
+      if (rel > acc.max_rel_residual) acc.max_rel_residual = rel;
+      if (!ss.converged) acc.converged = 0;
+    }
+    if (rc == FR_OK)
+      rc = imex_stage(ctx, tb.s + 1, dt, u, u_stage, uhat, R_hist, newton_tol, newton_maxit, gmres_rtol,
+                      gmres_maxit, refine, nullptr);
+    if (rc == FR_OK) {
+      if (cudaMemcpyAsync(u, u_stage, (size_t)ctx->E * ctx->nA * sizeof(double), cudaMemcpyDeviceToDevice,
+                          ctx->stream) != cudaSuccess)
+        rc = set_err(ctx, FR_ERR_CUDA, "imex_steps: copy of u_{n+1}");
+      else
+        ++acc.steps;
+    }
+  }
+  if (rc != FR_OK) acc.converged = 0;
+  acc.jacobian_refreshes = (int)(ctx->jac_refreshes - r0);
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (stats) *stats = acc;
+  return rc;
 }
 
 extern "C" int fr_profile_enable(fr_ctx* ctx, int on) {
