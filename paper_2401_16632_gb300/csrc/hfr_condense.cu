@@ -1818,10 +1818,18 @@ struct CondElem {
   double* t;
 };
 
+// barrier of one thread group (id 0 with the whole CTA is __syncthreads)
+__device__ __forceinline__ void grp_sync(int id, int nth) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nth) : "memory");
+}
+
 // Gauss-Jordan on [A | B | r] in shared memory with partial pivoting (rows not exchanged), then
-// S = D - C X_B and t = s - C x_r.  Ends with a CTA barrier, so the caller may reuse the memory.
+// S = D - C X_B and t = s - C x_r, by a group of nth threads (a multiple of 32; tid is the thread's
+// index in the group, bar its named barrier).  Ends with a group barrier, so the group may reuse
+// its memory.
 template <typename T>
-__device__ void condense_smem_elem(const CondElem<T>& e, unsigned char* smem_raw, int* status) {
+__device__ void condense_smem_elem(const CondElem<T>& e, unsigned char* smem_raw, int* status, int tid, int nth,
+                                   int bar) {
   const int nA = e.nA, nT = e.nT, nc = nA + nT + 1;
   const int big = nA > nT ? nA : nT;
   T* M = reinterpret_cast<T*>(smem_raw);  // nA x nc, physical rows
@@ -1829,17 +1837,17 @@ __device__ void condense_smem_elem(const CondElem<T>& e, unsigned char* smem_raw
   T* pr = W + (size_t)big * nA;           // nc
   T* cb = pr + nc;                        // nA
   int* ipiv = reinterpret_cast<int*>(cb + nA);
-  unsigned char* used = reinterpret_cast<unsigned char*>(ipiv + nA);
-  __shared__ int s_p;
-  __shared__ int s_bad;
-  const int tid = threadIdx.x;
-  for (int i = tid; i < nA * nc; i += GJS_THREADS) {
+  int* sflag = ipiv + nA;  // [0] pivot row of the step, [1] zero pivot seen
+  unsigned char* used = reinterpret_cast<unsigned char*>(sflag + 2);
+  int& s_p = sflag[0];
+  int& s_bad = sflag[1];
+  for (int i = tid; i < nA * nc; i += nth) {
     const int r = i / nc, j = i % nc;
     M[i] = j < nA ? e.A[(size_t)r * nA + j] : (j < nA + nT ? e.B[(size_t)r * nT + (j - nA)] : T(e.r[r]));
   }
-  for (int i = tid; i < nA; i += GJS_THREADS) used[i] = 0;
+  for (int i = tid; i < nA; i += nth) used[i] = 0;
   if (tid == 0) s_bad = 0;
-  __syncthreads();
+  grp_sync(bar, nth);
   for (int c = 0; c < nA; ++c) {
     if (tid < 32) {
       T best = T(-1);
@@ -1863,27 +1871,27 @@ __device__ void condense_smem_elem(const CondElem<T>& e, unsigned char* smem_raw
         if (!(best > T(0))) s_bad = 1;
       }
     }
-    __syncthreads();
+    grp_sync(bar, nth);
     const int p = s_p;
     const T pv = M[(size_t)p * nc + c];
     const T inv = pv != T(0) ? T(1) / pv : T(0);
-    for (int j = tid; j < nc; j += GJS_THREADS) pr[j] = j == c ? inv : M[(size_t)p * nc + j] * inv;
-    for (int r = tid; r < nA; r += GJS_THREADS) cb[r] = M[(size_t)r * nc + c];
-    __syncthreads();
-    for (int i = tid; i < nA * nc; i += GJS_THREADS) {
+    for (int j = tid; j < nc; j += nth) pr[j] = j == c ? inv : M[(size_t)p * nc + j] * inv;
+    for (int r = tid; r < nA; r += nth) cb[r] = M[(size_t)r * nc + c];
+    grp_sync(bar, nth);
+    for (int i = tid; i < nA * nc; i += nth) {
       const int r = i / nc, j = i % nc;
       if (r == p)
         M[i] = pr[j];
       else
         M[i] = (j == c ? T(0) : M[i]) - cb[r] * pr[j];
     }
-    __syncthreads();
+    grp_sync(bar, nth);
   }
   if (tid == 0 && s_bad) {
     atomicOr(status, DEV_ERR_SINGULAR);
     atomicMin(status + 1, e.id);
   }
-  for (int i = tid; i < nA * nc; i += GJS_THREADS) {
+  for (int i = tid; i < nA * nc; i += nth) {
     const int r = i / nc, j = i % nc;
     const int lr = ipiv[r];
     if (j < nA)
@@ -1894,9 +1902,9 @@ __device__ void condense_smem_elem(const CondElem<T>& e, unsigned char* smem_raw
       e.xr[lr] = double(M[i]);
   }
   // C into W; X rows in logical order are read through the pivot sequence
-  for (int i = tid; i < nT * nA; i += GJS_THREADS) W[i] = e.C[i];
-  __syncthreads();
-  for (int it = tid; it < nT * (nT + 1); it += GJS_THREADS) {
+  for (int i = tid; i < nT * nA; i += nth) W[i] = e.C[i];
+  grp_sync(bar, nth);
+  for (int it = tid; it < nT * (nT + 1); it += nth) {
     const int i = it / (nT + 1), j = it % (nT + 1);
     T acc = T(0);
     for (int l = 0; l < nA; ++l) acc += W[(size_t)i * nA + l] * M[(size_t)e.piv[l] * nc + nA + j];
@@ -1905,7 +1913,7 @@ __device__ void condense_smem_elem(const CondElem<T>& e, unsigned char* smem_raw
     else
       e.t[i] = e.s[i] - double(acc);
   }
-  __syncthreads();
+  grp_sync(bar, nth);
 }
 
 template <typename T>
@@ -1928,15 +1936,21 @@ __global__ void __launch_bounds__(GJS_THREADS) k_condense_smem(const __grid_cons
   e.xr = a.xr + (size_t)k * nA;
   e.S = reinterpret_cast<T*>(a.S) + (size_t)k * nT * nT;
   e.t = a.t + (size_t)k * nT;
-  condense_smem_elem<T>(e, smem_raw, a.status);
+  condense_smem_elem<T>(e, smem_raw, a.status, (int)threadIdx.x, GJS_THREADS, 0);
 }
 
 // Elements of uneven block shapes (e.g. several polynomial degrees) condensed in one persistent
-// launch: the CTAs walk a work list ordered by decreasing cost; element w of the list has shape
-// shape[2 e], shape[2 e + 1] and its blocks at the offsets off[5 e ..] into the packed arrays
-// (A-sized: A, LU; B-sized: B, C, X_B; D-sized: D, S; nA-sized: r, x_r, piv; nT-sized: s, t).
+// launch: the CTAs walk a list of bundles ordered by decreasing element cost.  A bundle holds up to
+// `groups` elements of one shape; the CTA splits into that many thread groups, each condensing one
+// element in its own slice of shared memory (stride bytes apart) with its own named barrier, so
+// small elements run several to a CTA while the dynamic shared memory is sized for the largest.
+// Element k has shape shape[2 k], shape[2 k + 1] and its blocks at the offsets off[5 k ..] into
+// the packed arrays (A-sized: A, LU; B-sized: B, C, X_B; D-sized: D, S; nA-sized: r, x_r, piv;
+// nT-sized: s, t).
+constexpr int UNEVEN_THREADS = 512, UNEVEN_MAX_GROUPS = 8;
 struct UnevenArgs {
-  int n;
+  int nb;
+  const int* bundle;  // per bundle: first position in order, elements, groups, stride (bytes)
   const int* order;
   const int* shape;
   const long long* off;
@@ -1952,34 +1966,42 @@ struct UnevenArgs {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(GJS_THREADS) k_condense_uneven(const __grid_constant__ UnevenArgs a) {
+__global__ void __launch_bounds__(UNEVEN_THREADS) k_condense_uneven(const __grid_constant__ UnevenArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  for (int w = blockIdx.x; w < a.n; w += gridDim.x) {
-    const int k = a.order[w];
-    const long long* o = a.off + 5 * (size_t)k;
-    CondElem<T> e;
-    e.nA = a.shape[2 * k];
-    e.nT = a.shape[2 * k + 1];
-    e.id = k;
-    e.A = reinterpret_cast<const T*>(a.A) + o[0];
-    e.LU = reinterpret_cast<T*>(a.LU) + o[0];
-    e.B = reinterpret_cast<const T*>(a.B) + o[1];
-    e.C = reinterpret_cast<const T*>(a.C) + o[1];
-    e.XB = reinterpret_cast<T*>(a.XB) + o[1];
-    e.D = reinterpret_cast<const T*>(a.D) + o[2];
-    e.S = reinterpret_cast<T*>(a.S) + o[2];
-    e.r = a.r + o[3];
-    e.xr = a.xr + o[3];
-    e.piv = a.piv + o[3];
-    e.s = a.s + o[4];
-    e.t = a.t + o[4];
-    condense_smem_elem<T>(e, smem_raw, a.status);
+  for (int b = blockIdx.x; b < a.nb; b += gridDim.x) {
+    const int* bd = a.bundle + 4 * (size_t)b;
+    const int start = bd[0], cnt = bd[1], groups = bd[2], stride = bd[3];
+    const int nth = UNEVEN_THREADS / groups;
+    const int g = (int)threadIdx.x / nth;
+    if (g < cnt) {
+      const int k = a.order[start + g];
+      const long long* o = a.off + 5 * (size_t)k;
+      CondElem<T> e;
+      e.nA = a.shape[2 * k];
+      e.nT = a.shape[2 * k + 1];
+      e.id = k;
+      e.A = reinterpret_cast<const T*>(a.A) + o[0];
+      e.LU = reinterpret_cast<T*>(a.LU) + o[0];
+      e.B = reinterpret_cast<const T*>(a.B) + o[1];
+      e.C = reinterpret_cast<const T*>(a.C) + o[1];
+      e.XB = reinterpret_cast<T*>(a.XB) + o[1];
+      e.D = reinterpret_cast<const T*>(a.D) + o[2];
+      e.S = reinterpret_cast<T*>(a.S) + o[2];
+      e.r = a.r + o[3];
+      e.xr = a.xr + o[3];
+      e.piv = a.piv + o[3];
+      e.s = a.s + o[4];
+      e.t = a.t + o[4];
+      condense_smem_elem<T>(e, smem_raw + (size_t)g * stride, a.status, (int)threadIdx.x - g * nth, nth,
+                            groups == 1 ? 0 : 1 + g);
+    }
+    __syncthreads();  // the next bundle reuses the memory
   }
 }
 
 static size_t smem_elem_bytes(size_t tb, int nA, int nT) {
   const int nc = nA + nT + 1, big = nA > nT ? nA : nT;
-  return tb * ((size_t)nA * nc + (size_t)big * nA + nc + nA) + sizeof(int) * nA + nA;
+  return tb * ((size_t)nA * nc + (size_t)big * nA + nc + nA) + sizeof(int) * (nA + 2) + nA;
 }
 
 cudaError_t launch_condense_uneven(int prec_bytes, int n, const int* nA, const int* nT, const void* A, const void* B,
@@ -2015,40 +2037,62 @@ cudaError_t launch_condense_uneven(int prec_bytes, int n, const int* nA, const i
     return a * a * (a + b) + b * b * a;
   };
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+  // bundles: runs of one shape in that order, as many elements per CTA as fit in its memory (a
+  // power of two, at most UNEVEN_MAX_GROUPS)
+  std::vector<int> bund;
+  for (int i = 0; i < n;) {
+    const int k0 = order[i];
+    int j = i;
+    while (j < n && nA[order[j]] == nA[k0] && nT[order[j]] == nT[k0]) ++j;
+    const size_t stride = (smem_elem_bytes(prec_bytes, nA[k0], nT[k0]) + 15) / 16 * 16;
+    int groups = 1;
+    while (groups < UNEVEN_MAX_GROUPS && (size_t)(2 * groups) * stride <= smem) groups *= 2;
+    for (int q = i; q < j; q += groups) {
+      bund.push_back(q);
+      bund.push_back(j - q < groups ? j - q : groups);
+      bund.push_back(groups);
+      bund.push_back((int)stride);
+    }
+    i = j;
+  }
+  const int nb = (int)(bund.size() / 4);
   void* dbuf = nullptr;
-  const size_t bytes_i = sizeof(int) * (3 * (size_t)n), bytes_o = sizeof(long long) * off.size();
+  const size_t bytes_i = sizeof(int) * (3 * (size_t)n + bund.size()), bytes_o = sizeof(long long) * off.size();
   cudaError_t e = cudaMallocAsync(&dbuf, bytes_o + bytes_i, st);
   if (e != cudaSuccess) return e;
   long long* d_off = reinterpret_cast<long long*>(dbuf);
   int* d_order = reinterpret_cast<int*>(d_off + off.size());
   int* d_shape = d_order + n;
-  UnevenArgs ua{n, d_order, d_shape, d_off, A, B, C, D, r, s, LU, piv, XB, xr, S, t, status};
+  int* d_bund = d_shape + 2 * (size_t)n;
+  UnevenArgs ua{nb, d_bund, d_order, d_shape, d_off, A, B, C, D, r, s, LU, piv, XB, xr, S, t, status};
   int dev = 0, nsm = 0, occ = 0;
   if ((e = cudaMemcpyAsync(d_off, off.data(), bytes_o, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(d_shape, shape.data(), sizeof(int) * 2 * n, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      (e = cudaMemcpyAsync(d_shape, shape.data(), sizeof(int) * 2 * n, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_bund, bund.data(), sizeof(int) * bund.size(), cudaMemcpyHostToDevice, st)) !=
+          cudaSuccess)
     goto done;
   if (prec_bytes == 8) {
     if ((e = cudaFuncSetAttribute(k_condense_uneven<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)
       goto done;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_condense_uneven<double>, GJS_THREADS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_condense_uneven<double>, UNEVEN_THREADS, smem);
   } else {
     if ((e = cudaFuncSetAttribute(k_condense_uneven<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)
       goto done;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_condense_uneven<float>, GJS_THREADS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_condense_uneven<float>, UNEVEN_THREADS, smem);
   }
   if (e != cudaSuccess) goto done;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) goto done;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) goto done;
   {
     int grid = nsm * (occ < 1 ? 1 : occ);
-    grid = n < grid ? n : grid;
+    grid = nb < grid ? nb : grid;
     if (prec_bytes == 8)
-      (hfr::count_launch(), k_condense_uneven<double><<<grid, GJS_THREADS, smem, st>>>(ua));
+      (hfr::count_launch(), k_condense_uneven<double><<<grid, UNEVEN_THREADS, smem, st>>>(ua));
     else
-      (hfr::count_launch(), k_condense_uneven<float><<<grid, GJS_THREADS, smem, st>>>(ua));
+      (hfr::count_launch(), k_condense_uneven<float><<<grid, UNEVEN_THREADS, smem, st>>>(ua));
     e = cudaGetLastError();
   }
 done:
@@ -2314,8 +2358,7 @@ static cudaError_t cond_reg(const CondArgs& a, cudaStream_t st) {
 
 template <typename T>
 static cudaError_t cond_smem(const CondArgs& a, cudaStream_t st) {
-  const int nc = a.nA + a.nT + 1, big = a.nA > a.nT ? a.nA : a.nT;
-  const size_t smem = sizeof(T) * ((size_t)a.nA * nc + (size_t)big * a.nA + nc + a.nA) + sizeof(int) * a.nA + a.nA;
+  const size_t smem = smem_elem_bytes(sizeof(T), a.nA, a.nT);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   cudaError_t err = cudaFuncSetAttribute(k_condense_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
