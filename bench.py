@@ -143,7 +143,7 @@ JAC_POLICY = {"every": 0, "once": 1}
 
 
 def time_path(pkg, torch, w, precision, refine, steps, warmup, dev, l2buf, jac="every", barrier=None, graph=False,
-              autotune=True):
+              autotune=True, cond_mode=None):
     ctx = pkg.Context(w.mesh, w.physics, precision=precision, tableau=pkg.FR_TAB_SDIRK2)
     ctx.refine = refine
     ctx.imex_set_jacobian_policy(JAC_POLICY[jac])
@@ -156,6 +156,8 @@ def time_path(pkg, torch, w, precision, refine, steps, warmup, dev, l2buf, jac="
     tune = None
     if autotune and precision == pkg.FR_PREC_FP32:  # pick the condensation form and GMRES cycle on this workload
         tune = ctx.hfr_autotune(u_n, uhat0, u_n, w.dt * (1.0 - 0.5 ** 0.5))
+    if cond_mode is not None:
+        ctx.hfr_condense_set_mode(cond_mode)
     R_hist = ctx.empty(3, *ctx.state_shape)
     u_stage = ctx.empty(*ctx.state_shape)
     stats = None
@@ -405,7 +407,7 @@ def kernel_rooflines(prof, stats, w, peaks, clocks, workload, cond_mode=2):
     per_it = E * nT * nT * 4 + ntrace * bs * bs * 4 + 4 * (its / 2 + 1) * nt_u * 4 + 2 * nt_u * 4
     out["gmres"] = entry("k_gmres_cycle", "hbm", per_it * its / (a * 1e-3) / 1e9, hbm_peak, "GB/s", tot, a)
     tot, a = avg("condense_factor")
-    inv = "k_inverse_tc" if cond_mode == 2 else ("k_inverse_warp" if nA <= 64 else "k_inverse_rq")
+    inv = "k_inverse_tc" if cond_mode >= 2 else ("k_inverse_warp" if nA <= 64 else "k_inverse_rq")
     out["condense_factor"] = entry(inv, "alu", E * 2.0 * nA**3 / (a * 1e-3) / 1e12, alu_peak, "TFLOP/s", tot, a)
     tot, a = avg("condense_products")
     fl = E * 2.0 * (nA * nA * (nT + 1) + nT * nA * (nT + 1)) / (a * 1e-3) / 1e12
@@ -442,6 +444,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="profiling aid: skip the host-buffer e2e leg")
     ap.add_argument("--no-uneven", action="store_true", help="skip the uneven-degree condensation leg")
     ap.add_argument("--no-reuse", action="store_true", help="skip the Jacobian-reuse (imex_steps) leg")
+    ap.add_argument("--no-tf32", action="store_true", help="skip the single-pass TF32 condensation leg")
     ap.add_argument("--no-autotune", action="store_true",
                     help="profiling aid: keep the default kernel forms (timings under a profiler would mislead the tuner)")
     args = ap.parse_args()
@@ -483,6 +486,14 @@ def main():
         fp64 = time_path(pkg, torch, w, pkg.FR_PREC_FP64, 0, args.steps, args.warmup, dev, l2buf, args.jacobian,
                          barrier)
         # the same mixed stage as one CUDA graph (no per-kernel phases: timed as a whole)
+        tf32 = None
+        if not args.no_tf32:
+            try:  # the same stream stage with the single-pass TF32 condensation (not the headline)
+                tf32 = time_path(pkg, torch, w, pkg.FR_PREC_FP32, args.refine, args.steps, args.warmup, dev, l2buf,
+                                 args.jacobian, barrier, autotune=not args.no_autotune,
+                                 cond_mode=pkg.FR_CONDENSE_TENSOR_TF32)
+            except Exception as exc:  # reported, never fatal
+                tf32 = {"error": str(exc)}
         graph = None
         if args.jacobian == "every":
             graph = time_path(pkg, torch, w, pkg.FR_PREC_FP32, args.refine, args.steps, args.warmup, dev, l2buf,
@@ -550,6 +561,18 @@ def main():
         "clocks": clocks,
         "peaks_source": peak_src,
     }
+    if tf32 is not None:
+        if "error" in tf32:
+            line["tf32_single_pass"] = tf32
+        else:
+            ms_t = replica_max([np.mean(tf32["ms"])], dist, dev)[0]
+            line["tf32_single_pass"] = {
+                "value": job_value(world, dofs, ms_t), "ms_per_step": ms_t,
+                "newton_iterations": tf32["stats"]["newton_iterations"],
+                "gmres_iterations": tf32["stats"]["gmres_iterations"], "converged": tf32["stats"]["converged"],
+                "max_rel_diff_vs_fp64": (tf32["u"] - fp64["u"]).abs().max().item() / inc,
+                "note": "stream stage with FR_CONDENSE_TENSOR_TF32 (one TF32 product per term in the tensor-core "
+                        "factorisation and products); compare stream_stage"}
     if not args.no_reuse:
         try:
             line["jacobian_reuse"] = jacobian_reuse(pkg, torch, mixed["ctx"], w, dev)

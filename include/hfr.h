@@ -180,9 +180,17 @@ int hfr_gmres_get_mode(const fr_ctx* ctx);
  * all on the tensor cores (tcgen05; TF32 operands split into high and low parts, three products
  * accumulated in FP32: about 2^-21 relative per product term).  FR_CONDENSE_TENSOR_PRODUCTS: the
  * products on the tensor cores, the factorisation on the FP32 FMA pipes.  FR_CONDENSE_FMA: both
- * on the FP32 FMA pipes.  set: FR_ERR_UNSUPPORTED where the requested form does not exist for the
- * context; get: the mode in effect, -1 for a null context. */
-enum fr_condense_mode { FR_CONDENSE_FMA = 0, FR_CONDENSE_TENSOR_PRODUCTS = 1, FR_CONDENSE_TENSOR = 2 };
+ * on the FP32 FMA pipes.  FR_CONDENSE_TENSOR_TF32: the FR_CONDENSE_TENSOR kernels with the single
+ * TF32 product hi*hi (about 2^-11 relative per product term; the FP64 Newton residual still decides
+ * convergence, which may take more iterations; hfr_autotune never chooses it).  set:
+ * FR_ERR_UNSUPPORTED where the requested form does not exist for the context; get: the mode in
+ * effect, -1 for a null context. */
+enum fr_condense_mode {
+  FR_CONDENSE_FMA = 0,
+  FR_CONDENSE_TENSOR_PRODUCTS = 1,
+  FR_CONDENSE_TENSOR = 2,
+  FR_CONDENSE_TENSOR_TF32 = 3
+};
 int hfr_condense_set_mode(fr_ctx* ctx, int mode);
 int hfr_condense_get_mode(const fr_ctx* ctx);
 

@@ -31,7 +31,7 @@ FR_TAB_BE, FR_TAB_SDIRK2 = 0, 1
 FR_PHYS_ADVDIFF, FR_PHYS_NAVIER_STOKES, FR_PHYS_EDAC = 0, 1, 2
 FR_GMRES_MULTI, FR_GMRES_FUSED = 0, 1
 FR_JAC_EVERY_NEWTON, FR_JAC_ONCE_PER_STAGE, FR_JAC_KEEP = 0, 1, 2
-FR_CONDENSE_FMA, FR_CONDENSE_TENSOR_PRODUCTS, FR_CONDENSE_TENSOR = 0, 1, 2
+FR_CONDENSE_FMA, FR_CONDENSE_TENSOR_PRODUCTS, FR_CONDENSE_TENSOR, FR_CONDENSE_TENSOR_TF32 = 0, 1, 2, 3
 (FR_OK, FR_ERR_INVALID_ARG, FR_ERR_CUDA, FR_ERR_SINGULAR, FR_ERR_NOT_CONVERGED, FR_ERR_DIVERGED, FR_ERR_TIMEOUT,
  FR_ERR_OOM, FR_ERR_UNSUPPORTED) = range(9)
 EXPORT = {"A": 0, "B": 1, "C": 2, "D": 3, "S": 4, "XB": 5, "xr": 6, "t_k": 7, "r": 8, "s": 9, "t": 10, "Pinv": 11}

@@ -988,9 +988,10 @@ extern "C" int hfr_gmres_set_mode(fr_ctx* ctx, int mode) {
 extern "C" int hfr_gmres_get_mode(const fr_ctx* ctx) { return ctx ? ctx->gm_mode : -1; }
 
 extern "C" int hfr_condense_set_mode(fr_ctx* ctx, int mode) {
-  if (!ctx || mode < FR_CONDENSE_FMA || mode > FR_CONDENSE_TENSOR)
+  if (!ctx || mode < FR_CONDENSE_FMA || mode > FR_CONDENSE_TENSOR_TF32)
     return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_condense_set_mode: bad argument");
-  if (mode > condense_tc_available(ctx->prec_bytes, ctx->nA, ctx->nT))
+  if ((mode == FR_CONDENSE_TENSOR_TF32 ? FR_CONDENSE_TENSOR : mode) >
+      condense_tc_available(ctx->prec_bytes, ctx->nA, ctx->nT))
     return set_err(ctx, FR_ERR_UNSUPPORTED, "hfr_condense_set_mode: no tensor-core form for this precision or shape");
   ctx->cond_mode = mode;
   return FR_OK;

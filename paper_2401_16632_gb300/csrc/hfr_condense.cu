@@ -916,8 +916,10 @@ __global__ void __launch_bounds__(128, 4) k_inverse_tc(const __grid_constant__ C
         for (int kk = 0; kk < 2; ++kk) {
           const uint32_t off = (uint32_t)kk * 256u;
           mma_tf32(tmem, desc_noswizzle(wh + off, 128, Sh::SBO), desc_noswizzle(ph + off, 128, Sh::SBO), idesc, 1);
-          mma_tf32(tmem, desc_noswizzle(wh + off, 128, Sh::SBO), desc_noswizzle(pl + off, 128, Sh::SBO), idesc, 1);
-          mma_tf32(tmem, desc_noswizzle(wl + off, 128, Sh::SBO), desc_noswizzle(ph + off, 128, Sh::SBO), idesc, 1);
+          if (a.tc_mode != 3) {  // 3xTF32; mode 3 keeps the single TF32 pass
+            mma_tf32(tmem, desc_noswizzle(wh + off, 128, Sh::SBO), desc_noswizzle(pl + off, 128, Sh::SBO), idesc, 1);
+            mma_tf32(tmem, desc_noswizzle(wl + off, 128, Sh::SBO), desc_noswizzle(ph + off, 128, Sh::SBO), idesc, 1);
+          }
         }
         mma_commit(smem_u32(mbar));
       }
@@ -1513,7 +1515,7 @@ __device__ __forceinline__ void tc_store_stage(const TcStage<NA, NT>& g, unsigne
 
 template <int NA, int NT>
 __device__ __forceinline__ void tc_issue(uint32_t td, unsigned char* Ahi, unsigned char* Alo, unsigned char* Bhi,
-                                         unsigned char* Blo, uint32_t idesc, uint32_t mbar) {
+                                         unsigned char* Blo, uint32_t idesc, uint32_t mbar, bool three) {
   using Sh = TcShape<NA, NT>;
   using namespace tc;
   fence_after_sync();
@@ -1522,8 +1524,10 @@ __device__ __forceinline__ void tc_issue(uint32_t td, unsigned char* Ahi, unsign
   for (int kk = 0; kk < Sh::K1 / 8; ++kk) {
     const uint32_t off = (uint32_t)kk * 256u;  // two core matrices along k per instruction
     mma_tf32(td, desc_noswizzle(ah + off, 128, Sh::SBO), desc_noswizzle(bh + off, 128, Sh::SBO), idesc, kk > 0);
-    mma_tf32(td, desc_noswizzle(ah + off, 128, Sh::SBO), desc_noswizzle(bl + off, 128, Sh::SBO), idesc, 1);
-    mma_tf32(td, desc_noswizzle(al + off, 128, Sh::SBO), desc_noswizzle(bh + off, 128, Sh::SBO), idesc, 1);
+    if (three) {  // 3xTF32 (single TF32 pass otherwise)
+      mma_tf32(td, desc_noswizzle(ah + off, 128, Sh::SBO), desc_noswizzle(bl + off, 128, Sh::SBO), idesc, 1);
+      mma_tf32(td, desc_noswizzle(al + off, 128, Sh::SBO), desc_noswizzle(bh + off, 128, Sh::SBO), idesc, 1);
+    }
   }
   mma_commit(mbar);
 }
@@ -1588,7 +1592,7 @@ __global__ void __launch_bounds__(256, 1) k_products_tc(const __grid_constant__ 
     fence_before_sync();
     __syncthreads();
     if (issuer && lane == 0) {
-      tc_issue<NA, NT>(tmem, Ahi, Alo, Bhi, Blo, idesc_tf32(128, Sh::N1), smem_u32(mbar));
+      tc_issue<NA, NT>(tmem, Ahi, Alo, Bhi, Blo, idesc_tf32(128, Sh::N1), smem_u32(mbar), a.tc_mode != 3);
       // L2 prefetch two elements ahead: the next element's operands are loaded in this iteration
       if (kn + G < a.Eim) {
         const size_t o = (size_t)kn + G;
@@ -1681,7 +1685,7 @@ __global__ void __launch_bounds__(256, 1) k_products_tc(const __grid_constant__ 
     fence_before_sync();
     __syncthreads();
     if (issuer && lane == 0)
-      tc_issue<NA, NT>(tmem + Sh::D2_COL, Ahi, Alo, Bhi, Blo, idesc_tf32(128, Sh::N2), smem_u32(mbar));
+      tc_issue<NA, NT>(tmem + Sh::D2_COL, Ahi, Alo, Bhi, Blo, idesc_tf32(128, Sh::N2), smem_u32(mbar), a.tc_mode != 3);
     if (kn + G < a.Eim && t < NA) pv_next = __ldg(a.piv + (size_t)(kn + G) * NA + t);
     // while GEMM 2 runs: this element's D and s
     const int cb2 = hh == 0 ? 0 : Sh::H2, ce2 = hh == 0 ? Sh::H2 : Sh::NCH2;
@@ -1773,7 +1777,7 @@ template <int NA, int NT>
 static cudaError_t cond_two_kernel(const CondArgs& a, cudaStream_t st, int part) {
   using P = ProdShape<NA, NT>;
   if (part == 0) {
-    if (a.tc_mode == 2) return launch_inverse_tc<NA>(a, st);
+    if (a.tc_mode >= 2) return launch_inverse_tc<NA>(a, st);
     if constexpr (NA <= 64) {
       constexpr int WPB = InvWShape<NA>::WPB;
       (hfr::count_launch(), k_inverse_warp<NA><<<(a.Eim + WPB - 1) / WPB, 32 * WPB, 0, st>>>(a));

@@ -349,6 +349,46 @@ def test_tensor_core_and_fma_condensation_agree(name):
             assert _rel(out[mode][key], ref) < 1e-4, (mode, key)
 
 
+@pytest.mark.parametrize("name", ["vortex_skew_p3", "vortex_p4"])
+def test_single_pass_tf32_condensation(name):
+    """FR_CONDENSE_TENSOR_TF32: the tensor-core kernels with one TF32 product per term.  Its
+    condensation is within TF32 accuracy of the oracle and visibly less accurate than 3xTF32 (the
+    mode is in effect); the implicit stage still converges to the FP64 stage's solution, since the
+    FP64 Newton residual decides convergence."""
+    ctx, d, u0, uh, ustar, a_dt, (A, B, C, D) = _blocks_both(name, pkg.FR_PREC_FP32)
+    r = ctx.hfr_export("r").cpu().numpy()
+    s = ctx.hfr_export("s").cpu().numpy()
+    XB, xr, S, t = condense(A, B, C, D, r, s)
+    err = {}
+    for mode in (pkg.FR_CONDENSE_TENSOR, pkg.FR_CONDENSE_TENSOR_TF32):
+        ctx.hfr_condense_set_mode(mode)
+        assert ctx.hfr_condense_get_mode() == mode
+        ctx.hfr_condense(refine=0)
+        got = {k: ctx.hfr_export(k).cpu().numpy().astype(np.float64) for k in ("S", "XB")}
+        err[mode] = max(_rel(got["S"], S), _rel(got["XB"], XB))
+    assert err[pkg.FR_CONDENSE_TENSOR] < 1e-4
+    assert err[pkg.FR_CONDENSE_TENSOR_TF32] < 2e-2
+    assert err[pkg.FR_CONDENSE_TENSOR_TF32] > 3 * err[pkg.FR_CONDENSE_TENSOR]
+    # the stage: same FP64 Newton test, same solution
+    mesh, u0, phys = CASES[name]()
+    res = {}
+    for prec in (pkg.FR_PREC_FP64, pkg.FR_PREC_FP32):
+        c = pkg.Context(mesh, phys, precision=prec, tableau=pkg.FR_TAB_SDIRK2)
+        if prec == pkg.FR_PREC_FP32:
+            c.hfr_condense_set_mode(pkg.FR_CONDENSE_TENSOR_TF32)
+        u = torch.tensor(u0, device=DEV)
+        uhat = c.hfr_initial_trace(u)
+        R_hist = c.empty(3, *c.state_shape)
+        us = c.empty(*c.state_shape)
+        c.imex_stage(0, 0.1, u, us, uhat, R_hist)
+        st = c.imex_stage(1, 0.1, u, us, uhat, R_hist, newton_tol=1e-11, newton_maxit=60, gmres_rtol=1e-6,
+                          gmres_maxit=3000)
+        assert st["converged"]
+        res[prec] = us.cpu().numpy()
+    inc = np.abs(res[pkg.FR_PREC_FP64] - u0).max()
+    assert np.abs(res[pkg.FR_PREC_FP32] - res[pkg.FR_PREC_FP64]).max() < 1e-8 * inc
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("name", ["vortex_skew_p3", "vortex_p4", "band_ns"])
 def test_graph_stage_equals_stream_stage(name, precision):
