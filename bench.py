@@ -37,9 +37,11 @@ WORKLOADS = {
     "vortex64": ("vortex64: 2D compressible Navier-Stokes isentropic vortex, M=0.5, gamma=1.4, Re=1e4, periodic "
                  "[0,10]^2, 64x64 quads, p=3 (blocks 64x64), SDIRK2 stage 1 at 10x explicit CFL, Newton to 1e-8"),
 }
-PATCH = {"vortex256": 14, "vortex64": 16, "vortex64p4": 10}
+PATCH = {"vortex256": 14, "vortex64": 16, "vortex64p4": 10, "vortex128p4": 12}
 # profiling aid: the p = 4 kernels of vortex256 on a 64x64 mesh (a few GB on the device)
-WORKLOADS["vortex64p4"] = "vortex64p4: vortex256's physics, p = 4 and noise on 64x64 quads (profiling size)"  # oracle sample: PATCH x PATCH elements at the workload's spacing
+WORKLOADS["vortex64p4"] = "vortex64p4: vortex256's physics, p = 4 and noise on 64x64 quads (profiling size)"
+# profiling aid: 128x128, so that the trace operator's S blocks (420 MB) exceed the 129 MB L2
+WORKLOADS["vortex128p4"] = "vortex128p4: vortex256's physics, p = 4 and noise on 128x128 quads (profiling size)"  # oracle sample: PATCH x PATCH elements at the workload's spacing
 NEWTON_TOL = 1e-8
 GMRES_RTOL = 1e-4
 FP32_PEAK_PER_SM_CLK = 256.0  # 128 FP32 FMA lanes x 2 flops
@@ -469,8 +471,10 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=dev)
-    w = (make_config("vortex", n=64, p=4, noise=1.0e-3, seed=1234) if args.workload == "vortex64p4"
-         else make_config(args.workload))
+    if args.workload in ("vortex64p4", "vortex128p4"):
+        w = make_config("vortex", n=64 if args.workload == "vortex64p4" else 128, p=4, noise=1.0e-3, seed=1234)
+    else:
+        w = make_config(args.workload)
     l2buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB
     if args.paths != "both":  # profiling aid: one path, no JSON contract line
         prec = pkg.FR_PREC_FP32 if args.paths == "mixed" else pkg.FR_PREC_FP64

@@ -123,3 +123,19 @@ def test_imex_steps_rejects_bad_arguments():
     assert ei.value.code == pkg.FR_ERR_INVALID_ARG
     st = ctx.imex_steps(0, 0.1, u, uh)
     assert st["steps"] == 0 and st["jacobian_refreshes"] == 0
+
+
+def test_kept_jacobian_steps_conserve_across_the_interface():
+    """Discrete conservation of every conserved variable over several steps on an IMEX band mesh
+    (Sec. 4): it rests on the converged trace residual and the tableau (bhat_{j+1} = b_j), not on
+    the Jacobian the Newton iterations used."""
+    mesh, u0, phys = _band_ns()
+    d = Discretisation(mesh, make_physics(phys))
+    ctx = pkg.Context(mesh, phys, precision=pkg.FR_PREC_FP64, tableau=pkg.FR_TAB_SDIRK2)
+    ctx.imex_set_jacobian_policy(pkg.FR_JAC_KEEP)
+    u, _, st = _steps(ctx, u0, 3, 0.02, newton_tol=1e-12, newton_maxit=80, gmres_rtol=1e-13, gmres_maxit=3000)
+    assert st["converged"] and st["jacobian_refreshes"] == 1
+    W = np.outer(d.ref.w, d.ref.w).reshape(-1)
+    m0 = np.einsum("s,es,esv->v", W, d.geo.J, u0)
+    m1 = np.einsum("s,es,esv->v", W, d.geo.J, u.cpu().numpy())
+    assert np.abs(m1 - m0).max() < 1e-10 * np.abs(m0).max() + 1e-12
