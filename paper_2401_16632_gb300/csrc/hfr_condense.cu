@@ -1951,7 +1951,7 @@ __global__ void __launch_bounds__(GJS_THREADS) k_condense_smem(const __grid_cons
 // Element k has shape shape[2 k], shape[2 k + 1] and its blocks at the offsets off[5 k ..] into
 // the packed arrays (A-sized: A, LU; B-sized: B, C, X_B; D-sized: D, S; nA-sized: r, x_r, piv;
 // nT-sized: s, t).
-constexpr int UNEVEN_THREADS = 512, UNEVEN_MAX_GROUPS = 8;
+constexpr int UNEVEN_THREADS = 1024, UNEVEN_MAX_GROUPS = 8;
 struct UnevenArgs {
   int nb;
   const int* bundle;  // per bundle: first position in order, elements, groups, stride (bytes)
