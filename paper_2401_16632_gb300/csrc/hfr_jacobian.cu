@@ -179,64 +179,50 @@ __global__ void __launch_bounds__(JAC_THREADS, sizeof(T) == 4 ? (P <= 3 ? 4 : (P
     w.rw[tid] = T(ref.w[tid]);
   }
   __syncthreads();
-  for (int j = tid; j < NF; j += JAC_THREADS) {
+  // one thread per (flux point, variable): face values, then the trace or the neighbour's state
+  for (int it = tid; it < NF * NV; it += JAC_THREADS) {
+    const int j = it / NV, v = it % NV;
     const int f = j / N, m = j % N, r = f >> 1;
     const T* l = (f & 1) ? w.rlp : w.rlm;
-    const int kf = w.kf[f];
+    T s = T(0);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      T s = T(0);
-#pragma unroll
-      for (int c = 0; c < N; ++c) s += l[c] * w.U[line_pt<N>(r, m, c)][v];
-      w.Uf[j][v] = s;
-    }
-    if (kf == FK_TRACE) {
+    for (int c = 0; c < N; ++c) s += l[c] * w.U[line_pt<N>(r, m, c)][v];
+    w.Uf[j][v] = s;
+    if (w.kf[f] == FK_TRACE) {
       const int t = a.tr_of[e * 4 + f];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        w.ub[j][v] = T(a.uhat[((size_t)t * N + m) * NV + v]);
-        w.un[j][v] = w.Uf[j][v];
-      }
+      w.ub[j][v] = T(a.uhat[((size_t)t * N + m) * NV + v]);
+      w.un[j][v] = s;
     } else {  // interface face: explicit neighbour's state is the common solution
       const int en = a.nbr[e * 4 + f], fnb = a.nbr_face[e * 4 + f];
-      const double* un = a.Uf_all + ((size_t)en * NF + fnb * N + m) * NV;
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        w.un[j][v] = T(un[v]);
-        w.ub[j][v] = T(un[v]);
-      }
+      const T un = T(a.Uf_all[((size_t)en * NF + fnb * N + m) * NV + v]);
+      w.un[j][v] = un;
+      w.ub[j][v] = un;
     }
   }
   __syncthreads();
   if (visc) {
-    for (int i = tid; i < NS; i += JAC_THREADS) {
+    for (int it = tid; it < NS * NV; it += JAC_THREADS) {  // one thread per (point, variable)
+      const int i = it / NV, v = it % NV;
       const int ai = i % N, bi = i / N;
+      T q0 = w.rdgL[ai] * w.ub[bi][v] + w.rdgR[ai] * w.ub[N + bi][v];
+      T q1 = w.rdgL[bi] * w.ub[2 * N + ai][v] + w.rdgR[bi] * w.ub[3 * N + ai][v];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        T q0 = w.rdgL[ai] * w.ub[bi][v] + w.rdgR[ai] * w.ub[N + bi][v];
-        T q1 = w.rdgL[bi] * w.ub[2 * N + ai][v] + w.rdgR[bi] * w.ub[3 * N + ai][v];
-#pragma unroll
-        for (int c = 0; c < N; ++c) {
-          q0 += w.rM[ai][c] * w.U[c + N * bi][v];
-          q1 += w.rM[bi][c] * w.U[ai + N * c][v];
-        }
-        w.q[i][0][v] = w.iJ[i] * (w.Sm[i][0][0] * q0 + w.Sm[i][1][0] * q1);
-        w.q[i][1][v] = w.iJ[i] * (w.Sm[i][0][1] * q0 + w.Sm[i][1][1] * q1);
+      for (int c = 0; c < N; ++c) {
+        q0 += w.rM[ai][c] * w.U[c + N * bi][v];
+        q1 += w.rM[bi][c] * w.U[ai + N * c][v];
       }
+      w.q[i][0][v] = w.iJ[i] * (w.Sm[i][0][0] * q0 + w.Sm[i][1][0] * q1);
+      w.q[i][1][v] = w.iJ[i] * (w.Sm[i][0][1] * q0 + w.Sm[i][1][1] * q1);
     }
     __syncthreads();
-    for (int j = tid; j < NF; j += JAC_THREADS) {
+    for (int it = tid; it < NF * 2 * NV; it += JAC_THREADS) {  // (flux point, direction, variable)
+      const int j = it / (2 * NV), c2 = (it / NV) % 2, v = it % NV;
       const int f = j / N, m = j % N, r = f >> 1;
       const T* l = (f & 1) ? w.rlp : w.rlm;
+      T s = T(0);
 #pragma unroll
-      for (int c2 = 0; c2 < 2; ++c2)
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          T s = T(0);
-#pragma unroll
-          for (int c = 0; c < N; ++c) s += l[c] * w.q[line_pt<N>(r, m, c)][c2][v];
-          w.qf[j][c2][v] = s;
-        }
+      for (int c = 0; c < N; ++c) s += l[c] * w.q[line_pt<N>(r, m, c)][c2][v];
+      w.qf[j][c2][v] = s;
     }
   } else {
     for (int i = tid; i < NS * 2 * NV; i += JAC_THREADS) (&w.q[0][0][0])[i] = T(0);
