@@ -1010,7 +1010,7 @@ struct ProdShape {
 template <int NA, int NT>
 __global__ void __launch_bounds__(ProdShape<NA, NT>::THREADS) k_condense_products(const __grid_constant__ CondArgs a) {
   using Sh = ProdShape<NA, NT>;
-  constexpr int TI = Sh::TI, TJ = Sh::TJ, NAP = Sh::NAP, LDW = Sh::LDW, LDB = Sh::LDB, THREADS = Sh::THREADS;
+  constexpr int TI = Sh::TI, TJ = Sh::TJ, LDW = Sh::LDW, LDB = Sh::LDB, THREADS = Sh::THREADS;
   extern __shared__ __align__(16) float sm[];
   float* W = sm;                    // NA x LDW: k-major left operand
   float* Bs = sm + (size_t)NA * LDW;  // NAP x LDB: k-major right operand

@@ -265,37 +265,37 @@ __device__ void pg_block_dots(PGShared<T>& sh, const T* V, size_t n, int nd, con
       for (int k = 0; k < PG_WARPS; ++k) t += sh.red[i][k];
       partial[(size_t)i * gridDim.x + blockIdx.x] = t;
     }
-    return;
-  }
-  for (int c0 = 0; c0 < nd; c0 += 16) {
-    T acc[16];
+  } else {
+    for (int c0 = 0; c0 < nd; c0 += 16) {
+      T acc[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = T(0);
-    // two entries per iteration: 34 independent loads in flight per thread
-    for (size_t xa = x0 + threadIdx.x; xa < x1; xa += 2 * PG_THREADS) {
-      const size_t xb = xa + PG_THREADS;
-      const bool okb = xb < x1;
-      const T wa = w[xa];
-      const T wb = okb ? w[xb] : T(0);
-      const size_t xbs = okb ? xb : xa;
+      for (int q = 0; q < 16; ++q) acc[q] = T(0);
+      // two entries per iteration: 34 independent loads in flight per thread
+      for (size_t xa = x0 + threadIdx.x; xa < x1; xa += 2 * PG_THREADS) {
+        const size_t xb = xa + PG_THREADS;
+        const bool okb = xb < x1;
+        const T wa = w[xa];
+        const T wb = okb ? w[xb] : T(0);
+        const size_t xbs = okb ? xb : xa;
 #pragma unroll
-      for (int q = 0; q < 16; ++q)
-        if (c0 + q < nd) {
-          const T va = V[(size_t)(c0 + q) * n + xa];
-          const T vb = V[(size_t)(c0 + q) * n + xbs];
-          acc[q] += va * wa + vb * wb;
-        }
+        for (int q = 0; q < 16; ++q)
+          if (c0 + q < nd) {
+            const T va = V[(size_t)(c0 + q) * n + xa];
+            const T vb = V[(size_t)(c0 + q) * n + xbs];
+            acc[q] += va * wa + vb * wb;
+          }
+      }
+      const T s = pg_scatter16(acc, lane);
+      const int vi = c0 + (lane >> 1);
+      if ((lane & 1) == 0 && vi < nd) sh.red[vi][wid] = s;
     }
-    const T s = pg_scatter16(acc, lane);
-    const int vi = c0 + (lane >> 1);
-    if ((lane & 1) == 0 && vi < nd) sh.red[vi][wid] = s;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < nd; i += PG_THREADS) {
-    T t = T(0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nd; i += PG_THREADS) {
+      T t = T(0);
 #pragma unroll
-    for (int k = 0; k < PG_WARPS; ++k) t += sh.red[i][k];
-    partial[(size_t)i * gridDim.x + blockIdx.x] = t;
+      for (int k = 0; k < PG_WARPS; ++k) t += sh.red[i][k];
+      partial[(size_t)i * gridDim.x + blockIdx.x] = t;
+    }
   }
 }
 
