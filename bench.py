@@ -355,12 +355,12 @@ def _threads():
 # (summaries under profiles/), per workload; None where not captured or the kernel changed since
 # vortex256: captured on the same kernels over 64x64 elements (p = 4) and scaled by the element
 # count (x16) where the traffic is per element (factorisation, products, Jacobian)
-NCU_TRAFFIC_BYTES = {"vortex256": {"k_inverse_tc": 16 * (165.62e6 + 109.38e6),
-                                   "k_products_tc": 16 * (584.50e6 + 209.42e6),
+NCU_TRAFFIC_BYTES = {"vortex256": {"k_inverse_tc": 16 * (165.51e6 + 109.29e6),
+                                   "k_products_tc": 16 * (539.59e6 + 209.25e6),
                                    "k_inverse_rq": 16 * (169.68e6 + 109.01e6),
                                    "k_products_x": 16 * (299.90e6 + 101.01e6),
                                    "k_products_s": 16 * (372.94e6 + 85.81e6),
-                                   "k_jacobian": 16 * (80.64e6 + 531.57e6)},
+                                   "k_jacobian": 16 * (82.50e6 + 528.51e6)},
                      "vortex64": {}}
 
 

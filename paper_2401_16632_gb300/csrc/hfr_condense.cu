@@ -1593,13 +1593,18 @@ __global__ void __launch_bounds__(256, 1) k_products_tc(const __grid_constant__ 
     __syncthreads();
     if (issuer && lane == 0) {
       tc_issue<NA, NT>(tmem, Ahi, Alo, Bhi, Blo, idesc_tf32(128, Sh::N1), smem_u32(mbar), a.tc_mode != 3);
-      // L2 prefetch two elements ahead: the next element's operands are loaded in this iteration
+      // L2 prefetch of the operands one load-phase ahead: the factor and B two elements ahead (the
+      // next element's are loaded into registers in this iteration), C and D one element ahead
+      // (this element's are read in this iteration); farther ahead overflows the L2 (measured)
       if (kn + G < a.Eim) {
         const size_t o = (size_t)kn + G;
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<const float*>(a.LU) + o * NA * NA),
                      "r"((unsigned)(NA * NA * 4)) : "memory");
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<const float*>(a.B) + o * NA * NT),
                      "r"((unsigned)(NA * NT * 4)) : "memory");
+      }
+      if (kn < a.Eim) {
+        const size_t o = (size_t)kn;
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<const float*>(a.C) + o * NT * NA),
                      "r"((unsigned)(NT * NA * 4)) : "memory");
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<const float*>(a.D) + o * NT * NT),
