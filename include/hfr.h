@@ -12,6 +12,9 @@
  *   hfr_backsolve       Sec. 3.2 eq. (localproblems), du_k = A_k^{-1}(r_k - B_k du^_k)
  *   imex_stage          Sec. 3.1 eqs. (9oind, 23nffsd) inside Algorithm 1 (alg:imex) with the
  *                       domain split of Sec. 4 (eq. explicitimex)
+ *   imex_steps          Algorithm 1 over whole steps, the Jacobian optionally kept across steps
+ *                       as in Sec. 5 (turbulent cylinder: refreshed every 100 steps)
+ *   fr_modal_filter     Appendix B (modal filter of the EDAC runs)
  *
  * Conventions
  *   - Every array argument is a DEVICE pointer owned by the caller unless it is marked
