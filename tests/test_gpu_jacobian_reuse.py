@@ -139,3 +139,45 @@ def test_kept_jacobian_steps_conserve_across_the_interface():
     m0 = np.einsum("s,es,esv->v", W, d.geo.J, u0)
     m1 = np.einsum("s,es,esv->v", W, d.geo.J, u.cpu().numpy())
     assert np.abs(m1 - m0).max() < 1e-10 * np.abs(m0).max() + 1e-12
+
+
+def _band_advdiff(n=8, p=2):
+    imp = np.zeros((n, n), bool)
+    imp[n // 2 - 1:n // 2 + 1, :] = True
+    mesh = structured_quads(uniform_nodes(n, 0, 1), uniform_nodes(n, 0, 1), p=p, implicit=imp.reshape(-1))
+    xy = sample_points(mesh, p)
+    u0 = np.exp(-20 * ((xy[..., 0] - 0.5) ** 2 + (xy[..., 1] - 0.4) ** 2))[..., None]
+    phys = {"kind": "advdiff", "beta": (1.0, 0.5), "nu": 0.01, "lref": 1.0}
+    return mesh, u0, phys
+
+
+@pytest.mark.parametrize("policy", ["every", "keep"])
+def test_backward_euler_steps_match_the_oracle(policy):
+    """imex_steps with backward Euler / ARS(1,2,1) on an IMEX band (advection-diffusion): two steps
+    against the oracle's two steps, under exact Newton and with the Jacobian kept."""
+    mesh, u0, phys = _band_advdiff()
+    d = Discretisation(mesh, make_physics(phys))
+    dt = 0.01
+    U, uh = u0, d.initial_trace(u0)
+    for _ in range(2):
+        U, uh, _ = imex_step(d, U, uh, dt, "be", tol=1e-13)
+    ctx = pkg.Context(mesh, phys, precision=pkg.FR_PREC_FP64, tableau=pkg.FR_TAB_BE)
+    if policy == "keep":
+        ctx.imex_set_jacobian_policy(pkg.FR_JAC_KEEP)
+    u, _, st = _steps(ctx, u0, 2, dt, newton_tol=1e-13, newton_maxit=80, gmres_rtol=1e-14, gmres_maxit=3000)
+    assert st["converged"] and st["steps"] == 2
+    # linear problem: exact Newton converges in one iteration per stage; kept blocks stay exact
+    assert st["jacobian_refreshes"] == (st["newton_iterations"] if policy == "every" else 1)
+    inc = np.abs(U - u0).max()
+    assert np.abs(u.cpu().numpy() - U).max() < 1e-10 * inc
+
+
+def test_single_pass_tf32_mode_needs_the_fp32_tensor_core_path():
+    w = make_config("vortex", n=3, p=2, re=500.0)
+    ctx = pkg.Context(w.mesh, w.physics, precision=pkg.FR_PREC_FP64, tableau=pkg.FR_TAB_SDIRK2)
+    with pytest.raises(pkg.HfrError) as ei:
+        ctx.hfr_condense_set_mode(pkg.FR_CONDENSE_TENSOR_TF32)
+    assert ei.value.code == pkg.FR_ERR_UNSUPPORTED
+    with pytest.raises(pkg.HfrError) as ei:
+        ctx.hfr_condense_set_mode(9)
+    assert ei.value.code == pkg.FR_ERR_INVALID_ARG
