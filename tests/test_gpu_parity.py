@@ -65,6 +65,7 @@ CASES = {
     "vortex_skew_p3": lambda: (lambda w: (w.mesh, w.u0, w.physics))(make_config("vortex", n=5, p=3, jitter=0.15, seed=9, re=200.0)),
     "vortex_p2": lambda: (lambda w: (w.mesh, w.u0, w.physics))(make_config("vortex", n=4, p=2, re=500.0)),
     "vortex_p4": lambda: (lambda w: (w.mesh, w.u0, w.physics))(make_config("vortex", n=3, p=4, re=500.0)),
+    "vortex_p5": lambda: (lambda w: (w.mesh, w.u0, w.physics))(make_config("vortex", n=3, p=5, re=500.0)),
     "band_advdiff": lambda: _band(8, 2, "advdiff"),
     "band_ns": lambda: _band(6, 3, "ns"),
 }
@@ -120,7 +121,7 @@ def _blocks_both(name, precision, a_dt=0.037):
 
 
 @pytest.mark.parametrize("name", ["advdiff8", "advdiff_skew_p3", "vortex_skew_p3", "vortex_p2", "vortex_p4",
-                                  "band_advdiff", "band_ns"])
+                                  "vortex_p5", "band_advdiff", "band_ns"])
 def test_element_blocks_fp64(name):
     ctx, d, u0, uh, ustar, a_dt, blocks = _blocks_both(name, pkg.FR_PREC_FP64)
     for key, ref in zip("ABCD", blocks):
@@ -135,7 +136,7 @@ def test_element_blocks_fp64(name):
     assert _rel(ctx.hfr_export("s").cpu().numpy(), s_ref) < 1e-11
 
 
-@pytest.mark.parametrize("name", ["vortex_skew_p3", "vortex_p4", "band_ns"])
+@pytest.mark.parametrize("name", ["vortex_skew_p3", "vortex_p4", "vortex_p5", "band_ns"])
 def test_element_blocks_and_condense_fp32(name):
     ctx, d, u0, uh, ustar, a_dt, blocks = _blocks_both(name, pkg.FR_PREC_FP32)
     for key, ref in zip("ABCD", blocks):
