@@ -25,6 +25,11 @@ section / equation it follows:
                    residual, and the monolithic global Jacobian.
 * ``solve``     -- static condensation, assembly, GMRES and back-substitution
                    (Sec. 3.2, eqs. assembly, assembly2, localproblems).
+* ``fr_mixed``  -- the FR / HFR residual and trace residual on meshes whose elements
+                   carry different degrees (Sec. 3.2, p-adaptive meshes): face points
+                   of the higher degree, L2 projection of face jumps back to each side.
+* ``blocks_mixed`` -- element blocks of uneven shapes on such meshes and the condensed
+                   Newton step, checked against the monolithic step.
 * ``stepping``  -- Newton on the DIRK stage equations (eqs. 9oind, 23nffsd), the
                    SDIRK2 and IMEX tableaux (Table butcherimex) and the IMEX step
                    (Algorithm 1, eqs. explicitimex, hfrimex).
