@@ -25,6 +25,9 @@ section / equation it follows:
                    residual, and the monolithic global Jacobian.
 * ``solve``     -- static condensation, assembly, GMRES and back-substitution
                    (Sec. 3.2, eqs. assembly, assembly2, localproblems).
+* ``efr``       -- interior-embedded FR (Sec. 2.2): the trace continuous on the implicit
+                   skeleton at GLL face points, its transmission conditions, and the
+                   condensed and monolithic Newton steps.
 * ``fr_mixed``  -- the FR / HFR residual and trace residual on meshes whose elements
                    carry different degrees (Sec. 3.2, p-adaptive meshes): face points
                    of the higher degree, L2 projection of face jumps back to each side.

@@ -47,6 +47,26 @@ def gauss_legendre(n: int):
     return x[order], w[order]
 
 
+def gauss_lobatto(n: int):
+    """n-point Gauss-Lobatto-Legendre nodes (ascending, n >= 2) and weights: x = -1, +1 and the
+    roots of P'_{n-1}, found by Newton's method with P''_m from Legendre's equation
+    (1 - x^2) P''_m = 2 x P'_m - m (m + 1) P_m, started at cos(pi i / (n - 1));
+    weights w_i = 2 / (n (n - 1) P_{n-1}(x_i)^2)."""
+    m = n - 1
+    x = -np.cos(np.pi * np.arange(1, m) / m)
+    for _ in range(100):
+        if x.size == 0:
+            break
+        P, dP = legendre(m, x)
+        dx = (1.0 - x * x) * dP / (2.0 * x * dP - m * (m + 1) * P)
+        x = x - dx
+        if np.max(np.abs(dx)) < 1e-16:
+            break
+    x = np.concatenate([[-1.0], np.sort(x), [1.0]])
+    P, _ = legendre(m, x)
+    return x, 2.0 / (n * m * P * P)
+
+
 def lagrange(nodes: np.ndarray, x) -> np.ndarray:
     """Matrix L[k, j] = l_j(x_k) of the Lagrange basis on ``nodes``."""
     x = np.atleast_1d(np.asarray(x, dtype=np.float64))

@@ -1,0 +1,284 @@
+"""Interior-embedded FR (EFR): the hybridized residual with a trace that is continuous on the
+implicit skeleton (Sec. 2.2; Secs. 4-5 pair it with explicit FR).  Test infrastructure: plain
+FP64, only ``tests/`` use it.
+
+The paper fixes: trace nodal basis continuous across interior faces, placed at the
+Gauss-Lobatto-Legendre (GLL) points of each face; Gauss solution points; tensor-product
+correction functions as for HFR, with an extra interpolation in the lift because face and flux
+points differ; discontinuous (no) traces on the IMEX interface, which carries the FR flux.  It
+defers the rest to its EFR reference.  Readings used here:
+
+* trace unknowns: one node per vertex of the implicit skeleton (vertices joined through trace
+  faces are one node) and the p - 1 interior GLL points of every trace face;
+* on a trace face each side evaluates its state, gradient, one-sided flux
+  F^ = F(u^) + s (u_f - u^) n - F^v(u^, q_f) (eq. hfrriemann) and J_f at the GLL points; the
+  element's own state and gradient there are its polynomials evaluated at those points
+  (interpolation along the face from its Gauss-aligned face values);
+* the lift works at the element's Gauss-aligned face points: the GLL values of J_f F^.n and of
+  the gradient jump u^ - u_f are interpolated there (degree-p Lagrange interpolation, exact for
+  the element's own polynomials) before the DG-recovering corrections spread them;
+* transmission condition of node i: g_i = sum over the trace faces f that carry node i and over
+  both sides of w^GLL_q J_f,q (F^.n)_q at the face point q of node i, the GLL rule applied to
+  the nodal basis function of i (collocated).  Summed over all nodes this is the face integral
+  of the interpolated flux jump, so the implicit region is conservative as a whole, as the paper
+  states for EFR, while single elements are not.
+
+Element-local trace layout is that of HFR (4 faces x (p+1) points x nv, a corner node appearing
+once on each of its two faces); the condensed system gathers both copies into one unknown.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from .basis import gauss_lobatto, lagrange
+from .blocks import element_blocks, EPS
+from .fr import Discretisation, IMEX_FACE, TRACE_FACE
+from .geometry import FACES_2D, _adjugate, _bilinear_derivs
+from .physics import cmax
+from .solve import condense, backsolve
+
+# corners (a + 2 b in the element's vertex order) at the first and last point of each face
+FACE_CORNERS = ((0, 2), (1, 3), (0, 1), (2, 3))
+
+
+class EmbeddedDiscretisation(Discretisation):
+    """EFR operators for a quad mesh with a single polynomial degree p >= 1."""
+
+    def __init__(self, mesh, physics):
+        super().__init__(mesh, physics)
+        n = self.n
+        self.xl, self.wl = gauss_lobatto(n)
+        self.IGL = lagrange(self.ref.x, self.xl)  # (GLL point q, Gauss-aligned point m)
+        self.ILG = lagrange(self.xl, self.ref.x)  # (Gauss-aligned point m, GLL point q)
+        self._gll_geometry()
+        self._number_nodes()
+
+    def _gll_geometry(self):
+        """Scaled normal, J_f and unit normal at the GLL points of every element face (the faces of
+        a bilinear element are straight, so these equal their values at the flux points)."""
+        verts = self.mesh.verts
+        E, n = verts.shape[0], self.n
+        NfL = np.zeros((E, 4, n, 2))
+        for f, (r, sg) in enumerate(FACES_2D):
+            fx, fe = (np.full(n, sg), self.xl) if r == 0 else (self.xl, np.full(n, sg))
+            a, b = _bilinear_derivs(verts, fx, fe)
+            _, Sf = _adjugate(a, b)
+            NfL[:, f] = sg * Sf[:, :, r, :]
+        self.JfL = np.sqrt(np.sum(NfL**2, axis=-1))
+        self.normalL = NfL / self.JfL[..., None]
+
+    def _number_nodes(self):
+        """node_of (E, 4, n): the global trace node at each GLL point of each element face
+        (-1 off trace faces).  Vertex nodes first (in increasing smallest element corner), then
+        the interior points of trace face t at nvert + t (p - 1) + m - 1."""
+        m = self.mesh
+        E, n = m.nelem, self.n
+        parent = np.arange(4 * E)
+
+        def find(i):
+            while parent[i] != i:
+                parent[i] = parent[parent[i]]
+                i = parent[i]
+            return i
+
+        touched = set()
+        for e in range(E):
+            for f in range(4):
+                if self.kind[e, f] != TRACE_FACE:
+                    continue
+                nb, nf = m.nbr[e, f], m.nbr_face[e, f]
+                for end in range(2):
+                    i, j = 4 * e + FACE_CORNERS[f][end], 4 * nb + FACE_CORNERS[nf][end]
+                    touched.update((i, j))
+                    ri, rj = find(i), find(j)
+                    if ri != rj:
+                        parent[max(ri, rj)] = min(ri, rj)
+        roots = sorted({find(i) for i in touched})
+        vid = {r: k for k, r in enumerate(roots)}
+        self.nvert = len(roots)
+        self.nnode = self.nvert + self.ntrace * (n - 2)
+        node_of = -np.ones((E, 4, n), dtype=np.int64)
+        for e in range(E):
+            for f in range(4):
+                t = self.tr_of[e, f]
+                if t < 0:
+                    continue
+                node_of[e, f, 0] = vid[find(4 * e + FACE_CORNERS[f][0])]
+                node_of[e, f, n - 1] = vid[find(4 * e + FACE_CORNERS[f][1])]
+                node_of[e, f, 1:n - 1] = self.nvert + t * (n - 2) + np.arange(n - 2)
+        self.node_of = node_of
+
+    # ----------------------------------------------------------------- residual
+    def residual(self, U, uhat_view):
+        """R(u, u^) at every element and J_f F^.n at every element face point: at the GLL
+        points on trace faces, at the Gauss-aligned flux points elsewhere.
+
+        U (E, Ns, nv); uhat_view (E, 4, n, nv) the trace at the GLL points of each element face
+        (read on trace faces only).  Returns R (E, Ns, nv) and Fn (E, 4, n, nv)."""
+        ph = self.phys
+        geo = self.geo
+        kind = self.kind[:, :, None, None]
+        trace = kind == TRACE_FACE
+        imp_e = self.imp[:, None, None, None]
+        Uf = self.interp_faces(U)
+        Uf_nb = self.neighbour(Uf)
+        UfL = np.einsum("qm,efm...->efq...", self.IGL, Uf)
+        if ph.viscous:
+            q = self.corrected_gradient(U, uhat_view)
+            qf = self.interp_faces(q)
+            qf_nb = self.neighbour(qf)
+            qfL = np.einsum("qm,efm...->efq...", self.IGL, qf)
+            F = ph.conv(U) - ph.visc(U, q)
+        else:
+            F = ph.conv(U)
+        Ft = np.einsum("esrc,escv->esrv", geo.S, F)
+        Ftf = self.interp_faces(Ft)
+        FDn = np.empty_like(Uf)
+        for f, (r, sg) in enumerate(FACES_2D):
+            FDn[:, f] = sg * Ftf[:, f, :, r, :]
+
+        def dotn(Fx, nrm):
+            return np.einsum("...cv,...c->...v", Fx, nrm)
+
+        # FR and IMEX-interface faces: the uniform operator's fluxes at the flux points
+        nrm = geo.normal
+        lam = cmax(ph.wave_speed(Uf, nrm), ph.wave_speed(Uf_nb, nrm))
+        Fr = 0.5 * dotn(ph.conv(Uf) + ph.conv(Uf_nb), nrm) + 0.5 * lam[..., None] * (Uf - Uf_nb)
+        if ph.viscous:
+            Fr_fr = Fr - 0.5 * dotn(ph.visc(Uf, qf) + ph.visc(Uf_nb, qf_nb), nrm)
+            U_im = np.where(imp_e, Uf, Uf_nb)
+            q_im = np.where(imp_e[..., None], qf, qf_nb)
+            Fr_im = Fr - dotn(ph.visc(U_im, q_im), nrm)
+        else:
+            Fr_fr = Fr_im = Fr
+        FnG = geo.Jf[..., None] * np.where(kind == IMEX_FACE, Fr_im, Fr_fr)
+        # trace faces: one-sided flux at the GLL points (faces without a trace evaluate it at a
+        # harmless state and discard it)
+        nrmL = self.normalL
+        uh = np.where(trace, uhat_view, UfL)
+        Fh = dotn(ph.conv(uh), nrmL) + ph.stab(uh, nrmL)[..., None] * (UfL - uh)
+        if ph.viscous:
+            Fh = Fh - dotn(ph.visc(uh, qfL), nrmL)
+        FnL = self.JfL[..., None] * Fh
+        FnL_G = np.einsum("mq,efq...->efm...", self.ILG, FnL)
+        H = np.where(trace, FnL_G, FnG) - FDn
+        dxi, deta = self.ref_derivative(Ft)
+        cx, cy = self.lift(H, signed=True)
+        R = -(dxi[:, :, 0] + deta[:, :, 1] + cx + cy) / geo.J[:, :, None]
+        return R, np.where(trace, FnL, FnG)
+
+    def corrected_gradient(self, U, uhat_view):
+        """Physical gradient q (E, Ns, 2, nv): the reference gradient of u^D plus the lifted jumps
+        u_bar - u_f, taken on trace faces at the GLL points (u_bar = u^) and interpolated to the
+        Gauss-aligned points, on the other faces as in the uniform operator."""
+        geo = self.geo
+        kind = self.kind[:, :, None, None]
+        imp_e = self.imp[:, None, None, None]
+        Uf = self.interp_faces(U)
+        Uf_nb = self.neighbour(Uf)
+        UfL = np.einsum("qm,efm...->efq...", self.IGL, Uf)
+        jump = np.einsum("mq,efq...->efm...", self.ILG, uhat_view - UfL)
+        jump = np.where(kind == TRACE_FACE, jump, 0.5 * (Uf_nb - Uf))
+        jump = np.where(kind == IMEX_FACE, np.where(imp_e, Uf_nb - Uf, 0.0 * Uf), jump)
+        dxi, deta = self.ref_derivative(U)
+        cx, cy = self.lift(jump, signed=False)
+        Qr = np.stack([dxi + cx, deta + cy], axis=2)
+        return np.einsum("esrc,esrv->escv", geo.S, Qr) / geo.J[:, :, None, None]
+
+    # ------------------------------------------------------------ trace helpers
+    def trace_view(self, uhat):
+        """Global trace (nnode, nv) -> per element face GLL point (E, 4, n, nv); zero off trace."""
+        view = np.zeros(self.node_of.shape + (self.nv,), dtype=uhat.dtype)
+        has = self.node_of >= 0
+        view[has] = uhat[self.node_of[has]]
+        return view
+
+    def trace_weights(self, Fn):
+        """Element contribution w^GLL_q Fn to the transmission conditions, zero off trace."""
+        gv = self.wl[None, None, :, None] * Fn
+        return np.where((self.kind == TRACE_FACE)[:, :, None, None], gv, 0.0)
+
+    def assemble_trace(self, gview):
+        """Sum element-face-point contributions (E, 4, n, nv) into the nodes (nnode, nv)."""
+        g = np.zeros((self.nnode, self.nv), dtype=gview.dtype)
+        has = self.node_of >= 0
+        np.add.at(g, self.node_of[has], gview[has])
+        return g
+
+    def initial_trace(self, U):
+        """Average, over every element face that carries a node, of that side's state there."""
+        UfL = np.einsum("qm,efm...->efq...", self.IGL, self.interp_faces(U))
+        has = self.node_of >= 0
+        acc = np.zeros((self.nnode, self.nv))
+        cnt = np.zeros(self.nnode)
+        np.add.at(acc, self.node_of[has], UfL[has])
+        np.add.at(cnt, self.node_of[has], 1.0)
+        return acc / cnt[:, None]
+
+    def full_residual(self, U, uhat):
+        """R (E, Ns, nv) and the transmission residual g (nnode, nv)."""
+        R, Fn = self.residual(U, self.trace_view(uhat))
+        return R, self.assemble_trace(self.trace_weights(Fn))
+
+    def trace_dof_map(self):
+        """(E, 4 n nv) global trace unknown of each element trace unknown, -1 off trace."""
+        nv = self.nv
+        idx = self.node_of[..., None] * nv + np.arange(nv)
+        idx = np.where(self.node_of[..., None] >= 0, idx, -1)
+        return idx.reshape(self.mesh.nelem, -1)
+
+
+def condensed_newton_step(d, U, uhat, Ustar, a_dt):
+    """One Newton step of the EFR stage equations by static condensation (Sec. 3.2): per element
+    S_k, t_k; L = sum_k P_k^T S_k P_k with P_k gathering the element's face points from the
+    nodes (both copies of a corner node sum); direct solve; back-substitution.
+    Returns (dU (E, Ns, nv) zero on explicit elements, duhat (nnode, nv))."""
+    imp = d.imp_idx
+    nA, nT = d.ns * d.nv, 4 * d.n * d.nv
+    R, Fn = d.residual(U, d.trace_view(uhat))
+    gv = d.trace_weights(Fn)
+    h = U[imp] - Ustar[imp] - a_dt * R[imp]
+    A, B, C, D = element_blocks(d, U, uhat, a_dt)
+    XB, xr, S, t = condense(A[imp], B[imp], C[imp], D[imp], -h.reshape(-1, nA),
+                            -gv[imp].reshape(-1, nT))
+    idx = d.trace_dof_map()[imp]
+    N = d.nnode * d.nv
+    rows = np.repeat(idx[:, :, None], nT, axis=2)
+    cols = np.repeat(idx[:, None, :], nT, axis=1)
+    ok = (rows >= 0) & (cols >= 0)
+    L = sp.coo_matrix((S[ok], (rows[ok], cols[ok])), shape=(N, N)).tocsc()
+    rhs = np.zeros(N)
+    np.add.at(rhs, idx[idx >= 0], t[idx >= 0])
+    duh = spla.spsolve(L, rhs).reshape(d.nnode, d.nv)
+    du = backsolve(XB, xr, d.trace_view(duh)[imp].reshape(len(imp), nT))
+    dU = np.zeros_like(U)
+    dU[imp] = du.reshape(len(imp), d.ns, d.nv)
+    return dU, duh
+
+
+def monolithic_newton_step(d, U, uhat, Ustar, a_dt):
+    """The same Newton step from the dense Jacobian of [h; g] in [u_implicit; u^] (tiny meshes)."""
+    imp = d.imp_idx
+    nA = d.ns * d.nv
+    nu, nh = len(imp) * nA, d.nnode * d.nv
+    Jm = np.zeros((nu + nh, nu + nh))
+    Uc, Hc = U.astype(np.complex128), uhat.astype(np.complex128)
+    for col in range(nu + nh):
+        Up, Hp = Uc.copy(), Hc.copy()
+        if col < nu:
+            k, j = divmod(col, nA)
+            Up[imp[k]].reshape(-1)[j] += 1j * EPS
+        else:
+            Hp.reshape(-1)[col - nu] += 1j * EPS
+        R, g = d.full_residual(Up, Hp)
+        Jm[:nu, col] = (Up[imp] - a_dt * R[imp]).imag.reshape(-1) / EPS
+        Jm[nu:, col] = g.imag.reshape(-1) / EPS
+    R, g = d.full_residual(U, uhat)
+    rhs = -np.concatenate([(U[imp] - Ustar[imp] - a_dt * R[imp]).reshape(-1), g.reshape(-1)])
+    x = np.linalg.solve(Jm, rhs)
+    dU = np.zeros_like(U)
+    dU[imp] = x[:nu].reshape(len(imp), d.ns, d.nv)
+    return dU, x[nu:].reshape(d.nnode, d.nv)
