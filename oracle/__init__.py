@@ -25,6 +25,8 @@ section / equation it follows:
                    residual, and the monolithic global Jacobian.
 * ``solve``     -- static condensation, assembly, GMRES and back-substitution
                    (Sec. 3.2, eqs. assembly, assembly2, localproblems).
+* ``boundary``  -- boundary faces: hybridized no-slip adiabatic walls and far field (eq. hfr2's
+                   boundary term), FR ghost state on explicit far-field faces.
 * ``efr``       -- interior-embedded FR (Sec. 2.2): the trace continuous on the implicit
                    skeleton at GLL face points, its transmission conditions, and the
                    condensed and monolithic Newton steps.
