@@ -30,6 +30,9 @@ section / equation it follows:
 * ``efr``       -- interior-embedded FR (Sec. 2.2): the trace continuous on the implicit
                    skeleton at GLL face points, its transmission conditions, and the
                    condensed and monolithic Newton steps.
+* ``fr3d``      -- the FR / HFR residual, blocks and condensed / monolithic Newton steps on
+                   hexahedra (trilinear map, six faces of (p+1)^2 points; Sec. 5.3's 3D
+                   cases), with ``physics.NavierStokes3D``.
 * ``fr_mixed``  -- the FR / HFR residual and trace residual on meshes whose elements
                    carry different degrees (Sec. 3.2, p-adaptive meshes): face points
                    of the higher degree, L2 projection of face jumps back to each side.

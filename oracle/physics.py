@@ -126,6 +126,67 @@ class NavierStokes2D:
         return self.wave_speed(uh, n) + self.mu / (uh[..., 0] * self.lref)
 
 
+class NavierStokes3D:
+    """The Navier-Stokes readings above in three dimensions: u = (rho, rho v_x, rho v_y, rho v_z, E),
+    p = (gamma - 1)(E - rho |v|^2 / 2), tau = mu (grad v + grad v^T - 2/3 div v I), heat flux
+    kappa grad T with T = p / rho."""
+
+    nv = 5
+
+    def __init__(self, gamma=1.4, mu=5e-5, Pr=0.72, lref=1.0):
+        self.gamma = float(gamma)
+        self.mu = float(mu)
+        self.Pr = float(Pr)
+        self.lref = float(lref)
+        self.viscous = self.mu != 0.0
+
+    def primitives(self, u):
+        rho = u[..., 0]
+        v = u[..., 1:4] / rho[..., None]
+        p = (self.gamma - 1.0) * (u[..., 4] - 0.5 * rho * np.sum(v * v, axis=-1))
+        return rho, v, p
+
+    def conv(self, u):
+        rho, v, p = self.primitives(u)
+        E = u[..., 4]
+        F = np.empty(u.shape[:-1] + (3, 5), dtype=u.dtype)
+        for d in range(3):
+            F[..., d, 0] = rho * v[..., d]
+            for k in range(3):
+                F[..., d, 1 + k] = rho * v[..., d] * v[..., k] + (p if k == d else 0.0)
+            F[..., d, 4] = (E + p) * v[..., d]
+        return F
+
+    def visc(self, u, q):
+        g = self.gamma
+        rho, v, p = self.primitives(u)
+        E = u[..., 4]
+        # dv[..., c, k] = d v_k / d x_c, dT[..., c] from the conserved-variable gradients
+        dv = (q[..., :, 1:4] - v[..., None, :] * q[..., :, :1]) / rho[..., None, None]
+        dT = (g - 1.0) * ((q[..., :, 4] - (E / rho)[..., None] * q[..., :, 0]) / rho[..., None]
+                          - np.einsum("...k,...ck->...c", v, dv))
+        div = dv[..., 0, 0] + dv[..., 1, 1] + dv[..., 2, 2]
+        mu = self.mu
+        kappa = mu * g / ((g - 1.0) * self.Pr)
+        F = np.zeros(u.shape[:-1] + (3, 5), dtype=np.result_type(u, q))
+        for c in range(3):
+            for k in range(3):
+                F[..., c, 1 + k] = mu * (dv[..., c, k] + dv[..., k, c] - (2.0 / 3.0 * div if c == k else 0.0))
+            F[..., c, 4] = np.einsum("...k,...k->...", v, F[..., c, 1:4]) + kappa * dT[..., c]
+        return F
+
+    def sound_speed(self, u):
+        rho, _, p = self.primitives(u)
+        return np.sqrt(self.gamma * p / rho)
+
+    def wave_speed(self, u, n):
+        _, v, _ = self.primitives(u)
+        return cabs(np.einsum("...c,...c->...", v, n)) + self.sound_speed(u)
+
+    def stab(self, uh, n):
+        return self.wave_speed(uh, n) + self.mu / (uh[..., 0] * self.lref)
+
+
 class EDAC2D:
     """Entropically damped artificial compressibility (Appendix A): u = (P, v_x, v_y),
     F^c_i = (v_i (P + Theta), v_i v_x + P delta_ix, v_i v_y + P delta_iy), F^v_i = nu du/dx_i,
@@ -174,6 +235,8 @@ def make_physics(spec: dict):
         return AdvectionDiffusion(spec["beta"], spec["nu"], spec.get("lref", 1.0))
     if kind == "ns":
         return NavierStokes2D(spec["gamma"], spec["mu"], spec["Pr"], spec.get("lref", 1.0))
+    if kind == "ns3d":
+        return NavierStokes3D(spec["gamma"], spec["mu"], spec["Pr"], spec.get("lref", 1.0))
     if kind == "edac":
         return EDAC2D(spec["theta"], spec["nu"], spec.get("lref", 1.0))
     raise KeyError(kind)

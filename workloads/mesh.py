@@ -175,3 +175,87 @@ def number_faces(nbr: np.ndarray, nbr_face: np.ndarray) -> np.ndarray:
                 face_of[nbr[e, f], nbr_face[e, f]] = nxt
             nxt += 1
     return face_of
+
+
+@dataclass
+class HexMesh:
+    """Structured hexahedral mesh: element e = i + nx (j + ny k); corner a + 2 b + 4 c at reference
+    (2a - 1, 2b - 1, 2c - 1); faces 0/1: xi = -1/+1, 2/3: eta = -1/+1, 4/5: zeta = -1/+1; the
+    points of a face are numbered along its two tangential axes in increasing axis order (the lower
+    axis fastest), the same from both sides."""
+
+    n: tuple
+    verts: np.ndarray  # (E, 8, 3)
+    nbr: np.ndarray  # (E, 6) neighbour element or -1
+    nbr_face: np.ndarray  # (E, 6)
+    bc: np.ndarray  # (E, 6) boundary tag
+    face_of: np.ndarray  # (E, 6)
+    implicit: np.ndarray  # (E,)
+    p: np.ndarray  # (E,)
+    period: tuple = (0.0, 0.0, 0.0)
+
+    @property
+    def nelem(self) -> int:
+        return int(self.verts.shape[0])
+
+    @property
+    def nface(self) -> int:
+        return int(self.face_of.max()) + 1
+
+    @property
+    def dim(self) -> int:
+        return 3
+
+
+def structured_hexes(xn, yn, zn, periodic=(True, False, True), jitter: float = 0.0, seed: int = 0,
+                     p=3, implicit=None, bc_y=(BC_WALL, BC_WALL)) -> HexMesh:
+    """Tensor-product hex mesh on node lines ``xn`` x ``yn`` x ``zn``; ``jitter`` displaces the
+    nodes interior to the unwrapped grid as in ``structured_quads`` (periodic copies together)."""
+    nodes = [np.asarray(v, dtype=np.float64) for v in (xn, yn, zn)]
+    N = [len(v) - 1 for v in nodes]
+    X = np.stack(np.meshgrid(*nodes, indexing="ij"), axis=-1)  # (nx+1, ny+1, nz+1, 3)
+    if jitter > 0.0:
+        rng = np.random.default_rng(seed)
+        h = np.array([np.diff(v).min() for v in nodes])
+        dX = rng.uniform(-jitter, jitter, size=X.shape) * h
+        for ax in range(3):
+            sl_lo = [slice(None)] * 3
+            sl_hi = [slice(None)] * 3
+            sl_lo[ax], sl_hi[ax] = 0, N[ax]
+            if periodic[ax]:
+                dX[tuple(sl_hi)] = dX[tuple(sl_lo)]
+            else:
+                dX[tuple(sl_lo)] = 0.0
+                dX[tuple(sl_hi)] = 0.0
+        X = X + dX
+    nx, ny, nz = N
+    E = nx * ny * nz
+    verts = np.zeros((E, 8, 3))
+    nbr = -np.ones((E, 6), dtype=np.int32)
+    nbr_face = -np.ones((E, 6), dtype=np.int32)
+    bc = np.zeros((E, 6), dtype=np.int32)
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                e = i + nx * (j + ny * k)
+                for c in range(2):
+                    for b in range(2):
+                        for a in range(2):
+                            verts[e, a + 2 * b + 4 * c] = X[i + a, j + b, k + c]
+                ijk = [i, j, k]
+                for ax in range(3):
+                    for side, step in ((0, -1), (1, 1)):
+                        f = 2 * ax + side
+                        nn = list(ijk)
+                        nn[ax] += step
+                        if 0 <= nn[ax] < N[ax] or periodic[ax]:
+                            nn[ax] %= N[ax]
+                            nbr[e, f] = nn[0] + nx * (nn[1] + ny * nn[2])
+                            nbr_face[e, f] = 2 * ax + 1 - side
+                        else:
+                            bc[e, f] = bc_y[side] if ax == 1 else BC_FARFIELD
+    face_of = number_faces(nbr, nbr_face)
+    pe = np.full(E, p, dtype=np.int32) if np.isscalar(p) else np.asarray(p, dtype=np.int32)
+    imp = np.ones(E, dtype=bool) if implicit is None else np.asarray(implicit, dtype=bool)
+    period = tuple(float(v[-1] - v[0]) if per else 0.0 for v, per in zip(nodes, periodic))
+    return HexMesh(tuple(N), verts, nbr, nbr_face, bc, face_of, imp, pe, period)
