@@ -17,8 +17,6 @@ from __future__ import annotations
 
 import numpy as np
 
-from .fr import TRACE_FACE
-
 EPS = 1.0e-30
 
 
@@ -42,7 +40,7 @@ def _elem_trace_layout(m, e):
     out, o = [], 0
     for f in range(4):
         k = int(m.nf[e, f])
-        t = int(m.tr_of[e, f]) if m.kind[e, f] == TRACE_FACE else -1
+        t = int(m.tr_of[e, f])
         out.append((f, t, k, o))
         o += k * m.nv
     return out, o

@@ -17,7 +17,9 @@ uniform-degree operator of ``oracle.fr`` when all degrees agree:
 * the discontinuous flux at a face point is the element's flux polynomial there (interpolation of
   the transformed flux from its solution points), as in the uniform operator.
 
-Face kinds, common fluxes and viscous readings are those of ``oracle.fr``.
+Face kinds, common fluxes and viscous readings are those of ``oracle.fr``; boundary faces (walls,
+far field) follow ``oracle.boundary``: a boundary face carries the element's own point count, a
+trace when its element is implicit, and the wall / far-field trace rows there.
 """
 
 from __future__ import annotations
@@ -25,20 +27,21 @@ from __future__ import annotations
 import numpy as np
 
 from .basis import RefElement1D, gauss_legendre, lagrange
+from .boundary import FARFIELD_FACE, WALL_FACE
 from .fr import FR_FACE, IMEX_FACE, TRACE_FACE
 from .geometry import FACES_2D, _adjugate, _bilinear_derivs
-from .physics import cmax
+from .physics import NavierStokes2D, cmax
+from workloads.mesh import BC_FARFIELD, BC_WALL
 
 
 class MixedDiscretisation:
     """FR/HFR operators element by element for a quad mesh with per-element degrees."""
 
-    def __init__(self, mesh, physics):
-        if np.any(mesh.nbr < 0):
-            raise NotImplementedError("oracle: boundary faces not implemented")
+    def __init__(self, mesh, physics, u_inf=None):
         self.mesh = mesh
         self.phys = physics
         self.nv = physics.nv
+        self.u_inf = None if u_inf is None else np.asarray(u_inf, dtype=np.float64)
         E = mesh.nelem
         self.E = E
         self.p = np.asarray(mesh.p, dtype=np.int64)
@@ -46,22 +49,33 @@ class MixedDiscretisation:
         self.refs = {int(p): RefElement1D(int(p)) for p in np.unique(self.p)}
         imp = np.asarray(mesh.implicit, dtype=bool)
         self.imp = imp
+        bnd = mesh.nbr < 0
+        self.bnd = bnd
+        nbr = np.where(bnd, np.arange(E)[:, None], mesh.nbr)  # boundary faces point at themselves
         kind = np.full((E, 4), FR_FACE, dtype=np.int32)
-        for f in range(4):
-            nb = mesh.nbr[:, f]
-            kind[imp & imp[nb], f] = TRACE_FACE
-            kind[imp != imp[nb], f] = IMEX_FACE
+        kind[~bnd & imp[:, None] & imp[nbr]] = TRACE_FACE
+        kind[~bnd & (imp[:, None] != imp[nbr])] = IMEX_FACE
+        kind[bnd & (mesh.bc == BC_WALL)] = WALL_FACE
+        kind[bnd & (mesh.bc == BC_FARFIELD)] = FARFIELD_FACE
+        if np.any(bnd & ~np.isin(mesh.bc, (BC_WALL, BC_FARFIELD))):
+            raise ValueError("boundary face without a wall or far-field tag")
+        if np.any(kind == WALL_FACE) and (np.any((kind == WALL_FACE) & ~imp[:, None])
+                                          or not isinstance(physics, NavierStokes2D)):
+            raise NotImplementedError("oracle: walls on implicit Navier-Stokes elements only")
+        if np.any(kind == FARFIELD_FACE) and self.u_inf is None:
+            raise ValueError("far-field faces need u_inf")
         self.kind = kind
-        # face point count: the higher degree of the two sides
-        self.nf = np.maximum(self.n[:, None], self.n[mesh.nbr])  # (E, 4)
+        self.traced = (kind == TRACE_FACE) | (bnd & imp[:, None])
+        # face point count: the higher degree of the two sides (the own one on boundaries)
+        self.nf = np.maximum(self.n[:, None], self.n[nbr])  # (E, 4)
         self.rule = {int(m): gauss_legendre(int(m)) for m in np.unique(self.nf)}
-        # trace numbering as in oracle.fr: trace faces in increasing global face id
+        # trace numbering as in oracle.fr: faces with a trace in increasing global face id
         fid = mesh.face_of
-        trace_fids = np.unique(fid[kind == TRACE_FACE])
+        trace_fids = np.unique(fid[self.traced])
         tr_of_fid = -np.ones(mesh.nface, dtype=np.int64)
         tr_of_fid[trace_fids] = np.arange(len(trace_fids))
         self.ntrace = len(trace_fids)
-        self.tr_of = np.where(kind == TRACE_FACE, tr_of_fid[fid], -1)
+        self.tr_of = np.where(self.traced, tr_of_fid[fid], -1)
         self.trace_sides = -np.ones((self.ntrace, 2, 2), dtype=np.int64)
         for e in range(E):
             for f in range(4):
@@ -155,7 +169,9 @@ class MixedDiscretisation:
 
     # ------------------------------------------------------------------ residual
     def residual(self, U, uhat):
-        """R(u, u^) and J_f F^.n at every element face point.
+        """R(u, u^) and J_f times the element's trace row at every element face point: its normal
+        flux J_f F^.n on interior faces, the wall / far-field rows of ``oracle.boundary`` on
+        boundary faces of implicit elements.
 
         U: list of (Ns_e, nv) arrays; uhat: list over trace faces of (n_f, nv) arrays.
         Returns R (list of (Ns_e, nv)) and Fn (list over elements of 4 arrays (n_f, nv))."""
@@ -164,8 +180,11 @@ class MixedDiscretisation:
         E = self.E
         Uf = [[self.to_face(e, f, U[e]) for f in range(4)] for e in range(E)]
 
-        def other(X, e, f):
-            return X[m.nbr[e, f]][m.nbr_face[e, f]]
+        def other_state(e, f):
+            """The other side's state at the face points: the neighbour's, u_inf on far field."""
+            if self.kind[e, f] == FARFIELD_FACE:
+                return np.broadcast_to(self.u_inf, Uf[e][f].shape)
+            return Uf[m.nbr[e, f]][m.nbr_face[e, f]]
 
         def face_trace(e, f):
             return uhat[self.tr_of[e, f]]
@@ -176,12 +195,12 @@ class MixedDiscretisation:
                 jumps = []
                 for f in range(4):
                     k = self.kind[e, f]
-                    if k == TRACE_FACE:
+                    if self.traced[e, f]:
                         ubar = face_trace(e, f)
                     elif k == IMEX_FACE:
-                        ubar = other(Uf, e, f) if self.imp[e] else Uf[e][f]
+                        ubar = other_state(e, f) if self.imp[e] else Uf[e][f]
                     else:
-                        ubar = 0.5 * (Uf[e][f] + other(Uf, e, f))
+                        ubar = 0.5 * (Uf[e][f] + other_state(e, f))
                     jumps.append(ubar - Uf[e][f])
                 dxi, deta = self.ref_derivative(e, U[e])
                 cx, cy = self.lift(e, jumps, signed=False)
@@ -189,6 +208,11 @@ class MixedDiscretisation:
                 qe = np.einsum("src,srv->scv", self.S[e], Qr) / self.J[e][:, None, None]
                 q.append(qe)
                 qf.append([self.to_face(e, f, qe) for f in range(4)])
+
+        def other_grad(e, f):
+            """The other side's gradient: the neighbour's, the element's own on boundary faces."""
+            return qf[e][f] if self.bnd[e, f] else qf[m.nbr[e, f]][m.nbr_face[e, f]]
+
         R, Fn = [], []
         for e in range(E):
             F = ph.conv(U[e]) - ph.visc(U[e], q[e]) if ph.viscous else ph.conv(U[e])
@@ -196,31 +220,40 @@ class MixedDiscretisation:
             Fn_e, H = [], []
             for f, (ax, sg) in enumerate(FACES_2D):
                 nrm = self.normal[e, f]
+                Jf = self.Jf[e, f][:, None]
 
                 def dotn(Fx):
                     return np.einsum("qcv,qc->qv", Fx, nrm)
 
-                uf, un = Uf[e][f], other(Uf, e, f)
+                uf = Uf[e][f]
                 k = self.kind[e, f]
-                if k == TRACE_FACE:
+                if self.traced[e, f]:
                     uh = face_trace(e, f)
-                    Fhat = dotn(ph.conv(uh)) + ph.stab(uh, nrm)[:, None] * (uf - uh)
+                    s = ph.stab(uh, nrm)[:, None]
+                    Fhat = dotn(ph.conv(uh)) + s * (uf - uh)
                     if ph.viscous:
                         Fhat = Fhat - dotn(ph.visc(uh, qf[e][f]))
+                    if k == FARFIELD_FACE:
+                        row = Jf * s * ((uf - uh) + (self.u_inf - uh))
+                    elif k == WALL_FACE:
+                        row = Jf * np.concatenate([Fhat[:, :1], s * uh[:, 1:3], Fhat[:, 3:]], axis=1)
+                    else:
+                        row = Jf * Fhat
                 else:
+                    un = other_state(e, f)
                     lam = cmax(ph.wave_speed(uf, nrm), ph.wave_speed(un, nrm))
                     Fhat = 0.5 * dotn(ph.conv(uf) + ph.conv(un)) + 0.5 * lam[:, None] * (uf - un)
                     if ph.viscous:
-                        qn = other(qf, e, f)
+                        qn = other_grad(e, f)
                         if k == IMEX_FACE:
                             u_im, q_im = (uf, qf[e][f]) if self.imp[e] else (un, qn)
                             Fhat = Fhat - dotn(ph.visc(u_im, q_im))
                         else:
                             Fhat = Fhat - 0.5 * dotn(ph.visc(uf, qf[e][f]) + ph.visc(un, qn))
-                fn = self.Jf[e, f][:, None] * Fhat
+                    row = Jf * Fhat
                 FDn = sg * self.to_face(e, f, Ft)[:, ax, :]
-                Fn_e.append(fn)
-                H.append(fn - FDn)
+                Fn_e.append(row)
+                H.append(Jf * Fhat - FDn)
             dxi, _ = self.ref_derivative(e, Ft[:, 0])
             _, deta = self.ref_derivative(e, Ft[:, 1])
             cx, cy = self.lift(e, H, signed=True)
@@ -237,16 +270,26 @@ class MixedDiscretisation:
             acc = 0.0
             for s in range(2):
                 e, f = self.trace_sides[t, s]
-                acc = acc + w[:, None] * Fn[e][f]
+                if e >= 0:
+                    acc = acc + w[:, None] * Fn[e][f]
             g.append(acc)
         return g
 
     def initial_trace(self, U):
-        """Average of both sides' interpolated states at each trace face's points."""
+        """Average of both sides' interpolated states at each trace face's points (boundary faces as
+        in ``oracle.boundary``)."""
         out = []
         for t in range(self.ntrace):
             (e0, f0), (e1, f1) = self.trace_sides[t]
-            out.append(0.5 * (self.to_face(e0, f0, U[e0]) + self.to_face(e1, f1, U[e1])))
+            u0 = self.to_face(e0, f0, U[e0])
+            if e1 >= 0:
+                out.append(0.5 * (u0 + self.to_face(e1, f1, U[e1])))
+            elif self.kind[e0, f0] == FARFIELD_FACE:
+                out.append(0.5 * (u0 + self.u_inf))
+            else:  # wall: the element's density and energy, no momentum
+                u0 = u0.copy()
+                u0[:, 1:3] = 0.0
+                out.append(u0)
         return out
 
     def full_residual(self, U, uhat):

@@ -171,3 +171,109 @@ def test_condensed_newton_step_equals_the_monolithic_step(phys):
     assert scale > 1e-3
     assert np.abs(dh1 - dh2).max() < 1e-12 * scale
     assert max(np.abs(du1[e] - du2[e]).max() for e in du1) < 1e-12 * scale
+
+
+# ------------------------------------------------------------ boundary faces (config-4 shape)
+from oracle.blocks import EPS  # noqa: E402
+from oracle.boundary import BoundaryDiscretisation  # noqa: E402
+from workloads.mesh import BC_FARFIELD, BC_WALL, geometric_nodes  # noqa: E402
+
+NS_WALL = {"kind": "ns", "gamma": 1.4, "mu": 2e-2, "Pr": 0.72, "lref": 1.0}
+REST = np.array([1.2, 0.0, 0.0, 2.0])
+U_INF = np.array([1.0, 0.3, 0.05, 2.6])
+
+
+def _bl_mesh(nx, degrees, imp_rows, bc_y, seed, h0=0.02, ratio=1.6, jitter=0.0):
+    """Wall-normal geometric growth from h0 (a stretched boundary-layer band), periodic in x."""
+    yn = geometric_nodes(h0, ratio, 0.25, 1.0)
+    ny = len(yn) - 1
+    imp = np.zeros((ny, nx), bool)
+    imp[imp_rows, :] = True
+    p = np.random.default_rng(seed).choice(degrees, size=nx * ny).astype(np.int32)
+    return structured_quads(uniform_nodes(nx, 0.0, 1.0), yn, periodic=(True, False), jitter=jitter,
+                            seed=seed, p=p, implicit=imp.reshape(-1), bc_y=bc_y)
+
+
+def _trace_solve(m, U, uh):
+    """Newton on g(u, u^) = 0 for u^ alone (dense complex-step Jacobian; tiny meshes)."""
+    off = np.concatenate([[0], np.cumsum(m.trace_npts * m.nv)])
+
+    def unflat(v):
+        return [v[off[t]:off[t + 1]].reshape(-1, m.nv) for t in range(m.ntrace)]
+
+    x = trace_flatten(uh)
+    Uc = [u.astype(np.complex128) for u in U]
+    for _ in range(30):
+        g = trace_flatten(m.full_residual(U, unflat(x))[1])
+        if np.abs(g).max() < 1e-13:
+            return unflat(x)
+        Jg = np.empty((x.size, x.size))
+        for k in range(x.size):
+            xp = x.astype(np.complex128)
+            xp[k] += 1j * EPS
+            Jg[:, k] = trace_flatten(m.full_residual(Uc, unflat(xp))[1]).imag / EPS
+        x = x - np.linalg.solve(Jg, g)
+    raise AssertionError("trace equations did not converge")
+
+
+@pytest.mark.parametrize("rows", [[0, 1], list(range(8))], ids=["explicit_far_field", "implicit_far_field"])
+def test_uniform_degree_with_walls_and_far_field_reduces_to_the_boundary_operator(rows):
+    mesh = _bl_mesh(3, [3], rows, (BC_WALL, BC_FARFIELD), seed=1, jitter=0.1)
+    assert mesh.ny == 8
+    ph = make_physics(NS_WALL)
+    d = BoundaryDiscretisation(mesh, ph, U_INF)
+    m = MixedDiscretisation(mesh, ph, U_INF)
+    rng = np.random.default_rng(0)
+    U = np.tile(U_INF, (mesh.nelem, d.ns, 1)) * (1 + 1e-2 * rng.standard_normal((mesh.nelem, d.ns, 4)))
+    uh = d.initial_trace(U) * (1 + 1e-2 * rng.standard_normal((d.ntrace, d.n, 4)))
+    R, g = d.full_residual(U, uh)
+    Rm, gm = m.full_residual(list(U), list(uh))
+    assert np.abs(np.stack(Rm) - R).max() <= 1e-13 * np.abs(R).max()
+    assert np.abs(np.stack(gm) - g).max() <= 1e-13 * np.abs(g).max()
+    assert np.abs(np.stack(m.initial_trace(list(U))) - d.initial_trace(U)).max() < 1e-15
+
+
+def test_rest_state_is_steady_on_a_stretched_mixed_degree_wall_band():
+    mesh = _bl_mesh(4, [2, 3, 4, 5], [0, 1, 2], (BC_WALL, BC_FARFIELD), seed=2)
+    assert len(set(mesh.p.tolist())) > 2
+    m = MixedDiscretisation(mesh, make_physics(NS_WALL), REST)
+    # boundary faces carry the element's own points; interior faces the higher degree's
+    e_b, f_b = np.nonzero(m.bnd)
+    assert len(e_b) == 2 * mesh.nx and np.all(m.nf[e_b, f_b] == m.n[e_b])
+    e_i, f_i = np.nonzero(~m.bnd)
+    assert np.all(m.nf[e_i, f_i] == np.maximum(m.n[e_i], m.n[mesh.nbr[e_i, f_i]]))
+    U = [np.tile(REST, ((int(mesh.p[e]) + 1) ** 2, 1)) for e in range(mesh.nelem)]
+    R, g = m.full_residual(U, m.initial_trace(U))
+    # R carries 1/h: rounding of O(1) fluxes over the thinnest cells (h0 = 0.02)
+    assert max(np.abs(r).max() for r in R) < 1e-12 / 0.02 and max(np.abs(x).max() for x in g) < 1e-12
+
+
+def test_walls_conserve_mass_and_energy_across_unequal_degrees():
+    mesh = _bl_mesh(3, [2, 3], [0, 4], (BC_WALL, BC_WALL), seed=3, ratio=1.0, h0=0.2)
+    m = MixedDiscretisation(mesh, make_physics(NS_WALL))
+    rng = np.random.default_rng(4)
+    U = [REST + 0.05 * rng.standard_normal(((int(mesh.p[e]) + 1) ** 2, 4)) for e in range(mesh.nelem)]
+    uh = _trace_solve(m, U, m.initial_trace(U))
+    R, _ = m.full_residual(U, uh)
+    total = sum(np.einsum("s,sv->v", _quad_weights(m, e), R[e]) for e in range(mesh.nelem))
+    scale = sum(np.einsum("s,sv->v", _quad_weights(m, e), np.abs(R[e])) for e in range(mesh.nelem))
+    assert abs(total[0]) < 1e-13 * scale[0] and abs(total[3]) < 1e-13 * scale[3]
+    for t in range(m.ntrace):
+        e, f = m.trace_sides[t, 0]
+        if m.kind[e, f] == 3:  # wall: no-slip
+            assert np.abs(uh[t][:, 1:3]).max() < 1e-14
+
+
+def test_condensed_step_equals_the_monolithic_step_on_a_boundary_layer_band():
+    mesh = _bl_mesh(3, [1, 2, 3], [0, 1], (BC_WALL, BC_FARFIELD), seed=5, ratio=2.0, h0=0.05)
+    m = MixedDiscretisation(mesh, make_physics(NS_WALL), U_INF)
+    rng = np.random.default_rng(6)
+    U = [U_INF * (1 + 1e-2 * rng.standard_normal(((int(mesh.p[e]) + 1) ** 2, 4))) for e in range(mesh.nelem)]
+    Ustar = [u + 1e-3 * rng.standard_normal(u.shape) for u in U]
+    uh = m.initial_trace(U)
+    du1, dh1 = hybridized_step(m, U, uh, Ustar, 0.03)
+    du2, dh2 = monolithic_step(m, U, uh, Ustar, 0.03)
+    scale = max(np.abs(dh2).max(), max(np.abs(v).max() for v in du2.values()))
+    assert scale > 1e-3
+    assert np.abs(dh1 - dh2).max() < 1e-12 * scale
+    assert max(np.abs(du1[e] - du2[e]).max() for e in du1) < 1e-12 * scale
