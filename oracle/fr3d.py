@@ -10,7 +10,8 @@ the same scheme on hexahedra, Sec. 5.3):
 * common fluxes, viscous readings, face kinds, trace residual g_q = w_q J_f (F^_+ . n_+ + F^_- . n_-)
   and trace numbering by increasing global face id exactly as in two dimensions.
 
-Periodic meshes only (boundary faces raise).
+Boundary faces (walls, far field) follow the readings of ``oracle.boundary`` with the momentum
+rows over the three velocity components.
 """
 
 from __future__ import annotations
@@ -21,9 +22,11 @@ import scipy.sparse.linalg as spla
 
 from .basis import RefElement1D
 from .blocks import EPS
+from .boundary import FARFIELD_FACE, WALL_FACE
 from .fr import FR_FACE, IMEX_FACE, TRACE_FACE
-from .physics import cmax
+from .physics import NavierStokes3D, cmax
 from .solve import backsolve, condense
+from workloads.mesh import BC_FARFIELD, BC_WALL
 
 # (axis, sign) of each local face
 FACES_3D = ((0, -1.0), (0, 1.0), (1, -1.0), (1, 1.0), (2, -1.0), (2, 1.0))
@@ -48,15 +51,14 @@ def adjugate3(x_xi, x_eta, x_zeta):
 
 
 class Discretisation3D:
-    """FR/HFR operators for a periodic hex mesh with a single polynomial degree."""
+    """FR/HFR operators for a hex mesh with a single polynomial degree (periodic, walls, far field)."""
 
-    def __init__(self, mesh, physics):
+    def __init__(self, mesh, physics, u_inf=None):
         p = int(mesh.p[0])
         if np.any(mesh.p != p):
             raise NotImplementedError("oracle: uniform p only")
-        if np.any(mesh.nbr < 0):
-            raise NotImplementedError("oracle: boundary faces not implemented in 3D")
         self.mesh, self.phys, self.p = mesh, physics, p
+        self.u_inf = None if u_inf is None else np.asarray(u_inf, dtype=np.float64)
         self.ref = RefElement1D(p)
         n = self.n = p + 1
         self.ns, self.nfp = n**3, n**2
@@ -83,18 +85,29 @@ class Discretisation3D:
         self.wvol = np.einsum("c,b,a->cba", *(self.ref.w,) * 3).reshape(-1)
         imp = np.asarray(mesh.implicit, dtype=bool)
         self.imp = imp
+        bnd = mesh.nbr < 0
+        self.bnd = bnd
+        nb = np.where(bnd, 0, mesh.nbr)
         kind = np.full((E, 6), FR_FACE, dtype=np.int32)
-        for f in range(6):
-            nb = mesh.nbr[:, f]
-            kind[imp & imp[nb], f] = TRACE_FACE
-            kind[imp != imp[nb], f] = IMEX_FACE
+        kind[~bnd & imp[:, None] & imp[nb]] = TRACE_FACE
+        kind[~bnd & (imp[:, None] != imp[nb])] = IMEX_FACE
+        kind[bnd & (mesh.bc == BC_WALL)] = WALL_FACE
+        kind[bnd & (mesh.bc == BC_FARFIELD)] = FARFIELD_FACE
+        if np.any(bnd & ~np.isin(mesh.bc, (BC_WALL, BC_FARFIELD))):
+            raise ValueError("boundary face without a wall or far-field tag")
+        if np.any(kind == WALL_FACE) and (np.any((kind == WALL_FACE) & ~imp[:, None])
+                                          or not isinstance(physics, NavierStokes3D)):
+            raise NotImplementedError("oracle: walls on implicit Navier-Stokes elements only")
+        if np.any(kind == FARFIELD_FACE) and self.u_inf is None:
+            raise ValueError("far-field faces need u_inf")
         self.kind = kind
+        self.traced = (kind == TRACE_FACE) | (bnd & imp[:, None])
         fid = mesh.face_of
-        trace_fids = np.unique(fid[kind == TRACE_FACE])
+        trace_fids = np.unique(fid[self.traced])
         tr_of_fid = -np.ones(mesh.nface, dtype=np.int64)
         tr_of_fid[trace_fids] = np.arange(len(trace_fids))
         self.ntrace = len(trace_fids)
-        self.tr_of = np.where(kind == TRACE_FACE, tr_of_fid[fid], -1)
+        self.tr_of = np.where(self.traced, tr_of_fid[fid], -1)
         self.trace_sides = -np.ones((self.ntrace, 2, 2), dtype=np.int64)
         for e in range(E):
             for f in range(6):
@@ -156,8 +169,17 @@ class Discretisation3D:
         return [o.reshape((E, self.ns) + rest) for o in out]
 
     def neighbour(self, Xf):
+        """Other side's face values; boundary faces get the element's own values."""
         m = self.mesh
-        return Xf[m.nbr, m.nbr_face]
+        out = Xf[np.where(self.bnd, 0, m.nbr), np.where(self.bnd, 0, m.nbr_face)]
+        return np.where(self.bnd.reshape(self.bnd.shape + (1,) * (Xf.ndim - 2)), Xf, out)
+
+    def _other_state(self, Uf):
+        """The neighbour's face state, the ghost u_inf on far-field faces."""
+        far = (self.kind == FARFIELD_FACE)[:, :, None, None]
+        if not np.any(far):
+            return self.neighbour(Uf)
+        return np.where(far, np.broadcast_to(self.u_inf, Uf.shape), self.neighbour(Uf))
 
     # ----------------------------------------------------------------- residual
     def corrected_gradient(self, U, uhat_view):
@@ -166,8 +188,8 @@ class Discretisation3D:
         kind = self.kind[:, :, None, None]
         imp_e = self.imp[:, None, None, None]
         Uf = self.interp_faces(U)
-        Uf_nb = self.neighbour(Uf)
-        jump = np.where(kind == TRACE_FACE, uhat_view - Uf, 0.5 * (Uf_nb - Uf))
+        Uf_nb = self._other_state(Uf)
+        jump = np.where(self.traced[:, :, None, None], uhat_view - Uf, 0.5 * (Uf_nb - Uf))
         jump = np.where(kind == IMEX_FACE, np.where(imp_e, Uf_nb - Uf, 0.0 * Uf), jump)
         d = self.ref_derivative(U)
         c = self.lift(jump, signed=False)
@@ -175,12 +197,15 @@ class Discretisation3D:
         return np.einsum("esrc,esrv->escv", self.S, Qr) / self.J[:, :, None, None]
 
     def residual(self, U, uhat_view):
-        """R (E, Ns, nv) and J_f F^.n at every element flux point (E, 6, n^2, nv)."""
+        """R (E, Ns, nv) and J_f times the element's trace row at every flux point (E, 6, n^2, nv):
+        J_f F^.n on interior faces, the wall / far-field rows on boundary faces of implicit
+        elements."""
         ph = self.phys
         kind = self.kind[:, :, None, None]
+        traced = self.traced[:, :, None, None]
         imp_e = self.imp[:, None, None, None]
         Uf = self.interp_faces(U)
-        Uf_nb = self.neighbour(Uf)
+        Uf_nb = self._other_state(Uf)
         if ph.viscous:
             q = self.corrected_gradient(U, uhat_view)
             qf = self.interp_faces(q)
@@ -198,8 +223,9 @@ class Discretisation3D:
         def dotn(Fx):
             return np.einsum("...cv,...c->...v", Fx, nrm)
 
-        uh = np.where(kind == TRACE_FACE, uhat_view, Uf)
-        Fh = dotn(ph.conv(uh)) + ph.stab(uh, nrm)[..., None] * (Uf - uh)
+        uh = np.where(traced, uhat_view, Uf)
+        stab = ph.stab(uh, nrm)[..., None]
+        Fh = dotn(ph.conv(uh)) + stab * (Uf - uh)
         lam = cmax(ph.wave_speed(Uf, nrm), ph.wave_speed(Uf_nb, nrm))
         Fr = 0.5 * dotn(ph.conv(Uf) + ph.conv(Uf_nb)) + 0.5 * lam[..., None] * (Uf - Uf_nb)
         if ph.viscous:
@@ -208,12 +234,19 @@ class Discretisation3D:
             Fr_im = Fr - dotn(ph.visc(np.where(imp_e, Uf, Uf_nb), np.where(imp_e[..., None], qf, qf_nb)))
         else:
             Fr_fr = Fr_im = Fr
-        Fhat = np.where(kind == TRACE_FACE, Fh, np.where(kind == IMEX_FACE, Fr_im, Fr_fr))
-        Fn = self.Jf[..., None] * Fhat
+        Fhat = np.where(traced, Fh, np.where(kind == IMEX_FACE, Fr_im, Fr_fr))
+        Jf = self.Jf[..., None]
+        Fn = Jf * Fhat
         d = self.ref_derivative(Ft)
         c = self.lift(Fn - FDn, signed=True)
         div = d[0][:, :, 0] + d[1][:, :, 1] + d[2][:, :, 2] + c[0] + c[1] + c[2]
-        return -div / self.J[:, :, None], Fn
+        G = Fn
+        if np.any(kind == FARFIELD_FACE):
+            G = np.where(kind == FARFIELD_FACE, Jf * stab * ((Uf - uh) + (self.u_inf - uh)), G)
+        if np.any(kind == WALL_FACE):
+            wall = Jf * np.concatenate([Fh[..., :1], stab * uh[..., 1:4], Fh[..., 4:]], axis=-1)
+            G = np.where(kind == WALL_FACE, wall, G)
+        return -div / self.J[:, :, None], G
 
     # ------------------------------------------------------------ trace helpers
     def trace_view(self, uhat):
@@ -224,18 +257,30 @@ class Discretisation3D:
 
     def trace_weights(self, Fn):
         gv = self.wface[None, None, :, None] * Fn
-        return np.where((self.kind == TRACE_FACE)[:, :, None, None], gv, 0.0)
+        return np.where(self.traced[:, :, None, None], gv, 0.0)
 
     def assemble_trace(self, gview):
         g = np.zeros((self.ntrace, self.nfp, self.nv), dtype=gview.dtype)
         for s in range(2):
-            g += gview[self.trace_sides[:, s, 0], self.trace_sides[:, s, 1]]
+            ok = self.trace_sides[:, s, 0] >= 0
+            g[ok] += gview[self.trace_sides[ok, s, 0], self.trace_sides[ok, s, 1]]
         return g
 
     def initial_trace(self, U):
+        """Average of both sides' states; with u_inf on far-field faces; on walls the element's
+        density and energy with zero momentum."""
         Uf = self.interp_faces(U)
-        ts = self.trace_sides
-        return 0.5 * (Uf[ts[:, 0, 0], ts[:, 0, 1]] + Uf[ts[:, 1, 0], ts[:, 1, 1]])
+        out = np.zeros((self.ntrace, self.nfp, self.nv))
+        for t in range(self.ntrace):
+            (e0, f0), (e1, f1) = self.trace_sides[t]
+            if e1 >= 0:
+                out[t] = 0.5 * (Uf[e0, f0] + Uf[e1, f1])
+            elif self.kind[e0, f0] == FARFIELD_FACE:
+                out[t] = 0.5 * (Uf[e0, f0] + self.u_inf)
+            else:
+                out[t] = Uf[e0, f0]
+                out[t, :, 1:4] = 0.0
+        return out
 
     def full_residual(self, U, uhat):
         R, Fn = self.residual(U, self.trace_view(uhat))

@@ -7,6 +7,7 @@ against the monolithic one."""
 import math
 
 import numpy as np
+import pytest
 
 from oracle.fr3d import Discretisation3D, condensed_newton_step, monolithic_newton_step
 from oracle.physics import AdvectionDiffusion, NavierStokes2D, NavierStokes3D, make_physics
@@ -165,3 +166,113 @@ def test_trace_residuals_sum_to_the_net_element_flux():
         R, g = d.full_residual(U, uh)
         total = np.einsum("s,es,esv->v", d.wvol, d.J, R)
         assert np.abs(g.sum(axis=(0, 1)) + total).max() < 1e-12 * np.abs(g).sum()
+
+
+# ------------------------------------------------------------------ walls (config-5 shape)
+from oracle.blocks import EPS  # noqa: E402
+from oracle.boundary import WALL_FACE, BoundaryDiscretisation  # noqa: E402
+from workloads.mesh import BC_FARFIELD, BC_WALL, structured_quads, tanh_nodes  # noqa: E402
+
+REST3 = np.array([1.2, 0.0, 0.0, 0.0, 2.0])
+
+
+def _channel(nx, ny, nz, p, imp_layers, bc_y=(BC_WALL, BC_WALL), yn=None):
+    """Box periodic in x and z, walls at y = -1, 1 with tanh clustering (beta = 2.5)."""
+    yn = tanh_nodes(ny, 2.5) if yn is None else yn
+    imp = np.zeros((nz, ny, nx), bool)
+    imp[:, imp_layers, :] = True
+    return structured_hexes(uniform_nodes(nx, 0, 2 * np.pi), yn, uniform_nodes(nz, 0, np.pi),
+                            periodic=(True, False, True), p=p, implicit=imp.reshape(-1), bc_y=bc_y)
+
+
+@pytest.mark.parametrize("rows", [[True, True, True, False], [True] * 4], ids=["explicit_top", "all_implicit"])
+def test_planar_states_reduce_to_the_2d_boundary_operator(rows):
+    """One periodic element in z, a z-invariant state with w = 0: every z-slice of the 3D residual is
+    the 2D residual with walls below and far field above (explicit or implicit far-field elements)."""
+    nx, p = 3, 2
+    yn = np.array([0.0, 0.05, 0.2, 0.5, 1.0])
+    imp = np.repeat(rows, nx)
+    ns2 = structured_quads(uniform_nodes(nx, 0, 1), yn, periodic=(True, False), p=p,
+                           implicit=imp, bc_y=(BC_WALL, BC_FARFIELD))
+    m3 = structured_hexes(uniform_nodes(nx, 0, 1), yn, uniform_nodes(1, 0, 0.3), periodic=(True, False, True),
+                          p=p, implicit=imp, bc_y=(BC_WALL, BC_FARFIELD))
+    u2inf = np.array([1.0, 0.3, 0.05, 2.6])
+    u3inf = np.array([1.0, 0.3, 0.05, 0.0, 2.6])
+    ph2 = NavierStokes2D(mu=2e-2)
+    d2 = BoundaryDiscretisation(ns2, ph2, u2inf)
+    d3 = Discretisation3D(m3, NavierStokes3D(mu=2e-2), u3inf)
+    rng = np.random.default_rng(0)
+    U2 = np.tile(u2inf, (ns2.nelem, d2.ns, 1)) * (1 + 1e-2 * rng.standard_normal((ns2.nelem, d2.ns, 4)))
+    uh2 = d2.initial_trace(U2) * (1 + 1e-2 * rng.standard_normal((d2.ntrace, d2.n, 4)))
+    n = p + 1
+    U3 = np.zeros((m3.nelem, d3.ns, 5))
+    for c in range(n):
+        U3[:, c * n * n:(c + 1) * n * n][..., [0, 1, 2, 4]] = U2
+    uh3 = d3.initial_trace(U3)
+    for t in range(d3.ntrace):
+        e, f = d3.trace_sides[t, 0]
+        if f < 4:  # x and y faces: 2D face point i, repeated along z
+            uh3[t][:, [0, 1, 2, 4]] = np.tile(uh2[d2.tr_of[e, f]], (n, 1))
+    R2, g2 = d2.full_residual(U2, uh2)
+    R3, g3 = d3.full_residual(U3, uh3)
+    for c in range(n):
+        sl = R3[:, c * n * n:(c + 1) * n * n]
+        assert np.abs(sl[..., [0, 1, 2, 4]] - R2).max() < 1e-12 * np.abs(R2).max()
+        assert np.abs(sl[..., 3]).max() < 1e-12 * np.abs(R2).max()
+    # trace rows of x and y faces: the 2D rows times the z weight and the z half-length
+    wz = d3.ref.w * 0.3 / 2
+    for t in range(d3.ntrace):
+        e, f = d3.trace_sides[t, 0]
+        if f < 4:
+            exp = np.kron(wz[:, None], np.ones((n, 1))) * np.tile(g2[d2.tr_of[e, f]], (n, 1))
+            assert np.abs(g3[t][:, [0, 1, 2, 4]] - exp).max() < 1e-12 * np.abs(g2).max()
+
+
+def test_rest_state_is_steady_in_a_wall_clustered_channel():
+    m = _channel(2, 6, 2, 3, [0, 5])
+    d = Discretisation3D(m, NavierStokes3D(mu=2e-2))
+    assert np.sum(d.kind == WALL_FACE) == 2 * 2 * 2
+    U = np.tile(REST3, (m.nelem, d.ns, 1))
+    R, g = d.full_residual(U, d.initial_trace(U))
+    hmin = np.diff(tanh_nodes(6, 2.5)).min()
+    assert np.abs(R).max() < 1e-12 / hmin and np.abs(g).max() < 1e-12
+
+
+def test_walls_conserve_mass_and_energy_in_3d():
+    m = _channel(2, 4, 2, 1, [0, 3])
+    d = Discretisation3D(m, NavierStokes3D(mu=2e-2))
+    rng = np.random.default_rng(1)
+    U = REST3 + 0.05 * rng.standard_normal((m.nelem, d.ns, 5))
+    uh = d.initial_trace(U)
+    for _ in range(20):  # Newton on g(u, u^) = 0 for u^ alone
+        _, g = d.full_residual(U, uh)
+        if np.abs(g).max() < 1e-13:
+            break
+        Jg = np.empty((uh.size, uh.size))
+        for k in range(uh.size):
+            hp = uh.astype(np.complex128)
+            hp.reshape(-1)[k] += 1j * EPS
+            Jg[:, k] = d.full_residual(U.astype(np.complex128), hp)[1].imag.reshape(-1) / EPS
+        uh = uh - np.linalg.solve(Jg, g.reshape(-1)).reshape(uh.shape)
+    R, g = d.full_residual(U, uh)
+    assert np.abs(g).max() < 1e-13
+    total = np.einsum("s,es,esv->v", d.wvol, d.J, R)
+    scale = np.einsum("s,es,esv->v", d.wvol, d.J, np.abs(R))
+    assert abs(total[0]) < 1e-13 * scale[0] and abs(total[4]) < 1e-13 * scale[4]
+    assert abs(total[1]) > 1e-6 * scale[1]  # wall shear: momentum is not conserved
+    walls = [t for t in range(d.ntrace) if d.trace_sides[t, 1, 0] < 0]
+    assert len(walls) == 8 and np.abs(uh[walls][..., 1:4]).max() < 1e-14
+
+
+def test_condensed_step_equals_the_monolithic_step_with_walls_3d():
+    m = _channel(2, 3, 2, 1, [0, 2])
+    d = Discretisation3D(m, NavierStokes3D(mu=2e-2))
+    rng = np.random.default_rng(2)
+    U = REST3 + np.array([0, 0.1, 0.05, 0.02, 0]) + 0.02 * rng.standard_normal((m.nelem, d.ns, 5))
+    Ustar = U + 1e-3 * rng.standard_normal(U.shape)
+    uh = d.initial_trace(U)
+    a = condensed_newton_step(d, U, uh, Ustar, 0.02)
+    b = monolithic_newton_step(d, U, uh, Ustar, 0.02)
+    scale = max(np.abs(b[0]).max(), np.abs(b[1]).max())
+    assert scale > 1e-4
+    assert max(np.abs(a[0] - b[0]).max(), np.abs(a[1] - b[1]).max()) < 1e-12 * scale
