@@ -11,8 +11,9 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .mesh import structured_quads, uniform_nodes
-from .states import edac_vortex, sample_points, gaussian_scalar, isentropic_vortex, uniform_noise
+from .mesh import BC_FARFIELD, BC_WALL, structured_hexes, structured_quads, tanh_nodes, uniform_nodes
+from .states import (channel_state, edac_vortex, freestream, gaussian_scalar, isentropic_vortex,
+                     sample_points, sample_points_hex, uniform_noise)
 
 
 @dataclass
@@ -29,11 +30,13 @@ class Workload:
 
     @property
     def nv(self) -> int:
-        return int(self.u0.shape[-1])
+        return int(self.u0[0].shape[-1])
 
     @property
     def dofs_implicit(self) -> int:
-        return int(self.mesh.implicit.sum()) * self.u0.shape[1] * self.u0.shape[2]
+        """Implicit solution unknowns (u0 is an (E, Ns, nv) array, or a list of (Ns_e, nv) arrays
+        when the degree varies per element)."""
+        return int(sum(self.u0[e].size for e in np.nonzero(self.mesh.implicit)[0]))
 
 
 def _advdiff(n=8, p=2, dt=0.05, jitter=0.0, seed=0, implicit=None):
@@ -77,6 +80,61 @@ def _edac(n=16, p=3, theta=100.0, re=1.0e3, cfl_mult=10.0, jitter=0.0, seed=0, i
     return mesh, u0, phys, cfl_mult * dt_ex
 
 
+def stiffness_indicator(verts: np.ndarray) -> np.ndarray:
+    """E_s = |Omega_k| / |dOmega_k| of each quad (area over perimeter; Sec. 5)."""
+    a, b, c, d = verts[:, 0], verts[:, 1], verts[:, 2], verts[:, 3]
+    area = 0.5 * np.abs((d[:, 0] - a[:, 0]) * (c[:, 1] - b[:, 1]) - (d[:, 1] - a[:, 1]) * (c[:, 0] - b[:, 0]))
+    perim = sum(np.linalg.norm(q - r, axis=1) for q, r in ((b, a), (d, b), (c, d), (a, c)))
+    return area / perim
+
+
+def _boundary_layer(nx=400, ny=500, h0=1.0e-5, ratio=1.15, dx=1.0e-2, degrees=(2, 3, 4, 5), if_target=0.2,
+                    re=1.7e6, mach=0.2, gamma=1.4, noise=1.0e-3, seed=2024):
+    """Stretched wall band: first cell h0 growing by ``ratio`` until the isotropic spacing dx, then
+    isotropic cells; wall below, far field above, periodic streamwise.  Implicit elements: the
+    if_target fraction with the smallest E_s, ties (equal cells) broken towards the wall."""
+    yn = [0.0]
+    h = h0
+    for _ in range(ny):
+        yn.append(yn[-1] + min(h, dx))
+        h *= ratio
+    mesh = structured_quads(uniform_nodes(nx, 0.0, nx * dx), np.asarray(yn), periodic=(True, False), p=2,
+                            bc_y=(BC_WALL, BC_FARFIELD))
+    es = stiffness_indicator(mesh.verts)
+    es = np.round(es / es.max(), 10)  # equal cells compare equal despite coordinate rounding
+    row = np.arange(mesh.nelem) // nx
+    order = np.lexsort((row, es))
+    imp = np.zeros(mesh.nelem, bool)
+    imp[order[:int(round(if_target * mesh.nelem))]] = True
+    mesh.implicit = imp
+    rng = np.random.default_rng(seed)
+    mesh.p = rng.choice(np.asarray(degrees), size=mesh.nelem).astype(np.int32)
+    u_inf = freestream((), gamma=gamma, mach=mach)
+    u0 = []
+    for e in range(mesh.nelem):
+        ns = (int(mesh.p[e]) + 1) ** 2
+        u0.append(u_inf + rng.uniform(-noise, noise, size=(ns, 4)))
+    phys = {"kind": "ns", "gamma": gamma, "mu": mach / re, "Pr": 0.72, "lref": 1.0, "u_inf": u_inf}
+    dt = dx / ((mach + 1.0) * (2 * max(degrees) + 1))  # explicit limit of the isotropic region
+    return mesh, u0, phys, dt
+
+
+def _channel3d(n=(64, 32, 48), p=3, beta=2.5, layers=3, re=1.6e3, mach=0.1, gamma=1.4):
+    """Box [0, 2 pi] x [-1, 1] x [0, pi], tanh-clustered in y, walls at y = +-1, periodic in x and z;
+    implicit: ``layers`` cell layers on each wall."""
+    nx, ny, nz = n
+    j = np.arange(nx * ny * nz) // nx % ny
+    imp = (j < layers) | (j >= ny - layers)
+    mesh = structured_hexes(uniform_nodes(nx, 0.0, 2 * np.pi), tanh_nodes(ny, beta),
+                            uniform_nodes(nz, 0.0, np.pi), periodic=(True, False, True), p=p,
+                            implicit=imp, bc_y=(BC_WALL, BC_WALL))
+    u0 = channel_state(sample_points_hex(mesh, p), gamma=gamma, mach=mach)
+    phys = {"kind": "ns3d", "gamma": gamma, "mu": mach / re, "Pr": 0.72, "lref": 1.0}
+    hx = min(2 * np.pi / nx, np.pi / nz)
+    dt = hx / ((mach + 1.0) * (2 * p + 1))
+    return mesh, u0, phys, dt
+
+
 def make_config(name: str, **kw) -> Workload:
     if name == "advdiff8":  # 8x8 p=2 advection-diffusion, one backward-Euler step
         mesh, u0, phys, dt = _advdiff(**kw)
@@ -100,6 +158,12 @@ def make_config(name: str, **kw) -> Workload:
     if name == "advdiff":
         mesh, u0, phys, dt = _advdiff(**kw)
         return Workload(name, mesh, int(mesh.p[0]), phys, u0, dt, "be")
+    if name == "boundary_layer":  # 400x500 stretched wall band, p in 2..5, IF = 0.2, IMEX stage
+        mesh, u0, phys, dt = _boundary_layer(**kw)
+        return Workload(name, mesh, -1, phys, u0, dt, "sdirk2")
+    if name == "channel3d":  # 64x32x48 hexes, p = 3, three implicit wall layers per wall
+        mesh, u0, phys, dt = _channel3d(**kw)
+        return Workload(name, mesh, int(mesh.p[0]), phys, u0, dt, "sdirk2")
     raise KeyError(name)
 
 
@@ -107,4 +171,6 @@ CONFIGS = {
     "advdiff8": "2D advection-diffusion, beta=(1,0.5), nu=0.01, periodic unit square, 8x8 quads, p=2, one backward-Euler step dt=0.05",
     "vortex64": "2D Navier-Stokes isentropic vortex, M=0.5, gamma=1.4, Re=1e4, periodic [0,10]^2, 64x64 quads, p=3, one SDIRK2 step at 10x the explicit CFL",
     "vortex256": "as vortex64 on 256x256 quads, p=4, plus U(-1e-3,1e-3) noise (seed 1234)",
+    "boundary_layer": "2D Navier-Stokes, Re=1.7e6, M=0.2: 400x500 quads, wall-normal growth 1.15 from 1e-5 to isotropic 1e-2 cells, wall below, far field above, p in {2,3,4,5} per element (seed 2024), the 20% stiffest elements by E_s implicit",
+    "channel3d": "3D Navier-Stokes, Re=1.6e3, M=0.1 Taylor-Green-like field: 64x32x48 hexes, tanh clustering beta=2.5, walls at y=+-1, p=3, three implicit wall layers per wall",
 }

@@ -96,3 +96,30 @@ def edac_vortex(xy: np.ndarray, strength=1.0, speed=1.0, center=(5.0, 5.0)) -> n
     vy = amp * dx
     P = -strength**2 / (8.0 * np.pi**2) * np.exp(1.0 - r2)
     return np.stack([P, vx, vy], axis=-1)
+
+
+def sample_points_hex(mesh, p: int) -> np.ndarray:
+    """Physical coordinates (E, (p+1)^3, 3) of the Gauss-Legendre tensor nodes of a hex mesh,
+    pt = a + n b + n^2 c, by trilinear corner interpolation."""
+    xg, _ = np.polynomial.legendre.leggauss(p + 1)
+    n = p + 1
+    xi, eta, zeta = np.tile(xg, n * n), np.tile(np.repeat(xg, n), n), np.repeat(xg, n * n)
+    sa = np.array([-1.0, 1, -1, 1, -1, 1, -1, 1])
+    sb = np.array([-1.0, -1, 1, 1, -1, -1, 1, 1])
+    sc = np.array([-1.0, -1, -1, -1, 1, 1, 1, 1])
+    N = 0.125 * (1 + sa * xi[:, None]) * (1 + sb * eta[:, None]) * (1 + sc * zeta[:, None])
+    return np.einsum("sk,ekd->esd", N, mesh.verts)
+
+
+def channel_state(xyz: np.ndarray, gamma=1.4, mach=0.1, rho=1.0) -> np.ndarray:
+    """(rho, rho v, E) of the Taylor-Green-like channel field: v = M (sin x cos y cos z,
+    -cos x sin y cos z, 0) (1 - y^2) (zero on walls at y = +-1), uniform density and pressure
+    1 / gamma (sound speed 1)."""
+    x, y, z = xyz[..., 0], xyz[..., 1], xyz[..., 2]
+    damp = 1.0 - y * y
+    u = mach * np.sin(x) * np.cos(y) * np.cos(z) * damp
+    v = -mach * np.cos(x) * np.sin(y) * np.cos(z) * damp
+    w = np.zeros_like(u)
+    p = np.full_like(u, 1.0 / gamma)
+    E = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)
+    return np.stack([np.full_like(u, rho), rho * u, rho * v, rho * w, E], axis=-1)
