@@ -282,3 +282,21 @@ def monolithic_newton_step(d, U, uhat, Ustar, a_dt):
     dU = np.zeros_like(U)
     dU[imp] = x[:nu].reshape(len(imp), d.ns, d.nv)
     return dU, x[nu:].reshape(d.nnode, d.nv)
+
+
+def newton_stage(d, U0, Ustar, uhat0, a_dt, tol=1e-8, maxit=25, linear="direct"):
+    """Newton on the EFR stage equations with condensed steps and the stopping test of the
+    uniform oracle, ||[h; g]||_2 <= tol ||[h; g]^0||_2.  Returns U, uhat, info."""
+    U, uhat = U0.copy(), uhat0.copy()
+    imp = d.imp_idx
+    hist = []
+    for it in range(maxit + 1):
+        R, g = d.full_residual(U, uhat)
+        h = U[imp] - Ustar[imp] - a_dt * R[imp]
+        hist.append(float(np.sqrt(np.sum(h * h) + np.sum(g * g))))
+        if hist[-1] <= tol * hist[0] or hist[-1] == 0.0 or it == maxit:
+            break
+        dU, duh = condensed_newton_step(d, U, uhat, Ustar, a_dt)
+        U, uhat = U + dU, uhat + duh
+    converged = hist[-1] <= tol * hist[0] or hist[-1] == 0.0
+    return U, uhat, {"history": hist, "iterations": len(hist) - 1, "converged": converged}

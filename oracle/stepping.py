@@ -87,8 +87,10 @@ def newton_stage(disc, U0, Ustar, uhat0, a_dt, tol=1e-8, maxit=25, linear="direc
                      "linear_iterations": lin_its, "converged": converged}
 
 
-def imex_step(disc, Un, uhat, dt, tableau="sdirk2", tol=1e-10, linear="direct", maxit=25):
-    """One IMEX step; returns U_{n+1}, trace, per-stage info."""
+def imex_step(disc, Un, uhat, dt, tableau="sdirk2", tol=1e-10, linear="direct", maxit=25, stage=None):
+    """One IMEX step; returns U_{n+1}, trace, per-stage info.  ``stage`` replaces
+    ``newton_stage`` (same signature) for discretisations with another trace space."""
+    stage = newton_stage if stage is None else stage
     tab = TABLEAUX[tableau] if isinstance(tableau, str) else tableau
     a, b, ahat, bhat = tab["a"], tab["b"], tab["ahat"], tab["bhat"]
     s = len(b)
@@ -105,8 +107,8 @@ def imex_step(disc, Un, uhat, dt, tableau="sdirk2", tol=1e-10, linear="direct", 
         for j in range(1, i):
             Ustar[imp] += dt * a[i - 1, j - 1] * Rim[j - 1][imp]
         Ui[imp] = Ustar[imp]
-        Ui, uhat, info = newton_stage(disc, Ui, Ustar, uhat, a[i - 1, i - 1] * dt, tol=tol,
-                                      linear=linear, maxit=maxit)
+        Ui, uhat, info = stage(disc, Ui, Ustar, uhat, a[i - 1, i - 1] * dt, tol=tol,
+                               linear=linear, maxit=maxit)
         infos.append(info)
         R, _ = disc.full_residual(Ui, uhat)
         Rim.append(R)

@@ -235,3 +235,22 @@ def test_mean_corrected_gradient_equals_the_gll_face_integral_of_the_jump():
     UfL = np.einsum("qm,efmv->efqv", d.IGL, d.interp_faces(U))
     face = np.einsum("q,efq,efqc,efqv->ecv", d.wl, d.JfL, d.normalL, view - UfL)
     assert np.abs(lhs - vol - face).max() < 1e-12 * np.abs(lhs).max()
+
+
+def test_efr_imex_step_conserves_across_the_interface():
+    """Algorithm 1 with EFR on the implicit band and FR elsewhere (Sec. 4): the FR flux on the
+    interface and b^_{j+1} = b_j make the step conservative for the whole domain, the implicit
+    region being conservative as a whole (the paper's statement for EFR)."""
+    from oracle import efr
+    from oracle.stepping import imex_step
+    n = 6
+    mesh = _mesh(n, 10.0, 2, _band(n, [2, 3]), jitter=0.15, seed=4)
+    d = EmbeddedDiscretisation(mesh, make_physics(dict(NS, mu=1e-2)))
+    U0 = isentropic_vortex(d.geo.xy)
+    W = np.outer(d.ref.w, d.ref.w).reshape(-1)
+    mass0 = np.einsum("s,es,esv->v", W, d.geo.J, U0)
+    U1, _, infos = imex_step(d, U0, d.initial_trace(U0), 0.05, "sdirk2", tol=1e-12, stage=efr.newton_stage)
+    assert all(i["converged"] for i in infos)
+    mass1 = np.einsum("s,es,esv->v", W, d.geo.J, U1)
+    assert np.abs(mass1 - mass0).max() < 1e-12 * np.abs(mass0).max()
+    assert np.abs(U1 - U0).max() > 1e-4  # the step moves the state
