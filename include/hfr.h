@@ -353,6 +353,26 @@ int hfr_condense_noalloc(int nimplicit, int nA, int nT, int precision, const voi
 int fr_last_error(const fr_ctx* ctx, fr_error_info* info /* host */);
 const char* fr_status_string(int code);
 
+/* Trace-node layout of the interior-embedded variant EFR (Sec. 2.2: the trace is continuous on
+ * the implicit skeleton, with nodes at the p + 1 Gauss-Lobatto points of every trace face; a
+ * face's end points are the mesh vertices it shares with the other trace faces meeting there).
+ * Host only: needs no device and no context.
+ *   nbr, nbr_face, face_of  host, (nelem, 4) each: neighbour element, its local face, global
+ *                           face id (the mesh arrays of fr_mesh_desc); all elements share one
+ *                           orientation, so the first point of a face meets the neighbour's first
+ *   implicit                host, (nelem,): nonzero for implicit elements; a trace face has both
+ *                           sides implicit
+ *   node_of                 host, (nelem, 4, p + 1) out: the node at each Gauss-Lobatto point of
+ *                           each element face, -1 on faces without a trace.  Vertex nodes first,
+ *                           in increasing smallest element corner 4 e + c of the vertex (corner
+ *                           c = a + 2 b), then the interior points m = 1..p-1 of trace face t
+ *                           (trace faces in increasing global face id) at nvert + t (p - 1) + m - 1
+ *   nvert_out, nnode_out    host out: vertex nodes and all nodes
+ * Errors: FR_ERR_INVALID_ARG (null pointer, nelem <= 0, p outside 1..5, indices out of range or a
+ * neighbour relation that is not symmetric), FR_ERR_UNSUPPORTED (boundary faces). */
+int efr_trace_nodes(int nelem, const int* nbr, const int* nbr_face, const int* face_of,
+                    const unsigned char* implicit, int p, int* node_of, int* nvert_out, int* nnode_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -38,6 +38,7 @@ EXPORT = {"A": 0, "B": 1, "C": 2, "D": 3, "S": 4, "XB": 5, "xr": 6, "t_k": 7, "r
 
 # every symbol declared in include/hfr.h
 ABI_SYMBOLS = [
+    "efr_trace_nodes",
     "fr_ctx_create",
     "fr_ctx_destroy",
     "fr_ctx_query",
@@ -216,6 +217,7 @@ def load_library(path: str = LIB_PATH):
     lib.fr_last_error.argtypes = [vp, ctypes.POINTER(fr_error_info)]
     lib.fr_status_string.argtypes = [ctypes.c_int]
     lib.fr_status_string.restype = ctypes.c_char_p
+    lib.efr_trace_nodes.argtypes = [ctypes.c_int, vp, vp, vp, vp, ctypes.c_int, vp, ip, ip]
     _lib = lib
     return lib
 
@@ -228,6 +230,26 @@ class HfrError(RuntimeError):
         if info is not None:
             msg += f" ({info.message.decode()}; element {info.element}, iteration {info.iteration}, value {info.value:g})"
         super().__init__(msg)
+
+
+def efr_trace_nodes(nbr, nbr_face, face_of, implicit, p):
+    """EFR trace-node layout of a quad mesh (host arrays in, host arrays out): (node_of (E, 4, p+1)
+    int32, nvert, nnode).  Raises HfrError on the library's error codes."""
+    import numpy as np
+
+    lib = load_library()
+    nbr = np.ascontiguousarray(nbr, dtype=np.int32)
+    nbr_face = np.ascontiguousarray(nbr_face, dtype=np.int32)
+    face_of = np.ascontiguousarray(face_of, dtype=np.int32)
+    imp = np.ascontiguousarray(implicit, dtype=np.uint8)
+    E = int(nbr.shape[0])
+    out = np.empty((E, 4, max(int(p), 0) + 1), dtype=np.int32)
+    nvert, nnode = ctypes.c_int(), ctypes.c_int()
+    rc = lib.efr_trace_nodes(E, nbr.ctypes.data, nbr_face.ctypes.data, face_of.ctypes.data, imp.ctypes.data,
+                             int(p), out.ctypes.data, ctypes.byref(nvert), ctypes.byref(nnode))
+    if rc != 0:
+        raise HfrError(rc)
+    return out, nvert.value, nnode.value
 
 
 def _ptr(t):

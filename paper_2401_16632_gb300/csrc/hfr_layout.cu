@@ -1,0 +1,95 @@
+// Host-side trace layouts that do not need a device: the node numbering of the interior-embedded
+// (EFR) trace space (Sec. 2.2: trace continuous on the implicit skeleton, nodes at the
+// Gauss-Lobatto points of every trace face, vertices shared by the faces that meet there).
+//
+// Vertices are found by union-find over element corners: the two ends of a trace face are joined
+// to the matching ends of the neighbour's face (all elements share one orientation, so the first
+// point of a face meets the first point of the neighbour's).  Each class is named by its smallest
+// corner index 4 e + c; vertex nodes are numbered in increasing name, then the p - 1 interior
+// points of trace face t (trace faces in increasing global face id) at nvert + t (p - 1) + m - 1.
+
+#include <algorithm>
+#include <vector>
+
+#include "../../include/hfr.h"
+
+namespace {
+
+// corners (a + 2 b) at the first and the last point of local faces 0..3
+constexpr int kFaceCorner[4][2] = {{0, 2}, {1, 3}, {0, 1}, {2, 3}};
+
+int find_root(std::vector<int>& parent, int i) {
+  while (parent[i] != i) {
+    parent[i] = parent[parent[i]];
+    i = parent[i];
+  }
+  return i;
+}
+
+}  // namespace
+
+extern "C" int efr_trace_nodes(int nelem, const int* nbr, const int* nbr_face, const int* face_of,
+                               const unsigned char* implicit, int p, int* node_of, int* nvert_out,
+                               int* nnode_out) {
+  if (nelem <= 0 || !nbr || !nbr_face || !face_of || !implicit || !node_of || !nvert_out || !nnode_out)
+    return FR_ERR_INVALID_ARG;
+  if (p < 1 || p > 5) return FR_ERR_INVALID_ARG;
+  const int n = p + 1;
+  int nface = 0;
+  for (int e = 0; e < nelem; ++e) {
+    for (int f = 0; f < 4; ++f) {
+      const int nb = nbr[4 * e + f], nf = nbr_face[4 * e + f], id = face_of[4 * e + f];
+      if (nb < 0) return FR_ERR_UNSUPPORTED;  // EFR here is for meshes without boundary faces
+      if (nb >= nelem || nf < 0 || nf > 3 || id < 0) return FR_ERR_INVALID_ARG;
+      if (nbr[4 * nb + nf] != e || nbr_face[4 * nb + nf] != f || face_of[4 * nb + nf] != id)
+        return FR_ERR_INVALID_ARG;  // the neighbour relation must be symmetric
+      nface = std::max(nface, id + 1);
+    }
+  }
+  // trace faces: both sides implicit, numbered in increasing global face id
+  std::vector<int> trace_of_face(nface, -1);
+  for (int e = 0; e < nelem; ++e)
+    for (int f = 0; f < 4; ++f)
+      if (implicit[e] && implicit[nbr[4 * e + f]]) trace_of_face[face_of[4 * e + f]] = 0;
+  int ntrace = 0;
+  for (int id = 0; id < nface; ++id)
+    if (trace_of_face[id] == 0) trace_of_face[id] = ntrace++;
+  // vertex classes over element corners, joined through trace faces only
+  std::vector<int> parent(4 * static_cast<size_t>(nelem));
+  for (size_t i = 0; i < parent.size(); ++i) parent[i] = static_cast<int>(i);
+  std::vector<unsigned char> touched(parent.size(), 0);
+  for (int e = 0; e < nelem; ++e) {
+    if (!implicit[e]) continue;
+    for (int f = 0; f < 4; ++f) {
+      const int nb = nbr[4 * e + f], nf = nbr_face[4 * e + f];
+      if (!implicit[nb]) continue;
+      for (int end = 0; end < 2; ++end) {
+        const int i = 4 * e + kFaceCorner[f][end], j = 4 * nb + kFaceCorner[nf][end];
+        touched[i] = touched[j] = 1;
+        const int ri = find_root(parent, i), rj = find_root(parent, j);
+        if (ri != rj) parent[std::max(ri, rj)] = std::min(ri, rj);
+      }
+    }
+  }
+  std::vector<int> vertex_id(parent.size(), -1);
+  int nvert = 0;
+  for (size_t i = 0; i < parent.size(); ++i)  // roots are the smallest corners of their classes
+    if (touched[i] && find_root(parent, static_cast<int>(i)) == static_cast<int>(i)) vertex_id[i] = nvert++;
+  for (int e = 0; e < nelem; ++e) {
+    for (int f = 0; f < 4; ++f) {
+      int* out = node_of + (static_cast<size_t>(e) * 4 + f) * n;
+      const int nb = nbr[4 * e + f];
+      if (!implicit[e] || !implicit[nb]) {
+        std::fill(out, out + n, -1);
+        continue;
+      }
+      const int t = trace_of_face[face_of[4 * e + f]];
+      out[0] = vertex_id[find_root(parent, 4 * e + kFaceCorner[f][0])];
+      out[n - 1] = vertex_id[find_root(parent, 4 * e + kFaceCorner[f][1])];
+      for (int m = 1; m < n - 1; ++m) out[m] = nvert + t * (n - 2) + m - 1;
+    }
+  }
+  *nvert_out = nvert;
+  *nnode_out = nvert + ntrace * (n - 2);
+  return FR_OK;
+}
