@@ -373,6 +373,26 @@ const char* fr_status_string(int code);
 int efr_trace_nodes(int nelem, const int* nbr, const int* nbr_face, const int* face_of,
                     const unsigned char* implicit, int p, int* node_of, int* nvert_out, int* nnode_out);
 
+/* Trace layout of a quad mesh whose elements carry different degrees p_e (Sec. 3.2: the element
+ * blocks admit faces with different numbers of trace points), with wall and far-field faces.
+ * A face between degrees p- and p+ carries the max(p-, p+) + 1 Gauss points of the higher degree;
+ * a boundary face the p_e + 1 of its element.  A face has a trace when both sides are implicit,
+ * or when it is a boundary face of an implicit element.  Host only.
+ *   nbr, nbr_face, face_of, bc  host, (nelem, 4): connectivity as in fr_mesh_desc; bc = 1 (wall)
+ *                               or 2 (far field) where nbr < 0
+ *   implicit, p                 host, (nelem,): implicit flags, degrees 1..5
+ *   face_pts                    host, (nelem, 4) out: points of each element face
+ *   trace_of                    host, (nelem, 4) out: trace index of each element face, or -1;
+ *                               traces numbered in increasing global face id
+ *   trace_off                   host, (4 nelem + 1) capacity, out: trace t's points start at
+ *                               trace_off[t] (trace_off[ntrace] = all trace points)
+ *   ntrace_out                  host out
+ * Errors: FR_ERR_INVALID_ARG (null pointer, nelem <= 0, a degree outside 1..5, indices out of
+ * range, asymmetric connectivity, a boundary face that is neither wall nor far field). */
+int mixed_trace_layout(int nelem, const int* nbr, const int* nbr_face, const int* face_of, const int* bc,
+                       const unsigned char* implicit, const int* p, int* face_pts, int* trace_of, int* trace_off,
+                       int* ntrace_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,6 +39,7 @@ EXPORT = {"A": 0, "B": 1, "C": 2, "D": 3, "S": 4, "XB": 5, "xr": 6, "t_k": 7, "r
 # every symbol declared in include/hfr.h
 ABI_SYMBOLS = [
     "efr_trace_nodes",
+    "mixed_trace_layout",
     "fr_ctx_create",
     "fr_ctx_destroy",
     "fr_ctx_query",
@@ -218,6 +219,7 @@ def load_library(path: str = LIB_PATH):
     lib.fr_status_string.argtypes = [ctypes.c_int]
     lib.fr_status_string.restype = ctypes.c_char_p
     lib.efr_trace_nodes.argtypes = [ctypes.c_int, vp, vp, vp, vp, ctypes.c_int, vp, ip, ip]
+    lib.mixed_trace_layout.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp, ip]
     _lib = lib
     return lib
 
@@ -250,6 +252,28 @@ def efr_trace_nodes(nbr, nbr_face, face_of, implicit, p):
     if rc != 0:
         raise HfrError(rc)
     return out, nvert.value, nnode.value
+
+
+def mixed_trace_layout(nbr, nbr_face, face_of, bc, implicit, p):
+    """Trace layout of a mixed-degree quad mesh (host arrays): (face_pts (E, 4), trace_of (E, 4),
+    trace_off (ntrace + 1,)), all int32.  Raises HfrError on the library's error codes."""
+    import numpy as np
+
+    lib = load_library()
+    a = [np.ascontiguousarray(x, dtype=np.int32) for x in (nbr, nbr_face, face_of, bc)]
+    imp = np.ascontiguousarray(implicit, dtype=np.uint8)
+    deg = np.ascontiguousarray(p, dtype=np.int32)
+    E = int(a[0].shape[0])
+    face_pts = np.empty((E, 4), dtype=np.int32)
+    trace_of = np.empty((E, 4), dtype=np.int32)
+    trace_off = np.empty(4 * E + 1, dtype=np.int32)
+    ntrace = ctypes.c_int()
+    rc = lib.mixed_trace_layout(E, *(x.ctypes.data for x in a), imp.ctypes.data, deg.ctypes.data,
+                                face_pts.ctypes.data, trace_of.ctypes.data, trace_off.ctypes.data,
+                                ctypes.byref(ntrace))
+    if rc != 0:
+        raise HfrError(rc)
+    return face_pts, trace_of, trace_off[:ntrace.value + 1].copy()
 
 
 def _ptr(t):

@@ -93,3 +93,60 @@ extern "C" int efr_trace_nodes(int nelem, const int* nbr, const int* nbr_face, c
   *nnode_out = nvert + ntrace * (n - 2);
   return FR_OK;
 }
+
+// Trace layout of a mesh whose elements carry different degrees (faces between unequal degrees
+// carry the Gauss points of the higher one; boundary faces the element's own), with wall and
+// far-field faces: a face has a trace when both sides are implicit, or when it is a boundary face
+// of an implicit element; traces are numbered in increasing global face id and stored one after
+// the other, trace t holding face_pts points from trace_off[t].
+extern "C" int mixed_trace_layout(int nelem, const int* nbr, const int* nbr_face, const int* face_of, const int* bc,
+                                  const unsigned char* implicit, const int* p, int* face_pts, int* trace_of,
+                                  int* trace_off, int* ntrace_out) {
+  if (nelem <= 0 || !nbr || !nbr_face || !face_of || !bc || !implicit || !p || !face_pts || !trace_of ||
+      !trace_off || !ntrace_out)
+    return FR_ERR_INVALID_ARG;
+  int nface = 0;
+  for (int e = 0; e < nelem; ++e) {
+    if (p[e] < 1 || p[e] > 5) return FR_ERR_INVALID_ARG;
+    for (int f = 0; f < 4; ++f) {
+      const int nb = nbr[4 * e + f], nf = nbr_face[4 * e + f], id = face_of[4 * e + f];
+      if (id < 0) return FR_ERR_INVALID_ARG;
+      nface = std::max(nface, id + 1);
+      if (nb < 0) {
+        if (bc[4 * e + f] != 1 && bc[4 * e + f] != 2) return FR_ERR_INVALID_ARG;  // wall or far field
+        continue;
+      }
+      if (nb >= nelem || nf < 0 || nf > 3) return FR_ERR_INVALID_ARG;
+      if (nbr[4 * nb + nf] != e || nbr_face[4 * nb + nf] != f || face_of[4 * nb + nf] != id)
+        return FR_ERR_INVALID_ARG;
+    }
+  }
+  std::vector<int> trace_of_face(nface, -1), pts_of_face(nface, 0);
+  for (int e = 0; e < nelem; ++e) {
+    for (int f = 0; f < 4; ++f) {
+      const int nb = nbr[4 * e + f];
+      const int pts = (nb < 0 ? p[e] : std::max(p[e], p[nb])) + 1;
+      face_pts[4 * e + f] = pts;
+      const bool traced = implicit[e] && (nb < 0 || implicit[nb]);
+      if (traced) {
+        trace_of_face[face_of[4 * e + f]] = 0;
+        pts_of_face[face_of[4 * e + f]] = pts;
+      }
+    }
+  }
+  int ntrace = 0;
+  trace_off[0] = 0;
+  for (int id = 0; id < nface; ++id) {
+    if (trace_of_face[id] != 0) continue;
+    trace_of_face[id] = ntrace;
+    trace_off[ntrace + 1] = trace_off[ntrace] + pts_of_face[id];
+    ++ntrace;
+  }
+  for (int e = 0; e < nelem; ++e)
+    for (int f = 0; f < 4; ++f) {
+      const int nb = nbr[4 * e + f];
+      trace_of[4 * e + f] = (implicit[e] && (nb < 0 || implicit[nb])) ? trace_of_face[face_of[4 * e + f]] : -1;
+    }
+  *ntrace_out = ntrace;
+  return FR_OK;
+}

@@ -72,3 +72,36 @@ def test_layout_errors(pkg):
     walls = structured_quads(uniform_nodes(3, 0, 1), uniform_nodes(3, 0, 1), periodic=(True, False), p=2)
     with pytest.raises(pkg.HfrError, match="unsupported|not"):
         pkg.efr_trace_nodes(walls.nbr, walls.nbr_face, walls.face_of, walls.implicit, 2)
+
+
+def test_mixed_degree_layout_equals_the_oracle(pkg):
+    """Face point counts, trace numbering and trace offsets of mixed-degree meshes (periodic, and
+    the stretched wall band with wall and far-field faces) against the mixed-degree oracle."""
+    from oracle.fr_mixed import MixedDiscretisation
+    from oracle.physics import NavierStokes2D
+    from workloads.mesh import BC_FARFIELD, BC_WALL
+
+    rng = np.random.default_rng(5)
+    u_inf = np.array([1.0, 0.2, 0.0, 2.5])
+    meshes = []
+    for k in range(5):
+        nx, ny = int(rng.integers(3, 7)), int(rng.integers(3, 7))
+        periodic = (True, bool(k % 2))
+        m = structured_quads(uniform_nodes(nx, 0, 1), uniform_nodes(ny, 0, 1), periodic=periodic, p=2,
+                             implicit=rng.random(nx * ny) < 0.6, bc_y=(BC_WALL, BC_FARFIELD))
+        m.p = rng.integers(1, 6, size=nx * ny).astype(np.int32)
+        m.implicit[:nx] = True  # the wall row is implicit (walls on implicit elements only)
+        meshes.append(m)
+    for m in meshes:
+        d = MixedDiscretisation(m, NavierStokes2D(mu=1e-2), u_inf)
+        face_pts, trace_of, trace_off = pkg.mixed_trace_layout(m.nbr, m.nbr_face, m.face_of, m.bc, m.implicit, m.p)
+        assert np.array_equal(face_pts, d.nf) and np.array_equal(trace_of, d.tr_of)
+        assert np.array_equal(trace_off, np.concatenate([[0], np.cumsum(d.trace_npts)]))
+    m = meshes[0]  # walls below, far field above
+    assert np.any(m.nbr < 0)
+    bad = m.bc.copy()
+    bad[m.nbr < 0] = 0  # a boundary face with no boundary kind
+    with pytest.raises(pkg.HfrError, match="invalid"):
+        pkg.mixed_trace_layout(m.nbr, m.nbr_face, m.face_of, bad, m.implicit, m.p)
+    with pytest.raises(pkg.HfrError, match="invalid"):
+        pkg.mixed_trace_layout(m.nbr, m.nbr_face, m.face_of, m.bc, m.implicit, np.full(m.nelem, 6))
