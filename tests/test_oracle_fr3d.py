@@ -168,7 +168,7 @@ def test_trace_residuals_sum_to_the_net_element_flux():
         assert np.abs(g.sum(axis=(0, 1)) + total).max() < 1e-12 * np.abs(g).sum()
 
 
-# ------------------------------------------------------------------ walls (config-5 shape)
+# ------------------------------------------------- walls in a tanh-clustered hexahedral channel
 from oracle.blocks import EPS  # noqa: E402
 from oracle.boundary import WALL_FACE, BoundaryDiscretisation  # noqa: E402
 from workloads.mesh import BC_FARFIELD, BC_WALL, structured_quads, tanh_nodes  # noqa: E402

@@ -173,7 +173,7 @@ def test_condensed_newton_step_equals_the_monolithic_step(phys):
     assert max(np.abs(du1[e] - du2[e]).max() for e in du1) < 1e-12 * scale
 
 
-# ------------------------------------------------------------ boundary faces (config-4 shape)
+# ------------------------------------ wall and far-field faces on a stretched mixed-degree wall band
 from oracle.blocks import EPS  # noqa: E402
 from oracle.boundary import BoundaryDiscretisation  # noqa: E402
 from workloads.mesh import BC_FARFIELD, BC_WALL, geometric_nodes  # noqa: E402
