@@ -38,7 +38,7 @@ FARFIELD_FACE = 4
 class BoundaryDiscretisation(Discretisation):
     """FR/HFR operators for a quad mesh of uniform degree with wall and far-field faces."""
 
-    def __init__(self, mesh, physics, u_inf):
+    def __init__(self, mesh, physics, u_inf=None):
         p = int(mesh.p[0])
         if np.any(mesh.p != p):
             raise NotImplementedError("oracle: uniform p only")
@@ -50,7 +50,7 @@ class BoundaryDiscretisation(Discretisation):
         self.ns = self.n**2
         self.nv = physics.nv
         self.geo = QuadGeometry(mesh.verts, self.ref)
-        self.u_inf = np.asarray(u_inf, dtype=np.float64)
+        self.u_inf = None if u_inf is None else np.asarray(u_inf, dtype=np.float64)
         E = mesh.nelem
         imp = np.asarray(mesh.implicit, dtype=bool)
         self.imp = imp
@@ -67,6 +67,8 @@ class BoundaryDiscretisation(Discretisation):
             raise NotImplementedError("oracle: walls on explicit elements")
         if np.any(kind == WALL_FACE) and not isinstance(physics, NavierStokes2D):
             raise NotImplementedError("oracle: walls for Navier-Stokes only")
+        if np.any(kind == FARFIELD_FACE) and self.u_inf is None:
+            raise ValueError("far-field faces need u_inf")
         self.kind = kind
         self.bnd = bnd
         # faces with a trace: interior trace faces and the boundary faces of implicit elements
@@ -99,6 +101,8 @@ class BoundaryDiscretisation(Discretisation):
         """The other side's face state: the neighbour's, u_inf on far-field faces (the ghost
         state; wall faces always carry a trace)."""
         far = (self.kind == FARFIELD_FACE)[:, :, None, None]
+        if self.u_inf is None:
+            return self.neighbour(Uf)
         return np.where(far, np.broadcast_to(self.u_inf, Uf.shape), self.neighbour(Uf))
 
     def corrected_gradient(self, U, uhat_view):
@@ -168,7 +172,7 @@ class BoundaryDiscretisation(Discretisation):
         cx, cy = self.lift(Fn - FDn, signed=True)
         R = -(dxi[:, :, 0] + deta[:, :, 1] + cx + cy) / geo.J[:, :, None]
         # trace rows
-        G = np.where(far, Jf * s * ((Uf - uh) + (self.u_inf - uh)), Fn)
+        G = Fn if self.u_inf is None else np.where(far, Jf * s * ((Uf - uh) + (self.u_inf - uh)), Fn)
         if self.nv == 4:
             wall = Jf * np.concatenate([Fh[..., :1], s * uh[..., 1:3], Fh[..., 3:]], axis=-1)
             G = np.where(kind == WALL_FACE, wall, G)

@@ -23,6 +23,9 @@ defers the rest to its EFR reference.  Readings used here:
   of the interpolated flux jump, so the implicit region is conservative as a whole, as the paper
   states for EFR, while single elements are not.
 
+Boundary faces of implicit elements keep a discontinuous trace at their Gauss points with the wall
+and far-field rows of ``oracle.boundary``; their nodes are their own.
+
 Element-local trace layout is that of HFR (4 faces x (p+1) points x nv, a corner node appearing
 once on each of its two faces); the condensed system gathers both copies into one unknown.
 """
@@ -35,7 +38,8 @@ import scipy.sparse.linalg as spla
 
 from .basis import gauss_lobatto, lagrange
 from .blocks import element_blocks, EPS
-from .fr import Discretisation, IMEX_FACE, TRACE_FACE
+from .boundary import FARFIELD_FACE, WALL_FACE, BoundaryDiscretisation
+from .fr import IMEX_FACE, TRACE_FACE
 from .geometry import FACES_2D, _adjugate, _bilinear_derivs
 from .physics import cmax
 from .solve import condense, backsolve
@@ -44,12 +48,17 @@ from .solve import condense, backsolve
 FACE_CORNERS = ((0, 2), (1, 3), (0, 1), (2, 3))
 
 
-class EmbeddedDiscretisation(Discretisation):
-    """EFR operators for a quad mesh with a single polynomial degree p >= 1."""
+class EmbeddedDiscretisation(BoundaryDiscretisation):
+    """EFR operators for a quad mesh with a single polynomial degree p >= 1: the continuous GLL
+    trace on interior trace faces; on wall and far-field faces of implicit elements the
+    discontinuous trace at the Gauss points with the boundary rows of ``oracle.boundary`` (the
+    paper keeps discontinuous traces on boundaries, Sec. 4)."""
 
-    def __init__(self, mesh, physics):
-        super().__init__(mesh, physics)
+    def __init__(self, mesh, physics, u_inf=None):
+        super().__init__(mesh, physics, u_inf)
         n = self.n
+        self.efr = self.kind == TRACE_FACE  # continuous trace at the GLL points
+        self.bface = self.traced & self.bnd  # discontinuous boundary trace at the Gauss points
         self.xl, self.wl = gauss_lobatto(n)
         self.IGL = lagrange(self.ref.x, self.xl)  # (GLL point q, Gauss-aligned point m)
         self.ILG = lagrange(self.xl, self.ref.x)  # (Gauss-aligned point m, GLL point q)
@@ -71,9 +80,10 @@ class EmbeddedDiscretisation(Discretisation):
         self.normalL = NfL / self.JfL[..., None]
 
     def _number_nodes(self):
-        """node_of (E, 4, n): the global trace node at each GLL point of each element face
-        (-1 off trace faces).  Vertex nodes first (in increasing smallest element corner), then
-        the interior points of trace face t at nvert + t (p - 1) + m - 1."""
+        """node_of (E, 4, n): the global trace node at each point of each element face (-1 without
+        a trace).  Vertex nodes first (in increasing smallest element corner), then the p - 1
+        interior GLL points of each interior trace face (in increasing global face id), then the
+        n Gauss points of each boundary trace face (same order)."""
         m = self.mesh
         E, n = m.nelem, self.n
         parent = np.arange(4 * E)
@@ -87,7 +97,7 @@ class EmbeddedDiscretisation(Discretisation):
         touched = set()
         for e in range(E):
             for f in range(4):
-                if self.kind[e, f] != TRACE_FACE:
+                if not self.efr[e, f]:
                     continue
                 nb, nf = m.nbr[e, f], m.nbr_face[e, f]
                 for end in range(2):
@@ -99,32 +109,58 @@ class EmbeddedDiscretisation(Discretisation):
         roots = sorted({find(i) for i in touched})
         vid = {r: k for k, r in enumerate(roots)}
         self.nvert = len(roots)
-        self.nnode = self.nvert + self.ntrace * (n - 2)
+        fid = m.face_of
+        inner = {g: k for k, g in enumerate(np.unique(fid[self.efr]))}
+        outer = {g: k for k, g in enumerate(np.unique(fid[self.bface]))}
+        base = self.nvert + len(inner) * (n - 2)
+        self.nnode = base + len(outer) * n
         node_of = -np.ones((E, 4, n), dtype=np.int64)
         for e in range(E):
             for f in range(4):
-                t = self.tr_of[e, f]
-                if t < 0:
-                    continue
-                node_of[e, f, 0] = vid[find(4 * e + FACE_CORNERS[f][0])]
-                node_of[e, f, n - 1] = vid[find(4 * e + FACE_CORNERS[f][1])]
-                node_of[e, f, 1:n - 1] = self.nvert + t * (n - 2) + np.arange(n - 2)
+                if self.efr[e, f]:
+                    node_of[e, f, 0] = vid[find(4 * e + FACE_CORNERS[f][0])]
+                    node_of[e, f, n - 1] = vid[find(4 * e + FACE_CORNERS[f][1])]
+                    node_of[e, f, 1:n - 1] = self.nvert + inner[fid[e, f]] * (n - 2) + np.arange(n - 2)
+                elif self.bface[e, f]:
+                    node_of[e, f] = base + outer[fid[e, f]] * n + np.arange(n)
         self.node_of = node_of
 
     # ----------------------------------------------------------------- residual
-    def residual(self, U, uhat_view):
-        """R(u, u^) at every element and J_f F^.n at every element face point: at the GLL
-        points on trace faces, at the Gauss-aligned flux points elsewhere.
+    def corrected_gradient(self, U, uhat_view):
+        """Physical gradient q (E, Ns, 2, nv): the reference gradient of u^D plus the lifted jumps
+        u_bar - u_f: on EFR faces taken at the GLL points (u_bar = u^) and interpolated to the
+        Gauss-aligned points; on boundary trace faces u^ at the Gauss points; on the other faces
+        as in the uniform operator (ghost u_inf on explicit far-field faces)."""
+        geo = self.geo
+        kind = self.kind[:, :, None, None]
+        imp_e = self.imp[:, None, None, None]
+        Uf = self.interp_faces(U)
+        Uf_nb = self._other_state(Uf)
+        UfL = np.einsum("qm,efm...->efq...", self.IGL, Uf)
+        jump = np.where(self.bface[:, :, None, None], uhat_view - Uf, 0.5 * (Uf_nb - Uf))
+        jump = np.where(self.efr[:, :, None, None],
+                        np.einsum("mq,efq...->efm...", self.ILG, uhat_view - UfL), jump)
+        jump = np.where(kind == IMEX_FACE, np.where(imp_e, Uf_nb - Uf, 0.0 * Uf), jump)
+        dxi, deta = self.ref_derivative(U)
+        cx, cy = self.lift(jump, signed=False)
+        Qr = np.stack([dxi + cx, deta + cy], axis=2)
+        return np.einsum("esrc,esrv->escv", geo.S, Qr) / geo.J[:, :, None, None]
 
-        U (E, Ns, nv); uhat_view (E, 4, n, nv) the trace at the GLL points of each element face
-        (read on trace faces only).  Returns R (E, Ns, nv) and Fn (E, 4, n, nv)."""
+    def residual(self, U, uhat_view):
+        """R(u, u^) and J_f times each element face point's trace row: J_f F^.n at the GLL points
+        of EFR faces, the boundary rows at the Gauss points of boundary trace faces, J_f F^.n at the
+        flux points elsewhere.
+
+        U (E, Ns, nv); uhat_view (E, 4, n, nv) the trace at each element face's trace points.
+        Returns R (E, Ns, nv) and that array (E, 4, n, nv)."""
         ph = self.phys
         geo = self.geo
         kind = self.kind[:, :, None, None]
-        trace = kind == TRACE_FACE
+        efr = self.efr[:, :, None, None]
+        bface = self.bface[:, :, None, None]
         imp_e = self.imp[:, None, None, None]
         Uf = self.interp_faces(U)
-        Uf_nb = self.neighbour(Uf)
+        Uf_nb = self._other_state(Uf)
         UfL = np.einsum("qm,efm...->efq...", self.IGL, Uf)
         if ph.viscous:
             q = self.corrected_gradient(U, uhat_view)
@@ -143,7 +179,14 @@ class EmbeddedDiscretisation(Discretisation):
         def dotn(Fx, nrm):
             return np.einsum("...cv,...c->...v", Fx, nrm)
 
-        # FR and IMEX-interface faces: the uniform operator's fluxes at the flux points
+        def one_sided(uf, uh, qfx, nrm):
+            s = ph.stab(uh, nrm)[..., None]
+            Fh = dotn(ph.conv(uh), nrm) + s * (uf - uh)
+            if ph.viscous:
+                Fh = Fh - dotn(ph.visc(uh, qfx), nrm)
+            return Fh, s
+
+        # FR and IMEX-interface faces at the flux points
         nrm = geo.normal
         lam = cmax(ph.wave_speed(Uf, nrm), ph.wave_speed(Uf_nb, nrm))
         Fr = 0.5 * dotn(ph.conv(Uf) + ph.conv(Uf_nb), nrm) + 0.5 * lam[..., None] * (Uf - Uf_nb)
@@ -154,52 +197,41 @@ class EmbeddedDiscretisation(Discretisation):
             Fr_im = Fr - dotn(ph.visc(U_im, q_im), nrm)
         else:
             Fr_fr = Fr_im = Fr
-        FnG = geo.Jf[..., None] * np.where(kind == IMEX_FACE, Fr_im, Fr_fr)
-        # trace faces: one-sided flux at the GLL points (faces without a trace evaluate it at a
-        # harmless state and discard it)
-        nrmL = self.normalL
-        uh = np.where(trace, uhat_view, UfL)
-        Fh = dotn(ph.conv(uh), nrmL) + ph.stab(uh, nrmL)[..., None] * (UfL - uh)
-        if ph.viscous:
-            Fh = Fh - dotn(ph.visc(uh, qfL), nrmL)
-        FnL = self.JfL[..., None] * Fh
+        Jf = geo.Jf[..., None]
+        FnG = Jf * np.where(kind == IMEX_FACE, Fr_im, Fr_fr)
+        # boundary trace faces: one-sided flux and boundary rows at the flux points
+        uhB = np.where(bface, uhat_view, Uf)
+        FhB, sB = one_sided(Uf, uhB, qf if ph.viscous else None, nrm)
+        rowB = Jf * FhB
+        if self.u_inf is not None:
+            rowB = np.where(kind == FARFIELD_FACE, Jf * sB * ((Uf - uhB) + (self.u_inf - uhB)), rowB)
+        if self.nv == 4:
+            wall = Jf * np.concatenate([FhB[..., :1], sB * uhB[..., 1:3], FhB[..., 3:]], axis=-1)
+            rowB = np.where(kind == WALL_FACE, wall, rowB)
+        # EFR faces: one-sided flux at the GLL points, interpolated to the flux points for the lift
+        uhL = np.where(efr, uhat_view, UfL)
+        FhL, _ = one_sided(UfL, uhL, qfL if ph.viscous else None, self.normalL)
+        FnL = self.JfL[..., None] * FhL
         FnL_G = np.einsum("mq,efq...->efm...", self.ILG, FnL)
-        H = np.where(trace, FnL_G, FnG) - FDn
+        Fn = np.where(efr, FnL_G, np.where(bface, Jf * FhB, FnG))
         dxi, deta = self.ref_derivative(Ft)
-        cx, cy = self.lift(H, signed=True)
+        cx, cy = self.lift(Fn - FDn, signed=True)
         R = -(dxi[:, :, 0] + deta[:, :, 1] + cx + cy) / geo.J[:, :, None]
-        return R, np.where(trace, FnL, FnG)
-
-    def corrected_gradient(self, U, uhat_view):
-        """Physical gradient q (E, Ns, 2, nv): the reference gradient of u^D plus the lifted jumps
-        u_bar - u_f, taken on trace faces at the GLL points (u_bar = u^) and interpolated to the
-        Gauss-aligned points, on the other faces as in the uniform operator."""
-        geo = self.geo
-        kind = self.kind[:, :, None, None]
-        imp_e = self.imp[:, None, None, None]
-        Uf = self.interp_faces(U)
-        Uf_nb = self.neighbour(Uf)
-        UfL = np.einsum("qm,efm...->efq...", self.IGL, Uf)
-        jump = np.einsum("mq,efq...->efm...", self.ILG, uhat_view - UfL)
-        jump = np.where(kind == TRACE_FACE, jump, 0.5 * (Uf_nb - Uf))
-        jump = np.where(kind == IMEX_FACE, np.where(imp_e, Uf_nb - Uf, 0.0 * Uf), jump)
-        dxi, deta = self.ref_derivative(U)
-        cx, cy = self.lift(jump, signed=False)
-        Qr = np.stack([dxi + cx, deta + cy], axis=2)
-        return np.einsum("esrc,esrv->escv", geo.S, Qr) / geo.J[:, :, None, None]
+        return R, np.where(efr, FnL, np.where(bface, rowB, FnG))
 
     # ------------------------------------------------------------ trace helpers
     def trace_view(self, uhat):
-        """Global trace (nnode, nv) -> per element face GLL point (E, 4, n, nv); zero off trace."""
+        """Global trace (nnode, nv) -> per element face point (E, 4, n, nv); zero off trace."""
         view = np.zeros(self.node_of.shape + (self.nv,), dtype=uhat.dtype)
         has = self.node_of >= 0
         view[has] = uhat[self.node_of[has]]
         return view
 
     def trace_weights(self, Fn):
-        """Element contribution w^GLL_q Fn to the transmission conditions, zero off trace."""
-        gv = self.wl[None, None, :, None] * Fn
-        return np.where((self.kind == TRACE_FACE)[:, :, None, None], gv, 0.0)
+        """Element contribution to the trace rows: w^GLL on EFR faces, the Gauss weights on
+        boundary trace faces, zero elsewhere."""
+        w = np.where(self.efr[:, :, None], self.wl[None, None, :], self.geo.wface[None, None, :])
+        return np.where(self.traced[:, :, None, None], w[..., None] * Fn, 0.0)
 
     def assemble_trace(self, gview):
         """Sum element-face-point contributions (E, 4, n, nv) into the nodes (nnode, nv)."""
@@ -209,17 +241,23 @@ class EmbeddedDiscretisation(Discretisation):
         return g
 
     def initial_trace(self, U):
-        """Average, over every element face that carries a node, of that side's state there."""
+        """EFR nodes: the average, over every element face carrying the node, of that side's state
+        there; boundary trace faces as in ``oracle.boundary``."""
         UfL = np.einsum("qm,efm...->efq...", self.IGL, self.interp_faces(U))
-        has = self.node_of >= 0
         acc = np.zeros((self.nnode, self.nv))
         cnt = np.zeros(self.nnode)
+        has = (self.node_of >= 0) & self.efr[:, :, None]
         np.add.at(acc, self.node_of[has], UfL[has])
         np.add.at(cnt, self.node_of[has], 1.0)
-        return acc / cnt[:, None]
+        out = acc / np.maximum(cnt, 1.0)[:, None]
+        if np.any(self.bface):
+            hfr = BoundaryDiscretisation.initial_trace(self, U)  # (ntrace, n, nv) by trace face
+            for e, f in zip(*np.nonzero(self.bface)):
+                out[self.node_of[e, f]] = hfr[self.tr_of[e, f]]
+        return out
 
     def full_residual(self, U, uhat):
-        """R (E, Ns, nv) and the transmission residual g (nnode, nv)."""
+        """R (E, Ns, nv) and the trace residual g (nnode, nv)."""
         R, Fn = self.residual(U, self.trace_view(uhat))
         return R, self.assemble_trace(self.trace_weights(Fn))
 

@@ -254,3 +254,107 @@ def test_efr_imex_step_conserves_across_the_interface():
     mass1 = np.einsum("s,es,esv->v", W, d.geo.J, U1)
     assert np.abs(mass1 - mass0).max() < 1e-12 * np.abs(mass0).max()
     assert np.abs(U1 - U0).max() > 1e-4  # the step moves the state
+
+
+# ------------------------------------------------------- EFR with walls and far field
+from oracle.blocks import EPS  # noqa: E402
+from oracle.boundary import FARFIELD_FACE, WALL_FACE  # noqa: E402
+from workloads.mesh import BC_FARFIELD, BC_WALL  # noqa: E402
+
+NS_B = make_physics(dict(NS, mu=2e-2))
+REST = np.array([1.2, 0.0, 0.0, 2.0])
+U_INF = np.array([1.0, 0.3, 0.05, 2.6])
+
+
+def _wall_mesh(nx, ny, p, rows, bc_y, jitter=0.1, seed=0):
+    imp = np.zeros((ny, nx), bool)
+    imp[rows, :] = True
+    return structured_quads(uniform_nodes(nx, 0, 1), uniform_nodes(ny, 0, 1), periodic=(True, False),
+                            jitter=jitter, seed=seed, p=p, implicit=imp.reshape(-1), bc_y=bc_y)
+
+
+def _solve_g(d, U, uh):
+    for _ in range(30):
+        _, g = d.full_residual(U, uh)
+        if np.abs(g).max() < 1e-13:
+            return uh
+        Jg = np.empty((uh.size, uh.size))
+        for k in range(uh.size):
+            hp = uh.astype(np.complex128)
+            hp.reshape(-1)[k] += 1j * EPS
+            Jg[:, k] = d.full_residual(U.astype(np.complex128), hp)[1].imag.reshape(-1) / EPS
+        uh = uh - np.linalg.solve(Jg, g.reshape(-1)).reshape(uh.shape)
+    raise AssertionError("trace equations did not converge")
+
+
+def test_boundary_faces_keep_their_own_gauss_point_nodes():
+    m = _wall_mesh(4, 4, 3, [0, 1, 2, 3], (BC_WALL, BC_FARFIELD))
+    d = EmbeddedDiscretisation(m, NS_B, U_INF)
+    nb = int(d.bface.sum())
+    assert nb == 8 and d.efr.sum() == 2 * (4 * 4 + 4 * 3)
+    # vertices of the interior skeleton: 5 rows of 4 (boundary vertex rows met by x-faces only)
+    assert d.nvert == 5 * 4 and d.nnode == d.nvert + (d.efr.sum() // 2) * (d.n - 2) + nb * d.n
+    own = d.node_of[d.bface]
+    assert len(np.unique(own)) == own.size and own.min() >= d.nnode - nb * d.n
+
+
+def test_rest_state_between_walls_is_steady():
+    m = _wall_mesh(4, 5, 2, [0, 1, 3, 4], (BC_WALL, BC_WALL), jitter=0.15, seed=3)
+    d = EmbeddedDiscretisation(m, NS_B)
+    U = np.tile(REST, (m.nelem, d.ns, 1))
+    R, g = d.full_residual(U, d.initial_trace(U))
+    assert np.abs(R).max() < 1e-12 and np.abs(g).max() < 1e-12
+
+
+def test_walls_conserve_mass_and_energy_with_the_solved_efr_trace():
+    m = _wall_mesh(3, 4, 2, [0, 3], (BC_WALL, BC_WALL), seed=4)
+    d = EmbeddedDiscretisation(m, NS_B)
+    rng = np.random.default_rng(4)
+    U = REST + 0.05 * rng.standard_normal((m.nelem, d.ns, 4))
+    uh = _solve_g(d, U, d.initial_trace(U))
+    R, _ = d.full_residual(U, uh)
+    W = np.outer(d.ref.w, d.ref.w).reshape(-1)
+    total = np.einsum("s,es,esv->v", W, d.geo.J, R)
+    scale = np.einsum("s,es,esv->v", W, d.geo.J, np.abs(R))
+    assert abs(total[0]) < 1e-13 * scale[0] and abs(total[3]) < 1e-13 * scale[3]
+    assert np.abs(uh[d.node_of[d.bface]][..., 1:3]).max() < 1e-14  # no-slip at the wall nodes
+
+
+def test_far_field_nodes_hold_the_average_and_condensed_equals_monolithic():
+    m = _wall_mesh(3, 3, 2, [0, 1, 2], (BC_WALL, BC_FARFIELD), seed=5)
+    d = EmbeddedDiscretisation(m, NS_B, U_INF)
+    rng = np.random.default_rng(6)
+    U = U_INF * (1 + 1e-2 * rng.standard_normal((m.nelem, d.ns, 4)))
+    uh = _solve_g(d, U, d.initial_trace(U))
+    Uf = d.interp_faces(U)
+    far = d.bface & (d.kind == FARFIELD_FACE)
+    assert far.sum() == 3
+    assert np.abs(uh[d.node_of[far]] - 0.5 * (Uf[far] + U_INF)).max() < 1e-14
+    Ustar = U + 1e-3 * rng.standard_normal(U.shape)
+    a = condensed_newton_step(d, U, d.initial_trace(U), Ustar, 0.03)
+    b = monolithic_newton_step(d, U, d.initial_trace(U), Ustar, 0.03)
+    scale = max(np.abs(b[0]).max(), np.abs(b[1]).max())
+    assert scale > 1e-3 and max(np.abs(a[0] - b[0]).max(), np.abs(a[1] - b[1]).max()) < 1e-12 * scale
+
+
+def test_mean_corrected_gradient_with_boundary_traces():
+    """Per element of an all-implicit wall / far-field mesh: sum_i W_i J_i q_i = volume term + the
+    GLL face sums of u^ - u_f on EFR faces + the Gauss face sums of u^ - u_f on boundary faces."""
+    m = _wall_mesh(3, 4, 2, [0, 1, 2, 3], (BC_WALL, BC_FARFIELD), jitter=0.2, seed=7)
+    d = EmbeddedDiscretisation(m, NS_B, U_INF)
+    rng = np.random.default_rng(8)
+    U = U_INF + 0.1 * rng.standard_normal((m.nelem, d.ns, 4))
+    view = d.trace_view(U_INF + 0.1 * rng.standard_normal((d.nnode, 4)))
+    q = d.corrected_gradient(U, view)
+    W = np.outer(d.ref.w, d.ref.w).reshape(-1)
+    lhs = np.einsum("s,es,escv->ecv", W, d.geo.J, q)
+    dxi, deta = d.ref_derivative(U)
+    vol = np.einsum("s,esrc,esrv->ecv", W, d.geo.S, np.stack([dxi, deta], axis=2))
+    Uf = d.interp_faces(U)
+    UfL = np.einsum("qm,efmv->efqv", d.IGL, Uf)
+    efr = d.efr[:, :, None, None]
+    bf = d.bface[:, :, None, None]
+    face = np.einsum("q,efq,efqc,efqv->ecv", d.wl, d.JfL, d.normalL, np.where(efr, view - UfL, 0.0))
+    face += np.einsum("q,efq,efqc,efqv->ecv", d.geo.wface, d.geo.Jf, d.geo.normal, np.where(bf, view - Uf, 0.0))
+    assert np.all(d.efr | d.bface)  # every face carries a trace here
+    assert np.abs(lhs - vol - face).max() < 1e-12 * np.abs(lhs).max()
