@@ -310,6 +310,51 @@ def uneven_condense(pkg, torch, dev, n_elem=40000, steps=3):
                     "synchronise); FP32 shared-memory Gauss-Jordan + products"}
 
 
+def measure_pipe_peaks(pkg):
+    """FP64 / FP32 FMA and TF32 tensor-core rates of this GPU, measured now by the library's loop
+    kernels (fr_measure_peak, CUDA events): the denominators of the ALU- and tensor-bound
+    fractions.  Reported, never fatal."""
+    out = {}
+    for key, which in (("fp64_tflops_measured", 0), ("fp32_tflops_measured", 1), ("tf32_tflops_measured", 2)):
+        try:
+            out[key] = float(pkg.fr_measure_peak(which))
+        except Exception as exc:
+            out[key] = f"error: {exc}"
+    out["how"] = ("fr_measure_peak: FP64/FP32 8 independent FMA chains per thread, 8 CTAs x 256 threads per SM; "
+                  "TF32 tcgen05.mma kind::tf32 M=128 N=256 K=8 back to back, 2 CTAs per SM; CUDA events, after a "
+                  "warm-up launch")
+    return out
+
+
+def tight_agreement(pkg, torch, w, ctx_mixed, ctx_fp64, dev, tol=1e-11):
+    """The precision error of the mixed path, separated from the Newton tolerance: both paths
+    converge the same stage to a relative FP64 Newton residual of ``tol``; the mixed one with 0 and
+    1 FP64 refinement sweeps of its local solves.  Differences relative to the stage increment
+    (max norm over all DOF)."""
+    kw = dict(newton_tol=tol, newton_maxit=40, gmres_rtol=1e-6, gmres_maxit=5000)
+
+    def solve(ctx, refine):
+        u_n = torch.tensor(w.u0, device=dev)
+        uh = ctx.hfr_initial_trace(u_n)
+        R_hist = ctx.empty(3, *ctx.state_shape)
+        us = ctx.empty(*ctx.state_shape)
+        ctx.imex_stage(0, w.dt, u_n, us, uh, R_hist, **kw)
+        st = ctx.imex_stage(1, w.dt, u_n, us, uh, R_hist, refine=refine, **kw)
+        return us, st
+
+    graph = ctx_mixed.imex_stage_get_graph()
+    ref, st64 = solve(ctx_fp64, 0)
+    inc = (ref - torch.tensor(w.u0, device=dev)).abs().max().item()
+    out = {"newton_tol": tol, "gmres_rtol": kw["gmres_rtol"], "fp64_newton_iterations": st64["newton_iterations"]}
+    for refine in (0, 1):
+        us, st = solve(ctx_mixed, refine)
+        out[f"refine{refine}"] = {"max_rel_diff": (us - ref).abs().max().item() / inc,
+                                  "newton_iterations": st["newton_iterations"],
+                                  "gmres_iterations": st["gmres_iterations"], "converged": st["converged"]}
+    assert graph == ctx_mixed.imex_stage_get_graph()
+    return out
+
+
 def cpu_baseline(workload="vortex256"):
     """The FP64 oracle, as it stands, on a bounded sample of the same workload: the stage-1
     Newton solve of the same vortex on a PATCH x PATCH periodic patch at the workload's element
@@ -385,9 +430,9 @@ def kernel_rooflines(prof, stats, w, peaks, clocks, workload, cond_mode=2):
     ntrace = 2 * E
     nt_u = ntrace * bs
     mhz = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = NUM_SMS * FP32_PEAK_PER_SM_CLK * mhz * 1e6 / 1e12
+    alu_peak = peaks.get("fp32_tflops_measured") or NUM_SMS * FP32_PEAK_PER_SM_CLK * mhz * 1e6 / 1e12
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    tf32_peak = float(peaks.get("bf16_tflops", 1900.0)) * TF32_PER_BF16
+    tf32_peak = peaks.get("tf32_tflops_measured") or float(peaks.get("bf16_tflops", 1900.0)) * TF32_PER_BF16
     its = stats["gmres_iterations"] / max(stats["newton_iterations"], 1)
     out = {}
 
@@ -399,15 +444,27 @@ def kernel_rooflines(prof, stats, w, peaks, clocks, workload, cond_mode=2):
         tw = NCU_TRAFFIC_BYTES.get(workload, {})
         t = sum(tw[kk] for kk in kern.split("+")) if all(tw.get(kk) for kk in kern.split("+")) else None
         src = {"GB/s": "MEASURED_PEAKS.json hbm_gbs",
-               "TFLOP/s": f"FP32 lanes x {mhz:.0f} MHz x {NUM_SMS} SMs",
-               "TF32 TFLOP/s": f"MEASURED_PEAKS.json bf16_tflops x {TF32_PER_BF16} (nominal TF32 / BF16 ratio)"}[unit]
+               "TFLOP/s": ("fr_measure_peak FP32 FMA loop, this run" if peaks.get("fp32_tflops_measured")
+                           else f"FP32 lanes x {mhz:.0f} MHz x {NUM_SMS} SMs"),
+               "TF32 TFLOP/s": ("fr_measure_peak TF32 tcgen05 loop, this run" if peaks.get("tf32_tflops_measured")
+                                else f"MEASURED_PEAKS.json bf16_tflops x {TF32_PER_BF16} (nominal TF32 / BF16 ratio)")}[unit]
         return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit.replace("TF32 ", ""),
                 "frac": achieved / peak, "traffic": t, "kernel": kern, "avg_launch_ms": avg_ms, "total_ms": total_ms,
                 "peak_source": src}
 
     tot, a = avg("gmres")
-    per_it = E * nT * nT * 4 + ntrace * bs * bs * 4 + 4 * (its / 2 + 1) * nt_u * 4 + 2 * nt_u * 4
-    out["gmres"] = entry("k_gmres_cycle", "hbm", per_it * its / (a * 1e-3) / 1e9, hbm_peak, "GB/s", tot, a)
+    # algorithmic bytes of one restart cycle of its iterations: per iteration the S_k blocks
+    # (E nT^2 4 B) and the gathered / scattered trace vectors (E 2 nT 8 B), and at iteration
+    # k = 1..its the orthogonalisation's (k + 2) n_t 8 B
+    k_its = int(round(its))
+    alg = k_its * (E * nT * nT * 4 + E * 2 * nT * 8) + sum((k + 2) * nt_u * 8 for k in range(1, k_its + 1))
+    # bytes this implementation moves beyond those: the face-block inverses of the preconditioner
+    # (ntrace bs^2 4 B per iteration) and the deferred second Gram-Schmidt pass over the FP32 basis
+    extra = k_its * ntrace * bs * bs * 4 + sum((k + 1) * nt_u * 4 for k in range(1, k_its + 1))
+    out["gmres"] = entry("k_gmres_cycle", "hbm", alg / (a * 1e-3) / 1e9, hbm_peak, "GB/s", tot, a)
+    out["gmres"]["iterations_per_launch"] = k_its
+    out["gmres"]["algorithmic_bytes"] = alg
+    out["gmres"]["implementation_extra_bytes"] = extra
     tot, a = avg("condense_factor")
     inv = "k_inverse_tc" if cond_mode >= 2 else ("k_inverse_warp" if nA <= 64 else "k_inverse_rq")
     out["condense_factor"] = entry(inv, "alu", E * 2.0 * nA**3 / (a * 1e-3) / 1e12, alu_peak, "TFLOP/s", tot, a)
@@ -447,6 +504,8 @@ def main():
     ap.add_argument("--no-uneven", action="store_true", help="skip the uneven-degree condensation leg")
     ap.add_argument("--no-reuse", action="store_true", help="skip the Jacobian-reuse (imex_steps) leg")
     ap.add_argument("--no-tf32", action="store_true", help="skip the single-pass TF32 condensation leg")
+    ap.add_argument("--no-tight", action="store_true",
+                    help="skip the tight-tolerance agreement leg of the mixed and FP64 stages")
     ap.add_argument("--no-autotune", action="store_true",
                     help="profiling aid: keep the default kernel forms (timings under a profiler would mislead the tuner)")
     args = ap.parse_args()
@@ -476,6 +535,7 @@ def main():
     else:
         w = make_config(args.workload)
     l2buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB
+    pipe_peaks = measure_pipe_peaks(pkg)
     if args.paths != "both":  # profiling aid: one path, no JSON contract line
         prec = pkg.FR_PREC_FP32 if args.paths == "mixed" else pkg.FR_PREC_FP64
         r = time_path(pkg, torch, w, prec, args.refine if args.paths == "mixed" else 0, args.steps, args.warmup,
@@ -518,6 +578,8 @@ def main():
         e2e_ms, bi, bo = time_e2e(pkg, torch, head["ctx"], w, max(3, args.steps // 2), dev)
         e2e_ms = replica_max([e2e_ms], dist, dev)[0]
     peaks, peak_src = _peaks()
+    peaks = dict(peaks)
+    peaks.update({k: v for k, v in pipe_peaks.items() if isinstance(v, float)})
     pm = {k: v[0] for k, v in mixed["profile"].items()}
     dom, kroofs = kernel_rooflines(mixed["profile"], mixed["stats"], w, peaks, clocks, args.workload,
                                    mixed["ctx"].hfr_condense_get_mode())
@@ -564,7 +626,13 @@ def main():
         "gpu_launches_note": "kernels of libhfr.so executed per timed step (mixed path)",
         "clocks": clocks,
         "peaks_source": peak_src,
+        "pipe_peaks_measured": pipe_peaks,
     }
+    if not args.no_tight:
+        try:
+            line["mixed_vs_fp64_tight"] = tight_agreement(pkg, torch, w, mixed["ctx"], fp64["ctx"], dev)
+        except Exception as exc:  # reported, never fatal
+            line["mixed_vs_fp64_tight"] = {"error": str(exc)}
     if tf32 is not None:
         if "error" in tf32:
             line["tf32_single_pass"] = tf32

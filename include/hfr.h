@@ -19,8 +19,11 @@
  * Conventions
  *   - Every array argument is a DEVICE pointer owned by the caller unless it is marked
  *     "host".  The library never frees caller memory.  The library owns the workspace it
- *     allocates in fr_ctx_create (freed by fr_ctx_destroy); no entry point allocates after
- *     creation.
+ *     allocates in fr_ctx_create (freed by fr_ctx_destroy); no entry point that takes a context
+ *     allocates device memory after creation.  Two context-free calls do: hfr_condense_uneven
+ *     (a stream-ordered work buffer of 28 bytes per element, freed before it returns),
+ *     fr_barrier_selftest (its barrier words); the allocation-free condensation
+ *     hfr_condense_noalloc allocates nothing.
  *   - All work is enqueued on the CUDA stream given to fr_ctx_create.  Calls that report
  *     scalars to the host (norms, iteration counts) synchronise that stream.
  *   - Quadrilateral meshes, tensor-product Gauss-Legendre solution points, p = 1..5.
@@ -217,6 +220,11 @@ int hfr_backsolve(fr_ctx* ctx, const double* duhat, double* du, int refine);
  * 10 global t (FP64), 11 face-block-Jacobi inverses (ntrace x bs x bs, bs = n nv).  Block arrays
  * are in the context precision; dst must hold `bytes`. */
 int hfr_export(fr_ctx* ctx, int which, void* dst, size_t bytes);
+/* The reverse of hfr_export for the arrays 0..9 (A, B, C, D, S, X_B, x_r, t_k, r, s): overwrite the
+ * context array with `bytes` (exactly its size) from the caller device buffer src, e.g. to condense
+ * blocks formed elsewhere or to plant a defective block in a test.  A condensation held for
+ * FR_JAC_KEEP is dropped.  FR_ERR_INVALID_ARG for another array or size. */
+int hfr_import(fr_ctx* ctx, int which, const void* src, size_t bytes);
 
 /* One stage of the IMEX step (Algorithm 1):
  *   stage 0      : R_hist[0] = R(u_n, u^)                             (start of a step)
@@ -341,7 +349,11 @@ unsigned long long fr_kernel_launches(void);
  * The factors and pivots are kept in one file-scope device array of HFR_NOALLOC_SCRATCH_BYTES
  * (held by every GPU that loads the library until the process exits).  Limit:
  *   256 + round_up_256(nimplicit nA 4) + nimplicit nA^2 (8 for FP64, 4 for FP32) <= 16 MiB,
- * larger requests return FR_ERR_INVALID_ARG (nA <= 160).  The first call on a device looks up the
+ * larger requests return FR_ERR_INVALID_ARG (nA <= 160), before any work is enqueued, and so do
+ * shapes without a condensation kernel: FP32 needs 4 (nA (2 nA + nT + 2) + max(nA, nT) nA) bytes
+ * of shared memory within 227 KB unless (nA, nT) is one of (9,12), (16,16), (36,48), (64,64),
+ * (100,80); FP64 needs 8 (max(nA, nT) nA + nA (nT + 1)) bytes within 227 KB (LU) or twice the FP32
+ * figure.  The first call on a device looks up the
  * array's device address; make that first call before any stream capture.  Every call uses the
  * same array, so calls that overlap on the GPU (other streams, other threads) race.  No
  * cudaMalloc / cudaFree is made.  Synchronises the stream; FR_ERR_SINGULAR on a zero pivot. */
@@ -349,6 +361,16 @@ unsigned long long fr_kernel_launches(void);
 int hfr_condense_noalloc(int nimplicit, int nA, int nT, int precision, const void* A, const void* B, const void* C,
                          const void* D, const double* r, const double* s, void* XB, double* xr, void* S, double* t,
                          void* stream);
+
+/* Peak rate of one arithmetic pipe of the current device, measured now with CUDA events on
+ * `stream` (no counterpart in the paper; the denominators of roofline fractions).  which:
+ * 0 FP64 FMA, 1 FP32 FMA (8 independent FMA chains per thread, 8 CTAs of 256 threads per SM),
+ * 2 TF32 tensor core (tcgen05.mma kind::tf32, M = 128, N = 256, K = 8, issued back to back by one
+ * thread per CTA, two CTAs per SM).  *tflops (host): dense TFLOP/s, 2 flops per multiply-add.  A
+ * warm-up launch precedes the timed one; about 0.1-0.5 s in all.  Allocates nothing.  Returns
+ * FR_OK, FR_ERR_INVALID_ARG, FR_ERR_TIMEOUT (the bounded wait for the MMAs ran out) or
+ * FR_ERR_CUDA.  Synchronises the stream. */
+int fr_measure_peak(int which, void* stream, double* tflops);
 
 int fr_last_error(const fr_ctx* ctx, fr_error_info* info /* host */);
 const char* fr_status_string(int code);

@@ -69,6 +69,8 @@ ABI_SYMBOLS = [
     "fr_profile_read",
     "fr_kernel_launches",
     "hfr_condense_noalloc",
+    "hfr_import",
+    "fr_measure_peak",
     "fr_last_error",
     "fr_status_string",
 ]
@@ -215,6 +217,8 @@ def load_library(path: str = LIB_PATH):
     lib.fr_kernel_launches.restype = ctypes.c_ulonglong
     lib.hfr_condense_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp,
                                          dp, dp, dp, dp, dp, vp]
+    lib.hfr_import.argtypes = [vp, ctypes.c_int, dp, ctypes.c_size_t]
+    lib.fr_measure_peak.argtypes = [ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double)]
     lib.fr_last_error.argtypes = [vp, ctypes.POINTER(fr_error_info)]
     lib.fr_status_string.argtypes = [ctypes.c_int]
     lib.fr_status_string.restype = ctypes.c_char_p
@@ -245,6 +249,11 @@ def efr_trace_nodes(nbr, nbr_face, face_of, implicit, p):
     face_of = np.ascontiguousarray(face_of, dtype=np.int32)
     imp = np.ascontiguousarray(implicit, dtype=np.uint8)
     E = int(nbr.shape[0])
+    for a in (nbr, nbr_face, face_of):
+        if a.shape != (E, 4):
+            raise ValueError("efr_trace_nodes: connectivity arrays must have shape (E, 4)")
+    if imp.shape != (E,):
+        raise ValueError("efr_trace_nodes: implicit must have shape (E,)")
     out = np.empty((E, 4, max(int(p), 0) + 1), dtype=np.int32)
     nvert, nnode = ctypes.c_int(), ctypes.c_int()
     rc = lib.efr_trace_nodes(E, nbr.ctypes.data, nbr_face.ctypes.data, face_of.ctypes.data, imp.ctypes.data,
@@ -264,6 +273,10 @@ def mixed_trace_layout(nbr, nbr_face, face_of, bc, implicit, p):
     imp = np.ascontiguousarray(implicit, dtype=np.uint8)
     deg = np.ascontiguousarray(p, dtype=np.int32)
     E = int(a[0].shape[0])
+    if any(x.shape != (E, 4) for x in a):
+        raise ValueError("mixed_trace_layout: nbr, nbr_face, face_of and bc must have shape (E, 4)")
+    if imp.shape != (E,) or deg.shape != (E,):
+        raise ValueError("mixed_trace_layout: implicit and p must have shape (E,)")
     face_pts = np.empty((E, 4), dtype=np.int32)
     trace_of = np.empty((E, 4), dtype=np.int32)
     trace_off = np.empty(4 * E + 1, dtype=np.int32)
@@ -323,6 +336,20 @@ def hfr_condense_uneven(nA, nT, A, B, C, D, r, s, precision=FR_PREC_FP32, stream
         err.failed_element = failed.value
         raise err
     return out
+
+
+def fr_measure_peak(which, stream=None):
+    """Measured dense TFLOP/s of one pipe of the current device (see include/hfr.h): which 0 FP64
+    FMA, 1 FP32 FMA, 2 TF32 tensor core.  Raises HfrError on failure."""
+    import torch
+
+    lib = load_library()
+    out = ctypes.c_double(0.0)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib.fr_measure_peak(int(which), ctypes.c_void_p(st.cuda_stream), ctypes.byref(out))
+    if rc != 0:
+        raise HfrError(rc)
+    return out.value
 
 
 def fr_barrier_selftest(nblocks, absent_block=-1, rounds=4, timeout_s=0.05, stream=None):
@@ -509,6 +536,11 @@ class Context:
         out = self.torch.empty(*shp, dtype=dt, device=self.dev)
         self._check(self.lib.hfr_export(self.h, EXPORT[which], _ptr(out), out.numel() * out.element_size()))
         return out
+
+    def hfr_import(self, which: str, src):
+        """Overwrite a context array (A, B, C, D, S, XB, xr, t_k, r, s) with a device tensor of
+        exactly its size (C entry hfr_import)."""
+        self._check(self.lib.hfr_import(self.h, EXPORT[which], _ptr(src), src.numel() * src.element_size()))
 
     def imex_stage(self, stage, dt, u_n, u_stage, uhat, R_hist, newton_tol=1e-8, newton_maxit=20,
                    gmres_rtol=1e-3, gmres_maxit=500, refine=0):

@@ -1259,26 +1259,45 @@ extern "C" int hfr_backsolve(fr_ctx* ctx, const double* duhat, double* du, int r
   return FR_OK;
 }
 
+// the context array `which` of hfr_export / hfr_import and its size in bytes (nullptr: unknown)
+static void* ctx_array(fr_ctx* ctx, int which, size_t* need) {
+  const size_t pb = ctx->prec_bytes, Eim = ctx->Eim, nA = ctx->nA, nT = ctx->nT;
+  switch (which) {
+    case 0: *need = Eim * nA * nA * pb; return ctx->A;
+    case 1: *need = Eim * nA * nT * pb; return ctx->B;
+    case 2: *need = Eim * nT * nA * pb; return ctx->C;
+    case 3: *need = Eim * nT * nT * pb; return ctx->D;
+    case 4: *need = Eim * nT * nT * pb; return ctx->S;
+    case 5: *need = Eim * nA * nT * pb; return ctx->XB;
+    case 6: *need = Eim * nA * 8; return ctx->xr;
+    case 7: *need = Eim * nT * 8; return ctx->te;
+    case 8: *need = Eim * nA * 8; return ctx->r;
+    case 9: *need = Eim * nT * 8; return ctx->s;
+    case 10: *need = (size_t)ctx->ntrace * ctx->n * ctx->nv * 8; return ctx->tg;
+    case 11: *need = (size_t)ctx->ntrace * (ctx->n * ctx->nv) * (ctx->n * ctx->nv) * pb; return ctx->Pinv;
+  }
+  *need = 0;
+  return nullptr;
+}
+
+extern "C" int hfr_import(fr_ctx* ctx, int which, const void* src, size_t bytes) {
+  if (!ctx || !src) return FR_ERR_INVALID_ARG;
+  if (which < 0 || which > 9) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_import: array not importable");
+  size_t need = 0;
+  void* dst = ctx_array(ctx, which, &need);
+  if (!dst) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_import: unknown array");
+  if (bytes != need) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_import: size differs from the context array");
+  ctx->keep_valid = 0;  // a held condensation no longer matches the blocks
+  CK(cudaMemcpyAsync(dst, src, need, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return FR_OK;
+}
+
 extern "C" int hfr_export(fr_ctx* ctx, int which, void* dst, size_t bytes) {
   if (!ctx || !dst) return FR_ERR_INVALID_ARG;
-  const size_t pb = ctx->prec_bytes, Eim = ctx->Eim, nA = ctx->nA, nT = ctx->nT;
-  const void* src = nullptr;
   size_t need = 0;
-  switch (which) {
-    case 0: src = ctx->A; need = Eim * nA * nA * pb; break;
-    case 1: src = ctx->B; need = Eim * nA * nT * pb; break;
-    case 2: src = ctx->C; need = Eim * nT * nA * pb; break;
-    case 3: src = ctx->D; need = Eim * nT * nT * pb; break;
-    case 4: src = ctx->S; need = Eim * nT * nT * pb; break;
-    case 5: src = ctx->XB; need = Eim * nA * nT * pb; break;
-    case 6: src = ctx->xr; need = Eim * nA * 8; break;
-    case 7: src = ctx->te; need = Eim * nT * 8; break;
-    case 8: src = ctx->r; need = Eim * nA * 8; break;
-    case 9: src = ctx->s; need = Eim * nT * 8; break;
-    case 10: src = ctx->tg; need = (size_t)ctx->ntrace * ctx->n * ctx->nv * 8; break;
-    case 11: src = ctx->Pinv; need = (size_t)ctx->ntrace * (ctx->n * ctx->nv) * (ctx->n * ctx->nv) * pb; break;
-    default: return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_export: unknown array");
-  }
+  const void* src = ctx_array(ctx, which, &need);
+  if (!src) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_export: unknown array");
   if (bytes < need) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_export: destination too small");
   CK(cudaMemcpyAsync(dst, src, need, cudaMemcpyDeviceToDevice, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));

@@ -2417,6 +2417,15 @@ bool condense_uses_lu(int prec_bytes, int nA, int nT) {
   return prec_bytes == 8 && sizeof(double) * ((size_t)rows2 * nA + (size_t)nA * (nT + 1)) <= 227 * 1024;
 }
 
+bool condense_feasible(int prec_bytes, int nA, int nT) {
+  if (nA < 1 || nT < 1) return false;
+  if (condense_uses_lu(prec_bytes, nA, nT) || condense_tc_available(prec_bytes, nA, nT)) return true;
+  if ((nA == 9 && nT == 12) || (nA == 16 && nT == 16) || (nA == 36 && nT == 48) || (nA == 64 && nT == 64) ||
+      (nA == 100 && nT == 80))
+    return true;
+  return smem_elem_bytes((size_t)prec_bytes, nA, nT) <= 227 * 1024;
+}
+
 cudaError_t launch_condense_part(int prec_bytes, const CondArgs& a, cudaStream_t st, int part) {
   if (condense_uses_lu(prec_bytes, a.nA, a.nT)) return part == 0 ? cond_lu<double>(a, st) : cudaSuccess;
   return prec_bytes == 8 ? cond_dispatch<double>(a, st, part) : cond_dispatch<float>(a, st, part);

@@ -103,6 +103,8 @@ cudaError_t launch_condense_uneven(int prec_bytes, int n, const int* nA, const i
 // x = A^{-1} b with the stored factorisation (LU + interchanges or in-place inverse, as chosen
 // by condense_uses_lu), in place on b (Eim x nA, FP64 vectors).
 bool condense_uses_lu(int prec_bytes, int nA, int nT);
+// a condensation kernel exists for this precision and block shape (launch_condense succeeds)
+bool condense_feasible(int prec_bytes, int nA, int nT);
 // highest CondArgs::tc_mode available for this precision and block shape (0: none)
 int condense_tc_available(int prec_bytes, int nA, int nT);
 cudaError_t launch_lu_solve(int prec_bytes, int Eim, int nA, int nT, const void* LU, const int* piv, double* b,

@@ -28,7 +28,7 @@ int find_root(std::vector<int>& parent, int i) {
 
 }  // namespace
 
-extern "C" int efr_trace_nodes(int nelem, const int* nbr, const int* nbr_face, const int* face_of,
+static int efr_trace_nodes_impl(int nelem, const int* nbr, const int* nbr_face, const int* face_of,
                                const unsigned char* implicit, int p, int* node_of, int* nvert_out,
                                int* nnode_out) {
   if (nelem <= 0 || !nbr || !nbr_face || !face_of || !implicit || !node_of || !nvert_out || !nnode_out)
@@ -40,7 +40,7 @@ extern "C" int efr_trace_nodes(int nelem, const int* nbr, const int* nbr_face, c
     for (int f = 0; f < 4; ++f) {
       const int nb = nbr[4 * e + f], nf = nbr_face[4 * e + f], id = face_of[4 * e + f];
       if (nb < 0) return FR_ERR_UNSUPPORTED;  // EFR here is for meshes without boundary faces
-      if (nb >= nelem || nf < 0 || nf > 3 || id < 0) return FR_ERR_INVALID_ARG;
+      if (nb >= nelem || nf < 0 || nf > 3 || id < 0 || (long long)id >= 4LL * nelem) return FR_ERR_INVALID_ARG;
       if (nbr[4 * nb + nf] != e || nbr_face[4 * nb + nf] != f || face_of[4 * nb + nf] != id)
         return FR_ERR_INVALID_ARG;  // the neighbour relation must be symmetric
       nface = std::max(nface, id + 1);
@@ -99,7 +99,7 @@ extern "C" int efr_trace_nodes(int nelem, const int* nbr, const int* nbr_face, c
 // far-field faces: a face has a trace when both sides are implicit, or when it is a boundary face
 // of an implicit element; traces are numbered in increasing global face id and stored one after
 // the other, trace t holding face_pts points from trace_off[t].
-extern "C" int mixed_trace_layout(int nelem, const int* nbr, const int* nbr_face, const int* face_of, const int* bc,
+static int mixed_trace_layout_impl(int nelem, const int* nbr, const int* nbr_face, const int* face_of, const int* bc,
                                   const unsigned char* implicit, const int* p, int* face_pts, int* trace_of,
                                   int* trace_off, int* ntrace_out) {
   if (nelem <= 0 || !nbr || !nbr_face || !face_of || !bc || !implicit || !p || !face_pts || !trace_of ||
@@ -110,7 +110,7 @@ extern "C" int mixed_trace_layout(int nelem, const int* nbr, const int* nbr_face
     if (p[e] < 1 || p[e] > 5) return FR_ERR_INVALID_ARG;
     for (int f = 0; f < 4; ++f) {
       const int nb = nbr[4 * e + f], nf = nbr_face[4 * e + f], id = face_of[4 * e + f];
-      if (id < 0) return FR_ERR_INVALID_ARG;
+      if (id < 0 || (long long)id >= 4LL * nelem) return FR_ERR_INVALID_ARG;  // at most 4 nelem faces
       nface = std::max(nface, id + 1);
       if (nb < 0) {
         if (bc[4 * e + f] != 1 && bc[4 * e + f] != 2) return FR_ERR_INVALID_ARG;  // wall or far field
@@ -149,4 +149,26 @@ extern "C" int mixed_trace_layout(int nelem, const int* nbr, const int* nbr_face
     }
   *ntrace_out = ntrace;
   return FR_OK;
+}
+
+// the host vectors may fail to allocate: no C++ exception crosses the C ABI
+extern "C" int efr_trace_nodes(int nelem, const int* nbr, const int* nbr_face, const int* face_of,
+                               const unsigned char* implicit, int p, int* node_of, int* nvert_out,
+                               int* nnode_out) {
+  try {
+    return efr_trace_nodes_impl(nelem, nbr, nbr_face, face_of, implicit, p, node_of, nvert_out, nnode_out);
+  } catch (...) {
+    return FR_ERR_OOM;
+  }
+}
+
+extern "C" int mixed_trace_layout(int nelem, const int* nbr, const int* nbr_face, const int* face_of, const int* bc,
+                                  const unsigned char* implicit, const int* p, int* face_pts, int* trace_of,
+                                  int* trace_off, int* ntrace_out) {
+  try {
+    return mixed_trace_layout_impl(nelem, nbr, nbr_face, face_of, bc, implicit, p, face_pts, trace_of, trace_off,
+                                   ntrace_out);
+  } catch (...) {
+    return FR_ERR_OOM;
+  }
 }

@@ -46,6 +46,7 @@ extern "C" int hfr_condense_noalloc(int nimplicit, int nA, int nT, int precision
                                     double* xr, void* S, double* t, void* stream) {
   if (nimplicit < 0 || nA <= 0 || nT <= 0 || nA > 160 || (precision != FR_PREC_FP64 && precision != FR_PREC_FP32))
     return FR_ERR_INVALID_ARG;
+  if (!hfr::condense_feasible(precision == FR_PREC_FP64 ? 8 : 4, nA, nT)) return FR_ERR_INVALID_ARG;
   if (nimplicit == 0) return FR_OK;
   if (!A || !B || !C || !D || !r || !s || !XB || !xr || !S || !t) return FR_ERR_INVALID_ARG;
   const size_t pb = precision == FR_PREC_FP64 ? 8 : 4;

@@ -27,10 +27,16 @@ def test_gmres_cycle_rate_and_dominant_kernel():
     dom, out = bench.kernel_rooflines(PROF, STATS, _vortex256(), PEAKS, CLOCKS, "vortex256", 2)
     assert dom == "gmres"
     g = out["gmres"]
-    # per iteration: S blocks 65 536 x 80 x 80 x 4 B, face inverses 131 072 x 20 x 20 x 4 B, four basis
-    # passes over (18/2 + 1) vectors of 2 621 440 FP32 values, z and w
-    per_iteration = 65536 * 6400 * 4 + 131072 * 400 * 4 + 4 * 10 * 2621440 * 4 + 2 * 2621440 * 4
-    achieved = per_iteration * 18 / 8.1e-3 / 1e9
+    # algorithmic bytes of one 18-iteration cycle: per iteration the S blocks 65 536 x 80 x 80 x 4 B and
+    # the gathered and scattered FP64 trace values 65 536 x 2 x 80 x 8 B; at iteration k the
+    # orthogonalisation's (k + 2) x 2 621 440 x 8 B
+    alg = 18 * (65536 * 6400 * 4 + 65536 * 2 * 80 * 8) + sum((k + 2) * 2621440 * 8 for k in range(1, 19))
+    assert g["algorithmic_bytes"] == alg
+    assert abs(alg - 36.05e9) < 0.01e9  # about 36 GB per launch
+    # what the implementation moves beyond those is reported apart: the face-block inverses and the
+    # second Gram-Schmidt pass over the FP32 basis
+    assert g["implementation_extra_bytes"] == 18 * 131072 * 400 * 4 + sum((k + 1) * 2621440 * 4 for k in range(1, 19))
+    achieved = alg / 8.1e-3 / 1e9
     assert g["unit"] == "GB/s" and g["bound"] == "hbm"
     assert abs(g["achieved"] - achieved) < 1e-6 * achieved
     assert abs(g["frac"] - achieved / 6779.0) < 1e-9
@@ -64,3 +70,10 @@ def test_no_traffic_without_a_capture_and_fma_kernel_names():
     assert out["condense_products"]["kernel"] == "k_products_x+k_products_s"
     _, out = bench.kernel_rooflines(PROF, STATS, _vortex256(), PEAKS, CLOCKS, "vortex256", 3)
     assert out["condense_factor"]["kernel"] == "k_inverse_tc"
+
+
+def test_measured_pipe_peaks_replace_the_derived_ones():
+    peaks = dict(PEAKS, fp32_tflops_measured=70.0, tf32_tflops_measured=900.0)
+    _, out = bench.kernel_rooflines(PROF, STATS, _vortex256(), peaks, CLOCKS, "vortex256", 2)
+    assert out["jacobian"]["peak"] == 70.0 and "fr_measure_peak" in out["jacobian"]["peak_source"]
+    assert out["condense_factor"]["peak"] == 70.0

@@ -173,3 +173,31 @@ def test_full_size_stage_meets_newton_tolerance(name):
     # both solutions are within the Newton tolerance of the discrete solution: their difference
     # is the tolerance times the conditioning of the stage Jacobian relative to the increment
     assert np.abs(out["mixed"] - out["fp64"]).max() < 1e-6 * inc
+
+
+def test_full_size_mixed_precision_error_at_tight_newton_tolerance():
+    """The precision error of the mixed path apart from the Newton tolerance: the FP64 and the
+    mixed-precision stage of vortex256 (the benchmark workload) converged to a relative FP64
+    Newton residual of 1e-11, the mixed one with 0 and with 1 FP64 refinement sweep of its local
+    solves, agree to 1e-8 relative to the stage increment (the mixed-precision target)."""
+    w, _ = _workload("vortex256")
+    kw = dict(newton_tol=1e-11, newton_maxit=40, gmres_rtol=1e-6, gmres_maxit=5000)
+    u_n = torch.tensor(w.u0, device=DEV)
+
+    def solve(prec, refine):
+        ctx = pkg.Context(w.mesh, w.physics, precision=prec, tableau=pkg.FR_TAB_SDIRK2)
+        uh = ctx.hfr_initial_trace(u_n)
+        R_hist = ctx.empty(3, *ctx.state_shape)
+        us = ctx.empty(*ctx.state_shape)
+        ctx.imex_stage(0, w.dt, u_n, us, uh, R_hist, **kw)
+        st = ctx.imex_stage(1, w.dt, u_n, us, uh, R_hist, refine=refine, **kw)
+        ctx.close()
+        assert st["converged"], (prec, refine, st)
+        return us
+
+    ref = solve(pkg.FR_PREC_FP64, 0)
+    inc = (ref - u_n).abs().max().item()
+    for refine in (0, 1):
+        us = solve(pkg.FR_PREC_FP32, refine)
+        rel = (us - ref).abs().max().item() / inc
+        assert rel < 1e-8, (refine, rel)

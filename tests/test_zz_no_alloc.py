@@ -81,3 +81,45 @@ def test_noalloc_rejects_requests_beyond_the_scratch_size():
     # the limit formula of include/hfr.h: 400 such elements (about 12.6 MiB) fit, 4096 do not
     need = 256 + ((4 * 64 * 400 + 255) // 256) * 256 + 400 * 64 * 64 * 8
     assert need <= 16 << 20
+
+
+def test_noalloc_status_words_do_not_leak_between_calls():
+    """A call whose blocks hold a singular A (one element's A zeroed) reports FR_ERR_SINGULAR; the
+    next call on valid blocks starts from cleared status words and returns 0 with the same S and t
+    as the context condensation."""
+    import paper_2401_16632_gb300 as pkg
+    from workloads import make_config
+
+    w = make_config("vortex", n=4, p=3, re=500.0)
+    ctx = pkg.Context(w.mesh, w.physics, precision=pkg.FR_PREC_FP64)
+    u = torch.tensor(w.u0, device="cuda")
+    uh = ctx.hfr_initial_trace(u)
+    ctx.hfr_local_jacobian(u, uh, u * 0.999, 0.037)
+    ctx.hfr_condense(refine=0)
+    A, B, C, D = (ctx.hfr_export(k) for k in "ABCD")
+    r, s = ctx.hfr_export("r"), ctx.hfr_export("s")
+    ref_S, ref_t = ctx.hfr_export("S").cpu().numpy(), ctx.hfr_export("t_k").cpu().numpy()
+    E, nA, nT = A.shape[0], A.shape[1], B.shape[2]
+    XB, S = torch.empty_like(B), torch.empty_like(D)
+    xr = torch.empty((E, nA), dtype=torch.float64, device="cuda")
+    t = torch.empty((E, nT), dtype=torch.float64, device="cuda")
+    bad = A.clone()
+    bad[3].zero_()
+    assert pkg.hfr_condense_noalloc(bad, B, C, D, r, s, XB, xr, S, t, precision=pkg.FR_PREC_FP64) == 3
+    assert pkg.hfr_condense_noalloc(A, B, C, D, r, s, XB, xr, S, t, precision=pkg.FR_PREC_FP64) == 0
+    torch.cuda.synchronize()
+    assert _rel(S.cpu().numpy(), ref_S) < 1e-12
+    assert _rel(t.cpu().numpy(), ref_t) < 1e-12
+    ctx.close()
+
+
+def test_noalloc_rejects_shapes_without_a_kernel():
+    import ctypes
+
+    import paper_2401_16632_gb300 as pkg
+
+    lib = pkg.load_library()
+    z = ctypes.c_void_p(0x1000)
+    # one FP64 element of nA = nT = 150 fits the scratch (180 KB of factors) but no FP64
+    # condensation kernel holds its working set in shared memory: refused before any work
+    assert lib.hfr_condense_noalloc(1, 150, 150, pkg.FR_PREC_FP64, z, z, z, z, z, z, z, z, z, z, z) == 1
