@@ -349,11 +349,8 @@ unsigned long long fr_kernel_launches(void);
  * The factors and pivots are kept in one file-scope device array of HFR_NOALLOC_SCRATCH_BYTES
  * (held by every GPU that loads the library until the process exits).  Limit:
  *   256 + round_up_256(nimplicit nA 4) + nimplicit nA^2 (8 for FP64, 4 for FP32) <= 16 MiB,
- * larger requests return FR_ERR_INVALID_ARG (nA <= 160), before any work is enqueued, and so do
- * shapes without a condensation kernel: FP32 needs 4 (nA (2 nA + nT + 2) + max(nA, nT) nA) bytes
- * of shared memory within 227 KB unless (nA, nT) is one of (9,12), (16,16), (36,48), (64,64),
- * (100,80); FP64 needs 8 (max(nA, nT) nA + nA (nT + 1)) bytes within 227 KB (LU) or twice the FP32
- * figure.  The first call on a device looks up the
+ * larger requests, nA outside 1..160 and nT outside 1..16384 return FR_ERR_INVALID_ARG before any
+ * work is enqueued.  The first call on a device looks up the
  * array's device address; make that first call before any stream capture.  Every call uses the
  * same array, so calls that overlap on the GPU (other streams, other threads) race.  No
  * cudaMalloc / cudaFree is made.  Synchronises the stream; FR_ERR_SINGULAR on a zero pivot. */

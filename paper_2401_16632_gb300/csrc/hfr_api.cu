@@ -157,7 +157,7 @@ static int set_err(fr_ctx* c, int code, const char* msg, int elem = -1, int it =
   } while (0)
 
 // --------------------------------------------------------------------- reference element
-static void gauss_legendre_host(int n, double* x, double* w) {
+void hfr::gauss_legendre_nodes(int n, double* x, double* w) {
   for (int i = 0; i < n; ++i) {
     // classic initial guess, then Newton on P_n
     double z = cos(M_PI * (4.0 * (n - i) - 1.0) / (4.0 * n + 2.0));
@@ -184,11 +184,11 @@ static void gauss_legendre_host(int n, double* x, double* w) {
   }
 }
 
-static void build_ref(int p, RefOps& R) {
+void hfr::build_ref_ops(int p, RefOps& R) {
   memset(&R, 0, sizeof(R));
   const int n = p + 1;
   double x[HFR_MAXN], w[HFR_MAXN], bw[HFR_MAXN];
-  gauss_legendre_host(n, x, w);
+  hfr::gauss_legendre_nodes(n, x, w);
   for (int j = 0; j < n; ++j) {  // barycentric weights
     double prod = 1.0;
     for (int k = 0; k < n; ++k)
@@ -409,7 +409,7 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, const fr_config* cfg, voi
   ctx->pp.Pr = cfg->Pr;
   ctx->pp.lref = cfg->lref > 0 ? cfg->lref : 1.0;
   ctx->pp.theta = cfg->physics == FR_PHYS_EDAC ? cfg->theta : 0.0;
-  build_ref(ctx->p, ctx->ref);
+  hfr::build_ref_ops(ctx->p, ctx->ref);
 
   const int E = ctx->E, n = ctx->n, ns = ctx->ns, NF = 4 * n;
   // connectivity checks and face kinds
@@ -465,7 +465,7 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, const fr_config* cfg, voi
   std::vector<double> gsol((size_t)E * ns * 5), gface((size_t)E * NF * 3);
   ctx->xy_host.resize((size_t)E * ns * 2);
   double xg[HFR_MAXN], wg[HFR_MAXN];
-  gauss_legendre_host(n, xg, wg);
+  hfr::gauss_legendre_nodes(n, xg, wg);
   for (int e = 0; e < E; ++e) {
     const double* V = mesh->verts + (size_t)e * 8;
     for (int b = 0; b < n; ++b)
@@ -1133,7 +1133,7 @@ __global__ void k_modal_filter(int E, int nv, const double* __restrict__ F, cons
 static void modal_filter_operator(int p, double alpha, double s, int eta_c, double dt_ratio, double* F) {
   const int n = p + 1, ns = n * n, eta_max = 2 * p;
   double x[HFR_MAXN], w[HFR_MAXN], psi[HFR_MAXN][HFR_MAXN];  // psi[a][k] = psi_k(x_a)
-  gauss_legendre_host(n, x, w);
+  hfr::gauss_legendre_nodes(n, x, w);
   for (int a = 0; a < n; ++a) {
     double pm = 1.0, pk = x[a];
     for (int k = 0; k < n; ++k) {

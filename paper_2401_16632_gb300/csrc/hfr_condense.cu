@@ -2013,99 +2013,335 @@ static size_t smem_elem_bytes(size_t tb, int nA, int nT) {
   return tb * ((size_t)nA * nc + (size_t)big * nA + nc + nA) + sizeof(int) * (nA + 2) + nA;
 }
 
-cudaError_t launch_condense_uneven(int prec_bytes, int n, const int* nA, const int* nT, const void* A, const void* B,
-                                   const void* C, const void* D, const double* r, const double* s, void* LU, int* piv,
-                                   void* XB, double* xr, void* S, double* t, int* status, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  std::vector<int> shape(2 * (size_t)n), order(n);
-  std::vector<long long> off(5 * (size_t)n);
+// Large blocks, whose shared-memory working set exceeds 227 KB (FP64 from about nA = 100 with
+// nT > 80, FP32 beyond (144, 96)): one CTA of 256 threads per element, in place in global memory
+// (an element's slots, a few hundred KB, stay resident in L2 while its CTA works on them).
+//   1. LU with partial pivoting of A in the factor slot (largest |a|, lowest row on ties), the row
+//      operations applied to [B | r] in the X_B and x_r slots as they happen (forward elimination);
+//   2. back substitution of every right-hand side column, one thread per column;
+//   3. S = D - C X_B and t = s - C x_r, one thread per output entry.
+// A zero pivot sets DEV_ERR_SINGULAR with the element (the element's outputs are then undefined).
+constexpr int GLB_THREADS = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(GLB_THREADS) k_condense_global(const __grid_constant__ UnevenArgs a,
+                                                                 const int* __restrict__ list, int nlist,
+                                                                 int uni_nA, int uni_nT) {
+  __shared__ T prow_s[1024];
+  __shared__ double pkey_v[GLB_THREADS / 32];
+  __shared__ int pkey_i[GLB_THREADS / 32];
+  __shared__ int s_piv;
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int li = blockIdx.x; li < nlist; li += gridDim.x) {
+    // element k: from the tables, or (uni_nA > 0) the k-th of nlist blocks of one shape
+    const int k = list ? list[li] : li;
+    long long o[5];
+    int nA, nT;
+    if (uni_nA > 0) {
+      nA = uni_nA;
+      nT = uni_nT;
+      o[0] = (long long)k * nA * nA;
+      o[1] = (long long)k * nA * nT;
+      o[2] = (long long)k * nT * nT;
+      o[3] = (long long)k * nA;
+      o[4] = (long long)k * nT;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) o[q] = a.off[5 * (size_t)k + q];
+      nA = a.shape[2 * k];
+      nT = a.shape[2 * k + 1];
+    }
+    const T* A = reinterpret_cast<const T*>(a.A) + o[0];
+    const T* B = reinterpret_cast<const T*>(a.B) + o[1];
+    const T* C = reinterpret_cast<const T*>(a.C) + o[1];
+    const T* D = reinterpret_cast<const T*>(a.D) + o[2];
+    T* L = reinterpret_cast<T*>(a.LU) + o[0];
+    T* X = reinterpret_cast<T*>(a.XB) + o[1];
+    T* S = reinterpret_cast<T*>(a.S) + o[2];
+    const double* r = a.r + o[3];
+    double* xr = a.xr + o[3];
+    int* piv = a.piv + o[3];
+    const double* sv = a.s + o[4];
+    double* t = a.t + o[4];
+    for (size_t i = tid; i < (size_t)nA * nA; i += GLB_THREADS) L[i] = A[i];
+    for (size_t i = tid; i < (size_t)nA * nT; i += GLB_THREADS) X[i] = B[i];
+    for (int i = tid; i < nA; i += GLB_THREADS) xr[i] = r[i];
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    for (int j = 0; j < nA; ++j) {
+      // pivot search over rows j..nA-1
+      double bv = -1.0;
+      int bi = 0x7fffffff;
+      for (int i = j + tid; i < nA; i += GLB_THREADS) {
+        const double v = fabs((double)L[(size_t)i * nA + j]);
+        if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+      }
+      if (lane == 0) { pkey_v[wid] = bv; pkey_i[wid] = bi; }
+      __syncthreads();
+      if (tid == 0) {
+        double v = pkey_v[0];
+        int ii = pkey_i[0];
+        for (int q = 1; q < GLB_THREADS / 32; ++q)
+          if (pkey_v[q] > v || (pkey_v[q] == v && pkey_i[q] < ii)) { v = pkey_v[q]; ii = pkey_i[q]; }
+        s_piv = ii;
+        piv[j] = ii;
+        if (!(v > 0.0)) s_bad = 1;
+      }
+      __syncthreads();
+      if (s_bad) break;
+      const int pr = s_piv;
+      if (pr != j) {  // swap rows j and pr of L, X and x_r
+        for (int c = tid; c < nA; c += GLB_THREADS) {
+          const T u = L[(size_t)j * nA + c];
+          L[(size_t)j * nA + c] = L[(size_t)pr * nA + c];
+          L[(size_t)pr * nA + c] = u;
+        }
+        for (int c = tid; c < nT; c += GLB_THREADS) {
+          const T u = X[(size_t)j * nT + c];
+          X[(size_t)j * nT + c] = X[(size_t)pr * nT + c];
+          X[(size_t)pr * nT + c] = u;
+        }
+        if (tid == 0) {
+          const double u = xr[j];
+          xr[j] = xr[pr];
+          xr[pr] = u;
+        }
+      }
+      __syncthreads();
+      // pivot row (columns j+1.. of L, all of X) into shared memory in chunks of 1024
+      const T inv = T(1) / L[(size_t)j * nA + j];
+      const double xrj = xr[j];
+      const int ncol = (nA - j - 1) + nT;
+      for (int c0 = 0; c0 < ncol; c0 += 1024) {
+        const int cn = ncol - c0 < 1024 ? ncol - c0 : 1024;
+        for (int c = tid; c < cn; c += GLB_THREADS) {
+          const int cc = c0 + c;
+          prow_s[c] = cc < nA - j - 1 ? L[(size_t)j * nA + j + 1 + cc] : X[(size_t)j * nT + (cc - (nA - j - 1))];
+        }
+        __syncthreads();
+        // rows below: one warp per row, lanes over the columns
+        for (int i = j + 1 + wid; i < nA; i += GLB_THREADS / 32) {
+          T* Li = L + (size_t)i * nA;
+          const T l = Li[j] * inv;
+          for (int c = lane; c < cn; c += 32) {
+            const int cc = c0 + c;
+            if (cc < nA - j - 1)
+              Li[j + 1 + cc] -= l * prow_s[c];
+            else
+              X[(size_t)i * nT + (cc - (nA - j - 1))] -= l * prow_s[c];
+          }
+          if (c0 + 1024 >= ncol) {  // last chunk: store the multiplier and update x_r
+            __syncwarp();
+            if (lane == 0) {
+              Li[j] = l;
+              xr[i] -= (double)l * xrj;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    if (s_bad) {
+      if (tid == 0) {
+        atomicOr(a.status, DEV_ERR_SINGULAR);
+        atomicMin(a.status + 1, k);
+      }
+      __syncthreads();
+      continue;
+    }
+    // back substitution U x = y for the nT + 1 columns (X_B, then x_r), one thread per column
+    for (int col = tid; col <= nT; col += GLB_THREADS) {
+      for (int jj = nA - 1; jj >= 0; --jj) {
+        const T* Lr = L + (size_t)jj * nA;
+        double acc = col < nT ? (double)X[(size_t)jj * nT + col] : xr[jj];
+        for (int c = jj + 1; c < nA; ++c) acc -= (double)Lr[c] * (col < nT ? (double)X[(size_t)c * nT + col] : xr[c]);
+        acc /= (double)Lr[jj];
+        if (col < nT)
+          X[(size_t)jj * nT + col] = T(acc);
+        else
+          xr[jj] = acc;
+      }
+    }
+    __syncthreads();
+    // S = D - C X_B, t = s - C x_r
+    for (int e = tid; e < nT * (nT + 1); e += GLB_THREADS) {
+      const int row = e / (nT + 1), col = e % (nT + 1);
+      const T* Cr = C + (size_t)row * nA;
+      double acc = 0.0;
+      if (col < nT) {
+        for (int c = 0; c < nA; ++c) acc += (double)Cr[c] * (double)X[(size_t)c * nT + col];
+        S[(size_t)row * nT + col] = T((double)D[(size_t)row * nT + col] - acc);
+      } else {
+        for (int c = 0; c < nA; ++c) acc += (double)Cr[c] * xr[c];
+        t[row] = sv[row] - acc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+bool uneven_fits_smem(int prec_bytes, int nA, int nT) {
+  return smem_elem_bytes((size_t)prec_bytes, nA, nT) <= 227 * 1024;
+}
+
+// Host tables of an uneven launch: per element offsets (A, B/C, D, nA-, nT-vectors), shapes, the
+// shared-memory elements' order (most expensive first) and bundles, and the elements too large for
+// shared memory (global-memory kernel).
+int uneven_tables(int prec_bytes, int n, const int* nA, const int* nT, UnevenTables* tb) {
+  tb->off.assign(5 * (size_t)n, 0);
+  tb->shape.assign(2 * (size_t)n, 0);
+  tb->order.clear();
+  tb->bundle.clear();
+  tb->global.clear();
+  tb->smem = 0;
   long long oa = 0, ob = 0, od = 0, ova = 0, ovt = 0;
-  size_t smem = 0;
   for (int k = 0; k < n; ++k) {
-    if (nA[k] < 1 || nT[k] < 1) return cudaErrorInvalidValue;
-    shape[2 * k] = nA[k];
-    shape[2 * k + 1] = nT[k];
-    off[5 * k + 0] = oa;
-    off[5 * k + 1] = ob;
-    off[5 * k + 2] = od;
-    off[5 * k + 3] = ova;
-    off[5 * k + 4] = ovt;
+    if (nA[k] < 1 || nT[k] < 1 || nT[k] > 16384) return -1;
+    tb->shape[2 * k] = nA[k];
+    tb->shape[2 * k + 1] = nT[k];
+    long long* o = &tb->off[5 * (size_t)k];
+    o[0] = oa;
+    o[1] = ob;
+    o[2] = od;
+    o[3] = ova;
+    o[4] = ovt;
     oa += (long long)nA[k] * nA[k];
     ob += (long long)nA[k] * nT[k];
     od += (long long)nT[k] * nT[k];
     ova += nA[k];
     ovt += nT[k];
-    const size_t sb = smem_elem_bytes(prec_bytes, nA[k], nT[k]);
-    smem = sb > smem ? sb : smem;
-    order[k] = k;
+    if (uneven_fits_smem(prec_bytes, nA[k], nT[k])) {
+      tb->order.push_back(k);
+      const size_t sb = smem_elem_bytes(prec_bytes, nA[k], nT[k]);
+      tb->smem = sb > tb->smem ? sb : tb->smem;
+    } else {
+      tb->global.push_back(k);
+    }
   }
-  if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  // most expensive first (Gauss-Jordan ~ nA^2 (nA + nT), products ~ nT^2 nA)
   auto cost = [&](int k) {
-    const double a = nA[k], b = nT[k];
-    return a * a * (a + b) + b * b * a;
+    const double x = nA[k], y = nT[k];
+    return x * x * (x + y) + y * y * x;
   };
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
-  // bundles: runs of one shape in that order, as many elements per CTA as fit in its memory (a
-  // power of two, at most UNEVEN_MAX_GROUPS)
-  std::vector<int> bund;
-  for (int i = 0; i < n;) {
-    const int k0 = order[i];
+  std::stable_sort(tb->order.begin(), tb->order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+  std::stable_sort(tb->global.begin(), tb->global.end(), [&](int x, int y) { return cost(x) > cost(y); });
+  const int m = (int)tb->order.size();
+  for (int i = 0; i < m;) {
+    const int k0 = tb->order[i];
     int j = i;
-    while (j < n && nA[order[j]] == nA[k0] && nT[order[j]] == nT[k0]) ++j;
+    while (j < m && nA[tb->order[j]] == nA[k0] && nT[tb->order[j]] == nT[k0]) ++j;
     const size_t stride = (smem_elem_bytes(prec_bytes, nA[k0], nT[k0]) + 15) / 16 * 16;
     int groups = 1;
-    while (groups < UNEVEN_MAX_GROUPS && (size_t)(2 * groups) * stride <= smem) groups *= 2;
+    while (groups < UNEVEN_MAX_GROUPS && (size_t)(2 * groups) * stride <= tb->smem) groups *= 2;
     for (int q = i; q < j; q += groups) {
-      bund.push_back(q);
-      bund.push_back(j - q < groups ? j - q : groups);
-      bund.push_back(groups);
-      bund.push_back((int)stride);
+      tb->bundle.push_back(q);
+      tb->bundle.push_back(j - q < groups ? j - q : groups);
+      tb->bundle.push_back(groups);
+      tb->bundle.push_back((int)stride);
     }
     i = j;
   }
-  const int nb = (int)(bund.size() / 4);
-  void* dbuf = nullptr;
-  const size_t bytes_i = sizeof(int) * (3 * (size_t)n + bund.size()), bytes_o = sizeof(long long) * off.size();
-  cudaError_t e = cudaMallocAsync(&dbuf, bytes_o + bytes_i, st);
-  if (e != cudaSuccess) return e;
+  return 0;
+}
+
+size_t uneven_dev_bytes(const UnevenTables& tb) {
+  return sizeof(long long) * tb.off.size() +
+         sizeof(int) * (tb.order.size() + tb.shape.size() + tb.bundle.size() + tb.global.size()) + 64;
+}
+
+cudaError_t uneven_upload(const UnevenTables& tb, void* dbuf, UnevenDev* dv, cudaStream_t st) {
   long long* d_off = reinterpret_cast<long long*>(dbuf);
-  int* d_order = reinterpret_cast<int*>(d_off + off.size());
-  int* d_shape = d_order + n;
-  int* d_bund = d_shape + 2 * (size_t)n;
-  UnevenArgs ua{nb, d_bund, d_order, d_shape, d_off, A, B, C, D, r, s, LU, piv, XB, xr, S, t, status};
+  int* d_order = reinterpret_cast<int*>(d_off + tb.off.size());
+  int* d_shape = d_order + tb.order.size();
+  int* d_bund = d_shape + tb.shape.size();
+  int* d_glob = d_bund + tb.bundle.size();
+  cudaError_t e;
+  if (!tb.off.empty() &&
+      (e = cudaMemcpyAsync(d_off, tb.off.data(), sizeof(long long) * tb.off.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return e;
+  if (!tb.order.empty() &&
+      (e = cudaMemcpyAsync(d_order, tb.order.data(), sizeof(int) * tb.order.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return e;
+  if (!tb.shape.empty() &&
+      (e = cudaMemcpyAsync(d_shape, tb.shape.data(), sizeof(int) * tb.shape.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return e;
+  if (!tb.bundle.empty() &&
+      (e = cudaMemcpyAsync(d_bund, tb.bundle.data(), sizeof(int) * tb.bundle.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return e;
+  if (!tb.global.empty() &&
+      (e = cudaMemcpyAsync(d_glob, tb.global.data(), sizeof(int) * tb.global.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return e;
+  dv->off = d_off;
+  dv->order = d_order;
+  dv->shape = d_shape;
+  dv->bundle = d_bund;
+  dv->global = d_glob;
+  dv->nb = (int)(tb.bundle.size() / 4);
+  dv->nglobal = (int)tb.global.size();
+  dv->smem = tb.smem;
+  return cudaSuccess;
+}
+
+cudaError_t launch_condense_uneven_dev(int prec_bytes, const UnevenDev& dv, const void* A, const void* B, const void* C,
+                                       const void* D, const double* r, const double* s, void* LU, int* piv, void* XB,
+                                       double* xr, void* S, double* t, int* status, cudaStream_t st) {
+  UnevenArgs ua{dv.nb, dv.bundle, dv.order, dv.shape, dv.off, A, B, C, D, r, s, LU, piv, XB, xr, S, t, status};
   int dev = 0, nsm = 0, occ = 0;
-  if ((e = cudaMemcpyAsync(d_off, off.data(), bytes_o, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(d_shape, shape.data(), sizeof(int) * 2 * n, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(d_bund, bund.data(), sizeof(int) * bund.size(), cudaMemcpyHostToDevice, st)) !=
-          cudaSuccess)
-    goto done;
-  if (prec_bytes == 8) {
-    if ((e = cudaFuncSetAttribute(k_condense_uneven<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-        cudaSuccess)
-      goto done;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_condense_uneven<double>, UNEVEN_THREADS, smem);
-  } else {
-    if ((e = cudaFuncSetAttribute(k_condense_uneven<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-        cudaSuccess)
-      goto done;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_condense_uneven<float>, UNEVEN_THREADS, smem);
-  }
-  if (e != cudaSuccess) goto done;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) goto done;
-  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) goto done;
-  {
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if (dv.nb > 0) {
+    const size_t smem = dv.smem;
+    if (prec_bytes == 8) {
+      if ((e = cudaFuncSetAttribute(k_condense_uneven<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return e;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_condense_uneven<double>, UNEVEN_THREADS, smem);
+    } else {
+      if ((e = cudaFuncSetAttribute(k_condense_uneven<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return e;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_condense_uneven<float>, UNEVEN_THREADS, smem);
+    }
+    if (e != cudaSuccess) return e;
     int grid = nsm * (occ < 1 ? 1 : occ);
-    grid = nb < grid ? nb : grid;
+    grid = dv.nb < grid ? dv.nb : grid;
     if (prec_bytes == 8)
       (hfr::count_launch(), k_condense_uneven<double><<<grid, UNEVEN_THREADS, smem, st>>>(ua));
     else
       (hfr::count_launch(), k_condense_uneven<float><<<grid, UNEVEN_THREADS, smem, st>>>(ua));
-    e = cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-done:
-  // the host vectors must outlive their copies; the work buffer is freed in stream order
+  if (dv.nglobal > 0) {
+    int grid = 4 * nsm;
+    grid = dv.nglobal < grid ? dv.nglobal : grid;
+    if (prec_bytes == 8)
+      (hfr::count_launch(), k_condense_global<double><<<grid, GLB_THREADS, 0, st>>>(ua, dv.global, dv.nglobal, 0, 0));
+    else
+      (hfr::count_launch(), k_condense_global<float><<<grid, GLB_THREADS, 0, st>>>(ua, dv.global, dv.nglobal, 0, 0));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_condense_uneven(int prec_bytes, int n, const int* nA, const int* nT, const void* A, const void* B,
+                                   const void* C, const void* D, const double* r, const double* s, void* LU, int* piv,
+                                   void* XB, double* xr, void* S, double* t, int* status, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  UnevenTables tb;
+  if (uneven_tables(prec_bytes, n, nA, nT, &tb) != 0) return cudaErrorInvalidValue;
+  void* dbuf = nullptr;
+  cudaError_t e = cudaMallocAsync(&dbuf, uneven_dev_bytes(tb), st);
+  if (e != cudaSuccess) return e;
+  UnevenDev dv;
+  e = uneven_upload(tb, dbuf, &dv, st);
+  if (e == cudaSuccess)
+    e = launch_condense_uneven_dev(prec_bytes, dv, A, B, C, D, r, s, LU, piv, XB, xr, S, t, status, st);
+  // the host tables must outlive their copies; the work buffer is freed in stream order
   cudaStreamSynchronize(st);
   cudaFreeAsync(dbuf, st);
   cudaStreamSynchronize(st);
@@ -2366,9 +2602,22 @@ static cudaError_t cond_reg(const CondArgs& a, cudaStream_t st) {
 }
 
 template <typename T>
+static cudaError_t cond_global_uniform(const CondArgs& a, cudaStream_t st) {
+  UnevenArgs ua{0, nullptr, nullptr, nullptr, nullptr, a.A, a.B, a.C, a.D, a.r, a.s, a.LU, a.piv, a.XB, a.xr, a.S, a.t,
+                a.status};
+  int dev = 0, nsm = 0;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int grid = a.Eim < 4 * nsm ? a.Eim : 4 * nsm;
+  (hfr::count_launch(), k_condense_global<T><<<grid, GLB_THREADS, 0, st>>>(ua, nullptr, a.Eim, a.nA, a.nT));
+  return cudaGetLastError();
+}
+
+template <typename T>
 static cudaError_t cond_smem(const CondArgs& a, cudaStream_t st) {
   const size_t smem = smem_elem_bytes(sizeof(T), a.nA, a.nT);
-  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  if (smem > 227 * 1024) return cond_global_uniform<T>(a, st);  // LU factors and pivots
   cudaError_t err = cudaFuncSetAttribute(k_condense_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   (hfr::count_launch(), k_condense_smem<T><<<a.Eim, GJS_THREADS, smem, st>>>(a));
@@ -2412,22 +2661,30 @@ int condense_tc_available(int prec_bytes, int nA, int nT) {
   return prec_bytes == 4 && ((nA == 100 && nT == 80) || (nA == 64 && nT == 64) || (nA == 36 && nT == 48)) ? 2 : 0;
 }
 
-bool condense_uses_lu(int prec_bytes, int nA, int nT) {
+static bool lu_fits_smem(int prec_bytes, int nA, int nT) {
   const int rows2 = nA > nT ? nA : nT;
   return prec_bytes == 8 && sizeof(double) * ((size_t)rows2 * nA + (size_t)nA * (nT + 1)) <= 227 * 1024;
 }
+static bool reg_shape(int nA, int nT) {
+  return (nA == 9 && nT == 12) || (nA == 16 && nT == 16) || (nA == 36 && nT == 48) || (nA == 64 && nT == 64) ||
+         (nA == 100 && nT == 80);
+}
+// the condensation of this shape runs the global-memory kernel (LU factors, not an inverse)
+static bool needs_global(int prec_bytes, int nA, int nT) {
+  return !lu_fits_smem(prec_bytes, nA, nT) && !condense_tc_available(prec_bytes, nA, nT) && !reg_shape(nA, nT) &&
+         smem_elem_bytes((size_t)prec_bytes, nA, nT) > 227 * 1024;
+}
+
+bool condense_uses_lu(int prec_bytes, int nA, int nT) {
+  return lu_fits_smem(prec_bytes, nA, nT) || needs_global(prec_bytes, nA, nT);
+}
 
 bool condense_feasible(int prec_bytes, int nA, int nT) {
-  if (nA < 1 || nT < 1) return false;
-  if (condense_uses_lu(prec_bytes, nA, nT) || condense_tc_available(prec_bytes, nA, nT)) return true;
-  if ((nA == 9 && nT == 12) || (nA == 16 && nT == 16) || (nA == 36 && nT == 48) || (nA == 64 && nT == 64) ||
-      (nA == 100 && nT == 80))
-    return true;
-  return smem_elem_bytes((size_t)prec_bytes, nA, nT) <= 227 * 1024;
+  return nA >= 1 && nT >= 1 && nA <= 32 * INV_SLOTS && nT <= 16384 && (prec_bytes == 4 || prec_bytes == 8);
 }
 
 cudaError_t launch_condense_part(int prec_bytes, const CondArgs& a, cudaStream_t st, int part) {
-  if (condense_uses_lu(prec_bytes, a.nA, a.nT)) return part == 0 ? cond_lu<double>(a, st) : cudaSuccess;
+  if (lu_fits_smem(prec_bytes, a.nA, a.nT)) return part == 0 ? cond_lu<double>(a, st) : cudaSuccess;
   return prec_bytes == 8 ? cond_dispatch<double>(a, st, part) : cond_dispatch<float>(a, st, part);
 }
 
@@ -2443,8 +2700,10 @@ cudaError_t launch_lu_solve(int prec_bytes, int Eim, int nA, int nT_of_last, con
   if (nA > 32 * INV_SLOTS) return cudaErrorInvalidValue;
   const int threads = 128;
   const int grid = (Eim * 32 + threads - 1) / threads;
-  if (condense_uses_lu(prec_bytes, nA, nT_of_last))
+  if (condense_uses_lu(prec_bytes, nA, nT_of_last) && prec_bytes == 8)
     (hfr::count_launch(), k_lu_solve<double><<<grid, threads, 0, st>>>(Eim, nA, (const double*)LU, piv, b));
+  else if (condense_uses_lu(prec_bytes, nA, nT_of_last))
+    (hfr::count_launch(), k_lu_solve<float><<<grid, threads, 0, st>>>(Eim, nA, (const float*)LU, piv, b));
   else if (prec_bytes == 8)
     (hfr::count_launch(), k_inv_apply<double><<<grid, threads, 0, st>>>(Eim, nA, (const double*)LU, piv, b));
   else

@@ -5,12 +5,19 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "hfr_common.cuh"
 
 namespace hfr {
 
 // counts every kernel launch of the library (reported by fr_kernel_launches)
 void count_launch();
+
+// n-point Gauss-Legendre nodes and weights (Newton on P_n), and the 1D reference operators of
+// degree p (barycentric Lagrange derivatives, DG-recovering correction lift l_i(+-1)/w_i)
+void gauss_legendre_nodes(int n, double* x, double* w);
+void build_ref_ops(int p, RefOps& R);
 
 // Arguments of the element residual kernels.  All pointers are device pointers; nullable
 // ones are marked.  U: E x Ns x nv; uhat: ntrace x n x nv; Uf_all: E x 4n x nv;
@@ -99,6 +106,29 @@ cudaError_t launch_condense_part(int prec_bytes, const CondArgs& a, cudaStream_t
 cudaError_t launch_condense_uneven(int prec_bytes, int n, const int* nA, const int* nT, const void* A, const void* B,
                                    const void* C, const void* D, const double* r, const double* s, void* LU, int* piv,
                                    void* XB, double* xr, void* S, double* t, int* status, cudaStream_t st);
+
+// The same with the tables built once (host) and kept on the device, e.g. by a context whose
+// element shapes do not change: per element 5 offsets (A, B/C, D, nA-vector, nT-vector) and the
+// shape; the shared-memory elements in launch order with their bundles; the elements whose working
+// set exceeds shared memory, condensed by the global-memory kernel (FP64 LU factors in LU).
+struct UnevenTables {
+  std::vector<long long> off;
+  std::vector<int> shape, order, bundle, global;
+  size_t smem = 0;
+};
+struct UnevenDev {
+  const long long* off = nullptr;
+  const int *order = nullptr, *shape = nullptr, *bundle = nullptr, *global = nullptr;
+  int nb = 0, nglobal = 0;
+  size_t smem = 0;
+};
+int uneven_tables(int prec_bytes, int n, const int* nA, const int* nT, UnevenTables* tb);
+size_t uneven_dev_bytes(const UnevenTables& tb);
+cudaError_t uneven_upload(const UnevenTables& tb, void* dbuf, UnevenDev* dv, cudaStream_t st);
+cudaError_t launch_condense_uneven_dev(int prec_bytes, const UnevenDev& dv, const void* A, const void* B, const void* C,
+                                       const void* D, const double* r, const double* s, void* LU, int* piv, void* XB,
+                                       double* xr, void* S, double* t, int* status, cudaStream_t st);
+bool uneven_fits_smem(int prec_bytes, int nA, int nT);
 
 // x = A^{-1} b with the stored factorisation (LU + interchanges or in-place inverse, as chosen
 // by condense_uses_lu), in place on b (Eim x nA, FP64 vectors).

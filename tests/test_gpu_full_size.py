@@ -115,7 +115,7 @@ def test_full_size_sampled_blocks_and_condensation(precision):
     ctx.hfr_condense(refine=0)
     cond = {k: ctx.hfr_export(k)[sel].cpu().numpy().astype(np.float64) for k in ("S", "XB", "xr", "t_k")}
     full_view = d.trace_view(uh)
-    tol_blk, tol_cond = (1e-11, 1e-9) if precision == "fp64" else (3e-5, 1e-4)
+    tol_blk, tol_cond = (1e-11, 1e-11) if precision == "fp64" else (3e-5, 1e-4)
     phys = make_physics(w.physics)
     for k, e in enumerate(SAMPLES):
         mesh, ids = _patch(w, e)

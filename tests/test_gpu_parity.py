@@ -3,9 +3,10 @@ seeded inputs, plus full-size checks of the bench workload by properties the ora
 evaluate cheaply.
 
 Tolerances.  FP64 path: the same discretisation evaluated in a different order, so agreement
-is to rounding: 1e-11 relative to the magnitude of the compared array for residuals and
-blocks, 1e-9 for quantities that pass through a linear solve (condition numbers of the
-element blocks are O(1e2)), and 1e-10 relative to the stage increment for converged stages.
+is to rounding: 1e-11 relative to the magnitude of the compared array for residuals, blocks
+and the condensed blocks (condition numbers of the element blocks are O(1)-O(10)), 1e-10 for the
+trace solution of GMRES at rtol 1e-13 and its back-substitution, and 1e-10 relative to the stage
+increment for converged stages.
 FP32 blocks (mixed path): 3e-5 relative (FP32 rounding of O(n) accumulated terms); the
 converged mixed-precision stage must match the FP64 stage to 1e-8 relative to the increment
 (the FP64 Newton residual fixes the solution).
@@ -161,20 +162,23 @@ def test_condense_gmres_backsolve_fp64(name):
     r = ctx.hfr_export("r").cpu().numpy()
     s = ctx.hfr_export("s").cpu().numpy()
     XB, xr, S, t = condense(A, B, C, D, r, s)
-    assert _rel(ctx.hfr_export("S").cpu().numpy(), S) < 1e-9
-    assert _rel(ctx.hfr_export("XB").cpu().numpy(), XB) < 1e-9
-    assert _rel(ctx.hfr_export("xr").cpu().numpy(), xr) < 1e-9
-    assert _rel(ctx.hfr_export("t_k").cpu().numpy(), t) < 1e-9
+    # FP64 path: 1e-11 for the condensed blocks (condition numbers of A are O(1)-O(10) here;
+    # measured on GB300 1e-15), 1e-10 for the GMRES solution at rtol 1e-13 and its back-substitution
+    # (measured 5e-14)
+    assert _rel(ctx.hfr_export("S").cpu().numpy(), S) < 1e-11
+    assert _rel(ctx.hfr_export("XB").cpu().numpy(), XB) < 1e-11
+    assert _rel(ctx.hfr_export("xr").cpu().numpy(), xr) < 1e-11
+    assert _rel(ctx.hfr_export("t_k").cpu().numpy(), t) < 1e-11
     # face-block Jacobi preconditioner blocks
     from oracle.solve import face_block_jacobi
-    assert _rel(ctx.hfr_export("Pinv").cpu().numpy(), face_block_jacobi(d, S, d.imp_idx)) < 1e-9
+    assert _rel(ctx.hfr_export("Pinv").cpu().numpy(), face_block_jacobi(d, S, d.imp_idx)) < 1e-11
     duh_ref, _, _ = solve_trace(d, S, t, d.imp_idx, method="direct")
     duh, its, rel = ctx.hfr_trace_gmres(rtol=1e-13, maxit=3000)
     assert rel <= 1e-12
-    assert _rel(duh.cpu().numpy().reshape(-1), duh_ref) < 1e-9
+    assert _rel(duh.cpu().numpy().reshape(-1), duh_ref) < 1e-10
     du = ctx.hfr_backsolve(duh, refine=0).cpu().numpy()
     dview = d.trace_view(duh_ref.reshape(d.ntrace, d.n, d.nv))[d.imp_idx].reshape(len(d.imp_idx), -1)
-    assert _rel(du, backsolve(XB, xr, dview)) < 1e-9
+    assert _rel(du, backsolve(XB, xr, dview)) < 1e-10
 
 
 def test_fp64_refinement_sweep_is_consistent():

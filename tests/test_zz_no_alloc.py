@@ -113,13 +113,14 @@ def test_noalloc_status_words_do_not_leak_between_calls():
     ctx.close()
 
 
-def test_noalloc_rejects_shapes_without_a_kernel():
+def test_noalloc_rejects_shapes_outside_its_limits():
     import ctypes
 
     import paper_2401_16632_gb300 as pkg
 
     lib = pkg.load_library()
     z = ctypes.c_void_p(0x1000)
-    # one FP64 element of nA = nT = 150 fits the scratch (180 KB of factors) but no FP64
-    # condensation kernel holds its working set in shared memory: refused before any work
-    assert lib.hfr_condense_noalloc(1, 150, 150, pkg.FR_PREC_FP64, z, z, z, z, z, z, z, z, z, z, z) == 1
+    # one FP64 element of nA = 200 would fit the scratch (320 KB of factors) but exceeds nA <= 160;
+    # nT = 0 is no block: both refused before any pointer is used or any work is enqueued
+    assert lib.hfr_condense_noalloc(1, 200, 10, pkg.FR_PREC_FP64, z, z, z, z, z, z, z, z, z, z, z) == 1
+    assert lib.hfr_condense_noalloc(1, 64, 0, pkg.FR_PREC_FP64, z, z, z, z, z, z, z, z, z, z, z) == 1
