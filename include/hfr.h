@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define HFR_ABI_VERSION 1
+#define HFR_ABI_VERSION 2
 
 enum fr_status {
   FR_OK = 0,
@@ -70,15 +70,33 @@ enum fr_tableau { FR_TAB_BE = 0, FR_TAB_SDIRK2 = 1 };
 
 typedef struct fr_ctx fr_ctx;
 
-/* Mesh description (all HOST arrays, copied by fr_ctx_create). */
+/* Boundary tags of fr_mesh_desc.bc (where nbr < 0). */
+enum fr_boundary { FR_BC_WALL = 1, FR_BC_FARFIELD = 2 };
+/* Element types of fr_mesh_desc.elem_type. */
+enum fr_elem_type { FR_ELEM_QUAD = 0 };
+
+/* Mesh description (all HOST arrays, copied by fr_ctx_create).
+ * A mesh whose elements all share one degree and that has no boundary face runs the uniform
+ * path (fixed-shape kernels: tensor-core condensation, single-launch GMRES, stage graph).  A mesh
+ * with per-element degrees (p_elem not all equal) or with boundary faces runs the general path
+ * (packed layouts, see fr_ctx_layout): faces between unequal degrees carry the Gauss points of
+ * the higher one (the element blocks admit faces with different numbers of trace points, Sec. 3.2
+ * eq. elemsystemB), boundary faces carry the boundary rows of the transmission conditions
+ * (Sec. 2.2 eq. hfr2): a hybridized far field (trace = average of the element state and u_inf) and
+ * a no-slip adiabatic wall (Navier-Stokes; momentum rows set the trace velocity to zero, mass and
+ * energy rows are the element's own normal fluxes).  Explicit elements may meet the far field
+ * (Rusanov against u_inf), not a wall. */
 typedef struct {
   int nelem;
-  int p;                         /* polynomial degree, 1..5 */
+  int p;                         /* polynomial degree 1..5 (all elements, unless p_elem is given) */
   const double* verts;           /* nelem x 4 x 2 corner coordinates, corner k = a + 2b at (2a-1, 2b-1) */
-  const int* nbr;                /* nelem x 4 neighbour element across each local face (no boundary faces) */
+  const int* nbr;                /* nelem x 4 neighbour element across each local face, -1 on a boundary */
   const int* nbr_face;           /* nelem x 4 neighbour's local face */
-  const int* face_of;            /* nelem x 4 global face id (first-appearance numbering) */
+  const int* face_of;            /* nelem x 4 global face id (first-appearance numbering), < 4 nelem */
   const unsigned char* implicit; /* nelem: 1 = hybridized implicit, 0 = explicit FR */
+  const int* p_elem;             /* nullable: nelem degrees 1..5 (general path: advection-diffusion, Navier-Stokes) */
+  const int* bc;                 /* nullable: nelem x 4 fr_boundary tags where nbr < 0 (required when there are) */
+  int elem_type;                 /* fr_elem_type */
 } fr_mesh_desc;
 
 typedef struct {
@@ -93,12 +111,19 @@ typedef struct {
   int tableau;     /* fr_tableau: implicit DIRK + explicit partner of the IMEX pair */
   int gmres_restart; /* m <= 64 */
   double theta;    /* EDAC: 1 / M^2 of the artificial Mach number */
+  double u_inf[5]; /* free-stream state of far-field faces (conserved variables) */
 } fr_config;
 
+/* Sizes of a context.  Uniform path: as named.  General path: p, n, ns the largest degree and its
+ * point counts, nA / nT the largest element blocks; the state, R and R_hist hold state_values
+ * values per copy, uhat and g trace_values (layouts from fr_ctx_layout). */
 typedef struct {
   int nelem, nimplicit, p, n, ns, nv, nA, nT, ntrace, nstages;
   int has_explicit;       /* mesh has FR faces / interface faces */
   size_t workspace_bytes; /* device memory held by the context */
+  int general;            /* 1: general path (packed layouts) */
+  size_t state_values;    /* values of one state copy (nelem ns nv on the uniform path) */
+  size_t trace_values;    /* values of one trace vector (ntrace n nv on the uniform path) */
 } fr_ctx_info;
 
 typedef struct {
@@ -124,8 +149,20 @@ typedef struct {
 int fr_ctx_create(const fr_mesh_desc* mesh, const fr_config* cfg, void* stream, fr_ctx** out);
 void fr_ctx_destroy(fr_ctx* ctx);
 int fr_ctx_query(const fr_ctx* ctx, fr_ctx_info* info /* host */);
-/* Physical coordinates (nelem x Ns x 2, device) of the solution points. */
+/* Physical coordinates (nelem x Ns x 2, device; general path: element after element, Ns_e
+ * points each) of the solution points. */
 int fr_solution_points(fr_ctx* ctx, double* xy);
+
+/* Packed layouts of a context (host arrays; NULL skips one).  elem_off (nelem + 1): element e's
+ * state values start at elem_off[e] (uniform path: e ns nv); trace_off (ntrace + 1): trace t's
+ * values (points x nv, the points of face t in order) start at trace_off[t]; blk_nA, blk_nT
+ * (nimplicit): the block sizes of each implicit element.  General path, per implicit element k
+ * (increasing element id): the local trace unknowns are the four faces' points in local face
+ * order (point count m_f = max(p_e, p_neighbour) + 1, p_e + 1 on boundaries; rows and columns of
+ * faces without a trace are zero), l = (sum_{f' < f} m_f') nv + q nv + v; hfr_export packs the
+ * element arrays one after another in k (A: nA_k^2, B, C, X_B: nA_k nT_k, D, S: nT_k^2, r, x_r:
+ * nA_k, s, t_k: nT_k) and the face-block inverses per trace ((m_t nv)^2).  FR_OK. */
+int fr_ctx_layout(const fr_ctx* ctx, long long* elem_off, long long* trace_off, int* blk_nA, int* blk_nT);
 
 /* Spatial residual du/dt = R(u, u^) at every element (R: nelem x nA) and, if g != NULL, the
  * trace residual g (ntrace x n x nv) = sum over the two sides of w_q J_f F^.n (eq. hfr2).

@@ -30,6 +30,8 @@ FR_PREC_FP64, FR_PREC_FP32 = 0, 1
 FR_TAB_BE, FR_TAB_SDIRK2 = 0, 1
 FR_PHYS_ADVDIFF, FR_PHYS_NAVIER_STOKES, FR_PHYS_EDAC = 0, 1, 2
 FR_GMRES_MULTI, FR_GMRES_FUSED = 0, 1
+FR_BC_WALL, FR_BC_FARFIELD = 1, 2
+FR_ELEM_QUAD = 0
 FR_JAC_EVERY_NEWTON, FR_JAC_ONCE_PER_STAGE, FR_JAC_KEEP = 0, 1, 2
 FR_CONDENSE_FMA, FR_CONDENSE_TENSOR_PRODUCTS, FR_CONDENSE_TENSOR, FR_CONDENSE_TENSOR_TF32 = 0, 1, 2, 3
 (FR_OK, FR_ERR_INVALID_ARG, FR_ERR_CUDA, FR_ERR_SINGULAR, FR_ERR_NOT_CONVERGED, FR_ERR_DIVERGED, FR_ERR_TIMEOUT,
@@ -43,6 +45,7 @@ ABI_SYMBOLS = [
     "fr_ctx_create",
     "fr_ctx_destroy",
     "fr_ctx_query",
+    "fr_ctx_layout",
     "fr_solution_points",
     "fr_residual",
     "hfr_local_jacobian",
@@ -88,6 +91,9 @@ class fr_mesh_desc(ctypes.Structure):
         ("nbr_face", ctypes.POINTER(ctypes.c_int)),
         ("face_of", ctypes.POINTER(ctypes.c_int)),
         ("implicit", ctypes.POINTER(ctypes.c_ubyte)),
+        ("p_elem", ctypes.POINTER(ctypes.c_int)),
+        ("bc", ctypes.POINTER(ctypes.c_int)),
+        ("elem_type", ctypes.c_int),
     ]
 
 
@@ -104,6 +110,7 @@ class fr_config(ctypes.Structure):
         ("tableau", ctypes.c_int),
         ("gmres_restart", ctypes.c_int),
         ("theta", ctypes.c_double),
+        ("u_inf", ctypes.c_double * 5),
     ]
 
 
@@ -121,6 +128,9 @@ class fr_ctx_info(ctypes.Structure):
         ("nstages", ctypes.c_int),
         ("has_explicit", ctypes.c_int),
         ("workspace_bytes", ctypes.c_size_t),
+        ("general", ctypes.c_int),
+        ("state_values", ctypes.c_size_t),
+        ("trace_values", ctypes.c_size_t),
     ]
 
 
@@ -186,6 +196,7 @@ def load_library(path: str = LIB_PATH):
     lib.fr_ctx_destroy.argtypes = [vp]
     lib.fr_ctx_destroy.restype = None
     lib.fr_ctx_query.argtypes = [vp, ctypes.POINTER(fr_ctx_info)]
+    lib.fr_ctx_layout.argtypes = [vp, vp, vp, vp, vp]
     lib.fr_solution_points.argtypes = [vp, dp]
     lib.fr_residual.argtypes = [vp, dp, dp, dp, dp]
     lib.hfr_local_jacobian.argtypes = [vp, dp, dp, dp, ctypes.c_double]
@@ -377,8 +388,13 @@ class Context:
 
         self.torch = torch
         self.lib = load_library()
-        p = int(np.asarray(mesh.p).reshape(-1)[0])
+        degs = np.asarray(mesh.p).reshape(-1)
+        p = int(degs[0])
         E = int(mesh.verts.shape[0])
+        general = bool(np.any(degs != p)) or bool(np.any(np.asarray(mesh.nbr) < 0))
+        self._deg = np.ascontiguousarray(np.broadcast_to(degs, (E,)), dtype=np.int32)
+        bc = getattr(mesh, "bc", None)
+        self._bc = np.ascontiguousarray(bc if bc is not None else np.zeros((E, 4)), dtype=np.int32)
         self._verts = np.ascontiguousarray(mesh.verts, dtype=np.float64)
         self._nbr = np.ascontiguousarray(mesh.nbr, dtype=np.int32)
         self._nbf = np.ascontiguousarray(mesh.nbr_face, dtype=np.int32)
@@ -391,6 +407,9 @@ class Context:
             self._nbf.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
             self._fid.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
             self._imp.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)),
+            self._deg.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) if general else None,
+            self._bc.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) if general else None,
+            0,
         )
         cfg = fr_config()
         if physics["kind"] == "advdiff":
@@ -404,6 +423,10 @@ class Context:
             cfg.physics = FR_PHYS_NAVIER_STOKES
             cfg.gamma, cfg.mu, cfg.Pr = physics["gamma"], physics["mu"], physics["Pr"]
         cfg.lref = physics.get("lref", 1.0)
+        if physics.get("u_inf") is not None:
+            ui = np.asarray(physics["u_inf"], dtype=np.float64).reshape(-1)
+            for i, x in enumerate(ui[:5]):
+                cfg.u_inf[i] = float(x)
         cfg.precision = precision
         cfg.tableau = tableau
         cfg.gmres_restart = gmres_restart
@@ -419,6 +442,15 @@ class Context:
         self.info = info
         self.precision = precision
         self.dev = torch.device("cuda", torch.cuda.current_device())
+        self.general = bool(info.general)
+        if self.general:
+            eo = np.zeros(info.nelem + 1, dtype=np.int64)
+            to = np.zeros(info.ntrace + 1, dtype=np.int64)
+            na = np.zeros(max(info.nimplicit, 1), dtype=np.int32)
+            nt = np.zeros(max(info.nimplicit, 1), dtype=np.int32)
+            self._check(self.lib.fr_ctx_layout(self.h, eo.ctypes.data, to.ctypes.data, na.ctypes.data, nt.ctypes.data))
+            self.elem_off, self.trace_off = eo, to
+            self.blk_nA, self.blk_nT = na[:info.nimplicit], nt[:info.nimplicit]
 
     # ----------------------------------------------------------------------- plumbing
     def close(self):
@@ -443,15 +475,55 @@ class Context:
 
     @property
     def trace_shape(self):
+        if self.general:
+            return (int(self.info.trace_values),)
         return (self.info.ntrace, self.info.n, self.info.nv)
 
     @property
     def state_shape(self):
+        if self.general:
+            return (int(self.info.state_values),)
         return (self.info.nelem, self.info.ns, self.info.nv)
+
+    # ------------------------------------------------------- packed layouts (general path)
+    def pack_state(self, U):
+        """List of per-element (Ns_e, nv) arrays -> the packed state vector (numpy)."""
+        return np.concatenate([np.asarray(u, dtype=np.float64).reshape(-1) for u in U])
+
+    def unpack_state(self, x):
+        x = np.asarray(x).reshape(-1)
+        nv = self.info.nv
+        return [x[self.elem_off[e]:self.elem_off[e + 1]].reshape(-1, nv) for e in range(self.info.nelem)]
+
+    def pack_trace(self, H):
+        return np.concatenate([np.asarray(h, dtype=np.float64).reshape(-1) for h in H]) if len(H) else np.zeros(0)
+
+    def unpack_trace(self, x):
+        x = np.asarray(x).reshape(-1)
+        nv = self.info.nv
+        return [x[self.trace_off[t]:self.trace_off[t + 1]].reshape(-1, nv) for t in range(self.info.ntrace)]
+
+    def export_blocks(self, which: str):
+        """General path: an exported element array split into its implicit elements (numpy list)."""
+        flat = self.hfr_export(which).cpu().numpy()
+        na, nt = self.blk_nA.astype(np.int64), self.blk_nT.astype(np.int64)
+        shapes = {"A": (na, na), "B": (na, nt), "C": (nt, na), "D": (nt, nt), "S": (nt, nt), "XB": (na, nt),
+                  "xr": (na, None), "r": (na, None), "t_k": (nt, None), "s": (nt, None)}[which]
+        out, o = [], 0
+        for k in range(self.info.nimplicit):
+            r = int(shapes[0][k])
+            c = 1 if shapes[1] is None else int(shapes[1][k])
+            blk = flat[o:o + r * c]
+            out.append(blk if shapes[1] is None else blk.reshape(r, c))
+            o += r * c
+        return out
 
     # -------------------------------------------------------------------- ABI calls
     def solution_points(self):
-        xy = self.empty(self.info.nelem, self.info.ns, 2)
+        if self.general:
+            xy = self.empty(2 * int(self.info.state_values) // self.info.nv)
+        else:
+            xy = self.empty(self.info.nelem, self.info.ns, 2)
         self._check(self.lib.fr_solution_points(self.h, _ptr(xy)))
         return xy
 
@@ -519,12 +591,30 @@ class Context:
         return int(self.lib.hfr_condense_get_mode(self.h))
 
     def hfr_backsolve(self, duhat, refine=0):
-        du = self.empty(self.info.nimplicit, self.info.nA)
+        if self.general:
+            du = self.empty(int(np.sum(self.blk_nA)))
+        else:
+            du = self.empty(self.info.nimplicit, self.info.nA)
         self._check(self.lib.hfr_backsolve(self.h, _ptr(duhat), _ptr(du), int(refine)))
         return du
 
     def hfr_export(self, which: str):
         i = self.info
+        if self.general:
+            blk = self.torch.float64 if self.precision == FR_PREC_FP64 else self.torch.float32
+            na, nt = self.blk_nA.astype(np.int64), self.blk_nT.astype(np.int64)
+            sizes = {"A": (int(np.sum(na * na)), blk), "B": (int(np.sum(na * nt)), blk), "C": (int(np.sum(na * nt)), blk),
+                     "D": (int(np.sum(nt * nt)), blk), "S": (int(np.sum(nt * nt)), blk), "XB": (int(np.sum(na * nt)), blk),
+                     "xr": (int(np.sum(na)), self.torch.float64), "t_k": (int(np.sum(nt)), self.torch.float64),
+                     "r": (int(np.sum(na)), self.torch.float64), "s": (int(np.sum(nt)), self.torch.float64),
+                     "t": (int(i.trace_values), self.torch.float64)}
+            if which == "Pinv":
+                tp = np.diff(self.trace_off) // i.nv
+                sizes["Pinv"] = (int(np.sum((tp * i.nv) ** 2)), blk)
+            n, dt = sizes[which]
+            out = self.torch.empty(max(n, 1), dtype=dt, device=self.dev)
+            self._check(self.lib.hfr_export(self.h, EXPORT[which], _ptr(out), n * out.element_size()))
+            return out[:n]
         E, nA, nT = i.nimplicit, i.nA, i.nT
         blk = self.torch.float64 if self.precision == FR_PREC_FP64 else self.torch.float32
         shapes = {"A": (E, nA, nA, blk), "B": (E, nA, nT, blk), "C": (E, nT, nA, blk), "D": (E, nT, nT, blk),

@@ -17,6 +17,7 @@
 #include "../../include/hfr.h"
 #include "hfr_internal.h"
 #include "hfr_krylov.h"
+#include "hfr_general.h"
 
 using namespace hfr;
 
@@ -44,6 +45,7 @@ struct StageGraphKey {
 };
 
 struct fr_ctx {
+  hfr::gen::GenCtx* gen = nullptr;  // general meshes (per-element degree, boundary faces)
   int E = 0, p = 0, n = 0, ns = 0, nv = 0, nA = 0, nT = 0, ntrace = 0, Eim = 0;
   int prec_bytes = 8;
   int tableau = 0;
@@ -150,6 +152,18 @@ static int set_err(fr_ctx* c, int code, const char* msg, int elem = -1, int it =
   }
   return code;
 }
+// hooks of the general path into this context
+static int hook_prof_begin(void* c, int ph) { return prof_begin((fr_ctx*)c, ph); }
+static void hook_prof_end(void* c, int h) { prof_end((fr_ctx*)c, h); }
+static int hook_set_err(void* c, int code, const char* msg, int elem, int it, double val) {
+  return set_err((fr_ctx*)c, code, msg, elem, it, val);
+}
+// entry points that the general path does not build
+#define NOT_GENERAL(ctx, name)                                                                       \
+  do {                                                                                               \
+    if ((ctx) && (ctx)->gen) return set_err((ctx), FR_ERR_UNSUPPORTED, name ": not built for general meshes"); \
+  } while (0)
+
 #define CK(call)                                                                            \
   do {                                                                                      \
     cudaError_t e_ = (call);                                                                \
@@ -379,6 +393,34 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, const fr_config* cfg, voi
   *out = nullptr;
   if (mesh->nelem <= 0 || !mesh->verts || !mesh->nbr || !mesh->nbr_face || !mesh->face_of || !mesh->implicit)
     return FR_ERR_INVALID_ARG;
+  if (mesh->elem_type != FR_ELEM_QUAD) return FR_ERR_UNSUPPORTED;
+  if (hfr::gen::mesh_is_general(mesh)) {
+    fr_ctx* ctx = new fr_ctx();
+    memset(&ctx->err, 0, sizeof(ctx->err));
+    ctx->stream = (cudaStream_t)stream;
+    hfr::gen::Hooks hk;
+    hk.owner = ctx;
+    hk.prof_begin = hook_prof_begin;
+    hk.prof_end = hook_prof_end;
+    hk.set_err = hook_set_err;
+    const int rc = hfr::gen::create(mesh, cfg, ctx->stream, hk, &ctx->gen);
+    if (rc != FR_OK) {
+      delete ctx;
+      return rc;
+    }
+    fr_ctx_info gi;
+    hfr::gen::query(ctx->gen, &gi);
+    ctx->E = gi.nelem;
+    ctx->Eim = gi.nimplicit;
+    ctx->nv = gi.nv;
+    ctx->ntrace = gi.ntrace;
+    ctx->tableau = cfg->tableau;
+    *out = ctx;
+    return FR_OK;
+  }
+  fr_mesh_desc um = *mesh;  // uniform path: one degree (p_elem, when given, holds it)
+  if (mesh->p_elem) um.p = mesh->p_elem[0];
+  mesh = &um;
   if (mesh->p < 1 || mesh->p > 5) return FR_ERR_UNSUPPORTED;
   if (cfg->physics != FR_PHYS_ADVDIFF && cfg->physics != FR_PHYS_NAVIER_STOKES && cfg->physics != FR_PHYS_EDAC)
     return FR_ERR_INVALID_ARG;
@@ -599,6 +641,7 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, const fr_config* cfg, voi
 
 extern "C" void fr_ctx_destroy(fr_ctx* ctx) {
   if (!ctx) return;
+  if (ctx->gen) hfr::gen::destroy(ctx->gen);
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   if (ctx->graph) cudaGraphDestroy(ctx->graph);
   for (cudaStream_t c : ctx->cap)
@@ -610,6 +653,11 @@ extern "C" void fr_ctx_destroy(fr_ctx* ctx) {
 
 extern "C" int fr_ctx_query(const fr_ctx* ctx, fr_ctx_info* info) {
   if (!ctx || !info) return FR_ERR_INVALID_ARG;
+  if (ctx->gen) {
+    hfr::gen::query(ctx->gen, info);
+    info->workspace_bytes = ctx->bytes + info->workspace_bytes;
+    return FR_OK;
+  }
   info->nelem = ctx->E;
   info->nimplicit = ctx->Eim;
   info->p = ctx->p;
@@ -622,11 +670,29 @@ extern "C" int fr_ctx_query(const fr_ctx* ctx, fr_ctx_info* info) {
   info->nstages = ctx->tableau == FR_TAB_SDIRK2 ? 2 : 1;
   info->has_explicit = ctx->has_explicit ? 1 : 0;
   info->workspace_bytes = ctx->bytes;
+  info->general = 0;
+  info->state_values = (size_t)ctx->E * ctx->nA;
+  info->trace_values = (size_t)ctx->ntrace * ctx->n * ctx->nv;
+  return FR_OK;
+}
+
+extern "C" int fr_ctx_layout(const fr_ctx* ctx, long long* elem_off, long long* trace_off, int* blk_nA, int* blk_nT) {
+  if (!ctx) return FR_ERR_INVALID_ARG;
+  if (ctx->gen) return hfr::gen::layout(ctx->gen, elem_off, trace_off, blk_nA, blk_nT);
+  if (elem_off)
+    for (int e = 0; e <= ctx->E; ++e) elem_off[e] = (long long)e * ctx->nA;
+  if (trace_off)
+    for (int t = 0; t <= ctx->ntrace; ++t) trace_off[t] = (long long)t * ctx->n * ctx->nv;
+  for (int k = 0; k < ctx->Eim; ++k) {
+    if (blk_nA) blk_nA[k] = ctx->nA;
+    if (blk_nT) blk_nT[k] = ctx->nT;
+  }
   return FR_OK;
 }
 
 extern "C" int fr_solution_points(fr_ctx* ctx, double* xy) {
   if (!ctx || !xy) return FR_ERR_INVALID_ARG;
+  if (ctx->gen) return hfr::gen::solution_points(ctx->gen, xy);
   CK(cudaMemcpyAsync(xy, ctx->xy_host.data(), ctx->xy_host.size() * sizeof(double), cudaMemcpyHostToDevice,
                      ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -668,6 +734,11 @@ static int residual_into(fr_ctx* ctx, const double* u, const double* uhat, doubl
 extern "C" int fr_residual(fr_ctx* ctx, const double* u, const double* uhat, double* R, double* g) {
   if (!ctx || !u || !R) return set_err(ctx, FR_ERR_INVALID_ARG, "fr_residual: null argument");
   if (ctx->ntrace > 0 && !uhat) return set_err(ctx, FR_ERR_INVALID_ARG, "fr_residual: uhat required");
+  if (ctx->gen) {
+    const int grc = hfr::gen::residual(ctx->gen, u, uhat, R, g);
+    prof_collect(ctx);
+    return grc;
+  }
   int rc = residual_into(ctx, u, uhat, R, ctx->gview, g);
   if (rc) return rc;
   CK(cudaStreamSynchronize(ctx->stream));
@@ -677,6 +748,7 @@ extern "C" int fr_residual(fr_ctx* ctx, const double* u, const double* uhat, dou
 
 extern "C" int hfr_initial_trace(fr_ctx* ctx, const double* u, double* uhat) {
   if (!ctx || !u || (ctx->ntrace > 0 && !uhat)) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_initial_trace: null argument");
+  if (ctx->gen) return hfr::gen::initial_trace(ctx->gen, u, uhat);
   // face states of every element into a scratch buffer of the same shape (E x 4n x nv)
   ResArgs a = res_args(ctx, u, nullptr);
   a.Uf_out = ctx->gview;
@@ -734,6 +806,11 @@ static int form_rhs(fr_ctx* ctx, const double* u, const double* ustar, double a_
 extern "C" int hfr_local_jacobian(fr_ctx* ctx, const double* u, const double* uhat, const double* ustar,
                                   double a_dt) {
   if (!ctx || !u || (ctx->ntrace > 0 && !uhat)) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_local_jacobian: null argument");
+  if (ctx->gen) {
+    const int grc = hfr::gen::local_jacobian(ctx->gen, u, uhat, ustar, a_dt);
+    prof_collect(ctx);
+    return grc;
+  }
   ctx->keep_valid = 0;  // the blocks no longer belong to an imex_stage linearisation
   // keep a copy of the linearisation point for later refinement sweeps
   CK(cudaMemcpyAsync(ctx->lin_Ubuf, u, (size_t)ctx->E * ctx->nA * sizeof(double), cudaMemcpyDeviceToDevice,
@@ -871,6 +948,11 @@ static int condense_rhs_impl(fr_ctx* ctx) {
 
 extern "C" int hfr_condense(fr_ctx* ctx, int refine) {
   if (!ctx) return FR_ERR_INVALID_ARG;
+  if (ctx->gen) {
+    const int grc = hfr::gen::condense(ctx->gen, refine);
+    prof_collect(ctx);
+    return grc;
+  }
   ctx->keep_valid = 0;
   int rc = condense_impl(ctx, refine);
   if (rc) return rc;
@@ -966,6 +1048,8 @@ static int gmres_impl(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* i
 extern "C" int imex_set_jacobian_policy(fr_ctx* ctx, int policy) {
   if (!ctx || (policy != FR_JAC_EVERY_NEWTON && policy != FR_JAC_ONCE_PER_STAGE && policy != FR_JAC_KEEP))
     return set_err(ctx, FR_ERR_INVALID_ARG, "imex_set_jacobian_policy: bad argument");
+  if (ctx->gen && policy != FR_JAC_EVERY_NEWTON)
+    return set_err(ctx, FR_ERR_UNSUPPORTED, "imex_set_jacobian_policy: general meshes re-linearise at every Newton iterate");
   ctx->jac_policy = policy;
   return FR_OK;
 }
@@ -977,6 +1061,8 @@ extern "C" int imex_refresh_jacobian(fr_ctx* ctx) {
 }
 
 extern "C" int hfr_gmres_set_mode(fr_ctx* ctx, int mode) {
+  if (ctx && ctx->gen && mode == FR_GMRES_MULTI) return FR_OK;
+  NOT_GENERAL(ctx, "hfr_gmres_set_mode (single-launch cycle)");
   if (!ctx || (mode != FR_GMRES_MULTI && mode != FR_GMRES_FUSED))
     return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_gmres_set_mode: bad argument");
   if (mode == FR_GMRES_FUSED && ctx->gm_fused_grid <= 0)
@@ -988,6 +1074,7 @@ extern "C" int hfr_gmres_set_mode(fr_ctx* ctx, int mode) {
 extern "C" int hfr_gmres_get_mode(const fr_ctx* ctx) { return ctx ? ctx->gm_mode : -1; }
 
 extern "C" int hfr_condense_set_mode(fr_ctx* ctx, int mode) {
+  NOT_GENERAL(ctx, "hfr_condense_set_mode");
   if (!ctx || mode < FR_CONDENSE_FMA || mode > FR_CONDENSE_TENSOR_TF32)
     return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_condense_set_mode: bad argument");
   if ((mode == FR_CONDENSE_TENSOR_TF32 ? FR_CONDENSE_TENSOR : mode) >
@@ -1000,7 +1087,14 @@ extern "C" int hfr_condense_set_mode(fr_ctx* ctx, int mode) {
 extern "C" int hfr_condense_get_mode(const fr_ctx* ctx) { return ctx ? ctx->cond_mode : -1; }
 
 // Autotuner: time the compiled alternatives on the context's own blocks and keep the fastest.
+static int autotune_uniform(fr_ctx* ctx, const double* u, const double* uhat, const double* ustar, double a_dt,
+                            fr_tune_report* out);
 extern "C" int hfr_autotune(fr_ctx* ctx, const double* u, const double* uhat, const double* ustar, double a_dt,
+                            fr_tune_report* out) {
+  NOT_GENERAL(ctx, "hfr_autotune");
+  return autotune_uniform(ctx, u, uhat, ustar, a_dt, out);
+}
+static int autotune_uniform(fr_ctx* ctx, const double* u, const double* uhat, const double* ustar, double a_dt,
                             fr_tune_report* out) {
   if (!ctx || !u || (ctx->ntrace > 0 && !uhat) || !ustar) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_autotune: null argument");
   fr_tune_report rep;
@@ -1168,6 +1262,7 @@ static void modal_filter_operator(int p, double alpha, double s, int eta_c, doub
 }
 
 extern "C" int fr_modal_filter(fr_ctx* ctx, double* u, double alpha, double s, int eta_c, double dt_ratio, int which) {
+  NOT_GENERAL(ctx, "fr_modal_filter");
   if (!ctx || !u || !(alpha >= 0.0) || !(s > 0.0) || eta_c < 0 || !(dt_ratio > 0.0) || which < 0 || which > 2)
     return set_err(ctx, FR_ERR_INVALID_ARG, "fr_modal_filter: bad argument");
   const int ns = ctx->ns;
@@ -1233,6 +1328,12 @@ extern "C" int fr_barrier_selftest(int nblocks, int absent_block, int rounds, do
 }
 
 extern "C" int hfr_trace_gmres(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* iters, double* final_rel) {
+  if (ctx && ctx->gen) {
+    if (!duhat) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_trace_gmres: null argument");
+    const int grc = hfr::gen::trace_gmres(ctx->gen, duhat, rtol, maxit, iters, final_rel);
+    prof_collect(ctx);
+    return grc;
+  }
   if (!ctx || !duhat || rtol < 0 || maxit < 1) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_trace_gmres: bad argument");
   const int rc = gmres_impl(ctx, duhat, rtol, maxit, iters, final_rel);
   prof_collect(ctx);
@@ -1251,6 +1352,12 @@ static int backsolve_impl(fr_ctx* ctx, const double* duhat, double* du, int refi
 }
 
 extern "C" int hfr_backsolve(fr_ctx* ctx, const double* duhat, double* du, int refine) {
+  if (ctx && ctx->gen) {
+    if (!du || (ctx->ntrace > 0 && !duhat)) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_backsolve: null argument");
+    const int grc = hfr::gen::backsolve(ctx->gen, duhat, du, refine);
+    prof_collect(ctx);
+    return grc;
+  }
   if (!ctx || !du || (ctx->ntrace > 0 && !duhat)) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_backsolve: null argument");
   int rc = backsolve_impl(ctx, duhat, du, refine);
   if (rc) return rc;
@@ -1282,6 +1389,10 @@ static void* ctx_array(fr_ctx* ctx, int which, size_t* need) {
 
 extern "C" int hfr_import(fr_ctx* ctx, int which, const void* src, size_t bytes) {
   if (!ctx || !src) return FR_ERR_INVALID_ARG;
+  if (ctx->gen) {
+    if (which < 0 || which > 9) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_import: array not importable");
+    return hfr::gen::export_array(ctx->gen, which, const_cast<void*>(src), bytes, true);
+  }
   if (which < 0 || which > 9) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_import: array not importable");
   size_t need = 0;
   void* dst = ctx_array(ctx, which, &need);
@@ -1295,6 +1406,7 @@ extern "C" int hfr_import(fr_ctx* ctx, int which, const void* src, size_t bytes)
 
 extern "C" int hfr_export(fr_ctx* ctx, int which, void* dst, size_t bytes) {
   if (!ctx || !dst) return FR_ERR_INVALID_ARG;
+  if (ctx->gen) return hfr::gen::export_array(ctx->gen, which, dst, bytes, false);
   size_t need = 0;
   const void* src = ctx_array(ctx, which, &need);
   if (!src) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_export: unknown array");
@@ -1646,6 +1758,7 @@ static int imex_stage_graph(fr_ctx* ctx, const StageGraphKey& key, fr_stage_stat
 }
 
 extern "C" int imex_stage_set_graph(fr_ctx* ctx, int on) {
+  if (ctx && ctx->gen && on) return set_err(ctx, FR_ERR_UNSUPPORTED, "imex_stage_set_graph: not built for general meshes");
   if (!ctx || (on != 0 && on != 1)) return set_err(ctx, FR_ERR_INVALID_ARG, "imex_stage_set_graph: bad argument");
   if (on && (ctx->Eim == 0 || (ctx->ntrace > 0 && ctx->gm_mode != 1)))
     return set_err(ctx, FR_ERR_UNSUPPORTED, "imex_stage_set_graph: needs implicit elements and the single-launch GMRES cycle");
@@ -1661,6 +1774,12 @@ extern "C" int imex_stage(fr_ctx* ctx, int stage, double dt, const double* u_n, 
                           int refine, fr_stage_stats* stats) {
   if (!ctx || !u_n || !u_stage || !R_hist || (ctx->ntrace > 0 && !uhat))
     return set_err(ctx, FR_ERR_INVALID_ARG, "imex_stage: null argument");
+  if (ctx->gen) {
+    const int grc = hfr::gen::stage(ctx->gen, stage, dt, u_n, u_stage, uhat, R_hist, newton_tol, newton_maxit,
+                                    gmres_rtol, gmres_maxit, refine, stats);
+    prof_collect(ctx);
+    return grc;
+  }
   const Tab tb = tableau(ctx->tableau);
   if (stage < 0 || stage > tb.s + 1) return set_err(ctx, FR_ERR_INVALID_ARG, "imex_stage: stage out of range");
   const int E = ctx->E, nA = ctx->nA;
@@ -1800,6 +1919,8 @@ extern "C" int imex_steps(fr_ctx* ctx, int nsteps, double dt, double* u, double*
   if (!ctx || !u || !R_hist || !u_stage || (ctx->ntrace > 0 && !uhat) || nsteps < 0 || !(dt > 0.0))
     return set_err(ctx, FR_ERR_INVALID_ARG, "imex_steps: bad argument");
   const Tab tb = tableau(ctx->tableau);
+  if (ctx->gen && ctx->jac_policy != FR_JAC_EVERY_NEWTON)
+    return set_err(ctx, FR_ERR_UNSUPPORTED, "imex_steps: general meshes re-linearise at every Newton iterate");
   fr_steps_stats acc;
   memset(&acc, 0, sizeof(acc));
   acc.converged = 1;
@@ -1823,8 +1944,8 @@ extern "C" int imex_steps(fr_ctx* ctx, int nsteps, double dt, double* u, double*
       rc = imex_stage(ctx, tb.s + 1, dt, u, u_stage, uhat, R_hist, newton_tol, newton_maxit, gmres_rtol,
                       gmres_maxit, refine, nullptr);
     if (rc == FR_OK) {
-      if (cudaMemcpyAsync(u, u_stage, (size_t)ctx->E * ctx->nA * sizeof(double), cudaMemcpyDeviceToDevice,
-                          ctx->stream) != cudaSuccess)
+      const size_t nst = ctx->gen ? hfr::gen::state_values(ctx->gen) : (size_t)ctx->E * ctx->nA;
+      if (cudaMemcpyAsync(u, u_stage, nst * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
         rc = set_err(ctx, FR_ERR_CUDA, "imex_steps: copy of u_{n+1}");
       else
         ++acc.steps;

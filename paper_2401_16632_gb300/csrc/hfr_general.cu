@@ -1,0 +1,2105 @@
+// The hybridized stage on general quadrilateral meshes: per-element polynomial degree p_e (faces
+// between unequal degrees) and wall / far-field boundary faces (Pereira & Vermeire,
+// arXiv 2401.16632: element blocks that admit faces with different numbers of trace points,
+// Sec. 3.2 eq. elemsystemB; the boundary term of the transmission conditions, Sec. 2.2 eq. hfr2).
+//
+// Readings (the paper writes no operator for either):
+//   * a face carries the Gauss points of the higher degree of its two sides, m = max(n-, n+)
+//     (a boundary face its element's own n); both sides evaluate their states, fluxes and
+//     gradients there, and the common fluxes, the trace unknowns and the trace residual
+//     g_q = w_q J_f (F^.n)_q live there;
+//   * an element lifts a face jump h from the m face points onto its own n face nodes by the L2
+//     projection with the face rule, (P h)_b = sum_q w_q l_b(s_q) h_q / w_b (the identity when
+//     m = n; P T = I for the interpolation T from nodes to points), then spreads it along the
+//     normal with its DG-recovering correction derivatives;
+//   * boundary faces of implicit elements carry a trace: far field g = w J s(u^)((u_f - u^) +
+//     (u_inf - u^)); no-slip adiabatic wall (Navier-Stokes): momentum rows w J s(u^) (rho v)^, mass
+//     and energy rows the element's own normal fluxes; explicit elements meet the far field with
+//     the FR Rusanov flux against a ghost holding u_inf (BR1 common value the average, viscous flux
+//     the average of both sides' with the element's own gradient).
+//
+// Layouts (packed; element e of degree p_e, n_e = p_e + 1, Ns_e = n_e^2):
+//   state u, R       element after element, u[uoff[e] + pt nv + v]
+//   trace u^, g      trace after trace (traces in increasing global face id), u^[toff[t] + q nv + v]
+//   face data        fixed stride of GN points per element face: [(4 e + f) GN + q][nv]
+//   blocks of the    implicit element k: A nA_k^2, B nA_k nT_k, C nT_k nA_k, D and S nT_k^2, packed in
+//   implicit ones    increasing k; nT_k = nv sum_f m(e, f) over all four faces in local order (rows
+//                    and columns of faces without a trace are zero), trace unknown
+//                    l = lto[f] + q nv + v
+// Kernels: one warp per element for the residual passes, one CTA of 256 threads per implicit
+// element for the blocks (dense tangents of the element operator, one warp per seed point), the
+// uneven-shape condensation (shared-memory Gauss-Jordan, or the global-memory LU for blocks too
+// large for shared memory), and warp-per-element / warp-per-face trace operators under the
+// multi-kernel GMRES driver.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "hfr_general.h"
+
+namespace hfr {
+namespace gen {
+
+constexpr int GN = HFR_MAXN;  // points per line / face (p <= 5)
+constexpr int GNS = GN * GN;
+constexpr int GF = 4 * GN;
+constexpr int GEPB = 4;       // elements (warps) per CTA of the residual passes
+constexpr int JT = 256;       // threads of the block kernel
+constexpr int JW = JT / 32;
+enum { FK_WALL = 3, FK_FAR = 4 };
+enum { BC_WALL = 1, BC_FAR = 2 };
+
+// Reference operators of every degree, and the face interpolation / projection of every pair
+// (n nodes, m >= n face points).  Built on the host, read from global memory.
+struct GenRef {
+  double M[GN + 1][GN][GN];
+  double lm[GN + 1][GN], lp[GN + 1][GN], dgL[GN + 1][GN], dgR[GN + 1][GN], w[GN + 1][GN];
+  double T[GN + 1][GN + 1][GN][GN];  // [n][m][q][b] = l_b(s_q): node b of n -> face point q of m
+  double P[GN + 1][GN + 1][GN][GN];  // [n][m][b][q] = w_q l_b(s_q) / w_b: face points -> nodes
+};
+
+static void build_genref(GenRef& R) {
+  memset(&R, 0, sizeof(R));
+  for (int n = 2; n <= GN; ++n) {
+    RefOps o;
+    build_ref_ops(n - 1, o);
+    for (int i = 0; i < n; ++i) {
+      for (int j = 0; j < n; ++j) R.M[n][i][j] = o.M[i][j];
+      R.lm[n][i] = o.lm[i];
+      R.lp[n][i] = o.lp[i];
+      R.dgL[n][i] = o.dgL[i];
+      R.dgR[n][i] = o.dgR[i];
+      R.w[n][i] = o.w[i];
+    }
+  }
+  for (int n = 2; n <= GN; ++n) {
+    double x[GN], wn[GN], bw[GN];
+    gauss_legendre_nodes(n, x, wn);
+    for (int j = 0; j < n; ++j) {
+      double prod = 1.0;
+      for (int k = 0; k < n; ++k)
+        if (k != j) prod *= (x[j] - x[k]);
+      bw[j] = 1.0 / prod;
+    }
+    for (int m = n; m <= GN; ++m) {
+      double s[GN], ws[GN];
+      gauss_legendre_nodes(m, s, ws);
+      for (int q = 0; q < m; ++q) {
+        // barycentric interpolation at s_q (exact node hits give the unit vector)
+        int hit = -1;
+        for (int b = 0; b < n; ++b)
+          if (s[q] == x[b]) hit = b;
+        double den = 0.0;
+        if (hit < 0)
+          for (int b = 0; b < n; ++b) den += bw[b] / (s[q] - x[b]);
+        for (int b = 0; b < n; ++b) {
+          const double l = hit >= 0 ? (b == hit ? 1.0 : 0.0) : (bw[b] / (s[q] - x[b])) / den;
+          R.T[n][m][q][b] = l;
+          R.P[n][m][b][q] = ws[q] * l / wn[b];
+        }
+      }
+    }
+  }
+}
+
+struct GArgs {
+  int E;
+  const int* deg;         // E: points per line n_e
+  const long long* uoff;  // E: state offset
+  const long long* goff;  // E: first solution point of the element in geo_sol
+  const double* geo_sol;  // [point][5] = {1/J, S00, S01, S10, S11}
+  const double* geo_face; // [(4 e + f) GN + q][3] = {J_f, n0, n1}
+  const int *nbr, *nbr_face, *kind, *tr_of, *nfp;  // 4 E
+  const long long* toff;  // trace value offsets
+  const unsigned char* implicit;
+  const GenRef* ref;
+  const double* U;
+  const double* uhat;
+  const double* Uf_all;   // face-point states of every element (FR / IMEX neighbours)
+  const double* qf_all;   // face-point gradients
+  double* Uf_out;
+  double* qf_out;
+  double* R;
+  double* gview;          // element trace rows w_q J_f (row)_q at face points, zero off traces
+  double uinf[5];
+};
+
+__device__ __forceinline__ int gline(int r, int m, int c, int n) { return r == 0 ? (c + n * m) : (m + n * c); }
+
+// Common normal flux of one face point, scaled by J_f (Fn: the element's own residual sees it) and
+// the element's trace row (row: trace faces only).  ub: the trace (traced faces) or the common
+// value; un, qn: the other side's state and gradient (FR / IMEX / explicit far field).
+template <int PHYS, typename S, typename R, int NV>
+__device__ __forceinline__ void gface_flux(const PhysConst<R>& pc, bool visc, int kf, bool traced, bool imp,
+                                           const S* uf, const S* ub, const S (&qf)[2][NV], const S* un,
+                                           const S (&qn)[2][NV], R Jf, R n0, R n1, const R* uinf, S* Fn, S* row) {
+  S F[2][NV];
+  if (traced) {
+    S Fh[NV];
+    Phys<PHYS>::template conv<S, R>(pc, ub, F);
+    const S s = Phys<PHYS>::template stab<S, R>(pc, ub, n0, n1);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Fh[v] = n0 * F[0][v] + n1 * F[1][v] + s * (uf[v] - ub[v]);
+    if (visc) {
+      Phys<PHYS>::template visc<S, R>(pc, ub, qf, F);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Fh[v] = Fh[v] - (n0 * F[0][v] + n1 * F[1][v]);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Fn[v] = Jf * Fh[v];
+    if (kf == FK_FAR) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) row[v] = Jf * s * ((uf[v] - ub[v]) + (uinf[v] - ub[v]));
+    } else if (kf == FK_WALL) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) row[v] = (v == 0 || v == NV - 1) ? Jf * Fh[v] : Jf * s * ub[v];
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) row[v] = Jf * Fh[v];
+    }
+    return;
+  }
+  S G[2][NV];
+  Phys<PHYS>::template conv<S, R>(pc, uf, F);
+  Phys<PHYS>::template conv<S, R>(pc, un, G);
+  const S lam = dmax(Phys<PHYS>::template wave<S, R>(pc, uf, n0, n1), Phys<PHYS>::template wave<S, R>(pc, un, n0, n1));
+  S Fh[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+    Fh[v] = R(0.5) * (n0 * (F[0][v] + G[0][v]) + n1 * (F[1][v] + G[1][v])) + R(0.5) * lam * (uf[v] - un[v]);
+  if (visc) {
+    if (kf == FK_FR || kf == FK_FAR) {  // both sides' viscous fluxes averaged
+      Phys<PHYS>::template visc<S, R>(pc, uf, qf, F);
+      Phys<PHYS>::template visc<S, R>(pc, un, qn, G);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Fh[v] = Fh[v] - R(0.5) * (n0 * (F[0][v] + G[0][v]) + n1 * (F[1][v] + G[1][v]));
+    } else {  // IMEX interface: the implicit side's viscous flux
+      if (imp)
+        Phys<PHYS>::template visc<S, R>(pc, uf, qf, F);
+      else
+        Phys<PHYS>::template visc<S, R>(pc, un, qn, F);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Fh[v] = Fh[v] - (n0 * F[0][v] + n1 * F[1][v]);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    Fn[v] = Jf * Fh[v];
+    row[v] = S(R(0));
+  }
+}
+
+// ------------------------------------------------------------------------ residual passes
+enum { GM_UF = 0, GM_QF = 1, GM_RES = 2 };
+
+template <int NV>
+struct GWork {
+  double U[GNS][NV];
+  double Ufn[GF][NV], Ufp[GF][NV], ubp[GF][NV], ubn[GF][NV];
+  double q[GNS][2][NV];
+  double qfn[GF][2][NV], qfp[GF][2][NV];
+  double Ft[GNS][2][NV];
+  double Fnp[GF][NV], Fnn[GF][NV];
+  double M[GN][GN], lm[GN], lp[GN], dgL[GN], dgR[GN];
+  double Tf[4][GN][GN], Pf[4][GN][GN], wq[4][GN];
+  int nf[4], kf[4], tr[4];
+};
+
+template <int PHYS, int MODE>
+__global__ void __launch_bounds__(32 * GEPB) k_gen_elem(const __grid_constant__ PhysParams pp,
+                                                       const __grid_constant__ GArgs a) {
+  constexpr int NV = Phys<PHYS>::NV;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  GWork<NV>& w = reinterpret_cast<GWork<NV>*>(smem_raw)[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const int e = blockIdx.x * GEPB + (threadIdx.x >> 5);
+  if (e >= a.E) return;  // whole warps leave; only warp-level synchronisation below
+  const int n = a.deg[e], ns = n * n;
+  const GenRef& RF = *a.ref;
+  const bool visc = phys_viscous(pp);
+  const PhysConst<double> pc = phys_const<double>(pp);
+  const bool imp = a.implicit[e] != 0;
+  for (int i = lane; i < n * n; i += 32) w.M[i / n][i % n] = RF.M[n][i / n][i % n];
+  if (lane < n) {
+    w.lm[lane] = RF.lm[n][lane];
+    w.lp[lane] = RF.lp[n][lane];
+    w.dgL[lane] = RF.dgL[n][lane];
+    w.dgR[lane] = RF.dgR[n][lane];
+  }
+  if (lane < 4) {
+    w.nf[lane] = a.nfp[4 * e + lane];
+    w.kf[lane] = a.kind[4 * e + lane];
+    w.tr[lane] = a.tr_of[4 * e + lane];
+  }
+  __syncwarp();
+  for (int i = lane; i < 4 * GN * GN; i += 32) {
+    const int f = i / (GN * GN), x = (i / GN) % GN, y = i % GN, m = w.nf[f];
+    w.Tf[f][x][y] = (x < m && y < n) ? RF.T[n][m][x][y] : 0.0;  // [q][b]
+    w.Pf[f][x][y] = (x < n && y < m) ? RF.P[n][m][x][y] : 0.0;  // [b][q]
+  }
+  if (lane < GF) w.wq[lane / GN][lane % GN] = (lane % GN) < w.nf[lane / GN] ? RF.w[w.nf[lane / GN]][lane % GN] : 0.0;
+  const double* Ue = a.U + a.uoff[e];
+  for (int i = lane; i < ns * NV; i += 32) w.U[i / NV][i % NV] = Ue[i];
+  __syncwarp();
+  // face node values (own degree), then the face points
+  for (int it = lane; it < 4 * n * NV; it += 32) {
+    const int f = it / (n * NV), b = (it / NV) % n, v = it % NV, r = f >> 1;
+    const double* l = (f & 1) ? w.lp : w.lm;
+    double s = 0.0;
+    for (int c = 0; c < n; ++c) s += l[c] * w.U[gline(r, b, c, n)][v];
+    w.Ufn[f * GN + b][v] = s;
+  }
+  __syncwarp();
+  for (int it = lane; it < GF * NV; it += 32) {
+    const int f = it / (GN * NV), q = (it / NV) % GN, v = it % NV;
+    if (q >= w.nf[f]) continue;
+    double s = 0.0;
+    for (int b = 0; b < n; ++b) s += w.Tf[f][q][b] * w.Ufn[f * GN + b][v];
+    w.Ufp[f * GN + q][v] = s;
+    if (MODE == GM_UF) a.Uf_out[((size_t)(4 * e + f) * GN + q) * NV + v] = s;
+  }
+  if (MODE == GM_UF) return;
+  __syncwarp();
+  // trace or common value at the face points
+  for (int it = lane; it < GF * NV; it += 32) {
+    const int f = it / (GN * NV), q = (it / NV) % GN, v = it % NV;
+    if (q >= w.nf[f]) continue;
+    const int kf = w.kf[f], t = w.tr[f];
+    const double uf = w.Ufp[f * GN + q][v];
+    double ub;
+    if (t >= 0) {
+      ub = a.uhat[a.toff[t] + q * NV + v];
+    } else if (kf == FK_FAR) {
+      ub = 0.5 * (uf + a.uinf[v]);
+    } else {
+      const int nb = a.nbr[4 * e + f], fn = a.nbr_face[4 * e + f];
+      const double un = a.Uf_all[((size_t)(4 * nb + fn) * GN + q) * NV + v];
+      ub = kf == FK_FR ? 0.5 * (uf + un) : (imp ? un : uf);
+    }
+    w.ubp[f * GN + q][v] = ub;
+  }
+  __syncwarp();
+  // common value at the own face nodes: u_f + P (u_bar - u_f(points))
+  for (int it = lane; it < 4 * n * NV; it += 32) {
+    const int f = it / (n * NV), b = (it / NV) % n, v = it % NV;
+    double s = w.Ufn[f * GN + b][v];
+    for (int q = 0; q < w.nf[f]; ++q) s += w.Pf[f][b][q] * (w.ubp[f * GN + q][v] - w.Ufp[f * GN + q][v]);
+    w.ubn[f * GN + b][v] = s;
+  }
+  __syncwarp();
+  const double* gs = a.geo_sol + (size_t)a.goff[e] * 5;
+  if (visc) {
+    for (int it = lane; it < ns * NV; it += 32) {
+      const int i = it / NV, v = it % NV, ai = i % n, bi = i / n;
+      const double* G = gs + i * 5;
+      double q0 = w.dgL[ai] * w.ubn[0 * GN + bi][v] + w.dgR[ai] * w.ubn[1 * GN + bi][v];
+      double q1 = w.dgL[bi] * w.ubn[2 * GN + ai][v] + w.dgR[bi] * w.ubn[3 * GN + ai][v];
+      for (int c = 0; c < n; ++c) {
+        q0 += w.M[ai][c] * w.U[c + n * bi][v];
+        q1 += w.M[bi][c] * w.U[ai + n * c][v];
+      }
+      w.q[i][0][v] = G[0] * (G[1] * q0 + G[3] * q1);
+      w.q[i][1][v] = G[0] * (G[2] * q0 + G[4] * q1);
+    }
+    __syncwarp();
+    for (int it = lane; it < 4 * n * 2 * NV; it += 32) {
+      const int f = it / (n * 2 * NV), b = (it / (2 * NV)) % n, c2 = (it / NV) % 2, v = it % NV, r = f >> 1;
+      const double* l = (f & 1) ? w.lp : w.lm;
+      double s = 0.0;
+      for (int c = 0; c < n; ++c) s += l[c] * w.q[gline(r, b, c, n)][c2][v];
+      w.qfn[f * GN + b][c2][v] = s;
+    }
+    __syncwarp();
+    for (int it = lane; it < GF * 2 * NV; it += 32) {
+      const int f = it / (GN * 2 * NV), q = (it / (2 * NV)) % GN, c2 = (it / NV) % 2, v = it % NV;
+      if (q >= w.nf[f]) continue;
+      double s = 0.0;
+      for (int b = 0; b < n; ++b) s += w.Tf[f][q][b] * w.qfn[f * GN + b][c2][v];
+      w.qfp[f * GN + q][c2][v] = s;
+      if (MODE == GM_QF) a.qf_out[(((size_t)(4 * e + f) * GN + q) * 2 + c2) * NV + v] = s;
+    }
+  } else if (MODE == GM_QF) {
+    for (int it = lane; it < GF * 2 * NV; it += 32) a.qf_out[(size_t)(4 * e) * GN * 2 * NV + it] = 0.0;
+  }
+  if (MODE == GM_QF) return;
+  __syncwarp();
+  // transformed flux at the solution points
+  for (int i = lane; i < ns; i += 32) {
+    const double* G = gs + i * 5;
+    double F[2][NV];
+    Phys<PHYS>::template conv<double, double>(pc, w.U[i], F);
+    if (visc) {
+      double Fv[2][NV];
+      Phys<PHYS>::template visc<double, double>(pc, w.U[i], w.q[i], Fv);
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) F[c][v] -= Fv[c][v];
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      w.Ft[i][0][v] = G[1] * F[0][v] + G[2] * F[1][v];
+      w.Ft[i][1][v] = G[3] * F[0][v] + G[4] * F[1][v];
+    }
+  }
+  // common normal flux at the face points
+  for (int j = lane; j < GF; j += 32) {
+    const int f = j / GN, q = j % GN;
+    if (q >= w.nf[f]) continue;
+    const int kf = w.kf[f];
+    const bool traced = w.tr[f] >= 0;
+    const double* G = a.geo_face + ((size_t)(4 * e + f) * GN + q) * 3;
+    double un[NV], qn[2][NV], Fn[NV], row[NV];
+    if (!traced) {
+      if (kf == FK_FAR) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          un[v] = a.uinf[v];
+          qn[0][v] = w.qfp[j][0][v];
+          qn[1][v] = w.qfp[j][1][v];
+        }
+      } else {
+        const int nb = a.nbr[4 * e + f], fn = a.nbr_face[4 * e + f];
+        const size_t nix = (size_t)(4 * nb + fn) * GN + q;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          un[v] = a.Uf_all[nix * NV + v];
+          qn[0][v] = a.qf_all[(nix * 2 + 0) * NV + v];
+          qn[1][v] = a.qf_all[(nix * 2 + 1) * NV + v];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) un[v] = qn[0][v] = qn[1][v] = 0.0;
+    }
+    if (!visc) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) w.qfp[j][0][v] = w.qfp[j][1][v] = 0.0;
+    }
+    gface_flux<PHYS, double, double, NV>(pc, visc, kf, traced, imp, w.Ufp[j], w.ubp[j], w.qfp[j], un, qn, G[0], G[1],
+                                         G[2], a.uinf, Fn, row);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) w.Fnp[j][v] = Fn[v];
+    if (a.gview) {
+      const double wq = traced ? w.wq[f][q] : 0.0;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) a.gview[((size_t)(4 * e + f) * GN + q) * NV + v] = wq * row[v];
+    }
+  }
+  __syncwarp();
+  for (int it = lane; it < 4 * n * NV; it += 32) {
+    const int f = it / (n * NV), b = (it / NV) % n, v = it % NV;
+    double s = 0.0;
+    for (int q = 0; q < w.nf[f]; ++q) s += w.Pf[f][b][q] * w.Fnp[f * GN + q][v];
+    w.Fnn[f * GN + b][v] = s;
+  }
+  __syncwarp();
+  for (int it = lane; it < ns * NV; it += 32) {
+    const int i = it / NV, v = it % NV, ai = i % n, bi = i / n;
+    double d = -w.dgL[ai] * w.Fnn[0 * GN + bi][v] + w.dgR[ai] * w.Fnn[1 * GN + bi][v] -
+               w.dgL[bi] * w.Fnn[2 * GN + ai][v] + w.dgR[bi] * w.Fnn[3 * GN + ai][v];
+    for (int c = 0; c < n; ++c) d += w.M[ai][c] * w.Ft[c + n * bi][0][v] + w.M[bi][c] * w.Ft[ai + n * c][1][v];
+    if (a.R) a.R[a.uoff[e] + it] = -gs[i * 5] * d;
+  }
+}
+
+// trace residual: g[t] = both sides' rows
+__global__ void k_gen_trace_sum(int ntrace, int nv, const long long* __restrict__ toff, const int* __restrict__ tpts,
+                                const int* __restrict__ sides, const double* __restrict__ gview, double* __restrict__ g) {
+  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (t >= ntrace) return;
+  const int cnt = tpts[t] * nv;
+  const int e0 = sides[4 * t], f0 = sides[4 * t + 1], e1 = sides[4 * t + 2], f1 = sides[4 * t + 3];
+  for (int i = lane; i < cnt; i += 32) {
+    double s = gview[(size_t)(4 * e0 + f0) * GN * nv + i];
+    if (e1 >= 0) s += gview[(size_t)(4 * e1 + f1) * GN * nv + i];
+    g[toff[t] + i] = s;
+  }
+}
+
+// initial trace: average of both sides' states at the trace points; far field: average with
+// u_inf; wall: the element's state with zero momentum
+__global__ void k_gen_initial_trace(int ntrace, int nv, const long long* __restrict__ toff, const int* __restrict__ tpts,
+                                    const int* __restrict__ sides, const int* __restrict__ kind,
+                                    const double* __restrict__ Uf, GArgs a, double* __restrict__ uhat) {
+  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (t >= ntrace) return;
+  const int cnt = tpts[t] * nv;
+  const int e0 = sides[4 * t], f0 = sides[4 * t + 1], e1 = sides[4 * t + 2], f1 = sides[4 * t + 3];
+  const int kf = kind[4 * e0 + f0];
+  for (int i = lane; i < cnt; i += 32) {
+    const int v = i % nv;
+    const double u0 = Uf[(size_t)(4 * e0 + f0) * GN * nv + i];
+    double x;
+    if (e1 >= 0)
+      x = 0.5 * (u0 + Uf[(size_t)(4 * e1 + f1) * GN * nv + i]);
+    else if (kf == FK_FAR)
+      x = 0.5 * (u0 + a.uinf[v]);
+    else
+      x = (v == 0 || v == nv - 1) ? u0 : 0.0;
+    uhat[toff[t] + i] = x;
+  }
+}
+
+// ------------------------------------------------------------------------ element blocks
+// One CTA per implicit element.  Primal state, pointwise Jacobians of the volume flux (state and
+// reference gradient) and of the face flux and trace row (face state, trace, face gradient) by
+// dual numbers, then one warp per seed point (a solution point: NV columns of A and C; a trace
+// face point: NV columns of B and D) propagating the unit tangent through the linear chain of the
+// element operator: face nodes -> face points -> common values at the nodes -> corrected gradient
+// -> flux tangents at the solution points and the face points -> projection to the face nodes ->
+// divergence.  Columns are staged per seed point and written as rows of NV consecutive values.
+struct JArgs {
+  int Eim;
+  const int* imp_idx;
+  const long long* offA;
+  const long long* offB;
+  const long long* offD;
+  const int* lto;  // 4 Eim: local offset of each face's trace unknowns
+  double a_dt;
+  void *A, *B, *C, *D;
+};
+
+template <int NV, typename T>
+struct JWork {
+  T U[GNS][NV];
+  T Ufn[GF][NV], Ufp[GF][NV], ubp[GF][NV], ubn[GF][NV], un[GF][NV];
+  T q[GNS][2][NV];
+  T qfn[GF][2][NV], qfp[GF][2][NV];
+  T iJ[GNS], ciJ[GNS], Sm[GNS][2][2];
+  T fJ[GF], fnr[GF][2];
+  T M[GN][GN], lm[GN], lp[GN], dgL[GN], dgR[GN];
+  T Tf[4][GN][GN], Pf[4][GN][GN], wq[4][GN];
+  // pointwise Jacobians, innermost index the input variable
+  T KU[GNS][2][NV][NV];
+  T KQ[GNS][2][2][NV][NV];
+  T GU[GF][NV][NV], GH[GF][NV][NV], GQ[GF][2][NV][NV];
+  T RU[GF][NV][NV], RH[GF][NV][NV], RQ[GF][2][NV][NV];
+  struct Col {
+    T dUfn[GF], dUfp[GF], dubp[GF], dubn[GF];
+    T dQ[GNS][2], dq[GNS][2];
+    T dqfn[GF][2], dqfp[GF][2];
+    T dFt[GNS][2][NV];
+    T dFnp[GF][NV], drow[GF][NV], dFnn[GF][NV];
+    T out[(GNS + GF) * NV][NV];
+  } col[JW];
+  T uinf[5];
+  int nf[4], kf[4], tr[4], lto[4];
+};
+
+static_assert(sizeof(JWork<4, double>) <= 227 * 1024, "block kernel workspace exceeds shared memory");
+static_assert(sizeof(GWork<4>) * GEPB <= 227 * 1024, "residual workspace exceeds shared memory");
+
+template <int PHYS, typename T>
+__global__ void __launch_bounds__(JT) k_gen_jacobian(const __grid_constant__ PhysParams pp,
+                                                    const __grid_constant__ GArgs a,
+                                                    const __grid_constant__ JArgs j) {
+  constexpr int NV = Phys<PHYS>::NV;
+  using DT = Dual<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  JWork<NV, T>& w = *reinterpret_cast<JWork<NV, T>*>(smem_raw);
+  const int k = blockIdx.x;
+  if (k >= j.Eim) return;
+  const int e = j.imp_idx[k];
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  const int n = a.deg[e], ns = n * n;
+  const int nA = ns * NV;
+  const GenRef& RF = *a.ref;
+  const bool visc = phys_viscous(pp);
+  const PhysConst<T> pc = phys_const<T>(pp);
+  const double* gs = a.geo_sol + (size_t)a.goff[e] * 5;
+  for (int i = tid; i < n * n; i += JT) w.M[i / n][i % n] = T(RF.M[n][i / n][i % n]);
+  if (tid < n) {
+    w.lm[tid] = T(RF.lm[n][tid]);
+    w.lp[tid] = T(RF.lp[n][tid]);
+    w.dgL[tid] = T(RF.dgL[n][tid]);
+    w.dgR[tid] = T(RF.dgR[n][tid]);
+  }
+  if (tid < 4) {
+    w.nf[tid] = a.nfp[4 * e + tid];
+    w.kf[tid] = a.kind[4 * e + tid];
+    w.tr[tid] = a.tr_of[4 * e + tid];
+    w.lto[tid] = j.lto[4 * k + tid];
+  }
+  if (tid < 5) w.uinf[tid] = T(a.uinf[tid]);
+  for (int i = tid; i < ns; i += JT) {
+    w.iJ[i] = T(gs[i * 5]);
+    w.ciJ[i] = T(j.a_dt * gs[i * 5]);
+    w.Sm[i][0][0] = T(gs[i * 5 + 1]);
+    w.Sm[i][0][1] = T(gs[i * 5 + 2]);
+    w.Sm[i][1][0] = T(gs[i * 5 + 3]);
+    w.Sm[i][1][1] = T(gs[i * 5 + 4]);
+  }
+  const double* Ue = a.U + a.uoff[e];
+  for (int i = tid; i < nA; i += JT) w.U[i / NV][i % NV] = T(Ue[i]);
+  __syncthreads();
+  for (int i = tid; i < 4 * GN * GN; i += JT) {
+    const int f = i / (GN * GN), x = (i / GN) % GN, y = i % GN, m = w.nf[f];
+    w.Tf[f][x][y] = (x < m && y < n) ? T(RF.T[n][m][x][y]) : T(0);
+    w.Pf[f][x][y] = (x < n && y < m) ? T(RF.P[n][m][x][y]) : T(0);
+  }
+  for (int jj = tid; jj < GF; jj += JT) {
+    const int f = jj / GN, q = jj % GN;
+    w.wq[f][q] = q < w.nf[f] ? T(RF.w[w.nf[f]][q]) : T(0);
+    const double* G = a.geo_face + ((size_t)(4 * e + f) * GN + q) * 3;
+    w.fJ[jj] = q < w.nf[f] ? T(G[0]) : T(0);
+    w.fnr[jj][0] = q < w.nf[f] ? T(G[1]) : T(0);
+    w.fnr[jj][1] = q < w.nf[f] ? T(G[2]) : T(0);
+  }
+  for (int it = tid; it < 4 * n * NV; it += JT) {
+    const int f = it / (n * NV), b = (it / NV) % n, v = it % NV, r = f >> 1;
+    const T* l = (f & 1) ? w.lp : w.lm;
+    T s = T(0);
+    for (int c = 0; c < n; ++c) s += l[c] * w.U[gline(r, b, c, n)][v];
+    w.Ufn[f * GN + b][v] = s;
+  }
+  __syncthreads();
+  for (int it = tid; it < GF * NV; it += JT) {
+    const int f = it / (GN * NV), q = (it / NV) % GN, v = it % NV;
+    T s = T(0), ub = T(0), un = T(0);
+    if (q < w.nf[f]) {
+      for (int b = 0; b < n; ++b) s += w.Tf[f][q][b] * w.Ufn[f * GN + b][v];
+      const int t = w.tr[f];
+      if (t >= 0) {
+        ub = T(a.uhat[a.toff[t] + q * NV + v]);
+        un = s;
+      } else {  // interface face of an implicit element: the explicit neighbour's state
+        const int nb = a.nbr[4 * e + f], fn = a.nbr_face[4 * e + f];
+        un = T(a.Uf_all[((size_t)(4 * nb + fn) * GN + q) * NV + v]);
+        ub = un;
+      }
+    }
+    w.Ufp[f * GN + q][v] = s;
+    w.ubp[f * GN + q][v] = ub;
+    w.un[f * GN + q][v] = un;
+  }
+  __syncthreads();
+  for (int it = tid; it < 4 * GN * NV; it += JT) {
+    const int f = it / (GN * NV), b = (it / NV) % GN, v = it % NV;
+    T s = T(0);
+    if (b < n) {
+      s = w.Ufn[f * GN + b][v];
+      for (int q = 0; q < w.nf[f]; ++q) s += w.Pf[f][b][q] * (w.ubp[f * GN + q][v] - w.Ufp[f * GN + q][v]);
+    }
+    w.ubn[f * GN + b][v] = s;
+  }
+  __syncthreads();
+  if (visc) {
+    for (int it = tid; it < ns * NV; it += JT) {
+      const int i = it / NV, v = it % NV, ai = i % n, bi = i / n;
+      T q0 = w.dgL[ai] * w.ubn[0 * GN + bi][v] + w.dgR[ai] * w.ubn[1 * GN + bi][v];
+      T q1 = w.dgL[bi] * w.ubn[2 * GN + ai][v] + w.dgR[bi] * w.ubn[3 * GN + ai][v];
+      for (int c = 0; c < n; ++c) {
+        q0 += w.M[ai][c] * w.U[c + n * bi][v];
+        q1 += w.M[bi][c] * w.U[ai + n * c][v];
+      }
+      w.q[i][0][v] = w.iJ[i] * (w.Sm[i][0][0] * q0 + w.Sm[i][1][0] * q1);
+      w.q[i][1][v] = w.iJ[i] * (w.Sm[i][0][1] * q0 + w.Sm[i][1][1] * q1);
+    }
+    __syncthreads();
+    for (int it = tid; it < 4 * n * 2 * NV; it += JT) {
+      const int f = it / (n * 2 * NV), b = (it / (2 * NV)) % n, c2 = (it / NV) % 2, v = it % NV, r = f >> 1;
+      const T* l = (f & 1) ? w.lp : w.lm;
+      T s = T(0);
+      for (int c = 0; c < n; ++c) s += l[c] * w.q[gline(r, b, c, n)][c2][v];
+      w.qfn[f * GN + b][c2][v] = s;
+    }
+    __syncthreads();
+    for (int it = tid; it < GF * 2 * NV; it += JT) {
+      const int f = it / (GN * 2 * NV), q = (it / (2 * NV)) % GN, c2 = (it / NV) % 2, v = it % NV;
+      T s = T(0);
+      if (q < w.nf[f])
+        for (int b = 0; b < n; ++b) s += w.Tf[f][q][b] * w.qfn[f * GN + b][c2][v];
+      w.qfp[f * GN + q][c2][v] = s;
+    }
+  } else {
+    for (int i = tid; i < GNS * 2 * NV; i += JT) (&w.q[0][0][0])[i] = T(0);
+    for (int i = tid; i < GF * 2 * NV; i += JT) (&w.qfp[0][0][0])[i] = T(0);
+  }
+  __syncthreads();
+
+  // -------------------------------------------------- pointwise Jacobians
+  for (int it = tid; it < 2 * ns * NV; it += JT) {
+    const bool isq = it >= ns * NV;
+    const int idx = isq ? it - ns * NV : it;
+    const int i = idx / NV, vp = idx % NV;
+    DT u[NV], qd[2][NV], F[2][NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      u[v] = DT(w.U[i][v], (!isq && v == vp) ? T(1) : T(0));
+      qd[0][v] = DT(w.q[i][0][v]);
+      qd[1][v] = DT(w.q[i][1][v]);
+    }
+    if (!isq) {
+      Phys<PHYS>::template conv<DT, T>(pc, u, F);
+      if (visc) {
+        DT Fv[2][NV];
+        Phys<PHYS>::template visc<DT, T>(pc, u, qd, Fv);
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+          for (int v = 0; v < NV; ++v) F[c][v] = F[c][v] - Fv[c][v];
+      }
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) w.KU[i][r][v][vp] = w.Sm[i][r][0] * F[0][v].d + w.Sm[i][r][1] * F[1][v].d;
+    } else {
+      T acc[2][2][NV];
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int r2 = 0; r2 < 2; ++r2)
+#pragma unroll
+          for (int v = 0; v < NV; ++v) acc[r][r2][v] = T(0);
+      if (visc) {
+#pragma unroll
+        for (int c2 = 0; c2 < 2; ++c2) {
+          qd[c2][vp].d = T(1);
+          Phys<PHYS>::template visc<DT, T>(pc, u, qd, F);
+          qd[c2][vp].d = T(0);
+#pragma unroll
+          for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+              const T dFr = -(w.Sm[i][r][0] * F[0][v].d + w.Sm[i][r][1] * F[1][v].d);
+#pragma unroll
+              for (int r2 = 0; r2 < 2; ++r2) acc[r][r2][v] += dFr * w.iJ[i] * w.Sm[i][r2][c2];
+            }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int r2 = 0; r2 < 2; ++r2)
+#pragma unroll
+          for (int v = 0; v < NV; ++v) w.KQ[i][r][r2][v][vp] = acc[r][r2][v];
+    }
+  }
+  for (int it = tid; it < GF * 4 * NV; it += JT) {
+    const int jj = it / (4 * NV), dir = it % (4 * NV), grp = dir / NV, vp = dir % NV;
+    const int f = jj / GN, q = jj % GN;
+    const bool live = q < w.nf[f];
+    const int kf = w.kf[f];
+    const bool traced = w.tr[f] >= 0;
+    DT uf[NV], ub[NV], un[NV], qf[2][NV], qn[2][NV], Fn[NV], row[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      uf[v] = DT(w.Ufp[jj][v], (grp == 0 && v == vp) ? T(1) : T(0));
+      ub[v] = DT(w.ubp[jj][v], (grp == 1 && v == vp) ? T(1) : T(0));
+      un[v] = DT(w.un[jj][v]);
+      qf[0][v] = DT(w.qfp[jj][0][v], (grp == 2 && v == vp) ? T(1) : T(0));
+      qf[1][v] = DT(w.qfp[jj][1][v], (grp == 3 && v == vp) ? T(1) : T(0));
+      qn[0][v] = qn[1][v] = DT(T(0));
+    }
+    const bool zero = !live || (grp >= 2 && !visc) || (grp == 1 && !traced);
+    if (!zero)
+      gface_flux<PHYS, DT, T, NV>(pc, visc, kf, traced, true, uf, ub, qf, un, qn, w.fJ[jj], w.fnr[jj][0],
+                                  w.fnr[jj][1], w.uinf, Fn, row);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const T d = zero ? T(0) : Fn[v].d;
+      const T dr = (zero || !traced) ? T(0) : row[v].d;
+      if (grp == 0) {
+        w.GU[jj][v][vp] = d;
+        w.RU[jj][v][vp] = dr;
+      } else if (grp == 1) {
+        w.GH[jj][v][vp] = d;
+        w.RH[jj][v][vp] = dr;
+      } else {
+        w.GQ[jj][grp - 2][v][vp] = d;
+        w.RQ[jj][grp - 2][v][vp] = dr;
+      }
+    }
+  }
+  __syncthreads();
+
+  // -------------------------------------------------- columns, one seed point per warp
+  int nseed_tr = 0;
+  for (int f = 0; f < 4; ++f)
+    if (w.tr[f] >= 0) nseed_tr += w.nf[f];
+  int nT = 0;
+  for (int f = 0; f < 4; ++f) nT += w.nf[f] * NV;
+  T* Ab = reinterpret_cast<T*>(j.A) + j.offA[k];
+  T* Bb = reinterpret_cast<T*>(j.B) + j.offB[k];
+  T* Cb = reinterpret_cast<T*>(j.C) + j.offB[k];
+  T* Db = reinterpret_cast<T*>(j.D) + j.offD[k];
+  // columns of faces without a trace are zero in B and D
+  for (int f = 0; f < 4; ++f) {
+    if (w.tr[f] >= 0) continue;
+    const int c0 = w.lto[f], cn = w.nf[f] * NV;
+    for (int it = tid; it < (nA + nT) * cn; it += JT) {
+      const int rrow = it / cn, c = c0 + it % cn;
+      if (rrow < nA)
+        Bb[(size_t)rrow * nT + c] = T(0);
+      else
+        Db[(size_t)(rrow - nA) * nT + c] = T(0);
+    }
+  }
+  typename JWork<NV, T>::Col& cw = w.col[wp];
+  for (int sp = wp; sp < ns + nseed_tr; sp += JW) {
+    const bool vol = sp < ns;
+    int a0 = 0, b0 = 0, f0 = -1, q0 = -1;
+    if (vol) {
+      a0 = sp % n;
+      b0 = sp / n;
+    } else {
+      int rem = sp - ns;
+      for (int f = 0; f < 4; ++f) {
+        if (w.tr[f] < 0) continue;
+        if (rem < w.nf[f]) {
+          f0 = f;
+          q0 = rem;
+          break;
+        }
+        rem -= w.nf[f];
+      }
+    }
+    for (int v0 = 0; v0 < NV; ++v0) {
+      // face node and face point tangents of the state, trace tangent
+      for (int jj = lane; jj < GF; jj += 32) {
+        const int f = jj / GN, b = jj % GN, r = f >> 1;
+        T d = T(0);
+        if (vol && b < n) {
+          const T* l = (f & 1) ? w.lp : w.lm;
+          if (r == 0 && b == b0) d = l[a0];
+          if (r == 1 && b == a0) d = l[b0];
+        }
+        cw.dUfn[jj] = d;
+        cw.dubp[jj] = (!vol && f == f0 && b == q0) ? T(1) : T(0);
+      }
+      __syncwarp();
+      for (int jj = lane; jj < GF; jj += 32) {
+        const int f = jj / GN, q = jj % GN;
+        T s = T(0);
+        if (q < w.nf[f])
+          for (int b = 0; b < n; ++b) s += w.Tf[f][q][b] * cw.dUfn[f * GN + b];
+        cw.dUfp[jj] = s;
+      }
+      __syncwarp();
+      if (visc) {
+        for (int jj = lane; jj < GF; jj += 32) {
+          const int f = jj / GN, b = jj % GN;
+          T s = T(0);
+          if (b < n) {
+            s = cw.dUfn[jj];
+            for (int q = 0; q < w.nf[f]; ++q) s += w.Pf[f][b][q] * (cw.dubp[f * GN + q] - cw.dUfp[f * GN + q]);
+          }
+          cw.dubn[jj] = s;
+        }
+        __syncwarp();
+        for (int i = lane; i < ns; i += 32) {
+          const int ai = i % n, bi = i / n;
+          T q0v = w.dgL[ai] * cw.dubn[0 * GN + bi] + w.dgR[ai] * cw.dubn[1 * GN + bi];
+          T q1v = w.dgL[bi] * cw.dubn[2 * GN + ai] + w.dgR[bi] * cw.dubn[3 * GN + ai];
+          if (vol && bi == b0) q0v += w.M[ai][a0];
+          if (vol && ai == a0) q1v += w.M[bi][b0];
+          cw.dQ[i][0] = q0v;
+          cw.dQ[i][1] = q1v;
+          cw.dq[i][0] = w.iJ[i] * (w.Sm[i][0][0] * q0v + w.Sm[i][1][0] * q1v);
+          cw.dq[i][1] = w.iJ[i] * (w.Sm[i][0][1] * q0v + w.Sm[i][1][1] * q1v);
+        }
+        __syncwarp();
+        for (int it = lane; it < GF * 2; it += 32) {
+          const int jj = it >> 1, c2 = it & 1, f = jj / GN, b = jj % GN, r = f >> 1;
+          T s = T(0);
+          if (b < n) {
+            const T* l = (f & 1) ? w.lp : w.lm;
+            for (int c = 0; c < n; ++c) s += l[c] * cw.dq[gline(r, b, c, n)][c2];
+          }
+          cw.dqfn[jj][c2] = s;
+        }
+        __syncwarp();
+        for (int it = lane; it < GF * 2; it += 32) {
+          const int jj = it >> 1, c2 = it & 1, f = jj / GN, q = jj % GN;
+          T s = T(0);
+          if (q < w.nf[f])
+            for (int b = 0; b < n; ++b) s += w.Tf[f][q][b] * cw.dqfn[f * GN + b][c2];
+          cw.dqfp[jj][c2] = s;
+        }
+      }
+      __syncwarp();
+      // flux tangents at the solution points
+      for (int it = lane; it < ns * 2 * NV; it += 32) {
+        const int i = it / (2 * NV), r = (it / NV) % 2, v = it % NV;
+        T s = T(0);
+        if (visc) s = w.KQ[i][r][0][v][v0] * cw.dQ[i][0] + w.KQ[i][r][1][v][v0] * cw.dQ[i][1];
+        if (vol && i == sp) s += w.KU[i][r][v][v0];
+        cw.dFt[i][r][v] = s;
+      }
+      // face-point flux and trace-row tangents
+      for (int it = lane; it < GF * NV; it += 32) {
+        const int jj = it / NV, v = it % NV, f = jj / GN, q = jj % GN;
+        T s = T(0), sr = T(0);
+        if (q < w.nf[f]) {
+          const T du = cw.dUfp[jj], dh = cw.dubp[jj];
+          s = w.GU[jj][v][v0] * du + w.GH[jj][v][v0] * dh;
+          sr = w.RU[jj][v][v0] * du + w.RH[jj][v][v0] * dh;
+          if (visc) {
+            s += w.GQ[jj][0][v][v0] * cw.dqfp[jj][0] + w.GQ[jj][1][v][v0] * cw.dqfp[jj][1];
+            sr += w.RQ[jj][0][v][v0] * cw.dqfp[jj][0] + w.RQ[jj][1][v][v0] * cw.dqfp[jj][1];
+          }
+        }
+        cw.dFnp[jj][v] = s;
+        cw.drow[jj][v] = sr;
+      }
+      __syncwarp();
+      for (int it = lane; it < GF * NV; it += 32) {
+        const int jj = it / NV, v = it % NV, f = jj / GN, b = jj % GN;
+        T s = T(0);
+        if (b < n)
+          for (int q = 0; q < w.nf[f]; ++q) s += w.Pf[f][b][q] * cw.dFnp[f * GN + q][v];
+        cw.dFnn[jj][v] = s;
+      }
+      __syncwarp();
+      // A / B column: a dt / J times the divergence tangent (plus the identity of A)
+      for (int it = lane; it < nA; it += 32) {
+        const int i = it / NV, v = it % NV, ai = i % n, bi = i / n;
+        T d = -w.dgL[ai] * cw.dFnn[0 * GN + bi][v] + w.dgR[ai] * cw.dFnn[1 * GN + bi][v] -
+              w.dgL[bi] * cw.dFnn[2 * GN + ai][v] + w.dgR[bi] * cw.dFnn[3 * GN + ai][v];
+        for (int c = 0; c < n; ++c) d += w.M[ai][c] * cw.dFt[c + n * bi][0][v] + w.M[bi][c] * cw.dFt[ai + n * c][1][v];
+        T o = w.ciJ[i] * d;
+        if (vol && i == sp && v == v0) o += T(1);
+        cw.out[it][v0] = o;
+      }
+      // C / D column: the element's trace rows w_q (row tangent), zero off traces
+      for (int it = lane; it < nT; it += 32) {
+        int f = 0, rem = it;
+        while (rem >= w.nf[f] * NV) {
+          rem -= w.nf[f] * NV;
+          ++f;
+        }
+        const int q = rem / NV, v = rem % NV;
+        cw.out[nA + it][v0] = w.tr[f] >= 0 ? w.wq[f][q] * cw.drow[f * GN + q][v] : T(0);
+      }
+      __syncwarp();
+    }
+    // the seed point's NV columns as rows of NV consecutive values
+    const int col0 = vol ? sp * NV : w.lto[f0] + q0 * NV;
+    const int ncol = vol ? nA : nT;
+    T* top = vol ? Ab : Bb;
+    T* bot = vol ? Cb : Db;
+    for (int rr = lane; rr < nA + nT; rr += 32) {
+      T* dst = rr < nA ? top + (size_t)rr * ncol + col0 : bot + (size_t)(rr - nA) * ncol + col0;
+#pragma unroll
+      for (int v0 = 0; v0 < NV; ++v0) dst[v0] = cw.out[rr][v0];
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------------ Newton pieces
+// r_k = -(u - u* - a dt R), s_k = -(element trace rows), one warp per implicit element
+__global__ void k_gen_form_rhs(int Eim, int nv, const int* __restrict__ imp_idx, const int* __restrict__ deg,
+                               const long long* __restrict__ uoff, const long long* __restrict__ offr,
+                               const long long* __restrict__ offs, const int* __restrict__ nfp,
+                               const int* __restrict__ lto, const double* __restrict__ U,
+                               const double* __restrict__ Ustar, const double* __restrict__ R,
+                               const double* __restrict__ gview, double adt, double* __restrict__ r,
+                               double* __restrict__ s) {
+  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (k >= Eim) return;
+  const int e = imp_idx[k], n = deg[e], nA = n * n * nv;
+  const long long u0 = uoff[e];
+  for (int i = lane; i < nA; i += 32) {
+    const double us = Ustar ? Ustar[u0 + i] : U[u0 + i];
+    r[offr[k] + i] = -(U[u0 + i] - us - adt * R[u0 + i]);
+  }
+  for (int f = 0; f < 4; ++f) {
+    const int cnt = nfp[4 * e + f] * nv;
+    for (int i = lane; i < cnt; i += 32)
+      s[offs[k] + lto[4 * k + f] + i] = -gview[(size_t)(4 * e + f) * GN * nv + i];
+  }
+}
+
+// element view of the trace operator: yv_k = S_k x[gmap_k] (one warp per implicit element; rows
+// one at a time, lanes along the row)
+template <typename T>
+__global__ void k_gen_matvec_elem(int Eim, const int* __restrict__ nTk, const long long* __restrict__ offD,
+                                  const long long* __restrict__ offs, const int* __restrict__ gmap,
+                                  const T* __restrict__ S, const double* __restrict__ x, double* __restrict__ yv,
+                                  const int* gate, int gj) {
+  if (gate && *gate >= 0 && gj >= *gate) return;
+  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (k >= Eim) return;
+  const int nT = nTk[k];
+  const T* Sk = S + offD[k];
+  const int* gm = gmap + offs[k];
+  T xl[16];  // nT <= 512
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const int l = lane + 32 * c;
+    const int g = l < nT ? gm[l] : -1;
+    xl[c] = g >= 0 ? T(x[g]) : T(0);
+  }
+  for (int row = 0; row < nT; ++row) {
+    T acc = T(0);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int l = lane + 32 * c;
+      if (l < nT) acc += Sk[(size_t)row * nT + l] * xl[c];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) yv[offs[k] + row] = double(acc);
+  }
+}
+
+// y[d] = sum over the sides of the element-view values of trace value d
+__global__ void k_gen_gather_sum(size_t nh, const long long* __restrict__ ginv, const double* __restrict__ yv,
+                                 double* __restrict__ y, const int* gate, int gj) {
+  if (gate && *gate >= 0 && gj >= *gate) return;
+  const size_t d = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= nh) return;
+  const long long i0 = ginv[2 * d], i1 = ginv[2 * d + 1];
+  double s = yv[i0];
+  if (i1 >= 0) s += yv[i1];
+  y[d] = s;
+}
+
+// face-block Jacobi: P_t = sum over the sides of the face's diagonal block of S_k, inverted by
+// Gauss-Jordan with partial pivoting (one warp per trace face, FP64 arithmetic, stored in T)
+template <typename T>
+__global__ void k_gen_precond_build(int ntrace, int nv, const int* __restrict__ tpts, const long long* __restrict__ poff,
+                                    const int* __restrict__ pside, const int* __restrict__ nTk,
+                                    const long long* __restrict__ offD, const T* __restrict__ S, T* __restrict__ Pinv,
+                                    double* __restrict__ work, int* status) {
+  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (t >= ntrace) return;
+  const int bs = tpts[t] * nv;
+  double* Wm = work + (size_t)poff[t] * 2;  // bs x 2bs augmented [P | I]
+  const int w2 = 2 * bs;
+  for (int i = lane; i < bs * w2; i += 32) {
+    const int r = i / w2, c = i % w2;
+    double v = 0.0;
+    if (c < bs) {
+      for (int sd = 0; sd < 2; ++sd) {
+        const int kk = pside[4 * t + 2 * sd], lo = pside[4 * t + 2 * sd + 1];
+        if (kk < 0) continue;
+        const int nT = nTk[kk];
+        v += double(S[offD[kk] + (size_t)(lo + r) * nT + lo + c]);
+      }
+    } else {
+      v = (c - bs == r) ? 1.0 : 0.0;
+    }
+    Wm[i] = v;
+  }
+  __syncwarp();
+  bool bad = false;
+  for (int c = 0; c < bs; ++c) {
+    double bv = -1.0;
+    int bi = bs;
+    for (int r = c + lane; r < bs; r += 32) {
+      const double v = fabs(Wm[r * w2 + c]);
+      if (v > bv || (v == bv && r < bi)) { bv = v; bi = r; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (!(bv > 0.0)) { bad = true; break; }
+    if (bi != c)
+      for (int x = lane; x < w2; x += 32) {
+        const double u = Wm[c * w2 + x];
+        Wm[c * w2 + x] = Wm[bi * w2 + x];
+        Wm[bi * w2 + x] = u;
+      }
+    __syncwarp();
+    const double inv = 1.0 / Wm[c * w2 + c];
+    __syncwarp();  // every lane holds the pivot before its row is scaled
+    for (int x = lane; x < w2; x += 32) Wm[c * w2 + x] *= inv;
+    __syncwarp();
+    for (int r = 0; r < bs; ++r) {
+      if (r == c) continue;
+      const double l = Wm[r * w2 + c];
+      __syncwarp();
+      for (int x = lane; x < w2; x += 32) Wm[r * w2 + x] -= l * Wm[c * w2 + x];
+    }
+    __syncwarp();
+  }
+  if (bad) {
+    if (lane == 0) {
+      atomicOr(status, DEV_ERR_SINGULAR);
+      atomicMin(status + 1, -1 - t);
+    }
+    return;
+  }
+  T* P = Pinv + poff[t];
+  for (int i = lane; i < bs * bs; i += 32) P[i] = T(Wm[(i / bs) * w2 + bs + i % bs]);
+}
+
+// z_t = Pinv_t v_t (v first normalised in place by *inv_h when given); one warp per trace face
+template <typename T>
+__global__ void k_gen_precond_apply(int ntrace, int nv, const int* __restrict__ tpts, const long long* __restrict__ toff,
+                                    const long long* __restrict__ poff, const T* __restrict__ Pinv,
+                                    double* __restrict__ x, double* __restrict__ y, const int* gate, int gj,
+                                    const double* inv_h, float* __restrict__ y32) {
+  if (gate && *gate >= 0 && gj >= *gate) return;
+  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (t >= ntrace) return;
+  const int bs = tpts[t] * nv;
+  const long long o = toff[t];
+  const T* P = Pinv + poff[t];
+  double xl[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int i = lane + 32 * c;
+    double v = i < bs ? x[o + i] : 0.0;
+    if (inv_h && i < bs) {
+      v *= *inv_h;
+      x[o + i] = v;
+    }
+    xl[c] = v;
+  }
+  for (int row = 0; row < bs; ++row) {
+    double acc = 0.0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = lane + 32 * c;
+      if (i < bs) acc += double(P[(size_t)row * bs + i]) * double(T(xl[c]));
+    }
+#pragma unroll
+    for (int of = 16; of > 0; of >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, of);
+    if (lane == 0) {
+      y[o + row] = acc;
+      if (y32) y32[o + row] = float(acc);
+    }
+  }
+}
+
+// du_k = x_r - X_B du^_k, one warp per implicit element
+template <typename T>
+__global__ void k_gen_backsolve(int Eim, const int* __restrict__ nAk, const int* __restrict__ nTk,
+                                const long long* __restrict__ offB, const long long* __restrict__ offr,
+                                const long long* __restrict__ offs, const int* __restrict__ gmap,
+                                const T* __restrict__ XB, const double* __restrict__ xr,
+                                const double* __restrict__ duhat, double* __restrict__ du) {
+  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (k >= Eim) return;
+  const int nA = nAk[k], nT = nTk[k];
+  const T* X = XB + offB[k];
+  const int* gm = gmap + offs[k];
+  double dl[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const int l = lane + 32 * c;
+    const int g = l < nT ? gm[l] : -1;
+    dl[c] = g >= 0 ? duhat[g] : 0.0;
+  }
+  for (int i = 0; i < nA; ++i) {
+    double acc = 0.0;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int l = lane + 32 * c;
+      if (l < nT) acc += double(X[(size_t)i * nT + l]) * dl[c];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) du[offr[k] + i] = xr[offr[k] + i] - acc;
+  }
+}
+
+// u[uoff[e_k] + i] += du_k[i]
+__global__ void k_gen_apply_du(int Eim, int nv, const int* __restrict__ imp_idx, const int* __restrict__ deg,
+                               const long long* __restrict__ uoff, const long long* __restrict__ offr,
+                               const double* __restrict__ du, double* __restrict__ U) {
+  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (k >= Eim) return;
+  const int e = imp_idx[k], n = deg[e], nA = n * n * nv;
+  for (int i = lane; i < nA; i += 32) U[uoff[e] + i] += du[offr[k] + i];
+}
+
+__global__ void k_gen_axpy(size_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] += a * x[i];
+}
+
+struct StageCoefG {
+  int nterm;
+  double ci[8], ce[8];
+  int hi[8];
+};
+// out = base + sum_j c_j R_hist[h_j], per value with its element's implicit flag
+__global__ void k_gen_stage_combine(size_t tot, const unsigned char* __restrict__ dof_imp,
+                                    const double* __restrict__ base, const double* __restrict__ Rh, StageCoefG sc,
+                                    double* __restrict__ out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= tot) return;
+  const bool im = dof_imp[i] != 0;
+  double v = base[i];
+  for (int jj = 0; jj < sc.nterm; ++jj) {
+    const double c = im ? sc.ci[jj] : sc.ce[jj];
+    if (c != 0.0) v += c * Rh[(size_t)sc.hi[jj] * tot + i];
+  }
+  out[i] = v;
+}
+
+__global__ void k_gen_sumsq_part(const double* __restrict__ a, size_t na, const double* __restrict__ b, size_t nb,
+                                 double* __restrict__ partial) {
+  __shared__ double red[8];
+  double s = 0.0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < na + nb; x += stride) {
+    const double v = x < na ? a[x] : b[x - na];
+    s += v * v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    partial[blockIdx.x] = t;
+  }
+}
+__global__ void k_gen_sumsq_final(const double* __restrict__ partial, int nblk, double* out) {
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x >= 32) return;
+  double t = 0.0;
+  for (int i = lane; i < nblk; i += 32) t += partial[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0) *out = t;
+}
+
+__global__ void k_gen_status_reset(int* status) {
+  status[0] = 0;
+  status[1] = 0x7fffffff;
+}
+
+// ------------------------------------------------------------------------ context
+struct GenCtx {
+  Hooks hk;
+  cudaStream_t st = 0;
+  int E = 0, Eim = 0, nv = 0, ntrace = 0, pb = 8, tableau = 0, restart = 30, pmax = 0;
+  int maxA = 0, maxT = 0;
+  bool need_nbr = false, has_explicit = false;
+  PhysParams pp;
+  double uinf[5] = {0, 0, 0, 0, 0};
+  size_t nstate = 0, nh = 0, sumA = 0, sumT = 0, sumAA = 0, sumAT = 0, sumTT = 0, sumP = 0;
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+  std::vector<long long> h_uoff, h_toff;
+  std::vector<int> h_nA, h_nT, h_deg;
+  std::vector<double> xy;
+  // device
+  GenRef* ref = nullptr;
+  int *deg = nullptr, *nbr = nullptr, *nbr_face = nullptr, *kind = nullptr, *tr_of = nullptr, *nfp = nullptr;
+  long long *uoff = nullptr, *goff = nullptr, *toff = nullptr;
+  double *geo_sol = nullptr, *geo_face = nullptr;
+  unsigned char *implicit = nullptr, *dof_imp = nullptr;
+  int *tpts = nullptr, *sides = nullptr, *pside = nullptr;
+  long long* poff = nullptr;
+  int *imp_idx = nullptr, *lto = nullptr, *nAk = nullptr, *nTk = nullptr, *gmap = nullptr;
+  long long *offA = nullptr, *offB = nullptr, *offD = nullptr, *offr = nullptr, *offs = nullptr, *ginv = nullptr;
+  double *Uf_all = nullptr, *qf_all = nullptr, *Rw = nullptr, *gview = nullptr, *gw = nullptr, *Ustar = nullptr;
+  double *r = nullptr, *s = nullptr, *xr = nullptr, *te = nullptr, *tg = nullptr, *yv = nullptr;
+  double *duhat = nullptr, *du = nullptr, *red = nullptr, *pwork = nullptr;
+  void *A = nullptr, *B = nullptr, *C = nullptr, *D = nullptr, *LU = nullptr, *XB = nullptr, *S = nullptr, *Pinv = nullptr;
+  int* piv = nullptr;
+  int* status = nullptr;
+  UnevenDev udev;
+  GmresBuffers gm;
+  bool lin_valid = false;
+};
+
+static int err(GenCtx* g, int code, const char* msg, int elem = -1, int it = -1, double val = 0.0) {
+  if (g && g->hk.set_err) return g->hk.set_err(g->hk.owner, code, msg, elem, it, val);
+  return code;
+}
+#define GCK(call)                                                                  \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) return err(g, FR_ERR_CUDA, cudaGetErrorString(e_));     \
+  } while (0)
+static int pbeg(GenCtx* g, int ph) { return g->hk.prof_begin ? g->hk.prof_begin(g->hk.owner, ph) : -1; }
+static void pend(GenCtx* g, int h) {
+  if (g->hk.prof_end) g->hk.prof_end(g->hk.owner, h);
+}
+static inline unsigned nb256(size_t n) { return (unsigned)((n + 255) / 256); }
+static inline unsigned nbw(size_t nwarps, int wpb = 8) { return (unsigned)((nwarps + wpb - 1) / wpb); }
+
+template <typename T>
+static T* galloc(GenCtx* g, size_t count, int* rc) {
+  if (count == 0) count = 1;
+  void* p = nullptr;
+  if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+    *rc = FR_ERR_OOM;
+    return nullptr;
+  }
+  g->allocs.push_back(p);
+  g->bytes += count * sizeof(T);
+  return (T*)p;
+}
+
+bool mesh_is_general(const fr_mesh_desc* mesh) {
+  if (!mesh) return false;
+  if (mesh->p_elem)
+    for (int e = 1; e < mesh->nelem; ++e)
+      if (mesh->p_elem[e] != mesh->p_elem[0]) return true;
+  if (mesh->nbr)
+    for (long long i = 0; i < 4LL * mesh->nelem; ++i)
+      if (mesh->nbr[i] < 0) return true;
+  return false;
+}
+
+static void bilinear_g(const double* V, double xi, double eta, double* J, double S[2][2], double* xy) {
+  const double sa[4] = {-1, 1, -1, 1}, sb[4] = {-1, -1, 1, 1};
+  double xx = 0, xe = 0, yx = 0, ye = 0, px = 0, py = 0;
+  for (int c = 0; c < 4; ++c) {
+    const double dNx = 0.25 * sa[c] * (1 + sb[c] * eta), dNe = 0.25 * sb[c] * (1 + sa[c] * xi);
+    const double Nc = 0.25 * (1 + sa[c] * xi) * (1 + sb[c] * eta);
+    xx += dNx * V[2 * c];
+    yx += dNx * V[2 * c + 1];
+    xe += dNe * V[2 * c];
+    ye += dNe * V[2 * c + 1];
+    px += Nc * V[2 * c];
+    py += Nc * V[2 * c + 1];
+  }
+  *J = xx * ye - xe * yx;
+  S[0][0] = ye;
+  S[0][1] = -xe;
+  S[1][0] = -yx;
+  S[1][1] = xx;
+  if (xy) {
+    xy[0] = px;
+    xy[1] = py;
+  }
+}
+
+void destroy(GenCtx* g) {
+  if (!g) return;
+  for (void* p : g->allocs) cudaFree(p);
+  delete g;
+}
+
+int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, const Hooks& hooks, GenCtx** out) {
+  *out = nullptr;
+  const int E = mesh->nelem;
+  if (cfg->physics != FR_PHYS_ADVDIFF && cfg->physics != FR_PHYS_NAVIER_STOKES) return FR_ERR_UNSUPPORTED;
+  if (cfg->precision != FR_PREC_FP64 && cfg->precision != FR_PREC_FP32) return FR_ERR_INVALID_ARG;
+  const int nv = cfg->physics == FR_PHYS_ADVDIFF ? 1 : 4;
+  std::vector<int> deg(E);
+  for (int e = 0; e < E; ++e) {
+    const int p = mesh->p_elem ? mesh->p_elem[e] : mesh->p;
+    if (p < 1 || p > 5) return FR_ERR_UNSUPPORTED;
+    deg[e] = p + 1;
+  }
+  // connectivity, face kinds, face point counts
+  std::vector<int> kind(4 * (size_t)E), nfp(4 * (size_t)E), nbr(4 * (size_t)E), nbf(4 * (size_t)E);
+  bool need_nbr = false;
+  for (int e = 0; e < E; ++e)
+    for (int f = 0; f < 4; ++f) {
+      const size_t i = 4 * (size_t)e + f;
+      const int nb = mesh->nbr[i], nf = mesh->nbr_face[i], id = mesh->face_of[i];
+      const bool ie = mesh->implicit[e] != 0;
+      if (id < 0 || (long long)id >= 4LL * E) return FR_ERR_INVALID_ARG;
+      if (nb < 0) {
+        const int bc = mesh->bc ? mesh->bc[i] : 0;
+        if (bc == BC_WALL) {
+          if (!ie || cfg->physics != FR_PHYS_NAVIER_STOKES) return FR_ERR_UNSUPPORTED;  // explicit walls: not built
+          kind[i] = FK_WALL;
+        } else if (bc == BC_FAR) {
+          kind[i] = FK_FAR;
+          if (!ie) need_nbr = true;
+        } else {
+          return FR_ERR_INVALID_ARG;
+        }
+        nbr[i] = -1;
+        nbf[i] = -1;
+        nfp[i] = deg[e];
+        continue;
+      }
+      if (nb >= E || nf < 0 || nf > 3 || mesh->nbr[4 * (size_t)nb + nf] != e || mesh->nbr_face[4 * (size_t)nb + nf] != f ||
+          mesh->face_of[4 * (size_t)nb + nf] != id)
+        return FR_ERR_INVALID_ARG;
+      const bool in = mesh->implicit[nb] != 0;
+      kind[i] = (ie && in) ? FK_TRACE : (ie != in ? FK_IMEX : FK_FR);
+      if (kind[i] != FK_TRACE) need_nbr = true;
+      nbr[i] = nb;
+      nbf[i] = nf;
+      nfp[i] = std::max(deg[e], deg[nb]);
+    }
+  GenCtx* g = new GenCtx();
+  g->hk = hooks;
+  g->st = st;
+  g->E = E;
+  g->nv = nv;
+  g->pb = cfg->precision == FR_PREC_FP64 ? 8 : 4;
+  g->tableau = cfg->tableau;
+  g->restart = cfg->gmres_restart > 0 ? std::min(cfg->gmres_restart, GM_MAXM) : 30;
+  g->need_nbr = need_nbr;
+  g->has_explicit = need_nbr;
+  memset(&g->pp, 0, sizeof(g->pp));
+  g->pp.kind = cfg->physics;
+  g->pp.beta[0] = cfg->beta[0];
+  g->pp.beta[1] = cfg->beta[1];
+  g->pp.nu = cfg->nu;
+  g->pp.gamma = cfg->gamma;
+  g->pp.mu = cfg->mu;
+  g->pp.Pr = cfg->Pr;
+  g->pp.lref = cfg->lref > 0 ? cfg->lref : 1.0;
+  for (int v = 0; v < 5; ++v) g->uinf[v] = cfg->u_inf[v];
+  g->h_deg = deg;
+  // trace numbering: faces with a trace (both sides implicit, or a boundary face of an implicit
+  // element) in increasing global face id
+  std::vector<int> tr_of(4 * (size_t)E, -1), tr_of_fid(4 * (size_t)E, -1), pts_of_fid(4 * (size_t)E, 0);
+  for (int e = 0; e < E; ++e)
+    for (int f = 0; f < 4; ++f) {
+      const size_t i = 4 * (size_t)e + f;
+      if (kind[i] == FK_TRACE || (nbr[i] < 0 && mesh->implicit[e])) {
+        tr_of_fid[mesh->face_of[i]] = 0;
+        pts_of_fid[mesh->face_of[i]] = nfp[i];
+      }
+    }
+  int nt = 0;
+  std::vector<int> tpts;
+  for (size_t id = 0; id < tr_of_fid.size(); ++id)
+    if (tr_of_fid[id] == 0) {
+      tr_of_fid[id] = nt++;
+      tpts.push_back(pts_of_fid[id]);
+    }
+  g->ntrace = nt;
+  std::vector<long long> toff(nt + 1, 0);
+  for (int t = 0; t < nt; ++t) toff[t + 1] = toff[t] + (long long)tpts[t] * nv;
+  g->nh = (size_t)toff[nt];
+  std::vector<int> sides(4 * (size_t)std::max(nt, 1), -1);
+  for (int e = 0; e < E; ++e)
+    for (int f = 0; f < 4; ++f) {
+      const size_t i = 4 * (size_t)e + f;
+      if (kind[i] == FK_TRACE || (nbr[i] < 0 && mesh->implicit[e])) {
+        const int t = tr_of_fid[mesh->face_of[i]];
+        tr_of[i] = t;
+        const int slot = sides[4 * (size_t)t] < 0 ? 0 : 1;
+        sides[4 * (size_t)t + 2 * slot] = e;
+        sides[4 * (size_t)t + 2 * slot + 1] = f;
+      }
+    }
+  // state offsets, implicit blocks
+  std::vector<long long> uoff(E + 1, 0), goff(E + 1, 0);
+  for (int e = 0; e < E; ++e) {
+    uoff[e + 1] = uoff[e] + (long long)deg[e] * deg[e] * nv;
+    goff[e + 1] = goff[e] + (long long)deg[e] * deg[e];
+    g->pmax = std::max(g->pmax, deg[e] - 1);
+  }
+  g->nstate = (size_t)uoff[E];
+  std::vector<int> imp_idx, comp(E, -1);
+  for (int e = 0; e < E; ++e)
+    if (mesh->implicit[e]) {
+      comp[e] = (int)imp_idx.size();
+      imp_idx.push_back(e);
+    }
+  const int Eim = (int)imp_idx.size();
+  g->Eim = Eim;
+  std::vector<int> nAk(std::max(Eim, 1)), nTk(std::max(Eim, 1)), lto(4 * (size_t)std::max(Eim, 1));
+  std::vector<long long> offA(Eim + 1, 0), offB(Eim + 1, 0), offD(Eim + 1, 0), offr(Eim + 1, 0), offs(Eim + 1, 0);
+  for (int k = 0; k < Eim; ++k) {
+    const int e = imp_idx[k];
+    nAk[k] = deg[e] * deg[e] * nv;
+    int o = 0;
+    for (int f = 0; f < 4; ++f) {
+      lto[4 * (size_t)k + f] = o;
+      o += nfp[4 * (size_t)e + f] * nv;
+    }
+    nTk[k] = o;
+    if (o > 512) {
+      destroy(g);
+      return FR_ERR_UNSUPPORTED;
+    }
+    offA[k + 1] = offA[k] + (long long)nAk[k] * nAk[k];
+    offB[k + 1] = offB[k] + (long long)nAk[k] * nTk[k];
+    offD[k + 1] = offD[k] + (long long)nTk[k] * nTk[k];
+    offr[k + 1] = offr[k] + nAk[k];
+    offs[k + 1] = offs[k] + nTk[k];
+    g->maxA = std::max(g->maxA, nAk[k]);
+    g->maxT = std::max(g->maxT, nTk[k]);
+  }
+  g->sumA = (size_t)offr[Eim];
+  g->sumT = (size_t)offs[Eim];
+  g->sumAA = (size_t)offA[Eim];
+  g->sumAT = (size_t)offB[Eim];
+  g->sumTT = (size_t)offD[Eim];
+  g->h_nA.assign(nAk.begin(), nAk.begin() + Eim);
+  g->h_nT.assign(nTk.begin(), nTk.begin() + Eim);
+  // gather map (element-local trace unknown -> trace value) and its inverse (two sides)
+  std::vector<int> gmap(std::max(g->sumT, (size_t)1), -1);
+  std::vector<long long> ginv(2 * std::max(g->nh, (size_t)1), -1);
+  std::vector<int> pside(4 * (size_t)std::max(nt, 1), -1);
+  for (int k = 0; k < Eim; ++k) {
+    const int e = imp_idx[k];
+    for (int f = 0; f < 4; ++f) {
+      const int t = tr_of[4 * (size_t)e + f];
+      if (t < 0) continue;
+      const int sd = sides[4 * (size_t)t] == e && sides[4 * (size_t)t + 1] == f ? 0 : 1;
+      pside[4 * (size_t)t + 2 * sd] = k;
+      pside[4 * (size_t)t + 2 * sd + 1] = lto[4 * (size_t)k + f];
+      const int cnt = tpts[t] * nv;
+      for (int i = 0; i < cnt; ++i) {
+        const long long l = offs[k] + lto[4 * (size_t)k + f] + i;
+        gmap[l] = (int)(toff[t] + i);
+        ginv[2 * (size_t)(toff[t] + i) + sd] = l;
+      }
+    }
+  }
+  std::vector<long long> poff(nt + 1, 0);
+  for (int t = 0; t < nt; ++t) poff[t + 1] = poff[t] + (long long)(tpts[t] * nv) * (tpts[t] * nv);
+  g->sumP = (size_t)poff[nt];
+  // geometry at the own solution points and at every face's points
+  std::vector<double> gsol(5 * (size_t)goff[E]), gface(3 * 4 * (size_t)E * GN, 0.0);
+  g->xy.assign(2 * (size_t)goff[E], 0.0);
+  for (int e = 0; e < E; ++e) {
+    const int n = deg[e];
+    double xg[GN], wg[GN];
+    gauss_legendre_nodes(n, xg, wg);
+    const double* V = mesh->verts + (size_t)e * 8;
+    for (int b = 0; b < n; ++b)
+      for (int a = 0; a < n; ++a) {
+        const size_t pt = (size_t)goff[e] + a + n * b;
+        double J, S[2][2];
+        bilinear_g(V, xg[a], xg[b], &J, S, &g->xy[2 * pt]);
+        double* G = &gsol[5 * pt];
+        G[0] = 1.0 / J;
+        G[1] = S[0][0];
+        G[2] = S[0][1];
+        G[3] = S[1][0];
+        G[4] = S[1][1];
+      }
+    for (int f = 0; f < 4; ++f) {
+      const int m = nfp[4 * (size_t)e + f], r = f >> 1;
+      const double sg = (f & 1) ? 1.0 : -1.0;
+      double sq[GN], wq[GN];
+      gauss_legendre_nodes(m, sq, wq);
+      for (int q = 0; q < m; ++q) {
+        const double xi = r == 0 ? sg : sq[q], eta = r == 0 ? sq[q] : sg;
+        double J, S[2][2];
+        bilinear_g(V, xi, eta, &J, S, nullptr);
+        const double N0 = sg * S[r][0], N1 = sg * S[r][1];
+        const double Jf = sqrt(N0 * N0 + N1 * N1);
+        double* G = &gface[3 * ((size_t)(4 * e + f) * GN + q)];
+        G[0] = Jf;
+        G[1] = N0 / Jf;
+        G[2] = N1 / Jf;
+      }
+    }
+  }
+  std::vector<unsigned char> dof_imp(std::max(g->nstate, (size_t)1), 0), impv(mesh->implicit, mesh->implicit + E);
+  for (int e = 0; e < E; ++e)
+    if (mesh->implicit[e])
+      for (long long i = uoff[e]; i < uoff[e + 1]; ++i) dof_imp[i] = 1;
+  GenRef href;
+  build_genref(href);
+  // condensation tables
+  UnevenTables tb;
+  if (Eim > 0 && uneven_tables(g->pb, Eim, nAk.data(), nTk.data(), &tb) != 0) {
+    destroy(g);
+    return FR_ERR_INVALID_ARG;
+  }
+  // device memory
+  int rc = FR_OK;
+  const size_t pb = g->pb;
+  g->ref = galloc<GenRef>(g, 1, &rc);
+  g->deg = galloc<int>(g, E, &rc);
+  g->nbr = galloc<int>(g, 4 * (size_t)E, &rc);
+  g->nbr_face = galloc<int>(g, 4 * (size_t)E, &rc);
+  g->kind = galloc<int>(g, 4 * (size_t)E, &rc);
+  g->tr_of = galloc<int>(g, 4 * (size_t)E, &rc);
+  g->nfp = galloc<int>(g, 4 * (size_t)E, &rc);
+  g->uoff = galloc<long long>(g, E + 1, &rc);
+  g->goff = galloc<long long>(g, E + 1, &rc);
+  g->toff = galloc<long long>(g, nt + 1, &rc);
+  g->geo_sol = galloc<double>(g, gsol.size(), &rc);
+  g->geo_face = galloc<double>(g, gface.size(), &rc);
+  g->implicit = galloc<unsigned char>(g, E, &rc);
+  g->dof_imp = galloc<unsigned char>(g, dof_imp.size(), &rc);
+  g->tpts = galloc<int>(g, std::max(nt, 1), &rc);
+  g->sides = galloc<int>(g, sides.size(), &rc);
+  g->pside = galloc<int>(g, pside.size(), &rc);
+  g->poff = galloc<long long>(g, nt + 1, &rc);
+  g->imp_idx = galloc<int>(g, std::max(Eim, 1), &rc);
+  g->lto = galloc<int>(g, lto.size(), &rc);
+  g->nAk = galloc<int>(g, nAk.size(), &rc);
+  g->nTk = galloc<int>(g, nTk.size(), &rc);
+  g->gmap = galloc<int>(g, gmap.size(), &rc);
+  g->ginv = galloc<long long>(g, ginv.size(), &rc);
+  g->offA = galloc<long long>(g, Eim + 1, &rc);
+  g->offB = galloc<long long>(g, Eim + 1, &rc);
+  g->offD = galloc<long long>(g, Eim + 1, &rc);
+  g->offr = galloc<long long>(g, Eim + 1, &rc);
+  g->offs = galloc<long long>(g, Eim + 1, &rc);
+  if (need_nbr) {
+    g->Uf_all = galloc<double>(g, 4 * (size_t)E * GN * nv, &rc);
+    g->qf_all = galloc<double>(g, 4 * (size_t)E * GN * 2 * nv, &rc);
+  }
+  g->Rw = galloc<double>(g, g->nstate, &rc);
+  g->gview = galloc<double>(g, 4 * (size_t)E * GN * nv, &rc);
+  g->gw = galloc<double>(g, g->nh, &rc);
+  g->Ustar = galloc<double>(g, g->nstate, &rc);
+  g->r = galloc<double>(g, g->sumA, &rc);
+  g->s = galloc<double>(g, g->sumT, &rc);
+  g->xr = galloc<double>(g, g->sumA, &rc);
+  g->te = galloc<double>(g, g->sumT, &rc);
+  g->tg = galloc<double>(g, g->nh, &rc);
+  g->yv = galloc<double>(g, g->sumT, &rc);
+  g->duhat = galloc<double>(g, g->nh, &rc);
+  g->du = galloc<double>(g, g->sumA, &rc);
+  g->red = galloc<double>(g, 1024 + 8, &rc);
+  g->pwork = galloc<double>(g, 2 * g->sumP, &rc);
+  g->A = galloc<unsigned char>(g, g->sumAA * pb, &rc);
+  g->B = galloc<unsigned char>(g, g->sumAT * pb, &rc);
+  g->C = galloc<unsigned char>(g, g->sumAT * pb, &rc);
+  g->D = galloc<unsigned char>(g, g->sumTT * pb, &rc);
+  g->LU = galloc<unsigned char>(g, g->sumAA * pb, &rc);
+  g->XB = galloc<unsigned char>(g, g->sumAT * pb, &rc);
+  g->S = galloc<unsigned char>(g, g->sumTT * pb, &rc);
+  g->Pinv = galloc<unsigned char>(g, g->sumP * pb, &rc);
+  g->piv = galloc<int>(g, g->sumA, &rc);
+  g->status = galloc<int>(g, 2, &rc);
+  void* ubuf = Eim > 0 ? galloc<unsigned char>(g, uneven_dev_bytes(tb), &rc) : nullptr;
+  g->gm.n = g->nh;
+  g->gm.V = galloc<double>(g, (size_t)(GM_MAXM + 1) * std::max(g->nh, (size_t)1), &rc);
+  g->gm.Z = galloc<double>(g, (size_t)GM_MAXM * std::max(g->nh, (size_t)1), &rc);
+  g->gm.z32 = nullptr;
+  g->gm.partial = galloc<double>(g, (size_t)GM_NBLK * (GM_MAXM + 1), &rc);
+  g->gm.ticket = galloc<unsigned int>(g, 1, &rc);
+  g->gm.state = galloc<GmresState>(g, 1, &rc);
+  if (rc != FR_OK) {
+    destroy(g);
+    return rc;
+  }
+#define GUP(dst, src, cnt)                                                                              \
+  if ((cnt) > 0 && cudaMemcpyAsync(dst, src, (cnt) * sizeof(*(src)), cudaMemcpyHostToDevice, st) != cudaSuccess) { \
+    destroy(g);                                                                                         \
+    return FR_ERR_CUDA;                                                                                 \
+  }
+  GUP(g->ref, &href, 1);
+  GUP(g->deg, deg.data(), (size_t)E);
+  GUP(g->nbr, nbr.data(), nbr.size());
+  GUP(g->nbr_face, nbf.data(), nbf.size());
+  GUP(g->kind, kind.data(), kind.size());
+  GUP(g->tr_of, tr_of.data(), tr_of.size());
+  GUP(g->nfp, nfp.data(), nfp.size());
+  GUP(g->uoff, uoff.data(), uoff.size());
+  GUP(g->goff, goff.data(), goff.size());
+  GUP(g->toff, toff.data(), toff.size());
+  GUP(g->geo_sol, gsol.data(), gsol.size());
+  GUP(g->geo_face, gface.data(), gface.size());
+  GUP(g->implicit, impv.data(), impv.size());
+  GUP(g->dof_imp, dof_imp.data(), dof_imp.size());
+  GUP(g->tpts, tpts.data(), tpts.size());
+  GUP(g->sides, sides.data(), sides.size());
+  GUP(g->pside, pside.data(), pside.size());
+  GUP(g->poff, poff.data(), poff.size());
+  GUP(g->imp_idx, imp_idx.data(), imp_idx.size());
+  GUP(g->lto, lto.data(), lto.size());
+  GUP(g->nAk, nAk.data(), nAk.size());
+  GUP(g->nTk, nTk.data(), nTk.size());
+  GUP(g->gmap, gmap.data(), gmap.size());
+  GUP(g->ginv, ginv.data(), ginv.size());
+  GUP(g->offA, offA.data(), offA.size());
+  GUP(g->offB, offB.data(), offB.size());
+  GUP(g->offD, offD.data(), offD.size());
+  GUP(g->offr, offr.data(), offr.size());
+  GUP(g->offs, offs.data(), offs.size());
+#undef GUP
+  if (Eim > 0 && uneven_upload(tb, ubuf, &g->udev, st) != cudaSuccess) {
+    destroy(g);
+    return FR_ERR_CUDA;
+  }
+  if (cudaMemsetAsync(g->status, 0, 2 * sizeof(int), st) != cudaSuccess ||
+      cudaMemsetAsync(g->gm.ticket, 0, sizeof(unsigned), st) != cudaSuccess ||
+      cudaMemsetAsync(g->gview, 0, 4 * (size_t)E * GN * nv * sizeof(double), st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    destroy(g);
+    return FR_ERR_CUDA;
+  }
+  g->h_uoff = uoff;
+  g->h_toff = toff;
+  *out = g;
+  return FR_OK;
+}
+
+void query(const GenCtx* g, fr_ctx_info* info) {
+  info->nelem = g->E;
+  info->nimplicit = g->Eim;
+  info->p = g->pmax;
+  info->n = g->pmax + 1;
+  info->ns = info->n * info->n;
+  info->nv = g->nv;
+  info->nA = g->maxA;
+  info->nT = g->maxT;
+  info->ntrace = g->ntrace;
+  info->nstages = g->tableau == FR_TAB_SDIRK2 ? 2 : 1;
+  info->has_explicit = g->has_explicit ? 1 : 0;
+  info->workspace_bytes = g->bytes;
+  info->general = 1;
+  info->state_values = g->nstate;
+  info->trace_values = g->nh;
+}
+
+int nstages(const GenCtx* g) { return g->tableau == FR_TAB_SDIRK2 ? 2 : 1; }
+size_t state_values(const GenCtx* g) { return g->nstate; }
+
+int layout(const GenCtx* g, long long* elem_off, long long* trace_off, int* blk_nA, int* blk_nT) {
+  if (elem_off) memcpy(elem_off, g->h_uoff.data(), sizeof(long long) * (g->E + 1));
+  if (trace_off) memcpy(trace_off, g->h_toff.data(), sizeof(long long) * (g->ntrace + 1));
+  if (blk_nA && g->Eim) memcpy(blk_nA, g->h_nA.data(), sizeof(int) * g->Eim);
+  if (blk_nT && g->Eim) memcpy(blk_nT, g->h_nT.data(), sizeof(int) * g->Eim);
+  return FR_OK;
+}
+
+int solution_points(GenCtx* g, double* xy) {
+  GCK(cudaMemcpyAsync(xy, g->xy.data(), g->xy.size() * sizeof(double), cudaMemcpyHostToDevice, g->st));
+  GCK(cudaStreamSynchronize(g->st));
+  return FR_OK;
+}
+
+static GArgs gargs(GenCtx* g, const double* u, const double* uhat) {
+  GArgs a;
+  memset(&a, 0, sizeof(a));
+  a.E = g->E;
+  a.deg = g->deg;
+  a.uoff = g->uoff;
+  a.goff = g->goff;
+  a.geo_sol = g->geo_sol;
+  a.geo_face = g->geo_face;
+  a.nbr = g->nbr;
+  a.nbr_face = g->nbr_face;
+  a.kind = g->kind;
+  a.tr_of = g->tr_of;
+  a.nfp = g->nfp;
+  a.toff = g->toff;
+  a.implicit = g->implicit;
+  a.ref = g->ref;
+  a.U = u;
+  a.uhat = uhat;
+  a.Uf_all = g->Uf_all;
+  a.qf_all = g->qf_all;
+  a.Uf_out = g->Uf_all;
+  a.qf_out = g->qf_all;
+  for (int v = 0; v < 5; ++v) a.uinf[v] = g->uinf[v];
+  return a;
+}
+
+template <int PHYS, int MODE>
+static cudaError_t launch_gen_elem(GenCtx* g, const GArgs& a) {
+  constexpr int NV = Phys<PHYS>::NV;
+  const size_t smem = sizeof(GWork<NV>) * GEPB;
+  auto kern = k_gen_elem<PHYS, MODE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = (a.E + GEPB - 1) / GEPB;
+  if (grid == 0) return cudaSuccess;
+  (count_launch(), kern<<<grid, 32 * GEPB, smem, g->st>>>(g->pp, a));
+  return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t gen_elem(GenCtx* g, const GArgs& a) {
+  return g->pp.kind == 0 ? launch_gen_elem<0, MODE>(g, a) : launch_gen_elem<1, MODE>(g, a);
+}
+
+// R, the element trace rows (gview) and, if g_out, the assembled trace residual
+static int residual_into(GenCtx* g, const double* u, const double* uhat, double* R, double* g_out) {
+  const int ph = pbeg(g, 0);
+  GArgs a = gargs(g, u, uhat);
+  if (g->need_nbr) {
+    GCK(gen_elem<GM_UF>(g, a));
+    GCK(gen_elem<GM_QF>(g, a));
+  }
+  a.R = R;
+  a.gview = g->gview;
+  GCK(gen_elem<GM_RES>(g, a));
+  if (g_out && g->ntrace) {
+    (count_launch(), k_gen_trace_sum<<<nbw(g->ntrace), 256, 0, g->st>>>(g->ntrace, g->nv, g->toff, g->tpts, g->sides,
+                                                                        g->gview, g_out));
+    GCK(cudaGetLastError());
+  }
+  pend(g, ph);
+  return FR_OK;
+}
+
+int residual(GenCtx* g, const double* u, const double* uhat, double* R, double* gtrace) {
+  int rc = residual_into(g, u, uhat, R, gtrace);
+  if (rc) return rc;
+  GCK(cudaStreamSynchronize(g->st));
+  return FR_OK;
+}
+
+int initial_trace(GenCtx* g, const double* u, double* uhat) {
+  GArgs a = gargs(g, u, nullptr);
+  double* buf = g->gview;  // face-point states of every element, scratch
+  a.Uf_out = buf;
+  GCK(gen_elem<GM_UF>(g, a));
+  if (g->ntrace) {
+    (count_launch(), k_gen_initial_trace<<<nbw(g->ntrace), 256, 0, g->st>>>(g->ntrace, g->nv, g->toff, g->tpts,
+                                                                            g->sides, g->kind, buf, a, uhat));
+    GCK(cudaGetLastError());
+  }
+  GCK(cudaMemsetAsync(g->gview, 0, 4 * (size_t)g->E * GN * g->nv * sizeof(double), g->st));
+  GCK(cudaStreamSynchronize(g->st));
+  return FR_OK;
+}
+
+template <int PHYS, typename T>
+static cudaError_t launch_gen_jac(GenCtx* g, const GArgs& a, const JArgs& j) {
+  constexpr int NV = Phys<PHYS>::NV;
+  const size_t smem = sizeof(JWork<NV, T>);
+  auto kern = k_gen_jacobian<PHYS, T>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (j.Eim == 0) return cudaSuccess;
+  (count_launch(), kern<<<j.Eim, JT, smem, g->st>>>(g->pp, a, j));
+  return cudaGetLastError();
+}
+
+static int jacobian_blocks(GenCtx* g, const double* u, const double* uhat, double a_dt) {
+  if (g->Eim == 0) return FR_OK;
+  const int ph = pbeg(g, 1);
+  GArgs a = gargs(g, u, uhat);
+  JArgs j;
+  j.Eim = g->Eim;
+  j.imp_idx = g->imp_idx;
+  j.offA = g->offA;
+  j.offB = g->offB;
+  j.offD = g->offD;
+  j.lto = g->lto;
+  j.a_dt = a_dt;
+  j.A = g->A;
+  j.B = g->B;
+  j.C = g->C;
+  j.D = g->D;
+  cudaError_t e;
+  if (g->pb == 8)
+    e = g->pp.kind == 0 ? launch_gen_jac<0, double>(g, a, j) : launch_gen_jac<1, double>(g, a, j);
+  else
+    e = g->pp.kind == 0 ? launch_gen_jac<0, float>(g, a, j) : launch_gen_jac<1, float>(g, a, j);
+  GCK(e);
+  pend(g, ph);
+  g->lin_valid = true;
+  return FR_OK;
+}
+
+static int form_rhs(GenCtx* g, const double* u, const double* ustar, double a_dt) {
+  if (g->Eim == 0) return FR_OK;
+  (count_launch(), k_gen_form_rhs<<<nbw(g->Eim), 256, 0, g->st>>>(g->Eim, g->nv, g->imp_idx, g->deg, g->uoff, g->offr,
+                                                                   g->offs, g->nfp, g->lto, u, ustar, g->Rw, g->gview,
+                                                                   a_dt, g->r, g->s));
+  GCK(cudaGetLastError());
+  return FR_OK;
+}
+
+int local_jacobian(GenCtx* g, const double* u, const double* uhat, const double* ustar, double a_dt) {
+  int rc = residual_into(g, u, uhat, g->Rw, nullptr);
+  if (!rc) rc = form_rhs(g, u, ustar, a_dt);
+  if (!rc) rc = jacobian_blocks(g, u, uhat, a_dt);
+  if (rc) return rc;
+  GCK(cudaStreamSynchronize(g->st));
+  return FR_OK;
+}
+
+static int condense_impl(GenCtx* g) {
+  (count_launch(), k_gen_status_reset<<<1, 1, 0, g->st>>>(g->status));
+  GCK(cudaGetLastError());
+  if (g->Eim == 0) return FR_OK;
+  int ph = pbeg(g, 2);
+  GCK(launch_condense_uneven_dev(g->pb, g->udev, g->A, g->B, g->C, g->D, g->r, g->s, g->LU, g->piv, g->XB, g->xr,
+                                 g->S, g->te, g->status, g->st));
+  pend(g, ph);
+  ph = pbeg(g, 3);
+  if (g->ntrace) {
+    (count_launch(), k_gen_gather_sum<<<nb256(g->nh), 256, 0, g->st>>>(g->nh, g->ginv, g->te, g->tg, nullptr, 0));
+    GCK(cudaGetLastError());
+    if (g->pb == 8)
+      (count_launch(), k_gen_precond_build<double><<<nbw(g->ntrace), 256, 0, g->st>>>(
+           g->ntrace, g->nv, g->tpts, g->poff, g->pside, g->nTk, g->offD, (const double*)g->S, (double*)g->Pinv,
+           g->pwork, g->status));
+    else
+      (count_launch(), k_gen_precond_build<float><<<nbw(g->ntrace), 256, 0, g->st>>>(
+           g->ntrace, g->nv, g->tpts, g->poff, g->pside, g->nTk, g->offD, (const float*)g->S, (float*)g->Pinv,
+           g->pwork, g->status));
+    GCK(cudaGetLastError());
+  }
+  pend(g, ph);
+  return FR_OK;
+}
+
+static int check_status(GenCtx* g, const char* where) {
+  int hs[2];
+  GCK(cudaMemcpyAsync(hs, g->status, sizeof(hs), cudaMemcpyDeviceToHost, g->st));
+  GCK(cudaStreamSynchronize(g->st));
+  if (hs[0] & DEV_ERR_SINGULAR) {
+    GCK(cudaMemsetAsync(g->status, 0, sizeof(int), g->st));
+    // element blocks report their compact index, face preconditioner blocks -1 - trace
+    return err(g, FR_ERR_SINGULAR, where, hs[1] >= 0 ? hs[1] : -1);
+  }
+  return FR_OK;
+}
+
+int condense(GenCtx* g, int refine) {
+  if (refine != 0) return err(g, FR_ERR_UNSUPPORTED, "hfr_condense: refinement sweeps are not built for general meshes");
+  int rc = condense_impl(g);
+  if (rc) return rc;
+  return check_status(g, "hfr_condense: zero pivot");
+}
+
+// GMRES callbacks
+static void cb_matvec_g(void* c, const double* x, double* y, cudaStream_t s) {
+  GenCtx* g = (GenCtx*)c;
+  const int ph = pbeg(g, 8);
+  if (g->pb == 8)
+    (count_launch(), k_gen_matvec_elem<double><<<nbw(g->Eim), 256, 0, s>>>(g->Eim, g->nTk, g->offD, g->offs, g->gmap,
+                                                                           (const double*)g->S, x, g->yv, nullptr, 0));
+  else
+    (count_launch(), k_gen_matvec_elem<float><<<nbw(g->Eim), 256, 0, s>>>(g->Eim, g->nTk, g->offD, g->offs, g->gmap,
+                                                                          (const float*)g->S, x, g->yv, nullptr, 0));
+  (count_launch(), k_gen_gather_sum<<<nb256(g->nh), 256, 0, s>>>(g->nh, g->ginv, g->yv, y, nullptr, 0));
+  pend(g, ph);
+}
+static void cb_gmatvec_g(void* c, const GmresState* st, int j, const double* x, const float*, double* y, cudaStream_t s) {
+  GenCtx* g = (GenCtx*)c;
+  if (g->pb == 8)
+    (count_launch(), k_gen_matvec_elem<double><<<nbw(g->Eim), 256, 0, s>>>(g->Eim, g->nTk, g->offD, g->offs, g->gmap,
+                                                                           (const double*)g->S, x, g->yv, &st->kdone, j));
+  else
+    (count_launch(), k_gen_matvec_elem<float><<<nbw(g->Eim), 256, 0, s>>>(g->Eim, g->nTk, g->offD, g->offs, g->gmap,
+                                                                          (const float*)g->S, x, g->yv, &st->kdone, j));
+  (count_launch(), k_gen_gather_sum<<<nb256(g->nh), 256, 0, s>>>(g->nh, g->ginv, g->yv, y, &st->kdone, j));
+}
+static void cb_precond_g(void* c, const GmresState* st, int j, double* x, double* y, float* y32, cudaStream_t s) {
+  GenCtx* g = (GenCtx*)c;
+  if (g->pb == 8)
+    (count_launch(), k_gen_precond_apply<double><<<nbw(g->ntrace), 256, 0, s>>>(
+         g->ntrace, g->nv, g->tpts, g->toff, g->poff, (const double*)g->Pinv, x, y, &st->kdone, j,
+         j > 0 ? &st->inv_hn : nullptr, y32));
+  else
+    (count_launch(), k_gen_precond_apply<float><<<nbw(g->ntrace), 256, 0, s>>>(
+         g->ntrace, g->nv, g->tpts, g->toff, g->poff, (const float*)g->Pinv, x, y, &st->kdone, j,
+         j > 0 ? &st->inv_hn : nullptr, y32));
+}
+
+static int gmres_impl(GenCtx* g, double* duhat, double rtol, int maxit, int* iters, double* final_rel) {
+  if (g->ntrace == 0) {
+    if (iters) *iters = 0;
+    if (final_rel) *final_rel = 0.0;
+    return FR_OK;
+  }
+  GmresOps ops;
+  ops.ctx = g;
+  ops.matvec = cb_matvec_g;
+  ops.gated_matvec = cb_gmatvec_g;
+  ops.precond = cb_precond_g;
+  GmresResult res;
+  memset(&res, 0, sizeof(res));
+  const int ph = pbeg(g, 4);
+  const int grc = run_gmres(ops, g->gm, g->tg, duhat, rtol, g->restart, maxit, 4, &res, g->st);
+  pend(g, ph);
+  if (grc != 0) return err(g, FR_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+  GCK(cudaGetLastError());
+  if (iters) *iters = res.iterations;
+  if (final_rel) *final_rel = res.rel;
+  if (res.nan) return err(g, FR_ERR_DIVERGED, "hfr_trace_gmres: non-finite residual", -1, res.iterations);
+  if (!res.converged && res.rel > rtol)
+    return err(g, FR_ERR_NOT_CONVERGED, "hfr_trace_gmres: iteration limit", -1, res.iterations, res.rel);
+  return FR_OK;
+}
+
+int trace_gmres(GenCtx* g, double* duhat, double rtol, int maxit, int* iters, double* final_rel) {
+  return gmres_impl(g, duhat, rtol, maxit, iters, final_rel);
+}
+
+static int backsolve_impl(GenCtx* g, const double* duhat, double* du) {
+  if (g->Eim == 0) return FR_OK;
+  const int ph = pbeg(g, 5);
+  if (g->pb == 8)
+    (count_launch(), k_gen_backsolve<double><<<nbw(g->Eim), 256, 0, g->st>>>(
+         g->Eim, g->nAk, g->nTk, g->offB, g->offr, g->offs, g->gmap, (const double*)g->XB, g->xr, duhat, du));
+  else
+    (count_launch(), k_gen_backsolve<float><<<nbw(g->Eim), 256, 0, g->st>>>(
+         g->Eim, g->nAk, g->nTk, g->offB, g->offr, g->offs, g->gmap, (const float*)g->XB, g->xr, duhat, du));
+  GCK(cudaGetLastError());
+  pend(g, ph);
+  return FR_OK;
+}
+
+int backsolve(GenCtx* g, const double* duhat, double* du, int refine) {
+  if (refine != 0) return err(g, FR_ERR_UNSUPPORTED, "hfr_backsolve: refinement sweeps are not built for general meshes");
+  int rc = backsolve_impl(g, duhat, du);
+  if (rc) return rc;
+  GCK(cudaStreamSynchronize(g->st));
+  return FR_OK;
+}
+
+int export_array(GenCtx* g, int which, void* buf, size_t bytes, bool import) {
+  const size_t pb = g->pb;
+  void* arr = nullptr;
+  size_t need = 0;
+  switch (which) {
+    case 0: arr = g->A; need = g->sumAA * pb; break;
+    case 1: arr = g->B; need = g->sumAT * pb; break;
+    case 2: arr = g->C; need = g->sumAT * pb; break;
+    case 3: arr = g->D; need = g->sumTT * pb; break;
+    case 4: arr = g->S; need = g->sumTT * pb; break;
+    case 5: arr = g->XB; need = g->sumAT * pb; break;
+    case 6: arr = g->xr; need = g->sumA * 8; break;
+    case 7: arr = g->te; need = g->sumT * 8; break;
+    case 8: arr = g->r; need = g->sumA * 8; break;
+    case 9: arr = g->s; need = g->sumT * 8; break;
+    case 10: if (!import) { arr = g->tg; need = g->nh * 8; } break;
+    case 11: if (!import) { arr = g->Pinv; need = g->sumP * pb; } break;
+  }
+  if (!arr) return err(g, FR_ERR_INVALID_ARG, "hfr_export / hfr_import: unknown array");
+  if (import ? bytes != need : bytes < need)
+    return err(g, FR_ERR_INVALID_ARG, "hfr_export / hfr_import: buffer size");
+  if (import) {
+    GCK(cudaMemcpyAsync(arr, buf, need, cudaMemcpyDeviceToDevice, g->st));
+  } else {
+    GCK(cudaMemcpyAsync(buf, arr, need, cudaMemcpyDeviceToDevice, g->st));
+  }
+  GCK(cudaStreamSynchronize(g->st));
+  return FR_OK;
+}
+
+static int sumsq(GenCtx* g, const double* a, size_t na, const double* b, size_t nb, double* out) {
+  const int nbk = 256;
+  (count_launch(), k_gen_sumsq_part<<<nbk, 256, 0, g->st>>>(a, na, b, nb, g->red));
+  (count_launch(), k_gen_sumsq_final<<<1, 32, 0, g->st>>>(g->red, nbk, g->red + 1024));
+  GCK(cudaGetLastError());
+  GCK(cudaMemcpyAsync(out, g->red + 1024, sizeof(double), cudaMemcpyDeviceToHost, g->st));
+  GCK(cudaStreamSynchronize(g->st));
+  return FR_OK;
+}
+
+struct TabG {
+  int s;
+  double a[2][2], b[2], ah[3][3], bh[3];
+};
+static TabG tableau_g(int which) {
+  TabG t;
+  memset(&t, 0, sizeof(t));
+  if (which == FR_TAB_SDIRK2) {
+    const double gm = 1.0 - sqrt(2.0) / 2.0, dl = -2.0 * sqrt(2.0) / 3.0;
+    t.s = 2;
+    t.a[0][0] = gm;
+    t.a[1][0] = 1.0 - gm;
+    t.a[1][1] = gm;
+    t.b[0] = 1.0 - gm;
+    t.b[1] = gm;
+    t.ah[1][0] = gm;
+    t.ah[2][0] = dl;
+    t.ah[2][1] = 1.0 - dl;
+    t.bh[1] = 1.0 - gm;
+    t.bh[2] = gm;
+  } else {
+    t.s = 1;
+    t.a[0][0] = 1.0;
+    t.b[0] = 1.0;
+    t.ah[1][0] = 1.0;
+    t.bh[1] = 1.0;
+  }
+  return t;
+}
+
+int stage(GenCtx* g, int stage, double dt, const double* u_n, double* u_stage, double* uhat, double* R_hist,
+          double newton_tol, int newton_maxit, double gmres_rtol, int gmres_maxit, int refine, fr_stage_stats* stats) {
+  if (refine != 0) return err(g, FR_ERR_UNSUPPORTED, "imex_stage: refinement sweeps are not built for general meshes");
+  const TabG tb = tableau_g(g->tableau);
+  if (stage < 0 || stage > tb.s + 1) return err(g, FR_ERR_INVALID_ARG, "imex_stage: stage out of range");
+  const size_t tot = g->nstate;
+  cudaStream_t st = g->st;
+  if (stats) memset(stats, 0, sizeof(*stats));
+  if (stage == 0) {
+    int rc = residual_into(g, u_n, uhat, R_hist, nullptr);
+    if (rc) return rc;
+    GCK(cudaStreamSynchronize(st));
+    return FR_OK;
+  }
+  if (stage == tb.s + 1) {
+    StageCoefG sc;
+    memset(&sc, 0, sizeof(sc));
+    sc.nterm = tb.s + 1;
+    for (int jj = 0; jj <= tb.s; ++jj) {
+      sc.hi[jj] = jj;
+      sc.ci[jj] = jj >= 1 ? dt * tb.b[jj - 1] : 0.0;
+      sc.ce[jj] = dt * tb.bh[jj];
+    }
+    (count_launch(), k_gen_stage_combine<<<nb256(tot), 256, 0, st>>>(tot, g->dof_imp, u_n, R_hist, sc, u_stage));
+    GCK(cudaGetLastError());
+    GCK(cudaStreamSynchronize(st));
+    return FR_OK;
+  }
+  const int i = stage;
+  StageCoefG sc;
+  memset(&sc, 0, sizeof(sc));
+  sc.nterm = i;
+  for (int jj = 0; jj < i; ++jj) {
+    sc.hi[jj] = jj;
+    sc.ce[jj] = dt * tb.ah[i][jj];
+    sc.ci[jj] = jj >= 1 ? dt * tb.a[i - 1][jj - 1] : 0.0;
+  }
+  (count_launch(), k_gen_stage_combine<<<nb256(tot), 256, 0, st>>>(tot, g->dof_imp, u_n, R_hist, sc, u_stage));
+  GCK(cudaGetLastError());
+  GCK(cudaMemcpyAsync(g->Ustar, u_stage, tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  const double adt = dt * tb.a[i - 1][i - 1];
+  double norm0 = -1.0, normk = 0.0;
+  int it = 0, gtot = 0;
+  bool conv = false;
+  for (;; ++it) {
+    int rc = residual_into(g, u_stage, uhat, g->Rw, g->gw);
+    const int phn = pbeg(g, 6);
+    if (!rc) rc = form_rhs(g, u_stage, g->Ustar, adt);
+    double ss = 0.0;
+    if (!rc) rc = sumsq(g, g->r, g->sumA, g->gw, g->nh, &ss);
+    pend(g, phn);
+    if (rc) return rc;
+    normk = sqrt(ss);
+    if (!(normk == normk)) return err(g, FR_ERR_DIVERGED, "imex_stage: non-finite Newton residual", -1, it);
+    if (norm0 < 0) norm0 = normk;
+    if (normk <= newton_tol * norm0 || normk == 0.0) {
+      conv = true;
+      break;
+    }
+    if (it >= newton_maxit) break;
+    rc = jacobian_blocks(g, u_stage, uhat, adt);
+    if (!rc) rc = condense_impl(g);
+    if (!rc) rc = check_status(g, "imex_stage: zero pivot in condensation");
+    if (rc) return rc;
+    int its = 0;
+    double rel = 0.0;
+    rc = gmres_impl(g, g->duhat, gmres_rtol, gmres_maxit, &its, &rel);
+    gtot += its;
+    if (rc && rc != FR_ERR_NOT_CONVERGED) return rc;
+    rc = backsolve_impl(g, g->duhat, g->du);
+    if (rc) return rc;
+    const int phu = pbeg(g, 6);
+    if (g->Eim) {
+      (count_launch(), k_gen_apply_du<<<nbw(g->Eim), 256, 0, st>>>(g->Eim, g->nv, g->imp_idx, g->deg, g->uoff, g->offr,
+                                                                   g->du, u_stage));
+      GCK(cudaGetLastError());
+    }
+    if (g->nh) {
+      (count_launch(), k_gen_axpy<<<nb256(g->nh), 256, 0, st>>>(g->nh, 1.0, g->duhat, uhat));
+      GCK(cudaGetLastError());
+    }
+    pend(g, phu);
+  }
+  GCK(cudaMemcpyAsync(R_hist + (size_t)i * tot, g->Rw, tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  GCK(cudaStreamSynchronize(st));
+  if (stats) {
+    stats->newton_iterations = it;
+    stats->gmres_iterations = gtot;
+    stats->residual0 = norm0;
+    stats->residual = normk;
+    stats->converged = conv ? 1 : 0;
+  }
+  if (!conv) return err(g, FR_ERR_NOT_CONVERGED, "imex_stage: Newton iteration limit", -1, it, normk);
+  return FR_OK;
+}
+
+}  // namespace gen
+}  // namespace hfr

@@ -30,6 +30,13 @@ def sample_points(mesh, p: int) -> np.ndarray:
     return np.einsum("sk,ekd->esd", N, mesh.verts)
 
 
+def sample_points_mixed(mesh) -> list:
+    """Per-element physical coordinates ((p_e+1)^2, 2) of the Gauss-Legendre tensor nodes of a mesh
+    whose elements carry their own degree mesh.p[e]."""
+    return [sample_points(type("M", (), {"verts": mesh.verts[e:e + 1]}), int(mesh.p[e]))[0]
+            for e in range(mesh.nelem)]
+
+
 def gaussian_scalar(xy: np.ndarray, center=(0.5, 0.5), alpha=50.0) -> np.ndarray:
     """u = exp(-alpha |x - c|^2), shape (..., 1)."""
     r2 = (xy[..., 0] - center[0]) ** 2 + (xy[..., 1] - center[1]) ** 2
