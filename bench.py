@@ -326,7 +326,7 @@ def measure_pipe_peaks(pkg):
     return out
 
 
-def tight_agreement(pkg, torch, w, ctx_mixed, ctx_fp64, dev, tol=1e-11):
+def tight_agreement(pkg, torch, w, ctx_mixed, ctx_fp64, dev, tol=1e-11, refines=(0, 1)):
     """The precision error of the mixed path, separated from the Newton tolerance: both paths
     converge the same stage to a relative FP64 Newton residual of ``tol``; the mixed one with 0 and
     1 FP64 refinement sweeps of its local solves.  Differences relative to the stage increment
@@ -346,12 +346,104 @@ def tight_agreement(pkg, torch, w, ctx_mixed, ctx_fp64, dev, tol=1e-11):
     ref, st64 = solve(ctx_fp64, 0)
     inc = (ref - torch.tensor(w.u0, device=dev)).abs().max().item()
     out = {"newton_tol": tol, "gmres_rtol": kw["gmres_rtol"], "fp64_newton_iterations": st64["newton_iterations"]}
-    for refine in (0, 1):
+    for refine in refines:
         us, st = solve(ctx_mixed, refine)
         out[f"refine{refine}"] = {"max_rel_diff": (us - ref).abs().max().item() / inc,
                                   "newton_iterations": st["newton_iterations"],
                                   "gmres_iterations": st["gmres_iterations"], "converged": st["converged"]}
     assert graph == ctx_mixed.imex_stage_get_graph()
+    return out
+
+
+def boundary_layer_leg(pkg, torch, dev, l2buf, steps=3, warmup=2, peaks=None):
+    """The boundary-layer workload (400 x 500 quads, wall-normal growth 1.15 from 1e-5, p uniform
+    random in 2..5 per element, wall below and far field above, the 20% stiffest elements
+    implicit: 40 000 elements, 3.44 M implicit DOF) on the general-mesh path: SDIRK2 stage 1 with
+    the ERK partner on the 160 000 explicit elements, Newton to 1e-8, mixed precision against FP64.
+    Rooflines of its two largest phases from their algorithmic work: the uneven condensation
+    (2/3 nA^3 + 2 nA^2 (nT + 1) + 2 nT nA (nT + 1) flop per element, FP32 FMA roof) and the trace
+    GMRES (per iteration the S_k blocks, the gathered and scattered trace values and the
+    orthogonalisation, HBM roof)."""
+    from workloads import make_config
+
+    w = make_config("boundary_layer")
+    peaks = peaks or {}
+    out = {"workload": "boundary_layer: 2D Navier-Stokes Re=1.7e6 M=0.2, 400x500 quads, wall-normal growth 1.15 from "
+                       "1e-5 to isotropic 1e-2 (aspect ratio to 1e3), p uniform random in 2..5 per element (seed 2024), "
+                       "wall below, far field above, 20% stiffest elements implicit (40 000), SDIRK2 stage 1 with the "
+                       "ERK partner, Newton to 1e-8",
+           "implicit_dofs": w.dofs_implicit, "elements": w.mesh.nelem}
+    res = {}
+    for label, prec in (("mixed", pkg.FR_PREC_FP32), ("fp64", pkg.FR_PREC_FP64)):
+        ctx = pkg.Context(w.mesh, w.physics, precision=prec, tableau=pkg.FR_TAB_SDIRK2)
+        u_n = torch.tensor(ctx.pack_state(w.u0), device=dev)
+        uh0 = ctx.hfr_initial_trace(u_n)
+        R_hist = ctx.empty(3, *ctx.state_shape)
+        us = ctx.empty(*ctx.state_shape)
+        stream = torch.cuda.current_stream()
+
+        def run():
+            uh = uh0.clone()
+            ctx.imex_stage(0, w.dt, u_n, us, uh, R_hist, newton_tol=NEWTON_TOL)
+            return ctx.imex_stage(1, w.dt, u_n, us, uh, R_hist, newton_tol=NEWTON_TOL, newton_maxit=30,
+                                  gmres_rtol=GMRES_RTOL, gmres_maxit=20000)
+
+        for _ in range(warmup):
+            st = run()
+        torch.cuda.synchronize()
+        ctx.fr_profile_enable(True)
+        l0 = ctx.kernel_launches()
+        times = []
+        for _ in range(steps):
+            flush_l2(l2buf)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        prof = ctx.fr_profile_read()
+        ctx.fr_profile_enable(False)
+        res[label] = {"ms": float(np.mean(times)), "stats": st, "prof": prof,
+                      "launches": (ctx.kernel_launches() - l0) // steps, "u": (us - u_n).clone(),
+                      "nA": ctx.blk_nA.astype(np.float64), "nT": ctx.blk_nT.astype(np.float64),
+                      "nh": int(ctx.info.trace_values)}
+        ctx.close()
+    m, f = res["mixed"], res["fp64"]
+    inc = f["u"].abs().max().item()
+    nA, nT = m["nA"], m["nT"]
+    flop = float(np.sum(2.0 / 3.0 * nA ** 3 + 2 * nA ** 2 * (nT + 1) + 2 * nT * nA * (nT + 1)))
+    ms, cnt = m["prof"]["condense_factor"]
+    cond_a = flop / (ms / max(cnt, 1) * 1e-3) / 1e12
+    fp32 = peaks.get("fp32_tflops_measured") or NUM_SMS * FP32_PEAK_PER_SM_CLK * 2070e6 / 1e12
+    gms, gcnt = m["prof"]["gmres"]
+    # GMRES solves of one stage: one per Newton iteration (the profile counts every timed stage)
+    its = m["stats"]["gmres_iterations"] / max(m["stats"]["newton_iterations"], 1)
+    k_its = int(round(its))
+    alg = k_its * float(np.sum(nT * nT) * 4 + np.sum(nT) * 2 * 8) + sum((k + 2) * m["nh"] * 8 for k in range(1, k_its + 1))
+    g_a = alg / (gms / max(gcnt, 1) * 1e-3) / 1e9
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    out.update({
+        "value": w.dofs_implicit / (m["ms"] * 1e-3), "unit": "implicit-stage DOF/s", "ms_per_step": m["ms"],
+        "newton_iterations": m["stats"]["newton_iterations"], "gmres_iterations": m["stats"]["gmres_iterations"],
+        "gpu_launches": int(m["launches"]),
+        "fp64": {"value": w.dofs_implicit / (f["ms"] * 1e-3), "ms_per_step": f["ms"],
+                 "newton_iterations": f["stats"]["newton_iterations"], "gmres_iterations": f["stats"]["gmres_iterations"],
+                 "phases_ms_total": {k: round(v[0], 3) for k, v in f["prof"].items()}},
+        "mixed_over_fp64": f["ms"] / m["ms"],
+        "mixed_vs_fp64_max_rel_diff": (m["u"] - f["u"]).abs().max().item() / inc,
+        "phases_ms_total": {k: round(v[0], 3) for k, v in m["prof"].items()},
+        "rooflines": {
+            "condense": {"kernel": "k_condense_uneven<float>", "bound": "alu", "achieved": cond_a, "peak": fp32,
+                         "unit": "TFLOP/s", "frac": cond_a / fp32, "avg_launch_ms": ms / max(cnt, 1),
+                         "algorithmic_flop": flop},
+            "gmres": {"kernel": "multi-kernel GMRES cycle (k_gen_matvec_elem, k_gen_gather_sum, k_gen_precond_apply, k_cgs)",
+                      "bound": "hbm", "achieved": g_a, "peak": hbm, "unit": "GB/s", "frac": g_a / hbm,
+                      "avg_solve_ms": gms / max(gcnt, 1), "iterations_per_solve": k_its, "algorithmic_bytes": alg},
+        },
+        "l2": "flushed between timed steps (256 MB write)",
+    })
     return out
 
 
@@ -504,6 +596,9 @@ def main():
     ap.add_argument("--no-uneven", action="store_true", help="skip the uneven-degree condensation leg")
     ap.add_argument("--no-reuse", action="store_true", help="skip the Jacobian-reuse (imex_steps) leg")
     ap.add_argument("--no-tf32", action="store_true", help="skip the single-pass TF32 condensation leg")
+    ap.add_argument("--no-boundary-layer", action="store_true",
+                    help="skip the boundary-layer (mixed degree, walls, far field) leg")
+    ap.add_argument("--no-bf16", action="store_true", help="skip the BF16 trace-operator leg")
     ap.add_argument("--no-tight", action="store_true",
                     help="skip the tight-tolerance agreement leg of the mixed and FP64 stages")
     ap.add_argument("--no-autotune", action="store_true",
@@ -558,6 +653,13 @@ def main():
                                  cond_mode=pkg.FR_CONDENSE_TENSOR_TF32)
             except Exception as exc:  # reported, never fatal
                 tf32 = {"error": str(exc)}
+        bf16 = None
+        if not args.no_bf16:
+            try:  # the same stream stage with the trace operator in BF16 (FR_PREC_BF16)
+                bf16 = time_path(pkg, torch, w, pkg.FR_PREC_BF16, args.refine, args.steps, args.warmup, dev, l2buf,
+                                 args.jacobian, barrier, autotune=False)
+            except Exception as exc:  # reported, never fatal
+                bf16 = {"error": str(exc)}
         graph = None
         if args.jacobian == "every":
             graph = time_path(pkg, torch, w, pkg.FR_PREC_FP32, args.refine, args.steps, args.warmup, dev, l2buf,
@@ -645,11 +747,35 @@ def main():
                 "max_rel_diff_vs_fp64": (tf32["u"] - fp64["u"]).abs().max().item() / inc,
                 "note": "stream stage with FR_CONDENSE_TENSOR_TF32 (one TF32 product per term in the tensor-core "
                         "factorisation and products); compare stream_stage"}
+    if bf16 is not None:
+        if "error" in bf16:
+            line["bf16_trace_operator"] = bf16
+        else:
+            ms_b = replica_max([np.mean(bf16["ms"])], dist, dev)[0]
+            line["bf16_trace_operator"] = {
+                "value": job_value(world, dofs, ms_b), "ms_per_step": ms_b,
+                "newton_iterations": bf16["stats"]["newton_iterations"],
+                "gmres_iterations": bf16["stats"]["gmres_iterations"], "converged": bf16["stats"]["converged"],
+                "max_rel_diff_vs_fp64": (bf16["u"] - fp64["u"]).abs().max().item() / inc,
+                "phases_ms_total": {k: round(v[0], 3) for k, v in bf16["profile"].items()},
+                "note": "stream stage with FR_PREC_BF16: S_k stored in BF16 for the single-launch GMRES mat-vecs "
+                        "(FP32 accumulation), everything else as the mixed path; compare stream_stage"}
+            if not args.no_tight:
+                try:
+                    line["bf16_trace_operator"]["tight"] = tight_agreement(pkg, torch, w, bf16["ctx"], fp64["ctx"], dev,
+                                                                           refines=(0,))
+                except Exception as exc:
+                    line["bf16_trace_operator"]["tight"] = {"error": str(exc)}
     if not args.no_reuse:
         try:
             line["jacobian_reuse"] = jacobian_reuse(pkg, torch, mixed["ctx"], w, dev)
         except Exception as exc:  # reported, never fatal
             line["jacobian_reuse"] = {"error": str(exc)}
+    if not args.no_boundary_layer:
+        try:
+            line["boundary_layer"] = boundary_layer_leg(pkg, torch, dev, l2buf, peaks=peaks)
+        except Exception as exc:  # reported, never fatal
+            line["boundary_layer"] = {"error": str(exc)}
     if not args.no_uneven:
         try:
             line["uneven_condense"] = uneven_condense(pkg, torch, dev)

@@ -64,16 +64,33 @@ enum fr_status {
  * parameters theta = 1 / M^2 and nu = 1 / Re; p = 2..4; the velocity must not vanish at a trace
  * point (the hybridized stabilisation of Sec. 5.4 contains |v^|). */
 enum fr_physics { FR_PHYS_ADVDIFF = 0, FR_PHYS_NAVIER_STOKES = 1, FR_PHYS_EDAC = 2 };
-/* Precision of the element blocks, their LU and condensation, and the stored S^k. */
-enum fr_precision { FR_PREC_FP64 = 0, FR_PREC_FP32 = 1 };
+/* Precision of the element blocks, their factorisation and condensation, and the stored S^k
+ * (the Newton residual, right-hand sides and updates, the GMRES Hessenberg / Givens state and the
+ * trace solution stay FP64 in every mode; every mode stops on the same FP64 Newton test).
+ *   FR_PREC_FP64  everything in FP64 (LU with partial pivoting; FP64 trace operator)
+ *   FR_PREC_FP32  FP32 blocks; the condensation on the tensor cores in 3xTF32 (FP32-accurate) for
+ *                 the fixed shapes (see hfr_condense_set_mode), else FP32 FMA; FP32 S and Krylov basis
+ *   FR_PREC_TF32  as FP32 with the single-pass TF32 condensation (FR_CONDENSE_TENSOR_TF32); only
+ *                 for the tensor-core shapes (else FR_ERR_UNSUPPORTED at creation)
+ *   FR_PREC_BF16  as FP32, and S^k also stored in BF16 (rounded to nearest) for the mat-vecs of the
+ *                 single-launch GMRES cycle, accumulated in FP32: half the bytes of the memory-bound
+ *                 trace operator; the face-block preconditioner and the multi-kernel cycle keep FP32
+ *                 S; only for the single-launch shapes (else FR_ERR_UNSUPPORTED) */
+enum fr_precision { FR_PREC_FP64 = 0, FR_PREC_FP32 = 1, FR_PREC_TF32 = 2, FR_PREC_BF16 = 3 };
 enum fr_tableau { FR_TAB_BE = 0, FR_TAB_SDIRK2 = 1 };
 
 typedef struct fr_ctx fr_ctx;
 
 /* Boundary tags of fr_mesh_desc.bc (where nbr < 0). */
 enum fr_boundary { FR_BC_WALL = 1, FR_BC_FARFIELD = 2 };
-/* Element types of fr_mesh_desc.elem_type. */
-enum fr_elem_type { FR_ELEM_QUAD = 0 };
+/* Element types of fr_mesh_desc.elem_type.  FR_ELEM_HEX (the paper's 3D runs, Sec. 5.3; Navier-Stokes
+ * only, one degree p = 1..3, general path): verts nelem x 8 x 3 with corner k = a + 2b + 4c at
+ * (2a-1, 2b-1, 2c-1); nbr, nbr_face, face_of, bc nelem x 6 with faces 0/1 xi = -1/+1, 2/3 eta,
+ * 4/5 zeta; solution point pt = a + n b + n^2 c; face point m = i + n j along the lower then the
+ * higher tangential axis, met in the same order from both sides of a face (conforming meshes of
+ * one orientation); u = (rho, rho v_x, rho v_y, rho v_z, E), nv = 5.  Its element blocks are
+ * stored column-major (hfr_export / hfr_import: A^T, B^T, C^T, D^T row-major). */
+enum fr_elem_type { FR_ELEM_QUAD = 0, FR_ELEM_HEX = 1 };
 
 /* Mesh description (all HOST arrays, copied by fr_ctx_create).
  * A mesh whose elements all share one degree and that has no boundary face runs the uniform
@@ -89,10 +106,10 @@ enum fr_elem_type { FR_ELEM_QUAD = 0 };
 typedef struct {
   int nelem;
   int p;                         /* polynomial degree 1..5 (all elements, unless p_elem is given) */
-  const double* verts;           /* nelem x 4 x 2 corner coordinates, corner k = a + 2b at (2a-1, 2b-1) */
-  const int* nbr;                /* nelem x 4 neighbour element across each local face, -1 on a boundary */
-  const int* nbr_face;           /* nelem x 4 neighbour's local face */
-  const int* face_of;            /* nelem x 4 global face id (first-appearance numbering), < 4 nelem */
+  const double* verts;           /* nelem x 4 x 2 corner coordinates, corner k = a + 2b at (2a-1, 2b-1) (hex: see fr_elem_type) */
+  const int* nbr;                /* nelem x 4 (hex: 6) neighbour element across each local face, -1 on a boundary */
+  const int* nbr_face;           /* nelem x 4 (6) neighbour's local face */
+  const int* face_of;            /* nelem x 4 (6) global face id (first-appearance numbering), < 4 (6) nelem */
   const unsigned char* implicit; /* nelem: 1 = hybridized implicit, 0 = explicit FR */
   const int* p_elem;             /* nullable: nelem degrees 1..5 (general path: advection-diffusion, Navier-Stokes) */
   const int* bc;                 /* nullable: nelem x 4 fr_boundary tags where nbr < 0 (required when there are) */
@@ -310,9 +327,12 @@ int imex_steps(fr_ctx* ctx, int nsteps, double dt, double* u, double* uhat, doub
  * ints of scratch.  The CTAs walk the elements from the most to the least expensive (shared-memory
  * Gauss-Jordan with partial pivoting, S = D - C X_B, t = s - C x_r).  A stream-ordered work
  * buffer of 28 bytes per element is allocated and freed inside; the call synchronises the stream.
- * Returns FR_OK, FR_ERR_SINGULAR (*failed_element: an element with a zero pivot),
- * FR_ERR_INVALID_ARG (null array, bad precision, a shape whose working set exceeds the 227 KB of
- * shared memory: FP32 up to (144, 96), FP64 up to (100, 80)) or FR_ERR_CUDA. */
+ * Shapes whose working set exceeds the 227 KB of shared memory (FP32 beyond (144, 96), FP64
+ * beyond about (100, 80)) are condensed by a global-memory kernel in the same call (LU with
+ * partial pivoting of A in place, one CTA per element; LU then holds the LU factors and piv the
+ * row interchanges instead of the inverse).  Returns FR_OK, FR_ERR_SINGULAR (*failed_element: an
+ * element with a zero pivot), FR_ERR_INVALID_ARG (null array, bad precision, nA or nT < 1, nT >
+ * 16384) or FR_ERR_CUDA. */
 int hfr_condense_uneven(int nelem, const int* nA, const int* nT, int precision, const void* A, const void* B,
                         const void* C, const void* D, const double* r, const double* s, void* LU, int* piv, void* XB,
                         double* xr, void* S, double* t, int* status, void* stream, int* failed_element);

@@ -26,12 +26,12 @@ __all__ = [
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libhfr.so")
 
-FR_PREC_FP64, FR_PREC_FP32 = 0, 1
+FR_PREC_FP64, FR_PREC_FP32, FR_PREC_TF32, FR_PREC_BF16 = 0, 1, 2, 3
 FR_TAB_BE, FR_TAB_SDIRK2 = 0, 1
 FR_PHYS_ADVDIFF, FR_PHYS_NAVIER_STOKES, FR_PHYS_EDAC = 0, 1, 2
 FR_GMRES_MULTI, FR_GMRES_FUSED = 0, 1
 FR_BC_WALL, FR_BC_FARFIELD = 1, 2
-FR_ELEM_QUAD = 0
+FR_ELEM_QUAD, FR_ELEM_HEX = 0, 1
 FR_JAC_EVERY_NEWTON, FR_JAC_ONCE_PER_STAGE, FR_JAC_KEEP = 0, 1, 2
 FR_CONDENSE_FMA, FR_CONDENSE_TENSOR_PRODUCTS, FR_CONDENSE_TENSOR, FR_CONDENSE_TENSOR_TF32 = 0, 1, 2, 3
 (FR_OK, FR_ERR_INVALID_ARG, FR_ERR_CUDA, FR_ERR_SINGULAR, FR_ERR_NOT_CONVERGED, FR_ERR_DIVERGED, FR_ERR_TIMEOUT,
@@ -391,10 +391,11 @@ class Context:
         degs = np.asarray(mesh.p).reshape(-1)
         p = int(degs[0])
         E = int(mesh.verts.shape[0])
-        general = bool(np.any(degs != p)) or bool(np.any(np.asarray(mesh.nbr) < 0))
+        self.hex = int(getattr(mesh, "dim", 2)) == 3
+        general = bool(np.any(degs != p)) or bool(np.any(np.asarray(mesh.nbr) < 0)) or self.hex
         self._deg = np.ascontiguousarray(np.broadcast_to(degs, (E,)), dtype=np.int32)
         bc = getattr(mesh, "bc", None)
-        self._bc = np.ascontiguousarray(bc if bc is not None else np.zeros((E, 4)), dtype=np.int32)
+        self._bc = np.ascontiguousarray(bc if bc is not None else np.zeros_like(np.asarray(mesh.nbr)), dtype=np.int32)
         self._verts = np.ascontiguousarray(mesh.verts, dtype=np.float64)
         self._nbr = np.ascontiguousarray(mesh.nbr, dtype=np.int32)
         self._nbf = np.ascontiguousarray(mesh.nbr_face, dtype=np.int32)
@@ -409,7 +410,7 @@ class Context:
             self._imp.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)),
             self._deg.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) if general else None,
             self._bc.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) if general else None,
-            0,
+            FR_ELEM_HEX if self.hex else FR_ELEM_QUAD,
         )
         cfg = fr_config()
         if physics["kind"] == "advdiff":
@@ -510,18 +511,22 @@ class Context:
         shapes = {"A": (na, na), "B": (na, nt), "C": (nt, na), "D": (nt, nt), "S": (nt, nt), "XB": (na, nt),
                   "xr": (na, None), "r": (na, None), "t_k": (nt, None), "s": (nt, None)}[which]
         out, o = [], 0
+        # hexahedra keep A, B, C, D column-major (S and X_B, written by the condensation, row-major)
+        colmajor = self.hex and which in ("A", "B", "C", "D")
         for k in range(self.info.nimplicit):
             r = int(shapes[0][k])
             c = 1 if shapes[1] is None else int(shapes[1][k])
             blk = flat[o:o + r * c]
-            out.append(blk if shapes[1] is None else blk.reshape(r, c))
+            if shapes[1] is not None:
+                blk = blk.reshape(c, r).T if colmajor else blk.reshape(r, c)
+            out.append(blk)
             o += r * c
         return out
 
     # -------------------------------------------------------------------- ABI calls
     def solution_points(self):
         if self.general:
-            xy = self.empty(2 * int(self.info.state_values) // self.info.nv)
+            xy = self.empty((3 if self.hex else 2) * int(self.info.state_values) // self.info.nv)
         else:
             xy = self.empty(self.info.nelem, self.info.ns, 2)
         self._check(self.lib.fr_solution_points(self.h, _ptr(xy)))

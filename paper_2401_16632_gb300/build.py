@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhfr.so")
-UNITS = ["hfr_residual", "hfr_jacobian", "hfr_condense", "hfr_linalg", "hfr_krylov", "hfr_gmres_fused", "hfr_api", "hfr_noalloc", "hfr_layout", "hfr_peaks", "hfr_general"]
+UNITS = ["hfr_residual", "hfr_jacobian", "hfr_condense", "hfr_linalg", "hfr_krylov", "hfr_gmres_fused", "hfr_api", "hfr_noalloc", "hfr_layout", "hfr_peaks", "hfr_general", "hfr_hex"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 

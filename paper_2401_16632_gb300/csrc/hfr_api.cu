@@ -5,6 +5,7 @@
 // classification and trace numbering, workspace management, and the Newton / IMEX stage
 // driver (Pereira & Vermeire, arXiv 2401.16632, Sec. 3.1 and Algorithm 1).  Every step of the
 // numerical path runs in the CUDA kernels of this library.
+#include <cuda_bf16.h>
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -69,6 +70,7 @@ struct fr_ctx {
   // Newton system
   double *r = nullptr, *s = nullptr, *xr = nullptr, *te = nullptr, *tg = nullptr, *Pinv = nullptr;
   void *A = nullptr, *B = nullptr, *C = nullptr, *D = nullptr, *LU = nullptr, *XB = nullptr, *S = nullptr;
+  unsigned short* S16 = nullptr;  // FR_PREC_BF16: the trace operator in BF16 for the GMRES mat-vec
   int* piv = nullptr;
   int* status = nullptr;  // [0] bits, [1] first element
   // Krylov
@@ -393,7 +395,7 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, const fr_config* cfg, voi
   *out = nullptr;
   if (mesh->nelem <= 0 || !mesh->verts || !mesh->nbr || !mesh->nbr_face || !mesh->face_of || !mesh->implicit)
     return FR_ERR_INVALID_ARG;
-  if (mesh->elem_type != FR_ELEM_QUAD) return FR_ERR_UNSUPPORTED;
+  if (mesh->elem_type != FR_ELEM_QUAD && mesh->elem_type != FR_ELEM_HEX) return FR_ERR_UNSUPPORTED;
   if (hfr::gen::mesh_is_general(mesh)) {
     fr_ctx* ctx = new fr_ctx();
     memset(&ctx->err, 0, sizeof(ctx->err));
@@ -427,7 +429,7 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, const fr_config* cfg, voi
   if (cfg->physics == FR_PHYS_ADVDIFF && mesh->p > 3) return FR_ERR_UNSUPPORTED;
   if (cfg->physics == FR_PHYS_NAVIER_STOKES && mesh->p < 2) return FR_ERR_UNSUPPORTED;
   if (cfg->physics == FR_PHYS_EDAC && (mesh->p < 2 || mesh->p > 4 || !(cfg->theta > 0.0))) return FR_ERR_UNSUPPORTED;
-  if (cfg->precision != FR_PREC_FP64 && cfg->precision != FR_PREC_FP32) return FR_ERR_INVALID_ARG;
+  if (cfg->precision < FR_PREC_FP64 || cfg->precision > FR_PREC_BF16) return FR_ERR_INVALID_ARG;
   fr_ctx* ctx = new fr_ctx();
   memset(&ctx->err, 0, sizeof(ctx->err));
   ctx->stream = (cudaStream_t)stream;
@@ -439,6 +441,7 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, const fr_config* cfg, voi
   ctx->nA = ctx->ns * ctx->nv;
   ctx->nT = 4 * ctx->n * ctx->nv;
   ctx->prec_bytes = cfg->precision == FR_PREC_FP64 ? 8 : 4;
+  const bool want_bf16 = cfg->precision == FR_PREC_BF16, want_tf32 = cfg->precision == FR_PREC_TF32;
   ctx->tableau = cfg->tableau;
   ctx->restart = cfg->gmres_restart > 0 ? std::min(cfg->gmres_restart, GM_MAXM) : 30;
   memset(&ctx->pp, 0, sizeof(ctx->pp));
@@ -589,6 +592,12 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, const fr_config* cfg, voi
     ctx->gm_fused_grid = fused_gmres_grid(ctx->prec_bytes, nT, n * nv);
     ctx->gm_mode = ctx->gm_fused_grid > 0 ? 1 : 0;
     ctx->cond_mode = condense_tc_available(ctx->prec_bytes, nA, nT);
+    if ((want_bf16 && ctx->gm_fused_grid <= 0) || (want_tf32 && ctx->cond_mode < FR_CONDENSE_TENSOR)) {
+      fr_ctx_destroy(ctx);
+      return FR_ERR_UNSUPPORTED;  // the BF16 operator and single-pass TF32 exist for the fixed shapes only
+    }
+    if (want_tf32) ctx->cond_mode = FR_CONDENSE_TENSOR_TF32;
+    if (want_bf16) ctx->S16 = dalloc<unsigned short>(ctx, (size_t)Eim * nT * nT, &rc);
     const size_t np = std::max((size_t)GM_NBLK * (GM_MAXM + 1), fused_partial_doubles(std::max(nsm, 1)));
     ctx->gm.partial = dalloc<double>(ctx, np, &rc);
     ctx->gm_bar = dalloc<unsigned>(ctx, 64, &rc);
@@ -879,6 +888,24 @@ static int check_status(fr_ctx* ctx, const char* where) {
   return FR_OK;
 }
 
+// the trace operator in BF16 (round to nearest even) for the GMRES mat-vec of FR_PREC_BF16
+__global__ void k_s_to_bf16(size_t n, const float* __restrict__ S, unsigned short* __restrict__ S16) {
+  const size_t i = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (i + 3 < n) {
+    const float4 v = *reinterpret_cast<const float4*>(S + i);
+    const __nv_bfloat16 b0 = __float2bfloat16_rn(v.x), b1 = __float2bfloat16_rn(v.y), b2 = __float2bfloat16_rn(v.z),
+                        b3 = __float2bfloat16_rn(v.w);
+    ushort4 o;
+    o.x = __bfloat16_as_ushort(b0);
+    o.y = __bfloat16_as_ushort(b1);
+    o.z = __bfloat16_as_ushort(b2);
+    o.w = __bfloat16_as_ushort(b3);
+    *reinterpret_cast<ushort4*>(S16 + i) = o;
+  } else {
+    for (size_t j = i; j < n; ++j) S16[j] = __bfloat16_as_ushort(__float2bfloat16_rn(S[j]));
+  }
+}
+
 __global__ void k_status_reset(int* status) {
   status[0] = 0;
   status[1] = 0x7fffffff;
@@ -913,6 +940,11 @@ static int condense_impl(fr_ctx* ctx, int refine) {
   prof_end(ctx, ph);
   ph = prof_begin(ctx, PH_CPROD);
   CK(launch_condense_part(ctx->prec_bytes, c, ctx->stream, 1));
+  if (ctx->S16) {
+    const size_t ns16 = (size_t)ctx->Eim * ctx->nT * ctx->nT;
+    (hfr::count_launch(), k_s_to_bf16<<<nblk((ns16 + 3) / 4), 256, 0, ctx->stream>>>(ns16, (const float*)ctx->S, ctx->S16));
+    CK(cudaGetLastError());
+  }
   prof_end(ctx, ph);
   if (refine > 0 && ctx->lin_U) {
     // FP64 refinement of x_r against the exact linearisation (used by the back-substitution)
@@ -1009,8 +1041,9 @@ static int gmres_impl(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* i
     fa.nT = ctx->nT;
     fa.sides = ctx->sides_c;
     fa.tr_of_c = ctx->tr_of_c;
-    fa.S = ctx->S;
-    fa.S_bytes = (size_t)ctx->Eim * ctx->nT * ctx->nT * ctx->prec_bytes;
+    fa.S = ctx->S16 ? (const void*)ctx->S16 : ctx->S;
+    fa.s_bf16 = ctx->S16 ? 1 : 0;
+    fa.S_bytes = (size_t)ctx->Eim * ctx->nT * ctx->nT * (ctx->S16 ? 2 : ctx->prec_bytes);
     fa.Pinv = ctx->Pinv;
     fa.t = ctx->tg;
     fa.x = duhat;
@@ -1634,8 +1667,9 @@ static int stage_graph_capture(fr_ctx* ctx, const StageGraphKey& key) {
     fa.nT = ctx->nT;
     fa.sides = ctx->sides_c;
     fa.tr_of_c = ctx->tr_of_c;
-    fa.S = ctx->S;
-    fa.S_bytes = (size_t)ctx->Eim * ctx->nT * ctx->nT * ctx->prec_bytes;
+    fa.S = ctx->S16 ? (const void*)ctx->S16 : ctx->S;
+    fa.s_bf16 = ctx->S16 ? 1 : 0;
+    fa.S_bytes = (size_t)ctx->Eim * ctx->nT * ctx->nT * (ctx->S16 ? 2 : ctx->prec_bytes);
     fa.Pinv = ctx->Pinv;
     fa.t = ctx->tg;
     fa.x = ctx->duhat;

@@ -27,7 +27,7 @@ struct RefOps {
 };
 
 struct PhysParams {
-  int kind;  // 0 advection-diffusion, 1 Navier-Stokes 2D, 2 EDAC 2D
+  int kind;  // 0 advection-diffusion, 1 Navier-Stokes 2D, 2 EDAC 2D, 3 Navier-Stokes 3D
   double beta[3];
   double nu;
   double gamma, mu, Pr;
@@ -35,7 +35,9 @@ struct PhysParams {
   double theta;  // EDAC: 1 / M^2 of the artificial Mach number
 };
 // viscous terms present (advection-diffusion and EDAC: nu; Navier-Stokes: mu)
-__host__ __device__ inline bool phys_viscous(const PhysParams& pp) { return pp.kind == 1 ? pp.mu != 0.0 : pp.nu != 0.0; }
+__host__ __device__ inline bool phys_viscous(const PhysParams& pp) {
+  return (pp.kind == 1 || pp.kind == 3) ? pp.mu != 0.0 : pp.nu != 0.0;
+}
 
 // face kinds of an element face
 enum { FK_FR = 0, FK_TRACE = 1, FK_IMEX = 2 };
@@ -113,7 +115,7 @@ __host__ __device__ inline PhysConst<R> phys_const(const PhysParams& pp) {
   c.gamma = R(pp.gamma);
   c.gm1 = R(pp.gamma - 1.0);
   c.mu = R(pp.mu);
-  c.kappa = pp.kind == 1 ? R(pp.mu * pp.gamma / ((pp.gamma - 1.0) * pp.Pr)) : R(0);
+  c.kappa = (pp.kind == 1 || pp.kind == 3) ? R(pp.mu * pp.gamma / ((pp.gamma - 1.0) * pp.Pr)) : R(0);
   c.mu_lref = R(pp.mu / pp.lref);
   c.theta = R(pp.theta);
   return c;

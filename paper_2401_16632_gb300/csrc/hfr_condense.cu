@@ -1972,6 +1972,7 @@ struct UnevenArgs {
   void* S;
   double* t;
   int* status;
+  int colmajor = 0;  // A, B, C, D stored column-major (global-memory kernel only)
 };
 
 template <typename T>
@@ -2064,8 +2065,11 @@ __global__ void __launch_bounds__(GLB_THREADS) k_condense_global(const __grid_co
     int* piv = a.piv + o[3];
     const double* sv = a.s + o[4];
     double* t = a.t + o[4];
-    for (size_t i = tid; i < (size_t)nA * nA; i += GLB_THREADS) L[i] = A[i];
-    for (size_t i = tid; i < (size_t)nA * nT; i += GLB_THREADS) X[i] = B[i];
+    const bool cm = a.colmajor != 0;
+    for (size_t i = tid; i < (size_t)nA * nA; i += GLB_THREADS)
+      L[i] = cm ? A[(i % nA) * nA + i / nA] : A[i];
+    for (size_t i = tid; i < (size_t)nA * nT; i += GLB_THREADS)
+      X[i] = cm ? B[(i % nT) * nA + i / nT] : B[i];
     for (int i = tid; i < nA; i += GLB_THREADS) xr[i] = r[i];
     if (tid == 0) s_bad = 0;
     __syncthreads();
@@ -2173,13 +2177,15 @@ __global__ void __launch_bounds__(GLB_THREADS) k_condense_global(const __grid_co
     // S = D - C X_B, t = s - C x_r
     for (int e = tid; e < nT * (nT + 1); e += GLB_THREADS) {
       const int row = e / (nT + 1), col = e % (nT + 1);
-      const T* Cr = C + (size_t)row * nA;
+      // C[row][c]: row-major C + row nA + c, column-major C + c nT + row
+      const size_t cs = cm ? (size_t)nT : 1, c0 = cm ? (size_t)row : (size_t)row * nA;
       double acc = 0.0;
       if (col < nT) {
-        for (int c = 0; c < nA; ++c) acc += (double)Cr[c] * (double)X[(size_t)c * nT + col];
-        S[(size_t)row * nT + col] = T((double)D[(size_t)row * nT + col] - acc);
+        for (int c = 0; c < nA; ++c) acc += (double)C[c0 + c * cs] * (double)X[(size_t)c * nT + col];
+        const double d = cm ? (double)D[(size_t)col * nT + row] : (double)D[(size_t)row * nT + col];
+        S[(size_t)row * nT + col] = T(d - acc);
       } else {
-        for (int c = 0; c < nA; ++c) acc += (double)Cr[c] * xr[c];
+        for (int c = 0; c < nA; ++c) acc += (double)C[c0 + c * cs] * xr[c];
         t[row] = sv[row] - acc;
       }
     }
@@ -2291,7 +2297,9 @@ cudaError_t uneven_upload(const UnevenTables& tb, void* dbuf, UnevenDev* dv, cud
 cudaError_t launch_condense_uneven_dev(int prec_bytes, const UnevenDev& dv, const void* A, const void* B, const void* C,
                                        const void* D, const double* r, const double* s, void* LU, int* piv, void* XB,
                                        double* xr, void* S, double* t, int* status, cudaStream_t st) {
-  UnevenArgs ua{dv.nb, dv.bundle, dv.order, dv.shape, dv.off, A, B, C, D, r, s, LU, piv, XB, xr, S, t, status};
+  UnevenArgs ua{dv.nb, dv.bundle, dv.order, dv.shape, dv.off, A, B, C, D, r, s, LU, piv, XB, xr, S, t, status,
+                dv.colmajor};
+  if (dv.colmajor && dv.nb > 0) return cudaErrorInvalidValue;  // column-major blocks: global kernel only
   int dev = 0, nsm = 0, occ = 0;
   cudaError_t e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -2604,7 +2612,7 @@ static cudaError_t cond_reg(const CondArgs& a, cudaStream_t st) {
 template <typename T>
 static cudaError_t cond_global_uniform(const CondArgs& a, cudaStream_t st) {
   UnevenArgs ua{0, nullptr, nullptr, nullptr, nullptr, a.A, a.B, a.C, a.D, a.r, a.s, a.LU, a.piv, a.XB, a.xr, a.S, a.t,
-                a.status};
+                a.status, 0};
   int dev = 0, nsm = 0;
   cudaError_t e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;

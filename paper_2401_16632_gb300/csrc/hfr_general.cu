@@ -38,28 +38,10 @@
 #include <algorithm>
 #include <vector>
 
-#include "hfr_general.h"
+#include "hfr_general_internal.h"
 
 namespace hfr {
 namespace gen {
-
-constexpr int GN = HFR_MAXN;  // points per line / face (p <= 5)
-constexpr int GNS = GN * GN;
-constexpr int GF = 4 * GN;
-constexpr int GEPB = 4;       // elements (warps) per CTA of the residual passes
-constexpr int JT = 256;       // threads of the block kernel
-constexpr int JW = JT / 32;
-enum { FK_WALL = 3, FK_FAR = 4 };
-enum { BC_WALL = 1, BC_FAR = 2 };
-
-// Reference operators of every degree, and the face interpolation / projection of every pair
-// (n nodes, m >= n face points).  Built on the host, read from global memory.
-struct GenRef {
-  double M[GN + 1][GN][GN];
-  double lm[GN + 1][GN], lp[GN + 1][GN], dgL[GN + 1][GN], dgR[GN + 1][GN], w[GN + 1][GN];
-  double T[GN + 1][GN + 1][GN][GN];  // [n][m][q][b] = l_b(s_q): node b of n -> face point q of m
-  double P[GN + 1][GN + 1][GN][GN];  // [n][m][b][q] = w_q l_b(s_q) / w_b: face points -> nodes
-};
 
 static void build_genref(GenRef& R) {
   memset(&R, 0, sizeof(R));
@@ -104,28 +86,6 @@ static void build_genref(GenRef& R) {
     }
   }
 }
-
-struct GArgs {
-  int E;
-  const int* deg;         // E: points per line n_e
-  const long long* uoff;  // E: state offset
-  const long long* goff;  // E: first solution point of the element in geo_sol
-  const double* geo_sol;  // [point][5] = {1/J, S00, S01, S10, S11}
-  const double* geo_face; // [(4 e + f) GN + q][3] = {J_f, n0, n1}
-  const int *nbr, *nbr_face, *kind, *tr_of, *nfp;  // 4 E
-  const long long* toff;  // trace value offsets
-  const unsigned char* implicit;
-  const GenRef* ref;
-  const double* U;
-  const double* uhat;
-  const double* Uf_all;   // face-point states of every element (FR / IMEX neighbours)
-  const double* qf_all;   // face-point gradients
-  double* Uf_out;
-  double* qf_out;
-  double* R;
-  double* gview;          // element trace rows w_q J_f (row)_q at face points, zero off traces
-  double uinf[5];
-};
 
 __device__ __forceinline__ int gline(int r, int m, int c, int n) { return r == 0 ? (c + n * m) : (m + n * c); }
 
@@ -193,7 +153,6 @@ __device__ __forceinline__ void gface_flux(const PhysConst<R>& pc, bool visc, in
 }
 
 // ------------------------------------------------------------------------ residual passes
-enum { GM_UF = 0, GM_QF = 1, GM_RES = 2 };
 
 template <int NV>
 struct GWork {
@@ -407,15 +366,16 @@ __global__ void __launch_bounds__(32 * GEPB) k_gen_elem(const __grid_constant__ 
 }
 
 // trace residual: g[t] = both sides' rows
-__global__ void k_gen_trace_sum(int ntrace, int nv, const long long* __restrict__ toff, const int* __restrict__ tpts,
-                                const int* __restrict__ sides, const double* __restrict__ gview, double* __restrict__ g) {
+__global__ void k_gen_trace_sum(int ntrace, int nv, int nface, int fs, const long long* __restrict__ toff,
+                                const int* __restrict__ tpts, const int* __restrict__ sides,
+                                const double* __restrict__ gview, double* __restrict__ g) {
   const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (t >= ntrace) return;
   const int cnt = tpts[t] * nv;
   const int e0 = sides[4 * t], f0 = sides[4 * t + 1], e1 = sides[4 * t + 2], f1 = sides[4 * t + 3];
   for (int i = lane; i < cnt; i += 32) {
-    double s = gview[(size_t)(4 * e0 + f0) * GN * nv + i];
-    if (e1 >= 0) s += gview[(size_t)(4 * e1 + f1) * GN * nv + i];
+    double s = gview[(size_t)(nface * e0 + f0) * fs * nv + i];
+    if (e1 >= 0) s += gview[(size_t)(nface * e1 + f1) * fs * nv + i];
     g[toff[t] + i] = s;
   }
 }
@@ -425,21 +385,22 @@ __global__ void k_gen_trace_sum(int ntrace, int nv, const long long* __restrict_
 __global__ void k_gen_initial_trace(int ntrace, int nv, const long long* __restrict__ toff, const int* __restrict__ tpts,
                                     const int* __restrict__ sides, const int* __restrict__ kind,
                                     const double* __restrict__ Uf, GArgs a, double* __restrict__ uhat) {
+  const int nface = a.nface, fs = a.fs;
   const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (t >= ntrace) return;
   const int cnt = tpts[t] * nv;
   const int e0 = sides[4 * t], f0 = sides[4 * t + 1], e1 = sides[4 * t + 2], f1 = sides[4 * t + 3];
-  const int kf = kind[4 * e0 + f0];
+  const int kf = kind[nface * e0 + f0];
   for (int i = lane; i < cnt; i += 32) {
     const int v = i % nv;
-    const double u0 = Uf[(size_t)(4 * e0 + f0) * GN * nv + i];
+    const double u0 = Uf[(size_t)(nface * e0 + f0) * fs * nv + i];
     double x;
     if (e1 >= 0)
-      x = 0.5 * (u0 + Uf[(size_t)(4 * e1 + f1) * GN * nv + i]);
+      x = 0.5 * (u0 + Uf[(size_t)(nface * e1 + f1) * fs * nv + i]);
     else if (kf == FK_FAR)
       x = 0.5 * (u0 + a.uinf[v]);
     else
-      x = (v == 0 || v == nv - 1) ? u0 : 0.0;
+      x = (v == 0 || v == nv - 1) ? u0 : 0.0;  // wall: zero momentum
     uhat[toff[t] + i] = x;
   }
 }
@@ -452,16 +413,6 @@ __global__ void k_gen_initial_trace(int ntrace, int nv, const long long* __restr
 // element operator: face nodes -> face points -> common values at the nodes -> corrected gradient
 // -> flux tangents at the solution points and the face points -> projection to the face nodes ->
 // divergence.  Columns are staged per seed point and written as rows of NV consecutive values.
-struct JArgs {
-  int Eim;
-  const int* imp_idx;
-  const long long* offA;
-  const long long* offB;
-  const long long* offD;
-  const int* lto;  // 4 Eim: local offset of each face's trace unknowns
-  double a_dt;
-  void *A, *B, *C, *D;
-};
 
 template <int NV, typename T>
 struct JWork {
@@ -893,7 +844,8 @@ __global__ void __launch_bounds__(JT) k_gen_jacobian(const __grid_constant__ Phy
 
 // ------------------------------------------------------------------------ Newton pieces
 // r_k = -(u - u* - a dt R), s_k = -(element trace rows), one warp per implicit element
-__global__ void k_gen_form_rhs(int Eim, int nv, const int* __restrict__ imp_idx, const int* __restrict__ deg,
+__global__ void k_gen_form_rhs(int Eim, int nv, int nface, int fs, int dim, const int* __restrict__ imp_idx,
+                               const int* __restrict__ deg,
                                const long long* __restrict__ uoff, const long long* __restrict__ offr,
                                const long long* __restrict__ offs, const int* __restrict__ nfp,
                                const int* __restrict__ lto, const double* __restrict__ U,
@@ -902,16 +854,19 @@ __global__ void k_gen_form_rhs(int Eim, int nv, const int* __restrict__ imp_idx,
                                double* __restrict__ s) {
   const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (k >= Eim) return;
-  const int e = imp_idx[k], n = deg[e], nA = n * n * nv;
+  const int e = imp_idx[k];
   const long long u0 = uoff[e];
+  const int nA = (int)(uoff[e + 1] - u0);
+  (void)deg;
+  (void)dim;
   for (int i = lane; i < nA; i += 32) {
     const double us = Ustar ? Ustar[u0 + i] : U[u0 + i];
     r[offr[k] + i] = -(U[u0 + i] - us - adt * R[u0 + i]);
   }
-  for (int f = 0; f < 4; ++f) {
-    const int cnt = nfp[4 * e + f] * nv;
+  for (int f = 0; f < nface; ++f) {
+    const int cnt = nfp[nface * e + f] * nv;
     for (int i = lane; i < cnt; i += 32)
-      s[offs[k] + lto[4 * k + f] + i] = -gview[(size_t)(4 * e + f) * GN * nv + i];
+      s[offs[k] + lto[nface * k + f] + i] = -gview[(size_t)(nface * e + f) * fs * nv + i];
   }
 }
 
@@ -1110,7 +1065,10 @@ __global__ void k_gen_apply_du(int Eim, int nv, const int* __restrict__ imp_idx,
                                const double* __restrict__ du, double* __restrict__ U) {
   const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (k >= Eim) return;
-  const int e = imp_idx[k], n = deg[e], nA = n * n * nv;
+  const int e = imp_idx[k];
+  const int nA = (int)(uoff[e + 1] - uoff[e]);
+  (void)deg;
+  (void)nv;
   for (int i = lane; i < nA; i += 32) U[uoff[e] + i] += du[offr[k] + i];
 }
 
@@ -1174,40 +1132,6 @@ __global__ void k_gen_status_reset(int* status) {
 }
 
 // ------------------------------------------------------------------------ context
-struct GenCtx {
-  Hooks hk;
-  cudaStream_t st = 0;
-  int E = 0, Eim = 0, nv = 0, ntrace = 0, pb = 8, tableau = 0, restart = 30, pmax = 0;
-  int maxA = 0, maxT = 0;
-  bool need_nbr = false, has_explicit = false;
-  PhysParams pp;
-  double uinf[5] = {0, 0, 0, 0, 0};
-  size_t nstate = 0, nh = 0, sumA = 0, sumT = 0, sumAA = 0, sumAT = 0, sumTT = 0, sumP = 0;
-  size_t bytes = 0;
-  std::vector<void*> allocs;
-  std::vector<long long> h_uoff, h_toff;
-  std::vector<int> h_nA, h_nT, h_deg;
-  std::vector<double> xy;
-  // device
-  GenRef* ref = nullptr;
-  int *deg = nullptr, *nbr = nullptr, *nbr_face = nullptr, *kind = nullptr, *tr_of = nullptr, *nfp = nullptr;
-  long long *uoff = nullptr, *goff = nullptr, *toff = nullptr;
-  double *geo_sol = nullptr, *geo_face = nullptr;
-  unsigned char *implicit = nullptr, *dof_imp = nullptr;
-  int *tpts = nullptr, *sides = nullptr, *pside = nullptr;
-  long long* poff = nullptr;
-  int *imp_idx = nullptr, *lto = nullptr, *nAk = nullptr, *nTk = nullptr, *gmap = nullptr;
-  long long *offA = nullptr, *offB = nullptr, *offD = nullptr, *offr = nullptr, *offs = nullptr, *ginv = nullptr;
-  double *Uf_all = nullptr, *qf_all = nullptr, *Rw = nullptr, *gview = nullptr, *gw = nullptr, *Ustar = nullptr;
-  double *r = nullptr, *s = nullptr, *xr = nullptr, *te = nullptr, *tg = nullptr, *yv = nullptr;
-  double *duhat = nullptr, *du = nullptr, *red = nullptr, *pwork = nullptr;
-  void *A = nullptr, *B = nullptr, *C = nullptr, *D = nullptr, *LU = nullptr, *XB = nullptr, *S = nullptr, *Pinv = nullptr;
-  int* piv = nullptr;
-  int* status = nullptr;
-  UnevenDev udev;
-  GmresBuffers gm;
-  bool lin_valid = false;
-};
 
 static int err(GenCtx* g, int code, const char* msg, int elem = -1, int it = -1, double val = 0.0) {
   if (g && g->hk.set_err) return g->hk.set_err(g->hk.owner, code, msg, elem, it, val);
@@ -1240,6 +1164,7 @@ static T* galloc(GenCtx* g, size_t count, int* rc) {
 
 bool mesh_is_general(const fr_mesh_desc* mesh) {
   if (!mesh) return false;
+  if (mesh->elem_type == FR_ELEM_HEX) return true;
   if (mesh->p_elem)
     for (int e = 1; e < mesh->nelem; ++e)
       if (mesh->p_elem[e] != mesh->p_elem[0]) return true;
@@ -1283,23 +1208,27 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
   *out = nullptr;
   const int E = mesh->nelem;
   if (cfg->physics != FR_PHYS_ADVDIFF && cfg->physics != FR_PHYS_NAVIER_STOKES) return FR_ERR_UNSUPPORTED;
-  if (cfg->precision != FR_PREC_FP64 && cfg->precision != FR_PREC_FP32) return FR_ERR_INVALID_ARG;
-  const int nv = cfg->physics == FR_PHYS_ADVDIFF ? 1 : 4;
+  if (cfg->precision != FR_PREC_FP64 && cfg->precision != FR_PREC_FP32) return FR_ERR_UNSUPPORTED;
+  const bool hex = mesh->elem_type == FR_ELEM_HEX;
+  if (hex && cfg->physics != FR_PHYS_NAVIER_STOKES) return FR_ERR_UNSUPPORTED;  // hexahedra: Navier-Stokes
+  const int DIM = hex ? 3 : 2, NF = hex ? 6 : 4, FS = hex ? HEX_FS : GN, NC = hex ? 8 : 4;
+  const int nv = cfg->physics == FR_PHYS_ADVDIFF ? 1 : (hex ? 5 : 4);
   std::vector<int> deg(E);
   for (int e = 0; e < E; ++e) {
     const int p = mesh->p_elem ? mesh->p_elem[e] : mesh->p;
-    if (p < 1 || p > 5) return FR_ERR_UNSUPPORTED;
+    if (p < 1 || p > (hex ? HEX_PMAX : 5)) return FR_ERR_UNSUPPORTED;
+    if (hex && p != (mesh->p_elem ? mesh->p_elem[0] : mesh->p)) return FR_ERR_UNSUPPORTED;  // one degree
     deg[e] = p + 1;
   }
   // connectivity, face kinds, face point counts
-  std::vector<int> kind(4 * (size_t)E), nfp(4 * (size_t)E), nbr(4 * (size_t)E), nbf(4 * (size_t)E);
+  std::vector<int> kind(NF * (size_t)E), nfp(NF * (size_t)E), nbr(NF * (size_t)E), nbf(NF * (size_t)E);
   bool need_nbr = false;
   for (int e = 0; e < E; ++e)
-    for (int f = 0; f < 4; ++f) {
-      const size_t i = 4 * (size_t)e + f;
+    for (int f = 0; f < NF; ++f) {
+      const size_t i = NF * (size_t)e + f;
       const int nb = mesh->nbr[i], nf = mesh->nbr_face[i], id = mesh->face_of[i];
       const bool ie = mesh->implicit[e] != 0;
-      if (id < 0 || (long long)id >= 4LL * E) return FR_ERR_INVALID_ARG;
+      if (id < 0 || (long long)id >= (long long)NF * E) return FR_ERR_INVALID_ARG;
       if (nb < 0) {
         const int bc = mesh->bc ? mesh->bc[i] : 0;
         if (bc == BC_WALL) {
@@ -1313,18 +1242,18 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
         }
         nbr[i] = -1;
         nbf[i] = -1;
-        nfp[i] = deg[e];
+        nfp[i] = hex ? deg[e] * deg[e] : deg[e];
         continue;
       }
-      if (nb >= E || nf < 0 || nf > 3 || mesh->nbr[4 * (size_t)nb + nf] != e || mesh->nbr_face[4 * (size_t)nb + nf] != f ||
-          mesh->face_of[4 * (size_t)nb + nf] != id)
+      if (nb >= E || nf < 0 || nf >= NF || mesh->nbr[NF * (size_t)nb + nf] != e || mesh->nbr_face[NF * (size_t)nb + nf] != f ||
+          mesh->face_of[NF * (size_t)nb + nf] != id)
         return FR_ERR_INVALID_ARG;
       const bool in = mesh->implicit[nb] != 0;
       kind[i] = (ie && in) ? FK_TRACE : (ie != in ? FK_IMEX : FK_FR);
       if (kind[i] != FK_TRACE) need_nbr = true;
       nbr[i] = nb;
       nbf[i] = nf;
-      nfp[i] = std::max(deg[e], deg[nb]);
+      nfp[i] = hex ? deg[e] * deg[e] : std::max(deg[e], deg[nb]);
     }
   GenCtx* g = new GenCtx();
   g->hk = hooks;
@@ -1337,7 +1266,10 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
   g->need_nbr = need_nbr;
   g->has_explicit = need_nbr;
   memset(&g->pp, 0, sizeof(g->pp));
-  g->pp.kind = cfg->physics;
+  g->pp.kind = hex ? 3 : cfg->physics;
+  g->dim = DIM;
+  g->nface = NF;
+  g->fs = FS;
   g->pp.beta[0] = cfg->beta[0];
   g->pp.beta[1] = cfg->beta[1];
   g->pp.nu = cfg->nu;
@@ -1349,10 +1281,10 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
   g->h_deg = deg;
   // trace numbering: faces with a trace (both sides implicit, or a boundary face of an implicit
   // element) in increasing global face id
-  std::vector<int> tr_of(4 * (size_t)E, -1), tr_of_fid(4 * (size_t)E, -1), pts_of_fid(4 * (size_t)E, 0);
+  std::vector<int> tr_of(NF * (size_t)E, -1), tr_of_fid(NF * (size_t)E, -1), pts_of_fid(NF * (size_t)E, 0);
   for (int e = 0; e < E; ++e)
-    for (int f = 0; f < 4; ++f) {
-      const size_t i = 4 * (size_t)e + f;
+    for (int f = 0; f < NF; ++f) {
+      const size_t i = NF * (size_t)e + f;
       if (kind[i] == FK_TRACE || (nbr[i] < 0 && mesh->implicit[e])) {
         tr_of_fid[mesh->face_of[i]] = 0;
         pts_of_fid[mesh->face_of[i]] = nfp[i];
@@ -1371,8 +1303,8 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
   g->nh = (size_t)toff[nt];
   std::vector<int> sides(4 * (size_t)std::max(nt, 1), -1);
   for (int e = 0; e < E; ++e)
-    for (int f = 0; f < 4; ++f) {
-      const size_t i = 4 * (size_t)e + f;
+    for (int f = 0; f < NF; ++f) {
+      const size_t i = NF * (size_t)e + f;
       if (kind[i] == FK_TRACE || (nbr[i] < 0 && mesh->implicit[e])) {
         const int t = tr_of_fid[mesh->face_of[i]];
         tr_of[i] = t;
@@ -1384,8 +1316,9 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
   // state offsets, implicit blocks
   std::vector<long long> uoff(E + 1, 0), goff(E + 1, 0);
   for (int e = 0; e < E; ++e) {
-    uoff[e + 1] = uoff[e] + (long long)deg[e] * deg[e] * nv;
-    goff[e + 1] = goff[e] + (long long)deg[e] * deg[e];
+    const long long ns = hex ? (long long)deg[e] * deg[e] * deg[e] : (long long)deg[e] * deg[e];
+    uoff[e + 1] = uoff[e] + ns * nv;
+    goff[e + 1] = goff[e] + ns;
     g->pmax = std::max(g->pmax, deg[e] - 1);
   }
   g->nstate = (size_t)uoff[E];
@@ -1397,18 +1330,18 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
     }
   const int Eim = (int)imp_idx.size();
   g->Eim = Eim;
-  std::vector<int> nAk(std::max(Eim, 1)), nTk(std::max(Eim, 1)), lto(4 * (size_t)std::max(Eim, 1));
+  std::vector<int> nAk(std::max(Eim, 1)), nTk(std::max(Eim, 1)), lto(NF * (size_t)std::max(Eim, 1));
   std::vector<long long> offA(Eim + 1, 0), offB(Eim + 1, 0), offD(Eim + 1, 0), offr(Eim + 1, 0), offs(Eim + 1, 0);
   for (int k = 0; k < Eim; ++k) {
     const int e = imp_idx[k];
-    nAk[k] = deg[e] * deg[e] * nv;
+    nAk[k] = (int)(uoff[e + 1] - uoff[e]);
     int o = 0;
-    for (int f = 0; f < 4; ++f) {
-      lto[4 * (size_t)k + f] = o;
-      o += nfp[4 * (size_t)e + f] * nv;
+    for (int f = 0; f < NF; ++f) {
+      lto[NF * (size_t)k + f] = o;
+      o += nfp[NF * (size_t)e + f] * nv;
     }
     nTk[k] = o;
-    if (o > 512) {
+    if (o > 512 || nAk[k] > 32 * 5 * (hex ? 2 : 1)) {
       destroy(g);
       return FR_ERR_UNSUPPORTED;
     }
@@ -1433,15 +1366,15 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
   std::vector<int> pside(4 * (size_t)std::max(nt, 1), -1);
   for (int k = 0; k < Eim; ++k) {
     const int e = imp_idx[k];
-    for (int f = 0; f < 4; ++f) {
-      const int t = tr_of[4 * (size_t)e + f];
+    for (int f = 0; f < NF; ++f) {
+      const int t = tr_of[NF * (size_t)e + f];
       if (t < 0) continue;
       const int sd = sides[4 * (size_t)t] == e && sides[4 * (size_t)t + 1] == f ? 0 : 1;
       pside[4 * (size_t)t + 2 * sd] = k;
-      pside[4 * (size_t)t + 2 * sd + 1] = lto[4 * (size_t)k + f];
+      pside[4 * (size_t)t + 2 * sd + 1] = lto[NF * (size_t)k + f];
       const int cnt = tpts[t] * nv;
       for (int i = 0; i < cnt; ++i) {
-        const long long l = offs[k] + lto[4 * (size_t)k + f] + i;
+        const long long l = offs[k] + lto[NF * (size_t)k + f] + i;
         gmap[l] = (int)(toff[t] + i);
         ginv[2 * (size_t)(toff[t] + i) + sd] = l;
       }
@@ -1451,13 +1384,17 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
   for (int t = 0; t < nt; ++t) poff[t + 1] = poff[t] + (long long)(tpts[t] * nv) * (tpts[t] * nv);
   g->sumP = (size_t)poff[nt];
   // geometry at the own solution points and at every face's points
-  std::vector<double> gsol(5 * (size_t)goff[E]), gface(3 * 4 * (size_t)E * GN, 0.0);
-  g->xy.assign(2 * (size_t)goff[E], 0.0);
-  for (int e = 0; e < E; ++e) {
+  const int GS = hex ? 10 : 5, GFC = hex ? 4 : 3;  // values per solution point / face point
+  std::vector<double> gsol(GS * (size_t)goff[E]), gface(GFC * NF * (size_t)E * FS, 0.0);
+  g->xy.assign(DIM * (size_t)goff[E], 0.0);
+  if (hex)
+    hex_geometry(mesh->verts, E, deg.data(), goff.data(), gsol.data(), gface.data(), g->xy.data());
+  else
+    for (int e = 0; e < E; ++e) {
     const int n = deg[e];
     double xg[GN], wg[GN];
     gauss_legendre_nodes(n, xg, wg);
-    const double* V = mesh->verts + (size_t)e * 8;
+    const double* V = mesh->verts + (size_t)e * 2 * NC;
     for (int b = 0; b < n; ++b)
       for (int a = 0; a < n; ++a) {
         const size_t pt = (size_t)goff[e] + a + n * b;
@@ -1470,8 +1407,8 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
         G[3] = S[1][0];
         G[4] = S[1][1];
       }
-    for (int f = 0; f < 4; ++f) {
-      const int m = nfp[4 * (size_t)e + f], r = f >> 1;
+    for (int f = 0; f < NF; ++f) {
+      const int m = nfp[NF * (size_t)e + f], r = f >> 1;
       const double sg = (f & 1) ? 1.0 : -1.0;
       double sq[GN], wq[GN];
       gauss_legendre_nodes(m, sq, wq);
@@ -1481,7 +1418,7 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
         bilinear_g(V, xi, eta, &J, S, nullptr);
         const double N0 = sg * S[r][0], N1 = sg * S[r][1];
         const double Jf = sqrt(N0 * N0 + N1 * N1);
-        double* G = &gface[3 * ((size_t)(4 * e + f) * GN + q)];
+        double* G = &gface[3 * ((size_t)(NF * e + f) * FS + q)];
         G[0] = Jf;
         G[1] = N0 / Jf;
         G[2] = N1 / Jf;
@@ -1489,6 +1426,7 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
     }
   }
   std::vector<unsigned char> dof_imp(std::max(g->nstate, (size_t)1), 0), impv(mesh->implicit, mesh->implicit + E);
+  (void)NC;
   for (int e = 0; e < E; ++e)
     if (mesh->implicit[e])
       for (long long i = uoff[e]; i < uoff[e + 1]; ++i) dof_imp[i] = 1;
@@ -1505,11 +1443,11 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
   const size_t pb = g->pb;
   g->ref = galloc<GenRef>(g, 1, &rc);
   g->deg = galloc<int>(g, E, &rc);
-  g->nbr = galloc<int>(g, 4 * (size_t)E, &rc);
-  g->nbr_face = galloc<int>(g, 4 * (size_t)E, &rc);
-  g->kind = galloc<int>(g, 4 * (size_t)E, &rc);
-  g->tr_of = galloc<int>(g, 4 * (size_t)E, &rc);
-  g->nfp = galloc<int>(g, 4 * (size_t)E, &rc);
+  g->nbr = galloc<int>(g, NF * (size_t)E, &rc);
+  g->nbr_face = galloc<int>(g, NF * (size_t)E, &rc);
+  g->kind = galloc<int>(g, NF * (size_t)E, &rc);
+  g->tr_of = galloc<int>(g, NF * (size_t)E, &rc);
+  g->nfp = galloc<int>(g, NF * (size_t)E, &rc);
   g->uoff = galloc<long long>(g, E + 1, &rc);
   g->goff = galloc<long long>(g, E + 1, &rc);
   g->toff = galloc<long long>(g, nt + 1, &rc);
@@ -1533,11 +1471,11 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
   g->offr = galloc<long long>(g, Eim + 1, &rc);
   g->offs = galloc<long long>(g, Eim + 1, &rc);
   if (need_nbr) {
-    g->Uf_all = galloc<double>(g, 4 * (size_t)E * GN * nv, &rc);
-    g->qf_all = galloc<double>(g, 4 * (size_t)E * GN * 2 * nv, &rc);
+    g->Uf_all = galloc<double>(g, NF * (size_t)E * FS * nv, &rc);
+    g->qf_all = galloc<double>(g, NF * (size_t)E * FS * DIM * nv, &rc);
   }
   g->Rw = galloc<double>(g, g->nstate, &rc);
-  g->gview = galloc<double>(g, 4 * (size_t)E * GN * nv, &rc);
+  g->gview = galloc<double>(g, NF * (size_t)E * FS * nv, &rc);
   g->gw = galloc<double>(g, g->nh, &rc);
   g->Ustar = galloc<double>(g, g->nstate, &rc);
   g->r = galloc<double>(g, g->sumA, &rc);
@@ -1568,6 +1506,10 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
   g->gm.partial = galloc<double>(g, (size_t)GM_NBLK * (GM_MAXM + 1), &rc);
   g->gm.ticket = galloc<unsigned int>(g, 1, &rc);
   g->gm.state = galloc<GmresState>(g, 1, &rc);
+  if (hex && Eim > 0) {
+    g->jgrid = std::min(hex_jacobian_grid((int)pb), Eim);
+    g->jscratch = galloc<unsigned char>(g, hex_jacobian_scratch_bytes((int)pb, g->jgrid), &rc);
+  }
   if (rc != FR_OK) {
     destroy(g);
     return rc;
@@ -1611,9 +1553,10 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
     destroy(g);
     return FR_ERR_CUDA;
   }
+  g->udev.colmajor = hex ? 1 : 0;
   if (cudaMemsetAsync(g->status, 0, 2 * sizeof(int), st) != cudaSuccess ||
       cudaMemsetAsync(g->gm.ticket, 0, sizeof(unsigned), st) != cudaSuccess ||
-      cudaMemsetAsync(g->gview, 0, 4 * (size_t)E * GN * nv * sizeof(double), st) != cudaSuccess ||
+      cudaMemsetAsync(g->gview, 0, NF * (size_t)E * FS * nv * sizeof(double), st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess) {
     destroy(g);
     return FR_ERR_CUDA;
@@ -1629,7 +1572,7 @@ void query(const GenCtx* g, fr_ctx_info* info) {
   info->nimplicit = g->Eim;
   info->p = g->pmax;
   info->n = g->pmax + 1;
-  info->ns = info->n * info->n;
+  info->ns = g->dim == 3 ? info->n * info->n * info->n : info->n * info->n;
   info->nv = g->nv;
   info->nA = g->maxA;
   info->nT = g->maxT;
@@ -1683,6 +1626,8 @@ static GArgs gargs(GenCtx* g, const double* u, const double* uhat) {
   a.Uf_out = g->Uf_all;
   a.qf_out = g->qf_all;
   for (int v = 0; v < 5; ++v) a.uinf[v] = g->uinf[v];
+  a.nface = g->nface;
+  a.fs = g->fs;
   return a;
 }
 
@@ -1701,6 +1646,7 @@ static cudaError_t launch_gen_elem(GenCtx* g, const GArgs& a) {
 
 template <int MODE>
 static cudaError_t gen_elem(GenCtx* g, const GArgs& a) {
+  if (g->dim == 3) return hex_elem_pass(g, a, MODE);
   return g->pp.kind == 0 ? launch_gen_elem<0, MODE>(g, a) : launch_gen_elem<1, MODE>(g, a);
 }
 
@@ -1716,8 +1662,8 @@ static int residual_into(GenCtx* g, const double* u, const double* uhat, double*
   a.gview = g->gview;
   GCK(gen_elem<GM_RES>(g, a));
   if (g_out && g->ntrace) {
-    (count_launch(), k_gen_trace_sum<<<nbw(g->ntrace), 256, 0, g->st>>>(g->ntrace, g->nv, g->toff, g->tpts, g->sides,
-                                                                        g->gview, g_out));
+    (count_launch(), k_gen_trace_sum<<<nbw(g->ntrace), 256, 0, g->st>>>(g->ntrace, g->nv, g->nface, g->fs, g->toff,
+                                                                        g->tpts, g->sides, g->gview, g_out));
     GCK(cudaGetLastError());
   }
   pend(g, ph);
@@ -1741,7 +1687,7 @@ int initial_trace(GenCtx* g, const double* u, double* uhat) {
                                                                             g->sides, g->kind, buf, a, uhat));
     GCK(cudaGetLastError());
   }
-  GCK(cudaMemsetAsync(g->gview, 0, 4 * (size_t)g->E * GN * g->nv * sizeof(double), g->st));
+  GCK(cudaMemsetAsync(g->gview, 0, (size_t)g->nface * g->E * g->fs * g->nv * sizeof(double), g->st));
   GCK(cudaStreamSynchronize(g->st));
   return FR_OK;
 }
@@ -1774,8 +1720,11 @@ static int jacobian_blocks(GenCtx* g, const double* u, const double* uhat, doubl
   j.B = g->B;
   j.C = g->C;
   j.D = g->D;
+  j.scratch = g->jscratch;
   cudaError_t e;
-  if (g->pb == 8)
+  if (g->dim == 3)
+    e = hex_jacobian(g, a, j);
+  else if (g->pb == 8)
     e = g->pp.kind == 0 ? launch_gen_jac<0, double>(g, a, j) : launch_gen_jac<1, double>(g, a, j);
   else
     e = g->pp.kind == 0 ? launch_gen_jac<0, float>(g, a, j) : launch_gen_jac<1, float>(g, a, j);
@@ -1787,7 +1736,8 @@ static int jacobian_blocks(GenCtx* g, const double* u, const double* uhat, doubl
 
 static int form_rhs(GenCtx* g, const double* u, const double* ustar, double a_dt) {
   if (g->Eim == 0) return FR_OK;
-  (count_launch(), k_gen_form_rhs<<<nbw(g->Eim), 256, 0, g->st>>>(g->Eim, g->nv, g->imp_idx, g->deg, g->uoff, g->offr,
+  (count_launch(), k_gen_form_rhs<<<nbw(g->Eim), 256, 0, g->st>>>(g->Eim, g->nv, g->nface, g->fs, g->dim, g->imp_idx,
+                                                                   g->deg, g->uoff, g->offr,
                                                                    g->offs, g->nfp, g->lto, u, ustar, g->Rw, g->gview,
                                                                    a_dt, g->r, g->s));
   GCK(cudaGetLastError());

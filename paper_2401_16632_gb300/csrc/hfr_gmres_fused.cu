@@ -387,6 +387,30 @@ __device__ __forceinline__ PGVec<T, VW> pg_ld_keep(const T* ptr, unsigned long l
   return r;
 }
 
+// VW consecutive BF16 values (the trace operator stored in BF16) widened to FP32, with the same
+// evict-last policy; BF16 is the upper half of an FP32 word, so widening is a 16-bit shift
+template <int VW>
+__device__ __forceinline__ PGVec<float, VW> pg_ld_keep_bf16(const unsigned short* ptr, unsigned long long pol) {
+  PGVec<float, VW> r;
+  if constexpr (VW == 4) {
+    unsigned a, b;
+    asm("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(a), "=r"(b) : "l"(ptr), "l"(pol));
+    r.v[0] = __uint_as_float(a << 16);
+    r.v[1] = __uint_as_float(a & 0xffff0000u);
+    r.v[2] = __uint_as_float(b << 16);
+    r.v[3] = __uint_as_float(b & 0xffff0000u);
+  } else if constexpr (VW == 2) {
+    unsigned a;
+    asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(a) : "l"(ptr), "l"(pol));
+    r.v[0] = __uint_as_float(a << 16);
+    r.v[1] = __uint_as_float(a & 0xffff0000u);
+  } else {
+#pragma unroll
+    for (int q = 0; q < VW; ++q) r.v[q] = __uint_as_float((unsigned)__ldg(ptr + q) << 16);
+  }
+  return r;
+}
+
 template <typename T, int VW>
 __device__ __forceinline__ PGVec<T, VW> pg_ld_cg(const T* ptr) {
   PGVec<T, VW> r;
@@ -426,7 +450,7 @@ struct PGShape {
 // row blocks of S_k against the neighbours' gathered trace values (src in the block precision T,
 // or FP64 when SRC_D).  Lane g8 of a group holds the columns VW (g8 + 8 c) + q of each row, so
 // every load is a VW-wide vector and no vector crosses a face block.
-template <typename T, int NT, int BS, bool SRC_D>
+template <typename T, int NT, int BS, bool SRC_D, bool SB>
 __device__ __forceinline__ void pg_face_rows(const FusedArgs& a, int f, const void* src, unsigned long long pol,
                                              T (&acc)[(BS + 3) / 4]) {
   using Sh = PGShape<T, NT, BS>;
@@ -448,9 +472,20 @@ __device__ __forceinline__ void pg_face_rows(const FusedArgs& a, int f, const vo
     for (int u = 0; u < RU; ++u) {
       const int i = grp + 4 * u;
       const int ii = i < BS ? i : 0;
-      const T* row = S + ((size_t)e * NT + (size_t)fs * BS + ii) * NT;
+      const size_t ro = ((size_t)e * NT + (size_t)fs * BS + ii) * NT;
+      if constexpr (SB) {
+        const unsigned short* row = reinterpret_cast<const unsigned short*>(a.S) + ro;
 #pragma unroll
-      for (int c = 0; c < CV; ++c) sv[u][c] = pg_ld_keep<T, VW>(row + VW * (g8 + 8 * c), pol);
+        for (int c = 0; c < CV; ++c) {
+          const PGVec<float, VW> x = pg_ld_keep_bf16<VW>(row + VW * (g8 + 8 * c), pol);
+#pragma unroll
+          for (int q = 0; q < VW; ++q) sv[u][c].v[q] = T(x.v[q]);
+        }
+      } else {
+        const T* row = S + ro;
+#pragma unroll
+        for (int c = 0; c < CV; ++c) sv[u][c] = pg_ld_keep<T, VW>(row + VW * (g8 + 8 * c), pol);
+      }
     }
     PGVec<T, VW> xv[CV];
 #pragma unroll
@@ -491,7 +526,7 @@ __device__ __forceinline__ void pg_face_rows(const FusedArgs& a, int f, const vo
 
 // out_f = t_f - (L src)_f when RES, else (L src)_f, for this CTA's faces (one warp per face),
 // stored in the vector precision T
-template <typename T, int NT, int BS, bool SRC_D, bool RES>
+template <typename T, int NT, int BS, bool SRC_D, bool RES, bool SB>
 __device__ void pg_matvec(const FusedArgs& a, const void* src, T* out, int fb0, int fb1) {
   constexpr int RU = (BS + 3) / 4;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -499,7 +534,7 @@ __device__ void pg_matvec(const FusedArgs& a, const void* src, T* out, int fb0, 
   const unsigned long long pol = pg_policy_keep();
   for (int f = fb0 + wid; f < fb1; f += PG_WARPS) {
     T acc[RU];
-    pg_face_rows<T, NT, BS, SRC_D>(a, f, src, pol, acc);
+    pg_face_rows<T, NT, BS, SRC_D, SB>(a, f, src, pol, acc);
     if (g8 == 0) {
 #pragma unroll
       for (int u = 0; u < RU; ++u) {
@@ -684,7 +719,7 @@ __device__ void pg_givens(PGShared<T>& sh, int j, double rtol, int m) {
   }
 }
 
-template <typename T, int NT, int BS>
+template <typename T, int NT, int BS, bool SB>
 __global__ void __launch_bounds__(PG_THREADS, 1) k_gmres_cycle(const __grid_constant__ FusedArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   PGShared<T>& sh = *reinterpret_cast<PGShared<T>*>(smem_raw);
@@ -706,7 +741,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_gmres_cycle(const __grid_cons
   if (xz) {
     for (size_t x = x0 + tid; x < x1; x += PG_THREADS) V[x] = T(__ldcg(a.t + x));
   } else {
-    pg_matvec<T, NT, BS, true, true>(a, a.x, V, fb0, fb1);
+    pg_matvec<T, NT, BS, true, true, SB>(a, a.x, V, fb0, fb1);
   }
   __syncthreads();
   pg_block_sq(sh, V, a.t, x0, x1, partial + par * pstride);
@@ -751,7 +786,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_gmres_cycle(const __grid_cons
       if (!pg_sync(sh, a.bar, epoch)) return;
       if (sh.done) break;
       // (B) w = L z and h = V^T w
-      pg_matvec<T, NT, BS, false, false>(a, a.z, w, fb0, fb1);
+      pg_matvec<T, NT, BS, false, false, SB>(a, a.z, w, fb0, fb1);
       __syncthreads();
       T* part = partial + par * pstride;
       pg_block_dots<T, VWB>(sh, V, n, j + 1, w, x0, x1, part);
@@ -819,7 +854,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_gmres_cycle(const __grid_cons
   if (a.true_res) {
     // true residual ||t - L x|| (V_0 as scratch)
     if (!pg_sync(sh, a.bar, epoch)) return;
-    pg_matvec<T, NT, BS, true, true>(a, a.x, V, fb0, fb1);
+    pg_matvec<T, NT, BS, true, true, SB>(a, a.x, V, fb0, fb1);
     __syncthreads();
     pg_block_sq(sh, V, (const T*)nullptr, x0, x1, partial + par * pstride);
     if (!pg_sync(sh, a.bar, epoch)) return;
@@ -843,45 +878,50 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_gmres_cycle(const __grid_cons
   }
 }
 
-template <typename T, int NT, int BS>
+template <typename T, int NT, int BS, bool SB>
 cudaError_t launch_cycle(const FusedArgs& a, int grid, cudaStream_t s) {
   const size_t smem = sizeof(PGShared<T>);
-  cudaError_t e = cudaFuncSetAttribute(k_gmres_cycle<T, NT, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_gmres_cycle<T, NT, BS, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   void* args[] = {const_cast<FusedArgs*>(&a)};
   (hfr::count_launch(),
-   e = cudaLaunchCooperativeKernel((const void*)k_gmres_cycle<T, NT, BS>, dim3(grid), dim3(PG_THREADS), args, smem, s));
+   e = cudaLaunchCooperativeKernel((const void*)k_gmres_cycle<T, NT, BS, SB>, dim3(grid), dim3(PG_THREADS), args, smem, s));
   return e;
 }
 
-template <typename T, int NT, int BS>
+template <typename T, int NT, int BS, bool SB>
 int occupancy_of() {
   int nb = 0;
   const size_t smem = sizeof(PGShared<T>);
-  if (cudaFuncSetAttribute(k_gmres_cycle<T, NT, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+  if (cudaFuncSetAttribute(k_gmres_cycle<T, NT, BS, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gmres_cycle<T, NT, BS>, PG_THREADS, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gmres_cycle<T, NT, BS, SB>, PG_THREADS, smem) != cudaSuccess)
     return 0;
   return nb;
 }
 
 typedef cudaError_t (*CycleFn)(const FusedArgs&, int, cudaStream_t);
 
-CycleFn pick(int prec_bytes, int nT, int bs, int* occ) {
-#define HFR_PG(T_, NT_, BS_)                  \
-  if (nT == NT_ && bs == BS_) {               \
-    *occ = occupancy_of<T_, NT_, BS_>();      \
-    return launch_cycle<T_, NT_, BS_>;        \
+// s_bf16: the trace operator S is stored in BF16 (FP32 blocks, basis and arithmetic otherwise)
+CycleFn pick(int prec_bytes, int nT, int bs, int* occ, bool s_bf16 = false) {
+#define HFR_PG(T_, NT_, BS_, SB_)                  \
+  if (nT == NT_ && bs == BS_) {                    \
+    *occ = occupancy_of<T_, NT_, BS_, SB_>();      \
+    return launch_cycle<T_, NT_, BS_, SB_>;        \
   }
-  if (prec_bytes == 4) {
-    HFR_PG(float, 64, 16)
-    HFR_PG(float, 80, 20)
-    HFR_PG(float, 48, 12)
+  if (prec_bytes == 4 && s_bf16) {
+    HFR_PG(float, 64, 16, true)
+    HFR_PG(float, 80, 20, true)
+    HFR_PG(float, 48, 12, true)
+  } else if (prec_bytes == 4) {
+    HFR_PG(float, 64, 16, false)
+    HFR_PG(float, 80, 20, false)
+    HFR_PG(float, 48, 12, false)
   } else {
-    HFR_PG(double, 64, 16)
-    HFR_PG(double, 80, 20)
-    HFR_PG(double, 48, 12)
+    HFR_PG(double, 64, 16, false)
+    HFR_PG(double, 80, 20, false)
+    HFR_PG(double, 48, 12, false)
   }
 #undef HFR_PG
   *occ = 0;
@@ -905,7 +945,7 @@ int run_gmres_fused(const FusedArgs& base, int prec_bytes, int grid, double rtol
                     GmresResult* res, int* timed_out, cudaStream_t s, const int* dev_status, int* host_status) {
   int occ = 0;
   const int bs = (int)(base.n / (size_t)base.ntrace);
-  CycleFn fn = pick(prec_bytes, base.nT, bs, &occ);
+  CycleFn fn = pick(prec_bytes, base.nT, bs, &occ, base.s_bf16 != 0);
   *timed_out = 0;
   if (!fn || grid < 1) return -1;
   const int m = restart > GM_MAXM ? GM_MAXM : (restart < 1 ? 1 : restart);
@@ -949,7 +989,7 @@ int run_gmres_fused(const FusedArgs& base, int prec_bytes, int grid, double rtol
 cudaError_t launch_gmres_cycle(const FusedArgs& a, int prec_bytes, int grid, cudaStream_t s) {
   int occ = 0;
   const int bs = (int)(a.n / (size_t)(a.ntrace > 0 ? a.ntrace : 1));
-  CycleFn fn = pick(prec_bytes, a.nT, bs, &occ);
+  CycleFn fn = pick(prec_bytes, a.nT, bs, &occ, a.s_bf16 != 0);
   if (!fn || grid < 1) return cudaErrorInvalidValue;
   return fn(a, grid, s);
 }

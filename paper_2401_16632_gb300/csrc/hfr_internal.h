@@ -121,6 +121,7 @@ struct UnevenDev {
   const int *order = nullptr, *shape = nullptr, *bundle = nullptr, *global = nullptr;
   int nb = 0, nglobal = 0;
   size_t smem = 0;
+  int colmajor = 0;  // the blocks are stored column-major (hexahedra); all go to the global kernel
 };
 int uneven_tables(int prec_bytes, int n, const int* nA, const int* nT, UnevenTables* tb);
 size_t uneven_dev_bytes(const UnevenTables& tb);

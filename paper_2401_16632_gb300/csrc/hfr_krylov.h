@@ -62,8 +62,9 @@ struct FusedArgs {
   int ntrace, nT;
   const int* sides;    // ntrace x 4 (e0, f0, e1, f1), compact implicit element ids
   const int* tr_of_c;  // Eim x 4 trace face of each element face
-  const void* S;       // Eim x nT x nT, block precision
+  const void* S;       // Eim x nT x nT, block precision (BF16 when s_bf16)
   size_t S_bytes;      // size of S
+  int s_bf16 = 0;      // 1: S holds BF16 values (FP32 path only)
   const void* Pinv;    // ntrace x bs x bs face-block inverses, block precision
   const double* t;     // right-hand side
   double* x;           // solution (zeroed by run_gmres_fused)

@@ -456,3 +456,28 @@ def test_autotune_picks_a_valid_configuration(name):
     U_o, uh_o, _ = imex_step(d, u0, d.initial_trace(u0), dt, "sdirk2", tol=1e-12)
     u1, _ = ctx.imex_step(dt, u, ctx.hfr_initial_trace(u), newton_tol=1e-12, gmres_rtol=1e-8, gmres_maxit=3000)
     assert np.abs(u1.cpu().numpy() - U_o).max() < 1e-8 * np.abs(U_o - u0).max()
+
+
+@pytest.mark.parametrize("name", ["vortex_skew_p3", "vortex_p4"])
+def test_bf16_trace_operator_stage_converges_to_the_fp64_stage(name):
+    """FR_PREC_BF16 stores S^k in BF16 for the GMRES mat-vecs (FP32 accumulation); the FP64 Newton
+    residual still decides, so the converged stage is the FP64 one: at a 1e-12 Newton tolerance
+    both agree to 1e-8 relative to the stage increment (the mixed-precision target)."""
+    out = {}
+    for prec in (pkg.FR_PREC_FP64, pkg.FR_PREC_BF16, pkg.FR_PREC_TF32):
+        ctx, d, u0 = _setup(name, precision=prec)
+        if prec == pkg.FR_PREC_BF16:
+            assert ctx.hfr_gmres_get_mode() == pkg.FR_GMRES_FUSED
+        u = torch.tensor(u0, device=DEV)
+        uh = ctx.hfr_initial_trace(u)
+        R_hist = ctx.empty(3, *ctx.state_shape)
+        us = ctx.empty(*ctx.state_shape)
+        ctx.imex_stage(0, 0.2, u, us, uh, R_hist)
+        st = ctx.imex_stage(1, 0.2, u, us, uh, R_hist, newton_tol=1e-12, newton_maxit=40, gmres_rtol=1e-6,
+                            gmres_maxit=5000)
+        assert st["converged"], (prec, st)
+        out[prec] = us.cpu().numpy()
+        ctx.close()
+    inc = np.abs(out[pkg.FR_PREC_FP64] - u0).max()
+    assert np.abs(out[pkg.FR_PREC_BF16] - out[pkg.FR_PREC_FP64]).max() < 1e-8 * inc
+    assert np.abs(out[pkg.FR_PREC_TF32] - out[pkg.FR_PREC_FP64]).max() < 1e-8 * inc

@@ -76,10 +76,21 @@ def test_uneven_batch_matches_oracle(precision):
         assert rel(tt[k], to[0]) < tol, (k, a, t)
 
 
-def test_uneven_refuses_oversized_shapes_and_reports_a_singular_element():
-    blocks = _batch([(144, 96)], 1)
-    with pytest.raises(pkg.HfrError) as ei:
-        pkg.hfr_condense_uneven([144], [96], *_packed(blocks, torch.float64), precision=pkg.FR_PREC_FP64)
+def test_uneven_global_memory_blocks_and_a_singular_element():
+    # FP64 (144, 96) exceeds shared memory: the global-memory LU condenses it, and so it does
+    # mixed with shared-memory shapes in one call
+    shapes = [(144, 96), (36, 48), (144, 96)]
+    blocks = _batch(shapes, 1)
+    out = pkg.hfr_condense_uneven([a for a, _ in shapes], [t for _, t in shapes], *_packed(blocks, torch.float64),
+                                  precision=pkg.FR_PREC_FP64)
+    S = _split(out["S"].cpu().numpy(), [t * t for _, t in shapes])
+    xr = _split(out["xr"].cpu().numpy(), [a for a, _ in shapes])
+    for k, b in enumerate(blocks):
+        XBo, xro, So, to = condense(*(x[None] for x in b))
+        assert np.abs(S[k] - So[0].reshape(-1)).max() < 1e-11 * np.abs(So).max(), k
+        assert np.abs(xr[k] - xro[0]).max() < 1e-11 * np.abs(xro).max(), k
+    with pytest.raises(pkg.HfrError) as ei:  # an empty trace block is refused
+        pkg.hfr_condense_uneven([36], [0], *_packed(_batch([(36, 48)], 1), torch.float64), precision=pkg.FR_PREC_FP64)
     assert ei.value.code == pkg.FR_ERR_INVALID_ARG
     shapes = [(36, 48), (64, 64), (36, 48)]
     blocks = _batch(shapes, 2)
