@@ -2014,184 +2014,9 @@ static size_t smem_elem_bytes(size_t tb, int nA, int nT) {
   return tb * ((size_t)nA * nc + (size_t)big * nA + nc + nA) + sizeof(int) * (nA + 2) + nA;
 }
 
-// Large blocks, whose shared-memory working set exceeds 227 KB (FP64 from about nA = 100 with
-// nT > 80, FP32 beyond (144, 96)): one CTA of 256 threads per element, in place in global memory
-// (an element's slots, a few hundred KB, stay resident in L2 while its CTA works on them).
-//   1. LU with partial pivoting of A in the factor slot (largest |a|, lowest row on ties), the row
-//      operations applied to [B | r] in the X_B and x_r slots as they happen (forward elimination);
-//   2. back substitution of every right-hand side column, one thread per column;
-//   3. S = D - C X_B and t = s - C x_r, one thread per output entry.
-// A zero pivot sets DEV_ERR_SINGULAR with the element (the element's outputs are then undefined).
-constexpr int GLB_THREADS = 256;
-
-template <typename T>
-__global__ void __launch_bounds__(GLB_THREADS) k_condense_global(const __grid_constant__ UnevenArgs a,
-                                                                 const int* __restrict__ list, int nlist,
-                                                                 int uni_nA, int uni_nT) {
-  __shared__ T prow_s[1024];
-  __shared__ double pkey_v[GLB_THREADS / 32];
-  __shared__ int pkey_i[GLB_THREADS / 32];
-  __shared__ int s_piv;
-  __shared__ int s_bad;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  for (int li = blockIdx.x; li < nlist; li += gridDim.x) {
-    // element k: from the tables, or (uni_nA > 0) the k-th of nlist blocks of one shape
-    const int k = list ? list[li] : li;
-    long long o[5];
-    int nA, nT;
-    if (uni_nA > 0) {
-      nA = uni_nA;
-      nT = uni_nT;
-      o[0] = (long long)k * nA * nA;
-      o[1] = (long long)k * nA * nT;
-      o[2] = (long long)k * nT * nT;
-      o[3] = (long long)k * nA;
-      o[4] = (long long)k * nT;
-    } else {
-#pragma unroll
-      for (int q = 0; q < 5; ++q) o[q] = a.off[5 * (size_t)k + q];
-      nA = a.shape[2 * k];
-      nT = a.shape[2 * k + 1];
-    }
-    const T* A = reinterpret_cast<const T*>(a.A) + o[0];
-    const T* B = reinterpret_cast<const T*>(a.B) + o[1];
-    const T* C = reinterpret_cast<const T*>(a.C) + o[1];
-    const T* D = reinterpret_cast<const T*>(a.D) + o[2];
-    T* L = reinterpret_cast<T*>(a.LU) + o[0];
-    T* X = reinterpret_cast<T*>(a.XB) + o[1];
-    T* S = reinterpret_cast<T*>(a.S) + o[2];
-    const double* r = a.r + o[3];
-    double* xr = a.xr + o[3];
-    int* piv = a.piv + o[3];
-    const double* sv = a.s + o[4];
-    double* t = a.t + o[4];
-    const bool cm = a.colmajor != 0;
-    for (size_t i = tid; i < (size_t)nA * nA; i += GLB_THREADS)
-      L[i] = cm ? A[(i % nA) * nA + i / nA] : A[i];
-    for (size_t i = tid; i < (size_t)nA * nT; i += GLB_THREADS)
-      X[i] = cm ? B[(i % nT) * nA + i / nT] : B[i];
-    for (int i = tid; i < nA; i += GLB_THREADS) xr[i] = r[i];
-    if (tid == 0) s_bad = 0;
-    __syncthreads();
-    for (int j = 0; j < nA; ++j) {
-      // pivot search over rows j..nA-1
-      double bv = -1.0;
-      int bi = 0x7fffffff;
-      for (int i = j + tid; i < nA; i += GLB_THREADS) {
-        const double v = fabs((double)L[(size_t)i * nA + j]);
-        if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
-      }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, bv, off);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
-      }
-      if (lane == 0) { pkey_v[wid] = bv; pkey_i[wid] = bi; }
-      __syncthreads();
-      if (tid == 0) {
-        double v = pkey_v[0];
-        int ii = pkey_i[0];
-        for (int q = 1; q < GLB_THREADS / 32; ++q)
-          if (pkey_v[q] > v || (pkey_v[q] == v && pkey_i[q] < ii)) { v = pkey_v[q]; ii = pkey_i[q]; }
-        s_piv = ii;
-        piv[j] = ii;
-        if (!(v > 0.0)) s_bad = 1;
-      }
-      __syncthreads();
-      if (s_bad) break;
-      const int pr = s_piv;
-      if (pr != j) {  // swap rows j and pr of L, X and x_r
-        for (int c = tid; c < nA; c += GLB_THREADS) {
-          const T u = L[(size_t)j * nA + c];
-          L[(size_t)j * nA + c] = L[(size_t)pr * nA + c];
-          L[(size_t)pr * nA + c] = u;
-        }
-        for (int c = tid; c < nT; c += GLB_THREADS) {
-          const T u = X[(size_t)j * nT + c];
-          X[(size_t)j * nT + c] = X[(size_t)pr * nT + c];
-          X[(size_t)pr * nT + c] = u;
-        }
-        if (tid == 0) {
-          const double u = xr[j];
-          xr[j] = xr[pr];
-          xr[pr] = u;
-        }
-      }
-      __syncthreads();
-      // pivot row (columns j+1.. of L, all of X) into shared memory in chunks of 1024
-      const T inv = T(1) / L[(size_t)j * nA + j];
-      const double xrj = xr[j];
-      const int ncol = (nA - j - 1) + nT;
-      for (int c0 = 0; c0 < ncol; c0 += 1024) {
-        const int cn = ncol - c0 < 1024 ? ncol - c0 : 1024;
-        for (int c = tid; c < cn; c += GLB_THREADS) {
-          const int cc = c0 + c;
-          prow_s[c] = cc < nA - j - 1 ? L[(size_t)j * nA + j + 1 + cc] : X[(size_t)j * nT + (cc - (nA - j - 1))];
-        }
-        __syncthreads();
-        // rows below: one warp per row, lanes over the columns
-        for (int i = j + 1 + wid; i < nA; i += GLB_THREADS / 32) {
-          T* Li = L + (size_t)i * nA;
-          const T l = Li[j] * inv;
-          for (int c = lane; c < cn; c += 32) {
-            const int cc = c0 + c;
-            if (cc < nA - j - 1)
-              Li[j + 1 + cc] -= l * prow_s[c];
-            else
-              X[(size_t)i * nT + (cc - (nA - j - 1))] -= l * prow_s[c];
-          }
-          if (c0 + 1024 >= ncol) {  // last chunk: store the multiplier and update x_r
-            __syncwarp();
-            if (lane == 0) {
-              Li[j] = l;
-              xr[i] -= (double)l * xrj;
-            }
-          }
-        }
-        __syncthreads();
-      }
-    }
-    if (s_bad) {
-      if (tid == 0) {
-        atomicOr(a.status, DEV_ERR_SINGULAR);
-        atomicMin(a.status + 1, k);
-      }
-      __syncthreads();
-      continue;
-    }
-    // back substitution U x = y for the nT + 1 columns (X_B, then x_r), one thread per column
-    for (int col = tid; col <= nT; col += GLB_THREADS) {
-      for (int jj = nA - 1; jj >= 0; --jj) {
-        const T* Lr = L + (size_t)jj * nA;
-        double acc = col < nT ? (double)X[(size_t)jj * nT + col] : xr[jj];
-        for (int c = jj + 1; c < nA; ++c) acc -= (double)Lr[c] * (col < nT ? (double)X[(size_t)c * nT + col] : xr[c]);
-        acc /= (double)Lr[jj];
-        if (col < nT)
-          X[(size_t)jj * nT + col] = T(acc);
-        else
-          xr[jj] = acc;
-      }
-    }
-    __syncthreads();
-    // S = D - C X_B, t = s - C x_r
-    for (int e = tid; e < nT * (nT + 1); e += GLB_THREADS) {
-      const int row = e / (nT + 1), col = e % (nT + 1);
-      // C[row][c]: row-major C + row nA + c, column-major C + c nT + row
-      const size_t cs = cm ? (size_t)nT : 1, c0 = cm ? (size_t)row : (size_t)row * nA;
-      double acc = 0.0;
-      if (col < nT) {
-        for (int c = 0; c < nA; ++c) acc += (double)C[c0 + c * cs] * (double)X[(size_t)c * nT + col];
-        const double d = cm ? (double)D[(size_t)col * nT + row] : (double)D[(size_t)row * nT + col];
-        S[(size_t)row * nT + col] = T(d - acc);
-      } else {
-        for (int c = 0; c < nA; ++c) acc += (double)C[c0 + c * cs] * xr[c];
-        t[row] = sv[row] - acc;
-      }
-    }
-    __syncthreads();
-  }
-}
+}  // namespace hfr
+#include "hfr_bigblock.cuh"
+namespace hfr {
 
 bool uneven_fits_smem(int prec_bytes, int nA, int nT) {
   return smem_elem_bytes((size_t)prec_bytes, nA, nT) <= 227 * 1024;
@@ -2229,6 +2054,8 @@ int uneven_tables(int prec_bytes, int n, const int* nA, const int* nT, UnevenTab
       tb->smem = sb > tb->smem ? sb : tb->smem;
     } else {
       tb->global.push_back(k);
+      tb->gmax_nA = nA[k] > tb->gmax_nA ? nA[k] : tb->gmax_nA;
+      tb->gmax_nT = nT[k] > tb->gmax_nT ? nT[k] : tb->gmax_nT;
     }
   }
   auto cost = [&](int k) {
@@ -2291,6 +2118,8 @@ cudaError_t uneven_upload(const UnevenTables& tb, void* dbuf, UnevenDev* dv, cud
   dv->nb = (int)(tb.bundle.size() / 4);
   dv->nglobal = (int)tb.global.size();
   dv->smem = tb.smem;
+  dv->gmax_nA = tb.gmax_nA;
+  dv->gmax_nT = tb.gmax_nT;
   return cudaSuccess;
 }
 
@@ -2325,13 +2154,9 @@ cudaError_t launch_condense_uneven_dev(int prec_bytes, const UnevenDev& dv, cons
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (dv.nglobal > 0) {
-    int grid = 4 * nsm;
-    grid = dv.nglobal < grid ? dv.nglobal : grid;
-    if (prec_bytes == 8)
-      (hfr::count_launch(), k_condense_global<double><<<grid, GLB_THREADS, 0, st>>>(ua, dv.global, dv.nglobal, 0, 0));
-    else
-      (hfr::count_launch(), k_condense_global<float><<<grid, GLB_THREADS, 0, st>>>(ua, dv.global, dv.nglobal, 0, 0));
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = prec_bytes == 8 ? big::condense_big<double>(ua, dv.global, dv.nglobal, 0, 0, dv.gmax_nA, dv.gmax_nT, st)
+                        : big::condense_big<float>(ua, dv.global, dv.nglobal, 0, 0, dv.gmax_nA, dv.gmax_nT, st);
+    if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -2617,9 +2442,8 @@ static cudaError_t cond_global_uniform(const CondArgs& a, cudaStream_t st) {
   cudaError_t e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  const int grid = a.Eim < 4 * nsm ? a.Eim : 4 * nsm;
-  (hfr::count_launch(), k_condense_global<T><<<grid, GLB_THREADS, 0, st>>>(ua, nullptr, a.Eim, a.nA, a.nT));
-  return cudaGetLastError();
+  (void)nsm;
+  return big::condense_big<T>(ua, nullptr, a.Eim, a.nA, a.nT, a.nA, a.nT, st);
 }
 
 template <typename T>

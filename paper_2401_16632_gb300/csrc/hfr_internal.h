@@ -115,6 +115,7 @@ struct UnevenTables {
   std::vector<long long> off;
   std::vector<int> shape, order, bundle, global;
   size_t smem = 0;
+  int gmax_nA = 0, gmax_nT = 0;  // largest shape of the global-memory elements
 };
 struct UnevenDev {
   const long long* off = nullptr;
@@ -122,6 +123,7 @@ struct UnevenDev {
   int nb = 0, nglobal = 0;
   size_t smem = 0;
   int colmajor = 0;  // the blocks are stored column-major (hexahedra); all go to the global kernel
+  int gmax_nA = 0, gmax_nT = 0;
 };
 int uneven_tables(int prec_bytes, int n, const int* nA, const int* nT, UnevenTables* tb);
 size_t uneven_dev_bytes(const UnevenTables& tb);
