@@ -355,28 +355,36 @@ def tight_agreement(pkg, torch, w, ctx_mixed, ctx_fp64, dev, tol=1e-11, refines=
     return out
 
 
-def boundary_layer_leg(pkg, torch, dev, l2buf, steps=3, warmup=2, peaks=None):
-    """The boundary-layer workload (400 x 500 quads, wall-normal growth 1.15 from 1e-5, p uniform
-    random in 2..5 per element, wall below and far field above, the 20% stiffest elements
-    implicit: 40 000 elements, 3.44 M implicit DOF) on the general-mesh path: SDIRK2 stage 1 with
-    the ERK partner on the 160 000 explicit elements, Newton to 1e-8, mixed precision against FP64.
-    Rooflines of its two largest phases from their algorithmic work: the uneven condensation
-    (2/3 nA^3 + 2 nA^2 (nT + 1) + 2 nT nA (nT + 1) flop per element, FP32 FMA roof) and the trace
-    GMRES (per iteration the S_k blocks, the gathered and scattered trace values and the
-    orthogonalisation, HBM roof)."""
-    from workloads import make_config
-
-    w = make_config("boundary_layer")
-    peaks = peaks or {}
-    out = {"workload": "boundary_layer: 2D Navier-Stokes Re=1.7e6 M=0.2, 400x500 quads, wall-normal growth 1.15 from "
+GENERAL_WORKLOADS = {
+    "boundary_layer": ("boundary_layer: 2D Navier-Stokes Re=1.7e6 M=0.2, 400x500 quads, wall-normal growth 1.15 from "
                        "1e-5 to isotropic 1e-2 (aspect ratio to 1e3), p uniform random in 2..5 per element (seed 2024), "
                        "wall below, far field above, 20% stiffest elements implicit (40 000), SDIRK2 stage 1 with the "
-                       "ERK partner, Newton to 1e-8",
-           "implicit_dofs": w.dofs_implicit, "elements": w.mesh.nelem}
+                       "ERK partner, Newton to 1e-8"),
+    "channel3d": ("channel3d: 3D Navier-Stokes Re=1.6e3 M=0.1 Taylor-Green-like field, 64x32x48 hexahedra, tanh "
+                  "clustering beta=2.5, walls at y=+-1, periodic x and z, p=3 (blocks 320 / 480), three implicit wall "
+                  "layers per wall (18 432 elements), SDIRK2 stage 1 with the ERK partner, Newton to 1e-8"),
+}
+
+
+def general_leg(pkg, torch, dev, l2buf, name, steps=(3, 2), warmup=(2, 1), peaks=None, paths=("mixed", "fp64")):
+    """A workload of the general-mesh path (boundary_layer: mixed degree, wall, far field; channel3d:
+    hexahedra with walls), mixed precision against FP64, each stage timed with CUDA events (steps /
+    warm-ups per path as given).  Rooflines of its two largest phases from their algorithmic work:
+    the condensation (2/3 nA^3 + 2 nA^2 (nT + 1) + 2 nT nA (nT + 1) flop per element, FP32 FMA
+    roof) and the trace GMRES (per iteration the S_k blocks, the gathered and scattered trace values
+    and the orthogonalisation, HBM roof)."""
+    from workloads import make_config
+
+    w = make_config(name)
+    peaks = peaks or {}
+    out = {"workload": GENERAL_WORKLOADS[name], "implicit_dofs": w.dofs_implicit, "elements": w.mesh.nelem}
     res = {}
-    for label, prec in (("mixed", pkg.FR_PREC_FP32), ("fp64", pkg.FR_PREC_FP64)):
+    for pi, (label, prec) in enumerate((("mixed", pkg.FR_PREC_FP32), ("fp64", pkg.FR_PREC_FP64))):
+        if label not in paths:
+            continue
         ctx = pkg.Context(w.mesh, w.physics, precision=prec, tableau=pkg.FR_TAB_SDIRK2)
-        u_n = torch.tensor(ctx.pack_state(w.u0), device=dev)
+        u0 = w.u0 if isinstance(w.u0, list) else list(w.u0)
+        u_n = torch.tensor(ctx.pack_state(u0), device=dev)
         uh0 = ctx.hfr_initial_trace(u_n)
         R_hist = ctx.empty(3, *ctx.state_shape)
         us = ctx.empty(*ctx.state_shape)
@@ -388,13 +396,13 @@ def boundary_layer_leg(pkg, torch, dev, l2buf, steps=3, warmup=2, peaks=None):
             return ctx.imex_stage(1, w.dt, u_n, us, uh, R_hist, newton_tol=NEWTON_TOL, newton_maxit=30,
                                   gmres_rtol=GMRES_RTOL, gmres_maxit=20000)
 
-        for _ in range(warmup):
+        for _ in range(warmup[pi]):
             st = run()
         torch.cuda.synchronize()
         ctx.fr_profile_enable(True)
         l0 = ctx.kernel_launches()
         times = []
-        for _ in range(steps):
+        for _ in range(steps[pi]):
             flush_l2(l2buf)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -405,11 +413,17 @@ def boundary_layer_leg(pkg, torch, dev, l2buf, steps=3, warmup=2, peaks=None):
             times.append(e0.elapsed_time(e1))
         prof = ctx.fr_profile_read()
         ctx.fr_profile_enable(False)
-        res[label] = {"ms": float(np.mean(times)), "stats": st, "prof": prof,
-                      "launches": (ctx.kernel_launches() - l0) // steps, "u": (us - u_n).clone(),
+        res[label] = {"ms": float(np.mean(times)), "stats": st, "prof": prof, "steps": steps[pi],
+                      "launches": (ctx.kernel_launches() - l0) // steps[pi], "u": (us - u_n).clone(),
                       "nA": ctx.blk_nA.astype(np.float64), "nT": ctx.blk_nT.astype(np.float64),
                       "nh": int(ctx.info.trace_values)}
         ctx.close()
+        del R_hist, us, uh0, u_n
+        torch.cuda.empty_cache()
+    if "fp64" not in res:  # profiling aid: the mixed path alone
+        m = res["mixed"]
+        return {"workload": out["workload"], "ms": m["ms"], "stats": m["stats"], "launches": m["launches"],
+                "phases_ms_total": {k: round(v[0], 3) for k, v in m["prof"].items()}}
     m, f = res["mixed"], res["fp64"]
     inc = f["u"].abs().max().item()
     nA, nT = m["nA"], m["nT"]
@@ -424,18 +438,20 @@ def boundary_layer_leg(pkg, torch, dev, l2buf, steps=3, warmup=2, peaks=None):
     alg = k_its * float(np.sum(nT * nT) * 4 + np.sum(nT) * 2 * 8) + sum((k + 2) * m["nh"] * 8 for k in range(1, k_its + 1))
     g_a = alg / (gms / max(gcnt, 1) * 1e-3) / 1e9
     hbm = float(peaks.get("hbm_gbs", 6800.0))
+    cond_kernel = ("k_big_lu + k_big_trsm_diag + k_big_gemm + k_big_xr (global-memory LU, batched GEMMs)"
+                   if name == "channel3d" else "k_condense_uneven<float> (shared-memory Gauss-Jordan bundles)")
     out.update({
         "value": w.dofs_implicit / (m["ms"] * 1e-3), "unit": "implicit-stage DOF/s", "ms_per_step": m["ms"],
-        "newton_iterations": m["stats"]["newton_iterations"], "gmres_iterations": m["stats"]["gmres_iterations"],
-        "gpu_launches": int(m["launches"]),
-        "fp64": {"value": w.dofs_implicit / (f["ms"] * 1e-3), "ms_per_step": f["ms"],
+        "steps": m["steps"], "newton_iterations": m["stats"]["newton_iterations"],
+        "gmres_iterations": m["stats"]["gmres_iterations"], "gpu_launches": int(m["launches"]),
+        "fp64": {"value": w.dofs_implicit / (f["ms"] * 1e-3), "ms_per_step": f["ms"], "steps": f["steps"],
                  "newton_iterations": f["stats"]["newton_iterations"], "gmres_iterations": f["stats"]["gmres_iterations"],
                  "phases_ms_total": {k: round(v[0], 3) for k, v in f["prof"].items()}},
         "mixed_over_fp64": f["ms"] / m["ms"],
         "mixed_vs_fp64_max_rel_diff": (m["u"] - f["u"]).abs().max().item() / inc,
         "phases_ms_total": {k: round(v[0], 3) for k, v in m["prof"].items()},
         "rooflines": {
-            "condense": {"kernel": "k_condense_uneven<float>", "bound": "alu", "achieved": cond_a, "peak": fp32,
+            "condense": {"kernel": cond_kernel, "bound": "alu", "achieved": cond_a, "peak": fp32,
                          "unit": "TFLOP/s", "frac": cond_a / fp32, "avg_launch_ms": ms / max(cnt, 1),
                          "algorithmic_flop": flop},
             "gmres": {"kernel": "multi-kernel GMRES cycle (k_gen_matvec_elem, k_gen_gather_sum, k_gen_precond_apply, k_cgs)",
@@ -501,6 +517,13 @@ NCU_TRAFFIC_BYTES = {"vortex256": {"k_inverse_tc": 16 * (165.51e6 + 109.29e6),
                      "vortex64": {}}
 
 
+# DRAM bytes (read + write) of k_gmres_cycle<float, 80, 20> per element and GMRES iteration, from
+# one ncu capture of the three cycle launches of a vortex128p4 stage (16 384 elements, 60 GMRES
+# iterations, 31.28 GB in all; profiles/vortex128p4_gmres_cycle_traffic.md), keyed by nT; a full
+# launch is that times its elements and iterations (the cycle's traffic grows with both)
+GMRES_TRAFFIC_PER_ELEM_ITER = {80: (30827120896 + 452353536) / (16384 * 60)}
+
+
 def kernel_rooflines(prof, stats, w, peaks, clocks, workload, cond_mode=2):
     """Roofline of every single-kernel phase of the timed step, from the live CUDA-event phase
     timings (average launch duration), and the dominant one (largest total time).
@@ -554,6 +577,8 @@ def kernel_rooflines(prof, stats, w, peaks, clocks, workload, cond_mode=2):
     # (ntrace bs^2 4 B per iteration) and the deferred second Gram-Schmidt pass over the FP32 basis
     extra = k_its * ntrace * bs * bs * 4 + sum((k + 1) * nt_u * 4 for k in range(1, k_its + 1))
     out["gmres"] = entry("k_gmres_cycle", "hbm", alg / (a * 1e-3) / 1e9, hbm_peak, "GB/s", tot, a)
+    per = GMRES_TRAFFIC_PER_ELEM_ITER.get(nT)
+    out["gmres"]["traffic"] = per * E * k_its if per else None
     out["gmres"]["iterations_per_launch"] = k_its
     out["gmres"]["algorithmic_bytes"] = alg
     out["gmres"]["implementation_extra_bytes"] = extra
@@ -596,6 +621,9 @@ def main():
     ap.add_argument("--no-uneven", action="store_true", help="skip the uneven-degree condensation leg")
     ap.add_argument("--no-reuse", action="store_true", help="skip the Jacobian-reuse (imex_steps) leg")
     ap.add_argument("--no-tf32", action="store_true", help="skip the single-pass TF32 condensation leg")
+    ap.add_argument("--no-channel", action="store_true", help="skip the hexahedral channel leg")
+    ap.add_argument("--general-only", default=None, choices=list(GENERAL_WORKLOADS),
+                    help="profiling aid: time only this general-mesh workload's mixed path")
     ap.add_argument("--no-boundary-layer", action="store_true",
                     help="skip the boundary-layer (mixed degree, walls, far field) leg")
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16 trace-operator leg")
@@ -631,6 +659,10 @@ def main():
         w = make_config(args.workload)
     l2buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB
     pipe_peaks = measure_pipe_peaks(pkg)
+    if args.general_only:  # profiling aid: one general-mesh workload, mixed path, no JSON contract line
+        print(json.dumps(general_leg(pkg, torch, dev, l2buf, args.general_only, steps=(args.steps, 0),
+                                     warmup=(args.warmup, 0), paths=("mixed",))))
+        return
     if args.paths != "both":  # profiling aid: one path, no JSON contract line
         prec = pkg.FR_PREC_FP32 if args.paths == "mixed" else pkg.FR_PREC_FP64
         r = time_path(pkg, torch, w, prec, args.refine if args.paths == "mixed" else 0, args.steps, args.warmup,
@@ -771,11 +803,21 @@ def main():
             line["jacobian_reuse"] = jacobian_reuse(pkg, torch, mixed["ctx"], w, dev)
         except Exception as exc:  # reported, never fatal
             line["jacobian_reuse"] = {"error": str(exc)}
+    # the vortex256 contexts are done: release their device memory before the general-mesh legs
+    for r in (mixed, fp64, tf32, bf16, graph):
+        if isinstance(r, dict) and r.get("ctx") is not None:
+            r["ctx"].close()
+    torch.cuda.empty_cache()
     if not args.no_boundary_layer:
         try:
-            line["boundary_layer"] = boundary_layer_leg(pkg, torch, dev, l2buf, peaks=peaks)
+            line["boundary_layer"] = general_leg(pkg, torch, dev, l2buf, "boundary_layer", peaks=peaks)
         except Exception as exc:  # reported, never fatal
             line["boundary_layer"] = {"error": str(exc)}
+    if not args.no_channel:
+        try:
+            line["channel3d"] = general_leg(pkg, torch, dev, l2buf, "channel3d", steps=(2, 1), warmup=(1, 1), peaks=peaks)
+        except Exception as exc:  # reported, never fatal
+            line["channel3d"] = {"error": str(exc)}
     if not args.no_uneven:
         try:
             line["uneven_condense"] = uneven_condense(pkg, torch, dev)

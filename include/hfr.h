@@ -81,6 +81,18 @@ enum fr_tableau { FR_TAB_BE = 0, FR_TAB_SDIRK2 = 1 };
 
 typedef struct fr_ctx fr_ctx;
 
+/* Trace space of the hybridized elements (Sec. 2.2).  FR_TRACE_HFR: a discontinuous trace per face,
+ * at the face's Gauss points.  FR_TRACE_EFR (interior-embedded FR): on interior trace faces the
+ * trace is continuous, with nodes at the Gauss-Lobatto points of the faces (vertex nodes shared by
+ * every trace face meeting there); each side evaluates its state, gradient, one-sided flux and J_f
+ * at those points, and the values of J_f F^.n and of u^ - u_f are interpolated to the element's
+ * Gauss-aligned face points for the lift; the transmission condition of a node sums w^GLL J_f F^.n
+ * over every face and side that carries it; boundary faces keep discontinuous traces at their
+ * Gauss points.  EFR runs on the general path (quadrilaterals, one degree); its trace vector holds
+ * one node per unit (fr_ctx_layout: ntrace = nodes) in the numbering of efr_trace_nodes, and its
+ * GMRES preconditioner is node-block Jacobi (nv x nv blocks: the nodes' blocks overlap faces). */
+enum fr_trace_kind { FR_TRACE_HFR = 0, FR_TRACE_EFR = 1 };
+
 /* Boundary tags of fr_mesh_desc.bc (where nbr < 0). */
 enum fr_boundary { FR_BC_WALL = 1, FR_BC_FARFIELD = 2 };
 /* Element types of fr_mesh_desc.elem_type.  FR_ELEM_HEX (the paper's 3D runs, Sec. 5.3; Navier-Stokes
@@ -129,6 +141,7 @@ typedef struct {
   int gmres_restart; /* m <= 64 */
   double theta;    /* EDAC: 1 / M^2 of the artificial Mach number */
   double u_inf[5]; /* free-stream state of far-field faces (conserved variables) */
+  int trace_kind;  /* fr_trace_kind */
 } fr_config;
 
 /* Sizes of a context.  Uniform path: as named.  General path: p, n, ns the largest degree and its
@@ -431,22 +444,28 @@ const char* fr_status_string(int code);
 
 /* Trace-node layout of the interior-embedded variant EFR (Sec. 2.2: the trace is continuous on
  * the implicit skeleton, with nodes at the p + 1 Gauss-Lobatto points of every trace face; a
- * face's end points are the mesh vertices it shares with the other trace faces meeting there).
- * Host only: needs no device and no context.
- *   nbr, nbr_face, face_of  host, (nelem, 4) each: neighbour element, its local face, global
- *                           face id (the mesh arrays of fr_mesh_desc); all elements share one
- *                           orientation, so the first point of a face meets the neighbour's first
+ * face's end points are the mesh vertices it shares with the other trace faces meeting there;
+ * boundary faces keep discontinuous traces).  Host only: needs no device and no context.
+ *   nbr, nbr_face, face_of  host, (nelem, 4) each: neighbour element (-1 on a boundary), its local
+ *                           face, global face id (the mesh arrays of fr_mesh_desc); all elements
+ *                           share one orientation, so the first point of a face meets the
+ *                           neighbour's first
+ *   bc                      host, (nelem, 4), nullable: FR_BC_WALL / FR_BC_FARFIELD where nbr < 0
+ *                           (required when the mesh has boundary faces)
  *   implicit                host, (nelem,): nonzero for implicit elements; a trace face has both
  *                           sides implicit
- *   node_of                 host, (nelem, 4, p + 1) out: the node at each Gauss-Lobatto point of
- *                           each element face, -1 on faces without a trace.  Vertex nodes first,
- *                           in increasing smallest element corner 4 e + c of the vertex (corner
- *                           c = a + 2 b), then the interior points m = 1..p-1 of trace face t
- *                           (trace faces in increasing global face id) at nvert + t (p - 1) + m - 1
+ *   node_of                 host, (nelem, 4, p + 1) out: the node at each point of each element
+ *                           face, -1 on faces without a trace.  Vertex nodes first, in increasing
+ *                           smallest element corner 4 e + c of the vertex (corner c = a + 2 b), then
+ *                           the interior Gauss-Lobatto points m = 1..p-1 of trace face t (trace faces
+ *                           in increasing global face id) at nvert + t (p - 1) + m - 1, then the
+ *                           p + 1 Gauss points of each boundary face of an implicit element (in
+ *                           increasing global face id) at nvert + ntrace (p - 1) + b (p + 1) + m
  *   nvert_out, nnode_out    host out: vertex nodes and all nodes
- * Errors: FR_ERR_INVALID_ARG (null pointer, nelem <= 0, p outside 1..5, indices out of range or a
- * neighbour relation that is not symmetric), FR_ERR_UNSUPPORTED (boundary faces). */
-int efr_trace_nodes(int nelem, const int* nbr, const int* nbr_face, const int* face_of,
+ * Errors: FR_ERR_INVALID_ARG (null pointer, nelem <= 0, p outside 1..5, indices out of range, a
+ * neighbour relation that is not symmetric, a boundary tag that is neither wall nor far field),
+ * FR_ERR_UNSUPPORTED (boundary faces without bc). */
+int efr_trace_nodes(int nelem, const int* nbr, const int* nbr_face, const int* face_of, const int* bc,
                     const unsigned char* implicit, int p, int* node_of, int* nvert_out, int* nnode_out);
 
 /* Trace layout of a quad mesh whose elements carry different degrees p_e (Sec. 3.2: the element

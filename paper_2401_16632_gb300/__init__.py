@@ -31,6 +31,7 @@ FR_TAB_BE, FR_TAB_SDIRK2 = 0, 1
 FR_PHYS_ADVDIFF, FR_PHYS_NAVIER_STOKES, FR_PHYS_EDAC = 0, 1, 2
 FR_GMRES_MULTI, FR_GMRES_FUSED = 0, 1
 FR_BC_WALL, FR_BC_FARFIELD = 1, 2
+FR_TRACE_HFR, FR_TRACE_EFR = 0, 1
 FR_ELEM_QUAD, FR_ELEM_HEX = 0, 1
 FR_JAC_EVERY_NEWTON, FR_JAC_ONCE_PER_STAGE, FR_JAC_KEEP = 0, 1, 2
 FR_CONDENSE_FMA, FR_CONDENSE_TENSOR_PRODUCTS, FR_CONDENSE_TENSOR, FR_CONDENSE_TENSOR_TF32 = 0, 1, 2, 3
@@ -111,6 +112,7 @@ class fr_config(ctypes.Structure):
         ("gmres_restart", ctypes.c_int),
         ("theta", ctypes.c_double),
         ("u_inf", ctypes.c_double * 5),
+        ("trace_kind", ctypes.c_int),
     ]
 
 
@@ -233,7 +235,7 @@ def load_library(path: str = LIB_PATH):
     lib.fr_last_error.argtypes = [vp, ctypes.POINTER(fr_error_info)]
     lib.fr_status_string.argtypes = [ctypes.c_int]
     lib.fr_status_string.restype = ctypes.c_char_p
-    lib.efr_trace_nodes.argtypes = [ctypes.c_int, vp, vp, vp, vp, ctypes.c_int, vp, ip, ip]
+    lib.efr_trace_nodes.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, ctypes.c_int, vp, ip, ip]
     lib.mixed_trace_layout.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp, ip]
     _lib = lib
     return lib
@@ -249,7 +251,7 @@ class HfrError(RuntimeError):
         super().__init__(msg)
 
 
-def efr_trace_nodes(nbr, nbr_face, face_of, implicit, p):
+def efr_trace_nodes(nbr, nbr_face, face_of, implicit, p, bc=None):
     """EFR trace-node layout of a quad mesh (host arrays in, host arrays out): (node_of (E, 4, p+1)
     int32, nvert, nnode).  Raises HfrError on the library's error codes."""
     import numpy as np
@@ -267,8 +269,12 @@ def efr_trace_nodes(nbr, nbr_face, face_of, implicit, p):
         raise ValueError("efr_trace_nodes: implicit must have shape (E,)")
     out = np.empty((E, 4, max(int(p), 0) + 1), dtype=np.int32)
     nvert, nnode = ctypes.c_int(), ctypes.c_int()
-    rc = lib.efr_trace_nodes(E, nbr.ctypes.data, nbr_face.ctypes.data, face_of.ctypes.data, imp.ctypes.data,
-                             int(p), out.ctypes.data, ctypes.byref(nvert), ctypes.byref(nnode))
+    bca = None if bc is None else np.ascontiguousarray(bc, dtype=np.int32)
+    if bca is not None and bca.shape != (E, 4):
+        raise ValueError("efr_trace_nodes: bc must have shape (E, 4)")
+    rc = lib.efr_trace_nodes(E, nbr.ctypes.data, nbr_face.ctypes.data, face_of.ctypes.data,
+                             None if bca is None else bca.ctypes.data, imp.ctypes.data, int(p), out.ctypes.data,
+                             ctypes.byref(nvert), ctypes.byref(nnode))
     if rc != 0:
         raise HfrError(rc)
     return out, nvert.value, nnode.value
@@ -383,7 +389,7 @@ class Context:
     """
 
     def __init__(self, mesh, physics: dict, precision: int = FR_PREC_FP64, tableau: int = FR_TAB_SDIRK2,
-                 gmres_restart: int = 30, stream=None):
+                 gmres_restart: int = 30, stream=None, trace_kind: int = FR_TRACE_HFR):
         import torch
 
         self.torch = torch
@@ -392,7 +398,8 @@ class Context:
         p = int(degs[0])
         E = int(mesh.verts.shape[0])
         self.hex = int(getattr(mesh, "dim", 2)) == 3
-        general = bool(np.any(degs != p)) or bool(np.any(np.asarray(mesh.nbr) < 0)) or self.hex
+        general = (bool(np.any(degs != p)) or bool(np.any(np.asarray(mesh.nbr) < 0)) or self.hex
+                   or trace_kind == FR_TRACE_EFR)
         self._deg = np.ascontiguousarray(np.broadcast_to(degs, (E,)), dtype=np.int32)
         bc = getattr(mesh, "bc", None)
         self._bc = np.ascontiguousarray(bc if bc is not None else np.zeros_like(np.asarray(mesh.nbr)), dtype=np.int32)
@@ -429,6 +436,7 @@ class Context:
             for i, x in enumerate(ui[:5]):
                 cfg.u_inf[i] = float(x)
         cfg.precision = precision
+        cfg.trace_kind = trace_kind
         cfg.tableau = tableau
         cfg.gmres_restart = gmres_restart
         self.stream = stream if stream is not None else torch.cuda.current_stream()

@@ -391,12 +391,13 @@ static inline unsigned nblk(size_t n, int t = 256) { return (unsigned)((n + t - 
 
 // ------------------------------------------------------------------------ context
 extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, const fr_config* cfg, void* stream, fr_ctx** out) {
+  FR_NVTX("fr_ctx_create");
   if (!mesh || !cfg || !out) return FR_ERR_INVALID_ARG;
   *out = nullptr;
   if (mesh->nelem <= 0 || !mesh->verts || !mesh->nbr || !mesh->nbr_face || !mesh->face_of || !mesh->implicit)
     return FR_ERR_INVALID_ARG;
   if (mesh->elem_type != FR_ELEM_QUAD && mesh->elem_type != FR_ELEM_HEX) return FR_ERR_UNSUPPORTED;
-  if (hfr::gen::mesh_is_general(mesh)) {
+  if (hfr::gen::mesh_is_general(mesh) || cfg->trace_kind == FR_TRACE_EFR) {
     fr_ctx* ctx = new fr_ctx();
     memset(&ctx->err, 0, sizeof(ctx->err));
     ctx->stream = (cudaStream_t)stream;
@@ -424,6 +425,7 @@ extern "C" int fr_ctx_create(const fr_mesh_desc* mesh, const fr_config* cfg, voi
   if (mesh->p_elem) um.p = mesh->p_elem[0];
   mesh = &um;
   if (mesh->p < 1 || mesh->p > 5) return FR_ERR_UNSUPPORTED;
+  if (cfg->trace_kind != FR_TRACE_HFR) return FR_ERR_INVALID_ARG;
   if (cfg->physics != FR_PHYS_ADVDIFF && cfg->physics != FR_PHYS_NAVIER_STOKES && cfg->physics != FR_PHYS_EDAC)
     return FR_ERR_INVALID_ARG;
   if (cfg->physics == FR_PHYS_ADVDIFF && mesh->p > 3) return FR_ERR_UNSUPPORTED;
@@ -741,6 +743,7 @@ static int residual_into(fr_ctx* ctx, const double* u, const double* uhat, doubl
 }
 
 extern "C" int fr_residual(fr_ctx* ctx, const double* u, const double* uhat, double* R, double* g) {
+  FR_NVTX("fr_residual");
   if (!ctx || !u || !R) return set_err(ctx, FR_ERR_INVALID_ARG, "fr_residual: null argument");
   if (ctx->ntrace > 0 && !uhat) return set_err(ctx, FR_ERR_INVALID_ARG, "fr_residual: uhat required");
   if (ctx->gen) {
@@ -756,6 +759,7 @@ extern "C" int fr_residual(fr_ctx* ctx, const double* u, const double* uhat, dou
 }
 
 extern "C" int hfr_initial_trace(fr_ctx* ctx, const double* u, double* uhat) {
+  FR_NVTX("hfr_initial_trace");
   if (!ctx || !u || (ctx->ntrace > 0 && !uhat)) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_initial_trace: null argument");
   if (ctx->gen) return hfr::gen::initial_trace(ctx->gen, u, uhat);
   // face states of every element into a scratch buffer of the same shape (E x 4n x nv)
@@ -814,6 +818,7 @@ static int form_rhs(fr_ctx* ctx, const double* u, const double* ustar, double a_
 
 extern "C" int hfr_local_jacobian(fr_ctx* ctx, const double* u, const double* uhat, const double* ustar,
                                   double a_dt) {
+  FR_NVTX("hfr_local_jacobian");
   if (!ctx || !u || (ctx->ntrace > 0 && !uhat)) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_local_jacobian: null argument");
   if (ctx->gen) {
     const int grc = hfr::gen::local_jacobian(ctx->gen, u, uhat, ustar, a_dt);
@@ -979,6 +984,7 @@ static int condense_rhs_impl(fr_ctx* ctx) {
 }
 
 extern "C" int hfr_condense(fr_ctx* ctx, int refine) {
+  FR_NVTX("hfr_condense");
   if (!ctx) return FR_ERR_INVALID_ARG;
   if (ctx->gen) {
     const int grc = hfr::gen::condense(ctx->gen, refine);
@@ -1124,6 +1130,7 @@ static int autotune_uniform(fr_ctx* ctx, const double* u, const double* uhat, co
                             fr_tune_report* out);
 extern "C" int hfr_autotune(fr_ctx* ctx, const double* u, const double* uhat, const double* ustar, double a_dt,
                             fr_tune_report* out) {
+  FR_NVTX("hfr_autotune");
   NOT_GENERAL(ctx, "hfr_autotune");
   return autotune_uniform(ctx, u, uhat, ustar, a_dt, out);
 }
@@ -1295,6 +1302,7 @@ static void modal_filter_operator(int p, double alpha, double s, int eta_c, doub
 }
 
 extern "C" int fr_modal_filter(fr_ctx* ctx, double* u, double alpha, double s, int eta_c, double dt_ratio, int which) {
+  FR_NVTX("fr_modal_filter");
   NOT_GENERAL(ctx, "fr_modal_filter");
   if (!ctx || !u || !(alpha >= 0.0) || !(s > 0.0) || eta_c < 0 || !(dt_ratio > 0.0) || which < 0 || which > 2)
     return set_err(ctx, FR_ERR_INVALID_ARG, "fr_modal_filter: bad argument");
@@ -1322,6 +1330,7 @@ extern "C" int hfr_condense_uneven(int nelem, const int* nA, const int* nT, int 
                                    const void* C, const void* D, const double* r, const double* s, void* LU, int* piv,
                                    void* XB, double* xr, void* S, double* t, int* status, void* stream,
                                    int* failed_element) {
+  FR_NVTX("hfr_condense_uneven");
   if (failed_element) *failed_element = -1;
   if (nelem < 0 || (nelem > 0 && (!nA || !nT || !A || !B || !C || !D || !r || !s || !LU || !piv || !XB || !xr || !S ||
                                   !t || !status)) ||
@@ -1361,6 +1370,7 @@ extern "C" int fr_barrier_selftest(int nblocks, int absent_block, int rounds, do
 }
 
 extern "C" int hfr_trace_gmres(fr_ctx* ctx, double* duhat, double rtol, int maxit, int* iters, double* final_rel) {
+  FR_NVTX("hfr_trace_gmres");
   if (ctx && ctx->gen) {
     if (!duhat) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_trace_gmres: null argument");
     const int grc = hfr::gen::trace_gmres(ctx->gen, duhat, rtol, maxit, iters, final_rel);
@@ -1385,6 +1395,7 @@ static int backsolve_impl(fr_ctx* ctx, const double* duhat, double* du, int refi
 }
 
 extern "C" int hfr_backsolve(fr_ctx* ctx, const double* duhat, double* du, int refine) {
+  FR_NVTX("hfr_backsolve");
   if (ctx && ctx->gen) {
     if (!du || (ctx->ntrace > 0 && !duhat)) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_backsolve: null argument");
     const int grc = hfr::gen::backsolve(ctx->gen, duhat, du, refine);
@@ -1806,6 +1817,7 @@ extern "C" int imex_stage_get_graph(const fr_ctx* ctx) { return ctx ? ctx->use_g
 extern "C" int imex_stage(fr_ctx* ctx, int stage, double dt, const double* u_n, double* u_stage, double* uhat,
                           double* R_hist, double newton_tol, int newton_maxit, double gmres_rtol, int gmres_maxit,
                           int refine, fr_stage_stats* stats) {
+  FR_NVTX("imex_stage");
   if (!ctx || !u_n || !u_stage || !R_hist || (ctx->ntrace > 0 && !uhat))
     return set_err(ctx, FR_ERR_INVALID_ARG, "imex_stage: null argument");
   if (ctx->gen) {
@@ -1950,6 +1962,7 @@ extern "C" int imex_stage(fr_ctx* ctx, int stage, double dt, const double* u_n, 
 extern "C" int imex_steps(fr_ctx* ctx, int nsteps, double dt, double* u, double* uhat, double* R_hist,
                           double* u_stage, int refresh_every, double newton_tol, int newton_maxit,
                           double gmres_rtol, int gmres_maxit, int refine, fr_steps_stats* stats) {
+  FR_NVTX("imex_steps");
   if (!ctx || !u || !R_hist || !u_stage || (ctx->ntrace > 0 && !uhat) || nsteps < 0 || !(dt > 0.0))
     return set_err(ctx, FR_ERR_INVALID_ARG, "imex_steps: bad argument");
   const Tab tb = tableau(ctx->tableau);

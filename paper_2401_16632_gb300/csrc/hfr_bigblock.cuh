@@ -1,25 +1,35 @@
 // Condensation of element blocks too large for one CTA's shared memory (FP64 p = 5 quadrilaterals,
 // hexahedra: nA = 320, nT = 480), as a sequence of batched kernels over all such elements:
-//   1. LU with partial pivoting of A in place (one CTA per element, rank-1 updates in L2-resident
-//      global memory; largest |a|, lowest row on ties);
+//   1. blocked right-looking LU with partial pivoting of A in place, panel by panel of LB columns:
+//      the panel (all its rows) factorised in shared memory by one CTA per element (largest |a|,
+//      lowest row on ties), its row interchanges applied to the columns left and right of it and
+//      the block row right of it solved with the panel's unit lower triangle (same kernel); then
+//      the trailing matrix updated by the batched GEMM;
 //   2. X = P [B] (the row interchanges applied to the right-hand sides);
 //   3. forward substitution with the unit lower factor and back substitution with the upper factor,
 //      both blocked by NB rows: a small triangular solve of the diagonal block (one thread per
 //      right-hand side column), then the rest of the rows updated by a batched GEMM;
 //   4. S = D - C X_B by the same batched GEMM;
 //   5. x_r = A^{-1} r and t = s - C x_r in FP64 arithmetic (one CTA per element).
-// The batched GEMM is a register-tiled CUDA-core kernel: 64 x 64 output tiles, 256 threads with
-// 4 x 4 outputs each, K staged through shared memory 16 at a time; arithmetic in the block
-// precision T.  Included by hfr_condense.cu (uses UnevenArgs and DEV_ERR_*).
+// The batched GEMM is a register-tiled CUDA-core kernel: 128 x 128 output tiles in FP32 (64 x 64 in
+// FP64), 256 threads with 8 x 8 (4 x 4) outputs each, K staged through two shared-memory buffers 8
+// at a time; arithmetic in the block precision T.  Included by hfr_condense.cu (uses UnevenArgs and DEV_ERR_*).
 #pragma once
 
 namespace hfr {
 namespace big {
 
 constexpr int NB = 32;       // rows per diagonal block of the triangular solves
-constexpr int GT = 64;       // GEMM output tile
-constexpr int GK = 16;       // GEMM K chunk
 constexpr int BT = 256;      // threads per CTA
+// LU panel width: the panel of up to 1024 rows stays in shared memory (128 KB at most)
+template <typename T>
+__host__ __device__ constexpr int lu_panel() {
+  return sizeof(T) == 8 ? 16 : 32;
+}
+template <typename T>
+size_t lu_panel_smem(int max_nA) {
+  return (size_t)max_nA * (lu_panel<T>() + 1) * sizeof(T);
+}
 
 // element of list position li: its id, five offsets and shape (tables, or one uniform shape)
 struct Elem {
@@ -46,77 +56,139 @@ __device__ __forceinline__ Elem elem_of(const UnevenArgs& a, const int* list, in
   return e;
 }
 
-// 1. LU factors in the LU slot (A copied in, transposed when stored column-major), pivots
+// 1a. A copied into the LU slot (transposed when stored column-major); identity pivots
 template <typename T>
-__global__ void __launch_bounds__(BT) k_big_lu(const __grid_constant__ UnevenArgs a, const int* __restrict__ list,
-                                               int nlist, int uni_nA, int uni_nT) {
-  __shared__ T prow[1024];
-  __shared__ double pkey_v[BT / 32];
-  __shared__ int pkey_i[BT / 32];
-  __shared__ int s_piv, s_bad;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+__global__ void __launch_bounds__(BT) k_big_lu_init(const __grid_constant__ UnevenArgs a, const int* __restrict__ list,
+                                                    int nlist, int uni_nA, int uni_nT) {
   for (int li = blockIdx.x; li < nlist; li += gridDim.x) {
     const Elem E = elem_of(a, list, li, uni_nA, uni_nT);
     const int nA = E.nA;
     const T* A = reinterpret_cast<const T*>(a.A) + E.o[0];
     T* L = reinterpret_cast<T*>(a.LU) + E.o[0];
-    int* piv = a.piv + E.o[3];
     const bool cm = a.colmajor != 0;
-    for (size_t i = tid; i < (size_t)nA * nA; i += BT) L[i] = cm ? A[(i % nA) * nA + i / nA] : A[i];
+    for (size_t i = threadIdx.x; i < (size_t)nA * nA; i += BT) L[i] = cm ? A[(i % nA) * nA + i / nA] : A[i];
+    for (int i = threadIdx.x; i < nA; i += BT) a.piv[E.o[3] + i] = i;
+  }
+}
+
+// 1b. panel jb (columns [j0, j0 + w), rows [j0, nA)) of every element: factorised in shared memory
+// (row stride LB + 1), pivots recorded as global rows, the interchanges applied to the other
+// columns, and the block row U12 = L11^{-1} A12 right of the panel solved (one thread per column)
+template <typename T>
+__global__ void __launch_bounds__(BT) k_big_lu_panel(const __grid_constant__ UnevenArgs a, const int* __restrict__ list,
+                                                     int nlist, int uni_nA, int uni_nT, int jb) {
+  constexpr int LB = lu_panel<T>(), PS = LB + 1;
+  extern __shared__ __align__(16) unsigned char lu_smem[];
+  T* P = reinterpret_cast<T*>(lu_smem);
+  __shared__ T rkey_v[BT / 32];
+  __shared__ int rkey_i[BT / 32];
+  __shared__ int spiv[LB];
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int li = blockIdx.x; li < nlist; li += gridDim.x) {
+    const Elem E = elem_of(a, list, li, uni_nA, uni_nT);
+    const int nA = E.nA, j0 = jb * LB;
+    if (j0 >= nA) continue;  // uniform over the CTA
+    const int w = min(LB, nA - j0), R = nA - j0;
+    T* L = reinterpret_cast<T*>(a.LU) + E.o[0];
+    int* piv = a.piv + E.o[3];
+    __syncthreads();  // the previous element's panel is free
+    for (int i = tid; i < R * w; i += BT) {
+      const int r = i / w, c = i % w;
+      P[r * PS + c] = L[(size_t)(j0 + r) * nA + j0 + c];
+    }
     if (tid == 0) s_bad = 0;
     __syncthreads();
-    for (int j = 0; j < nA; ++j) {
-      double bv = -1.0;
+    for (int c = 0; c < w; ++c) {
+      T bv = T(-1);
       int bi = 0x7fffffff;
-      for (int i = j + tid; i < nA; i += BT) {
-        const double v = fabs((double)L[(size_t)i * nA + j]);
-        if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+      for (int r = c + tid; r < R; r += BT) {
+        const T v = fabs(P[r * PS + c]);
+        if (v > bv || (v == bv && r < bi)) {
+          bv = v;
+          bi = r;
+        }
       }
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, bv, off);
+        const T ov = __shfl_xor_sync(0xffffffffu, bv, off);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+        if (ov > bv || (ov == bv && oi < bi)) {
+          bv = ov;
+          bi = oi;
+        }
       }
-      if (lane == 0) { pkey_v[wid] = bv; pkey_i[wid] = bi; }
+      if (lane == 0) {
+        rkey_v[wid] = bv;
+        rkey_i[wid] = bi;
+      }
       __syncthreads();
       if (tid == 0) {
-        double v = pkey_v[0];
-        int ii = pkey_i[0];
+        T v = rkey_v[0];
+        int ii = rkey_i[0];
         for (int q = 1; q < BT / 32; ++q)
-          if (pkey_v[q] > v || (pkey_v[q] == v && pkey_i[q] < ii)) { v = pkey_v[q]; ii = pkey_i[q]; }
-        s_piv = ii;
-        piv[j] = ii;
-        if (!(v > 0.0)) s_bad = 1;
+          if (rkey_v[q] > v || (rkey_v[q] == v && rkey_i[q] < ii)) {
+            v = rkey_v[q];
+            ii = rkey_i[q];
+          }
+        spiv[c] = ii;
+        if (!(v > T(0))) s_bad = 1;
       }
       __syncthreads();
       if (s_bad) break;
-      const int pr = s_piv;
-      if (pr != j)
-        for (int c = tid; c < nA; c += BT) {
-          const T u = L[(size_t)j * nA + c];
-          L[(size_t)j * nA + c] = L[(size_t)pr * nA + c];
-          L[(size_t)pr * nA + c] = u;
+      const int pr = spiv[c];
+      if (pr != c)
+        for (int x = tid; x < w; x += BT) {
+          const T u = P[c * PS + x];
+          P[c * PS + x] = P[pr * PS + x];
+          P[pr * PS + x] = u;
         }
       __syncthreads();
-      const T inv = T(1) / L[(size_t)j * nA + j];
-      const int ncol = nA - j - 1;  // <= 1024 (nA <= 1025)
-      for (int c = tid; c < ncol; c += BT) prow[c] = L[(size_t)j * nA + j + 1 + c];
-      __syncthreads();
-      for (int i = j + 1 + wid; i < nA; i += BT / 32) {
-        T* Li = L + (size_t)i * nA;
-        const T l = Li[j] * inv;
-        for (int c = lane; c < ncol; c += 32) Li[j + 1 + c] -= l * prow[c];
-        __syncwarp();
-        if (lane == 0) Li[j] = l;
+      const T inv = T(1) / P[c * PS + c];
+      for (int r = c + 1 + tid; r < R; r += BT) {
+        const T l = P[r * PS + c] * inv;
+        P[r * PS + c] = l;
+        for (int x = c + 1; x < w; ++x) P[r * PS + x] -= l * P[c * PS + x];
       }
       __syncthreads();
     }
-    if (s_bad && tid == 0) {
-      atomicOr(a.status, DEV_ERR_SINGULAR);
-      atomicMin(a.status + 1, E.k);
+    if (s_bad) {
+      if (tid == 0) {
+        atomicOr(a.status, DEV_ERR_SINGULAR);
+        atomicMin(a.status + 1, E.k);
+      }
+      continue;  // the element's factors are left unfinished; its pivots stay in range
     }
-    __syncthreads();
+    for (int i = tid; i < R * w; i += BT) {
+      const int r = i / w, c = i % w;
+      L[(size_t)(j0 + r) * nA + j0 + c] = P[r * PS + c];
+    }
+    for (int c = tid; c < w; c += BT) piv[j0 + c] = j0 + spiv[c];
+    // the interchanges on the columns outside the panel; U12 on those right of it
+    for (int col = tid; col < nA - w; col += BT) {
+      const int cc = col < j0 ? col : col + w;
+      for (int q = 0; q < w; ++q) {
+        const int pr = spiv[q];
+        if (pr != q) {
+          const T u = L[(size_t)(j0 + q) * nA + cc];
+          L[(size_t)(j0 + q) * nA + cc] = L[(size_t)(j0 + pr) * nA + cc];
+          L[(size_t)(j0 + pr) * nA + cc] = u;
+        }
+      }
+      if (cc >= j0 + w) {
+        T x[LB];
+#pragma unroll
+        for (int q = 0; q < LB; ++q) {
+          if (q < w) {
+            T v = L[(size_t)(j0 + q) * nA + cc];
+#pragma unroll
+            for (int s2 = 0; s2 < q; ++s2) v -= P[q * PS + s2] * x[s2];
+            x[q] = v;
+            L[(size_t)(j0 + q) * nA + cc] = v;
+          }
+        }
+      }
+    }
   }
 }
 
@@ -194,22 +266,51 @@ __global__ void __launch_bounds__(128) k_big_trsm_diag(const __grid_constant__ U
     if (r0 + q < r1) X[(size_t)(r0 + q) * nT + col] = x[q];
 }
 
-// 3b / 4. batched GEMM Out -= A B on 64 x 64 tiles:
+// 3b / 4. batched GEMM Out -= A B, per element:
 //   phase 0: rows [r1, nA) of X -= L[r1:, r0:r1] X[r0:r1, :]     (forward, block jb)
 //   phase 1: rows [0, r0) of X  -= L[:r0, r0:r1] X[r0:r1, :]     (backward, block jb)
 //   phase 2: S = D - C X_B (C, D column-major when the blocks are)
+//   phase 3: L[j1:, j1:] -= L[j1:, j0:j1] L[j0:j1, j1:]          (LU trailing update, panel jb)
+// 16 x 16 threads, each with TM x TM outputs in two TM/2-wide halves of rows and of columns (so
+// that its shared-memory operands are two 16-byte vectors per k), GKK values of k per stage, two
+// shared-memory stages with the next stage's global values held in registers meanwhile.
+template <typename T>
+struct GemmCfg {
+  static constexpr int TM = sizeof(T) == 8 ? 4 : 8;  // outputs per thread and dimension
+  static constexpr int H = TM / 2;                   // one 16-byte vector
+  static constexpr int BM = 16 * TM;                 // output tile (rows = columns)
+  static constexpr int GKK = 8;                      // k per stage
+  static constexpr int PAD = 16 / sizeof(T);
+  static constexpr int LD = BM * GKK / BT;           // values of each operand a thread loads per stage
+};
+template <typename T>
+__device__ __forceinline__ void gemm_vec_ld(const T* p, T (&v)[GemmCfg<T>::H]) {
+  if constexpr (sizeof(T) == 8) {
+    const double2 x = *reinterpret_cast<const double2*>(p);
+    v[0] = x.x;
+    v[1] = x.y;
+  } else {
+    const float4 x = *reinterpret_cast<const float4*>(p);
+    v[0] = x.x;
+    v[1] = x.y;
+    v[2] = x.z;
+    v[3] = x.w;
+  }
+}
 template <typename T>
 __global__ void __launch_bounds__(BT) k_big_gemm(const __grid_constant__ UnevenArgs a, const int* __restrict__ list,
                                                  int base, int nlist, int uni_nA, int uni_nT, int phase, int jb) {
-  __shared__ T As[GK][GT + 4];  // [k][m]
-  __shared__ T Bs[GK][GT];      // [k][n]
+  using C = GemmCfg<T>;
+  constexpr int TM = C::TM, H = C::H, BM = C::BM, GKK = C::GKK, LDN = C::LD;
+  __shared__ __align__(16) T As[2][GKK][BM + C::PAD];  // [k][m]
+  __shared__ __align__(16) T Bs[2][GKK][BM + C::PAD];  // [k][n]
   if ((int)blockIdx.z >= nlist) return;
   const int li = base + blockIdx.z;
   const Elem E = elem_of(a, list, li, uni_nA, uni_nT);
   const int nA = E.nA, nT = E.nT;
   const bool cm = a.colmajor != 0;
-  int M, N, K, m_off = 0, k_off = 0;
-  const T* L = reinterpret_cast<const T*>(a.LU) + E.o[0];
+  int M, N, K, m_off = 0, k_off = 0, n_off = 0;
+  T* L = reinterpret_cast<T*>(a.LU) + E.o[0];
   T* X = reinterpret_cast<T*>(a.XB) + E.o[1];
   const T* Cm = reinterpret_cast<const T*>(a.C) + E.o[1];
   const T* Dm = reinterpret_cast<const T*>(a.D) + E.o[2];
@@ -226,70 +327,103 @@ __global__ void __launch_bounds__(BT) k_big_gemm(const __grid_constant__ UnevenA
     M = r0;
     N = nT;
     K = r1 - r0;
-    m_off = 0;
     k_off = r0;
-  } else {
+  } else if (phase == 2) {
     M = nT;
     N = nT;
     K = nA;
+  } else {
+    const int j0 = jb * lu_panel<T>(), j1 = min(nA, j0 + lu_panel<T>());
+    M = nA - j1;
+    N = nA - j1;
+    K = j1 - j0;
+    m_off = j1;
+    n_off = j1;
+    k_off = j0;
   }
-  const int tm0 = blockIdx.y * GT, tn0 = blockIdx.x * GT;
+  const int tm0 = blockIdx.y * BM, tn0 = blockIdx.x * BM;
   if (M <= 0 || K <= 0 || tm0 >= M || tn0 >= N) return;
   const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
-  T acc[4][4];
+  // operand A element (m, k) of the tile: k contiguous in memory except column-major C
+  const bool a_mfast = phase == 2 && cm;
+  auto lda = [&](int m, int k) -> T {
+    if (m >= M || k >= K) return T(0);
+    if (phase != 2) return L[(size_t)(m_off + m) * nA + k_off + k];
+    return cm ? Cm[(size_t)k * nT + m] : Cm[(size_t)m * nA + k];
+  };
+  auto ldb = [&](int k, int n) -> T {
+    if (n >= N || k >= K) return T(0);
+    return phase == 3 ? L[(size_t)(k_off + k) * nA + n_off + n] : X[(size_t)(k_off + k) * nT + n];
+  };
+  // thread's load slots: A (m, k) with k fastest (or m fastest), B (k, n) with n fastest
+  T ra[LDN], rb[LDN];
+  auto gload = [&](int k0) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int jj = 0; jj < 4; ++jj) acc[i][jj] = T(0);
-  for (int k0 = 0; k0 < K; k0 += GK) {
-    // A tile (64 rows m x 16 k) and B tile (16 k x 64 n)
-    for (int idx = tid; idx < GT * GK; idx += BT) {
-      const int mm = idx % GT, kk = idx / GT;
-      const int m = tm0 + mm, k = k0 + kk;
-      T v = T(0);
-      if (m < M && k < K) {
-        if (phase <= 1)
-          v = L[(size_t)(m_off + m) * nA + k_off + k];
-        else
-          v = cm ? Cm[(size_t)k * nT + m] : Cm[(size_t)m * nA + k];
-      }
-      As[kk][mm] = v;
+    for (int q = 0; q < LDN; ++q) {
+      const int idx = tid + q * BT;
+      if (a_mfast)
+        ra[q] = lda(tm0 + idx % BM, k0 + idx / BM);
+      else
+        ra[q] = lda(tm0 + idx / GKK, k0 + idx % GKK);
+      rb[q] = ldb(k0 + idx / BM, tn0 + idx % BM);
     }
-    for (int idx = tid; idx < GT * GK; idx += BT) {
-      const int nn = idx % GT, kk = idx / GT;
-      const int n = tn0 + nn, k = k0 + kk;
-      T v = T(0);
-      if (n < N && k < K) v = X[(size_t)(k_off + k) * nT + n];
-      Bs[kk][nn] = v;
+  };
+  auto sstore = [&](int st) {
+#pragma unroll
+    for (int q = 0; q < LDN; ++q) {
+      const int idx = tid + q * BT;
+      if (a_mfast)
+        As[st][idx / BM][idx % BM] = ra[q];
+      else
+        As[st][idx % GKK][idx / GKK] = ra[q];
+      Bs[st][idx / BM][idx % BM] = rb[q];
     }
-    __syncthreads();
+  };
+  T acc[TM][TM];
 #pragma unroll
-    for (int kk = 0; kk < GK; ++kk) {
-      T av[4], bv[4];
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+    for (int j = 0; j < TM; ++j) acc[i][j] = T(0);
+  gload(0);
+  sstore(0);
+  __syncthreads();
+  int st = 0;
+  for (int k0 = 0; k0 < K; k0 += GKK) {
+    const bool more = k0 + GKK < K;
+    if (more) gload(k0 + GKK);
 #pragma unroll
-      for (int jj = 0; jj < 4; ++jj) bv[jj] = Bs[kk][tx + 16 * jj];
+    for (int kk = 0; kk < GKK; ++kk) {
+      T av[TM], bv[TM];
+      gemm_vec_ld<T>(&As[st][kk][ty * H], *reinterpret_cast<T(*)[H]>(&av[0]));
+      gemm_vec_ld<T>(&As[st][kk][BM / 2 + ty * H], *reinterpret_cast<T(*)[H]>(&av[H]));
+      gemm_vec_ld<T>(&Bs[st][kk][tx * H], *reinterpret_cast<T(*)[H]>(&bv[0]));
+      gemm_vec_ld<T>(&Bs[st][kk][BM / 2 + tx * H], *reinterpret_cast<T(*)[H]>(&bv[H]));
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) acc[i][jj] += av[i] * bv[jj];
+        for (int j = 0; j < TM; ++j) acc[i][j] += av[i] * bv[j];
     }
-    __syncthreads();
+    if (more) {
+      sstore(st ^ 1);
+      __syncthreads();
+      st ^= 1;
+    }
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int m = tm0 + ty + 16 * i;
+  for (int i = 0; i < TM; ++i) {
+    const int m = tm0 + (i < H ? ty * H + i : BM / 2 + ty * H + i - H);
     if (m >= M) continue;
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
-      const int n = tn0 + tx + 16 * jj;
+    for (int j = 0; j < TM; ++j) {
+      const int n = tn0 + (j < H ? tx * H + j : BM / 2 + tx * H + j - H);
       if (n >= N) continue;
       if (phase <= 1) {
-        X[(size_t)(m_off + m) * nT + n] -= acc[i][jj];
+        X[(size_t)(m_off + m) * nT + n] -= acc[i][j];
+      } else if (phase == 3) {
+        L[(size_t)(m_off + m) * nA + n_off + n] -= acc[i][j];
       } else {
         const T d = cm ? Dm[(size_t)n * nT + m] : Dm[(size_t)m * nT + n];
-        S[(size_t)m * nT + n] = d - acc[i][jj];
+        S[(size_t)m * nT + n] = d - acc[i][j];
       }
     }
   }
@@ -357,8 +491,29 @@ cudaError_t condense_big(const UnevenArgs& a, const int* list, int nlist, int un
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int grid1 = nlist < 4 * nsm ? nlist : 4 * nsm;
   cudaError_t e;
-  (hfr::count_launch(), k_big_lu<T><<<grid1, BT, 0, st>>>(a, list, nlist, uni_nA, uni_nT));
+  const size_t psm = lu_panel_smem<T>(max_nA);
+  if ((e = cudaFuncSetAttribute(k_big_lu_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm)) !=
+      cudaSuccess)
+    return e;
+  int occ = 1;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_big_lu_panel<T>, BT, psm)) != cudaSuccess) return e;
+  const int gridp = nlist < occ * nsm ? nlist : (occ > 0 ? occ : 1) * nsm;
+  (hfr::count_launch(), k_big_lu_init<T><<<grid1, BT, 0, st>>>(a, list, nlist, uni_nA, uni_nT));
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int npan = (max_nA + lu_panel<T>() - 1) / lu_panel<T>();
+  for (int jb = 0; jb < npan; ++jb) {
+    (hfr::count_launch(), k_big_lu_panel<T><<<gridp, BT, psm, st>>>(a, list, nlist, uni_nA, uni_nT, jb));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (jb + 1 == npan) break;
+    const int rest = max_nA - (jb + 1) * lu_panel<T>();
+    for (int base = 0; base < nlist; base += 65535) {
+      const int cnt = nlist - base < 65535 ? nlist - base : 65535;
+      constexpr int TB = GemmCfg<T>::BM;
+      const dim3 gl((rest + TB - 1) / TB, (rest + TB - 1) / TB, cnt);
+      (hfr::count_launch(), k_big_gemm<T><<<gl, BT, 0, st>>>(a, list, base, cnt, uni_nA, uni_nT, 3, jb));
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   (hfr::count_launch(), k_big_rhs<T><<<grid1, BT, 0, st>>>(a, list, nlist, uni_nA, uni_nT));
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int nblk = (max_nA + NB - 1) / NB;
@@ -366,7 +521,8 @@ cudaError_t condense_big(const UnevenArgs& a, const int* list, int nlist, int un
   for (int base = 0; base < nlist; base += CH) {
     const int cnt = nlist - base < CH ? nlist - base : CH;
     const dim3 gd((max_nT + 127) / 128, cnt);
-    const dim3 gg((max_nT + GT - 1) / GT, (max_nA + GT - 1) / GT, cnt);
+    constexpr int TB = GemmCfg<T>::BM;
+    const dim3 gg((max_nT + TB - 1) / TB, (max_nA + TB - 1) / TB, cnt);
     for (int jb = 0; jb < nblk; ++jb) {
       (hfr::count_launch(), k_big_trsm_diag<T><<<gd, 128, 0, st>>>(a, list, base, cnt, uni_nA, uni_nT, jb, 0));
       if (jb + 1 < nblk)
@@ -376,7 +532,7 @@ cudaError_t condense_big(const UnevenArgs& a, const int* list, int nlist, int un
       (hfr::count_launch(), k_big_trsm_diag<T><<<gd, 128, 0, st>>>(a, list, base, cnt, uni_nA, uni_nT, jb, 1));
       if (jb > 0) (hfr::count_launch(), k_big_gemm<T><<<gg, BT, 0, st>>>(a, list, base, cnt, uni_nA, uni_nT, 1, jb));
     }
-    const dim3 gs((max_nT + GT - 1) / GT, (max_nT + GT - 1) / GT, cnt);
+    const dim3 gs((max_nT + TB - 1) / TB, (max_nT + TB - 1) / TB, cnt);
     (hfr::count_launch(), k_big_gemm<T><<<gs, BT, 0, st>>>(a, list, base, cnt, uni_nA, uni_nT, 2, 0));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }

@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(GJ_THREADS) k_condense_reg(const __grid_consta
       const T ov = __shfl_xor_sync(0x0000ffffu << (tid & 16), val, o);
       if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; val = ov; }
     }
+    if (bi >= NA) bi = c;  // no candidate compared (NaN column): any row, flagged singular below
     if (rg == 0) {
       s_piv[buf] = bi;
       s_ipiv[bi] = c;
@@ -359,6 +360,7 @@ __global__ void __launch_bounds__(InvShape<NA>::THREADS, NA <= 64 ? 8 : 3) k_inv
       b = __shfl_sync(0xffffffffu, b, 0);
       p = __shfl_sync(0xffffffffu, p, 0);
     }
+    if (p >= NA) p = c;  // no candidate compared (NaN column): any row, flagged singular below
     const int sp = p & 3;
     if (g == (p >> 2)) {
 #pragma unroll
@@ -1845,9 +1847,11 @@ __device__ void condense_smem_elem(const CondElem<T>& e, unsigned char* smem_raw
   T* W = M + (size_t)nA * nc;             // big x nA
   T* pr = W + (size_t)big * nA;           // nc
   T* cb = pr + nc;                        // nA
-  int* ipiv = reinterpret_cast<int*>(cb + nA);
-  int* sflag = ipiv + nA;  // [0] pivot row of the step, [1] zero pivot seen
+  int* ipiv = reinterpret_cast<int*>(cb + nA);  // physical row -> elimination step
+  int* lpiv = ipiv + nA;                          // elimination step -> physical row
+  int* sflag = lpiv + nA;  // [0] pivot row of the step, [1] zero pivot seen
   unsigned char* used = reinterpret_cast<unsigned char*>(sflag + 2);
+  const int lane = tid & 31, wid = tid >> 5, nw = nth >> 5;
   int& s_p = sflag[0];
   int& s_bad = sflag[1];
   for (int i = tid; i < nA * nc; i += nth) {
@@ -1872,10 +1876,12 @@ __device__ void condense_smem_elem(const CondElem<T>& e, unsigned char* smem_raw
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
+      if (bi >= nA) bi = c;  // no candidate compared (NaN column): any row, flagged singular
       if (tid == 0) {
         s_p = bi;
         used[bi] = 1;
         ipiv[bi] = c;
+        lpiv[c] = bi;
         e.piv[c] = bi;
         if (!(best > T(0))) s_bad = 1;
       }
@@ -1887,12 +1893,15 @@ __device__ void condense_smem_elem(const CondElem<T>& e, unsigned char* smem_raw
     for (int j = tid; j < nc; j += nth) pr[j] = j == c ? inv : M[(size_t)p * nc + j] * inv;
     for (int r = tid; r < nA; r += nth) cb[r] = M[(size_t)r * nc + c];
     grp_sync(bar, nth);
-    for (int i = tid; i < nA * nc; i += nth) {
-      const int r = i / nc, j = i % nc;
-      if (r == p)
-        M[i] = pr[j];
-      else
-        M[i] = (j == c ? T(0) : M[i]) - cb[r] * pr[j];
+    // one warp per row, lanes along the row
+    for (int r = wid; r < nA; r += nw) {
+      T* Mr = M + (size_t)r * nc;
+      if (r == p) {
+        for (int j = lane; j < nc; j += 32) Mr[j] = pr[j];
+      } else {
+        const T l = cb[r];
+        for (int j = lane; j < nc; j += 32) Mr[j] = (j == c ? T(0) : Mr[j]) - l * pr[j];
+      }
     }
     grp_sync(bar, nth);
   }
@@ -1913,14 +1922,46 @@ __device__ void condense_smem_elem(const CondElem<T>& e, unsigned char* smem_raw
   // C into W; X rows in logical order are read through the pivot sequence
   for (int i = tid; i < nT * nA; i += nth) W[i] = e.C[i];
   grp_sync(bar, nth);
-  for (int it = tid; it < nT * (nT + 1); it += nth) {
-    const int i = it / (nT + 1), j = it % (nT + 1);
-    T acc = T(0);
-    for (int l = 0; l < nA; ++l) acc += W[(size_t)i * nA + l] * M[(size_t)e.piv[l] * nc + nA + j];
-    if (j < nT)
-      e.S[(size_t)i * nT + j] = e.D[(size_t)i * nT + j] - acc;
-    else
-      e.t[i] = e.s[i] - double(acc);
+  // [S | t] = [D | s] - C [X_B | x_r]: 4 x 4 outputs per thread (rows i0.., columns j0..)
+  const int ni = (nT + 3) >> 2, nj = (nT + 4) >> 2;
+  for (int it = tid; it < ni * nj; it += nth) {
+    const int i0 = (it / nj) * 4, j0 = (it % nj) * 4;
+    T acc[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[q][u] = T(0);
+    const T* Wr[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Wr[q] = W + (size_t)min(i0 + q, nT - 1) * nA;
+    int jc[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) jc[u] = nA + min(j0 + u, nT);
+    for (int l = 0; l < nA; ++l) {
+      const T* Xl = M + (size_t)lpiv[l] * nc;
+      T a4[4], b4[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) a4[q] = Wr[q][l];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) b4[u] = Xl[jc[u]];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[q][u] += a4[q] * b4[u];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = i0 + q;
+      if (i >= nT) continue;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = j0 + u;
+        if (j < nT)
+          e.S[(size_t)i * nT + j] = e.D[(size_t)i * nT + j] - acc[q][u];
+        else if (j == nT)
+          e.t[i] = e.s[i] - double(acc[q][u]);
+      }
+    }
   }
   grp_sync(bar, nth);
 }
@@ -2011,7 +2052,7 @@ __global__ void __launch_bounds__(UNEVEN_THREADS) k_condense_uneven(const __grid
 
 static size_t smem_elem_bytes(size_t tb, int nA, int nT) {
   const int nc = nA + nT + 1, big = nA > nT ? nA : nT;
-  return tb * ((size_t)nA * nc + (size_t)big * nA + nc + nA) + sizeof(int) * (nA + 2) + nA;
+  return tb * ((size_t)nA * nc + (size_t)big * nA + nc + nA) + sizeof(int) * (2 * (size_t)nA + 2) + nA;
 }
 
 }  // namespace hfr

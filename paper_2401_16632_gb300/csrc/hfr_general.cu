@@ -43,8 +43,75 @@
 namespace hfr {
 namespace gen {
 
+// n-point Gauss-Lobatto rule: the end points and the roots of P'_{n-1} (Newton from the Chebyshev-
+// Gauss-Lobatto points), weights 2 / (n (n - 1) P_{n-1}(x)^2)
+static void gauss_lobatto_nodes(int n, double* x, double* w) {
+  const int N = n - 1;
+  for (int i = 0; i < n; ++i) {
+    double z = -cos(M_PI * i / N);
+    if (i > 0 && i < N) {
+      for (int it = 0; it < 100; ++it) {
+        double p0 = 1.0, p1 = z;  // P_0, P_1 -> P_{N-1}, P_N
+        for (int k = 2; k <= N; ++k) {
+          const double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+          p0 = p1;
+          p1 = pk;
+        }
+        const double dp = N * (p0 - z * p1) / (1.0 - z * z);            // P'_N
+        const double d2 = (2.0 * z * dp - N * (N + 1.0) * p1) / (1.0 - z * z);  // P''_N
+        const double dz = dp / d2;
+        z -= dz;
+        if (fabs(dz) < 1e-16) break;
+      }
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= N; ++k) {
+      const double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = pk;
+    }
+    const double PN = N == 0 ? 1.0 : p1;
+    x[i] = z;
+    w[i] = 2.0 / (N * (N + 1.0) * PN * PN);
+  }
+}
+
+// barycentric interpolation weights of nodes x (n) at point z into l (exact node hits: unit vector)
+static void lagrange_at(int n, const double* x, double z, double* l) {
+  int hit = -1;
+  for (int b = 0; b < n; ++b)
+    if (z == x[b]) hit = b;
+  if (hit >= 0) {
+    for (int b = 0; b < n; ++b) l[b] = b == hit ? 1.0 : 0.0;
+    return;
+  }
+  double den = 0.0, bw[GN];
+  for (int j = 0; j < n; ++j) {
+    double prod = 1.0;
+    for (int k = 0; k < n; ++k)
+      if (k != j) prod *= (x[j] - x[k]);
+    bw[j] = 1.0 / prod;
+    den += bw[j] / (z - x[j]);
+  }
+  for (int b = 0; b < n; ++b) l[b] = (bw[b] / (z - x[b])) / den;
+}
+
 static void build_genref(GenRef& R) {
   memset(&R, 0, sizeof(R));
+  for (int n = 2; n <= GN; ++n) {
+    double xg[GN], wg[GN], xl[GN], wl[GN], l[GN];
+    gauss_legendre_nodes(n, xg, wg);
+    gauss_lobatto_nodes(n, xl, wl);
+    for (int q = 0; q < n; ++q) {
+      R.wl[n][q] = wl[q];
+      lagrange_at(n, xg, xl[q], l);  // Gauss node basis at GLL point q
+      for (int b = 0; b < n; ++b) R.TL[n][q][b] = l[b];
+    }
+    for (int b = 0; b < n; ++b) {
+      lagrange_at(n, xl, xg[b], l);  // GLL point basis at Gauss node b
+      for (int q = 0; q < n; ++q) R.PL[n][b][q] = l[q];
+    }
+  }
   for (int n = 2; n <= GN; ++n) {
     RefOps o;
     build_ref_ops(n - 1, o);
@@ -196,10 +263,14 @@ __global__ void __launch_bounds__(32 * GEPB) k_gen_elem(const __grid_constant__ 
   __syncwarp();
   for (int i = lane; i < 4 * GN * GN; i += 32) {
     const int f = i / (GN * GN), x = (i / GN) % GN, y = i % GN, m = w.nf[f];
-    w.Tf[f][x][y] = (x < m && y < n) ? RF.T[n][m][x][y] : 0.0;  // [q][b]
-    w.Pf[f][x][y] = (x < n && y < m) ? RF.P[n][m][x][y] : 0.0;  // [b][q]
+    const bool gll = a.fset[4 * e + f] != 0;  // EFR face: its n Gauss-Lobatto points
+    w.Tf[f][x][y] = (x < m && y < n) ? (gll ? RF.TL[n][x][y] : RF.T[n][m][x][y]) : 0.0;  // [q][b]
+    w.Pf[f][x][y] = (x < n && y < m) ? (gll ? RF.PL[n][x][y] : RF.P[n][m][x][y]) : 0.0;  // [b][q]
   }
-  if (lane < GF) w.wq[lane / GN][lane % GN] = (lane % GN) < w.nf[lane / GN] ? RF.w[w.nf[lane / GN]][lane % GN] : 0.0;
+  if (lane < GF) {
+    const int f = lane / GN, q = lane % GN;
+    w.wq[f][q] = q < w.nf[f] ? (a.fset[4 * e + f] ? RF.wl[n][q] : RF.w[w.nf[f]][q]) : 0.0;
+  }
   const double* Ue = a.U + a.uoff[e];
   for (int i = lane; i < ns * NV; i += 32) w.U[i / NV][i % NV] = Ue[i];
   __syncwarp();
@@ -230,7 +301,7 @@ __global__ void __launch_bounds__(32 * GEPB) k_gen_elem(const __grid_constant__ 
     const double uf = w.Ufp[f * GN + q][v];
     double ub;
     if (t >= 0) {
-      ub = a.uhat[a.toff[t] + q * NV + v];
+      ub = a.uhat[(size_t)a.fnode[(4 * e + f) * GN + q] * NV + v];
     } else if (kf == FK_FAR) {
       ub = 0.5 * (uf + a.uinf[v]);
     } else {
@@ -365,44 +436,43 @@ __global__ void __launch_bounds__(32 * GEPB) k_gen_elem(const __grid_constant__ 
   }
 }
 
-// trace residual: g[t] = both sides' rows
-__global__ void k_gen_trace_sum(int ntrace, int nv, int nface, int fs, const long long* __restrict__ toff,
-                                const int* __restrict__ tpts, const int* __restrict__ sides,
-                                const double* __restrict__ gview, double* __restrict__ g) {
-  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (t >= ntrace) return;
-  const int cnt = tpts[t] * nv;
-  const int e0 = sides[4 * t], f0 = sides[4 * t + 1], e1 = sides[4 * t + 2], f1 = sides[4 * t + 3];
-  for (int i = lane; i < cnt; i += 32) {
-    double s = gview[(size_t)(nface * e0 + f0) * fs * nv + i];
-    if (e1 >= 0) s += gview[(size_t)(nface * e1 + f1) * fs * nv + i];
-    g[toff[t] + i] = s;
-  }
+// trace residual: every trace point's value is the sum of the element rows at the element face
+// points that carry it (two sides on HFR faces, every face meeting at an EFR node)
+__global__ void k_gen_trace_sum(size_t npts, int nv, const long long* __restrict__ gptr,
+                                const long long* __restrict__ gidx, const double* __restrict__ gview,
+                                double* __restrict__ g) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npts * nv) return;
+  const size_t pt = i / nv;
+  const int v = (int)(i % nv);
+  double s = 0.0;
+  for (long long c = gptr[pt]; c < gptr[pt + 1]; ++c) s += gview[(size_t)gidx[c] * nv + v];
+  g[i] = s;
 }
 
-// initial trace: average of both sides' states at the trace points; far field: average with
-// u_inf; wall: the element's state with zero momentum
-__global__ void k_gen_initial_trace(int ntrace, int nv, const long long* __restrict__ toff, const int* __restrict__ tpts,
-                                    const int* __restrict__ sides, const int* __restrict__ kind,
+// initial trace: the average of the states at the element face points that carry the trace point;
+// a boundary trace point (one side): far field, the average with u_inf; wall, the element's state
+// with zero momentum
+__global__ void k_gen_initial_trace(size_t npts, int nv, const long long* __restrict__ gptr,
+                                    const long long* __restrict__ gidx, const int* __restrict__ kind,
                                     const double* __restrict__ Uf, GArgs a, double* __restrict__ uhat) {
-  const int nface = a.nface, fs = a.fs;
-  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (t >= ntrace) return;
-  const int cnt = tpts[t] * nv;
-  const int e0 = sides[4 * t], f0 = sides[4 * t + 1], e1 = sides[4 * t + 2], f1 = sides[4 * t + 3];
-  const int kf = kind[nface * e0 + f0];
-  for (int i = lane; i < cnt; i += 32) {
-    const int v = i % nv;
-    const double u0 = Uf[(size_t)(nface * e0 + f0) * fs * nv + i];
-    double x;
-    if (e1 >= 0)
-      x = 0.5 * (u0 + Uf[(size_t)(nface * e1 + f1) * fs * nv + i]);
-    else if (kf == FK_FAR)
-      x = 0.5 * (u0 + a.uinf[v]);
-    else
-      x = (v == 0 || v == nv - 1) ? u0 : 0.0;  // wall: zero momentum
-    uhat[toff[t] + i] = x;
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npts * nv) return;
+  const size_t pt = i / nv;
+  const int v = (int)(i % nv);
+  const long long c0 = gptr[pt], c1 = gptr[pt + 1];
+  const int kf = kind[gidx[c0] / a.fs];
+  double x;
+  if (kf == FK_FAR) {
+    x = 0.5 * (Uf[(size_t)gidx[c0] * nv + v] + a.uinf[v]);
+  } else if (kf == FK_WALL) {
+    x = (v == 0 || v == nv - 1) ? Uf[(size_t)gidx[c0] * nv + v] : 0.0;  // zero momentum
+  } else {
+    double s = 0.0;
+    for (long long c = c0; c < c1; ++c) s += Uf[(size_t)gidx[c] * nv + v];
+    x = s / (double)(c1 - c0);
   }
+  uhat[i] = x;
 }
 
 // ------------------------------------------------------------------------ element blocks
@@ -489,12 +559,13 @@ __global__ void __launch_bounds__(JT) k_gen_jacobian(const __grid_constant__ Phy
   __syncthreads();
   for (int i = tid; i < 4 * GN * GN; i += JT) {
     const int f = i / (GN * GN), x = (i / GN) % GN, y = i % GN, m = w.nf[f];
-    w.Tf[f][x][y] = (x < m && y < n) ? T(RF.T[n][m][x][y]) : T(0);
-    w.Pf[f][x][y] = (x < n && y < m) ? T(RF.P[n][m][x][y]) : T(0);
+    const bool gll = a.fset[4 * e + f] != 0;
+    w.Tf[f][x][y] = (x < m && y < n) ? T(gll ? RF.TL[n][x][y] : RF.T[n][m][x][y]) : T(0);
+    w.Pf[f][x][y] = (x < n && y < m) ? T(gll ? RF.PL[n][x][y] : RF.P[n][m][x][y]) : T(0);
   }
   for (int jj = tid; jj < GF; jj += JT) {
     const int f = jj / GN, q = jj % GN;
-    w.wq[f][q] = q < w.nf[f] ? T(RF.w[w.nf[f]][q]) : T(0);
+    w.wq[f][q] = q < w.nf[f] ? T(a.fset[4 * e + f] ? RF.wl[n][q] : RF.w[w.nf[f]][q]) : T(0);
     const double* G = a.geo_face + ((size_t)(4 * e + f) * GN + q) * 3;
     w.fJ[jj] = q < w.nf[f] ? T(G[0]) : T(0);
     w.fnr[jj][0] = q < w.nf[f] ? T(G[1]) : T(0);
@@ -515,7 +586,7 @@ __global__ void __launch_bounds__(JT) k_gen_jacobian(const __grid_constant__ Phy
       for (int b = 0; b < n; ++b) s += w.Tf[f][q][b] * w.Ufn[f * GN + b][v];
       const int t = w.tr[f];
       if (t >= 0) {
-        ub = T(a.uhat[a.toff[t] + q * NV + v]);
+        ub = T(a.uhat[(size_t)a.fnode[(4 * e + f) * GN + q] * NV + v]);
         un = s;
       } else {  // interface face of an implicit element: the explicit neighbour's state
         const int nb = a.nbr[4 * e + f], fn = a.nbr_face[4 * e + f];
@@ -903,89 +974,173 @@ __global__ void k_gen_matvec_elem(int Eim, const int* __restrict__ nTk, const lo
   }
 }
 
-// y[d] = sum over the sides of the element-view values of trace value d
-__global__ void k_gen_gather_sum(size_t nh, const long long* __restrict__ ginv, const double* __restrict__ yv,
-                                 double* __restrict__ y, const int* gate, int gj) {
+// y[d] = the sum of the element-view values of trace value d (CSR over its entries)
+__global__ void k_gen_gather_sum(size_t nh, const long long* __restrict__ vptr, const long long* __restrict__ vidx,
+                                 const double* __restrict__ yv, double* __restrict__ y, const int* gate, int gj) {
   if (gate && *gate >= 0 && gj >= *gate) return;
   const size_t d = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (d >= nh) return;
-  const long long i0 = ginv[2 * d], i1 = ginv[2 * d + 1];
-  double s = yv[i0];
-  if (i1 >= 0) s += yv[i1];
+  double s = 0.0;
+  for (long long c = vptr[d]; c < vptr[d + 1]; ++c) s += yv[vidx[c]];
   y[d] = s;
 }
 
-// face-block Jacobi: P_t = sum over the sides of the face's diagonal block of S_k, inverted by
-// Gauss-Jordan with partial pivoting (one warp per trace face, FP64 arithmetic, stored in T)
+// EFR node-block Jacobi: P_i = sum over the element entries of node i of the nv x nv diagonal
+// block of S_k at that entry, inverted by Gauss-Jordan with partial pivoting (one thread per node,
+// FP64), stored in the block precision
 template <typename T>
-__global__ void k_gen_precond_build(int ntrace, int nv, const int* __restrict__ tpts, const long long* __restrict__ poff,
-                                    const int* __restrict__ pside, const int* __restrict__ nTk,
-                                    const long long* __restrict__ offD, const T* __restrict__ S, T* __restrict__ Pinv,
-                                    double* __restrict__ work, int* status) {
-  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+__global__ void k_gen_precond_build_node(size_t nnode, int nv, const long long* __restrict__ nptr,
+                                         const int* __restrict__ nent_k, const int* __restrict__ nent_l,
+                                         const int* __restrict__ nTk, const long long* __restrict__ offD,
+                                         const T* __restrict__ S, T* __restrict__ Pinv, int* status) {
+  const size_t node = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= nnode) return;
+  double W[5][10];
+  for (int r = 0; r < nv; ++r)
+    for (int c = 0; c < 2 * nv; ++c) W[r][c] = (c >= nv && c - nv == r) ? 1.0 : 0.0;
+  for (long long e = nptr[node]; e < nptr[node + 1]; ++e) {
+    const int k = nent_k[e], l = nent_l[e], nT = nTk[k];
+    const T* Sk = S + offD[k];
+    for (int r = 0; r < nv; ++r)
+      for (int c = 0; c < nv; ++c) W[r][c] += double(Sk[(size_t)(l + r) * nT + l + c]);
+  }
+  for (int c = 0; c < nv; ++c) {
+    int pr = c;
+    double bv = fabs(W[c][c]);
+    for (int r = c + 1; r < nv; ++r)
+      if (fabs(W[r][c]) > bv) {
+        bv = fabs(W[r][c]);
+        pr = r;
+      }
+    if (!(bv > 0.0)) {
+      atomicOr(status, DEV_ERR_SINGULAR);
+      atomicMin(status + 1, -1);
+      return;
+    }
+    if (pr != c)
+      for (int x = 0; x < 2 * nv; ++x) {
+        const double u = W[c][x];
+        W[c][x] = W[pr][x];
+        W[pr][x] = u;
+      }
+    const double inv = 1.0 / W[c][c];
+    for (int x = 0; x < 2 * nv; ++x) W[c][x] *= inv;
+    for (int r = 0; r < nv; ++r) {
+      if (r == c) continue;
+      const double l = W[r][c];
+      for (int x = 0; x < 2 * nv; ++x) W[r][x] -= l * W[c][x];
+    }
+  }
+  T* P = Pinv + node * nv * nv;
+  for (int r = 0; r < nv; ++r)
+    for (int c = 0; c < nv; ++c) P[r * nv + c] = T(W[r][nv + c]);
+}
+
+// face-block Jacobi: P_t = sum over the sides of the face's diagonal block of S_k, inverted in
+// place in shared memory by Gauss-Jordan elimination with partial pivoting (row interchanges,
+// undone at the end as column interchanges in reverse order), in the block precision T; one CTA
+// of GP_THREADS per trace face, bs x bs values plus bs multipliers and bs pivot rows of shared memory
+constexpr int GP_THREADS = 128;
+template <typename T>
+size_t precond_smem_bytes(int bsmax) {
+  return ((size_t)bsmax * bsmax + bsmax) * sizeof(T) + (size_t)bsmax * sizeof(int);
+}
+template <typename T>
+__global__ void __launch_bounds__(GP_THREADS) k_gen_precond_build(int ntrace, int nv, const int* __restrict__ tpts,
+                                                                const long long* __restrict__ poff,
+                                                                const int* __restrict__ pside,
+                                                                const int* __restrict__ nTk,
+                                                                const long long* __restrict__ offD,
+                                                                const T* __restrict__ S, T* __restrict__ Pinv,
+                                                                int* status) {
+  extern __shared__ __align__(16) unsigned char gp_smem[];
+  __shared__ int s_piv, s_bad;
+  const int t = blockIdx.x, tid = threadIdx.x;
   if (t >= ntrace) return;
   const int bs = tpts[t] * nv;
-  double* Wm = work + (size_t)poff[t] * 2;  // bs x 2bs augmented [P | I]
-  const int w2 = 2 * bs;
-  for (int i = lane; i < bs * w2; i += 32) {
-    const int r = i / w2, c = i % w2;
-    double v = 0.0;
-    if (c < bs) {
-      for (int sd = 0; sd < 2; ++sd) {
-        const int kk = pside[4 * t + 2 * sd], lo = pside[4 * t + 2 * sd + 1];
-        if (kk < 0) continue;
-        const int nT = nTk[kk];
-        v += double(S[offD[kk] + (size_t)(lo + r) * nT + lo + c]);
-      }
-    } else {
-      v = (c - bs == r) ? 1.0 : 0.0;
+  T* W = reinterpret_cast<T*>(gp_smem);  // bs x bs, row-major
+  T* L = W + (size_t)bs * bs;             // multipliers of the current column
+  int* perm = reinterpret_cast<int*>(L + bs);
+  for (int i = tid; i < bs * bs; i += GP_THREADS) {
+    const int r = i / bs, c = i % bs;
+    T v = T(0);
+    for (int sd = 0; sd < 2; ++sd) {
+      const int kk = pside[4 * t + 2 * sd], lo = pside[4 * t + 2 * sd + 1];
+      if (kk < 0) continue;
+      const int nT = nTk[kk];
+      v += S[offD[kk] + (size_t)(lo + r) * nT + lo + c];
     }
-    Wm[i] = v;
+    W[i] = v;
   }
-  __syncwarp();
-  bool bad = false;
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
   for (int c = 0; c < bs; ++c) {
-    double bv = -1.0;
-    int bi = bs;
-    for (int r = c + lane; r < bs; r += 32) {
-      const double v = fabs(Wm[r * w2 + c]);
-      if (v > bv || (v == bv && r < bi)) { bv = v; bi = r; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
-    }
-    if (!(bv > 0.0)) { bad = true; break; }
-    if (bi != c)
-      for (int x = lane; x < w2; x += 32) {
-        const double u = Wm[c * w2 + x];
-        Wm[c * w2 + x] = Wm[bi * w2 + x];
-        Wm[bi * w2 + x] = u;
+    if (tid < 32) {
+      T bv = T(-1);
+      int bi = bs;
+      for (int r = c + tid; r < bs; r += 32) {
+        const T v = fabs(W[r * bs + c]);
+        if (v > bv || (v == bv && r < bi)) {
+          bv = v;
+          bi = r;
+        }
       }
-    __syncwarp();
-    const double inv = 1.0 / Wm[c * w2 + c];
-    __syncwarp();  // every lane holds the pivot before its row is scaled
-    for (int x = lane; x < w2; x += 32) Wm[c * w2 + x] *= inv;
-    __syncwarp();
-    for (int r = 0; r < bs; ++r) {
-      if (r == c) continue;
-      const double l = Wm[r * w2 + c];
-      __syncwarp();
-      for (int x = lane; x < w2; x += 32) Wm[r * w2 + x] -= l * Wm[c * w2 + x];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) {
+          bv = ov;
+          bi = oi;
+        }
+      }
+      if (tid == 0) {
+        s_piv = bi;
+        perm[c] = bi;
+        if (!(bv > T(0))) s_bad = 1;
+      }
     }
-    __syncwarp();
+    __syncthreads();
+    if (s_bad) break;
+    const int pv = s_piv;
+    if (pv != c)
+      for (int x = tid; x < bs; x += GP_THREADS) {
+        const T u = W[c * bs + x];
+        W[c * bs + x] = W[pv * bs + x];
+        W[pv * bs + x] = u;
+      }
+    __syncthreads();
+    const T inv = T(1) / W[c * bs + c];
+    for (int r = tid; r < bs; r += GP_THREADS) L[r] = r == c ? T(0) : W[r * bs + c];
+    __syncthreads();
+    for (int x = tid; x < bs; x += GP_THREADS) W[c * bs + x] = (x == c ? T(1) : W[c * bs + x]) * inv;
+    __syncthreads();
+    for (int i = tid; i < bs * bs; i += GP_THREADS) {
+      const int r = i / bs, x = i % bs;
+      if (r == c) continue;
+      W[i] = (x == c ? T(0) : W[i]) - L[r] * W[c * bs + x];
+    }
+    __syncthreads();
   }
-  if (bad) {
-    if (lane == 0) {
+  if (s_bad) {
+    if (tid == 0) {
       atomicOr(status, DEV_ERR_SINGULAR);
       atomicMin(status + 1, -1 - t);
     }
     return;
   }
+  for (int c = bs - 1; c >= 0; --c) {
+    const int pv = perm[c];
+    if (pv != c)
+      for (int r = tid; r < bs; r += GP_THREADS) {
+        const T u = W[r * bs + c];
+        W[r * bs + c] = W[r * bs + pv];
+        W[r * bs + pv] = u;
+      }
+    __syncthreads();
+  }
   T* P = Pinv + poff[t];
-  for (int i = lane; i < bs * bs; i += 32) P[i] = T(Wm[(i / bs) * w2 + bs + i % bs]);
+  for (int i = tid; i < bs * bs; i += GP_THREADS) P[i] = W[i];
 }
 
 // z_t = Pinv_t v_t (v first normalised in place by *inv_h when given); one warp per trace face
@@ -1000,7 +1155,9 @@ __global__ void k_gen_precond_apply(int ntrace, int nv, const int* __restrict__ 
   const int bs = tpts[t] * nv;
   const long long o = toff[t];
   const T* P = Pinv + poff[t];
-  double xl[4];
+  // the product runs in the block precision (FP32 blocks: the FP32 pipe; the FP64 pipe of this
+  // part is a small fraction of the FP32 one)
+  T xl[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const int i = lane + 32 * c;
@@ -1009,19 +1166,19 @@ __global__ void k_gen_precond_apply(int ntrace, int nv, const int* __restrict__ 
       v *= *inv_h;
       x[o + i] = v;
     }
-    xl[c] = v;
+    xl[c] = T(v);
   }
   for (int row = 0; row < bs; ++row) {
-    double acc = 0.0;
+    T acc = T(0);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const int i = lane + 32 * c;
-      if (i < bs) acc += double(P[(size_t)row * bs + i]) * double(T(xl[c]));
+      if (i < bs) acc += P[(size_t)row * bs + i] * xl[c];
     }
 #pragma unroll
     for (int of = 16; of > 0; of >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, of);
     if (lane == 0) {
-      y[o + row] = acc;
+      y[o + row] = double(acc);
       if (y32) y32[o + row] = float(acc);
     }
   }
@@ -1039,23 +1196,24 @@ __global__ void k_gen_backsolve(int Eim, const int* __restrict__ nAk, const int*
   const int nA = nAk[k], nT = nTk[k];
   const T* X = XB + offB[k];
   const int* gm = gmap + offs[k];
-  double dl[16];
+  // the product in the block precision; x_r and the difference in FP64
+  T dl[16];
 #pragma unroll
   for (int c = 0; c < 16; ++c) {
     const int l = lane + 32 * c;
     const int g = l < nT ? gm[l] : -1;
-    dl[c] = g >= 0 ? duhat[g] : 0.0;
+    dl[c] = g >= 0 ? T(duhat[g]) : T(0);
   }
   for (int i = 0; i < nA; ++i) {
-    double acc = 0.0;
+    T acc = T(0);
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
       const int l = lane + 32 * c;
-      if (l < nT) acc += double(X[(size_t)i * nT + l]) * dl[c];
+      if (l < nT) acc += X[(size_t)i * nT + l] * dl[c];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) du[offr[k] + i] = xr[offr[k] + i] - acc;
+    if (lane == 0) du[offr[k] + i] = xr[offr[k] + i] - double(acc);
   }
 }
 
@@ -1210,6 +1368,9 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
   if (cfg->physics != FR_PHYS_ADVDIFF && cfg->physics != FR_PHYS_NAVIER_STOKES) return FR_ERR_UNSUPPORTED;
   if (cfg->precision != FR_PREC_FP64 && cfg->precision != FR_PREC_FP32) return FR_ERR_UNSUPPORTED;
   const bool hex = mesh->elem_type == FR_ELEM_HEX;
+  const bool efr = cfg->trace_kind == FR_TRACE_EFR;
+  if (cfg->trace_kind != FR_TRACE_HFR && cfg->trace_kind != FR_TRACE_EFR) return FR_ERR_INVALID_ARG;
+  if (efr && hex) return FR_ERR_UNSUPPORTED;  // EFR: quadrilaterals
   if (hex && cfg->physics != FR_PHYS_NAVIER_STOKES) return FR_ERR_UNSUPPORTED;  // hexahedra: Navier-Stokes
   const int DIM = hex ? 3 : 2, NF = hex ? 6 : 4, FS = hex ? HEX_FS : GN, NC = hex ? 8 : 4;
   const int nv = cfg->physics == FR_PHYS_ADVDIFF ? 1 : (hex ? 5 : 4);
@@ -1217,7 +1378,7 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
   for (int e = 0; e < E; ++e) {
     const int p = mesh->p_elem ? mesh->p_elem[e] : mesh->p;
     if (p < 1 || p > (hex ? HEX_PMAX : 5)) return FR_ERR_UNSUPPORTED;
-    if (hex && p != (mesh->p_elem ? mesh->p_elem[0] : mesh->p)) return FR_ERR_UNSUPPORTED;  // one degree
+    if ((hex || efr) && p != (mesh->p_elem ? mesh->p_elem[0] : mesh->p)) return FR_ERR_UNSUPPORTED;  // one degree
     deg[e] = p + 1;
   }
   // connectivity, face kinds, face point counts
@@ -1270,6 +1431,11 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
   g->dim = DIM;
   g->nface = NF;
   g->fs = FS;
+  g->efr = efr ? 1 : 0;
+  // EFR: interior trace faces carry the Gauss-Lobatto points (n of them: one degree)
+  std::vector<unsigned char> fset(NF * (size_t)E, 0);
+  if (efr)
+    for (size_t i = 0; i < fset.size(); ++i) fset[i] = kind[i] == FK_TRACE ? 1 : 0;
   g->pp.beta[0] = cfg->beta[0];
   g->pp.beta[1] = cfg->beta[1];
   g->pp.nu = cfg->nu;
@@ -1279,40 +1445,79 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
   g->pp.lref = cfg->lref > 0 ? cfg->lref : 1.0;
   for (int v = 0; v < 5; ++v) g->uinf[v] = cfg->u_inf[v];
   g->h_deg = deg;
-  // trace numbering: faces with a trace (both sides implicit, or a boundary face of an implicit
-  // element) in increasing global face id
-  std::vector<int> tr_of(NF * (size_t)E, -1), tr_of_fid(NF * (size_t)E, -1), pts_of_fid(NF * (size_t)E, 0);
-  for (int e = 0; e < E; ++e)
-    for (int f = 0; f < NF; ++f) {
-      const size_t i = NF * (size_t)e + f;
-      if (kind[i] == FK_TRACE || (nbr[i] < 0 && mesh->implicit[e])) {
-        tr_of_fid[mesh->face_of[i]] = 0;
-        pts_of_fid[mesh->face_of[i]] = nfp[i];
-      }
-    }
+  // trace units.  HFR: the trace faces (both sides implicit, or a boundary face of an implicit
+  // element) in increasing global face id, each with its face points.  EFR: the trace nodes
+  // (vertices of the implicit skeleton, interior Gauss-Lobatto points of the trace faces, the
+  // Gauss points of boundary trace faces; efr_trace_nodes), one point each.  fnode: the trace
+  // point of every element face point.
+  std::vector<int> tr_of(NF * (size_t)E, -1), tpts, sides, fnode(NF * (size_t)E * FS, -1);
   int nt = 0;
-  std::vector<int> tpts;
-  for (size_t id = 0; id < tr_of_fid.size(); ++id)
-    if (tr_of_fid[id] == 0) {
-      tr_of_fid[id] = nt++;
-      tpts.push_back(pts_of_fid[id]);
+  if (efr) {
+    const int n0 = deg[0];
+    std::vector<int> node_of((size_t)E * 4 * n0);
+    int nvert = 0, nnode = 0;
+    const int lrc = efr_trace_nodes(E, mesh->nbr, mesh->nbr_face, mesh->face_of, mesh->bc, mesh->implicit, n0 - 1,
+                                    node_of.data(), &nvert, &nnode);
+    if (lrc != FR_OK) {
+      destroy(g);
+      return lrc;
     }
+    nt = nnode;
+    tpts.assign(nt, 1);
+    for (int e = 0; e < E; ++e)
+      for (int f = 0; f < NF; ++f) {
+        const size_t i = NF * (size_t)e + f;
+        if (node_of[i * n0] < 0) continue;
+        tr_of[i] = node_of[i * n0];  // a face with a trace (its first node)
+        for (int q = 0; q < n0; ++q) fnode[i * FS + q] = node_of[i * n0 + q];
+      }
+  } else {
+    std::vector<int> tr_of_fid(NF * (size_t)E, -1), pts_of_fid(NF * (size_t)E, 0);
+    for (int e = 0; e < E; ++e)
+      for (int f = 0; f < NF; ++f) {
+        const size_t i = NF * (size_t)e + f;
+        if (kind[i] == FK_TRACE || (nbr[i] < 0 && mesh->implicit[e])) {
+          tr_of_fid[mesh->face_of[i]] = 0;
+          pts_of_fid[mesh->face_of[i]] = nfp[i];
+        }
+      }
+    for (size_t id = 0; id < tr_of_fid.size(); ++id)
+      if (tr_of_fid[id] == 0) {
+        tr_of_fid[id] = nt++;
+        tpts.push_back(pts_of_fid[id]);
+      }
+    sides.assign(4 * (size_t)std::max(nt, 1), -1);
+    std::vector<long long> tpt0(nt + 1, 0);
+    for (int t = 0; t < nt; ++t) tpt0[t + 1] = tpt0[t] + tpts[t];
+    for (int e = 0; e < E; ++e)
+      for (int f = 0; f < NF; ++f) {
+        const size_t i = NF * (size_t)e + f;
+        if (kind[i] == FK_TRACE || (nbr[i] < 0 && mesh->implicit[e])) {
+          const int t = tr_of_fid[mesh->face_of[i]];
+          tr_of[i] = t;
+          const int slot = sides[4 * (size_t)t] < 0 ? 0 : 1;
+          sides[4 * (size_t)t + 2 * slot] = e;
+          sides[4 * (size_t)t + 2 * slot + 1] = f;
+          for (int q = 0; q < nfp[i]; ++q) fnode[i * FS + q] = (int)(tpt0[t] + q);
+        }
+      }
+  }
   g->ntrace = nt;
   std::vector<long long> toff(nt + 1, 0);
   for (int t = 0; t < nt; ++t) toff[t + 1] = toff[t] + (long long)tpts[t] * nv;
   g->nh = (size_t)toff[nt];
-  std::vector<int> sides(4 * (size_t)std::max(nt, 1), -1);
-  for (int e = 0; e < E; ++e)
-    for (int f = 0; f < NF; ++f) {
-      const size_t i = NF * (size_t)e + f;
-      if (kind[i] == FK_TRACE || (nbr[i] < 0 && mesh->implicit[e])) {
-        const int t = tr_of_fid[mesh->face_of[i]];
-        tr_of[i] = t;
-        const int slot = sides[4 * (size_t)t] < 0 ? 0 : 1;
-        sides[4 * (size_t)t + 2 * slot] = e;
-        sides[4 * (size_t)t + 2 * slot + 1] = f;
-      }
-    }
+  g->npts = g->nh / nv;
+  // trace point <- element face points (CSR, element order)
+  std::vector<long long> gptr(g->npts + 1, 0), gidx;
+  for (size_t i = 0; i < fnode.size(); ++i)
+    if (fnode[i] >= 0) ++gptr[fnode[i] + 1];
+  for (size_t q = 0; q < g->npts; ++q) gptr[q + 1] += gptr[q];
+  gidx.assign(std::max((size_t)gptr[g->npts], (size_t)1), 0);
+  {
+    std::vector<long long> fill(gptr.begin(), gptr.end() - 1);
+    for (size_t i = 0; i < fnode.size(); ++i)
+      if (fnode[i] >= 0) gidx[fill[fnode[i]]++] = (long long)i;
+  }
   // state offsets, implicit blocks
   std::vector<long long> uoff(E + 1, 0), goff(E + 1, 0);
   for (int e = 0; e < E; ++e) {
@@ -1360,29 +1565,73 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
   g->sumTT = (size_t)offD[Eim];
   g->h_nA.assign(nAk.begin(), nAk.begin() + Eim);
   g->h_nT.assign(nTk.begin(), nTk.begin() + Eim);
-  // gather map (element-local trace unknown -> trace value) and its inverse (two sides)
+  // gather map (element-local trace unknown -> trace value) and its inverse (CSR, element order);
+  // HFR face blocks: the two sides' local offsets; EFR node blocks: every entry of each node
   std::vector<int> gmap(std::max(g->sumT, (size_t)1), -1);
-  std::vector<long long> ginv(2 * std::max(g->nh, (size_t)1), -1);
   std::vector<int> pside(4 * (size_t)std::max(nt, 1), -1);
+  std::vector<long long> vptr(g->nh + 1, 0), nptr(efr ? g->npts + 1 : 1, 0);
   for (int k = 0; k < Eim; ++k) {
     const int e = imp_idx[k];
     for (int f = 0; f < NF; ++f) {
-      const int t = tr_of[NF * (size_t)e + f];
+      const size_t i = NF * (size_t)e + f;
+      const int t = tr_of[i];
       if (t < 0) continue;
-      const int sd = sides[4 * (size_t)t] == e && sides[4 * (size_t)t + 1] == f ? 0 : 1;
-      pside[4 * (size_t)t + 2 * sd] = k;
-      pside[4 * (size_t)t + 2 * sd + 1] = lto[NF * (size_t)k + f];
-      const int cnt = tpts[t] * nv;
-      for (int i = 0; i < cnt; ++i) {
-        const long long l = offs[k] + lto[NF * (size_t)k + f] + i;
-        gmap[l] = (int)(toff[t] + i);
-        ginv[2 * (size_t)(toff[t] + i) + sd] = l;
+      if (!efr) {
+        const int sd = sides[4 * (size_t)t] == e && sides[4 * (size_t)t + 1] == f ? 0 : 1;
+        pside[4 * (size_t)t + 2 * sd] = k;
+        pside[4 * (size_t)t + 2 * sd + 1] = lto[NF * (size_t)k + f];
+      }
+      for (int q = 0; q < nfp[i]; ++q) {
+        const int pt = fnode[i * FS + q];
+        if (efr) ++nptr[pt + 1];
+        for (int v = 0; v < nv; ++v) {
+          const long long l = offs[k] + lto[NF * (size_t)k + f] + q * nv + v;
+          gmap[l] = pt * nv + v;
+          ++vptr[(size_t)pt * nv + v + 1];
+        }
+      }
+    }
+  }
+  for (size_t d = 0; d < g->nh; ++d) vptr[d + 1] += vptr[d];
+  std::vector<long long> vidx(std::max((size_t)vptr[g->nh], (size_t)1), 0);
+  {
+    std::vector<long long> fill(vptr.begin(), vptr.end() - 1);
+    for (size_t l = 0; l < g->sumT; ++l)
+      if (gmap[l] >= 0) vidx[fill[gmap[l]]++] = (long long)l;
+  }
+  for (size_t q = 0; efr && q < g->npts; ++q) nptr[q + 1] += nptr[q];
+  std::vector<int> nent_k(efr ? std::max((size_t)nptr[g->npts], (size_t)1) : 1, 0), nent_l(nent_k.size(), 0);
+  if (efr) {
+    std::vector<long long> fill(nptr.begin(), nptr.end() - 1);
+    for (int k = 0; k < Eim; ++k) {
+      const int e = imp_idx[k];
+      for (int f = 0; f < NF; ++f) {
+        const size_t i = NF * (size_t)e + f;
+        if (tr_of[i] < 0) continue;
+        for (int q = 0; q < nfp[i]; ++q) {
+          const int pt = fnode[i * FS + q];
+          nent_k[fill[pt]] = k;
+          nent_l[fill[pt]++] = lto[NF * (size_t)k + f] + q * nv;
+        }
       }
     }
   }
   std::vector<long long> poff(nt + 1, 0);
   for (int t = 0; t < nt; ++t) poff[t + 1] = poff[t] + (long long)(tpts[t] * nv) * (tpts[t] * nv);
   g->sumP = (size_t)poff[nt];
+  g->bsmax = 0;
+  for (int t = 0; t < nt; ++t) g->bsmax = std::max(g->bsmax, tpts[t] * nv);
+  if (!efr && nt > 0) {
+    const size_t sm = g->pb == 8 ? precond_smem_bytes<double>(g->bsmax) : precond_smem_bytes<float>(g->bsmax);
+    const cudaError_t ea = g->pb == 8 ? cudaFuncSetAttribute(k_gen_precond_build<double>,
+                                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
+                                   : cudaFuncSetAttribute(k_gen_precond_build<float>,
+                                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (ea != cudaSuccess) {
+      destroy(g);
+      return FR_ERR_UNSUPPORTED;
+    }
+  }
   // geometry at the own solution points and at every face's points
   const int GS = hex ? 10 : 5, GFC = hex ? 4 : 3;  // values per solution point / face point
   std::vector<double> gsol(GS * (size_t)goff[E]), gface(GFC * NF * (size_t)E * FS, 0.0);
@@ -1411,7 +1660,10 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
       const int m = nfp[NF * (size_t)e + f], r = f >> 1;
       const double sg = (f & 1) ? 1.0 : -1.0;
       double sq[GN], wq[GN];
-      gauss_legendre_nodes(m, sq, wq);
+      if (fset[NF * (size_t)e + f])
+        gauss_lobatto_nodes(m, sq, wq);
+      else
+        gauss_legendre_nodes(m, sq, wq);
       for (int q = 0; q < m; ++q) {
         const double xi = r == 0 ? sg : sq[q], eta = r == 0 ? sq[q] : sg;
         double J, S[2][2];
@@ -1456,7 +1708,7 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
   g->implicit = galloc<unsigned char>(g, E, &rc);
   g->dof_imp = galloc<unsigned char>(g, dof_imp.size(), &rc);
   g->tpts = galloc<int>(g, std::max(nt, 1), &rc);
-  g->sides = galloc<int>(g, sides.size(), &rc);
+  g->sides = galloc<int>(g, std::max(sides.size(), (size_t)1), &rc);
   g->pside = galloc<int>(g, pside.size(), &rc);
   g->poff = galloc<long long>(g, nt + 1, &rc);
   g->imp_idx = galloc<int>(g, std::max(Eim, 1), &rc);
@@ -1464,7 +1716,15 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
   g->nAk = galloc<int>(g, nAk.size(), &rc);
   g->nTk = galloc<int>(g, nTk.size(), &rc);
   g->gmap = galloc<int>(g, gmap.size(), &rc);
-  g->ginv = galloc<long long>(g, ginv.size(), &rc);
+  g->fnode = galloc<int>(g, fnode.size(), &rc);
+  g->fset = galloc<unsigned char>(g, fset.size(), &rc);
+  g->gptr = galloc<long long>(g, gptr.size(), &rc);
+  g->gidx = galloc<long long>(g, gidx.size(), &rc);
+  g->vptr = galloc<long long>(g, vptr.size(), &rc);
+  g->vidx = galloc<long long>(g, vidx.size(), &rc);
+  g->nptr = galloc<long long>(g, nptr.size(), &rc);
+  g->nent_k = galloc<int>(g, nent_k.size(), &rc);
+  g->nent_l = galloc<int>(g, nent_l.size(), &rc);
   g->offA = galloc<long long>(g, Eim + 1, &rc);
   g->offB = galloc<long long>(g, Eim + 1, &rc);
   g->offD = galloc<long long>(g, Eim + 1, &rc);
@@ -1487,7 +1747,6 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
   g->duhat = galloc<double>(g, g->nh, &rc);
   g->du = galloc<double>(g, g->sumA, &rc);
   g->red = galloc<double>(g, 1024 + 8, &rc);
-  g->pwork = galloc<double>(g, 2 * g->sumP, &rc);
   g->A = galloc<unsigned char>(g, g->sumAA * pb, &rc);
   g->B = galloc<unsigned char>(g, g->sumAT * pb, &rc);
   g->C = galloc<unsigned char>(g, g->sumAT * pb, &rc);
@@ -1534,7 +1793,7 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
   GUP(g->implicit, impv.data(), impv.size());
   GUP(g->dof_imp, dof_imp.data(), dof_imp.size());
   GUP(g->tpts, tpts.data(), tpts.size());
-  GUP(g->sides, sides.data(), sides.size());
+  if (!sides.empty()) GUP(g->sides, sides.data(), sides.size());
   GUP(g->pside, pside.data(), pside.size());
   GUP(g->poff, poff.data(), poff.size());
   GUP(g->imp_idx, imp_idx.data(), imp_idx.size());
@@ -1542,7 +1801,15 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
   GUP(g->nAk, nAk.data(), nAk.size());
   GUP(g->nTk, nTk.data(), nTk.size());
   GUP(g->gmap, gmap.data(), gmap.size());
-  GUP(g->ginv, ginv.data(), ginv.size());
+  GUP(g->fnode, fnode.data(), fnode.size());
+  GUP(g->fset, fset.data(), fset.size());
+  GUP(g->gptr, gptr.data(), gptr.size());
+  GUP(g->gidx, gidx.data(), gidx.size());
+  GUP(g->vptr, vptr.data(), vptr.size());
+  GUP(g->vidx, vidx.data(), vidx.size());
+  GUP(g->nptr, nptr.data(), nptr.size());
+  GUP(g->nent_k, nent_k.data(), nent_k.size());
+  GUP(g->nent_l, nent_l.data(), nent_l.size());
   GUP(g->offA, offA.data(), offA.size());
   GUP(g->offB, offB.data(), offB.size());
   GUP(g->offD, offD.data(), offD.size());
@@ -1628,6 +1895,8 @@ static GArgs gargs(GenCtx* g, const double* u, const double* uhat) {
   for (int v = 0; v < 5; ++v) a.uinf[v] = g->uinf[v];
   a.nface = g->nface;
   a.fs = g->fs;
+  a.fnode = g->fnode;
+  a.fset = g->fset;
   return a;
 }
 
@@ -1662,8 +1931,8 @@ static int residual_into(GenCtx* g, const double* u, const double* uhat, double*
   a.gview = g->gview;
   GCK(gen_elem<GM_RES>(g, a));
   if (g_out && g->ntrace) {
-    (count_launch(), k_gen_trace_sum<<<nbw(g->ntrace), 256, 0, g->st>>>(g->ntrace, g->nv, g->nface, g->fs, g->toff,
-                                                                        g->tpts, g->sides, g->gview, g_out));
+    (count_launch(), k_gen_trace_sum<<<nb256(g->nh), 256, 0, g->st>>>(g->npts, g->nv, g->gptr, g->gidx, g->gview,
+                                                                       g_out));
     GCK(cudaGetLastError());
   }
   pend(g, ph);
@@ -1683,8 +1952,8 @@ int initial_trace(GenCtx* g, const double* u, double* uhat) {
   a.Uf_out = buf;
   GCK(gen_elem<GM_UF>(g, a));
   if (g->ntrace) {
-    (count_launch(), k_gen_initial_trace<<<nbw(g->ntrace), 256, 0, g->st>>>(g->ntrace, g->nv, g->toff, g->tpts,
-                                                                            g->sides, g->kind, buf, a, uhat));
+    (count_launch(), k_gen_initial_trace<<<nb256(g->nh), 256, 0, g->st>>>(g->npts, g->nv, g->gptr, g->gidx, g->kind,
+                                                                           buf, a, uhat));
     GCK(cudaGetLastError());
   }
   GCK(cudaMemsetAsync(g->gview, 0, (size_t)g->nface * g->E * g->fs * g->nv * sizeof(double), g->st));
@@ -1763,16 +2032,26 @@ static int condense_impl(GenCtx* g) {
   pend(g, ph);
   ph = pbeg(g, 3);
   if (g->ntrace) {
-    (count_launch(), k_gen_gather_sum<<<nb256(g->nh), 256, 0, g->st>>>(g->nh, g->ginv, g->te, g->tg, nullptr, 0));
+    (count_launch(), k_gen_gather_sum<<<nb256(g->nh), 256, 0, g->st>>>(g->nh, g->vptr, g->vidx, g->te, g->tg, nullptr, 0));
     GCK(cudaGetLastError());
-    if (g->pb == 8)
-      (count_launch(), k_gen_precond_build<double><<<nbw(g->ntrace), 256, 0, g->st>>>(
-           g->ntrace, g->nv, g->tpts, g->poff, g->pside, g->nTk, g->offD, (const double*)g->S, (double*)g->Pinv,
-           g->pwork, g->status));
+    if (g->efr && g->pb == 8)
+      (count_launch(), k_gen_precond_build_node<double><<<nb256(g->npts), 256, 0, g->st>>>(
+           g->npts, g->nv, g->nptr, g->nent_k, g->nent_l, g->nTk, g->offD, (const double*)g->S, (double*)g->Pinv,
+           g->status));
+    else if (g->efr)
+      (count_launch(), k_gen_precond_build_node<float><<<nb256(g->npts), 256, 0, g->st>>>(
+           g->npts, g->nv, g->nptr, g->nent_k, g->nent_l, g->nTk, g->offD, (const float*)g->S, (float*)g->Pinv,
+           g->status));
+    else if (g->pb == 8)
+      (count_launch(), k_gen_precond_build<double><<<g->ntrace, GP_THREADS, precond_smem_bytes<double>(g->bsmax),
+                                                      g->st>>>(g->ntrace, g->nv, g->tpts, g->poff, g->pside, g->nTk,
+                                                               g->offD, (const double*)g->S, (double*)g->Pinv,
+                                                               g->status));
     else
-      (count_launch(), k_gen_precond_build<float><<<nbw(g->ntrace), 256, 0, g->st>>>(
-           g->ntrace, g->nv, g->tpts, g->poff, g->pside, g->nTk, g->offD, (const float*)g->S, (float*)g->Pinv,
-           g->pwork, g->status));
+      (count_launch(), k_gen_precond_build<float><<<g->ntrace, GP_THREADS, precond_smem_bytes<float>(g->bsmax),
+                                                     g->st>>>(g->ntrace, g->nv, g->tpts, g->poff, g->pside, g->nTk,
+                                                              g->offD, (const float*)g->S, (float*)g->Pinv,
+                                                              g->status));
     GCK(cudaGetLastError());
   }
   pend(g, ph);
@@ -1808,7 +2087,7 @@ static void cb_matvec_g(void* c, const double* x, double* y, cudaStream_t s) {
   else
     (count_launch(), k_gen_matvec_elem<float><<<nbw(g->Eim), 256, 0, s>>>(g->Eim, g->nTk, g->offD, g->offs, g->gmap,
                                                                           (const float*)g->S, x, g->yv, nullptr, 0));
-  (count_launch(), k_gen_gather_sum<<<nb256(g->nh), 256, 0, s>>>(g->nh, g->ginv, g->yv, y, nullptr, 0));
+  (count_launch(), k_gen_gather_sum<<<nb256(g->nh), 256, 0, s>>>(g->nh, g->vptr, g->vidx, g->yv, y, nullptr, 0));
   pend(g, ph);
 }
 static void cb_gmatvec_g(void* c, const GmresState* st, int j, const double* x, const float*, double* y, cudaStream_t s) {
@@ -1819,7 +2098,7 @@ static void cb_gmatvec_g(void* c, const GmresState* st, int j, const double* x, 
   else
     (count_launch(), k_gen_matvec_elem<float><<<nbw(g->Eim), 256, 0, s>>>(g->Eim, g->nTk, g->offD, g->offs, g->gmap,
                                                                           (const float*)g->S, x, g->yv, &st->kdone, j));
-  (count_launch(), k_gen_gather_sum<<<nb256(g->nh), 256, 0, s>>>(g->nh, g->ginv, g->yv, y, &st->kdone, j));
+  (count_launch(), k_gen_gather_sum<<<nb256(g->nh), 256, 0, s>>>(g->nh, g->vptr, g->vidx, g->yv, y, &st->kdone, j));
 }
 static void cb_precond_g(void* c, const GmresState* st, int j, double* x, double* y, float* y32, cudaStream_t s) {
   GenCtx* g = (GenCtx*)c;

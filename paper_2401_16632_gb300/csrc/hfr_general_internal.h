@@ -27,6 +27,10 @@ struct GenRef {
   double lm[GN + 1][GN], lp[GN + 1][GN], dgL[GN + 1][GN], dgR[GN + 1][GN], w[GN + 1][GN];
   double T[GN + 1][GN + 1][GN][GN];  // [n][m][q][b] = l_b(s_q): node b of n -> face point q of m
   double P[GN + 1][GN + 1][GN][GN];  // [n][m][b][q] = w_q l_b(s_q) / w_b: face points -> nodes
+  // EFR faces: the n Gauss-Lobatto points of a face (interpolation both ways, GLL weights)
+  double TL[GN + 1][GN][GN];  // [n][q][b] = l_b(x^GLL_q): Gauss node b -> GLL point q
+  double PL[GN + 1][GN][GN];  // [n][b][q] = l^GLL_q(x_b): GLL point q -> Gauss node b
+  double wl[GN + 1][GN];      // GLL weights
 };
 
 struct GArgs {
@@ -38,6 +42,8 @@ struct GArgs {
   const double* geo_face; // [(4 e + f) GN + q][3] = {J_f, n0, n1}
   const int *nbr, *nbr_face, *kind, *tr_of, *nfp;  // 4 E
   const long long* toff;  // trace value offsets
+  const int* fnode;       // (e nface + f) fs + q: trace point of each element face point, -1 off traces
+  const unsigned char* fset;  // e nface + f: 1 where the face points are Gauss-Lobatto (EFR faces)
   const unsigned char* implicit;
   const GenRef* ref;
   const double* U;
@@ -74,7 +80,10 @@ struct GenCtx {
   PhysParams pp;
   double uinf[5] = {0, 0, 0, 0, 0};
   int dim = 2, nface = 4, fs = GN;  // dimension, faces per element, face-point stride per face
+  int efr = 0;                      // trace continuous at GLL points on interior trace faces
+  size_t npts = 0;                  // trace points (units: HFR trace faces, EFR nodes)
   size_t nstate = 0, nh = 0, sumA = 0, sumT = 0, sumAA = 0, sumAT = 0, sumTT = 0, sumP = 0;
+  int bsmax = 0;  // largest face block of the preconditioner
   size_t bytes = 0;
   std::vector<void*> allocs;
   std::vector<long long> h_uoff, h_toff;
@@ -89,10 +98,16 @@ struct GenCtx {
   int *tpts = nullptr, *sides = nullptr, *pside = nullptr;
   long long* poff = nullptr;
   int *imp_idx = nullptr, *lto = nullptr, *nAk = nullptr, *nTk = nullptr, *gmap = nullptr;
-  long long *offA = nullptr, *offB = nullptr, *offD = nullptr, *offr = nullptr, *offs = nullptr, *ginv = nullptr;
+  long long *offA = nullptr, *offB = nullptr, *offD = nullptr, *offr = nullptr, *offs = nullptr;
+  int* fnode = nullptr;            // per element face point: its trace point (-1 off traces)
+  unsigned char* fset = nullptr;   // per element face: 1 = GLL points (EFR)
+  long long *gptr = nullptr, *gidx = nullptr;  // trace point <- element face points (CSR)
+  long long *vptr = nullptr, *vidx = nullptr;  // trace value <- element-view entries (CSR)
+  long long* nptr = nullptr;       // EFR node blocks: entries (implicit element, local row) per node
+  int *nent_k = nullptr, *nent_l = nullptr;
   double *Uf_all = nullptr, *qf_all = nullptr, *Rw = nullptr, *gview = nullptr, *gw = nullptr, *Ustar = nullptr;
   double *r = nullptr, *s = nullptr, *xr = nullptr, *te = nullptr, *tg = nullptr, *yv = nullptr;
-  double *duhat = nullptr, *du = nullptr, *red = nullptr, *pwork = nullptr;
+  double *duhat = nullptr, *du = nullptr, *red = nullptr;
   void *A = nullptr, *B = nullptr, *C = nullptr, *D = nullptr, *LU = nullptr, *XB = nullptr, *S = nullptr, *Pinv = nullptr;
   int* piv = nullptr;
   int* status = nullptr;

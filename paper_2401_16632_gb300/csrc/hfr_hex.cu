@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(HT) k_hex_elem(const __grid_constant__ PhysPar
     const double uf = w.Uf[f * nf + m][v];
     double ub;
     if (t >= 0) {
-      ub = a.uhat[a.toff[t] + m * HNV + v];
+      ub = a.uhat[(size_t)a.fnode[(6 * e + f) * FS + m] * HNV + v];
     } else if (kf == FK_FAR) {
       ub = 0.5 * (uf + a.uinf[v]);
     } else {
@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(HJT, 1) k_hex_jacobian(const __grid_constant__
       w.Uf[f * nf + m][v] = s;
       const int t = w.tr[f];
       if (t >= 0) {
-        w.ub[f * nf + m][v] = T(a.uhat[a.toff[t] + m * HNV + v]);
+        w.ub[f * nf + m][v] = T(a.uhat[(size_t)a.fnode[(6 * e + f) * FS + m] * HNV + v]);
         w.un[f * nf + m][v] = s;
       } else {  // interface face: the explicit neighbour's state
         const int nb = a.nbr[6 * e + f], fn = a.nbr_face[6 * e + f];

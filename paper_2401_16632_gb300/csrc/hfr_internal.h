@@ -5,11 +5,22 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <vector>
 
 #include "hfr_common.cuh"
 
 namespace hfr {
+
+// NVTX range around one C-ABI call (host timeline of the enqueued work; a no-op without a tool)
+struct NvtxScope {
+  explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+  ~NvtxScope() { nvtxRangePop(); }
+  NvtxScope(const NvtxScope&) = delete;
+  NvtxScope& operator=(const NvtxScope&) = delete;
+};
+#define FR_NVTX(name) ::hfr::NvtxScope fr_nvtx_scope_(name)
 
 // counts every kernel launch of the library (reported by fr_kernel_launches)
 void count_launch();

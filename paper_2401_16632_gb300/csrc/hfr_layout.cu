@@ -28,9 +28,8 @@ int find_root(std::vector<int>& parent, int i) {
 
 }  // namespace
 
-static int efr_trace_nodes_impl(int nelem, const int* nbr, const int* nbr_face, const int* face_of,
-                               const unsigned char* implicit, int p, int* node_of, int* nvert_out,
-                               int* nnode_out) {
+static int efr_trace_nodes_impl(int nelem, const int* nbr, const int* nbr_face, const int* face_of, const int* bc,
+                                const unsigned char* implicit, int p, int* node_of, int* nvert_out, int* nnode_out) {
   if (nelem <= 0 || !nbr || !nbr_face || !face_of || !implicit || !node_of || !nvert_out || !nnode_out)
     return FR_ERR_INVALID_ARG;
   if (p < 1 || p > 5) return FR_ERR_INVALID_ARG;
@@ -39,18 +38,30 @@ static int efr_trace_nodes_impl(int nelem, const int* nbr, const int* nbr_face, 
   for (int e = 0; e < nelem; ++e) {
     for (int f = 0; f < 4; ++f) {
       const int nb = nbr[4 * e + f], nf = nbr_face[4 * e + f], id = face_of[4 * e + f];
-      if (nb < 0) return FR_ERR_UNSUPPORTED;  // EFR here is for meshes without boundary faces
-      if (nb >= nelem || nf < 0 || nf > 3 || id < 0 || (long long)id >= 4LL * nelem) return FR_ERR_INVALID_ARG;
+      if (id < 0 || (long long)id >= 4LL * nelem) return FR_ERR_INVALID_ARG;
+      nface = std::max(nface, id + 1);
+      if (nb < 0) {  // boundary face: wall or far field
+        if (!bc) return FR_ERR_UNSUPPORTED;
+        if (bc[4 * e + f] != 1 && bc[4 * e + f] != 2) return FR_ERR_INVALID_ARG;
+        continue;
+      }
+      if (nb >= nelem || nf < 0 || nf > 3) return FR_ERR_INVALID_ARG;
       if (nbr[4 * nb + nf] != e || nbr_face[4 * nb + nf] != f || face_of[4 * nb + nf] != id)
         return FR_ERR_INVALID_ARG;  // the neighbour relation must be symmetric
-      nface = std::max(nface, id + 1);
     }
   }
-  // trace faces: both sides implicit, numbered in increasing global face id
-  std::vector<int> trace_of_face(nface, -1);
+  // trace faces: both sides implicit, numbered in increasing global face id; boundary faces of
+  // implicit elements (discontinuous traces at their Gauss points) numbered apart, the same way
+  std::vector<int> trace_of_face(nface, -1), bface_of(nface, -1);
   for (int e = 0; e < nelem; ++e)
-    for (int f = 0; f < 4; ++f)
-      if (implicit[e] && implicit[nbr[4 * e + f]]) trace_of_face[face_of[4 * e + f]] = 0;
+    for (int f = 0; f < 4; ++f) {
+      const int nb = nbr[4 * e + f];
+      if (nb >= 0 && implicit[e] && implicit[nb]) trace_of_face[face_of[4 * e + f]] = 0;
+      if (nb < 0 && implicit[e]) bface_of[face_of[4 * e + f]] = 0;
+    }
+  int nbface = 0;
+  for (int id = 0; id < nface; ++id)
+    if (bface_of[id] == 0) bface_of[id] = nbface++;
   int ntrace = 0;
   for (int id = 0; id < nface; ++id)
     if (trace_of_face[id] == 0) trace_of_face[id] = ntrace++;
@@ -62,7 +73,7 @@ static int efr_trace_nodes_impl(int nelem, const int* nbr, const int* nbr_face, 
     if (!implicit[e]) continue;
     for (int f = 0; f < 4; ++f) {
       const int nb = nbr[4 * e + f], nf = nbr_face[4 * e + f];
-      if (!implicit[nb]) continue;
+      if (nb < 0 || !implicit[nb]) continue;
       for (int end = 0; end < 2; ++end) {
         const int i = 4 * e + kFaceCorner[f][end], j = 4 * nb + kFaceCorner[nf][end];
         touched[i] = touched[j] = 1;
@@ -79,7 +90,12 @@ static int efr_trace_nodes_impl(int nelem, const int* nbr, const int* nbr_face, 
     for (int f = 0; f < 4; ++f) {
       int* out = node_of + (static_cast<size_t>(e) * 4 + f) * n;
       const int nb = nbr[4 * e + f];
-      if (!implicit[e] || !implicit[nb]) {
+      if (nb < 0 && implicit[e]) {  // boundary trace: n nodes of its own after the interior ones
+        const int base = nvert + ntrace * (n - 2) + bface_of[face_of[4 * e + f]] * n;
+        for (int m = 0; m < n; ++m) out[m] = base + m;
+        continue;
+      }
+      if (!implicit[e] || nb < 0 || !implicit[nb]) {
         std::fill(out, out + n, -1);
         continue;
       }
@@ -90,7 +106,7 @@ static int efr_trace_nodes_impl(int nelem, const int* nbr, const int* nbr_face, 
     }
   }
   *nvert_out = nvert;
-  *nnode_out = nvert + ntrace * (n - 2);
+  *nnode_out = nvert + ntrace * (n - 2) + nbface * n;
   return FR_OK;
 }
 
@@ -152,11 +168,11 @@ static int mixed_trace_layout_impl(int nelem, const int* nbr, const int* nbr_fac
 }
 
 // the host vectors may fail to allocate: no C++ exception crosses the C ABI
-extern "C" int efr_trace_nodes(int nelem, const int* nbr, const int* nbr_face, const int* face_of,
+extern "C" int efr_trace_nodes(int nelem, const int* nbr, const int* nbr_face, const int* face_of, const int* bc,
                                const unsigned char* implicit, int p, int* node_of, int* nvert_out,
                                int* nnode_out) {
   try {
-    return efr_trace_nodes_impl(nelem, nbr, nbr_face, face_of, implicit, p, node_of, nvert_out, nnode_out);
+    return efr_trace_nodes_impl(nelem, nbr, nbr_face, face_of, bc, implicit, p, node_of, nvert_out, nnode_out);
   } catch (...) {
     return FR_ERR_OOM;
   }

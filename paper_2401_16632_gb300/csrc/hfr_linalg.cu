@@ -179,6 +179,7 @@ __global__ void k_precond_build(const __grid_constant__ TraceArgs a, T* __restri
       const int op = __shfl_xor_sync(0xffffffffu, p, o);
       if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
     }
+    if (p >= bs) p = c;  // no candidate compared (NaN column): any row, flagged singular
     if (!(best > T(0))) bad = true;
     if (lane == p) used = true;
     if (lane == 0) {

@@ -70,8 +70,34 @@ def test_layout_errors(pkg):
     with pytest.raises(pkg.HfrError, match="invalid"):
         pkg.efr_trace_nodes(bad, mesh.nbr_face, mesh.face_of, mesh.implicit, 2)
     walls = structured_quads(uniform_nodes(3, 0, 1), uniform_nodes(3, 0, 1), periodic=(True, False), p=2)
-    with pytest.raises(pkg.HfrError, match="unsupported|not"):
+    with pytest.raises(pkg.HfrError, match="unsupported|not"):  # boundary faces need their tags
         pkg.efr_trace_nodes(walls.nbr, walls.nbr_face, walls.face_of, walls.implicit, 2)
+    bad = walls.bc.copy()
+    bad[walls.nbr < 0] = 0
+    with pytest.raises(pkg.HfrError, match="invalid"):
+        pkg.efr_trace_nodes(walls.nbr, walls.nbr_face, walls.face_of, walls.implicit, 2, bc=bad)
+
+
+def test_layout_with_wall_and_far_field_faces_equals_the_oracle(pkg):
+    """Boundary faces of implicit elements carry discontinuous traces at their Gauss points,
+    numbered after the interior nodes as the oracle numbers them (walls below, far field above,
+    implicit wall rows and random masks)."""
+    from oracle.physics import NavierStokes2D
+    from workloads.mesh import BC_FARFIELD, BC_WALL
+
+    rng = np.random.default_rng(8)
+    u_inf = np.array([1.0, 0.2, 0.0, 2.5])
+    for k in range(5):
+        nx, ny = int(rng.integers(3, 7)), int(rng.integers(3, 7))
+        imp = rng.random(nx * ny) < 0.5 + 0.1 * k
+        imp[:nx] = True  # walls on implicit elements
+        m = structured_quads(uniform_nodes(nx, 0, 1), uniform_nodes(ny, 0, 1), periodic=(True, False),
+                             p=int(rng.integers(1, 6)), implicit=imp, bc_y=(BC_WALL, BC_FARFIELD))
+        d = EmbeddedDiscretisation(m, NavierStokes2D(mu=1e-2), u_inf)
+        node_of, nvert, nnode = pkg.efr_trace_nodes(m.nbr, m.nbr_face, m.face_of, m.implicit, int(m.p[0]),
+                                                    bc=m.bc)
+        assert nvert == d.nvert and nnode == d.nnode
+        assert np.array_equal(node_of, d.node_of)
 
 
 def test_mixed_degree_layout_equals_the_oracle(pkg):
