@@ -363,6 +363,9 @@ GENERAL_WORKLOADS = {
     "channel3d": ("channel3d: 3D Navier-Stokes Re=1.6e3 M=0.1 Taylor-Green-like field, 64x32x48 hexahedra, tanh "
                   "clustering beta=2.5, walls at y=+-1, periodic x and z, p=3 (blocks 320 / 480), three implicit wall "
                   "layers per wall (18 432 elements), SDIRK2 stage 1 with the ERK partner, Newton to 1e-8"),
+    "efr_vortex256": ("efr_vortex256: the vortex256 workload (256x256 periodic quads, p=4, all implicit, seeded 1e-3 "
+                      "noise, SDIRK2 stage 1 at 10x explicit CFL, Newton to 1e-8) with the EFR trace: continuous at the "
+                      "Gauss-Lobatto points of the trace faces (Sec. 2.2), 458 752 trace nodes x 4 variables"),
 }
 
 
@@ -375,14 +378,16 @@ def general_leg(pkg, torch, dev, l2buf, name, steps=(3, 2), warmup=(2, 1), peaks
     and the orthogonalisation, HBM roof)."""
     from workloads import make_config
 
-    w = make_config(name)
+    efr = name.startswith("efr_")
+    w = make_config(name[len("efr_"):] if efr else name)
+    tkind = pkg.FR_TRACE_EFR if efr else pkg.FR_TRACE_HFR
     peaks = peaks or {}
     out = {"workload": GENERAL_WORKLOADS[name], "implicit_dofs": w.dofs_implicit, "elements": w.mesh.nelem}
     res = {}
     for pi, (label, prec) in enumerate((("mixed", pkg.FR_PREC_FP32), ("fp64", pkg.FR_PREC_FP64))):
         if label not in paths:
             continue
-        ctx = pkg.Context(w.mesh, w.physics, precision=prec, tableau=pkg.FR_TAB_SDIRK2)
+        ctx = pkg.Context(w.mesh, w.physics, precision=prec, tableau=pkg.FR_TAB_SDIRK2, trace_kind=tkind)
         u0 = w.u0 if isinstance(w.u0, list) else list(w.u0)
         u_n = torch.tensor(ctx.pack_state(u0), device=dev)
         uh0 = ctx.hfr_initial_trace(u_n)
@@ -417,13 +422,33 @@ def general_leg(pkg, torch, dev, l2buf, name, steps=(3, 2), warmup=(2, 1), peaks
                       "launches": (ctx.kernel_launches() - l0) // steps[pi], "u": (us - u_n).clone(),
                       "nA": ctx.blk_nA.astype(np.float64), "nT": ctx.blk_nT.astype(np.float64),
                       "nh": int(ctx.info.trace_values)}
+        if label == "mixed" and steps[pi] > 0:
+            # the same stage as one CUDA graph (the per-phase times above come from the stream form)
+            ctx.imex_stage_set_graph(True)
+            for _ in range(max(warmup[pi], 1)):
+                run()
+            torch.cuda.synchronize()
+            l1 = ctx.kernel_launches()
+            gt = []
+            for _ in range(steps[pi]):
+                flush_l2(l2buf)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                gst = run()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                gt.append(e0.elapsed_time(e1))
+            res[label].update({"graph_ms": float(np.mean(gt)), "graph_launches": (ctx.kernel_launches() - l1) // steps[pi],
+                               "graph_stats": gst, "u_graph": (us - u_n).clone()})
+            ctx.imex_stage_set_graph(False)
         ctx.close()
         del R_hist, us, uh0, u_n
         torch.cuda.empty_cache()
     if "fp64" not in res:  # profiling aid: the mixed path alone
         m = res["mixed"]
-        return {"workload": out["workload"], "ms": m["ms"], "stats": m["stats"], "launches": m["launches"],
-                "phases_ms_total": {k: round(v[0], 3) for k, v in m["prof"].items()}}
+        return {"workload": out["workload"], "ms": m["ms"], "graph_ms": m.get("graph_ms"), "stats": m["stats"],
+                "launches": m["launches"], "phases_ms_total": {k: round(v[0], 3) for k, v in m["prof"].items()}}
     m, f = res["mixed"], res["fp64"]
     inc = f["u"].abs().max().item()
     nA, nT = m["nA"], m["nT"]
@@ -438,16 +463,20 @@ def general_leg(pkg, torch, dev, l2buf, name, steps=(3, 2), warmup=(2, 1), peaks
     alg = k_its * float(np.sum(nT * nT) * 4 + np.sum(nT) * 2 * 8) + sum((k + 2) * m["nh"] * 8 for k in range(1, k_its + 1))
     g_a = alg / (gms / max(gcnt, 1) * 1e-3) / 1e9
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    cond_kernel = ("k_big_lu + k_big_trsm_diag + k_big_gemm + k_big_xr (global-memory LU, batched GEMMs)"
+    cond_kernel = ("k_big_lu_panel + k_big_trsm_diag + k_big_gemm + k_big_xr (blocked LU, batched GEMMs)"
                    if name == "channel3d" else "k_condense_uneven<float> (shared-memory Gauss-Jordan bundles)")
     out.update({
-        "value": w.dofs_implicit / (m["ms"] * 1e-3), "unit": "implicit-stage DOF/s", "ms_per_step": m["ms"],
-        "steps": m["steps"], "newton_iterations": m["stats"]["newton_iterations"],
-        "gmres_iterations": m["stats"]["gmres_iterations"], "gpu_launches": int(m["launches"]),
+        "value": w.dofs_implicit / (m["graph_ms"] * 1e-3), "unit": "implicit-stage DOF/s", "ms_per_step": m["graph_ms"],
+        "stage_execution": "one CUDA graph per stage (mixed); the FP64 path and the per-phase times: stream form",
+        "stream_stage": {"ms_per_step": m["ms"], "value": w.dofs_implicit / (m["ms"] * 1e-3),
+                         "gpu_launches": int(m["launches"]),
+                         "graph_equals_stream": bool(torch.equal(m["u"], m["u_graph"]))},
+        "steps": m["steps"], "newton_iterations": m["graph_stats"]["newton_iterations"],
+        "gmres_iterations": m["graph_stats"]["gmres_iterations"], "gpu_launches": int(m["graph_launches"]),
         "fp64": {"value": w.dofs_implicit / (f["ms"] * 1e-3), "ms_per_step": f["ms"], "steps": f["steps"],
                  "newton_iterations": f["stats"]["newton_iterations"], "gmres_iterations": f["stats"]["gmres_iterations"],
                  "phases_ms_total": {k: round(v[0], 3) for k, v in f["prof"].items()}},
-        "mixed_over_fp64": f["ms"] / m["ms"],
+        "mixed_over_fp64": f["ms"] / m["graph_ms"],
         "mixed_vs_fp64_max_rel_diff": (m["u"] - f["u"]).abs().max().item() / inc,
         "phases_ms_total": {k: round(v[0], 3) for k, v in m["prof"].items()},
         "rooflines": {
@@ -460,13 +489,16 @@ def general_leg(pkg, torch, dev, l2buf, name, steps=(3, 2), warmup=(2, 1), peaks
         },
         "l2": "flushed between timed steps (256 MB write)",
     })
+    if efr:
+        out["trace_values"] = m["nh"]
+        out["hfr_trace_values"] = int(2 * w.mesh.nelem * (w.p + 1) * 4)
     return out
 
 
-def cpu_baseline(workload="vortex256"):
+def cpu_baseline(workload="vortex256", npatch=None):
     """The FP64 oracle, as it stands, on a bounded sample of the same workload: the stage-1
-    Newton solve of the same vortex on a PATCH x PATCH periodic patch at the workload's element
-    size, p and time step, direct trace solve."""
+    Newton solve of the same vortex on a PATCH x PATCH periodic patch (or npatch x npatch) at the
+    workload's element size, p and time step, direct trace solve."""
     from oracle.fr import Discretisation
     from oracle.physics import make_physics
     from oracle.stepping import TABLEAUX, newton_stage
@@ -474,7 +506,7 @@ def cpu_baseline(workload="vortex256"):
     from workloads.states import isentropic_vortex, sample_points
 
     full = make_config(workload)
-    npatch = PATCH[workload]
+    npatch = npatch or PATCH[workload]
     nfull = int(round(np.sqrt(full.mesh.nelem)))
     w = make_config("vortex", n=npatch, p=full.p)
     scale = (10.0 / nfull) / (10.0 / npatch)
@@ -492,6 +524,19 @@ def cpu_baseline(workload="vortex256"):
             "sample": f"stage-1 Newton solve (to 1e-8, {info['iterations']} iterations, direct trace solve) of the "
                       f"vortex on a {npatch}x{npatch} periodic patch at the {workload} spacing, p={full.p}, same dt: "
                       f"{mesh.nelem} elements, {dofs} DOF, {el:.1f} s"}
+
+
+def cpu_baseline_single_core(workload="vortex256", npatch=8):
+    """The same oracle sample on one host core: a child process with every BLAS / OpenMP pool
+    limited to one thread before numpy loads (a smaller patch keeps it to seconds)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1", VECLIB_MAXIMUM_THREADS="1", NUMEXPR_NUM_THREADS="1")
+    code = ("import json, bench; r = bench.cpu_baseline(%r, npatch=%d); r['cores'] = 1; print(json.dumps(r))"
+            % (workload, npatch))
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    if out.returncode != 0:
+        return {"error": out.stderr.strip().splitlines()[-1] if out.stderr.strip() else "failed"}
+    return json.loads(out.stdout.strip().splitlines()[-1])
 
 
 def _threads():
@@ -622,6 +667,7 @@ def main():
     ap.add_argument("--no-reuse", action="store_true", help="skip the Jacobian-reuse (imex_steps) leg")
     ap.add_argument("--no-tf32", action="store_true", help="skip the single-pass TF32 condensation leg")
     ap.add_argument("--no-channel", action="store_true", help="skip the hexahedral channel leg")
+    ap.add_argument("--no-efr", action="store_true", help="skip the EFR-trace leg on the vortex256 mesh")
     ap.add_argument("--general-only", default=None, choices=list(GENERAL_WORKLOADS),
                     help="profiling aid: time only this general-mesh workload's mixed path")
     ap.add_argument("--no-boundary-layer", action="store_true",
@@ -818,6 +864,12 @@ def main():
             line["channel3d"] = general_leg(pkg, torch, dev, l2buf, "channel3d", steps=(2, 1), warmup=(1, 1), peaks=peaks)
         except Exception as exc:  # reported, never fatal
             line["channel3d"] = {"error": str(exc)}
+    if not args.no_efr:
+        try:
+            line["efr_vortex256"] = general_leg(pkg, torch, dev, l2buf, "efr_vortex256", steps=(3, 1), warmup=(1, 1),
+                                                peaks=peaks)
+        except Exception as exc:  # reported, never fatal
+            line["efr_vortex256"] = {"error": str(exc)}
     if not args.no_uneven:
         try:
             line["uneven_condense"] = uneven_condense(pkg, torch, dev)
@@ -828,6 +880,10 @@ def main():
             line["cpu_baseline"] = cpu_baseline(args.workload)
         except Exception as exc:  # reported, never fatal
             line["cpu_baseline"] = {"error": str(exc)}
+        try:
+            line["cpu_baseline"]["single_core"] = cpu_baseline_single_core(args.workload)
+        except Exception as exc:  # reported, never fatal
+            line["cpu_baseline"]["single_core"] = {"error": str(exc)}
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:

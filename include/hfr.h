@@ -154,6 +154,7 @@ typedef struct {
   int general;            /* 1: general path (packed layouts) */
   size_t state_values;    /* values of one state copy (nelem ns nv on the uniform path) */
   size_t trace_values;    /* values of one trace vector (ntrace n nv on the uniform path) */
+  int face_points;        /* general path: entries of the face-point trace map (hfr_export 64) */
 } fr_ctx_info;
 
 typedef struct {
@@ -284,13 +285,16 @@ int hfr_backsolve(fr_ctx* ctx, const double* duhat, double* du, int refine);
 
 /* Copy a context block array to a caller device buffer (for inspection / parity tests).
  * which: 0 A, 1 B, 2 C, 3 D, 4 S, 5 X_B, 6 x_r (FP64), 7 t_k (FP64), 8 r (FP64), 9 s (FP64),
- * 10 global t (FP64), 11 face-block-Jacobi inverses (ntrace x bs x bs, bs = n nv).  Block arrays
- * are in the context precision; dst must hold `bytes`. */
+ * 10 global t (FP64), 11 face-block-Jacobi inverses (ntrace x bs x bs, bs = n nv); general-mesh
+ * contexts also 64: the trace point of every element face point (int32, nface x nelem x face-point
+ * stride, -1 off traces).  Block arrays are in the context precision; dst must hold `bytes`. */
 int hfr_export(fr_ctx* ctx, int which, void* dst, size_t bytes);
 /* The reverse of hfr_export for the arrays 0..9 (A, B, C, D, S, X_B, x_r, t_k, r, s): overwrite the
  * context array with `bytes` (exactly its size) from the caller device buffer src, e.g. to condense
  * blocks formed elsewhere or to plant a defective block in a test.  A condensation held for
- * FR_JAC_KEEP is dropped.  FR_ERR_INVALID_ARG for another array or size. */
+ * FR_JAC_KEEP is dropped.  In a bounds-checked build (FR_CHECKED) a general-mesh context also takes
+ * array 64 (the face-point trace map), to plant a corrupted index that the device checks must catch.
+ * FR_ERR_INVALID_ARG for another array or size. */
 int hfr_import(fr_ctx* ctx, int which, const void* src, size_t bytes);
 
 /* One stage of the IMEX step (Algorithm 1):
@@ -409,6 +413,16 @@ int fr_profile_enable(fr_ctx* ctx, int on);
 int fr_profile_read(const fr_ctx* ctx, fr_profile* out /* host */);
 /* Number of kernels this library has launched in this process (all contexts). */
 unsigned long long fr_kernel_launches(void);
+
+/* Bounds-checked build (library compiled with FR_CHECKED; no counterpart in the paper: the
+ * substitute for a memory checker on devices where none may run).  Every mesh-derived gather /
+ * scatter index of the residual, the element blocks, the trace assembly, the element-view
+ * mat-vec and the back-substitution is checked on the device: an index outside its array is
+ * counted, the first one recorded, and the access redirected to entry 0 (no trap, the kernel goes
+ * on; results are then meaningless).  Reads and clears the record of every kernel so far: first =
+ * (site << 48) | index of the first failure (0: none), count = failures.  FR_ERR_UNSUPPORTED in a
+ * build without the checks. */
+int fr_checked_status(unsigned long long* first, unsigned long long* count);
 
 /* Allocation-free condensation, for callers that cannot let a library allocate device memory
  * (a host code with its own pooled device-memory budget, a plugin handed pre-allocated buffers).

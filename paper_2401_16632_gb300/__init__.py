@@ -25,6 +25,8 @@ __all__ = [
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libhfr.so")
+# the bounds-checked build (FR_CHECKED), built by build(checked=True)
+LIB_CHECKED_PATH = os.path.join(HERE, "libhfr_checked.so")
 
 FR_PREC_FP64, FR_PREC_FP32, FR_PREC_TF32, FR_PREC_BF16 = 0, 1, 2, 3
 FR_TAB_BE, FR_TAB_SDIRK2 = 0, 1
@@ -37,7 +39,8 @@ FR_JAC_EVERY_NEWTON, FR_JAC_ONCE_PER_STAGE, FR_JAC_KEEP = 0, 1, 2
 FR_CONDENSE_FMA, FR_CONDENSE_TENSOR_PRODUCTS, FR_CONDENSE_TENSOR, FR_CONDENSE_TENSOR_TF32 = 0, 1, 2, 3
 (FR_OK, FR_ERR_INVALID_ARG, FR_ERR_CUDA, FR_ERR_SINGULAR, FR_ERR_NOT_CONVERGED, FR_ERR_DIVERGED, FR_ERR_TIMEOUT,
  FR_ERR_OOM, FR_ERR_UNSUPPORTED) = range(9)
-EXPORT = {"A": 0, "B": 1, "C": 2, "D": 3, "S": 4, "XB": 5, "xr": 6, "t_k": 7, "r": 8, "s": 9, "t": 10, "Pinv": 11}
+EXPORT = {"A": 0, "B": 1, "C": 2, "D": 3, "S": 4, "XB": 5, "xr": 6, "t_k": 7, "r": 8, "s": 9, "t": 10, "Pinv": 11,
+          "fnode": 64}
 
 # every symbol declared in include/hfr.h
 ABI_SYMBOLS = [
@@ -72,6 +75,7 @@ ABI_SYMBOLS = [
     "fr_profile_enable",
     "fr_profile_read",
     "fr_kernel_launches",
+    "fr_checked_status",
     "hfr_condense_noalloc",
     "hfr_import",
     "fr_measure_peak",
@@ -133,6 +137,7 @@ class fr_ctx_info(ctypes.Structure):
         ("general", ctypes.c_int),
         ("state_values", ctypes.c_size_t),
         ("trace_values", ctypes.c_size_t),
+        ("face_points", ctypes.c_int),
     ]
 
 
@@ -228,6 +233,7 @@ def load_library(path: str = LIB_PATH):
     lib.fr_profile_read.argtypes = [vp, ctypes.POINTER(fr_profile)]
     lib.fr_kernel_launches.argtypes = []
     lib.fr_kernel_launches.restype = ctypes.c_ulonglong
+    lib.fr_checked_status.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]
     lib.hfr_condense_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp,
                                          dp, dp, dp, dp, dp, vp]
     lib.hfr_import.argtypes = [vp, ctypes.c_int, dp, ctypes.c_size_t]
@@ -353,6 +359,18 @@ def hfr_condense_uneven(nA, nT, A, B, C, D, r, s, precision=FR_PREC_FP32, stream
         err.failed_element = failed.value
         raise err
     return out
+
+
+def fr_checked_status():
+    """Bounds-checked build (see include/hfr.h): (site, index, count) of the index failures the
+    device checks recorded since the last call (site 0: none); raises HfrError (FR_ERR_UNSUPPORTED)
+    in a build without the checks."""
+    lib = load_library()
+    first, count = ctypes.c_ulonglong(0), ctypes.c_ulonglong(0)
+    rc = lib.fr_checked_status(ctypes.byref(first), ctypes.byref(count))
+    if rc != 0:
+        raise HfrError(rc)
+    return int(first.value >> 48), int(first.value & ((1 << 48) - 1)), int(count.value)
 
 
 def fr_measure_peak(which, stream=None):
@@ -624,6 +642,7 @@ class Context:
             if which == "Pinv":
                 tp = np.diff(self.trace_off) // i.nv
                 sizes["Pinv"] = (int(np.sum((tp * i.nv) ** 2)), blk)
+            sizes["fnode"] = (int(i.face_points), self.torch.int32)
             n, dt = sizes[which]
             out = self.torch.empty(max(n, 1), dtype=dt, device=self.dev)
             self._check(self.lib.hfr_export(self.h, EXPORT[which], _ptr(out), n * out.element_size()))

@@ -15,6 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhfr.so")
+LIB_CHECKED = os.path.join(HERE, "libhfr_checked.so")
 UNITS = ["hfr_residual", "hfr_jacobian", "hfr_condense", "hfr_linalg", "hfr_krylov", "hfr_gmres_fused", "hfr_api", "hfr_noalloc", "hfr_layout", "hfr_peaks", "hfr_general", "hfr_hex"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
@@ -38,17 +39,20 @@ def _sources_newer_than(target: str) -> bool:
     return os.path.getmtime(hdr) > t
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    """Compile every CUDA translation unit for sm_103a and link libhfr.so; returns its path."""
-    if not force and not _sources_newer_than(LIB):
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=None, checked: bool = False) -> str:
+    """Compile every CUDA translation unit for sm_103a and link libhfr.so (checked: the
+    bounds-checked variant libhfr_checked.so, compiled with FR_CHECKED); returns its path."""
+    lib = LIB_CHECKED if checked else LIB
+    bdir = BUILD + "_checked" if checked else BUILD
+    if not force and not _sources_newer_than(lib):
+        return lib
+    os.makedirs(bdir, exist_ok=True)
     exe = nvcc()
-    extra = list(extra_flags or [])
+    extra = list(extra_flags or []) + (["-DFR_CHECKED"] if checked else [])
 
     def compile_unit(u):
         src = os.path.join(CSRC, u + ".cu")
-        obj = os.path.join(BUILD, u + ".o")
+        obj = os.path.join(bdir, u + ".o")
         cmd = [exe, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -59,13 +63,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
 
     with ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
         objs = list(ex.map(compile_unit, UNITS))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [exe, "-shared", *ARCH, *objs, "-ldl", "-o", tmp]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

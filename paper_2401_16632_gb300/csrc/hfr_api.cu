@@ -24,6 +24,20 @@ using namespace hfr;
 
 static std::atomic<unsigned long long> g_launches(0);
 void hfr::count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long hfr::launch_count() { return g_launches.load(std::memory_order_relaxed); }
+namespace {
+using ChkCollect = int (*)(unsigned long long*, unsigned long long*);
+std::vector<ChkCollect>& checked_units() {
+  static std::vector<ChkCollect> v;
+  return v;
+}
+}  // namespace
+void hfr::checked_register(int (*collect)(unsigned long long* first, unsigned long long* count)) {
+  checked_units().push_back(collect);
+}
+void hfr::launch_count_add(long long delta) {
+  g_launches.fetch_add((unsigned long long)delta, std::memory_order_relaxed);
+}
 
 // Device-side state of a stage run as one CUDA graph (imex_stage_set_graph): Newton norms and
 // counters, and the arguments of the next GMRES restart cycle.
@@ -684,6 +698,7 @@ extern "C" int fr_ctx_query(const fr_ctx* ctx, fr_ctx_info* info) {
   info->general = 0;
   info->state_values = (size_t)ctx->E * ctx->nA;
   info->trace_values = (size_t)ctx->ntrace * ctx->n * ctx->nv;
+  info->face_points = 0;
   return FR_OK;
 }
 
@@ -727,6 +742,7 @@ static ResArgs res_args(fr_ctx* ctx, const double* u, const double* uhat) {
   a.qf_all = ctx->qf_all;
   a.Uf_out = ctx->Uf_all;
   a.qf_out = ctx->qf_all;
+  a.ntrace = ctx->ntrace;
   return a;
 }
 
@@ -791,6 +807,8 @@ static int jacobian_blocks(fr_ctx* ctx, const double* u, const double* uhat, dou
   j.kind = ctx->kind;
   j.tr_of = ctx->tr_of;
   j.Uf_all = ctx->Uf_all;
+  j.E = ctx->E;
+  j.ntrace = ctx->ntrace;
   j.a_dt = a_dt;
   j.A = ctx->A;
   j.B = ctx->B;
@@ -1434,7 +1452,12 @@ static void* ctx_array(fr_ctx* ctx, int which, size_t* need) {
 extern "C" int hfr_import(fr_ctx* ctx, int which, const void* src, size_t bytes) {
   if (!ctx || !src) return FR_ERR_INVALID_ARG;
   if (ctx->gen) {
-    if (which < 0 || which > 9) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_import: array not importable");
+#ifdef FR_CHECKED
+    const bool map = which == 64;  // the face-point trace map, a planted defect in checked builds
+#else
+    const bool map = false;
+#endif
+    if ((which < 0 || which > 9) && !map) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_import: array not importable");
     return hfr::gen::export_array(ctx->gen, which, const_cast<void*>(src), bytes, true);
   }
   if (which < 0 || which > 9) return set_err(ctx, FR_ERR_INVALID_ARG, "hfr_import: array not importable");
@@ -1559,8 +1582,8 @@ __global__ void k_gmres_after(StageDev* sd, const GmresState* st, const unsigned
 __global__ void k_gmres_end(StageDev* sd) { sd->gtot += sd->gm_total; }
 
 // a conditional node after the work captured so far on s; returns its body graph
-static cudaError_t add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
-                                   cudaGraph_t* body) {
+cudaError_t hfr::graph_add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                                       cudaGraph_t* body) {
   cudaStreamCaptureStatus cs;
   cudaGraph_t g = nullptr;
   const cudaGraphNode_t* deps = nullptr;
@@ -1580,6 +1603,21 @@ static cudaError_t add_conditional(cudaStream_t s, cudaGraphConditionalHandle h,
   if ((e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &p)) != cudaSuccess) return e;
   *body = p.conditional.phGraph_out[0];
   return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// a conditional handle of the graph that s is capturing into
+cudaError_t hfr::graph_conditional_handle(cudaStream_t s, unsigned dflt, unsigned flags, cudaGraphConditionalHandle* h) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  return cudaGraphConditionalHandleCreate(h, g, dflt, flags);
+}
+using hfr::graph_add_conditional;
+static inline cudaError_t add_conditional(cudaStream_t s, cudaGraphConditionalHandle h,
+                                          cudaGraphConditionalNodeType type, cudaGraph_t* body) {
+  return graph_add_conditional(s, h, type, body);
 }
 
 static int stage_graph_capture(fr_ctx* ctx, const StageGraphKey& key) {
@@ -1803,8 +1841,12 @@ static int imex_stage_graph(fr_ctx* ctx, const StageGraphKey& key, fr_stage_stat
 }
 
 extern "C" int imex_stage_set_graph(fr_ctx* ctx, int on) {
-  if (ctx && ctx->gen && on) return set_err(ctx, FR_ERR_UNSUPPORTED, "imex_stage_set_graph: not built for general meshes");
   if (!ctx || (on != 0 && on != 1)) return set_err(ctx, FR_ERR_INVALID_ARG, "imex_stage_set_graph: bad argument");
+  if (ctx->gen) {
+    const int rc = hfr::gen::set_graph(ctx->gen, on);
+    if (rc == FR_OK) ctx->use_graph = on;
+    return rc;
+  }
   if (on && (ctx->Eim == 0 || (ctx->ntrace > 0 && ctx->gm_mode != 1)))
     return set_err(ctx, FR_ERR_UNSUPPORTED, "imex_stage_set_graph: needs implicit elements and the single-launch GMRES cycle");
   ctx->use_graph = on;
@@ -2032,6 +2074,23 @@ extern "C" int fr_profile_read(const fr_ctx* ctx, fr_profile* out) {
 }
 
 extern "C" unsigned long long fr_kernel_launches(void) { return g_launches.load(); }
+
+extern "C" int fr_checked_status(unsigned long long* first, unsigned long long* count) {
+  if (!first || !count) return FR_ERR_INVALID_ARG;
+  *first = 0;
+  *count = 0;
+#ifdef FR_CHECKED
+  for (ChkCollect f : checked_units()) {
+    unsigned long long a = 0, c = 0;
+    if (f(&a, &c) != 0) return FR_ERR_CUDA;
+    if (*first == 0 && a != 0) *first = a;
+    *count += c;
+  }
+  return FR_OK;
+#else
+  return FR_ERR_UNSUPPORTED;
+#endif
+}
 
 extern "C" int fr_last_error(const fr_ctx* ctx, fr_error_info* info) {
   if (!ctx || !info) return FR_ERR_INVALID_ARG;

@@ -16,6 +16,11 @@
 // at a time; arithmetic in the block precision T.  Included by hfr_condense.cu (uses UnevenArgs and DEV_ERR_*).
 #pragma once
 
+// FP32 batched GEMMs on the tensor cores (1) or the CUDA cores (0): a build flag for timing
+#ifndef HFR_BIG_GEMM_TC
+#define HFR_BIG_GEMM_TC 1
+#endif
+
 namespace hfr {
 namespace big {
 
@@ -429,6 +434,216 @@ __global__ void __launch_bounds__(BT) k_big_gemm(const __grid_constant__ UnevenA
   }
 }
 
+// 3b' / 4'. the same batched GEMMs for FP32 blocks on the tensor cores (tcgen05, 3xTF32: each
+// operand split into a TF32 high part and the remainder, hi*hi + hi*lo + lo*hi accumulated in FP32
+// in tensor memory).  One CTA per output tile of 256 rows (m) x 128 columns (n) of one element,
+// computed transposed: the tensor-memory lanes hold the 128 columns n and its 256 FP32 columns the
+// rows m, so that in the epilogue the 32 lanes of a warp read and write 32 consecutive n of one
+// row (coalesced).  K runs in chunks of 32, staged K-major without swizzle (hfr_tc.cuh) in two
+// shared-memory buffers, one mbarrier per buffer; the next chunk's global loads are in flight
+// while the tensor core works on the current one.  Thread 0 issues the MMAs; in the epilogue warp
+// w reads lanes 32 (w % 4).. and the column half w / 4 of the accumulator.
+namespace btc {
+constexpr int TM = 256, TN = 128, KC = 32, THREADS = 256;
+constexpr uint32_t SBO = (KC / 4) * 128u + 16u;  // 8-row groups padded by 16 bytes
+constexpr uint32_t N_BYTES = (TN / 8) * SBO;     // the n-rows operand (MMA A, 128 rows), hi or lo
+constexpr uint32_t M_BYTES = (TM / 8) * SBO;     // the m-rows operand (MMA B, 256 rows), hi or lo
+constexpr uint32_t STAGE = 2 * N_BYTES + 2 * M_BYTES;
+constexpr uint32_t SMEM = 2 * STAGE + 64;
+constexpr int A_PER = TM * KC / THREADS, B_PER = TN * KC / THREADS;  // values a thread stages per chunk
+static_assert(SMEM <= 232448, "shared memory");
+}  // namespace btc
+
+__global__ void __launch_bounds__(btc::THREADS, 1) k_big_gemm_tc(const __grid_constant__ UnevenArgs a,
+                                                                const int* __restrict__ list, int base, int nlist,
+                                                                int uni_nA, int uni_nT, int phase, int jb) {
+  using namespace tc;
+  using namespace btc;
+  extern __shared__ __align__(1024) unsigned char btc_smem[];
+  if ((int)blockIdx.z >= nlist) return;
+  const Elem E = elem_of(a, list, base + blockIdx.z, uni_nA, uni_nT);
+  const int nA = E.nA, nT = E.nT;
+  const bool cm = a.colmajor != 0;
+  int M, N, K, m_off = 0, k_off = 0, n_off = 0;
+  float* L = reinterpret_cast<float*>(a.LU) + E.o[0];
+  float* X = reinterpret_cast<float*>(a.XB) + E.o[1];
+  const float* Cm = reinterpret_cast<const float*>(a.C) + E.o[1];
+  const float* Dm = reinterpret_cast<const float*>(a.D) + E.o[2];
+  float* S = reinterpret_cast<float*>(a.S) + E.o[2];
+  if (phase == 0) {
+    const int r0 = jb * NB, r1 = min(nA, r0 + NB);
+    M = nA - r1;
+    N = nT;
+    K = r1 - r0;
+    m_off = r1;
+    k_off = r0;
+  } else if (phase == 1) {
+    const int r0 = jb * NB, r1 = min(nA, r0 + NB);
+    M = r0;
+    N = nT;
+    K = r1 - r0;
+    k_off = r0;
+  } else if (phase == 2) {
+    M = nT;
+    N = nT;
+    K = nA;
+  } else {
+    const int j0 = jb * lu_panel<float>(), j1 = min(nA, j0 + lu_panel<float>());
+    M = nA - j1;
+    N = nA - j1;
+    K = j1 - j0;
+    m_off = j1;
+    n_off = j1;
+    k_off = j0;
+  }
+  const int tm0 = blockIdx.y * TM, tn0 = blockIdx.x * TN;
+  if (M <= 0 || K <= 0 || tm0 >= M || tn0 >= N) return;  // uniform over the CTA
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(btc_smem + 2 * STAGE);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  if (t == 0) {
+    mbar_init(smem_u32(mbar), 1);
+    mbar_init(smem_u32(mbar + 1), 1);
+  }
+  if (w == 0) tmem_alloc(smem_u32(tslot), 256);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *tslot;
+  const bool a_mfast = phase == 2 && cm;  // A(m, k) contiguous in m (column-major C)
+  // staging slots of this thread: A (m, k) with k fastest: rows (t >> 3) + 32 u, k 4 (t & 7) + e;
+  // m fastest: row 32 w + lane, k = u; B (k, n): column t & 127, k (t >> 7) + 2 u
+  float ra[A_PER], rb[B_PER];
+  auto gload = [&](int k0) {
+#pragma unroll
+    for (int u = 0; u < A_PER; ++u) {
+      const int m = tm0 + (a_mfast ? 32 * w + lane : (t >> 3) + 32 * (u >> 2));
+      const int k = k0 + (a_mfast ? u : 4 * (t & 7) + (u & 3));
+      float v = 0.f;
+      if (m < M && k < K) {
+        if (phase != 2)
+          v = L[(size_t)(m_off + m) * nA + k_off + k];
+        else
+          v = cm ? Cm[(size_t)k * nT + m] : Cm[(size_t)m * nA + k];
+      }
+      ra[u] = v;
+    }
+#pragma unroll
+    for (int u = 0; u < B_PER; ++u) {
+      const int n = tn0 + (t & 127), k = k0 + (t >> 7) + 2 * u;
+      float v = 0.f;
+      if (n < N && k < K) v = phase == 3 ? L[(size_t)(k_off + k) * nA + n_off + n] : X[(size_t)(k_off + k) * nT + n];
+      rb[u] = v;
+    }
+  };
+  auto sstore = [&](int b) {
+    unsigned char* Nhi = btc_smem + b * STAGE;
+    unsigned char* Nlo = Nhi + N_BYTES;
+    unsigned char* Mhi = Nlo + N_BYTES;
+    unsigned char* Mlo = Mhi + M_BYTES;
+    if (a_mfast) {
+#pragma unroll
+      for (int u = 0; u < A_PER; ++u) {
+        float h, l;
+        split_tf32(ra[u], h, l);
+        const uint32_t o = kmajor_offset(32 * w + lane, u, SBO);
+        *reinterpret_cast<float*>(Mhi + o) = h;
+        *reinterpret_cast<float*>(Mlo + o) = l;
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < A_PER; u += 4) {
+        float h[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) split_tf32(ra[u + e], h[e], l[e]);
+        const uint32_t o = kmajor_offset((t >> 3) + 32 * (u >> 2), 4 * (t & 7), SBO);
+        *reinterpret_cast<float4*>(Mhi + o) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4*>(Mlo + o) = make_float4(l[0], l[1], l[2], l[3]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < B_PER; ++u) {
+      float h, l;
+      split_tf32(rb[u], h, l);
+      const uint32_t o = kmajor_offset(t & 127, (t >> 7) + 2 * u, SBO);
+      *reinterpret_cast<float*>(Nhi + o) = h;
+      *reinterpret_cast<float*>(Nlo + o) = l;
+    }
+  };
+  const int nch = (K + KC - 1) / KC;
+  const uint32_t idesc = idesc_tf32(TN, TM);  // M = 128 (n on the lanes), N = 256 (m)
+  bool ok = true;
+  gload(0);
+  for (int c = 0; c < nch; ++c) {
+    const int b = c & 1;
+    if (c >= 2) {  // the MMAs of chunk c - 2 read this buffer
+      ok = mbar_wait(smem_u32(mbar + b), (uint32_t)(((c - 2) >> 1) & 1), TIMEOUT_NS);
+      if (__syncthreads_or(!ok)) {
+        ok = false;
+        break;
+      }
+      fence_after_sync();
+    }
+    sstore(b);
+    fence_proxy_async();
+    fence_before_sync();
+    __syncthreads();
+    if (t == 0) {
+      fence_after_sync();
+      const uint32_t nh = smem_u32(btc_smem + b * STAGE), nl = nh + N_BYTES, mh = nl + N_BYTES, ml = mh + M_BYTES;
+#pragma unroll 1
+      for (int kk = 0; kk < KC / 8; ++kk) {
+        const uint32_t off = (uint32_t)kk * 256u;  // two core matrices along k per instruction
+        const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+        mma_tf32(tmem, desc_noswizzle(nh + off, 128, SBO), desc_noswizzle(mh + off, 128, SBO), idesc, acc);
+        mma_tf32(tmem, desc_noswizzle(nh + off, 128, SBO), desc_noswizzle(ml + off, 128, SBO), idesc, 1u);
+        mma_tf32(tmem, desc_noswizzle(nl + off, 128, SBO), desc_noswizzle(mh + off, 128, SBO), idesc, 1u);
+      }
+      mma_commit(smem_u32(mbar + b));
+    }
+    if (c + 1 < nch) gload((c + 1) * KC);
+  }
+  if (ok) {  // the last commit completes after every MMA before it
+    ok = mbar_wait(smem_u32(mbar + ((nch - 1) & 1)), (uint32_t)(((nch - 1) >> 1) & 1), TIMEOUT_NS);
+    ok = !__syncthreads_or(!ok);
+  }
+  fence_after_sync();
+  if (ok) {
+    const int q = w & 3, hh = w >> 2;
+    const int n = tn0 + 32 * q + lane;
+    const uint32_t tl = (uint32_t)(32 * q) << 16;
+#pragma unroll 1
+    for (int cc = 0; cc < 8; ++cc) {
+      float v[16];
+      const int m0 = tm0 + 128 * hh + 16 * cc;
+      tmem_ld16(tmem + tl + (uint32_t)(128 * hh + 16 * cc), v);
+      if (n >= N) continue;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int m = m0 + u;
+        if (m >= M) break;
+        if (phase <= 1) {
+          X[(size_t)(m_off + m) * nT + n] -= v[u];
+        } else if (phase == 3) {
+          L[(size_t)(m_off + m) * nA + n_off + n] -= v[u];
+        } else {
+          const float d = cm ? Dm[(size_t)n * nT + m] : Dm[(size_t)m * nT + n];
+          S[(size_t)m * nT + n] = d - v[u];
+        }
+      }
+    }
+  } else if (t == 0) {
+    atomicOr(a.status, DEV_ERR_TIMEOUT);
+    // the MMAs in flight finish (bounded) before their tensor memory is released
+    mbar_wait(smem_u32(mbar), 0, TIMEOUT_NS);
+    mbar_wait(smem_u32(mbar + 1), 0, TIMEOUT_NS);
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  if (w == 0) tmem_dealloc(tmem, 256);
+}
+
 // 5. x_r = A^{-1} r (interchanges, forward, backward; FP64) and t = s - C x_r
 template <typename T>
 __global__ void __launch_bounds__(BT) k_big_xr(const __grid_constant__ UnevenArgs a, const int* __restrict__ list,
@@ -500,6 +715,25 @@ cudaError_t condense_big(const UnevenArgs& a, const int* list, int nlist, int un
   const int gridp = nlist < occ * nsm ? nlist : (occ > 0 ? occ : 1) * nsm;
   (hfr::count_launch(), k_big_lu_init<T><<<grid1, BT, 0, st>>>(a, list, nlist, uni_nA, uni_nT));
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const bool tcg = sizeof(T) == 4 && HFR_BIG_GEMM_TC;  // FP32 GEMMs on the tensor cores
+  if (tcg && (e = cudaFuncSetAttribute(k_big_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)btc::SMEM)) != cudaSuccess)
+    return e;
+  // one batched GEMM phase over elements [base, base + cnt): rows x cols of the largest shape.  The
+  // tensor cores take S = D - C X_B (K = nA); the K = 32 updates of the LU and the triangular
+  // solves, bound by the read-modify-write of their outputs, stay on the CUDA cores (two CTAs per
+  // SM against one of the tensor-core kernel: measured faster on hexahedra)
+  auto gemm = [&](int base, int cnt, int rows, int cols, int phase, int jb) {
+    if (tcg && phase == 2) {
+      const dim3 g((cols + btc::TN - 1) / btc::TN, (rows + btc::TM - 1) / btc::TM, cnt);
+      (hfr::count_launch(), k_big_gemm_tc<<<g, btc::THREADS, btc::SMEM, st>>>(a, list, base, cnt, uni_nA, uni_nT,
+                                                                                 phase, jb));
+    } else {
+      constexpr int TB = GemmCfg<T>::BM;
+      const dim3 g((cols + TB - 1) / TB, (rows + TB - 1) / TB, cnt);
+      (hfr::count_launch(), k_big_gemm<T><<<g, BT, 0, st>>>(a, list, base, cnt, uni_nA, uni_nT, phase, jb));
+    }
+  };
   const int npan = (max_nA + lu_panel<T>() - 1) / lu_panel<T>();
   for (int jb = 0; jb < npan; ++jb) {
     (hfr::count_launch(), k_big_lu_panel<T><<<gridp, BT, psm, st>>>(a, list, nlist, uni_nA, uni_nT, jb));
@@ -508,9 +742,7 @@ cudaError_t condense_big(const UnevenArgs& a, const int* list, int nlist, int un
     const int rest = max_nA - (jb + 1) * lu_panel<T>();
     for (int base = 0; base < nlist; base += 65535) {
       const int cnt = nlist - base < 65535 ? nlist - base : 65535;
-      constexpr int TB = GemmCfg<T>::BM;
-      const dim3 gl((rest + TB - 1) / TB, (rest + TB - 1) / TB, cnt);
-      (hfr::count_launch(), k_big_gemm<T><<<gl, BT, 0, st>>>(a, list, base, cnt, uni_nA, uni_nT, 3, jb));
+      gemm(base, cnt, rest, rest, 3, jb);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -521,19 +753,15 @@ cudaError_t condense_big(const UnevenArgs& a, const int* list, int nlist, int un
   for (int base = 0; base < nlist; base += CH) {
     const int cnt = nlist - base < CH ? nlist - base : CH;
     const dim3 gd((max_nT + 127) / 128, cnt);
-    constexpr int TB = GemmCfg<T>::BM;
-    const dim3 gg((max_nT + TB - 1) / TB, (max_nA + TB - 1) / TB, cnt);
     for (int jb = 0; jb < nblk; ++jb) {
       (hfr::count_launch(), k_big_trsm_diag<T><<<gd, 128, 0, st>>>(a, list, base, cnt, uni_nA, uni_nT, jb, 0));
-      if (jb + 1 < nblk)
-        (hfr::count_launch(), k_big_gemm<T><<<gg, BT, 0, st>>>(a, list, base, cnt, uni_nA, uni_nT, 0, jb));
+      if (jb + 1 < nblk) gemm(base, cnt, max_nA - (jb + 1) * NB, max_nT, 0, jb);
     }
     for (int jb = nblk - 1; jb >= 0; --jb) {
       (hfr::count_launch(), k_big_trsm_diag<T><<<gd, 128, 0, st>>>(a, list, base, cnt, uni_nA, uni_nT, jb, 1));
-      if (jb > 0) (hfr::count_launch(), k_big_gemm<T><<<gg, BT, 0, st>>>(a, list, base, cnt, uni_nA, uni_nT, 1, jb));
+      if (jb > 0) gemm(base, cnt, jb * NB, max_nT, 1, jb);
     }
-    const dim3 gs((max_nT + TB - 1) / TB, (max_nT + TB - 1) / TB, cnt);
-    (hfr::count_launch(), k_big_gemm<T><<<gs, BT, 0, st>>>(a, list, base, cnt, uni_nA, uni_nT, 2, 0));
+    gemm(base, cnt, max_nT, max_nT, 2, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   (hfr::count_launch(), k_big_xr<T><<<grid1, BT, 0, st>>>(a, list, nlist, uni_nA, uni_nT));

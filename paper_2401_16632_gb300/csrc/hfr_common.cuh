@@ -257,3 +257,28 @@ __device__ __forceinline__ int line_pt(int r, int m, int c) {
 
 // status word bits written by kernels (never trap)
 enum { DEV_ERR_SINGULAR = 1, DEV_ERR_NAN = 2, DEV_ERR_INDEX = 4, DEV_ERR_TIMEOUT = 8 };
+
+// -------------------------------------------------------------------------------------------
+// Bounds-checked build (compile flag FR_CHECKED): every mesh-derived gather / scatter index of
+// the general path (trace point of an element face point, neighbour element and face, element
+// face point of a trace point, element-view entry of a trace value, trace value of an
+// element-view entry) and of the uniform path's residual and blocks (trace face, neighbour) goes
+// through FR_IDX(i, n, site): an index outside [0, n) is recorded in this translation unit's
+// device word (the first one: site and index; and a count) and replaced by 0, so the access
+// stays in bounds and the kernel goes on (never a trap).  fr_checked_status reads and clears the
+// words of every unit.  Without the flag FR_IDX is the index itself.
+#ifdef FR_CHECKED
+namespace fr_chk {
+static __device__ unsigned long long g_first;  // (site << 48) | (index & (2^48 - 1)), 0 = none
+static __device__ unsigned long long g_count;
+__device__ __forceinline__ long long idx(long long i, long long n, int site) {
+  if (i >= 0 && i < n) return i;
+  atomicCAS(&g_first, 0ull, ((unsigned long long)(site & 0xFFFF) << 48) | ((unsigned long long)i & 0xFFFFFFFFFFFFull));
+  atomicAdd(&g_count, 1ull);
+  return 0;
+}
+}  // namespace fr_chk
+#define FR_IDX(i, n, site) ::fr_chk::idx((long long)(i), (long long)(n), (site))
+#else
+#define FR_IDX(i, n, site) (i)
+#endif

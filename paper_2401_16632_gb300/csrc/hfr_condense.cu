@@ -2063,10 +2063,21 @@ bool uneven_fits_smem(int prec_bytes, int nA, int nT) {
   return smem_elem_bytes((size_t)prec_bytes, nA, nT) <= 227 * 1024;
 }
 
+// largest nA of an uneven batch that goes to the shared-memory Gauss-Jordan bundles; larger blocks
+// take the blocked LU with batched GEMMs.  Measured on 10 000 FP32 blocks of nA = 144, nT = 96
+// (p = 5): 40.3 ms in the bundles (one element per CTA, shared-memory bound rank-1 steps), 26.4 ms
+// blocked.  A build flag, for timing the two forms against each other.
+#ifndef HFR_UNEVEN_SMEM_MAX_NA
+#define HFR_UNEVEN_SMEM_MAX_NA 128
+#endif
+static bool uneven_route_smem(int prec_bytes, int nA, int nT) {
+  return uneven_fits_smem(prec_bytes, nA, nT) && nA <= HFR_UNEVEN_SMEM_MAX_NA;
+}
+
 // Host tables of an uneven launch: per element offsets (A, B/C, D, nA-, nT-vectors), shapes, the
 // shared-memory elements' order (most expensive first) and bundles, and the elements too large for
 // shared memory (global-memory kernel).
-int uneven_tables(int prec_bytes, int n, const int* nA, const int* nT, UnevenTables* tb) {
+int uneven_tables(int prec_bytes, int n, const int* nA, const int* nT, UnevenTables* tb, const unsigned char* skip) {
   tb->off.assign(5 * (size_t)n, 0);
   tb->shape.assign(2 * (size_t)n, 0);
   tb->order.clear();
@@ -2089,7 +2100,8 @@ int uneven_tables(int prec_bytes, int n, const int* nA, const int* nT, UnevenTab
     od += (long long)nT[k] * nT[k];
     ova += nA[k];
     ovt += nT[k];
-    if (uneven_fits_smem(prec_bytes, nA[k], nT[k])) {
+    if (skip && skip[k]) continue;  // condensed elsewhere: offsets only
+    if (uneven_route_smem(prec_bytes, nA[k], nT[k])) {
       tb->order.push_back(k);
       const size_t sb = smem_elem_bytes(prec_bytes, nA[k], nT[k]);
       tb->smem = sb > tb->smem ? sb : tb->smem;
@@ -2200,6 +2212,153 @@ cudaError_t launch_condense_uneven_dev(int prec_bytes, const UnevenDev& dv, cons
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// ------------------------------------------- one shape class of a packed uneven batch
+// Elements of one shape (nA, nT) scattered through the packed arrays of an uneven batch, condensed
+// by the fixed-shape kernels of that shape (e.g. the tensor-core inverse and products) through a
+// contiguous scratch batch: gather, launch_condense, scatter, in chunks of at most `cap` elements.
+struct ClassScratch {
+  size_t a, b, d, va, vt;  // values per chunk: nA^2, nA nT, nT^2, nA, nT (times cap)
+  float *A, *B, *C, *D, *LU, *XB, *S;
+  double *r, *s, *xr, *t;
+  int* piv;
+  int* status;  // two words: the chunk's own status (DEV_ERR_*, first failing chunk element)
+};
+size_t class_scratch_bytes(int nA, int nT, int cap) {
+  const size_t c = (size_t)cap, a = c * nA * nA, b = c * nA * nT, d = c * nT * nT;
+  return 4 * (2 * a + 3 * b + 2 * d) + 8 * (2 * c * nA + 2 * c * nT) + 4 * c * nA + 64 + 8 * 16;
+}
+static ClassScratch class_scratch(void* buf, int nA, int nT, int cap) {
+  ClassScratch cs;
+  const size_t c = (size_t)cap;
+  cs.a = c * nA * nA;
+  cs.b = c * nA * nT;
+  cs.d = c * nT * nT;
+  cs.va = c * nA;
+  cs.vt = c * nT;
+  cs.status = reinterpret_cast<int*>(buf);  // first 16 bytes: the same place for every shape
+  double* dp = reinterpret_cast<double*>(reinterpret_cast<char*>(buf) + 16);
+  cs.r = dp;
+  cs.xr = cs.r + cs.va;
+  cs.s = cs.xr + cs.va;
+  cs.t = cs.s + cs.vt;
+  float* fp = reinterpret_cast<float*>(cs.t + cs.vt);
+  cs.A = fp;
+  cs.LU = cs.A + cs.a;
+  cs.B = cs.LU + cs.a;
+  cs.C = cs.B + cs.b;
+  cs.XB = cs.C + cs.b;
+  cs.D = cs.XB + cs.b;
+  cs.S = cs.D + cs.d;
+  cs.piv = reinterpret_cast<int*>(cs.S + cs.d);
+  return cs;
+}
+
+// copies of n values (16-byte vectors where both sides allow them)
+__device__ __forceinline__ void class_copy(const float* __restrict__ src, float* __restrict__ dst, size_t n) {
+  if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0) {
+    const size_t n4 = n / 4;
+    for (size_t i = threadIdx.x; i < n4; i += blockDim.x)
+      reinterpret_cast<float4*>(dst)[i] = reinterpret_cast<const float4*>(src)[i];
+    for (size_t i = 4 * n4 + threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+  } else {
+    for (size_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+  }
+}
+template <typename V>
+__device__ __forceinline__ void class_copy_v(const V* __restrict__ src, V* __restrict__ dst, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+// chunk element i (one CTA each) <- packed element list[i]
+__global__ void __launch_bounds__(256) k_class_gather(const int* __restrict__ list, const long long* __restrict__ off,
+                                                      int nA, int nT, const float* A, const float* B, const float* C,
+                                                      const float* D, const double* r, const double* s,
+                                                      ClassScratch cs) {
+  const int i = blockIdx.x, k = list[i];
+  const long long* o = off + 5 * (size_t)k;
+  const size_t a = (size_t)nA * nA, b = (size_t)nA * nT, d = (size_t)nT * nT;
+  class_copy(A + o[0], cs.A + i * a, a);
+  class_copy(B + o[1], cs.B + i * b, b);
+  class_copy(C + o[1], cs.C + i * b, b);
+  class_copy(D + o[2], cs.D + i * d, d);
+  class_copy_v(r + o[3], cs.r + (size_t)i * nA, nA);
+  class_copy_v(s + o[4], cs.s + (size_t)i * nT, nT);
+}
+
+// packed element list[i] <- chunk element i: factors, pivots, X_B, x_r, S, t
+__global__ void __launch_bounds__(256) k_class_scatter(const int* __restrict__ list, const long long* __restrict__ off,
+                                                       int nA, int nT, ClassScratch cs, float* LU, int* piv, float* XB,
+                                                       double* xr, float* S, double* t) {
+  const int i = blockIdx.x, k = list[i];
+  const long long* o = off + 5 * (size_t)k;
+  const size_t a = (size_t)nA * nA, b = (size_t)nA * nT, d = (size_t)nT * nT;
+  class_copy(cs.LU + i * a, LU + o[0], a);
+  class_copy(cs.XB + i * b, XB + o[1], b);
+  class_copy(cs.S + i * d, S + o[2], d);
+  class_copy_v(cs.piv + (size_t)i * nA, piv + o[3], nA);
+  class_copy_v(cs.xr + (size_t)i * nA, xr + o[3], nA);
+  class_copy_v(cs.t + (size_t)i * nT, t + o[4], nT);
+}
+
+// the chunk's status into the batch's (its first failing element as a packed element id)
+__global__ void k_class_status(int* cstatus, const int* __restrict__ list, int cnt, int* status) {
+  if (cstatus[0] != 0) {
+    atomicOr(status, cstatus[0]);
+    const int i = cstatus[1];
+    atomicMin(status + 1, (i >= 0 && i < cnt) ? list[i] : -1);
+  }
+  cstatus[0] = 0;
+  cstatus[1] = 0x7fffffff;
+}
+
+cudaError_t launch_condense_class(const int* list, int count, int nA, int nT, const long long* off, const void* A,
+                                  const void* B, const void* C, const void* D, const double* r, const double* s,
+                                  void* LU, int* piv, void* XB, double* xr, void* S, double* t, int* status,
+                                  void* scratch, int cap, int tc_mode, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  if (cap <= 0 || !condense_feasible(4, nA, nT)) return cudaErrorInvalidValue;
+  const ClassScratch cs = class_scratch(scratch, nA, nT, cap);
+  cudaError_t e;
+  for (int base = 0; base < count; base += cap) {
+    const int cnt = count - base < cap ? count - base : cap;
+    (hfr::count_launch(), k_class_gather<<<cnt, 256, 0, st>>>(list + base, off, nA, nT, (const float*)A,
+                                                               (const float*)B, (const float*)C, (const float*)D, r, s,
+                                                               cs));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    CondArgs ca;
+    ca.Eim = cnt;
+    ca.nA = nA;
+    ca.nT = nT;
+    ca.A = cs.A;
+    ca.B = cs.B;
+    ca.C = cs.C;
+    ca.D = cs.D;
+    ca.r = cs.r;
+    ca.s = cs.s;
+    ca.LU = cs.LU;
+    ca.piv = cs.piv;
+    ca.XB = cs.XB;
+    ca.xr = cs.xr;
+    ca.S = cs.S;
+    ca.t = cs.t;
+    ca.status = cs.status;
+    ca.tc_mode = tc_mode;
+    if ((e = launch_condense(4, ca, st)) != cudaSuccess) return e;
+    (hfr::count_launch(), k_class_scatter<<<cnt, 256, 0, st>>>(list + base, off, nA, nT, cs, (float*)LU, piv,
+                                                                (float*)XB, xr, (float*)S, t));
+    (hfr::count_launch(), k_class_status<<<1, 1, 0, st>>>(cs.status, list + base, cnt, status));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t class_scratch_init_status(void* scratch, cudaStream_t st) {
+  const int init[2] = {0, 0x7fffffff};
+  cudaError_t e = cudaMemcpyAsync(scratch, init, sizeof(init), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(st);
 }
 
 cudaError_t launch_condense_uneven(int prec_bytes, int n, const int* nA, const int* nT, const void* A, const void* B,

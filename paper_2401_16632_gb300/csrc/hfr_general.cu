@@ -301,11 +301,11 @@ __global__ void __launch_bounds__(32 * GEPB) k_gen_elem(const __grid_constant__ 
     const double uf = w.Ufp[f * GN + q][v];
     double ub;
     if (t >= 0) {
-      ub = a.uhat[(size_t)a.fnode[(4 * e + f) * GN + q] * NV + v];
+      ub = a.uhat[(size_t)FR_IDX(a.fnode[(4 * e + f) * GN + q], a.npts, 1) * NV + v];
     } else if (kf == FK_FAR) {
       ub = 0.5 * (uf + a.uinf[v]);
     } else {
-      const int nb = a.nbr[4 * e + f], fn = a.nbr_face[4 * e + f];
+      const int nb = (int)FR_IDX(a.nbr[4 * e + f], a.E, 2), fn = (int)FR_IDX(a.nbr_face[4 * e + f], 4, 3);
       const double un = a.Uf_all[((size_t)(4 * nb + fn) * GN + q) * NV + v];
       ub = kf == FK_FR ? 0.5 * (uf + un) : (imp ? un : uf);
     }
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(32 * GEPB) k_gen_elem(const __grid_constant__ 
           qn[1][v] = w.qfp[j][1][v];
         }
       } else {
-        const int nb = a.nbr[4 * e + f], fn = a.nbr_face[4 * e + f];
+        const int nb = (int)FR_IDX(a.nbr[4 * e + f], a.E, 2), fn = (int)FR_IDX(a.nbr_face[4 * e + f], 4, 3);
         const size_t nix = (size_t)(4 * nb + fn) * GN + q;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
@@ -440,13 +440,13 @@ __global__ void __launch_bounds__(32 * GEPB) k_gen_elem(const __grid_constant__ 
 // points that carry it (two sides on HFR faces, every face meeting at an EFR node)
 __global__ void k_gen_trace_sum(size_t npts, int nv, const long long* __restrict__ gptr,
                                 const long long* __restrict__ gidx, const double* __restrict__ gview,
-                                double* __restrict__ g) {
+                                double* __restrict__ g, long long nview) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= npts * nv) return;
   const size_t pt = i / nv;
   const int v = (int)(i % nv);
   double s = 0.0;
-  for (long long c = gptr[pt]; c < gptr[pt + 1]; ++c) s += gview[(size_t)gidx[c] * nv + v];
+  for (long long c = gptr[pt]; c < gptr[pt + 1]; ++c) s += gview[(size_t)FR_IDX(gidx[c], nview, 5) * nv + v];
   g[i] = s;
 }
 
@@ -461,15 +461,17 @@ __global__ void k_gen_initial_trace(size_t npts, int nv, const long long* __rest
   const size_t pt = i / nv;
   const int v = (int)(i % nv);
   const long long c0 = gptr[pt], c1 = gptr[pt + 1];
-  const int kf = kind[gidx[c0] / a.fs];
+  const long long nview = (long long)a.nface * a.E * a.fs;
+  const long long i0 = FR_IDX(gidx[c0], nview, 6);
+  const int kf = kind[i0 / a.fs];
   double x;
   if (kf == FK_FAR) {
-    x = 0.5 * (Uf[(size_t)gidx[c0] * nv + v] + a.uinf[v]);
+    x = 0.5 * (Uf[(size_t)i0 * nv + v] + a.uinf[v]);
   } else if (kf == FK_WALL) {
-    x = (v == 0 || v == nv - 1) ? Uf[(size_t)gidx[c0] * nv + v] : 0.0;  // zero momentum
+    x = (v == 0 || v == nv - 1) ? Uf[(size_t)i0 * nv + v] : 0.0;  // zero momentum
   } else {
     double s = 0.0;
-    for (long long c = c0; c < c1; ++c) s += Uf[(size_t)gidx[c] * nv + v];
+    for (long long c = c0; c < c1; ++c) s += Uf[(size_t)FR_IDX(gidx[c], nview, 6) * nv + v];
     x = s / (double)(c1 - c0);
   }
   uhat[i] = x;
@@ -586,10 +588,10 @@ __global__ void __launch_bounds__(JT) k_gen_jacobian(const __grid_constant__ Phy
       for (int b = 0; b < n; ++b) s += w.Tf[f][q][b] * w.Ufn[f * GN + b][v];
       const int t = w.tr[f];
       if (t >= 0) {
-        ub = T(a.uhat[(size_t)a.fnode[(4 * e + f) * GN + q] * NV + v]);
+        ub = T(a.uhat[(size_t)FR_IDX(a.fnode[(4 * e + f) * GN + q], a.npts, 4) * NV + v]);
         un = s;
       } else {  // interface face of an implicit element: the explicit neighbour's state
-        const int nb = a.nbr[4 * e + f], fn = a.nbr_face[4 * e + f];
+        const int nb = (int)FR_IDX(a.nbr[4 * e + f], a.E, 2), fn = (int)FR_IDX(a.nbr_face[4 * e + f], 4, 3);
         un = T(a.Uf_all[((size_t)(4 * nb + fn) * GN + q) * NV + v]);
         ub = un;
       }
@@ -941,47 +943,65 @@ __global__ void k_gen_form_rhs(int Eim, int nv, int nface, int fs, int dim, cons
   }
 }
 
-// element view of the trace operator: yv_k = S_k x[gmap_k] (one warp per implicit element; rows
-// one at a time, lanes along the row)
+// element view of the trace operator: yv_k = S_k x[gmap_k]
 template <typename T>
-__global__ void k_gen_matvec_elem(int Eim, const int* __restrict__ nTk, const long long* __restrict__ offD,
-                                  const long long* __restrict__ offs, const int* __restrict__ gmap,
-                                  const T* __restrict__ S, const double* __restrict__ x, double* __restrict__ yv,
-                                  const int* gate, int gj) {
+__global__ void __launch_bounds__(256) k_gen_matvec_elem(int Eim, const int* __restrict__ nTk,
+                                                         const long long* __restrict__ offD,
+                                                         const long long* __restrict__ offs,
+                                                         const int* __restrict__ gmap, const T* __restrict__ S,
+                                                         const double* __restrict__ x, double* __restrict__ yv,
+                                                         const int* gate, int gj, long long nh) {
+  // y_k = S_k x_k, one warp per implicit element: the element's gathered trace values staged in the
+  // warp's shared memory, then 8 rows at a time with 4 lanes per row, each lane taking every 4th
+  // 16-byte run of the row (FP32 rows of a multiple of 4 values on 16-byte boundaries; scalar
+  // otherwise), a 4-lane sum per row
+  __shared__ __align__(16) T xs[8][512];
   if (gate && *gate >= 0 && gj >= *gate) return;
-  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * (blockDim.x >> 5) + wp;
   if (k >= Eim) return;
   const int nT = nTk[k];
   const T* Sk = S + offD[k];
   const int* gm = gmap + offs[k];
-  T xl[16];  // nT <= 512
-#pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    const int l = lane + 32 * c;
-    const int g = l < nT ? gm[l] : -1;
-    xl[c] = g >= 0 ? T(x[g]) : T(0);
+  T* xk = xs[wp];
+  for (int l = lane; l < nT; l += 32) {
+    const int g = gm[l];
+    xk[l] = g >= 0 ? T(x[FR_IDX(g, nh, 8)]) : T(0);
   }
-  for (int row = 0; row < nT; ++row) {
+  __syncwarp();
+  const int r8 = lane >> 2, c4 = lane & 3;
+  const bool vec = sizeof(T) == 4 && (nT & 3) == 0 && (offD[k] & 3) == 0;
+  for (int r0 = 0; r0 < nT; r0 += 8) {
+    const int row = r0 + r8;
     T acc = T(0);
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      const int l = lane + 32 * c;
-      if (l < nT) acc += Sk[(size_t)row * nT + l] * xl[c];
+    if (row < nT) {
+      const T* Sr = Sk + (size_t)row * nT;
+      if (vec) {
+        const float4* S4 = reinterpret_cast<const float4*>(Sr);
+        const float4* x4 = reinterpret_cast<const float4*>(xk);
+        for (int c = c4; c < (nT >> 2); c += 4) {
+          const float4 sv = __ldg(S4 + c), xv = x4[c];
+          acc += sv.x * xv.x + sv.y * xv.y + sv.z * xv.z + sv.w * xv.w;
+        }
+      } else {
+        for (int l = c4; l < nT; l += 4) acc += Sr[l] * xk[l];
+      }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) yv[offs[k] + row] = double(acc);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (c4 == 0 && row < nT) yv[offs[k] + row] = double(acc);
   }
 }
 
 // y[d] = the sum of the element-view values of trace value d (CSR over its entries)
 __global__ void k_gen_gather_sum(size_t nh, const long long* __restrict__ vptr, const long long* __restrict__ vidx,
-                                 const double* __restrict__ yv, double* __restrict__ y, const int* gate, int gj) {
+                                 const double* __restrict__ yv, double* __restrict__ y, const int* gate, int gj,
+                                 long long nview) {
   if (gate && *gate >= 0 && gj >= *gate) return;
   const size_t d = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (d >= nh) return;
   double s = 0.0;
-  for (long long c = vptr[d]; c < vptr[d + 1]; ++c) s += yv[vidx[c]];
+  for (long long c = vptr[d]; c < vptr[d + 1]; ++c) s += yv[FR_IDX(vidx[c], nview, 7)];
   y[d] = s;
 }
 
@@ -1190,7 +1210,7 @@ __global__ void k_gen_backsolve(int Eim, const int* __restrict__ nAk, const int*
                                 const long long* __restrict__ offB, const long long* __restrict__ offr,
                                 const long long* __restrict__ offs, const int* __restrict__ gmap,
                                 const T* __restrict__ XB, const double* __restrict__ xr,
-                                const double* __restrict__ duhat, double* __restrict__ du) {
+                                const double* __restrict__ duhat, double* __restrict__ du, long long nh) {
   const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (k >= Eim) return;
   const int nA = nAk[k], nT = nTk[k];
@@ -1202,7 +1222,7 @@ __global__ void k_gen_backsolve(int Eim, const int* __restrict__ nAk, const int*
   for (int c = 0; c < 16; ++c) {
     const int l = lane + 32 * c;
     const int g = l < nT ? gm[l] : -1;
-    dl[c] = g >= 0 ? T(duhat[g]) : T(0);
+    dl[c] = g >= 0 ? T(duhat[FR_IDX(g, nh, 9)]) : T(0);
   }
   for (int i = 0; i < nA; ++i) {
     T acc = T(0);
@@ -1300,7 +1320,9 @@ static int err(GenCtx* g, int code, const char* msg, int elem = -1, int it = -1,
     cudaError_t e_ = (call);                                                       \
     if (e_ != cudaSuccess) return err(g, FR_ERR_CUDA, cudaGetErrorString(e_));     \
   } while (0)
-static int pbeg(GenCtx* g, int ph) { return g->hk.prof_begin ? g->hk.prof_begin(g->hk.owner, ph) : -1; }
+static int pbeg(GenCtx* g, int ph) {
+  return (g->hk.prof_begin && !g->capturing) ? g->hk.prof_begin(g->hk.owner, ph) : -1;
+}
 static void pend(GenCtx* g, int h) {
   if (g->hk.prof_end) g->hk.prof_end(g->hk.owner, h);
 }
@@ -1358,6 +1380,10 @@ static void bilinear_g(const double* V, double xi, double eta, double* J, double
 
 void destroy(GenCtx* g) {
   if (!g) return;
+  if (g->gexec) cudaGraphExecDestroy(g->gexec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  for (auto& c : g->cap)
+    if (c) cudaStreamDestroy(c);
   for (void* p : g->allocs) cudaFree(p);
   delete g;
 }
@@ -1684,9 +1710,21 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
       for (long long i = uoff[e]; i < uoff[e + 1]; ++i) dof_imp[i] = 1;
   GenRef href;
   build_genref(href);
-  // condensation tables
+  // condensation tables: FP32 quadrilateral shapes with a tensor-core form go by class (skipped
+  // by the uneven launch)
+  std::vector<unsigned char> tc_skip(std::max(Eim, 1), 0);
+  std::vector<std::pair<std::pair<int, int>, std::vector<int>>> tc_cls;
+  if (g->pb == 4 && !hex)
+    for (int k = 0; k < Eim; ++k) {
+      if (condense_tc_available(4, nAk[k], nTk[k]) < 2) continue;
+      size_t c = 0;
+      while (c < tc_cls.size() && tc_cls[c].first != std::make_pair(nAk[k], nTk[k])) ++c;
+      if (c == tc_cls.size()) tc_cls.push_back({{nAk[k], nTk[k]}, {}});
+      tc_cls[c].second.push_back(k);
+      tc_skip[k] = 1;
+    }
   UnevenTables tb;
-  if (Eim > 0 && uneven_tables(g->pb, Eim, nAk.data(), nTk.data(), &tb) != 0) {
+  if (Eim > 0 && uneven_tables(g->pb, Eim, nAk.data(), nTk.data(), &tb, tc_skip.data()) != 0) {
     destroy(g);
     return FR_ERR_INVALID_ARG;
   }
@@ -1821,6 +1859,33 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
     return FR_ERR_CUDA;
   }
   g->udev.colmajor = hex ? 1 : 0;
+  // class lists and one scratch batch for the largest class chunk
+  {
+    constexpr int CLASS_CAP = 16384;
+    size_t sbytes = 0;
+    for (auto& c : tc_cls) {
+      GenCtx::TcClass tc;
+      tc.nA = c.first.first;
+      tc.nT = c.first.second;
+      tc.count = (int)c.second.size();
+      tc.list = galloc<int>(g, c.second.size(), &rc);
+      if (rc != FR_OK || cudaMemcpyAsync(tc.list, c.second.data(), c.second.size() * sizeof(int),
+                                         cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        destroy(g);
+        return rc != FR_OK ? rc : FR_ERR_CUDA;
+      }
+      g->tc_classes.push_back(tc);
+      g->ccap = std::max(g->ccap, std::min(tc.count, CLASS_CAP));
+    }
+    for (auto& tc : g->tc_classes) sbytes = std::max(sbytes, class_scratch_bytes(tc.nA, tc.nT, g->ccap));
+    if (sbytes) {
+      g->cscratch = galloc<unsigned char>(g, sbytes, &rc);
+      if (rc != FR_OK || class_scratch_init_status(g->cscratch, st) != cudaSuccess) {
+        destroy(g);
+        return rc != FR_OK ? rc : FR_ERR_CUDA;
+      }
+    }
+  }
   if (cudaMemsetAsync(g->status, 0, 2 * sizeof(int), st) != cudaSuccess ||
       cudaMemsetAsync(g->gm.ticket, 0, sizeof(unsigned), st) != cudaSuccess ||
       cudaMemsetAsync(g->gview, 0, NF * (size_t)E * FS * nv * sizeof(double), st) != cudaSuccess ||
@@ -1850,6 +1915,7 @@ void query(const GenCtx* g, fr_ctx_info* info) {
   info->general = 1;
   info->state_values = g->nstate;
   info->trace_values = g->nh;
+  info->face_points = g->nface * g->E * g->fs;
 }
 
 int nstages(const GenCtx* g) { return g->tableau == FR_TAB_SDIRK2 ? 2 : 1; }
@@ -1897,6 +1963,7 @@ static GArgs gargs(GenCtx* g, const double* u, const double* uhat) {
   a.fs = g->fs;
   a.fnode = g->fnode;
   a.fset = g->fset;
+  a.npts = (long long)g->npts;
   return a;
 }
 
@@ -1932,7 +1999,7 @@ static int residual_into(GenCtx* g, const double* u, const double* uhat, double*
   GCK(gen_elem<GM_RES>(g, a));
   if (g_out && g->ntrace) {
     (count_launch(), k_gen_trace_sum<<<nb256(g->nh), 256, 0, g->st>>>(g->npts, g->nv, g->gptr, g->gidx, g->gview,
-                                                                       g_out));
+                                                                       g_out, (long long)g->nface * g->E * g->fs));
     GCK(cudaGetLastError());
   }
   pend(g, ph);
@@ -2027,12 +2094,16 @@ static int condense_impl(GenCtx* g) {
   GCK(cudaGetLastError());
   if (g->Eim == 0) return FR_OK;
   int ph = pbeg(g, 2);
+  for (const auto& tc : g->tc_classes)
+    GCK(launch_condense_class(tc.list, tc.count, tc.nA, tc.nT, g->udev.off, g->A, g->B, g->C, g->D, g->r, g->s, g->LU,
+                              g->piv, g->XB, g->xr, g->S, g->te, g->status, g->cscratch, g->ccap, 2, g->st));
   GCK(launch_condense_uneven_dev(g->pb, g->udev, g->A, g->B, g->C, g->D, g->r, g->s, g->LU, g->piv, g->XB, g->xr,
                                  g->S, g->te, g->status, g->st));
   pend(g, ph);
   ph = pbeg(g, 3);
   if (g->ntrace) {
-    (count_launch(), k_gen_gather_sum<<<nb256(g->nh), 256, 0, g->st>>>(g->nh, g->vptr, g->vidx, g->te, g->tg, nullptr, 0));
+    (count_launch(), k_gen_gather_sum<<<nb256(g->nh), 256, 0, g->st>>>(g->nh, g->vptr, g->vidx, g->te, g->tg, nullptr, 0,
+                                                                        (long long)g->sumT));
     GCK(cudaGetLastError());
     if (g->efr && g->pb == 8)
       (count_launch(), k_gen_precond_build_node<double><<<nb256(g->npts), 256, 0, g->st>>>(
@@ -2083,22 +2154,28 @@ static void cb_matvec_g(void* c, const double* x, double* y, cudaStream_t s) {
   const int ph = pbeg(g, 8);
   if (g->pb == 8)
     (count_launch(), k_gen_matvec_elem<double><<<nbw(g->Eim), 256, 0, s>>>(g->Eim, g->nTk, g->offD, g->offs, g->gmap,
-                                                                           (const double*)g->S, x, g->yv, nullptr, 0));
+                                                                           (const double*)g->S, x, g->yv, nullptr, 0,
+                                                                           (long long)g->nh));
   else
     (count_launch(), k_gen_matvec_elem<float><<<nbw(g->Eim), 256, 0, s>>>(g->Eim, g->nTk, g->offD, g->offs, g->gmap,
-                                                                          (const float*)g->S, x, g->yv, nullptr, 0));
-  (count_launch(), k_gen_gather_sum<<<nb256(g->nh), 256, 0, s>>>(g->nh, g->vptr, g->vidx, g->yv, y, nullptr, 0));
+                                                                          (const float*)g->S, x, g->yv, nullptr, 0,
+                                                                          (long long)g->nh));
+  (count_launch(), k_gen_gather_sum<<<nb256(g->nh), 256, 0, s>>>(g->nh, g->vptr, g->vidx, g->yv, y, nullptr, 0,
+                                                                    (long long)g->sumT));
   pend(g, ph);
 }
 static void cb_gmatvec_g(void* c, const GmresState* st, int j, const double* x, const float*, double* y, cudaStream_t s) {
   GenCtx* g = (GenCtx*)c;
   if (g->pb == 8)
     (count_launch(), k_gen_matvec_elem<double><<<nbw(g->Eim), 256, 0, s>>>(g->Eim, g->nTk, g->offD, g->offs, g->gmap,
-                                                                           (const double*)g->S, x, g->yv, &st->kdone, j));
+                                                                           (const double*)g->S, x, g->yv, &st->kdone, j,
+                                                                           (long long)g->nh));
   else
     (count_launch(), k_gen_matvec_elem<float><<<nbw(g->Eim), 256, 0, s>>>(g->Eim, g->nTk, g->offD, g->offs, g->gmap,
-                                                                          (const float*)g->S, x, g->yv, &st->kdone, j));
-  (count_launch(), k_gen_gather_sum<<<nb256(g->nh), 256, 0, s>>>(g->nh, g->vptr, g->vidx, g->yv, y, &st->kdone, j));
+                                                                          (const float*)g->S, x, g->yv, &st->kdone, j,
+                                                                          (long long)g->nh));
+  (count_launch(), k_gen_gather_sum<<<nb256(g->nh), 256, 0, s>>>(g->nh, g->vptr, g->vidx, g->yv, y, &st->kdone, j,
+                                                                    (long long)g->sumT));
 }
 static void cb_precond_g(void* c, const GmresState* st, int j, double* x, double* y, float* y32, cudaStream_t s) {
   GenCtx* g = (GenCtx*)c;
@@ -2147,10 +2224,12 @@ static int backsolve_impl(GenCtx* g, const double* duhat, double* du) {
   const int ph = pbeg(g, 5);
   if (g->pb == 8)
     (count_launch(), k_gen_backsolve<double><<<nbw(g->Eim), 256, 0, g->st>>>(
-         g->Eim, g->nAk, g->nTk, g->offB, g->offr, g->offs, g->gmap, (const double*)g->XB, g->xr, duhat, du));
+         g->Eim, g->nAk, g->nTk, g->offB, g->offr, g->offs, g->gmap, (const double*)g->XB, g->xr, duhat, du,
+         (long long)g->nh));
   else
     (count_launch(), k_gen_backsolve<float><<<nbw(g->Eim), 256, 0, g->st>>>(
-         g->Eim, g->nAk, g->nTk, g->offB, g->offr, g->offs, g->gmap, (const float*)g->XB, g->xr, duhat, du));
+         g->Eim, g->nAk, g->nTk, g->offB, g->offr, g->offs, g->gmap, (const float*)g->XB, g->xr, duhat, du,
+         (long long)g->nh));
   GCK(cudaGetLastError());
   pend(g, ph);
   return FR_OK;
@@ -2181,6 +2260,13 @@ int export_array(GenCtx* g, int which, void* buf, size_t bytes, bool import) {
     case 9: arr = g->s; need = g->sumT * 8; break;
     case 10: if (!import) { arr = g->tg; need = g->nh * 8; } break;
     case 11: if (!import) { arr = g->Pinv; need = g->sumP * pb; } break;
+    case 64:  // the trace point of every element face point (int32); written only by checked builds
+#ifndef FR_CHECKED
+      if (import) break;
+#endif
+      arr = g->fnode;
+      need = (size_t)g->nface * g->E * g->fs * sizeof(int);
+      break;
   }
   if (!arr) return err(g, FR_ERR_INVALID_ARG, "hfr_export / hfr_import: unknown array");
   if (import ? bytes != need : bytes < need)
@@ -2234,6 +2320,245 @@ static TabG tableau_g(int which) {
   return t;
 }
 
+// ------------------------------------------------------------------ whole-stage CUDA graph
+// The implicit stage as one executable graph, as on the uniform path: the Newton loop a WHILE
+// node, its linear solve an IF node, the GMRES restart cycles a nested WHILE node
+// (capture_gmres); small kernels take on the device the decisions the stream path takes on the
+// host (same tests, same order), and the host reads the counters once after the launch.
+struct GStageDev {
+  double norm0, norm;
+  int it, gtot, conv, err, sing, cycles;
+};
+__global__ void k_gs_init(GStageDev* sd) {
+  sd->norm0 = -1.0;
+  sd->norm = 0.0;
+  sd->it = 0;
+  sd->gtot = 0;
+  sd->conv = 0;
+  sd->err = 0;
+  sd->sing = -1;
+  sd->cycles = 0;
+}
+__global__ void k_gs_newton_check(GStageDev* sd, const double* ss, double tol, int maxit,
+                                  cudaGraphConditionalHandle hn, cudaGraphConditionalHandle hs) {
+  const double nrm = sqrt(*ss);
+  if (sd->norm0 < 0.0) sd->norm0 = nrm;
+  sd->norm = nrm;
+  if (!(nrm == nrm)) sd->err |= 1;
+  const int conv = (nrm <= tol * sd->norm0 || nrm == 0.0) ? 1 : 0;
+  sd->conv = conv;
+  const int cont = (!conv && sd->err == 0 && sd->it < maxit) ? 1 : 0;
+  if (cont) sd->it += 1;
+  cudaGraphSetConditional(hn, (unsigned)cont);
+  cudaGraphSetConditional(hs, (unsigned)cont);
+}
+// a zero pivot in the condensation ends the Newton loop at its next test
+__global__ void k_gs_cond_check(GStageDev* sd, const int* status) {
+  if (status[0] & DEV_ERR_SINGULAR) {
+    sd->err |= 8;
+    if (sd->sing < 0) sd->sing = status[1];
+  }
+}
+__global__ void k_gs_gmres_done(GStageDev* sd, const GmresGraphDev* gd) {
+  sd->gtot += gd->total;
+  sd->cycles += gd->cycles;
+  if (gd->nan) sd->err |= 2;
+}
+
+int set_graph(GenCtx* g, int on) {
+  if (on && g->Eim == 0) return err(g, FR_ERR_UNSUPPORTED, "imex_stage_set_graph: needs implicit elements");
+  g->use_graph = on;
+  g->gvalid = false;
+  return FR_OK;
+}
+
+static int stage_graph_capture(GenCtx* g, const GenCtx::GKey& key) {
+  const TabG tb = tableau_g(g->tableau);
+  const int i = key.stage;
+  const size_t tot = g->nstate;
+  for (auto& c : g->cap)
+    if (!c && cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking) != cudaSuccess)
+      return err(g, FR_ERR_CUDA, "imex_stage: stream creation failed");
+  if (!g->gdev) {
+    int rc = FR_OK;
+    g->gdev = galloc<unsigned char>(g, 256, &rc);
+    if (rc) return err(g, rc, "imex_stage: out of device memory");
+  }
+  GStageDev* sd = reinterpret_cast<GStageDev*>(g->gdev);
+  GmresGraphDev* gd = reinterpret_cast<GmresGraphDev*>(reinterpret_cast<char*>(g->gdev) + 128);
+  cudaStream_t user = g->st;
+  cudaGraph_t gr = nullptr, bn = nullptr, bs = nullptr;
+  int depth = 0;
+  auto fail = [&](cudaError_t e) {
+    for (int d = depth - 1; d >= 0; --d) {
+      cudaGraph_t tmp = nullptr;
+      cudaStreamEndCapture(g->cap[d], &tmp);
+    }
+    g->st = user;
+    g->capturing = false;
+    if (gr) cudaGraphDestroy(gr);
+    cudaGetLastError();
+    return err(g, FR_ERR_CUDA, cudaGetErrorString(e));
+  };
+#define SK(x)                              \
+  do {                                     \
+    const cudaError_t e_ = (x);            \
+    if (e_ != cudaSuccess) return fail(e_); \
+  } while (0)
+#define SR(x)                                    \
+  do {                                           \
+    const int r_ = (x);                          \
+    if (r_ != FR_OK) return fail(cudaErrorUnknown); \
+  } while (0)
+  g->capturing = true;
+  const unsigned long long l0 = launch_count();
+  SK(cudaGraphCreate(&gr, 0));
+  SK(cudaStreamBeginCaptureToGraph(g->cap[0], gr, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  depth = 1;
+  g->st = g->cap[0];
+  double* u_stage = const_cast<double*>(key.u_stage);
+  double* uhat = const_cast<double*>(key.uhat);
+  {
+    StageCoefG sc;
+    memset(&sc, 0, sizeof(sc));
+    sc.nterm = i;
+    for (int jj = 0; jj < i; ++jj) {
+      sc.hi[jj] = jj;
+      sc.ce[jj] = key.dt * tb.ah[i][jj];
+      sc.ci[jj] = jj >= 1 ? key.dt * tb.a[i - 1][jj - 1] : 0.0;
+    }
+    (count_launch(), k_gen_stage_combine<<<nb256(tot), 256, 0, g->st>>>(tot, g->dof_imp, key.u_n, key.R_hist, sc,
+                                                                        u_stage));
+    SK(cudaGetLastError());
+  }
+  SK(cudaMemcpyAsync(g->Ustar, u_stage, tot * sizeof(double), cudaMemcpyDeviceToDevice, g->st));
+  (count_launch(), k_gs_init<<<1, 1, 0, g->st>>>(sd));
+  SK(cudaGetLastError());
+  const double adt = key.dt * tb.a[i - 1][i - 1];
+  cudaGraphConditionalHandle hn, hs;
+  SK(graph_conditional_handle(g->cap[0], 1u, cudaGraphCondAssignDefault, &hn));
+  SK(graph_add_conditional(g->cap[0], hn, cudaGraphCondTypeWhile, &bn));
+  const unsigned long long l1 = launch_count();
+  // ---- Newton body: residual, right-hand sides, norm test
+  SK(cudaStreamBeginCaptureToGraph(g->cap[1], bn, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  depth = 2;
+  g->st = g->cap[1];
+  SK(graph_conditional_handle(g->cap[1], 0u, 0u, &hs));
+  SR(residual_into(g, u_stage, uhat, g->Rw, g->gw));
+  SR(form_rhs(g, u_stage, g->Ustar, adt));
+  {
+    const int nbk = 256;
+    (count_launch(), k_gen_sumsq_part<<<nbk, 256, 0, g->st>>>(g->r, g->sumA, g->gw, g->nh, g->red));
+    (count_launch(), k_gen_sumsq_final<<<1, 32, 0, g->st>>>(g->red, nbk, g->red + 1024));
+    (count_launch(), k_gs_newton_check<<<1, 1, 0, g->st>>>(sd, g->red + 1024, key.ntol, key.nmax, hn, hs));
+    SK(cudaGetLastError());
+  }
+  SK(graph_add_conditional(g->cap[1], hs, cudaGraphCondTypeIf, &bs));
+  const unsigned long long l2 = launch_count();
+  // ---- solve body: blocks, condensation, GMRES cycles, back-substitution, update
+  SK(cudaStreamBeginCaptureToGraph(g->cap[2], bs, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  depth = 3;
+  g->st = g->cap[2];
+  SR(jacobian_blocks(g, u_stage, uhat, adt));
+  SR(condense_impl(g));
+  (count_launch(), k_gs_cond_check<<<1, 1, 0, g->st>>>(sd, g->status));
+  SK(cudaGetLastError());
+  unsigned long long lg0 = launch_count(), lg1 = lg0;
+  if (g->ntrace > 0) {
+    GmresOps ops;
+    ops.ctx = g;
+    ops.matvec = cb_matvec_g;
+    ops.gated_matvec = cb_gmatvec_g;
+    ops.precond = cb_precond_g;
+    const cudaStream_t sc[2] = {g->cap[3], g->cap[4]};
+    lg0 = launch_count();
+    SK(capture_gmres(ops, g->gm, g->tg, g->duhat, key.grtol, g->restart, key.gmax, gd, g->st, sc, &g->gl_gm));
+    lg1 = launch_count();
+    (count_launch(), k_gs_gmres_done<<<1, 1, 0, g->st>>>(sd, gd));
+    SK(cudaGetLastError());
+  } else {
+    SK(cudaMemsetAsync(g->duhat, 0, std::max(g->nh, (size_t)1) * sizeof(double), g->st));
+  }
+  SR(backsolve_impl(g, g->duhat, g->du));
+  if (g->Eim) {
+    (count_launch(), k_gen_apply_du<<<nbw(g->Eim), 256, 0, g->st>>>(g->Eim, g->nv, g->imp_idx, g->deg, g->uoff, g->offr,
+                                                                     g->du, u_stage));
+    SK(cudaGetLastError());
+  }
+  if (g->nh) {
+    (count_launch(), k_gen_axpy<<<nb256(g->nh), 256, 0, g->st>>>(g->nh, 1.0, g->duhat, uhat));
+    SK(cudaGetLastError());
+  }
+  SK(cudaStreamEndCapture(g->cap[2], &bs));
+  depth = 2;
+  const unsigned long long l3 = launch_count();
+  SK(cudaStreamEndCapture(g->cap[1], &bn));
+  depth = 1;
+  g->st = g->cap[0];
+  SK(cudaMemcpyAsync(const_cast<double*>(key.R_hist) + (size_t)i * tot, g->Rw, tot * sizeof(double),
+                     cudaMemcpyDeviceToDevice, g->st));
+  SK(cudaStreamEndCapture(g->cap[0], &gr));
+  depth = 0;
+  const unsigned long long l4 = launch_count();
+  g->st = user;
+  g->capturing = false;
+  cudaGraphExec_t ex = nullptr;
+  {
+    const cudaError_t e = cudaGraphInstantiate(&ex, gr, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(gr);
+      cudaGetLastError();
+      return err(g, FR_ERR_CUDA, cudaGetErrorString(e));
+    }
+  }
+  if (g->gexec) cudaGraphExecDestroy(g->gexec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  g->graph = gr;
+  g->gexec = ex;
+  g->gkey = key;
+  g->gvalid = true;
+  // the capture counted each kernel once: a replay's count follows from its loop counts
+  launch_count_add(-(long long)(l4 - l0));
+  g->gl_top = (int)((l1 - l0) + (l4 - l3));
+  g->gl_newton = (int)(l2 - l1);
+  g->gl_solve = (int)((l3 - l2) - (lg1 - lg0));
+#undef SK
+#undef SR
+  return FR_OK;
+}
+
+static int stage_graph(GenCtx* g, const GenCtx::GKey& key, fr_stage_stats* stats) {
+  if (!g->gvalid || !(g->gkey == key)) {
+    const int rc = stage_graph_capture(g, key);
+    if (rc) return rc;
+  }
+  cudaStream_t st = g->st;
+  GCK(cudaGraphLaunch(g->gexec, st));
+  GStageDev h;
+  GCK(cudaMemcpyAsync(&h, g->gdev, sizeof(h), cudaMemcpyDeviceToHost, st));
+  GCK(cudaStreamSynchronize(st));
+  const int solves = g->ntrace > 0 ? h.it : 0;
+  launch_count_add((long long)g->gl_top + (long long)(h.it + 1) * g->gl_newton + (long long)h.it * g->gl_solve +
+                   (long long)solves * g->gl_gm.fixed + (long long)h.cycles * g->gl_gm.cycle +
+                   (long long)(h.cycles - solves) * g->gl_gm.residual);
+  if (stats) {
+    stats->newton_iterations = h.it;
+    stats->gmres_iterations = h.gtot;
+    stats->residual0 = h.norm0;
+    stats->residual = h.norm;
+    stats->converged = h.conv;
+  }
+  if (h.err & 8) {
+    GCK(cudaMemsetAsync(g->status, 0, sizeof(int), st));
+    GCK(cudaStreamSynchronize(st));
+    return err(g, FR_ERR_SINGULAR, "imex_stage: zero pivot in condensation", h.sing >= 0 ? h.sing : -1, h.it);
+  }
+  if (h.err & 1) return err(g, FR_ERR_DIVERGED, "imex_stage: non-finite Newton residual", -1, h.it);
+  if (h.err & 2) return err(g, FR_ERR_DIVERGED, "imex_stage: non-finite GMRES residual", -1, h.it);
+  if (!h.conv) return err(g, FR_ERR_NOT_CONVERGED, "imex_stage: Newton iteration limit", -1, h.it, h.norm);
+  return FR_OK;
+}
+
 int stage(GenCtx* g, int stage, double dt, const double* u_n, double* u_stage, double* uhat, double* R_hist,
           double newton_tol, int newton_maxit, double gmres_rtol, int gmres_maxit, int refine, fr_stage_stats* stats) {
   if (refine != 0) return err(g, FR_ERR_UNSUPPORTED, "imex_stage: refinement sweeps are not built for general meshes");
@@ -2263,6 +2588,20 @@ int stage(GenCtx* g, int stage, double dt, const double* u_n, double* u_stage, d
     return FR_OK;
   }
   const int i = stage;
+  if (g->use_graph) {
+    GenCtx::GKey key;
+    key.stage = i;
+    key.dt = dt;
+    key.u_n = u_n;
+    key.u_stage = u_stage;
+    key.uhat = uhat;
+    key.R_hist = R_hist;
+    key.ntol = newton_tol;
+    key.nmax = newton_maxit;
+    key.grtol = gmres_rtol;
+    key.gmax = gmres_maxit;
+    return stage_graph(g, key, stats);
+  }
   StageCoefG sc;
   memset(&sc, 0, sizeof(sc));
   sc.nterm = i;
@@ -2332,3 +2671,5 @@ int stage(GenCtx* g, int stage, double dt, const double* u_n, double* u_stage, d
 
 }  // namespace gen
 }  // namespace hfr
+
+#include "hfr_checked_unit.inc"

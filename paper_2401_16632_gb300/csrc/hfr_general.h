@@ -36,6 +36,8 @@ int backsolve(GenCtx* g, const double* duhat, double* du, int refine);
 int export_array(GenCtx* g, int which, void* dst, size_t bytes, bool import);
 int stage(GenCtx* g, int stage, double dt, const double* u_n, double* u_stage, double* uhat, double* R_hist,
           double newton_tol, int newton_maxit, double gmres_rtol, int gmres_maxit, int refine, fr_stage_stats* st);
+// the implicit stages as one CUDA graph each (captured on the first call with a new key)
+int set_graph(GenCtx* g, int on);
 int nstages(const GenCtx* g);
 size_t state_values(const GenCtx* g);
 

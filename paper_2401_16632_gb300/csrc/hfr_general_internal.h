@@ -56,6 +56,7 @@ struct GArgs {
   double* gview;          // element trace rows w_q J_f (row)_q at face points, zero off traces
   double uinf[5];
   int nface, fs;          // faces per element, face-point stride per face
+  long long npts;         // trace points (bound of fnode in the checked build)
 };
 
 
@@ -112,10 +113,40 @@ struct GenCtx {
   int* piv = nullptr;
   int* status = nullptr;
   UnevenDev udev;
+  // FP32 quadrilaterals: shape classes with the fixed-shape tensor-core condensation, condensed
+  // through a contiguous scratch batch (the other elements by the uneven launch)
+  struct TcClass {
+    int nA, nT, count;
+    int* list;  // device: compact implicit ids of the class
+  };
+  std::vector<TcClass> tc_classes;
+  void* cscratch = nullptr;
+  int ccap = 0;
   GmresBuffers gm;
   bool lin_valid = false;
   void* jscratch = nullptr;  // hexahedra: pointwise Jacobians, one slab per CTA of the block kernel
   int jgrid = 0;
+  // the implicit stage as one CUDA graph (imex_stage_set_graph), captured per key
+  struct GKey {
+    int stage = -1;
+    double dt = 0.0;
+    const double *u_n = nullptr, *u_stage = nullptr, *uhat = nullptr, *R_hist = nullptr;
+    double ntol = 0.0, grtol = 0.0;
+    int nmax = 0, gmax = 0;
+    bool operator==(const GKey& o) const {
+      return stage == o.stage && dt == o.dt && u_n == o.u_n && u_stage == o.u_stage && uhat == o.uhat &&
+             R_hist == o.R_hist && ntol == o.ntol && grtol == o.grtol && nmax == o.nmax && gmax == o.gmax;
+    }
+  };
+  int use_graph = 0;
+  bool gvalid = false, capturing = false;
+  GKey gkey;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t cap[5] = {};
+  void* gdev = nullptr;  // the stage's and the GMRES solve's device counters
+  int gl_top = 0, gl_newton = 0, gl_solve = 0;
+  GmresGraphLaunches gl_gm;
 };
 
 // hexahedra (hfr_hex.cu): the residual passes (mode GM_UF / GM_QF / GM_RES) and the element

@@ -220,11 +220,11 @@ __global__ void __launch_bounds__(HT) k_hex_elem(const __grid_constant__ PhysPar
     const double uf = w.Uf[f * nf + m][v];
     double ub;
     if (t >= 0) {
-      ub = a.uhat[(size_t)a.fnode[(6 * e + f) * FS + m] * HNV + v];
+      ub = a.uhat[(size_t)FR_IDX(a.fnode[(6 * e + f) * FS + m], a.npts, 10) * HNV + v];
     } else if (kf == FK_FAR) {
       ub = 0.5 * (uf + a.uinf[v]);
     } else {
-      const int nb = a.nbr[6 * e + f], fn = a.nbr_face[6 * e + f];
+      const int nb = (int)FR_IDX(a.nbr[6 * e + f], a.E, 11), fn = (int)FR_IDX(a.nbr_face[6 * e + f], 6, 12);
       const double un = a.Uf_all[((size_t)(6 * nb + fn) * FS + m) * HNV + v];
       ub = kf == FK_FR ? 0.5 * (uf + un) : (imp ? un : uf);
     }
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(HT) k_hex_elem(const __grid_constant__ PhysPar
 #pragma unroll
       for (int v = 0; v < HNV; ++v) qf[c][v] = visc ? w.qf[jj][c][v] : 0.0;
     if (!traced && kf != FK_FAR) {
-      const int nb = a.nbr[6 * e + f], fn = a.nbr_face[6 * e + f];
+      const int nb = (int)FR_IDX(a.nbr[6 * e + f], a.E, 11), fn = (int)FR_IDX(a.nbr_face[6 * e + f], 6, 12);
       const size_t nix = (size_t)(6 * nb + fn) * FS + m;
 #pragma unroll
       for (int v = 0; v < HNV; ++v) {
@@ -369,7 +369,9 @@ struct HJac {
   T RU[HFP][HNV][HNV], RH[HFP][HNV][HNV], RQ[HFP][3][HNV][HNV];
 };
 
-template <typename T>
+// NC: points per line as a compile-time constant (the index arithmetic of the lines folds), or 0
+// for the element's own degree at run time
+template <typename T, int NC>
 __global__ void __launch_bounds__(HJT, 1) k_hex_jacobian(const __grid_constant__ PhysParams pp,
                                                         const __grid_constant__ GArgs a,
                                                         const __grid_constant__ JArgs j) {
@@ -383,7 +385,7 @@ __global__ void __launch_bounds__(HJT, 1) k_hex_jacobian(const __grid_constant__
   const GenRef& RF = *a.ref;
   for (int k = blockIdx.x; k < j.Eim; k += gridDim.x) {
     const int e = j.imp_idx[k];
-    const int n = a.deg[e], ns = n * n * n, nf = n * n, FS = a.fs;
+    const int n = NC > 0 ? NC : a.deg[e], ns = n * n * n, nf = n * n, FS = a.fs;
     const int nA = ns * HNV, nT = 6 * nf * HNV;
     const double* gs = a.geo_sol + (size_t)a.goff[e] * 10;
     __syncthreads();  // the previous element's buffers are free
@@ -426,10 +428,10 @@ __global__ void __launch_bounds__(HJT, 1) k_hex_jacobian(const __grid_constant__
       w.Uf[f * nf + m][v] = s;
       const int t = w.tr[f];
       if (t >= 0) {
-        w.ub[f * nf + m][v] = T(a.uhat[(size_t)a.fnode[(6 * e + f) * FS + m] * HNV + v]);
+        w.ub[f * nf + m][v] = T(a.uhat[(size_t)FR_IDX(a.fnode[(6 * e + f) * FS + m], a.npts, 10) * HNV + v]);
         w.un[f * nf + m][v] = s;
       } else {  // interface face: the explicit neighbour's state
-        const int nb = a.nbr[6 * e + f], fn = a.nbr_face[6 * e + f];
+        const int nb = (int)FR_IDX(a.nbr[6 * e + f], a.E, 11), fn = (int)FR_IDX(a.nbr_face[6 * e + f], 6, 12);
         const T un = T(a.Uf_all[((size_t)(6 * nb + fn) * FS + m) * HNV + v]);
         w.un[f * nf + m][v] = un;
         w.ub[f * nf + m][v] = un;
@@ -681,6 +683,18 @@ __global__ void __launch_bounds__(HJT, 1) k_hex_jacobian(const __grid_constant__
   }
 }
 
+// the kernel for a mesh whose elements all have n points per line (hexahedral meshes carry one
+// degree), the run-time form otherwise
+template <typename T>
+static auto hex_jac_kernel(int n) -> decltype(&k_hex_jacobian<T, 0>) {
+  switch (n) {
+    case 2: return &k_hex_jacobian<T, 2>;
+    case 3: return &k_hex_jacobian<T, 3>;
+    case 4: return &k_hex_jacobian<T, 4>;
+    default: return &k_hex_jacobian<T, 0>;
+  }
+}
+
 int hex_jacobian_grid(int prec_bytes) {
   int dev = 0, nsm = 1;
   cudaGetDevice(&dev);
@@ -697,16 +711,16 @@ cudaError_t hex_jacobian(GenCtx* g, const GArgs& a, const JArgs& j) {
   if (j.Eim == 0) return cudaSuccess;
   if (g->pb == 8) {
     const size_t smem = sizeof(HJWork<double>);
-    if ((e = cudaFuncSetAttribute(k_hex_jacobian<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-        cudaSuccess)
+    auto kern = hex_jac_kernel<double>(g->h_deg.empty() ? 0 : g->h_deg[0]);
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
       return e;
-    (count_launch(), k_hex_jacobian<double><<<g->jgrid, HJT, smem, g->st>>>(g->pp, a, j));
+    (count_launch(), kern<<<g->jgrid, HJT, smem, g->st>>>(g->pp, a, j));
   } else {
     const size_t smem = sizeof(HJWork<float>);
-    if ((e = cudaFuncSetAttribute(k_hex_jacobian<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-        cudaSuccess)
+    auto kern = hex_jac_kernel<float>(g->h_deg.empty() ? 0 : g->h_deg[0]);
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
       return e;
-    (count_launch(), k_hex_jacobian<float><<<g->jgrid, HJT, smem, g->st>>>(g->pp, a, j));
+    (count_launch(), kern<<<g->jgrid, HJT, smem, g->st>>>(g->pp, a, j));
   }
   return cudaGetLastError();
 }
@@ -787,3 +801,5 @@ void hex_geometry(const double* verts, int E, const int* deg, const long long* g
 
 }  // namespace gen
 }  // namespace hfr
+
+#include "hfr_checked_unit.inc"

@@ -22,8 +22,21 @@ struct NvtxScope {
 };
 #define FR_NVTX(name) ::hfr::NvtxScope fr_nvtx_scope_(name)
 
-// counts every kernel launch of the library (reported by fr_kernel_launches)
+// Stream-capture helpers of the whole-stage graphs: a conditional handle of the graph that s is
+// capturing into, and a conditional node (WHILE / IF) after the work captured so far on s, whose
+// body graph is returned for capture on another stream
+cudaError_t graph_conditional_handle(cudaStream_t s, unsigned dflt, unsigned flags, cudaGraphConditionalHandle* h);
+cudaError_t graph_add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                                  cudaGraph_t* body);
+
+// counts every kernel launch of the library (reported by fr_kernel_launches); launch_count reads
+// the counter, launch_count_add corrects it for graphs (a capture counts its kernels once, a
+// replay runs them as often as its loops turn)
 void count_launch();
+// bounds-checked build: the collectors of the translation units' device words (FR_IDX)
+void checked_register(int (*collect)(unsigned long long* first, unsigned long long* count));
+unsigned long long launch_count();
+void launch_count_add(long long delta);
 
 // n-point Gauss-Legendre nodes and weights (Newton on P_n), and the 1D reference operators of
 // degree p (barycentric Lagrange derivatives, DG-recovering correction lift l_i(+-1)/w_i)
@@ -54,6 +67,7 @@ struct ResArgs {
   double* dR;            // nullable (JVP)
   double* gview;         // nullable: w_q J_f F^.n on trace faces
   double* dgview;        // nullable (JVP)
+  int ntrace;            // trace faces (bounds of tr_of in the checked build)
 };
 
 cudaError_t launch_residual(int p, const RefOps& ref, const PhysParams& pp, const ResArgs& a, bool need_nbr,
@@ -76,6 +90,7 @@ struct JacArgs {
   const int* kind;
   const int* tr_of;
   const double* Uf_all;  // neighbour face states for interface faces
+  int E, ntrace;         // elements and trace faces (bounds in the checked build)
   double a_dt;
   void* A;
   void* B;
@@ -136,7 +151,20 @@ struct UnevenDev {
   int colmajor = 0;  // the blocks are stored column-major (hexahedra); all go to the global kernel
   int gmax_nA = 0, gmax_nT = 0;
 };
-int uneven_tables(int prec_bytes, int n, const int* nA, const int* nT, UnevenTables* tb);
+// skip (nullable): elements condensed elsewhere keep their offsets but are not scheduled
+int uneven_tables(int prec_bytes, int n, const int* nA, const int* nT, UnevenTables* tb,
+                  const unsigned char* skip = nullptr);
+// One shape class of a packed uneven FP32 batch (list: its elements, off: the batch's per-element
+// offsets as uploaded with its tables) through the fixed-shape kernels of that shape, in chunks of
+// cap elements staged in scratch (class_scratch_bytes; one buffer may serve every shape: its
+// leading status words, set once by class_scratch_init_status, are where every shape expects
+// them).  The chunk's failures go to status with packed element ids.
+size_t class_scratch_bytes(int nA, int nT, int cap);
+cudaError_t class_scratch_init_status(void* scratch, cudaStream_t st);
+cudaError_t launch_condense_class(const int* list, int count, int nA, int nT, const long long* off, const void* A,
+                                  const void* B, const void* C, const void* D, const double* r, const double* s,
+                                  void* LU, int* piv, void* XB, double* xr, void* S, double* t, int* status,
+                                  void* scratch, int cap, int tc_mode, cudaStream_t st);
 size_t uneven_dev_bytes(const UnevenTables& tb);
 cudaError_t uneven_upload(const UnevenTables& tb, void* dbuf, UnevenDev* dv, cudaStream_t st);
 cudaError_t launch_condense_uneven_dev(int prec_bytes, const UnevenDev& dv, const void* A, const void* B, const void* C,

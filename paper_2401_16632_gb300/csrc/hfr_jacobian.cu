@@ -189,11 +189,11 @@ __global__ void __launch_bounds__(JAC_THREADS, sizeof(T) == 4 ? (P <= 3 ? 4 : (P
     for (int c = 0; c < N; ++c) s += l[c] * w.U[line_pt<N>(r, m, c)][v];
     w.Uf[j][v] = s;
     if (w.kf[f] == FK_TRACE) {
-      const int t = a.tr_of[e * 4 + f];
+      const int t = (int)FR_IDX(a.tr_of[e * 4 + f], a.ntrace, 23);
       w.ub[j][v] = T(a.uhat[((size_t)t * N + m) * NV + v]);
       w.un[j][v] = s;
     } else {  // interface face: explicit neighbour's state is the common solution
-      const int en = a.nbr[e * 4 + f], fnb = a.nbr_face[e * 4 + f];
+      const int en = (int)FR_IDX(a.nbr[e * 4 + f], a.E, 24), fnb = (int)FR_IDX(a.nbr_face[e * 4 + f], 4, 25);
       const T un = T(a.Uf_all[((size_t)en * NF + fnb * N + m) * NV + v]);
       w.un[j][v] = un;
       w.ub[j][v] = un;
@@ -571,3 +571,5 @@ cudaError_t launch_jacobian(int p, int prec_bytes, const RefOps& ref, const Phys
 }
 
 }  // namespace hfr
+
+#include "hfr_checked_unit.inc"

@@ -142,6 +142,7 @@ __global__ void k_axpy_multi(const GmresState* st, int j, const double* __restri
   if (which < 2 && gated(st, j)) return;
   const double* c = which == 0 ? st->hc : (which == 1 ? st->h2 : st->y);
   const double sg = which == 2 ? 1.0 : -1.0;
+  if (nvec < 0) nvec = st->k;  // the cycle's length, from the device state
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
     double acc = 0.0;
@@ -328,6 +329,118 @@ int run_gmres(const GmresOps& ops, const GmresBuffers& b, const double* t, doubl
   res->bnorm = hs.bnorm;
   res->rel = hs.bnorm > 0.0 ? hs.beta / hs.bnorm : 0.0;
   return 0;
+}
+
+// ------------------------------------------------------------ GMRES inside a captured graph
+__global__ void k_gg_begin(GmresGraphDev* d, cudaGraphConditionalHandle hw) {
+  d->first = 1;
+  d->total = 0;
+  d->cycles = 0;
+  d->nan = 0;
+  d->converged = 0;
+  cudaGraphSetConditional(hw, 1u);
+}
+// the residual mat-vec runs on every cycle but the first (x = 0 there)
+__global__ void k_gg_ifres(const GmresGraphDev* d, cudaGraphConditionalHandle hi) {
+  cudaGraphSetConditional(hi, d->first ? 0u : 1u);
+}
+// V0 = t on the first cycle (later ones hold t - L x already)
+__global__ void k_gg_start(const GmresGraphDev* d, const double* __restrict__ t, double* __restrict__ v0, size_t n) {
+  if (!d->first) return;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) v0[x] = t[x];
+}
+// the restart decision of the host driver, on the device
+__global__ void k_gg_after(GmresGraphDev* d, const GmresState* st, int maxit, cudaGraphConditionalHandle hw) {
+  const int k = st->k;
+  d->total += k;
+  d->cycles += 1;
+  d->first = 0;
+  if (st->nan) d->nan = 1;
+  d->converged = st->converged;
+  const int cont = (st->nan || st->converged || d->total >= maxit || k == 0) ? 0 : 1;
+  cudaGraphSetConditional(hw, (unsigned)cont);
+}
+
+cudaError_t capture_gmres(const GmresOps& ops, const GmresBuffers& b, const double* t, double* x, double rtol,
+                          int restart, int maxit, GmresGraphDev* dev, cudaStream_t s, const cudaStream_t sc[2],
+                          GmresGraphLaunches* counts) {
+  const size_t n = b.n;
+  const int m = restart > GM_MAXM ? GM_MAXM : (restart < 1 ? 1 : restart);
+  GmresState* st = b.state;
+  const int nb = grid_for(n);
+  cudaError_t e;
+  const unsigned long long l0 = hfr::launch_count();
+  cudaGraphConditionalHandle hw, hi;
+  if ((e = graph_conditional_handle(s, 0u, 0u, &hw)) != cudaSuccess) return e;
+  (hfr::count_launch(), k_reset_state<<<1, 32, 0, s>>>(st));
+  norm_into(b, 0, const_cast<double*>(t), n, 4, rtol, m, s);  // bnorm
+  if ((e = cudaMemsetAsync(x, 0, n * sizeof(double), s)) != cudaSuccess) return e;
+  (hfr::count_launch(), k_gg_begin<<<1, 1, 0, s>>>(dev, hw));
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  cudaGraph_t body = nullptr, ifb = nullptr;
+  if ((e = graph_add_conditional(s, hw, cudaGraphCondTypeWhile, &body)) != cudaSuccess) return e;
+  const unsigned long long l1 = hfr::launch_count();
+  // ---- one restart cycle
+  if ((e = cudaStreamBeginCaptureToGraph(sc[0], body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) !=
+      cudaSuccess)
+    return e;
+  auto abort0 = [&](cudaError_t ee) {
+    cudaGraph_t tmp = nullptr;
+    cudaStreamEndCapture(sc[0], &tmp);
+    return ee;
+  };
+  if ((e = graph_conditional_handle(sc[0], 0u, 0u, &hi)) != cudaSuccess) return abort0(e);
+  (hfr::count_launch(), k_gg_ifres<<<1, 1, 0, sc[0]>>>(dev, hi));
+  if ((e = graph_add_conditional(sc[0], hi, cudaGraphCondTypeIf, &ifb)) != cudaSuccess) return abort0(e);
+  const unsigned long long l2 = hfr::launch_count();
+  if ((e = cudaStreamBeginCaptureToGraph(sc[1], ifb, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) !=
+      cudaSuccess)
+    return abort0(e);
+  ops.matvec(ops.ctx, x, b.V, sc[1]);  // L x into V0
+  (hfr::count_launch(), k_sub<<<nb, KB, 0, sc[1]>>>(t, b.V, b.V, n));
+  e = cudaGetLastError();
+  {
+    cudaGraph_t tmp = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(sc[1], &tmp);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e != cudaSuccess) return abort0(e);
+  const unsigned long long l3 = hfr::launch_count();
+  (hfr::count_launch(), k_gg_start<<<nb, KB, 0, sc[0]>>>(dev, t, b.V, n));
+  norm_into(b, 0, b.V, n, 3, rtol, m, sc[0]);  // beta
+  (hfr::count_launch(), k_cycle_start<<<nb, KB, 0, sc[0]>>>(st, b.V, n, rtol));
+  for (int j = 0; j < m; ++j) {  // every iteration enqueued; those after the cycle's end return at once
+    double* vj = b.V + (size_t)j * n;
+    double* w = b.V + (size_t)(j + 1) * n;
+    double* zj = b.Z + (size_t)j * n;
+    ops.precond(ops.ctx, st, j, vj, zj, b.z32, sc[0]);
+    ops.gated_matvec(ops.ctx, st, j, zj, b.z32, w, sc[0]);
+    (hfr::count_launch(), k_cgs<<<nb, KB, 0, sc[0]>>>(st, j, b.V, n, j + 1, 0, b.V, j + 2, w, b.partial, b.ticket, 5,
+                                                       rtol, m, 0));
+    (hfr::count_launch(), k_cgs<<<nb, KB, 0, sc[0]>>>(st, j, b.V, n, j + 1, 1, w, 1, w, b.partial, b.ticket, 6, rtol,
+                                                       m, 0));
+    (hfr::count_launch(), k_cgs<<<nb, KB, 0, sc[0]>>>(st, j, b.V, n, j + 1, 0, b.V, j + 1, w, b.partial, b.ticket, 1,
+                                                       rtol, m, 1));
+    (hfr::count_launch(), k_cgs<<<nb, KB, 0, sc[0]>>>(st, j, b.V, n, j + 1, 2, w, 1, w, b.partial, b.ticket, 2, rtol,
+                                                       m, 1));
+  }
+  (hfr::count_launch(), k_solve_y<<<1, 32, 0, sc[0]>>>(st));
+  (hfr::count_launch(), k_axpy_multi<<<nb, KB, 0, sc[0]>>>(st, 0, b.Z, n, -1, x, 2));
+  (hfr::count_launch(), k_gg_after<<<1, 1, 0, sc[0]>>>(dev, st, maxit, hw));
+  e = cudaGetLastError();
+  {
+    cudaGraph_t tmp = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(sc[0], &tmp);
+    if (e == cudaSuccess) e = e2;
+  }
+  const unsigned long long l4 = hfr::launch_count();
+  if (counts) {
+    counts->fixed = (int)(l1 - l0);
+    counts->cycle = (int)((l4 - l3) + (l2 - l1));
+    counts->residual = (int)(l3 - l2);
+  }
+  return e;
 }
 
 }  // namespace hfr

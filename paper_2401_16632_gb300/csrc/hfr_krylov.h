@@ -103,4 +103,21 @@ int barrier_selftest(int nblocks, int absent, int rounds, double timeout_s, int*
 int run_gmres(const GmresOps& ops, const GmresBuffers& b, const double* t, double* x, double rtol, int restart,
               int maxit, int check_every, GmresResult* res, cudaStream_t s);
 
+// The same GMRES(m) enqueued on a capturing stream s for a whole-stage graph: the restart cycles
+// are a WHILE node (body captured on sc[0]) whose restart decision is taken on the device, the
+// residual mat-vec of every cycle but the first an IF node (body on sc[1]), and the m iterations
+// of a cycle enqueued unrolled, each returning at once after the cycle's end (device state).
+// The iteration limit is checked per cycle.  dev: the solve's counters (device memory).
+struct GmresGraphDev {
+  int first, total, cycles, nan, converged;
+};
+struct GmresGraphLaunches {
+  int fixed = 0;     // once per solve
+  int cycle = 0;     // per cycle
+  int residual = 0;  // per cycle but the first
+};
+cudaError_t capture_gmres(const GmresOps& ops, const GmresBuffers& b, const double* t, double* x, double rtol,
+                          int restart, int maxit, GmresGraphDev* dev, cudaStream_t s, const cudaStream_t sc[2],
+                          GmresGraphLaunches* counts);
+
 }  // namespace hfr

@@ -78,14 +78,14 @@ __global__ void __launch_bounds__(TPE* EPB) k_element(const __grid_constant__ Re
         continue;
       }
       if (kf == FK_TRACE) {
-        const int t = a.tr_of[e * 4 + f];
+        const int t = (int)FR_IDX(a.tr_of[e * 4 + f], a.ntrace, 20);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           size_t ix = ((size_t)t * N + m) * NV + v;
           w.ub[j][v] = mk<S>(a.uhat[ix], a.duhat ? a.duhat[ix] : 0.0);
         }
       } else {
-        const int en = a.nbr[e * 4 + f], fn = a.nbr_face[e * 4 + f];
+        const int en = (int)FR_IDX(a.nbr[e * 4 + f], a.E, 21), fn = (int)FR_IDX(a.nbr_face[e * 4 + f], 4, 22);
         const double* un = a.Uf_all + ((size_t)en * NF + fn * N + m) * NV;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(TPE* EPB) k_element(const __grid_constant__ Re
           for (int v = 0; v < NV; ++v) Fh[v] = Fh[v] - (n0 * Fv[0][v] + n1 * Fv[1][v]);
         }
       } else {
-        const int en = a.nbr[e * 4 + f], fn = a.nbr_face[e * 4 + f];
+        const int en = (int)FR_IDX(a.nbr[e * 4 + f], a.E, 21), fn = (int)FR_IDX(a.nbr_face[e * 4 + f], 4, 22);
         const size_t nix = (size_t)en * NF + fn * N + m;
         S un[NV];
 #pragma unroll
@@ -364,3 +364,5 @@ cudaError_t launch_trace_assemble(const double* gview, const int* sides, int ntr
 }
 
 }  // namespace hfr
+
+#include "hfr_checked_unit.inc"

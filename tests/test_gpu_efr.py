@@ -166,3 +166,26 @@ def test_efr_stage_matches_oracle_newton(name, prec):
     inc = np.abs(Uo - U).max()
     assert np.abs(us.cpu().numpy() - Uo.reshape(-1)).max() < 1e-9 * inc
     ctx.close()
+
+
+def test_efr_graph_stage_equals_stream_stage():
+    """The EFR stage as one CUDA graph gives the stream stage's result bit for bit."""
+    mesh, phys, U = _case("band_p2")
+    out = []
+    for graph in (False, True):
+        ctx = pkg.Context(mesh, phys, precision=pkg.FR_PREC_FP32, tableau=pkg.FR_TAB_SDIRK2,
+                          trace_kind=pkg.FR_TRACE_EFR)
+        if graph:
+            ctx.imex_stage_set_graph(True)
+        u_n = torch.tensor(U.reshape(-1), device=DEV)
+        uh = ctx.hfr_initial_trace(u_n)
+        R_hist = ctx.empty(3, *ctx.state_shape)
+        us = ctx.empty(*ctx.state_shape)
+        ctx.imex_stage(0, 0.05, u_n, us, uh, R_hist)
+        st = ctx.imex_stage(1, 0.05, u_n, us, uh, R_hist, newton_tol=1e-12, newton_maxit=30, gmres_rtol=1e-8,
+                            gmres_maxit=5000)
+        assert st["converged"]
+        out.append((us.clone(), uh.clone(), st["newton_iterations"], st["gmres_iterations"]))
+        ctx.close()
+    assert out[0][2:] == out[1][2:]
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])

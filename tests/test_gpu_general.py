@@ -286,6 +286,38 @@ def test_general_stage_matches_oracle_newton(name, prec):
     ctx.close()
 
 
+@pytest.mark.parametrize("name,prec", [("wall_band_ns", pkg.FR_PREC_FP64), ("wall_band_ns", pkg.FR_PREC_FP32),
+                                       ("mixed_band_advdiff", pkg.FR_PREC_FP32)])
+def test_general_graph_stage_equals_stream_stage(name, prec):
+    """The implicit stage as one CUDA graph (Newton WHILE node, solve IF node, GMRES restart cycles
+    as a nested WHILE node with device-side decisions) gives the stream stage's result bit for
+    bit, with the same Newton and GMRES iteration counts; a second launch reuses the graph."""
+    mesh, phys, U = _case(name)
+    dt = 0.004 if name.startswith("wall") else 0.05
+    out = []
+    for graph in (False, True):
+        ctx = pkg.Context(mesh, phys, precision=prec, tableau=pkg.FR_TAB_SDIRK2)
+        if graph:
+            ctx.imex_stage_set_graph(True)
+        u_n = torch.tensor(ctx.pack_state(U), device=DEV)
+        res = []
+        for _ in range(2):
+            uh = ctx.hfr_initial_trace(u_n)
+            R_hist = ctx.empty(3, *ctx.state_shape)
+            us = ctx.empty(*ctx.state_shape)
+            ctx.imex_stage(0, dt, u_n, us, uh, R_hist)
+            st = ctx.imex_stage(1, dt, u_n, us, uh, R_hist, newton_tol=1e-12, newton_maxit=30, gmres_rtol=1e-8,
+                                gmres_maxit=5000)
+            assert st["converged"]
+            res.append((us.clone(), uh.clone(), st["newton_iterations"], st["gmres_iterations"]))
+        assert torch.equal(res[0][0], res[1][0])  # the replay repeats the first launch
+        out.append(res[0])
+        ctx.close()
+    (u0, h0, n0, g0), (u1, h1, n1, g1) = out
+    assert (n0, g0) == (n1, g1)
+    assert torch.equal(u0, u1) and torch.equal(h0, h1)
+
+
 # ------------------------------------------------------------------ full size (boundary layer)
 _BL = {}
 

@@ -100,3 +100,26 @@ def test_uneven_global_memory_blocks_and_a_singular_element():
     with pytest.raises(pkg.HfrError) as ei:
         pkg.hfr_condense_uneven([36, 64, 36], [48, 64, 48], *_packed(blocks, torch.float32), precision=pkg.FR_PREC_FP32)
     assert ei.value.code == pkg.FR_ERR_SINGULAR and ei.value.failed_element == 1
+
+
+def test_uneven_fp32_large_blocks_take_the_blocked_lu_and_report_a_singular_element():
+    """FP32 (144, 96) blocks go to the blocked LU with the tensor-core GEMMs (3xTF32): the same
+    condensation as the oracle's to FP32 accuracy, and a zero column found by the panel pivot
+    search is reported with its element."""
+    shapes = [(144, 96), (36, 48), (144, 96), (144, 96)]
+    blocks = _batch(shapes, 5)
+    out = pkg.hfr_condense_uneven([a for a, _ in shapes], [t for _, t in shapes], *_packed(blocks, torch.float32),
+                                  precision=pkg.FR_PREC_FP32)
+    S = _split(out["S"].cpu().numpy().astype(np.float64), [t * t for _, t in shapes])
+    XB = _split(out["XB"].cpu().numpy().astype(np.float64), [a * t for a, t in shapes])
+    for k, b in enumerate(blocks):
+        XBo, xro, So, to = condense(*(x[None] for x in b))
+        assert np.abs(S[k] - So[0].reshape(-1)).max() < 1e-5 * np.abs(So).max(), k
+        assert np.abs(XB[k] - XBo[0].reshape(-1)).max() < 1e-5 * np.abs(XBo).max(), k
+    A2 = blocks[2][0].copy()
+    A2[:, 100] = 0.0  # no pivot in column 100 (the fourth panel)
+    blocks[2] = (A2,) + blocks[2][1:]
+    with pytest.raises(pkg.HfrError) as ei:
+        pkg.hfr_condense_uneven([a for a, _ in shapes], [t for _, t in shapes], *_packed(blocks, torch.float32),
+                                precision=pkg.FR_PREC_FP32)
+    assert ei.value.code == pkg.FR_ERR_SINGULAR and ei.value.failed_element == 2
