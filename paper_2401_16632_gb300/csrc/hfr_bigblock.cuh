@@ -5,12 +5,14 @@
 //      lowest row on ties), its row interchanges applied to the columns left and right of it and
 //      the block row right of it solved with the panel's unit lower triangle (same kernel); then
 //      the trailing matrix updated by the batched GEMM;
-//   2. X = P [B] (the row interchanges applied to the right-hand sides);
-//   3. forward substitution with the unit lower factor and back substitution with the upper factor,
-//      both blocked by NB rows: a small triangular solve of the diagonal block (one thread per
-//      right-hand side column), then the rest of the rows updated by a batched GEMM;
+//   2-3. X = A^{-1} P B: one CTA per block of 32 columns of one element, the block whole in shared
+//      memory (permuted columns of B in, forward and back substitution by factor panels staged in
+//      shared memory, X out once); where the block does not fit: the row interchanges applied to
+//      the right-hand sides, then forward / back substitution blocked by NB rows (a small
+//      triangular solve of the diagonal block, the rest of the rows updated by a batched GEMM);
 //   4. S = D - C X_B by the same batched GEMM;
-//   5. x_r = A^{-1} r and t = s - C x_r in FP64 arithmetic (one CTA per element).
+//   5. t = s - C x_r with FP64 accumulation (one CTA per element); x_r is the right-hand side's
+//      column of the column-block solve, or, on the blocked path, A^{-1} r by FP64 substitution.
 // The batched GEMM is a register-tiled CUDA-core kernel: 128 x 128 output tiles in FP32 (64 x 64 in
 // FP64), 256 threads with 8 x 8 (4 x 4) outputs each, K staged through two shared-memory buffers 8
 // at a time; arithmetic in the block precision T.  Included by hfr_condense.cu (uses UnevenArgs and DEV_ERR_*).
@@ -201,7 +203,7 @@ __global__ void __launch_bounds__(BT) k_big_lu_panel(const __grid_constant__ Une
 template <typename T>
 __global__ void __launch_bounds__(BT) k_big_rhs(const __grid_constant__ UnevenArgs a, const int* __restrict__ list,
                                                 int nlist, int uni_nA, int uni_nT) {
-  __shared__ int perm[1024];
+  __shared__ int perm[1024], pvs[1024];
   for (int li = blockIdx.x; li < nlist; li += gridDim.x) {
     const Elem E = elem_of(a, list, li, uni_nA, uni_nT);
     const int nA = E.nA, nT = E.nT;
@@ -209,10 +211,14 @@ __global__ void __launch_bounds__(BT) k_big_rhs(const __grid_constant__ UnevenAr
     T* X = reinterpret_cast<T*>(a.XB) + E.o[1];
     const int* piv = a.piv + E.o[3];
     __syncthreads();
+    for (int i = threadIdx.x; i < nA; i += BT) {
+      pvs[i] = piv[i];
+      perm[i] = i;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-      for (int i = 0; i < nA; ++i) perm[i] = i;
       for (int j = 0; j < nA; ++j) {
-        const int p = piv[j];
+        const int p = pvs[j];
         if (p >= 0 && p < nA && p != j) {
           const int u = perm[j];
           perm[j] = perm[p];
@@ -269,6 +275,158 @@ __global__ void __launch_bounds__(128) k_big_trsm_diag(const __grid_constant__ U
 #pragma unroll
   for (int q = 0; q < NB; ++q)
     if (r0 + q < r1) X[(size_t)(r0 + q) * nT + col] = x[q];
+}
+
+// 2'-3'. X = A^{-1} P B for a block of SC columns per CTA, whole in shared memory: the permuted
+// columns of B loaded once, forward substitution with the unit lower factor and back substitution
+// with the upper factor by panels of SP pivots (the factor's panel staged in shared memory: an
+// in-panel solve of SP steps, then one register-tiled update of every row outside the panel), X
+// written once.  Replaces the row interchange copy and the blocked triangular solves when the two
+// tiles fit shared memory.
+constexpr int SC = 32;  // columns of X per CTA (the lanes of a warp)
+constexpr int SP = 32;  // pivots per factor panel
+template <typename T>
+size_t solve_smem(int max_nA) {
+  return ((size_t)max_nA * SC + (size_t)max_nA * SP) * sizeof(T) + (size_t)max_nA * sizeof(int);
+}
+// Xs rows [ra, rb) -= (factor panel rows, staged at Lp row r - lbase) x (solved panel rows of Xs,
+// p0 .. p0 + w - 1): eight rows per warp pass, four pivots per step (one 16-byte broadcast of the
+// factor per row, four values of the solved rows per lane); the factor panel is zero beyond w
+template <typename T>
+__device__ __forceinline__ void solve_update(T* Xs, const T* Lp, int p0, int w, int ra, int rb, int lbase, int lane,
+                                             int wid) {
+  constexpr int NW = BT / 32;
+  for (int r0 = ra + 8 * wid; r0 < rb; r0 += 8 * NW) {
+    T acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = T(0);
+    for (int j = 0; j < w; j += 4) {
+      T xv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) xv[u] = j + u < w ? Xs[(p0 + j + u) * SC + lane] : T(0);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (r0 + q < rb) {
+          const T* lr = Lp + (size_t)(r0 + q - lbase) * SP + j;  // 16-byte aligned (j % 4 == 0)
+          if constexpr (sizeof(T) == 4) {
+            const float4 l4 = *reinterpret_cast<const float4*>(lr);
+            acc[q] += l4.x * xv[0] + l4.y * xv[1] + l4.z * xv[2] + l4.w * xv[3];
+          } else {
+            const double2 la = reinterpret_cast<const double2*>(lr)[0], lb = reinterpret_cast<const double2*>(lr)[1];
+            acc[q] += la.x * xv[0] + la.y * xv[1] + lb.x * xv[2] + lb.y * xv[3];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (r0 + q < rb) Xs[(r0 + q) * SC + lane] -= acc[q];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BT, 2) k_big_solve(const __grid_constant__ UnevenArgs a, const int* __restrict__ list,
+                                                  int base, int nlist, int uni_nA, int uni_nT) {
+  extern __shared__ __align__(16) unsigned char sv_smem[];
+  if ((int)blockIdx.y >= nlist) return;
+  const Elem E = elem_of(a, list, base + blockIdx.y, uni_nA, uni_nT);
+  const int nA = E.nA, nT = E.nT, c0 = blockIdx.x * SC;
+  if (c0 > nT) return;  // uniform over the CTA (column nT is r: x_r)
+  T* Xs = reinterpret_cast<T*>(sv_smem);  // nA x SC
+  T* Lp = Xs + (size_t)nA * SC;            // nA x SP: rows of the current factor panel
+  int* perm = reinterpret_cast<int*>(Lp + (size_t)nA * SP);
+  const T* L = reinterpret_cast<const T*>(a.LU) + E.o[0];
+  const T* B = reinterpret_cast<const T*>(a.B) + E.o[1];
+  T* X = reinterpret_cast<T*>(a.XB) + E.o[1];
+  const int* piv = a.piv + E.o[3];
+  const bool cm = a.colmajor != 0;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  constexpr int NW = BT / 32;
+  // rows in the order the interchanges leave them: the pivots staged in shared memory (the factor
+  // panel's space, free until the forward sweep), then applied in sequence by one thread
+  int* pvs = reinterpret_cast<int*>(Lp);
+  for (int i = tid; i < nA; i += BT) {
+    pvs[i] = piv[i];
+    perm[i] = i;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int j = 0; j < nA; ++j) {
+      const int p = pvs[j];
+      if (p >= 0 && p < nA && p != j) {
+        const int u = perm[j];
+        perm[j] = perm[p];
+        perm[p] = u;
+      }
+    }
+  }
+  __syncthreads();
+  const int c = c0 + lane;
+  const bool live = c < nT;
+  const double* rv = a.r + E.o[3];
+  for (int i = wid; i < nA; i += NW) {
+    const int src = perm[i];
+    Xs[i * SC + lane] = live ? (cm ? B[(size_t)c * nA + src] : B[(size_t)src * nT + c]) : (c == nT ? T(rv[src]) : T(0));
+  }
+  // ---- forward: unit lower factor, panels top to bottom
+  for (int p0 = 0; p0 < nA; p0 += SP) {
+    const int w = min(SP, nA - p0);
+    __syncthreads();  // the previous panel's readers are done
+    for (int idx = tid; idx < (nA - p0) * SP; idx += BT) {
+      const int r = idx / SP, j = idx % SP;
+      Lp[r * SP + j] = j < w ? L[(size_t)(p0 + r) * nA + p0 + j] : T(0);
+    }
+    __syncthreads();
+    if (wid == 0) {  // in-panel solve: one warp, lane = column, the panel's rows in registers
+      T x[SP];
+#pragma unroll
+      for (int r = 0; r < SP; ++r) x[r] = r < w ? Xs[(p0 + r) * SC + lane] : T(0);
+#pragma unroll
+      for (int j = 0; j < SP; ++j)
+#pragma unroll
+        for (int r = j + 1; r < SP; ++r) x[r] -= Lp[r * SP + j] * x[j];  // zero beyond w
+#pragma unroll
+      for (int r = 0; r < SP; ++r)
+        if (r < w) Xs[(p0 + r) * SC + lane] = x[r];
+    }
+    __syncthreads();
+    // rows below the panel: X[r] -= L[r, panel] X[panel]
+    solve_update<T>(Xs, Lp, p0, w, p0 + w, nA, p0, lane, wid);
+  }
+  // ---- backward: upper factor, panels bottom to top
+  const int np = (nA + SP - 1) / SP;
+  for (int pb = np - 1; pb >= 0; --pb) {
+    const int p0 = pb * SP, w = min(SP, nA - p0);
+    __syncthreads();
+    for (int idx = tid; idx < (p0 + w) * SP; idx += BT) {
+      const int r = idx / SP, j = idx % SP;
+      Lp[r * SP + j] = j < w ? L[(size_t)r * nA + p0 + j] : T(0);
+    }
+    __syncthreads();
+    if (wid == 0) {
+      T x[SP];
+#pragma unroll
+      for (int r = 0; r < SP; ++r) x[r] = r < w ? Xs[(p0 + r) * SC + lane] : T(0);
+#pragma unroll
+      for (int j = SP - 1; j >= 0; --j) {
+        if (j < w) {
+          x[j] = x[j] / Lp[(p0 + j) * SP + j];
+#pragma unroll
+          for (int r = 0; r < j; ++r) x[r] -= Lp[(p0 + r) * SP + j] * x[j];
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < SP; ++r)
+        if (r < w) Xs[(p0 + r) * SC + lane] = x[r];
+    }
+    __syncthreads();
+    solve_update<T>(Xs, Lp, p0, w, 0, p0, 0, lane, wid);  // rows above the panel
+  }
+  __syncthreads();
+  if (live)
+    for (int i = wid; i < nA; i += NW) X[(size_t)i * nT + c] = Xs[i * SC + lane];
+  else if (c == nT)
+    for (int i = wid; i < nA; i += NW) a.xr[E.o[3] + i] = double(Xs[i * SC + lane]);
 }
 
 // 3b / 4. batched GEMM Out -= A B, per element:
@@ -644,11 +802,12 @@ __global__ void __launch_bounds__(btc::THREADS, 1) k_big_gemm_tc(const __grid_co
   if (w == 0) tmem_dealloc(tmem, 256);
 }
 
-// 5. x_r = A^{-1} r (interchanges, forward, backward; FP64) and t = s - C x_r
+// 5. t = s - C x_r; unless solved with X: x_r = A^{-1} r (interchanges, forward, backward; FP64)
 template <typename T>
 __global__ void __launch_bounds__(BT) k_big_xr(const __grid_constant__ UnevenArgs a, const int* __restrict__ list,
-                                               int nlist, int uni_nA, int uni_nT) {
+                                               int nlist, int uni_nA, int uni_nT, int solved) {
   __shared__ double y[1024];
+  __shared__ int pvs[1024];
   for (int li = blockIdx.x; li < nlist; li += gridDim.x) {
     const Elem E = elem_of(a, list, li, uni_nA, uni_nT);
     const int nA = E.nA, nT = E.nT;
@@ -661,31 +820,41 @@ __global__ void __launch_bounds__(BT) k_big_xr(const __grid_constant__ UnevenArg
     double* t = a.t + E.o[4];
     const bool cm = a.colmajor != 0;
     __syncthreads();
-    for (int i = threadIdx.x; i < nA; i += BT) y[i] = r[i];
-    __syncthreads();
-    if (threadIdx.x == 0)
-      for (int j = 0; j < nA; ++j) {
-        const int p = piv[j];
-        if (p >= 0 && p < nA && p != j) {
-          const double u = y[j];
-          y[j] = y[p];
-          y[p] = u;
-        }
+    if (solved) {  // x_r came with X (the right-hand side's column of the column-block solve)
+      for (int i = threadIdx.x; i < nA; i += BT) y[i] = xr[i];
+      __syncthreads();
+    }
+    if (!solved) {
+      for (int i = threadIdx.x; i < nA; i += BT) {
+        y[i] = r[i];
+        pvs[i] = piv[i];
       }
-    __syncthreads();
-    for (int j = 0; j < nA; ++j) {  // unit lower
-      const double yj = y[j];
-      for (int i = j + 1 + threadIdx.x; i < nA; i += BT) y[i] -= (double)L[(size_t)i * nA + j] * yj;
       __syncthreads();
+      if (threadIdx.x == 0)
+        for (int j = 0; j < nA; ++j) {
+          const int p = pvs[j];
+          if (p >= 0 && p < nA && p != j) {
+            const double u = y[j];
+            y[j] = y[p];
+            y[p] = u;
+          }
+        }
+      __syncthreads();
+      for (int j = 0; j < nA; ++j) {  // unit lower
+        const double yj = y[j];
+        for (int i = j + 1 + threadIdx.x; i < nA; i += BT) y[i] -= (double)L[(size_t)i * nA + j] * yj;
+        __syncthreads();
+      }
+      for (int j = nA - 1; j >= 0; --j) {  // upper
+        if (threadIdx.x == 0) y[j] /= (double)L[(size_t)j * nA + j];
+        __syncthreads();
+        const double yj = y[j];
+        for (int i = threadIdx.x; i < j; i += BT) y[i] -= (double)L[(size_t)i * nA + j] * yj;
+        __syncthreads();
+      }
     }
-    for (int j = nA - 1; j >= 0; --j) {  // upper
-      if (threadIdx.x == 0) y[j] /= (double)L[(size_t)j * nA + j];
-      __syncthreads();
-      const double yj = y[j];
-      for (int i = threadIdx.x; i < j; i += BT) y[i] -= (double)L[(size_t)i * nA + j] * yj;
-      __syncthreads();
-    }
-    for (int i = threadIdx.x; i < nA; i += BT) xr[i] = y[i];
+    if (!solved)
+      for (int i = threadIdx.x; i < nA; i += BT) xr[i] = y[i];
     for (int row = threadIdx.x; row < nT; row += BT) {
       double acc = 0.0;
       for (int c = 0; c < nA; ++c) acc += (double)(cm ? Cm[(size_t)c * nT + row] : Cm[(size_t)row * nA + c]) * y[c];
@@ -746,25 +915,39 @@ cudaError_t condense_big(const UnevenArgs& a, const int* list, int nlist, int un
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  (hfr::count_launch(), k_big_rhs<T><<<grid1, BT, 0, st>>>(a, list, nlist, uni_nA, uni_nT));
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // X = A^{-1} P B: column blocks whole in shared memory when they fit, else the interchange copy
+  // and the blocked triangular solves
+  const size_t ssm = solve_smem<T>(max_nA);
+  const bool fused = ssm <= 227 * 1024 &&
+                     cudaFuncSetAttribute(k_big_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm) ==
+                         cudaSuccess;
+  cudaGetLastError();
+  if (!fused) {
+    (hfr::count_launch(), k_big_rhs<T><<<grid1, BT, 0, st>>>(a, list, nlist, uni_nA, uni_nT));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   const int nblk = (max_nA + NB - 1) / NB;
   constexpr int CH = 65535;  // grid y / z extent per launch
   for (int base = 0; base < nlist; base += CH) {
     const int cnt = nlist - base < CH ? nlist - base : CH;
-    const dim3 gd((max_nT + 127) / 128, cnt);
-    for (int jb = 0; jb < nblk; ++jb) {
-      (hfr::count_launch(), k_big_trsm_diag<T><<<gd, 128, 0, st>>>(a, list, base, cnt, uni_nA, uni_nT, jb, 0));
-      if (jb + 1 < nblk) gemm(base, cnt, max_nA - (jb + 1) * NB, max_nT, 0, jb);
-    }
-    for (int jb = nblk - 1; jb >= 0; --jb) {
-      (hfr::count_launch(), k_big_trsm_diag<T><<<gd, 128, 0, st>>>(a, list, base, cnt, uni_nA, uni_nT, jb, 1));
-      if (jb > 0) gemm(base, cnt, jb * NB, max_nT, 1, jb);
+    if (fused) {
+      const dim3 gv((max_nT + 1 + SC - 1) / SC, cnt);  // and the column of r
+      (hfr::count_launch(), k_big_solve<T><<<gv, BT, ssm, st>>>(a, list, base, cnt, uni_nA, uni_nT));
+    } else {
+      const dim3 gd((max_nT + 127) / 128, cnt);
+      for (int jb = 0; jb < nblk; ++jb) {
+        (hfr::count_launch(), k_big_trsm_diag<T><<<gd, 128, 0, st>>>(a, list, base, cnt, uni_nA, uni_nT, jb, 0));
+        if (jb + 1 < nblk) gemm(base, cnt, max_nA - (jb + 1) * NB, max_nT, 0, jb);
+      }
+      for (int jb = nblk - 1; jb >= 0; --jb) {
+        (hfr::count_launch(), k_big_trsm_diag<T><<<gd, 128, 0, st>>>(a, list, base, cnt, uni_nA, uni_nT, jb, 1));
+        if (jb > 0) gemm(base, cnt, jb * NB, max_nT, 1, jb);
+      }
     }
     gemm(base, cnt, max_nT, max_nT, 2, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  (hfr::count_launch(), k_big_xr<T><<<grid1, BT, 0, st>>>(a, list, nlist, uni_nA, uni_nT));
+  (hfr::count_launch(), k_big_xr<T><<<grid1, BT, 0, st>>>(a, list, nlist, uni_nA, uni_nT, fused ? 1 : 0));
   return cudaGetLastError();
 }
 

@@ -2303,11 +2303,11 @@ __global__ void __launch_bounds__(256) k_class_scatter(const int* __restrict__ l
 }
 
 // the chunk's status into the batch's (its first failing element as a packed element id)
-__global__ void k_class_status(int* cstatus, const int* __restrict__ list, int cnt, int* status) {
+__global__ void k_class_status(int* cstatus, const int* __restrict__ list, int k0, int cnt, int* status) {
   if (cstatus[0] != 0) {
     atomicOr(status, cstatus[0]);
     const int i = cstatus[1];
-    atomicMin(status + 1, (i >= 0 && i < cnt) ? list[i] : -1);
+    atomicMin(status + 1, (i >= 0 && i < cnt) ? (list ? list[i] : k0 + i) : -1);
   }
   cstatus[0] = 0;
   cstatus[1] = 0x7fffffff;
@@ -2316,11 +2316,37 @@ __global__ void k_class_status(int* cstatus, const int* __restrict__ list, int c
 cudaError_t launch_condense_class(const int* list, int count, int nA, int nT, const long long* off, const void* A,
                                   const void* B, const void* C, const void* D, const double* r, const double* s,
                                   void* LU, int* piv, void* XB, double* xr, void* S, double* t, int* status,
-                                  void* scratch, int cap, int tc_mode, cudaStream_t st) {
+                                  void* scratch, int cap, int tc_mode, cudaStream_t st, int contig_k0,
+                                  const long long* contig_off) {
   if (count <= 0) return cudaSuccess;
-  if (cap <= 0 || !condense_feasible(4, nA, nT)) return cudaErrorInvalidValue;
-  const ClassScratch cs = class_scratch(scratch, nA, nT, cap);
+  if (!condense_feasible(4, nA, nT)) return cudaErrorInvalidValue;
   cudaError_t e;
+  if (contig_k0 >= 0) {  // consecutive elements of one shape: uniform strides, condensed in place
+    const long long* o = contig_off;
+    CondArgs ca;
+    ca.Eim = count;
+    ca.nA = nA;
+    ca.nT = nT;
+    ca.A = static_cast<const float*>(A) + o[0];
+    ca.B = static_cast<const float*>(B) + o[1];
+    ca.C = static_cast<const float*>(C) + o[1];
+    ca.D = static_cast<const float*>(D) + o[2];
+    ca.r = r + o[3];
+    ca.s = s + o[4];
+    ca.LU = static_cast<float*>(LU) + o[0];
+    ca.piv = piv + o[3];
+    ca.XB = static_cast<float*>(XB) + o[1];
+    ca.xr = xr + o[3];
+    ca.S = static_cast<float*>(S) + o[2];
+    ca.t = t + o[4];
+    ca.status = reinterpret_cast<int*>(scratch);  // the scratch buffer's leading status words
+    ca.tc_mode = tc_mode;
+    if ((e = launch_condense(4, ca, st)) != cudaSuccess) return e;
+    (hfr::count_launch(), k_class_status<<<1, 1, 0, st>>>(ca.status, nullptr, contig_k0, count, status));
+    return cudaGetLastError();
+  }
+  if (cap <= 0) return cudaErrorInvalidValue;
+  const ClassScratch cs = class_scratch(scratch, nA, nT, cap);
   for (int base = 0; base < count; base += cap) {
     const int cnt = count - base < cap ? count - base : cap;
     (hfr::count_launch(), k_class_gather<<<cnt, 256, 0, st>>>(list + base, off, nA, nT, (const float*)A,
@@ -2348,7 +2374,7 @@ cudaError_t launch_condense_class(const int* list, int count, int nA, int nT, co
     if ((e = launch_condense(4, ca, st)) != cudaSuccess) return e;
     (hfr::count_launch(), k_class_scatter<<<cnt, 256, 0, st>>>(list + base, off, nA, nT, cs, (float*)LU, piv,
                                                                 (float*)XB, xr, (float*)S, t));
-    (hfr::count_launch(), k_class_status<<<1, 1, 0, st>>>(cs.status, list + base, cnt, status));
+    (hfr::count_launch(), k_class_status<<<1, 1, 0, st>>>(cs.status, list + base, 0, cnt, status));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -461,7 +461,8 @@ __global__ void k_gen_initial_trace(size_t npts, int nv, const long long* __rest
   const size_t pt = i / nv;
   const int v = (int)(i % nv);
   const long long c0 = gptr[pt], c1 = gptr[pt + 1];
-  const long long nview = (long long)a.nface * a.E * a.fs;
+  const long long nview = (long long)a.nface * a.E * a.fs;  // the bound of the checked build
+  (void)nview;
   const long long i0 = FR_IDX(gidx[c0], nview, 6);
   const int kf = kind[i0 / a.fs];
   double x;
@@ -1135,10 +1136,10 @@ __global__ void __launch_bounds__(GP_THREADS) k_gen_precond_build(int ntrace, in
     __syncthreads();
     for (int x = tid; x < bs; x += GP_THREADS) W[c * bs + x] = (x == c ? T(1) : W[c * bs + x]) * inv;
     __syncthreads();
-    for (int i = tid; i < bs * bs; i += GP_THREADS) {
-      const int r = i / bs, x = i % bs;
+    for (int r = tid >> 5; r < bs; r += GP_THREADS / 32) {  // one warp per row, lanes along it
       if (r == c) continue;
-      W[i] = (x == c ? T(0) : W[i]) - L[r] * W[c * bs + x];
+      const T l = L[r];
+      for (int x = tid & 31; x < bs; x += 32) W[r * bs + x] = (x == c ? T(0) : W[r * bs + x]) - l * W[c * bs + x];
     }
     __syncthreads();
   }
@@ -1201,6 +1202,39 @@ __global__ void k_gen_precond_apply(int ntrace, int nv, const int* __restrict__ 
       y[o + row] = double(acc);
       if (y32) y32[o + row] = float(acc);
     }
+  }
+}
+
+// the same for blocks of at most 8 values (EFR node blocks, bs = nv): one thread per trace unit
+template <typename T>
+__global__ void k_gen_precond_apply_small(int ntrace, int nv, const int* __restrict__ tpts,
+                                          const long long* __restrict__ toff, const long long* __restrict__ poff,
+                                          const T* __restrict__ Pinv, double* __restrict__ x, double* __restrict__ y,
+                                          const int* gate, int gj, const double* inv_h, float* __restrict__ y32) {
+  if (gate && *gate >= 0 && gj >= *gate) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntrace) return;
+  const int bs = tpts[t] * nv;
+  const long long o = toff[t];
+  const T* P = Pinv + poff[t];
+  const double sc = inv_h ? *inv_h : 1.0;
+  T xl[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    double v = c < bs ? x[o + c] : 0.0;
+    if (inv_h && c < bs) {
+      v *= sc;
+      x[o + c] = v;
+    }
+    xl[c] = T(v);
+  }
+  for (int r = 0; r < bs; ++r) {
+    T acc = T(0);
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      if (c < bs) acc += P[(size_t)r * bs + c] * xl[c];
+    y[o + r] = double(acc);
+    if (y32) y32[o + r] = float(acc);
   }
 }
 
@@ -1868,6 +1902,15 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
       tc.nA = c.first.first;
       tc.nT = c.first.second;
       tc.count = (int)c.second.size();
+      const int kf = c.second.front(), kl = c.second.back();
+      if (kl - kf + 1 == tc.count) {  // increasing ids: consecutive exactly when the span matches
+        tc.k0 = kf;
+        tc.off0[0] = offA[kf];
+        tc.off0[1] = offB[kf];
+        tc.off0[2] = offD[kf];
+        tc.off0[3] = offr[kf];
+        tc.off0[4] = offs[kf];
+      }
       tc.list = galloc<int>(g, c.second.size(), &rc);
       if (rc != FR_OK || cudaMemcpyAsync(tc.list, c.second.data(), c.second.size() * sizeof(int),
                                          cudaMemcpyHostToDevice, st) != cudaSuccess) {
@@ -1875,9 +1918,10 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
         return rc != FR_OK ? rc : FR_ERR_CUDA;
       }
       g->tc_classes.push_back(tc);
-      g->ccap = std::max(g->ccap, std::min(tc.count, CLASS_CAP));
+      if (tc.k0 < 0) g->ccap = std::max(g->ccap, std::min(tc.count, CLASS_CAP));
     }
-    for (auto& tc : g->tc_classes) sbytes = std::max(sbytes, class_scratch_bytes(tc.nA, tc.nT, g->ccap));
+    for (auto& tc : g->tc_classes)
+      sbytes = std::max(sbytes, tc.k0 < 0 ? class_scratch_bytes(tc.nA, tc.nT, g->ccap) : (size_t)64);
     if (sbytes) {
       g->cscratch = galloc<unsigned char>(g, sbytes, &rc);
       if (rc != FR_OK || class_scratch_init_status(g->cscratch, st) != cudaSuccess) {
@@ -2096,7 +2140,8 @@ static int condense_impl(GenCtx* g) {
   int ph = pbeg(g, 2);
   for (const auto& tc : g->tc_classes)
     GCK(launch_condense_class(tc.list, tc.count, tc.nA, tc.nT, g->udev.off, g->A, g->B, g->C, g->D, g->r, g->s, g->LU,
-                              g->piv, g->XB, g->xr, g->S, g->te, g->status, g->cscratch, g->ccap, 2, g->st));
+                              g->piv, g->XB, g->xr, g->S, g->te, g->status, g->cscratch, g->ccap, 2, g->st, tc.k0,
+                              tc.off0));
   GCK(launch_condense_uneven_dev(g->pb, g->udev, g->A, g->B, g->C, g->D, g->r, g->s, g->LU, g->piv, g->XB, g->xr,
                                  g->S, g->te, g->status, g->st));
   pend(g, ph);
@@ -2179,6 +2224,17 @@ static void cb_gmatvec_g(void* c, const GmresState* st, int j, const double* x, 
 }
 static void cb_precond_g(void* c, const GmresState* st, int j, double* x, double* y, float* y32, cudaStream_t s) {
   GenCtx* g = (GenCtx*)c;
+  if (g->bsmax <= 8) {  // small blocks (EFR nodes): one thread per block
+    if (g->pb == 8)
+      (count_launch(), k_gen_precond_apply_small<double><<<nb256(g->ntrace), 256, 0, s>>>(
+           g->ntrace, g->nv, g->tpts, g->toff, g->poff, (const double*)g->Pinv, x, y, &st->kdone, j,
+           j > 0 ? &st->inv_hn : nullptr, y32));
+    else
+      (count_launch(), k_gen_precond_apply_small<float><<<nb256(g->ntrace), 256, 0, s>>>(
+           g->ntrace, g->nv, g->tpts, g->toff, g->poff, (const float*)g->Pinv, x, y, &st->kdone, j,
+           j > 0 ? &st->inv_hn : nullptr, y32));
+    return;
+  }
   if (g->pb == 8)
     (count_launch(), k_gen_precond_apply<double><<<nbw(g->ntrace), 256, 0, s>>>(
          g->ntrace, g->nv, g->tpts, g->toff, g->poff, (const double*)g->Pinv, x, y, &st->kdone, j,

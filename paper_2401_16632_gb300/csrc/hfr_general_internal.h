@@ -117,7 +117,9 @@ struct GenCtx {
   // through a contiguous scratch batch (the other elements by the uneven launch)
   struct TcClass {
     int nA, nT, count;
-    int* list;  // device: compact implicit ids of the class
+    int* list;          // device: compact implicit ids of the class
+    int k0 = -1;        // >= 0: the class is the consecutive elements k0.. (condensed in place)
+    long long off0[5];  // host: the offsets of element k0 (A, B/C, D, nA-vector, nT-vector)
   };
   std::vector<TcClass> tc_classes;
   void* cscratch = nullptr;

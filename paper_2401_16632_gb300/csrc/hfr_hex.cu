@@ -628,13 +628,16 @@ __global__ void __launch_bounds__(HJT, 1) k_hex_jacobian(const __grid_constant__
             cw.dqf[jj][c2] = s;
           }
         }
-        // flux tangents at the solution points
+        // flux tangents at the solution points (the gradient tangent vanishes off the seed's lines:
+        // the pointwise Jacobians are read only where a tangent is nonzero)
         for (int it = lane; it < ns * 3 * HNV; it += 32) {
           const int i = it / (3 * HNV), r = (it / HNV) % 3, v = it % HNV;
           T s = T(0);
-          if (visc)
-            s = J.KQ[i][r][0][v][v0] * cw.dQ[i][0] + J.KQ[i][r][1][v][v0] * cw.dQ[i][1] +
-                J.KQ[i][r][2][v][v0] * cw.dQ[i][2];
+          if (visc) {
+            const T q0 = cw.dQ[i][0], q1 = cw.dQ[i][1], q2 = cw.dQ[i][2];
+            if (q0 != T(0) || q1 != T(0) || q2 != T(0))
+              s = J.KQ[i][r][0][v][v0] * q0 + J.KQ[i][r][1][v][v0] * q1 + J.KQ[i][r][2][v][v0] * q2;
+          }
           if (vol && i == sp) s += J.KU[i][r][v][v0];
           cw.dFt[i][r][v] = s;
         }
@@ -644,13 +647,23 @@ __global__ void __launch_bounds__(HJT, 1) k_hex_jacobian(const __grid_constant__
           T du = T(0);  // face state tangent: l_sigma[a_r(sp)] on the face point of sp's r-line
           if (vol && hfacept(sp, r, n) == m) du = ((f & 1) ? w.lp : w.lm)[hcoord(sp, r, n)];
           const T dh = (!vol && f == f0 && m == m0) ? T(1) : T(0);
-          T s = J.GU[jj][v][v0] * du + J.GH[jj][v][v0] * dh;
-          T sr = J.RU[jj][v][v0] * du + J.RH[jj][v][v0] * dh;
+          T s = T(0), sr = T(0);
+          if (du != T(0)) {
+            s += J.GU[jj][v][v0] * du;
+            sr += J.RU[jj][v][v0] * du;
+          }
+          if (dh != T(0)) {
+            s += J.GH[jj][v][v0] * dh;
+            sr += J.RH[jj][v][v0] * dh;
+          }
           if (visc) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-              s += J.GQ[jj][c][v][v0] * cw.dqf[jj][c];
-              sr += J.RQ[jj][c][v][v0] * cw.dqf[jj][c];
+              const T dq = cw.dqf[jj][c];
+              if (dq != T(0)) {
+                s += J.GQ[jj][c][v][v0] * dq;
+                sr += J.RQ[jj][c][v][v0] * dq;
+              }
             }
           }
           cw.dFn[jj][v] = s;

@@ -158,13 +158,16 @@ int uneven_tables(int prec_bytes, int n, const int* nA, const int* nT, UnevenTab
 // offsets as uploaded with its tables) through the fixed-shape kernels of that shape, in chunks of
 // cap elements staged in scratch (class_scratch_bytes; one buffer may serve every shape: its
 // leading status words, set once by class_scratch_init_status, are where every shape expects
-// them).  The chunk's failures go to status with packed element ids.
+// them).  The chunk's failures go to status with packed element ids.  contig_k0 >= 0: the class is
+// the consecutive elements contig_k0.. (uniform strides from the host offsets contig_off of its
+// first element: A, B/C, D, nA-vector, nT-vector), condensed in place without the scratch batch.
 size_t class_scratch_bytes(int nA, int nT, int cap);
 cudaError_t class_scratch_init_status(void* scratch, cudaStream_t st);
 cudaError_t launch_condense_class(const int* list, int count, int nA, int nT, const long long* off, const void* A,
                                   const void* B, const void* C, const void* D, const double* r, const double* s,
                                   void* LU, int* piv, void* XB, double* xr, void* S, double* t, int* status,
-                                  void* scratch, int cap, int tc_mode, cudaStream_t st);
+                                  void* scratch, int cap, int tc_mode, cudaStream_t st, int contig_k0 = -1,
+                                  const long long* contig_off = nullptr);
 size_t uneven_dev_bytes(const UnevenTables& tb);
 cudaError_t uneven_upload(const UnevenTables& tb, void* dbuf, UnevenDev* dv, cudaStream_t st);
 cudaError_t launch_condense_uneven_dev(int prec_bytes, const UnevenDev& dv, const void* A, const void* B, const void* C,
