@@ -289,6 +289,26 @@ template <typename T>
 size_t solve_smem(int max_nA) {
   return ((size_t)max_nA * SC + (size_t)max_nA * SP) * sizeof(T) + (size_t)max_nA * sizeof(int);
 }
+// Lp[r][j] = L[r0 + r][p0 + j] for r < nrows, j < w (zero for w <= j < SP); SU loads per thread in
+// flight before their stores
+template <typename T>
+__device__ __forceinline__ void solve_stage_panel(T* Lp, const T* L, int nA, int r0, int nrows, int p0, int w,
+                                                  int tid) {
+  constexpr int SU = 8;
+  const int cnt = nrows * SP;
+  for (int b = tid; b < cnt; b += BT * SU) {
+    T v[SU];
+#pragma unroll
+    for (int u = 0; u < SU; ++u) {
+      const int idx = b + BT * u, r = idx / SP, j = idx % SP;
+      v[u] = (idx < cnt && j < w) ? L[(size_t)(r0 + r) * nA + p0 + j] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < SU; ++u)
+      if (b + BT * u < cnt) Lp[b + BT * u] = v[u];
+  }
+}
+
 // Xs rows [ra, rb) -= (factor panel rows, staged at Lp row r - lbase) x (solved panel rows of Xs,
 // p0 .. p0 + w - 1): eight rows per warp pass, four pivots per step (one 16-byte broadcast of the
 // factor per row, four values of the solved rows per lane); the factor panel is zero beyond w
@@ -364,18 +384,28 @@ __global__ void __launch_bounds__(BT, 2) k_big_solve(const __grid_constant__ Une
   const int c = c0 + lane;
   const bool live = c < nT;
   const double* rv = a.r + E.o[3];
-  for (int i = wid; i < nA; i += NW) {
-    const int src = perm[i];
-    Xs[i * SC + lane] = live ? (cm ? B[(size_t)c * nA + src] : B[(size_t)src * nT + c]) : (c == nT ? T(rv[src]) : T(0));
+  // global loads in batches of SU per thread, all in flight before their shared-memory stores
+  constexpr int SU = 8;
+  for (int i0 = wid; i0 < nA; i0 += NW * SU) {
+    T v[SU];
+#pragma unroll
+    for (int u = 0; u < SU; ++u) {
+      const int i = i0 + NW * u;
+      v[u] = T(0);
+      if (i < nA) {
+        const int src = perm[i];
+        v[u] = live ? (cm ? B[(size_t)c * nA + src] : B[(size_t)src * nT + c]) : (c == nT ? T(rv[src]) : T(0));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < SU; ++u)
+      if (i0 + NW * u < nA) Xs[(i0 + NW * u) * SC + lane] = v[u];
   }
   // ---- forward: unit lower factor, panels top to bottom
   for (int p0 = 0; p0 < nA; p0 += SP) {
     const int w = min(SP, nA - p0);
     __syncthreads();  // the previous panel's readers are done
-    for (int idx = tid; idx < (nA - p0) * SP; idx += BT) {
-      const int r = idx / SP, j = idx % SP;
-      Lp[r * SP + j] = j < w ? L[(size_t)(p0 + r) * nA + p0 + j] : T(0);
-    }
+    solve_stage_panel<T>(Lp, L, nA, p0, nA - p0, p0, w, tid);
     __syncthreads();
     if (wid == 0) {  // in-panel solve: one warp, lane = column, the panel's rows in registers
       T x[SP];
@@ -398,10 +428,7 @@ __global__ void __launch_bounds__(BT, 2) k_big_solve(const __grid_constant__ Une
   for (int pb = np - 1; pb >= 0; --pb) {
     const int p0 = pb * SP, w = min(SP, nA - p0);
     __syncthreads();
-    for (int idx = tid; idx < (p0 + w) * SP; idx += BT) {
-      const int r = idx / SP, j = idx % SP;
-      Lp[r * SP + j] = j < w ? L[(size_t)r * nA + p0 + j] : T(0);
-    }
+    solve_stage_panel<T>(Lp, L, nA, 0, p0 + w, p0, w, tid);
     __syncthreads();
     if (wid == 0) {
       T x[SP];

@@ -783,70 +783,72 @@ __global__ void __launch_bounds__(JT) k_gen_jacobian(const __grid_constant__ Phy
         rem -= w.nf[f];
       }
     }
-    for (int v0 = 0; v0 < NV; ++v0) {
-      // face node and face point tangents of the state, trace tangent
+    // the tangents of the linear chain (face values, common values, gradients) depend on the seed
+    // point only: formed once for its NV columns
+    // face node and face point tangents of the state, trace tangent
+    for (int jj = lane; jj < GF; jj += 32) {
+      const int f = jj / GN, b = jj % GN, r = f >> 1;
+      T d = T(0);
+      if (vol && b < n) {
+        const T* l = (f & 1) ? w.lp : w.lm;
+        if (r == 0 && b == b0) d = l[a0];
+        if (r == 1 && b == a0) d = l[b0];
+      }
+      cw.dUfn[jj] = d;
+      cw.dubp[jj] = (!vol && f == f0 && b == q0) ? T(1) : T(0);
+    }
+    __syncwarp();
+    for (int jj = lane; jj < GF; jj += 32) {
+      const int f = jj / GN, q = jj % GN;
+      T s = T(0);
+      if (q < w.nf[f])
+        for (int b = 0; b < n; ++b) s += w.Tf[f][q][b] * cw.dUfn[f * GN + b];
+      cw.dUfp[jj] = s;
+    }
+    __syncwarp();
+    if (visc) {
       for (int jj = lane; jj < GF; jj += 32) {
-        const int f = jj / GN, b = jj % GN, r = f >> 1;
-        T d = T(0);
-        if (vol && b < n) {
-          const T* l = (f & 1) ? w.lp : w.lm;
-          if (r == 0 && b == b0) d = l[a0];
-          if (r == 1 && b == a0) d = l[b0];
+        const int f = jj / GN, b = jj % GN;
+        T s = T(0);
+        if (b < n) {
+          s = cw.dUfn[jj];
+          for (int q = 0; q < w.nf[f]; ++q) s += w.Pf[f][b][q] * (cw.dubp[f * GN + q] - cw.dUfp[f * GN + q]);
         }
-        cw.dUfn[jj] = d;
-        cw.dubp[jj] = (!vol && f == f0 && b == q0) ? T(1) : T(0);
+        cw.dubn[jj] = s;
       }
       __syncwarp();
-      for (int jj = lane; jj < GF; jj += 32) {
-        const int f = jj / GN, q = jj % GN;
+      for (int i = lane; i < ns; i += 32) {
+        const int ai = i % n, bi = i / n;
+        T q0v = w.dgL[ai] * cw.dubn[0 * GN + bi] + w.dgR[ai] * cw.dubn[1 * GN + bi];
+        T q1v = w.dgL[bi] * cw.dubn[2 * GN + ai] + w.dgR[bi] * cw.dubn[3 * GN + ai];
+        if (vol && bi == b0) q0v += w.M[ai][a0];
+        if (vol && ai == a0) q1v += w.M[bi][b0];
+        cw.dQ[i][0] = q0v;
+        cw.dQ[i][1] = q1v;
+        cw.dq[i][0] = w.iJ[i] * (w.Sm[i][0][0] * q0v + w.Sm[i][1][0] * q1v);
+        cw.dq[i][1] = w.iJ[i] * (w.Sm[i][0][1] * q0v + w.Sm[i][1][1] * q1v);
+      }
+      __syncwarp();
+      for (int it = lane; it < GF * 2; it += 32) {
+        const int jj = it >> 1, c2 = it & 1, f = jj / GN, b = jj % GN, r = f >> 1;
+        T s = T(0);
+        if (b < n) {
+          const T* l = (f & 1) ? w.lp : w.lm;
+          for (int c = 0; c < n; ++c) s += l[c] * cw.dq[gline(r, b, c, n)][c2];
+        }
+        cw.dqfn[jj][c2] = s;
+      }
+      __syncwarp();
+      for (int it = lane; it < GF * 2; it += 32) {
+        const int jj = it >> 1, c2 = it & 1, f = jj / GN, q = jj % GN;
         T s = T(0);
         if (q < w.nf[f])
-          for (int b = 0; b < n; ++b) s += w.Tf[f][q][b] * cw.dUfn[f * GN + b];
-        cw.dUfp[jj] = s;
+          for (int b = 0; b < n; ++b) s += w.Tf[f][q][b] * cw.dqfn[f * GN + b][c2];
+        cw.dqfp[jj][c2] = s;
       }
-      __syncwarp();
-      if (visc) {
-        for (int jj = lane; jj < GF; jj += 32) {
-          const int f = jj / GN, b = jj % GN;
-          T s = T(0);
-          if (b < n) {
-            s = cw.dUfn[jj];
-            for (int q = 0; q < w.nf[f]; ++q) s += w.Pf[f][b][q] * (cw.dubp[f * GN + q] - cw.dUfp[f * GN + q]);
-          }
-          cw.dubn[jj] = s;
-        }
-        __syncwarp();
-        for (int i = lane; i < ns; i += 32) {
-          const int ai = i % n, bi = i / n;
-          T q0v = w.dgL[ai] * cw.dubn[0 * GN + bi] + w.dgR[ai] * cw.dubn[1 * GN + bi];
-          T q1v = w.dgL[bi] * cw.dubn[2 * GN + ai] + w.dgR[bi] * cw.dubn[3 * GN + ai];
-          if (vol && bi == b0) q0v += w.M[ai][a0];
-          if (vol && ai == a0) q1v += w.M[bi][b0];
-          cw.dQ[i][0] = q0v;
-          cw.dQ[i][1] = q1v;
-          cw.dq[i][0] = w.iJ[i] * (w.Sm[i][0][0] * q0v + w.Sm[i][1][0] * q1v);
-          cw.dq[i][1] = w.iJ[i] * (w.Sm[i][0][1] * q0v + w.Sm[i][1][1] * q1v);
-        }
-        __syncwarp();
-        for (int it = lane; it < GF * 2; it += 32) {
-          const int jj = it >> 1, c2 = it & 1, f = jj / GN, b = jj % GN, r = f >> 1;
-          T s = T(0);
-          if (b < n) {
-            const T* l = (f & 1) ? w.lp : w.lm;
-            for (int c = 0; c < n; ++c) s += l[c] * cw.dq[gline(r, b, c, n)][c2];
-          }
-          cw.dqfn[jj][c2] = s;
-        }
-        __syncwarp();
-        for (int it = lane; it < GF * 2; it += 32) {
-          const int jj = it >> 1, c2 = it & 1, f = jj / GN, q = jj % GN;
-          T s = T(0);
-          if (q < w.nf[f])
-            for (int b = 0; b < n; ++b) s += w.Tf[f][q][b] * cw.dqfn[f * GN + b][c2];
-          cw.dqfp[jj][c2] = s;
-        }
-      }
-      __syncwarp();
+    }
+    __syncwarp();
+    for (int v0 = 0; v0 < NV; ++v0) {
       // flux tangents at the solution points
       for (int it = lane; it < ns * 2 * NV; it += 32) {
         const int i = it / (2 * NV), r = (it / NV) % 2, v = it % NV;

@@ -599,35 +599,37 @@ __global__ void __launch_bounds__(HJT, 1) k_hex_jacobian(const __grid_constant__
         }
       }
       const int r0 = vol ? -1 : f0 >> 1;
-      for (int v0 = 0; v0 < HNV; ++v0) {
-        // reference and physical gradient tangents (the seed's lines only)
-        if (visc) {
-          for (int i = lane; i < ns; i += 32) {
-            T Q[3];
+      // the gradient tangents depend on the seed point only: formed once for its HNV columns
+      // reference and physical gradient tangents (the seed's lines only)
+      if (visc) {
+        for (int i = lane; i < ns; i += 32) {
+          T Q[3];
 #pragma unroll
-            for (int r = 0; r < 3; ++r) {
-              T s = T(0);
-              if (vol) {  // on sp's r-line: M[a_r(i)][a_r(sp)]
-                if (hfacept(i, r, n) == hfacept(sp, r, n)) s = w.M[hcoord(i, r, n)][hcoord(sp, r, n)];
-              } else if (r == r0 && hfacept(i, r, n) == m0) {
-                s = (f0 & 1) ? w.dgR[hcoord(i, r, n)] : w.dgL[hcoord(i, r, n)];
-              }
-              Q[r] = s;
-              cw.dQ[i][r] = s;
-            }
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-              cw.dq[i][c] = w.iJ[i] * (w.Sm[i][0][c] * Q[0] + w.Sm[i][1][c] * Q[1] + w.Sm[i][2][c] * Q[2]);
-          }
-          __syncwarp();
-          for (int it = lane; it < 6 * nf * 3; it += 32) {
-            const int jj = it / 3, c2 = it % 3, f = jj / nf, m = jj % nf, r = f >> 1;
-            const T* l = (f & 1) ? w.lp : w.lm;
+          for (int r = 0; r < 3; ++r) {
             T s = T(0);
-            for (int c = 0; c < n; ++c) s += l[c] * cw.dq[hline(r, m, c, n)][c2];
-            cw.dqf[jj][c2] = s;
+            if (vol) {  // on sp's r-line: M[a_r(i)][a_r(sp)]
+              if (hfacept(i, r, n) == hfacept(sp, r, n)) s = w.M[hcoord(i, r, n)][hcoord(sp, r, n)];
+            } else if (r == r0 && hfacept(i, r, n) == m0) {
+              s = (f0 & 1) ? w.dgR[hcoord(i, r, n)] : w.dgL[hcoord(i, r, n)];
+            }
+            Q[r] = s;
+            cw.dQ[i][r] = s;
           }
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            cw.dq[i][c] = w.iJ[i] * (w.Sm[i][0][c] * Q[0] + w.Sm[i][1][c] * Q[1] + w.Sm[i][2][c] * Q[2]);
         }
+        __syncwarp();
+        for (int it = lane; it < 6 * nf * 3; it += 32) {
+          const int jj = it / 3, c2 = it % 3, f = jj / nf, m = jj % nf, r = f >> 1;
+          const T* l = (f & 1) ? w.lp : w.lm;
+          T s = T(0);
+          for (int c = 0; c < n; ++c) s += l[c] * cw.dq[hline(r, m, c, n)][c2];
+          cw.dqf[jj][c2] = s;
+        }
+      }
+      __syncwarp();
+      for (int v0 = 0; v0 < HNV; ++v0) {
         // flux tangents at the solution points (the gradient tangent vanishes off the seed's lines:
         // the pointwise Jacobians are read only where a tangent is nonzero)
         for (int it = lane; it < ns * 3 * HNV; it += 32) {
