@@ -2064,14 +2064,20 @@ bool uneven_fits_smem(int prec_bytes, int nA, int nT) {
 }
 
 // largest nA of an uneven batch that goes to the shared-memory Gauss-Jordan bundles; larger blocks
-// take the blocked LU with batched GEMMs.  Measured on 10 000 FP32 blocks of nA = 144, nT = 96
-// (p = 5): 40.3 ms in the bundles (one element per CTA, shared-memory bound rank-1 steps), 26.4 ms
-// blocked.  A build flag, for timing the two forms against each other.
+// take the blocked LU with the column-block solve and batched GEMMs.  Measured on 10 000 FP32
+// blocks per shape (call wall time): nA = 144, nT = 96: 40.3 ms in the bundles (shared-memory
+// bound rank-1 steps), 26.0 ms blocked; nA = 100, nT = 80: 23.0 / 18.6 ms; nA = 64, nT = 64: 13.4
+// / 13.2 ms (even).  FP64 blocks keep the bundles up to nA = 128 (both forms on the FP64 pipe).
+// Build flags, for timing the two forms against each other.
 #ifndef HFR_UNEVEN_SMEM_MAX_NA
-#define HFR_UNEVEN_SMEM_MAX_NA 128
+#define HFR_UNEVEN_SMEM_MAX_NA 64
+#endif
+#ifndef HFR_UNEVEN_SMEM_MAX_NA_FP64
+#define HFR_UNEVEN_SMEM_MAX_NA_FP64 128
 #endif
 static bool uneven_route_smem(int prec_bytes, int nA, int nT) {
-  return uneven_fits_smem(prec_bytes, nA, nT) && nA <= HFR_UNEVEN_SMEM_MAX_NA;
+  return uneven_fits_smem(prec_bytes, nA, nT) &&
+         nA <= (prec_bytes == 8 ? HFR_UNEVEN_SMEM_MAX_NA_FP64 : HFR_UNEVEN_SMEM_MAX_NA);
 }
 
 // Host tables of an uneven launch: per element offsets (A, B/C, D, nA-, nT-vectors), shapes, the
