@@ -463,8 +463,10 @@ def general_leg(pkg, torch, dev, l2buf, name, steps=(3, 2), warmup=(2, 1), peaks
     alg = k_its * float(np.sum(nT * nT) * 4 + np.sum(nT) * 2 * 8) + sum((k + 2) * m["nh"] * 8 for k in range(1, k_its + 1))
     g_a = alg / (gms / max(gcnt, 1) * 1e-3) / 1e9
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    cond_kernel = ("k_big_lu_panel + k_big_trsm_diag + k_big_gemm + k_big_xr (blocked LU, batched GEMMs)"
-                   if name == "channel3d" else "k_condense_uneven<float> (shared-memory Gauss-Jordan bundles)")
+    cond_kernel = ("k_big_lu_panel + k_big_gemm (blocked LU), k_big_solve (column-block solve), k_big_gemm_tc "
+                   "(S on tcgen05), k_big_xr" if name == "channel3d" else
+                   "k_inverse_tc + k_products_tc (tensor-core shape classes), k_condense_uneven<float> (shared-memory "
+                   "Gauss-Jordan bundles, nA <= 64), the blocked-LU kernels (larger blocks)")
     out.update({
         "value": w.dofs_implicit / (m["graph_ms"] * 1e-3), "unit": "implicit-stage DOF/s", "ms_per_step": m["graph_ms"],
         "stage_execution": "one CUDA graph per stage (mixed); the FP64 path and the per-phase times: stream form",

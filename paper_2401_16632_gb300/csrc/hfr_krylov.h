@@ -6,7 +6,7 @@
 namespace hfr {
 
 constexpr int GM_MAXM = 64;
-constexpr int GM_NBLK = 304;  // two blocks per SM for the vector passes
+constexpr int GM_NBLK = 608;  // four blocks per SM for the vector passes
 
 // scalars first: the host reads only the head (sizeof(GmresHead)) between iterations
 struct GmresHead {

@@ -189,3 +189,37 @@ def test_efr_graph_stage_equals_stream_stage():
         ctx.close()
     assert out[0][2:] == out[1][2:]
     assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+
+
+# ------------------------------------------------------------------ full size (vortex256 mesh)
+def test_full_size_efr_free_stream_and_mixed_against_fp64():
+    """The EFR trace on the 256 x 256 p = 4 vortex mesh (458 752 trace nodes): a uniform state
+    with its initial trace is steady (R and g vanish to rounding over all 65 536 elements), and the
+    implicit stage converges on the FP64 and the mixed-precision path to the same state, to what
+    the Newton tolerance fixes."""
+    w = make_config("vortex256")
+    ctx = pkg.Context(w.mesh, w.physics, precision=pkg.FR_PREC_FP64, tableau=pkg.FR_TAB_SDIRK2,
+                      trace_kind=pkg.FR_TRACE_EFR)
+    assert ctx.general and ctx.info.ntrace == 458752
+    ufs = np.array([1.0, 0.5, 0.0, 1.0 / (1.4 * 0.4) + 0.125])
+    U = torch.tensor(np.tile(ufs, int(ctx.info.state_values) // 4), device=DEV)
+    uh = ctx.hfr_initial_trace(U)
+    R, g = ctx.fr_residual(U, uh)
+    assert R.abs().max().item() < 1e-10
+    assert g.abs().max().item() < 1e-12
+    ctx.close()
+    out = {}
+    for label, prec in (("fp64", pkg.FR_PREC_FP64), ("mixed", pkg.FR_PREC_FP32)):
+        ctx = pkg.Context(w.mesh, w.physics, precision=prec, tableau=pkg.FR_TAB_SDIRK2, trace_kind=pkg.FR_TRACE_EFR)
+        u_n = torch.tensor(w.u0.reshape(-1), device=DEV)
+        uh = ctx.hfr_initial_trace(u_n)
+        R_hist = ctx.empty(3, *ctx.state_shape)
+        us = ctx.empty(*ctx.state_shape)
+        ctx.imex_stage(0, w.dt, u_n, us, uh, R_hist)
+        st = ctx.imex_stage(1, w.dt, u_n, us, uh, R_hist, newton_tol=1e-11, newton_maxit=30, gmres_rtol=1e-6,
+                            gmres_maxit=5000)
+        assert st["converged"], (label, st)
+        out[label] = (us - u_n).cpu().numpy()
+        ctx.close()
+    inc = np.abs(out["fp64"]).max()
+    assert np.abs(out["mixed"] - out["fp64"]).max() < 1e-9 * inc
