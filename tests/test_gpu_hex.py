@@ -212,6 +212,30 @@ def _channel():
     return _CH["w"]
 
 
+@pytest.mark.parametrize("prec", [pkg.FR_PREC_FP64, pkg.FR_PREC_FP32])
+def test_hex_graph_stage_equals_stream_stage(prec):
+    """The hexahedral stage as one CUDA graph gives the stream stage's result bit for bit, with the
+    same Newton and GMRES iteration counts."""
+    mesh, U = _case("channel_p3")
+    out = []
+    for graph in (False, True):
+        ctx = pkg.Context(mesh, NS3, precision=prec, tableau=pkg.FR_TAB_SDIRK2)
+        if graph:
+            ctx.imex_stage_set_graph(True)
+        u_n = torch.tensor(U.reshape(-1), device=DEV)
+        uh = ctx.hfr_initial_trace(u_n)
+        R_hist = ctx.empty(3, *ctx.state_shape)
+        us = ctx.empty(*ctx.state_shape)
+        ctx.imex_stage(0, 0.01, u_n, us, uh, R_hist)
+        st = ctx.imex_stage(1, 0.01, u_n, us, uh, R_hist, newton_tol=1e-12, newton_maxit=30, gmres_rtol=1e-10,
+                            gmres_maxit=5000)
+        assert st["converged"]
+        out.append((us.clone(), uh.clone(), st["newton_iterations"], st["gmres_iterations"]))
+        ctx.close()
+    assert out[0][2:] == out[1][2:]
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+
+
 def test_full_size_channel_rest_state_is_steady():
     w = _channel()
     ctx = pkg.Context(w.mesh, w.physics, precision=pkg.FR_PREC_FP32, tableau=pkg.FR_TAB_SDIRK2)
