@@ -388,9 +388,12 @@ int hfr_autotune(fr_ctx* ctx, const double* u, const double* uhat, const double*
  * device kernels, so that the host launches the stage once and reads its counters once.  The
  * first call with a given (stage, dt, buffers, tolerances, limits, refine) captures and
  * instantiates the graph; later calls with the same arguments replay it.  Results equal the
- * stream path's.  Requires implicit elements, FR_JAC_EVERY_NEWTON and (with a trace)
- * FR_GMRES_FUSED: FR_ERR_UNSUPPORTED otherwise.  Per-phase profiling (fr_profile_*) sees no
- * phases of a graph stage. */
+ * stream path's.  Uniform meshes: requires implicit elements, FR_JAC_EVERY_NEWTON and (with a
+ * trace) FR_GMRES_FUSED.  General meshes (mixed degree, boundary faces, hexahedra, EFR): requires
+ * implicit elements; the GMRES restart cycle is the multi-kernel one, its m iterations enqueued
+ * in the graph and skipped on the device once the cycle has ended, its restart decision taken on
+ * the device, and the iteration limit checked per cycle.  FR_ERR_UNSUPPORTED otherwise.
+ * Per-phase profiling (fr_profile_*) sees no phases of a graph stage. */
 int imex_stage_set_graph(fr_ctx* ctx, int on);
 int imex_stage_get_graph(const fr_ctx* ctx);
 
