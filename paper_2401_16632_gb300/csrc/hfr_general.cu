@@ -508,7 +508,6 @@ struct JWork {
     T dqfn[GF][2], dqfp[GF][2];
     T dFt[GNS][2][NV];
     T dFnp[GF][NV], drow[GF][NV], dFnn[GF][NV];
-    T out[(GNS + GF) * NV][NV];
   } col[JW];
   T uinf[5];
   int nf[4], kf[4], tr[4], lto[4];
@@ -518,7 +517,7 @@ static_assert(sizeof(JWork<4, double>) <= 227 * 1024, "block kernel workspace ex
 static_assert(sizeof(GWork<4>) * GEPB <= 227 * 1024, "residual workspace exceeds shared memory");
 
 template <int PHYS, typename T>
-__global__ void __launch_bounds__(JT) k_gen_jacobian(const __grid_constant__ PhysParams pp,
+__global__ void __launch_bounds__(JT, sizeof(T) == 4 ? 3 : 1) k_gen_jacobian(const __grid_constant__ PhysParams pp,
                                                     const __grid_constant__ GArgs a,
                                                     const __grid_constant__ JArgs j) {
   constexpr int NV = Phys<PHYS>::NV;
@@ -848,6 +847,12 @@ __global__ void __launch_bounds__(JT) k_gen_jacobian(const __grid_constant__ Phy
       }
     }
     __syncwarp();
+    // the seed point's NV columns, written column by column (the writes of one seed point's
+    // columns meet in the same sectors in L2)
+    const int col0 = vol ? sp * NV : w.lto[f0] + q0 * NV;
+    const int ncol = vol ? nA : nT;
+    T* top = vol ? Ab : Bb;
+    T* bot = vol ? Cb : Db;
     for (int v0 = 0; v0 < NV; ++v0) {
       // flux tangents at the solution points
       for (int it = lane; it < ns * 2 * NV; it += 32) {
@@ -890,7 +895,7 @@ __global__ void __launch_bounds__(JT) k_gen_jacobian(const __grid_constant__ Phy
         for (int c = 0; c < n; ++c) d += w.M[ai][c] * cw.dFt[c + n * bi][0][v] + w.M[bi][c] * cw.dFt[ai + n * c][1][v];
         T o = w.ciJ[i] * d;
         if (vol && i == sp && v == v0) o += T(1);
-        cw.out[it][v0] = o;
+        top[(size_t)it * ncol + col0 + v0] = o;
       }
       // C / D column: the element's trace rows w_q (row tangent), zero off traces
       for (int it = lane; it < nT; it += 32) {
@@ -900,21 +905,10 @@ __global__ void __launch_bounds__(JT) k_gen_jacobian(const __grid_constant__ Phy
           ++f;
         }
         const int q = rem / NV, v = rem % NV;
-        cw.out[nA + it][v0] = w.tr[f] >= 0 ? w.wq[f][q] * cw.drow[f * GN + q][v] : T(0);
+        bot[(size_t)it * ncol + col0 + v0] = w.tr[f] >= 0 ? w.wq[f][q] * cw.drow[f * GN + q][v] : T(0);
       }
       __syncwarp();
     }
-    // the seed point's NV columns as rows of NV consecutive values
-    const int col0 = vol ? sp * NV : w.lto[f0] + q0 * NV;
-    const int ncol = vol ? nA : nT;
-    T* top = vol ? Ab : Bb;
-    T* bot = vol ? Cb : Db;
-    for (int rr = lane; rr < nA + nT; rr += 32) {
-      T* dst = rr < nA ? top + (size_t)rr * ncol + col0 : bot + (size_t)(rr - nA) * ncol + col0;
-#pragma unroll
-      for (int v0 = 0; v0 < NV; ++v0) dst[v0] = cw.out[rr][v0];
-    }
-    __syncwarp();
   }
 }
 

@@ -123,3 +123,24 @@ def test_uneven_fp32_large_blocks_take_the_blocked_lu_and_report_a_singular_elem
         pkg.hfr_condense_uneven([a for a, _ in shapes], [t for _, t in shapes], *_packed(blocks, torch.float32),
                                 precision=pkg.FR_PREC_FP32)
     assert ei.value.code == pkg.FR_ERR_SINGULAR and ei.value.failed_element == 2
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_uneven_batch_of_quadrilateral_and_hexahedral_shapes(precision):
+    """Element types mixed in one call: hexahedral Navier-Stokes blocks (p = 2: 135 / 270; p = 3:
+    320 / 480) beside quadrilateral ones, each condensed by the form its shape takes (shared-memory
+    bundles, blocked LU with the column-block solve), against the oracle's condensation."""
+    shapes = [(320, 480), (36, 48), (135, 270), (100, 80), (320, 480), (64, 64)]
+    blocks = _batch(shapes, 9)
+    prec = pkg.FR_PREC_FP64 if precision == "fp64" else pkg.FR_PREC_FP32
+    dtype = torch.float64 if precision == "fp64" else torch.float32
+    out = pkg.hfr_condense_uneven([a for a, _ in shapes], [t for _, t in shapes], *_packed(blocks, dtype), precision=prec)
+    S = _split(out["S"].cpu().numpy().astype(np.float64), [t * t for _, t in shapes])
+    XB = _split(out["XB"].cpu().numpy().astype(np.float64), [a * t for a, t in shapes])
+    xr = _split(out["xr"].cpu().numpy(), [a for a, _ in shapes])
+    tol = 1e-11 if precision == "fp64" else 2e-5
+    for k, b in enumerate(blocks):
+        XBo, xro, So, to = condense(*(x[None] for x in b))
+        assert np.abs(S[k] - So[0].reshape(-1)).max() < tol * np.abs(So).max(), (k, shapes[k])
+        assert np.abs(XB[k] - XBo[0].reshape(-1)).max() < tol * np.abs(XBo).max(), (k, shapes[k])
+        assert np.abs(xr[k] - xro[0]).max() < tol * np.abs(xro).max(), (k, shapes[k])
