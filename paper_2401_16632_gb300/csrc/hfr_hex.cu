@@ -372,7 +372,7 @@ struct HJac {
 // NC: points per line as a compile-time constant (the index arithmetic of the lines folds), or 0
 // for the element's own degree at run time
 template <typename T, int NC>
-__global__ void __launch_bounds__(HJT, 1) k_hex_jacobian(const __grid_constant__ PhysParams pp,
+__global__ void __launch_bounds__(HJT, sizeof(T) == 4 ? 2 : 1) k_hex_jacobian(const __grid_constant__ PhysParams pp,
                                                         const __grid_constant__ GArgs a,
                                                         const __grid_constant__ JArgs j) {
   using DT = Dual<T>;
