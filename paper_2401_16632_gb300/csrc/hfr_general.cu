@@ -241,8 +241,9 @@ __global__ void __launch_bounds__(32 * GEPB) k_gen_elem(const __grid_constant__ 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   GWork<NV>& w = reinterpret_cast<GWork<NV>*>(smem_raw)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
-  const int e = blockIdx.x * GEPB + (threadIdx.x >> 5);
-  if (e >= a.E) return;  // whole warps leave; only warp-level synchronisation below
+  const int idx = blockIdx.x * GEPB + (threadIdx.x >> 5);
+  if (idx >= (a.elist ? a.nlist : a.E)) return;  // whole warps leave; only warp-level synchronisation below
+  const int e = a.elist ? a.elist[idx] : idx;
   const int n = a.deg[e], ns = n * n;
   const GenRef& RF = *a.ref;
   const bool visc = phys_viscous(pp);
@@ -1583,12 +1584,15 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
     g->pmax = std::max(g->pmax, deg[e] - 1);
   }
   g->nstate = (size_t)uoff[E];
-  std::vector<int> imp_idx, comp(E, -1);
+  std::vector<int> imp_idx, exp_idx, comp(E, -1);
   for (int e = 0; e < E; ++e)
     if (mesh->implicit[e]) {
       comp[e] = (int)imp_idx.size();
       imp_idx.push_back(e);
+    } else {
+      exp_idx.push_back(e);
     }
+  g->Eex = (int)exp_idx.size();
   const int Eim = (int)imp_idx.size();
   g->Eim = Eim;
   std::vector<int> nAk(std::max(Eim, 1)), nTk(std::max(Eim, 1)), lto(NF * (size_t)std::max(Eim, 1));
@@ -1780,6 +1784,7 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
   g->pside = galloc<int>(g, pside.size(), &rc);
   g->poff = galloc<long long>(g, nt + 1, &rc);
   g->imp_idx = galloc<int>(g, std::max(Eim, 1), &rc);
+  g->exp_list = galloc<int>(g, std::max(g->Eex, 1), &rc);
   g->lto = galloc<int>(g, lto.size(), &rc);
   g->nAk = galloc<int>(g, nAk.size(), &rc);
   g->nTk = galloc<int>(g, nTk.size(), &rc);
@@ -1865,6 +1870,7 @@ int create(const fr_mesh_desc* mesh, const fr_config* cfg, cudaStream_t st, cons
   GUP(g->pside, pside.data(), pside.size());
   GUP(g->poff, poff.data(), poff.size());
   GUP(g->imp_idx, imp_idx.data(), imp_idx.size());
+  if (!exp_idx.empty()) GUP(g->exp_list, exp_idx.data(), exp_idx.size());
   GUP(g->lto, lto.data(), lto.size());
   GUP(g->nAk, nAk.data(), nAk.size());
   GUP(g->nTk, nTk.data(), nTk.size());
@@ -2014,7 +2020,7 @@ static cudaError_t launch_gen_elem(GenCtx* g, const GArgs& a) {
   auto kern = k_gen_elem<PHYS, MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int grid = (a.E + GEPB - 1) / GEPB;
+  const int grid = ((a.elist ? a.nlist : a.E) + GEPB - 1) / GEPB;
   if (grid == 0) return cudaSuccess;
   (count_launch(), kern<<<grid, 32 * GEPB, smem, g->st>>>(g->pp, a));
   return cudaGetLastError();
@@ -2042,6 +2048,58 @@ static int residual_into(GenCtx* g, const double* u, const double* uhat, double*
                                                                        g_out, (long long)g->nface * g->E * g->fs));
     GCK(cudaGetLastError());
   }
+  pend(g, ph);
+  return FR_OK;
+}
+
+// The residual inside the Newton loop of a stage.  The explicit elements' states are fixed during
+// the loop, and so are their face states and gradients: an implicit element reads them at its
+// interface faces, while an explicit element takes its own state there.  So the explicit
+// elements' face passes run once before the loop (stage_res_prepare), each Newton iterate
+// evaluates the implicit elements alone (stage_res_newton: R and the trace rows), and once the loop
+// ends the implicit elements' face passes and the explicit elements' residual at the final state
+// complete R (stage_res_finish), as a full residual_into would.
+static GArgs gargs_list(GenCtx* g, const double* u, const double* uhat, const int* list, int n) {
+  GArgs a = gargs(g, u, uhat);
+  a.elist = list;
+  a.nlist = n;
+  return a;
+}
+static int stage_res_prepare(GenCtx* g, const double* u) {
+  if (!g->need_nbr || g->Eex == 0) return FR_OK;
+  const int ph = pbeg(g, 0);
+  GArgs a = gargs_list(g, u, nullptr, g->exp_list, g->Eex);
+  GCK(gen_elem<GM_UF>(g, a));
+  GCK(gen_elem<GM_QF>(g, a));
+  pend(g, ph);
+  return FR_OK;
+}
+static int stage_res_newton(GenCtx* g, const double* u, const double* uhat) {
+  const int ph = pbeg(g, 0);
+  GArgs a = gargs_list(g, u, uhat, g->imp_idx, g->Eim);
+  a.R = g->Rw;
+  a.gview = g->gview;
+  if (g->Eim) GCK(gen_elem<GM_RES>(g, a));
+  if (g->ntrace) {
+    (count_launch(), k_gen_trace_sum<<<nb256(g->nh), 256, 0, g->st>>>(g->npts, g->nv, g->gptr, g->gidx, g->gview,
+                                                                       g->gw, (long long)g->nface * g->E * g->fs));
+    GCK(cudaGetLastError());
+  }
+  pend(g, ph);
+  return FR_OK;
+}
+static int stage_res_finish(GenCtx* g, const double* u, const double* uhat) {
+  if (g->Eex == 0) return FR_OK;
+  const int ph = pbeg(g, 0);
+  if (g->need_nbr && g->Eim) {
+    GArgs ai = gargs_list(g, u, uhat, g->imp_idx, g->Eim);
+    GCK(gen_elem<GM_UF>(g, ai));
+    GCK(gen_elem<GM_QF>(g, ai));
+  }
+  GArgs a = gargs_list(g, u, uhat, g->exp_list, g->Eex);
+  a.R = g->Rw;
+  a.gview = g->gview;
+  GCK(gen_elem<GM_RES>(g, a));
   pend(g, ph);
   return FR_OK;
 }
@@ -2487,6 +2545,7 @@ static int stage_graph_capture(GenCtx* g, const GenCtx::GKey& key) {
   (count_launch(), k_gs_init<<<1, 1, 0, g->st>>>(sd));
   SK(cudaGetLastError());
   const double adt = key.dt * tb.a[i - 1][i - 1];
+  SR(stage_res_prepare(g, u_stage));
   cudaGraphConditionalHandle hn, hs;
   SK(graph_conditional_handle(g->cap[0], 1u, cudaGraphCondAssignDefault, &hn));
   SK(graph_add_conditional(g->cap[0], hn, cudaGraphCondTypeWhile, &bn));
@@ -2496,7 +2555,7 @@ static int stage_graph_capture(GenCtx* g, const GenCtx::GKey& key) {
   depth = 2;
   g->st = g->cap[1];
   SK(graph_conditional_handle(g->cap[1], 0u, 0u, &hs));
-  SR(residual_into(g, u_stage, uhat, g->Rw, g->gw));
+  SR(stage_res_newton(g, u_stage, uhat));
   SR(form_rhs(g, u_stage, g->Ustar, adt));
   {
     const int nbk = 256;
@@ -2547,6 +2606,7 @@ static int stage_graph_capture(GenCtx* g, const GenCtx::GKey& key) {
   SK(cudaStreamEndCapture(g->cap[1], &bn));
   depth = 1;
   g->st = g->cap[0];
+  SR(stage_res_finish(g, u_stage, uhat));
   SK(cudaMemcpyAsync(const_cast<double*>(key.R_hist) + (size_t)i * tot, g->Rw, tot * sizeof(double),
                      cudaMemcpyDeviceToDevice, g->st));
   SK(cudaStreamEndCapture(g->cap[0], &gr));
@@ -2669,8 +2729,12 @@ int stage(GenCtx* g, int stage, double dt, const double* u_n, double* u_stage, d
   double norm0 = -1.0, normk = 0.0;
   int it = 0, gtot = 0;
   bool conv = false;
+  {
+    const int rc = stage_res_prepare(g, u_stage);
+    if (rc) return rc;
+  }
   for (;; ++it) {
-    int rc = residual_into(g, u_stage, uhat, g->Rw, g->gw);
+    int rc = stage_res_newton(g, u_stage, uhat);
     const int phn = pbeg(g, 6);
     if (!rc) rc = form_rhs(g, u_stage, g->Ustar, adt);
     double ss = 0.0;
@@ -2707,6 +2771,10 @@ int stage(GenCtx* g, int stage, double dt, const double* u_n, double* u_stage, d
       GCK(cudaGetLastError());
     }
     pend(g, phu);
+  }
+  {
+    const int rc = stage_res_finish(g, u_stage, uhat);  // R of the explicit elements at the final state
+    if (rc) return rc;
   }
   GCK(cudaMemcpyAsync(R_hist + (size_t)i * tot, g->Rw, tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
   GCK(cudaStreamSynchronize(st));

@@ -57,6 +57,8 @@ struct GArgs {
   double uinf[5];
   int nface, fs;          // faces per element, face-point stride per face
   long long npts;         // trace points (bound of fnode in the checked build)
+  const int* elist;       // nullable: the elements of this pass (nlist of them) instead of 0..E-1
+  int nlist;
 };
 
 
@@ -112,6 +114,8 @@ struct GenCtx {
   void *A = nullptr, *B = nullptr, *C = nullptr, *D = nullptr, *LU = nullptr, *XB = nullptr, *S = nullptr, *Pinv = nullptr;
   int* piv = nullptr;
   int* status = nullptr;
+  int* exp_list = nullptr;  // the explicit elements (Eex)
+  int Eex = 0;
   UnevenDev udev;
   // FP32 quadrilaterals: shape classes with the fixed-shape tensor-core condensation, condensed
   // through a contiguous scratch batch (the other elements by the uneven launch)

@@ -180,8 +180,8 @@ template <int MODE>
 __global__ void __launch_bounds__(HT) k_hex_elem(const __grid_constant__ PhysParams pp, const __grid_constant__ GArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   HWork& w = *reinterpret_cast<HWork*>(smem_raw);
-  const int e = blockIdx.x;
-  if (e >= a.E) return;
+  if ((int)blockIdx.x >= (a.elist ? a.nlist : a.E)) return;
+  const int e = a.elist ? a.elist[blockIdx.x] : (int)blockIdx.x;
   const int tid = threadIdx.x;
   const int n = a.deg[e], ns = n * n * n, nf = n * n, FS = a.fs;
   const GenRef& RF = *a.ref;
@@ -334,8 +334,9 @@ cudaError_t hex_elem_pass(GenCtx* g, const GArgs& a, int mode) {
   cudaError_t e;
   auto kern = mode == GM_UF ? k_hex_elem<GM_UF> : (mode == GM_QF ? k_hex_elem<GM_QF> : k_hex_elem<GM_RES>);
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-  if (a.E == 0) return cudaSuccess;
-  (count_launch(), kern<<<a.E, HT, smem, g->st>>>(g->pp, a));
+  const int cnt = a.elist ? a.nlist : a.E;
+  if (cnt == 0) return cudaSuccess;
+  (count_launch(), kern<<<cnt, HT, smem, g->st>>>(g->pp, a));
   return cudaGetLastError();
 }
 
